@@ -1,0 +1,300 @@
+"""Seeded synthetic inputs for the Richards solver.
+
+This module only *describes* problems: grid sizes, soil parameters, boundary
+descriptors, sink parameters, initial states and time-step settings.  It holds
+none of the method's arithmetic (no constitutive law, no operator, no solver),
+so that both the CUDA path and the CPU oracle can consume the same inputs
+without sharing any code that computes a result.
+
+Problem layout (a plain ``dict``):
+
+* ``dim``: 1, 2 or 3.  The last active axis (``dim-1``) is the vertical axis,
+  with elevation ``z`` increasing upward (the bottom face is ``z = 0``).
+* ``n``: cells per axis, a 3-tuple; axes ``>= dim`` have ``n = 1``.
+* ``L``: domain length per axis (the units of the problem; cm for the
+  Celia column, m elsewhere).
+* ``soil``: ``model`` (``HAVERKAMP``/``GARDNER``/``VANGENUCHTEN``), scalars
+  ``Ks, theta_s, theta_r, p1..p4`` and optional per-cell fields
+  ``Ks_field, p1_field, p2_field`` (x-fastest, float64).
+  Parameter meaning per model (Table 1 of the paper):
+  Haverkamp p1=alpha, p2=beta, p3=A, p4=gamma; Gardner p1=alpha;
+  van Genuchten p1=alpha, p2=n, p3=l (pore-connectivity, 0.5).
+* ``bc``: per face ``2*axis+side`` (side 0 = low end, 1 = high end):
+  ``kind`` (``DIRICHLET``/``NOFLUX``/``FLUX``/``FREE_DRAINAGE``), ``value``
+  (head for Dirichlet, inflow rate for flux), optional ``value_field`` and
+  ``mask_field`` over the face cells (lexicographic over the other axes).
+* ``sink``: Feddes-type root-water-uptake parameters (``enabled``, ``Tp``,
+  ``root_depth``, ``root_decay``, ``h1..h4``).
+* ``psi0`` (and optionally ``psi_prev``): initial state, float64, x-fastest.
+* ``dt``, ``nsteps``, ``scheme`` (1 = BDF1, 2 = BDF2).
+* ``opts``: solver options (sweeps, kappa mode, xi, tolerance, ...).
+
+Per-cell soil fields are rounded to float32-representable doubles so that a
+float32 copy on the device is exact; the CPU oracle reads the same values.
+"""
+from __future__ import annotations
+
+import copy
+import math
+
+import numpy as np
+
+HAVERKAMP, GARDNER, VANGENUCHTEN = 0, 1, 2
+DIRICHLET, NOFLUX, FLUX, FREE_DRAINAGE = 0, 1, 2, 3
+
+MODEL_NAMES = {HAVERKAMP: "haverkamp", GARDNER: "gardner", VANGENUCHTEN: "vangenuchten"}
+
+# 5 mm/day of potential transpiration, in m/s.
+TP_5MM_PER_DAY = 5.0e-3 / 86400.0
+
+
+def f32exact(x):
+    """Round to the nearest float32 and return float64 (exactly representable)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def default_opts(**kw):
+    o = dict(nu1=2, nu2=2, coarse_max_sweeps=50, coarse_rtol=0.1,
+             coarsest_max_n=4, max_levels=0,
+             kappa_mode=0, kappa=0.0, xi=0.0,
+             tol=1e-8, max_cycles=60,
+             ordering=1,          # 0 = lexicographic, 1 = red-black
+             newton_iters=2,      # 0 = to tolerance; k > 0 = exactly k steps
+             precision=0,         # 0 = FP64 plain, 1 = FP32 inner / FP64 outer
+             inner_cycles=2, inner_rtol=1e-3, max_outer=20,
+             tail_cells=4096)
+    o.update(kw)
+    return o
+
+
+def no_sink():
+    return dict(enabled=0, Tp=0.0, root_depth=0.3, root_decay=0.1,
+                h1=-0.10, h2=-0.25, h3=-5.0, h4=-80.0)
+
+
+def feddes_sink(Tp=TP_5MM_PER_DAY):
+    return dict(enabled=1, Tp=Tp, root_depth=0.3, root_decay=0.1,
+                h1=-0.10, h2=-0.25, h3=-5.0, h4=-80.0)
+
+
+def _bc(kinds, values=None):
+    kinds = list(kinds) + [NOFLUX] * (6 - len(kinds))
+    values = list(values or []) + [0.0] * (6 - len(values or []))
+    return dict(kind=kinds, value=values, value_field=[None] * 6, mask_field=[None] * 6)
+
+
+def _soil(model, Ks, theta_s, theta_r, p1=0.0, p2=0.0, p3=0.0, p4=0.0,
+          Ks_field=None, p1_field=None, p2_field=None):
+    return dict(model=model, Ks=float(Ks), theta_s=float(theta_s), theta_r=float(theta_r),
+                p1=float(p1), p2=float(p2), p3=float(p3), p4=float(p4),
+                Ks_field=Ks_field, p1_field=p1_field, p2_field=p2_field)
+
+
+def ncells(prob):
+    n = prob["n"]
+    return int(n[0] * n[1] * n[2])
+
+
+# ---------------------------------------------------------------------------
+# The paper's 1D Celia/Haverkamp column (Section 4.1, Table 2), in cm and s.
+# ---------------------------------------------------------------------------
+def celia_1d(n=128, dt=10.0, nsteps=36, **optkw):
+    soil = _soil(HAVERKAMP, Ks=0.00944, theta_s=0.287, theta_r=0.075,
+                 p1=1.611e6, p2=3.96, p3=1.175e6, p4=4.74)
+    bc = _bc([DIRICHLET, DIRICHLET], [-61.5, -20.7])   # bottom, top (cm)
+    # The paper's shift kappa = 0.1 goes with its tau = 0.1 s; at dt = 10 s it
+    # under-relaxes the dry cells so strongly that the cycles stall, so the
+    # 10 s workload uses kappa = 0 (pass kappa=0.1, dt=0.1 for the paper's run).
+    opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0)
+    opts.update(optkw)
+    return dict(name=f"celia1d_n{n}", dim=1, n=(n, 1, 1), L=(40.0, 1.0, 1.0),
+                soil=soil, bc=bc, sink=no_sink(),
+                psi0=np.full(n, -61.5), psi_prev=None,
+                dt=dt, nsteps=nsteps, scheme=1, opts=opts)
+
+
+# ---------------------------------------------------------------------------
+# 2D strip infiltration (513^2 over 1 m^2, van Genuchten), in m and s.
+# ---------------------------------------------------------------------------
+def strip_2d(n=513, dt=60.0, nsteps=100, **optkw):
+    soil = _soil(VANGENUCHTEN, Ks=1e-5, theta_s=0.368, theta_r=0.102,
+                 p1=3.35, p2=2.0, p3=0.5)
+    # axis 0 = x, axis 1 = z (vertical).  Faces: 0 x-low, 1 x-high, 2 bottom, 3 top.
+    bc = _bc([NOFLUX, NOFLUX, DIRICHLET, DIRICHLET], [0.0, 0.0, -10.0, -0.1])
+    h = 1.0 / n
+    xc = (np.arange(n) + 0.5) * h
+    bc["mask_field"][3] = (np.abs(xc - 0.5) <= 0.1).astype(np.uint8)
+    opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0)
+    opts.update(optkw)
+    return dict(name=f"strip2d_n{n}", dim=2, n=(n, n, 1), L=(1.0, 1.0, 1.0),
+                soil=soil, bc=bc, sink=no_sink(),
+                psi0=np.full(n * n, -10.0), psi_prev=None,
+                dt=dt, nsteps=nsteps, scheme=2, opts=opts)
+
+
+def gaussian_log_field(shape, corr_cells, seed):
+    """Standardised Gaussian random field with covariance ~ exp(-r^2/corr^2).
+
+    White noise (seeded PCG64) convolved, with periodic wrap via FFT, with a
+    Gaussian kernel of standard deviation corr/sqrt(2) cells; then shifted and
+    scaled to sample mean 0 and standard deviation 1.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = rng.standard_normal(shape)
+    s = corr_cells / math.sqrt(2.0)
+    F = np.fft.rfftn(w)
+    freqs = [np.fft.fftfreq(m) for m in shape[:-1]] + [np.fft.rfftfreq(shape[-1])]
+    grids = np.meshgrid(*freqs, indexing="ij")
+    k2 = sum(g * g for g in grids)
+    F *= np.exp(-2.0 * (math.pi ** 2) * (s ** 2) * k2)
+    G = np.fft.irfftn(F, s=shape)
+    G = (G - G.mean()) / G.std()
+    return G
+
+
+# ---------------------------------------------------------------------------
+# 3D drainage (256^3 over 1 m^3, heterogeneous van Genuchten), m and s.
+# ---------------------------------------------------------------------------
+def drainage_3d(n=256, dt=300.0, nsteps=50, seed_ks=3, seed_vg=4, **optkw):
+    shape_zyx = (n, n, n)
+    G = gaussian_log_field(shape_zyx, 8.0, seed_ks)          # indexed [z, y, x]
+    Ks = f32exact(np.exp(math.log(1e-5) + 1.0 * G)).reshape(-1)   # x fastest
+    rng = np.random.Generator(np.random.PCG64(seed_vg))
+    alpha = f32exact(rng.uniform(2.0, 5.0, n ** 3))
+    nvg = f32exact(rng.uniform(1.5, 2.5, n ** 3))
+    soil = _soil(VANGENUCHTEN, Ks=1e-5, theta_s=0.368, theta_r=0.102,
+                 p1=3.5, p2=2.0, p3=0.5, Ks_field=Ks, p1_field=alpha, p2_field=nvg)
+    # faces: x-low, x-high, y-low, y-high, bottom (free drainage), top (no flux)
+    bc = _bc([NOFLUX, NOFLUX, NOFLUX, NOFLUX, FREE_DRAINAGE, NOFLUX])
+    opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0, precision=1)
+    opts.update(optkw)
+    return dict(name=f"drainage3d_n{n}", dim=3, n=(n, n, n), L=(1.0, 1.0, 1.0),
+                soil=soil, bc=bc, sink=no_sink(),
+                psi0=np.zeros(n ** 3), psi_prev=None,
+                dt=dt, nsteps=nsteps, scheme=2, opts=opts)
+
+
+# ---------------------------------------------------------------------------
+# Batched root-uptake columns (lengths U{64..1024} over 1 m), m and s.
+# ---------------------------------------------------------------------------
+def columns(ncol=4096, seed=5, dt=600.0, nsteps=144, nmin=64, nmax=1024, **optkw):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lengths = rng.integers(nmin, nmax + 1, ncol)
+    alpha = f32exact(rng.uniform(0.5, 5.0, ncol))
+    nvg = f32exact(rng.uniform(1.2, 3.0, ncol))
+    Ks = f32exact(np.exp(rng.uniform(math.log(1e-7), math.log(1e-4), ncol)))
+    out = []
+    for c in range(ncol):
+        m = int(lengths[c])
+        soil = _soil(VANGENUCHTEN, Ks=Ks[c], theta_s=0.368, theta_r=0.102,
+                     p1=alpha[c], p2=nvg[c], p3=0.5)
+        bc = _bc([FREE_DRAINAGE, FLUX], [0.0, 0.0])
+        opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0, precision=1)
+        opts.update(optkw)
+        out.append(dict(name=f"column{c}_n{m}", dim=1, n=(m, 1, 1), L=(1.0, 1.0, 1.0),
+                        soil=soil, bc=bc, sink=feddes_sink(),
+                        psi0=np.full(m, -1.0), psi_prev=None,
+                        dt=dt, nsteps=nsteps, scheme=1, opts=opts))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Serving trace: Poisson arrivals of mixed 2D/3D solves.
+# ---------------------------------------------------------------------------
+def serving_trace(rate=200.0, seconds=60.0, seed=6, sizes2d=(129, 257, 513, 1025),
+                  sizes3d=(65, 129, 257), max_requests=None):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    reqs = []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        if max_requests is not None and len(reqs) >= max_requests:
+            break
+        is3d = rng.random() < 0.5
+        n = int(rng.choice(sizes3d if is3d else sizes2d))
+        model = int(rng.integers(0, 3))
+        Ks = float(f32exact(math.exp(rng.uniform(math.log(1e-7), math.log(1e-4)))))
+        if model == HAVERKAMP:
+            s = rng.uniform(0.8, 1.2)
+            # C1 parameters converted from cm to m: A*100^-gamma, alpha*100^-beta
+            soil = _soil(HAVERKAMP, Ks, 0.287, 0.075, p1=1.611e6 * 100.0 ** -3.96 * s,
+                         p2=3.96, p3=1.175e6 * 100.0 ** -4.74 * s, p4=4.74)
+        elif model == GARDNER:
+            soil = _soil(GARDNER, Ks, 0.368, 0.102, p1=float(rng.uniform(1.0, 5.0)))
+        else:
+            soil = _soil(VANGENUCHTEN, Ks, 0.368, 0.102, p1=float(rng.uniform(0.5, 5.0)),
+                         p2=float(rng.uniform(1.2, 3.0)), p3=0.5)
+        steps = int(rng.integers(20, 201))
+        sink = feddes_sink() if rng.random() < 0.5 else no_sink()
+        if is3d:
+            bc = _bc([NOFLUX, NOFLUX, NOFLUX, NOFLUX, FREE_DRAINAGE, DIRICHLET],
+                     [0, 0, 0, 0, 0, -0.1])
+            prob = dict(name=f"req{len(reqs)}_3d_n{n}", dim=3, n=(n, n, n), L=(1.0, 1.0, 1.0),
+                        psi0=np.full(n ** 3, -1.0), dt=300.0)
+        else:
+            bc = _bc([NOFLUX, NOFLUX, DIRICHLET, DIRICHLET], [0, 0, -10.0, -0.1])
+            h = 1.0 / n
+            xc = (np.arange(n) + 0.5) * h
+            bc["mask_field"][3] = (np.abs(xc - 0.5) <= 0.1).astype(np.uint8)
+            prob = dict(name=f"req{len(reqs)}_2d_n{n}", dim=2, n=(n, n, 1), L=(1.0, 1.0, 1.0),
+                        psi0=np.full(n * n, -10.0 if not sink["enabled"] else -1.0), dt=60.0)
+        prob.update(soil=soil, bc=bc, sink=sink, psi_prev=None, nsteps=steps, scheme=2,
+                    opts=default_opts(precision=1), arrival=t)
+        reqs.append(prob)
+    return reqs
+
+
+# ---------------------------------------------------------------------------
+# Small random problems for parity tests (odd sizes, every BC kind and model).
+# ---------------------------------------------------------------------------
+def random_problem(dim, n, model, seed, bc_kinds=None, hetero=False, sink=False,
+                   psi_range=(-2.0, -0.05), L=1.0, dt=60.0, scheme=1, **optkw):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nn = [1, 1, 1]
+    for a in range(dim):
+        nn[a] = int(n[a]) if hasattr(n, "__len__") else int(n)
+    N = nn[0] * nn[1] * nn[2]
+    if model == HAVERKAMP:
+        soil = _soil(HAVERKAMP, 1e-5, 0.287, 0.075, p1=1.611e6 * 100.0 ** -3.96,
+                     p2=3.96, p3=1.175e6 * 100.0 ** -4.74, p4=4.74)
+        if hetero:
+            soil["p1_field"] = f32exact(soil["p1"] * rng.uniform(0.7, 1.3, N))
+            soil["p2_field"] = f32exact(rng.uniform(3.0, 4.5, N))
+    elif model == GARDNER:
+        soil = _soil(GARDNER, 1e-5, 0.45, 0.15, p1=2.0)
+        if hetero:
+            soil["p1_field"] = f32exact(rng.uniform(1.0, 5.0, N))
+    else:
+        soil = _soil(VANGENUCHTEN, 1e-5, 0.368, 0.102, p1=3.35, p2=2.0, p3=0.5)
+        if hetero:
+            soil["p1_field"] = f32exact(rng.uniform(2.0, 5.0, N))
+            soil["p2_field"] = f32exact(rng.uniform(1.5, 2.5, N))
+    if hetero:
+        soil["Ks_field"] = f32exact(np.exp(np.log(1e-5) + rng.standard_normal(N)))
+    if bc_kinds is None:
+        bc_kinds = [NOFLUX] * (2 * dim - 2) + [FREE_DRAINAGE, DIRICHLET]
+    vals = []
+    for k in bc_kinds:
+        if k == DIRICHLET:
+            vals.append(float(rng.uniform(*psi_range)))
+        elif k == FLUX:
+            vals.append(float(rng.uniform(0.0, 2e-6)))
+        else:
+            vals.append(0.0)
+    bc = _bc(bc_kinds, vals)
+    psi0 = rng.uniform(psi_range[0], psi_range[1], N)
+    opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0)
+    opts.update(optkw)
+    return dict(name=f"rand{dim}d_m{model}_s{seed}", dim=dim, n=tuple(nn),
+                L=(L, L, L), soil=soil, bc=bc,
+                sink=feddes_sink(Tp=TP_5MM_PER_DAY * 50) if sink else no_sink(),
+                psi0=psi0, psi_prev=None, dt=dt, nsteps=3, scheme=scheme, opts=opts)
+
+
+def with_opts(prob, **kw):
+    p = copy.copy(prob)
+    p["opts"] = dict(prob["opts"])
+    p["opts"].update(kw)
+    return p

@@ -1,0 +1,511 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed-form discrete steady states, the structural results of
+Section 3 (Prop. 3.1, Lemma 3.1, Theorem 3.1), exact conservation, a
+brute-force Newton solve of the whole system, and convergence orders.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+from oracle.dense import dense_newton
+from oracle.oracle import ORC_OK, Oracle
+from paper_2606_04292_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+CELIA = dict(Ks=0.00944, theta_s=0.287, theta_r=0.075, alpha=1.611e6, beta=3.96,
+             A=1.175e6, gamma=4.74)
+
+
+def load_golden(name):
+    vals = {}
+    with open(os.path.join(HERE, "golden", name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            k, v, dec = line.split()
+            vals[k] = (float(v), int(dec))
+    return vals
+
+
+def soil_probe(model, Ks, theta_s, theta_r, p1=0.0, p2=0.0, p3=0.0, p4=0.0):
+    """A two-cell column carrying one soil; used to evaluate the laws."""
+    p = W.random_problem(1, 2, W.GARDNER, 0)
+    p["soil"] = W._soil(model, Ks, theta_s, theta_r, p1, p2, p3, p4)
+    return Oracle(p)
+
+
+def haverkamp_probe():
+    c = CELIA
+    return soil_probe(W.HAVERKAMP, c["Ks"], c["theta_s"], c["theta_r"], c["alpha"], c["beta"],
+                      c["A"], c["gamma"])
+
+
+# ---------------------------------------------------------------------------
+# Constitutive laws (Table 1) pinned by the paper's printed calibration.
+# ---------------------------------------------------------------------------
+def test_haverkamp_half_suction_points():
+    g = load_golden("calibration.txt")
+    c = CELIA
+    o = haverkamp_probe()
+    h_th = c["alpha"] ** (1.0 / c["beta"])
+    h_K = c["A"] ** (1.0 / c["gamma"])
+    assert round(h_th, g["h_theta_half"][1]) == g["h_theta_half"][0]
+    assert round(h_K, g["h_K_half"][1]) == g["h_K_half"][0]
+    th, _, _ = o.soil(0, -h_th)
+    _, _, K = o.soil(0, -h_K)
+    assert abs(th - 0.5 * (c["theta_s"] + c["theta_r"])) <= 1e-15
+    assert abs(K - 0.5 * c["Ks"]) <= 1e-17
+
+
+def test_gardner_calibration():
+    g = load_golden("calibration.txt")
+    c = CELIA
+    h_th = c["alpha"] ** (1.0 / c["beta"])
+    aG = math.log(2.0) / h_th
+    assert round(aG, g["alpha_G"][1]) == g["alpha_G"][0]
+    o = soil_probe(W.GARDNER, c["Ks"], c["theta_s"], c["theta_r"], p1=aG)
+    th, _, K = o.soil(0, -h_th)
+    assert abs(th - 0.5 * (c["theta_s"] + c["theta_r"])) <= 1e-15
+    assert abs(K - 0.5 * c["Ks"]) <= 1e-17
+
+
+def test_van_genuchten_calibration():
+    """The root n* of K_VG(h^K_1/2) = Ks/2 with alpha_VG(n) fixing the WRC
+    half point reproduces the printed n*, alpha_VG and m (pins the VG WRC and
+    the Mualem HCF with l = 0.5)."""
+    g = load_golden("calibration.txt")
+    c = CELIA
+    h_th = c["alpha"] ** (1.0 / c["beta"])
+    h_K = c["A"] ** (1.0 / c["gamma"])
+
+    def alpha_of(n):
+        m = 1.0 - 1.0 / n
+        return (2.0 ** (1.0 / m) - 1.0) ** (1.0 / n) / h_th
+
+    def f(n):
+        o = soil_probe(W.VANGENUCHTEN, c["Ks"], c["theta_s"], c["theta_r"],
+                       p1=alpha_of(n), p2=n, p3=g["l_VG"][0])
+        th, _, _ = o.soil(0, -h_th)
+        assert abs(th - 0.5 * (c["theta_s"] + c["theta_r"])) <= 1e-14
+        _, _, K = o.soil(0, -h_K)
+        return K / c["Ks"] - 0.5
+
+    n_star = brentq(f, 1.2, 10.0, xtol=1e-14)
+    assert round(n_star, g["n_star"][1]) == g["n_star"][0]
+    assert round(alpha_of(n_star), g["alpha_VG"][1]) == g["alpha_VG"][0]
+    assert round(1.0 - 1.0 / n_star, g["m_VG"][1]) == g["m_VG"][0]
+
+
+@pytest.mark.parametrize("model", [W.HAVERKAMP, W.GARDNER, W.VANGENUCHTEN])
+def test_theta_derivative_matches_central_difference(model):
+    p = W.random_problem(1, 4, model, 3)
+    o = Oracle(p)
+    for psi in [-5.0, -1.3, -0.37, -0.05, -0.004]:
+        h = 1e-4 * abs(psi)
+        tp, _, _ = o.soil(0, psi + h)
+        tm, _, _ = o.soil(0, psi - h)
+        th, d, _ = o.soil(0, psi)
+        fd = (tp - tm) / (2 * h)
+        # truncation O(h^2) plus the round-off of differencing theta ~ theta_s
+        tol = 1e-6 * abs(d) + 8 * np.finfo(float).eps * th / h
+        assert abs(d - fd) <= tol, (psi, d, fd)
+        assert d > 0.0
+    # saturated branch: theta_s, Ks, zero capacity (reading for psi >= 0)
+    th, d, K = o.soil(0, 0.3)
+    assert th == p["soil"]["theta_s"] and d == 0.0 and K == p["soil"]["Ks"]
+
+
+@pytest.mark.parametrize("model", [W.HAVERKAMP, W.GARDNER, W.VANGENUCHTEN])
+def test_theta_monotone_and_bounded(model):
+    """Assumption (A1) on psi < 0: theta increasing, theta_r < theta < theta_s."""
+    o = Oracle(W.random_problem(1, 4, model, 4))
+    s = o.prob["soil"]
+    psis = -np.logspace(-4, 2, 200)[::-1]
+    ths = [o.soil(0, x)[0] for x in psis]
+    assert all(s["theta_r"] <= t < s["theta_s"] for t in ths[:-1])
+    assert all(np.diff(ths) >= 0)
+
+
+def test_sink_reading_shape():
+    """Feddes reading of S: zero when over-wet or too dry, increasing on the
+    rising branch [h4, h3] (assumption A2), right derivatives at kinks."""
+    p = W.random_problem(1, 8, W.VANGENUCHTEN, 5, sink=True)
+    o = Oracle(p)
+    k = p["sink"]
+    cell = p["n"][0] - 1        # top cell, inside the root zone
+    S_mid, _ = o.sink(cell, -1.0)
+    assert S_mid > 0
+    for psi, expect in [(k["h1"], 0.0), (0.5 * (k["h1"] + k["h2"]), 0.5 * S_mid),
+                        (k["h2"], S_mid), (k["h3"], S_mid),
+                        (0.5 * (k["h3"] + k["h4"]), 0.5 * S_mid), (k["h4"], 0.0), (-100.0, 0.0)]:
+        S, _ = o.sink(cell, psi)
+        assert abs(S - expect) <= 1e-15 * S_mid + 1e-30, (psi, S, expect)
+    for psi in [-40.0, -3.0, -0.2]:
+        h = 1e-7
+        Sp, _ = o.sink(cell, psi + h)
+        S0, dS = o.sink(cell, psi)
+        assert abs((Sp - S0) / h - dS) <= 1e-6 * S_mid
+    _, dS = o.sink(cell, -40.0)
+    assert dS > 0          # rising branch (A2)
+
+
+# ---------------------------------------------------------------------------
+# Operator assembly: Prop. 3.1 and closed-form discrete steady states.
+# ---------------------------------------------------------------------------
+BC_SETS = {
+    1: [[W.DIRICHLET, W.DIRICHLET], [W.FREE_DRAINAGE, W.FLUX], [W.FREE_DRAINAGE, W.DIRICHLET]],
+    2: [[W.NOFLUX, W.NOFLUX, W.DIRICHLET, W.DIRICHLET],
+        [W.DIRICHLET, W.NOFLUX, W.FREE_DRAINAGE, W.FLUX]],
+    3: [[W.NOFLUX] * 4 + [W.FREE_DRAINAGE, W.DIRICHLET],
+        [W.DIRICHLET] * 6],
+}
+SIZES = {1: (7,), 2: (5, 6), 3: (3, 4, 5)}
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("bci", [0, 1])
+def test_prop31_matrix_structure(dim, bci):
+    """Prop. 3.1: m_ii > 0, m_ij >= 0 (M has -m_ij off the diagonal) and the
+    off-diagonal row sum equals m_ii on rows without a Dirichlet face; M is
+    symmetric.  Checked on every level of the hierarchy."""
+    kinds = BC_SETS[dim][bci % len(BC_SETS[dim])]
+    p = W.random_problem(dim, SIZES[dim], W.VANGENUCHTEN, 7 + bci, bc_kinds=kinds, hetero=True)
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    for lev in range(o.nlevels):
+        M = o.dense_M(lev)
+        n = M.shape[0]
+        assert np.all(np.diag(M) > 0)
+        off = M - np.diag(np.diag(M))
+        assert np.all(off <= 0)
+        assert np.allclose(M, M.T, rtol=1e-14, atol=0)
+        excess = M.sum(axis=1)       # m_ii - sum_{j != i} m_ij >= 0
+        assert np.all(excess >= -1e-15 * np.abs(np.diag(M)))
+        # interior rows (all faces interior) have zero excess
+        nn = o.level_n(lev)
+        for i in range(n):
+            ii = (i % nn[0], (i // nn[0]) % nn[1], i // (nn[0] * nn[1]))
+            interior = all(0 < ii[a] < nn[a] - 1 for a in range(dim))
+            if interior:
+                assert abs(excess[i]) <= 1e-14 * M[i, i]
+
+
+@pytest.mark.parametrize("dim,model", [(1, W.HAVERKAMP), (2, W.VANGENUCHTEN), (3, W.GARDNER)])
+def test_hydrostatic_state_is_exact_steady_state(dim, model):
+    """psi = H - z with matching Dirichlet heads top and bottom and no-flux
+    sides has zero flux everywhere: the residual vanishes and a time step
+    leaves it unchanged (pins the gravity sign and the elevations)."""
+    n = {1: (9,), 2: (6, 7), 3: (3, 4, 5)}[dim]
+    kinds = [W.NOFLUX] * (2 * dim - 2) + [W.DIRICHLET, W.DIRICHLET]
+    p = W.random_problem(dim, n, model, 11, bc_kinds=kinds, hetero=True)
+    H, Lz = 0.3, p["L"][dim - 1]
+    p["bc"]["value"][2 * dim - 2] = H - 0.0
+    p["bc"]["value"][2 * dim - 1] = H - Lz
+    nn = p["n"]
+    hz = Lz / nn[dim - 1]
+    idx = np.arange(nn[0] * nn[1] * nn[2])
+    iz = [idx % nn[0], (idx // nn[0]) % nn[1], idx // (nn[0] * nn[1])][dim - 1]
+    psi = H - (iz + 0.5) * hz
+    p["psi0"] = psi
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    r, nrm = o.residual(psi)
+    scale = np.max(np.abs(o.g()))
+    assert nrm <= 1e-13 * scale
+    st, info = o.step()
+    assert st == ORC_OK and info["cycles"] == 0
+    assert np.max(np.abs(o.state() - psi)) <= 1e-12
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_saturated_linear_head_is_exact(dim):
+    """Saturated (psi >= 0, K = Ks) flow between two Dirichlet heads: the
+    linear total head is the exact discrete solution.  This pins the
+    half-cell distance of the Dirichlet faces."""
+    n = {1: (10,), 2: (4, 9)}[dim]
+    kinds = [W.NOFLUX] * (2 * dim - 2) + [W.DIRICHLET, W.DIRICHLET]
+    p = W.random_problem(dim, n, W.VANGENUCHTEN, 12, bc_kinds=kinds)
+    Lz = p["L"][dim - 1]
+    P0, P1 = 1.0, 0.5
+    p["bc"]["value"][2 * dim - 2] = P0
+    p["bc"]["value"][2 * dim - 1] = P1
+    nn = p["n"]
+    hz = Lz / nn[dim - 1]
+    idx = np.arange(nn[0] * nn[1] * nn[2])
+    iz = [idx % nn[0], (idx // nn[0]) % nn[1], idx // (nn[0] * nn[1])][dim - 1]
+    z = (iz + 0.5) * hz
+    Hz = P0 + ((P1 + Lz) - P0) * z / Lz
+    psi = Hz - z
+    assert np.all(psi >= 0)
+    p["psi0"] = psi
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    _, nrm = o.residual(psi)
+    assert nrm <= 1e-13 * np.max(np.abs(o.g()))
+    # a wrong boundary distance would leave a residual of order Ks*(P1+Lz-P0)/(Lz*hz)
+    assert p["soil"]["Ks"] * ((P1 + Lz - P0) / Lz) / hz > 1e6 * nrm
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_constant_flux_column_is_exact(dim):
+    """Uniform psi0 < 0 with inflow K(psi0) on top and free drainage at the
+    bottom is a steady unit-gradient flow: zero residual (pins the gravity
+    term, the prescribed-flux and the free-drainage boundaries)."""
+    n = {1: (8,), 2: (5, 6), 3: (3, 4, 5)}[dim]
+    kinds = [W.NOFLUX] * (2 * dim - 2) + [W.FREE_DRAINAGE, W.FLUX]
+    p = W.random_problem(dim, n, W.HAVERKAMP, 13, bc_kinds=kinds)
+    psi0 = -0.4
+    o0 = Oracle(p)
+    _, _, K0 = o0.soil(0, psi0)
+    p["bc"]["value"][2 * dim - 1] = K0
+    p["psi0"] = np.full(len(p["psi0"]), psi0)
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    _, nrm = o.residual(p["psi0"])
+    assert nrm <= 1e-13 * np.max(np.abs(o.g()))
+    # flipping the flux direction must leave a residual
+    p["bc"]["value"][2 * dim - 1] = -K0
+    o2 = Oracle(p)
+    o2.prepare(p["dt"], 1)
+    _, nrm2 = o2.residual(p["psi0"])
+    assert nrm2 > 1e6 * nrm
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_discrete_mass_balance_identity(scheme, dim):
+    """Conservation: sum_i V (a theta(psi_i) - hist_i) equals the boundary
+    inflow minus uptake minus the xi term plus the volume-weighted residual,
+    to round-off, for any psi (interior fluxes telescope)."""
+    kinds = {1: [W.FREE_DRAINAGE, W.DIRICHLET], 2: [W.DIRICHLET, W.FLUX, W.FREE_DRAINAGE, W.DIRICHLET],
+             3: [W.NOFLUX, W.DIRICHLET, W.FLUX, W.NOFLUX, W.FREE_DRAINAGE, W.DIRICHLET]}[dim]
+    n = {1: (11,), 2: (6, 7), 3: (4, 3, 5)}[dim]
+    p = W.random_problem(dim, n, W.VANGENUCHTEN, 21 + dim, bc_kinds=kinds, hetero=True,
+                         sink=True, xi=3e-4, scheme=scheme)
+    rng = np.random.default_rng(5)
+    if scheme == 2:
+        p["psi_prev"] = p["psi0"] + rng.uniform(-0.05, 0.05, len(p["psi0"]))
+    o = Oracle(p)
+    assert o.prepare(p["dt"], scheme) == scheme
+    psi = o.vcycle(p["psi0"])               # any state: the identity is exact
+    V = o.cell_volume()
+    a = o.a
+    hist = o.array(7)
+    pstar = o.array(6)
+    th = np.array([o.soil(i, x)[0] for i, x in enumerate(psi)])
+    S = np.array([o.sink(i, x)[0] for i, x in enumerate(psi)])
+    r, _ = o.residual(psi)
+    lhs = V * np.sum(a * th - hist)
+    Q = o.boundary_inflow(psi)
+    xi = p["opts"]["xi"]
+    rhs = Q - V * np.sum(S) - xi * V * np.sum(psi - pstar) - V * np.sum(r)
+    scale = V * (np.sum(np.abs(a * th)) + np.sum(np.abs(hist))) + abs(Q)
+    assert abs(lhs - rhs) <= 1e-13 * scale, (lhs, rhs)
+
+
+# ---------------------------------------------------------------------------
+# Section 3: Lemma 3.1, Theorem 3.1 and the scalar point update.
+# ---------------------------------------------------------------------------
+def _splitting(M):
+    Lo = np.tril(M, -1)
+    D = np.diag(np.diag(M))
+    U = np.triu(M, 1)
+    return Lo, D, U
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lemma31_bounds(seed):
+    p = W.random_problem(2, (4, 5), W.VANGENUCHTEN, 30 + seed, hetero=True,
+                         bc_kinds=[W.DIRICHLET, W.NOFLUX, W.FREE_DRAINAGE, W.DIRICHLET])
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    M = o.dense_M()
+    Lo, D, U = _splitting(M)
+    rng = np.random.default_rng(seed)
+    n = M.shape[0]
+    scale = np.mean(np.diag(M))
+    kap = rng.uniform(0.01, 1.0, n) * scale
+    mu = rng.uniform(0.01, 1.0, n) * scale
+    al, be = rng.uniform(0.1, 2.0, 2)
+    Uk = U - np.diag(kap)
+    rows = np.abs(Uk).sum(axis=1)
+    lam_bar, lam_low = rows.max(), rows.min()
+    # first bullet: ||alpha I - beta U_kappa||_inf = alpha + beta lam_bar(U_kappa)
+    assert abs(np.abs(al * np.eye(n) - be * Uk).sum(axis=1).max() - (al + be * lam_bar)) \
+        <= 1e-12 * (al + be * lam_bar)
+    # second bullet
+    Aop = al * np.diag(mu) + be * (Lo + D + np.diag(kap))
+    inv_norm = np.abs(np.linalg.inv(Aop)).sum(axis=1).max()
+    assert inv_norm <= 1.0 / (al * mu.min() + be * lam_low) * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("ordering", [0, 1])
+@pytest.mark.parametrize("model", [W.HAVERKAMP, W.VANGENUCHTEN])
+def test_theorem31_contraction_per_sweep(ordering, model):
+    """With Remark 3.1's shift (equal row sums of U_kappa) the NGS sweep
+    contracts the max-norm error by at most
+    lam(U_kappa) / (min lambda_i + xi + lam(U_kappa)) each sweep, for the
+    lexicographic order and for red-black (both are triangular splittings)."""
+    p = W.random_problem(2, (6, 5), model, 40, hetero=True, kappa_mode=1, xi=0.0,
+                         ordering=ordering, newton_iters=0, tol=1e-15, max_levels=1,
+                         coarse_max_sweeps=5000, coarse_rtol=1e-16,
+                         bc_kinds=[W.NOFLUX, W.NOFLUX, W.FREE_DRAINAGE, W.DIRICHLET])
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    star, st, info = o.solve_current(p["psi0"])
+    assert info["resid"] <= 1e-13
+    M = o.dense_M()
+    _, _, U = _splitting(M) if ordering == 0 else (None, None, None)
+    kap = o.array(5)
+    if ordering == 0:
+        u = -U.sum(axis=1)
+    else:
+        nn = o.level_n(0)
+        idx = np.arange(M.shape[0])
+        color = (idx % nn[0] + (idx // nn[0]) % nn[1]) % 2
+        u = np.where(color == 0, -(M - np.diag(np.diag(M))).sum(axis=1), 0.0)
+    rows = kap + u
+    assert np.allclose(rows, rows.max(), rtol=1e-12)
+    lam = rows.max()
+    a = o.a
+    rng = np.random.default_rng(1)
+    psi = star + rng.uniform(-0.3, 0.3, len(star))
+    for s in range(6):
+        new = o.sweep(psi)
+        e0 = np.max(np.abs(psi - star))
+        e1 = np.max(np.abs(new - star))
+        lo = np.minimum(new, star)
+        hi = np.maximum(new, star)
+        dmin = np.array([min(o.soil(i, lo[i])[1], o.soil(i, hi[i])[1]) for i in range(len(star))])
+        rho = lam / (a * dmin.min() + 0.0 + lam)
+        assert e1 <= rho * e0 * (1 + 1e-9) + 1e-14, (s, e1, e0, rho)
+        psi = new
+
+
+@pytest.mark.parametrize("model", [W.HAVERKAMP, W.GARDNER, W.VANGENUCHTEN])
+def test_point_solve_matches_bracketing_root(model):
+    p = W.random_problem(1, 6, model, 50, sink=True)
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    a = o.a
+    rng = np.random.default_rng(2)
+    cell = p["n"][0] - 1
+    for _ in range(25):
+        cc = 10 ** rng.uniform(-4, 1)
+        target = rng.uniform(-3.0, 0.2)
+        th, _, _ = o.soil(cell, target)
+        S, _ = o.sink(cell, target)
+        f = a * th + S + cc * target
+
+        def F(x):
+            return a * o.soil(cell, x)[0] + o.sink(cell, x)[0] + cc * x - f
+
+        lo, hi = target - 10.0, target + 10.0
+        root = brentq(F, lo, hi, xtol=1e-15, rtol=4 * np.finfo(float).eps)
+        x, it = o.point_solve(cell, cc, f, x0=rng.uniform(-3, 0), newton_iters=0)
+        assert abs(x - root) <= 1e-12 * max(1.0, abs(root)), (x, root, it)
+        x60, _ = o.point_solve(cell, cc, f, x0=root, newton_iters=3)
+        assert abs(x60 - root) <= 1e-12 * max(1.0, abs(root))
+
+
+# ---------------------------------------------------------------------------
+# The implicit step: FAS-NGS reaches the plain solution of N_h(psi) = g_h.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(1, (9,)), (2, (5, 7)), (3, (4, 3, 5))])
+@pytest.mark.parametrize("model", [W.HAVERKAMP, W.GARDNER, W.VANGENUCHTEN])
+def test_fas_solution_equals_dense_newton(dim, n, model):
+    kinds = [W.NOFLUX] * (2 * dim - 2) + [W.FREE_DRAINAGE, W.DIRICHLET]
+    p = W.random_problem(dim, n, model, 60 + dim, bc_kinds=kinds, hetero=True, sink=True,
+                         tol=1e-13, coarsest_max_n=2)
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    psi_fas, st, info = o.solve_current(p["psi0"])
+    assert st == ORC_OK
+    psi_dn, res = dense_newton(o, p["psi0"])
+    assert res <= 1e-13
+    assert np.max(np.abs(psi_fas - psi_dn)) <= 1e-10 * max(1.0, np.max(np.abs(psi_dn)))
+
+
+def test_fas_fixed_point_independent_of_hierarchy():
+    """The converged FAS answer does not depend on restriction, prolongation
+    or coarse operators: V-cycles, plain NGS and both orderings agree."""
+    base = W.random_problem(2, (13, 11), W.VANGENUCHTEN, 70, hetero=True, tol=1e-13,
+                            bc_kinds=[W.NOFLUX, W.NOFLUX, W.DIRICHLET, W.DIRICHLET])
+    sols = []
+    for kw in [dict(), dict(ordering=0), dict(max_levels=1, coarse_max_sweeps=100000,
+                                              coarse_rtol=1e-15, max_cycles=2)]:
+        p = W.with_opts(base, **kw)
+        o = Oracle(p)
+        o.prepare(p["dt"], 1)
+        psi, st, info = o.solve_current(p["psi0"])
+        assert st == ORC_OK, (kw, info)
+        sols.append(psi)
+    for s in sols[1:]:
+        assert np.max(np.abs(s - sols[0])) <= 1e-9
+
+
+def _median_factor(o, psi, cycle, ncyc):
+    res = [o.residual(psi)[1]]
+    for _ in range(ncyc):
+        psi = cycle(psi)
+        res.append(o.residual(psi)[1])
+        if res[-1] / o.a < 1e-12:
+            break
+    return float(np.median([res[i + 1] / res[i] for i in range(1, len(res) - 1)]))
+
+
+def test_multigrid_factor_bounded_under_refinement():
+    """Multigrid (Section 3.2): the V(2,2) contraction factor per cycle stays
+    well below 1 as the Celia column is refined (N = 128 -> 2048), while a
+    plain NGS sweep's factor tends to 1 (why Table 3's GS(100) is slow)."""
+    for n in (128, 512, 2048):
+        p = W.celia_1d(n=n, nsteps=3)
+        o = Oracle(p)
+        for _ in range(2):
+            o.prepare(p["dt"], 1)
+            f = _median_factor(o, o.state(), o.vcycle, 10)
+            assert f <= 0.3, (n, f)
+            st, _ = o.step()
+            assert st == ORC_OK
+    p = W.celia_1d(n=2048, nsteps=3)
+    o = Oracle(p)
+    o.step()
+    o.prepare(p["dt"], 1)
+    assert _median_factor(o, o.state(), o.sweep, 40) >= 0.9
+
+
+def _time_error(scheme, nsteps_list, T=1800.0):
+    base = W.random_problem(1, 32, W.GARDNER, 80, bc_kinds=[W.DIRICHLET, W.DIRICHLET],
+                            tol=1e-14, newton_iters=0)
+    base["soil"]["p1"] = 1.0
+    base["bc"]["value"][0] = -1.0
+    base["bc"]["value"][1] = -0.3
+    z = (np.arange(32) + 0.5) / 32
+    base["psi0"] = -1.0 + 0.7 * z
+    out = {}
+    for ns in nsteps_list:
+        o = Oracle(base)
+        for _ in range(ns):
+            st, _ = o.step(T / ns, scheme)
+            assert st == ORC_OK
+        out[ns] = o.state()
+    return out
+
+
+@pytest.mark.parametrize("scheme,order", [(1, 1.0), (2, 2.0)])
+def test_temporal_convergence_order(scheme, order):
+    """First-order BDF1 as in the paper's temporal study (Section 4.1); the
+    BDF2 reading must show second order (self-convergence against a fine-step
+    run on the same grid)."""
+    sols = _time_error(scheme, [8, 16, 32, 1024])
+    ref = sols[1024]
+    errs = [np.max(np.abs(sols[k] - ref)) for k in (8, 16, 32)]
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(s - order) <= 0.35 for s in slopes), (errs, slopes)
