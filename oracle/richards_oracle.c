@@ -606,10 +606,13 @@ static double point_solve(const orc_ctx *c, const level *L, long i, double cc, d
     if (F == 0.0) break;
     if (F > 0.0) hi = x; else lo = x;
     double xn = x - F / dF;
-    if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
+    /* keep a Newton step that lands strictly inside the bracket, or one that
+       moves less than round-off (converged); otherwise bisect */
+    const double tiny = 1e-15 * (fabs(x) > 1.0 ? fabs(x) : 1.0);
+    if (!(xn > lo && xn < hi) && !(fabs(xn - x) <= tiny)) xn = 0.5 * (lo + hi);
     const double step = fabs(xn - x);
     x = xn;
-    if (kfixed <= 0 && step <= 1e-15 * (fabs(x) > 1.0 ? fabs(x) : 1.0)) break;
+    if (kfixed <= 0 && step <= tiny) break;
   }
   if (iters) *iters = it;
   return x;
