@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark: NGS-FAS Richards solver on the 3D drainage workload (256^3).
+
+One bench step is one implicit BDF2 time step of the whole path (per-step
+preparation, FP64 defect correction around FP32 FAS V-cycles with red-black
+NGS, stop test in FP64, history shift) on 256^3 cells of heterogeneous van
+Genuchten soil draining from saturation.  Inputs (16.8 M cells, 134 MB per
+FP64 array) are larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own
+replica (the path has no exchange step here): weak scaling, value = the
+cell-updates of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NGS cell-updates/s and time-steps/s at 256^3; p50/p99 solve latency, vs FP64 plain @1e-8"
+UNIT = "cell-updates/s"
+WORKLOAD = "3D drainage 256^3, heterogeneous VG (lognormal Ks, sigma_lnK=1, corr 8 cells; alpha U[2,5], n U[1.5,2.5]), " \
+           "psi0=0, free drainage bottom, BDF2 dt=300 s, mixed FP32 inner / FP64 outer, tol 1e-8"
+
+# Algorithmic bytes per unit for the kernels that can dominate (per cell the
+# launch covers; a half-sweep covers the cells of one colour).  The NGS
+# figure is the mixed-mode inner update of the heterogeneous workload:
+# delta read+write, Kc, r, psi0, alpha, n (7 x 4 B).
+BYTES_PER_CELL = {
+    "sweep32": 28.0,
+    "residual32": 28.0,
+    "sweep64": 48.0,
+    "residual64": 56.0,
+    "outer_residual": 52.0,
+    "prep": 88.0,
+    "restrict32": 9.0,
+    "prolong32": 9.0,
+    "tau32": 36.0,
+    "apply_delta": 12.0,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=None,
+                    help="steps with kernel timing (default: all timed steps)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def roofline(prof, ms_total):
+    """Roofline of the dominant kernel (largest summed device time)."""
+    by_name = {}
+    for r in prof:
+        by_name.setdefault(r["name"], []).append(r)
+    totals = {k: sum(x["ms"] for x in v) for k, v in by_name.items()}
+    dom = max(totals, key=totals.get)
+    recs = by_name[dom]
+    fine = [r for r in recs if r["level"] == 0] or sorted(recs, key=lambda r: -r["ms"])[:1]
+    launches = sum(r["launches"] for r in fine)
+    ms = sum(r["ms"] for r in fine)
+    cells = sum(r["cells"] for r in fine)
+    pk, src = peaks()
+    shares = {k: round(v / max(sum(totals.values()), 1e-30), 4) for k, v in
+              sorted(totals.items(), key=lambda kv: -kv[1])}
+    out = {"kernel": dom, "level": fine[0]["level"], "launches": launches,
+           "avg_launch_ms": ms / max(launches, 1), "share_of_kernel_time": shares[dom],
+           "kernel_shares": shares}
+    if dom in BYTES_PER_CELL:
+        bytes_per_launch = BYTES_PER_CELL[dom] * cells / max(launches, 1)
+        achieved = bytes_per_launch / (ms / max(launches, 1) * 1e-3) / 1e9
+        out.update({"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"], "peak_source": src + " hbm_gbs",
+                    "algorithmic_bytes_per_launch": bytes_per_launch, "traffic": None})
+    else:
+        out.update({"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": None,
+                    "traffic": None})
+    return out
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(prob, psi, nsweeps=3):
+    """The CPU oracle, as it stands, on a bounded sample of the same workload:
+    red-black NGS sweeps of the 256^3 fine level at the given state."""
+    from oracle.oracle import Oracle
+    o = Oracle(prob)
+    o.set_state(psi)
+    o.prepare(prob["dt"], 1)
+    cur = psi
+    t0 = time.perf_counter()
+    for _ in range(nsweeps):
+        cur = o.sweep(cur)
+    dt = time.perf_counter() - t0
+    n = len(psi)
+    return {"value": nsweeps * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsweeps} red-black NGS sweeps (Newton k=2) of the {round(n ** (1 / 3))}^3 fine level "
+                      f"at the benchmark state, single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host, one fine-level
+    sweep of the same 256^3 workload per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_2606_04292_gb300 import workloads as W
+    prob = W.drainage_3d(n=args.n)
+    o = Oracle(prob)
+    o.prepare(prob["dt"], 1)
+    psi = np.array(prob["psi0"], dtype=np.float64)
+    for _ in range(args.warmup):
+        psi = o.sweep(psi)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        psi = o.sweep(psi)
+    dt = time.perf_counter() - t0
+    n = len(psi)
+    v = args.steps * n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "one red-black NGS sweep of the "
+                                            "fine level of the first time step per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} fine-level NGS sweeps at {args.n}^3, single thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2606_04292_gb300 import richards as R
+    from paper_2606_04292_gb300 import workloads as W
+
+    prob = W.drainage_3d(n=args.n)
+    N = W.ncells(prob)
+    stream = torch.cuda.current_stream()
+    gs = R.Solver(prob, stream=stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    infos = []
+    for _ in range(args.warmup):
+        st, info = gs.step()
+    barrier()
+    prof_steps = args.steps if args.profile_steps is None else args.profile_steps
+    gs.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        e0.record(stream)
+        for k in range(args.steps):
+            if k == prof_steps:
+                gs.profile(False)
+            st, info = gs.step(check=False)
+            if st != R.RICH_OK:
+                raise RuntimeError(f"step failed: {R.STATUS_NAMES[st]} {info}")
+            infos.append(info)
+        e1.record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    gs.profile(False)
+    ms = e0.elapsed_time(e1)
+    prof = gs.profile_read()
+    updates = sum(i["cell_updates"] for i in infos)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    up_t = torch.tensor([float(updates)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(up_t, op=dist.ReduceOp.SUM)
+    ms_max, updates_all = ms_t.item(), up_t.item()
+    value = updates_all / (ms_max * 1e-3)
+    steps_per_s = world * args.steps / (ms_max * 1e-3)
+    launches = sum(r["launches"] for r in prof) if prof_steps >= args.steps else None
+
+    # end to end through the C ABI: inputs from pinned host memory each step,
+    # result read back each step
+    e2e = None
+    if not args.no_e2e:
+        host_psi = torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+        host_prev = torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+        host_out = torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+        host_psi[:] = gs.state()
+        host_prev[:] = host_psi
+        ge = R.Solver(prob, stream=stream.cuda_stream)
+        ge.set_state(host_psi, host_prev)
+        ge.step()
+        barrier()
+        ke = max(1, min(args.steps, 5))
+        upd = 0
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            ge.set_state(host_psi, host_prev)
+            st, info = ge.step(check=False)
+            upd += info["cell_updates"]
+            lib = R.lib()
+            R._check(lib.richards_get_state(ge.h, R._dp(host_out), 0), ge.h)
+            host_prev, host_psi, host_out = host_psi, host_out, host_prev
+        barrier()
+        te = time.perf_counter() - t0
+        e2e = {"value": upd / te * world, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N,
+               "steps": ke, "time_steps_per_s": ke / te}
+        ge.close()
+
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        # FP64 plain on the same workload from the same initial state; the
+        # mixed result of the same number of steps is compared with it.
+        nfp = 3
+        gf = R.Solver(W.with_opts(prob, precision=0), stream=stream.cuda_stream)
+        gm = R.Solver(prob, stream=stream.cuda_stream)
+        gf.step()
+        gm.step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        upd = 0
+        for _ in range(nfp - 1):
+            st, info = gf.step(check=False)
+            upd += info["cell_updates"]
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for _ in range(nfp - 1):
+            gm.step()
+        torch.cuda.synchronize()
+        tm = time.perf_counter() - t0
+        a, b = gm.state(), gf.state()
+        fp64 = {"time_steps_per_s": (nfp - 1) / tf, "cell_updates_per_s": upd / tf,
+                "mixed_time_steps_per_s_same_steps": (nfp - 1) / tm,
+                "mixed_speedup_in_steps_per_s": tf / tm,
+                "mixed_vs_fp64_max_abs_dpsi_after_3_steps": float(np.max(np.abs(a - b))),
+                "status_last": R.STATUS_NAMES[st]}
+        gf.close()
+        gm.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob, gs.state())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": N, "levels": gs.nlevels, "l2": "inputs larger than L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "time_steps_per_s": steps_per_s,
+            "v_cycles_per_step": statistics.mean(i["cycles"] for i in infos),
+            "outer_iters_per_step": statistics.mean(i["outer_iters"] for i in infos),
+            "resid_last": infos[-1]["resid"],
+            "wall_s_timed": t_wall,
+            "gpu_launches": launches,
+            "roofline": roofline(prof, ms_max) if prof else None,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "fp64_plain": fp64,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    gs.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * richards.h -- C ABI of the GB300 (sm_103a) NGS-FAS solver for the
+ * Richards equation (conservative finite differences, implicit BDF1/BDF2 in
+ * time, full-approximation-scheme multigrid with a red-black nonlinear
+ * Gauss-Seidel smoother).
+ *
+ * Every array argument is a plain pointer with an explicit size.  Host input
+ * arrays are copied during the call (the caller keeps ownership).  The context
+ * owns every device allocation it makes and releases them in
+ * richards_destroy().  No exception crosses the ABI: every call returns a
+ * richards_status and richards_last_error() holds a message for the last
+ * failing call.  A context is bound to one CUDA stream (given at creation;
+ * NULL = the legacy default stream) and must not be used from two host
+ * threads at once.
+ *
+ * Layout of every cell array: lexicographic with the first index fastest
+ * (Section 2, the flattening s(i)); axis dim-1 is the vertical axis, its
+ * low end the bottom (elevation z = 0).  Face arrays (boundary values and
+ * masks) are indexed lexicographically over the two other axes.
+ *
+ * Units are the caller's, used consistently (the paper's 1-d column is in cm
+ * and s; SI works the same way).
+ */
+#ifndef RICHARDS_H
+#define RICHARDS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct richards_ctx richards_ctx;   /* opaque; owns its device memory */
+
+typedef enum {
+  RICH_OK = 0,
+  RICH_EINVAL = 1,    /* invalid argument or parameter                     */
+  RICH_ENOMEM = 2,    /* device allocation failed                          */
+  RICH_ENOCONV = 3,   /* max_cycles / max_outer reached above tolerance     */
+  RICH_ENAN = 4,      /* NaN/Inf in the iterate; state rolled back to psi^n */
+  RICH_ETIMEOUT = 5,  /* a bounded device wait gave up                     */
+  RICH_ECUDA = 6,     /* a CUDA runtime call failed                        */
+  RICH_EBUSY = 7      /* context busy (batch in flight)                    */
+} richards_status;
+
+/* Grid (Section 2, reading: cell-centred, h = L/n per axis).  dim in 1..3;
+   n[a] >= 1 cells on axis a; axes a >= dim must have n[a] = 1. */
+typedef struct {
+  int dim;
+  int n[3];
+  double L[3];
+} richards_grid;
+
+/* Constitutive laws of Table 1.  Parameters:
+     RICH_HAVERKAMP:     p1 = alpha, p2 = beta, p3 = A, p4 = gamma
+     RICH_GARDNER:       p1 = alpha
+     RICH_VANGENUCHTEN:  p1 = alpha, p2 = n (> 1), p3 = l (Mualem, 0.5)
+   Ks_field / p1_field / p2_field: optional per-cell host arrays (ncell
+   doubles) replacing the scalar.  For psi >= 0 all laws give theta_s, Ks. */
+enum { RICH_HAVERKAMP = 0, RICH_GARDNER = 1, RICH_VANGENUCHTEN = 2 };
+typedef struct {
+  int model;
+  double Ks, theta_s, theta_r, p1, p2, p3, p4;
+  const double *Ks_field, *p1_field, *p2_field;
+} richards_soil;
+
+/* Boundary conditions per face f = 2*axis + side (side 0 = low end).
+     DIRICHLET     value = head psi_b on the face (or value_field per face
+                   cell); with mask_field, Dirichlet where mask != 0 and
+                   no-flux elsewhere.  Face conductivity (K_i + K(psi_b))/2
+                   over half a cell.
+     NOFLUX        zero flux (diffusion and gravity).
+     FLUX          prescribed inflow rate (volume / area / time) value or
+                   value_field.
+     FREE_DRAINAGE unit gradient of total head: outflow K(psi*) of the
+                   bottom cell; only on the bottom face (axis dim-1, side 0). */
+enum { RICH_BC_DIRICHLET = 0, RICH_BC_NOFLUX = 1, RICH_BC_FLUX = 2, RICH_BC_FREE_DRAINAGE = 3 };
+typedef struct {
+  int kind[6];
+  double value[6];
+  const double *value_field[6];
+  const unsigned char *mask_field[6];
+} richards_bc;
+
+/* Root-water-uptake sink S(psi) = alpha_F(psi) Tp beta(depth) (the paper
+   leaves S unspecified beyond assumption (A2); this is a Feddes-type reading):
+   alpha_F piecewise linear through (h4,0), (h3,1), (h2,1), (h1,0), zero
+   outside; beta = exp(-depth/root_decay) normalised on [0, root_depth]. */
+typedef struct {
+  int enabled;
+  double Tp, root_depth, root_decay, h1, h2, h3, h4;
+} richards_sink;
+
+/* Solver options.
+     nu1, nu2             pre/post NGS sweeps per level (Section 3.2)
+     coarse_max_sweeps,   coarsest level: sweeps until the defect drops by
+     coarse_rtol          coarse_rtol or coarse_max_sweeps are done
+     coarsest_max_n,      coarsen every axis with n > 1 to ceil(n/2) while
+     max_levels           max n > coarsest_max_n (max_levels > 0 caps it)
+     kappa_mode, kappa    diagonal shift Lambda_kappa of Lemma 3.1: 0 =
+                          constant kappa (1/time), 2 = zero
+     xi                   stabilisation of eq. (fully-bdf1) (1/time)
+     tol                  stop when tau_eff ||N(psi) - g||_inf <= tol,
+                          tau_eff = 1/a (residual in theta units)
+     max_cycles           V-cycles per step (FP64) / inner cycles (mixed)
+     ordering             1 = red-black (the only GPU ordering)
+     newton_iters         k > 0: exactly k safeguarded Newton steps per point
+                          update; 0: to round-off
+     precision            0 = FP64 throughout; 1 = FP32 inner V-cycles on the
+                          correction equation inside an FP64 defect
+                          correction (residual, stop test in FP64)
+     inner_cycles,        mixed mode: FP32 V-cycles per outer iteration, stop
+     inner_rtol, max_outer  early below inner_rtol x initial inner defect
+     tail_cells           levels with at most this many cells run in one
+                          thread block (the coarse tail of the V-cycle) */
+typedef struct {
+  int nu1, nu2, coarse_max_sweeps;
+  double coarse_rtol;
+  int coarsest_max_n, max_levels;
+  int kappa_mode;
+  double kappa, xi, tol;
+  int max_cycles, ordering, newton_iters, precision;
+  int inner_cycles;
+  double inner_rtol;
+  int max_outer, tail_cells;
+} richards_opts;
+
+typedef struct {
+  int cycles;            /* V-cycles (FP64) or FP32 inner V-cycles (mixed)  */
+  int outer_iters;       /* FP64 defect-correction iterations (mixed)       */
+  int scheme_used;       /* 1 or 2 (BDF2 falls back to BDF1 on a first step) */
+  double resid0, resid;  /* tau_eff ||g - N(psi)||_inf at start / at exit    */
+  long long cell_updates;/* NGS point updates over all levels this step     */
+} richards_step_info;
+
+/* Create a context for one grid; allocates the multigrid hierarchy on the
+   device.  stream: a cudaStream_t (NULL = default stream).  On success
+   *out receives the context.  Errors: EINVAL (bad grid/opts), ENOMEM, ECUDA. */
+richards_status richards_create(const richards_grid *grid, const richards_opts *opts,
+                                void *stream, richards_ctx **out);
+
+/* Soil law and parameters (Table 1).  EINVAL: Ks <= 0, theta_s <= theta_r,
+   theta_r < 0, VG n <= 1, Haverkamp A/alpha/beta/gamma <= 0, Gardner alpha
+   <= 0, or a non-finite value in a field. */
+richards_status richards_set_soil(richards_ctx *ctx, const richards_soil *soil);
+
+/* Boundary conditions (see richards_bc).  EINVAL: unknown kind, free
+   drainage off the bottom face, non-finite value. */
+richards_status richards_set_bc(richards_ctx *ctx, const richards_bc *bc);
+
+/* Sink S(psi) (reading of assumption (A2)).  EINVAL: not h4 < h3 <= h2 < h1. */
+richards_status richards_set_sink(richards_ctx *ctx, const richards_sink *sink);
+
+/* State psi^n (host array, ncell doubles) and, for BDF2, psi^{n-1}
+   (nullable: the next BDF2 step then falls back to BDF1).  t: model time.
+   EINVAL on a non-finite value. */
+richards_status richards_set_state(richards_ctx *ctx, const double *psi,
+                                   const double *psi_prev, double t);
+
+/* One implicit step of size dt: BDF1 (eq. fully-bdf1) for scheme 1, the BDF2
+   reading for scheme 2.  Cycles to the tolerance, then shifts the history.
+   info (nullable) receives the step statistics.  ENOCONV: psi^{n+1} is the
+   last iterate and the history is shifted all the same; ENAN: state rolled
+   back to psi^n. */
+richards_status richards_step(richards_ctx *ctx, double dt, int scheme,
+                              richards_step_info *info);
+
+/* nsteps calls of richards_step; stops at the first error.  last receives
+   the last step's statistics. */
+richards_status richards_solve(richards_ctx *ctx, double dt, int nsteps, int scheme,
+                               richards_step_info *last);
+
+/* Copy psi^n out.  on_device = 0: psi_out is a host array of ncell doubles;
+   1: a device pointer (ordered on the context's stream). */
+richards_status richards_get_state(richards_ctx *ctx, double *psi_out, int on_device);
+
+/* Model time and number of cells of the finest level. */
+double richards_time(const richards_ctx *ctx);
+long long richards_ncell(const richards_ctx *ctx);
+
+/* Message describing the last failure on this context (static storage
+   owned by the context); "" when none. */
+const char *richards_last_error(const richards_ctx *ctx);
+
+/* Release the context and all its device memory.  NULL is accepted. */
+void richards_destroy(richards_ctx *ctx);
+
+/* ---------------------------------------------------------------------
+ * Inspection and kernel-level entry points.  They run single stages of the
+ * step on the context's current data so that each kernel can be checked
+ * against the CPU oracle.  Levels count from 0 (finest).
+ * --------------------------------------------------------------------- */
+
+/* Per-step set-up without solving: lagged state psi*, Kc = K(psi*), the
+   boundary conductances and the right side g of eq. (Nh-def) on the finest
+   level, restricted Kc and conductances on coarser levels; the iterate of
+   level 0 is set to psi^n.  Returns the scheme used through *scheme_used. */
+richards_status richards_prepare(richards_ctx *ctx, double dt, int scheme, int *scheme_used);
+
+int richards_nlevels(const richards_ctx *ctx);
+richards_status richards_level_dims(const richards_ctx *ctx, int level, int n_out[3]);
+
+/* Arrays of a level (FP64 copies, host buffers):
+     0 iterate psi, 1 right side g, 2 Kc, 3 p1, 4 p2, 5 sink coefficient,
+     6 FAS restricted iterate psi_bar, 7 defect d, 10+f boundary conductance
+     of face f (face cells).  set accepts 0 (iterate) and 1 (right side). */
+richards_status richards_get_level(richards_ctx *ctx, int level, int which, double *out,
+                                   long long n);
+richards_status richards_set_level(richards_ctx *ctx, int level, int which, const double *in,
+                                   long long n);
+
+/* One red (color 0) or black (color 1) half-sweep of eq. (point-update) on
+   a level's iterate with its right side (FP64); color -1: both. */
+richards_status richards_sweep(richards_ctx *ctx, int level, int color);
+
+/* d = g - N(psi) on a level (FP64) into the level's defect; *norm gets
+   ||d||_inf (nullable). */
+richards_status richards_residual(richards_ctx *ctx, int level, double *norm);
+
+/* FAS steps 2-4 from `level` to level+1: defect, restriction of iterate and
+   defect, coarse right side g_H = N_H(psi_bar_H) + d_H, coarse iterate =
+   psi_bar_H (FP64). */
+richards_status richards_restrict_tau(richards_ctx *ctx, int level);
+
+/* FAS step 6: psi_level += P (psi_{level+1} - psi_bar_{level+1}) (FP64). */
+richards_status richards_prolong(richards_ctx *ctx, int level);
+
+/* One FP64 V-cycle from the finest level (the same launches as a step). */
+richards_status richards_vcycle(richards_ctx *ctx);
+
+/* ---------------------------------------------------------------------
+ * Kernel timing.  While enabled, every kernel launch of the context is
+ * bracketed by CUDA events on the context's stream; richards_profile_read
+ * synchronises the stream and returns, per kernel name and level, the number
+ * of launches, their summed device time and the cells they covered (a
+ * half-sweep covers the cells of one colour).
+ * --------------------------------------------------------------------- */
+typedef struct {
+  char name[32];
+  int level;
+  long long launches;
+  double ms;
+  long long cells;
+} richards_kernel_stat;
+
+/* enable = 1: clear the records and start recording; 0: stop. */
+richards_status richards_profile(richards_ctx *ctx, int enable);
+
+/* Writes up to max records into out; returns the number of records (or -1
+   on error). */
+int richards_profile_read(richards_ctx *ctx, richards_kernel_stat *out, int max);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1036 @@
+// C ABI of the solver: context, multigrid hierarchy, set-up calls and the
+// FP64 / mixed-precision step drivers.  Each stage of a step is one of the
+// kernels in k64.cu / k32.cu; the host only sequences launches and reads the
+// 8-byte residual norms that drive the stop tests.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "launch.h"
+#include "richards.h"
+
+using rich::Level;
+using rich::Phys;
+using rich::Xfer;
+
+namespace {
+
+constexpr int MAXLEV = 24;
+constexpr int NSCRATCH = 32;   // norm slots + statistics
+
+struct HLevel {
+  int n[3] = {1, 1, 1};
+  double h[3] = {1, 1, 1};
+  long long ncell = 0;
+  long long nface[6] = {0, 0, 0, 0, 0, 0};
+  double *u = nullptr, *ubar = nullptr, *g = nullptr, *d = nullptr, *Kc = nullptr;
+  double *p1 = nullptr, *p2 = nullptr, *smax = nullptr;
+  double* kb[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  float *uf = nullptr, *ubarf = nullptr, *gf = nullptr, *df = nullptr, *Kcf = nullptr;
+  float *p1f = nullptr, *p2f = nullptr, *smaxf = nullptr, *psi0f = nullptr;
+  float* kbf[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // transfer tables to the next coarser level
+  int *pc[3] = {}, *pj[3] = {}, *rc[3] = {}, *ri[3] = {};
+  double *pw[3] = {}, *rw[3] = {};
+  float *pwf[3] = {}, *rwf[3] = {};
+};
+
+}  // namespace
+
+struct richards_ctx {
+  cudaStream_t s = nullptr;
+  richards_grid grid{};
+  richards_opts opts{};
+  int nlev = 0, tail_start = 0;
+  HLevel L[MAXLEV];
+  richards_soil soil{};
+  bool soil_set = false, het_p1 = false, het_p2 = false, het_Ks = false;
+  richards_bc bc{};
+  bool bc_set = false;
+  rich::BcDev bcdev{};
+  richards_sink sink{};
+  double *psi_n = nullptr, *psi_nm1 = nullptr, *Ks = nullptr;
+  bool have_state = false, have_prev = false;
+  double t = 0.0, a = 0.0, dt = 0.0;
+  int scheme_used = 1;
+  bool prepared = false;
+  Level<double>* dL64 = nullptr;
+  Xfer<double>* dX64 = nullptr;
+  Level<float>* dL32 = nullptr;
+  Xfer<float>* dX32 = nullptr;
+  unsigned long long* scratch = nullptr;
+  unsigned long long* hscratch = nullptr;    // pinned
+  std::vector<void*> allocs;
+  std::vector<void*> bc_allocs;
+  std::string err;
+  long long updates_host = 0;
+  // kernel timing (richards_profile)
+  struct ProfRec { const char* name; int level; long long cells; cudaEvent_t a, b; };
+  struct ProfAgg { long long launches = 0; double ms = 0.0; long long cells = 0; };
+  bool prof = false;
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  std::map<std::pair<std::string, int>, ProfAgg> prof_agg;
+};
+
+namespace {
+
+richards_status fail(richards_ctx* c, richards_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(c, RICH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+richards_status dalloc(richards_ctx* c, T** p, long long n, std::vector<void*>* list = nullptr) {
+  void* q = nullptr;
+  size_t bytes = sizeof(T) * (size_t)(n > 0 ? n : 1);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, RICH_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  (list ? list : &c->allocs)->push_back(q);
+  *p = (T*)q;
+  return RICH_OK;
+}
+
+#define TRY(x)                           \
+  do {                                   \
+    richards_status st_ = (x);           \
+    if (st_ != RICH_OK) return st_;      \
+  } while (0)
+
+// ------------------------------------------------------------------------
+// Kernel timing: CUDA events on the context's stream around each launch.
+// ------------------------------------------------------------------------
+cudaEvent_t prof_event(richards_ctx* c) {
+  if (c->ev_pool.empty()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t e = c->ev_pool.back();
+  c->ev_pool.pop_back();
+  return e;
+}
+
+void prof_flush(richards_ctx* c) {
+  if (c->prof_pending.empty()) return;
+  cudaStreamSynchronize(c->s);
+  for (auto& r : c->prof_pending) {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto& g = c->prof_agg[{std::string(r.name), r.level}];
+    g.launches += 1;
+    g.ms += ms;
+    g.cells += r.cells;
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+}
+
+struct Prof {
+  richards_ctx* c;
+  const char* name;
+  int level;
+  long long cells;
+  cudaEvent_t a = nullptr;
+  Prof(richards_ctx* c_, const char* n, int l, long long cells_) : c(c_), name(n), level(l), cells(cells_) {
+    if (c->prof) {
+      a = prof_event(c);
+      cudaEventRecord(a, c->s);
+    }
+  }
+  ~Prof() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(c);
+    cudaEventRecord(b, c->s);
+    c->prof_pending.push_back({name, level, cells, a, b});
+    if (c->prof_pending.size() > 8192) prof_flush(c);
+  }
+};
+
+bool finite_all(const double* a, long long n) {
+  for (long long i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+// ------------------------------------------------------------------------
+// Transfer tables along one axis.  Reading of "standard full weighting and
+// linear interpolation" for cell-centred, possibly non-nested levels: the
+// coarse coordinate of fine cell i is ((2i+1) nc - nf) / (2 nf); P mixes the
+// two nearest coarse centres, folding a ghost beyond the end into the end
+// cell with factor s (+1 constant extrapolation, -1 on a fully Dirichlet
+// face); R is the transpose of P with s = +1, each row scaled to sum 1.
+// ------------------------------------------------------------------------
+struct Row {
+  int cnt = 0;
+  int idx[rich::RMAX];
+  double w[rich::RMAX];
+  bool add(int j, double wt) {
+    if (wt == 0.0) return true;
+    for (int k = 0; k < cnt; ++k)
+      if (idx[k] == j) { w[k] += wt; return true; }
+    if (cnt >= rich::RMAX) return false;
+    idx[cnt] = j;
+    w[cnt] = wt;
+    ++cnt;
+    return true;
+  }
+};
+
+Row interp(int nf, int nc, int i, double slo, double shi) {
+  Row r;
+  if (nf == 1) { r.add(0, 1.0); return r; }
+  const long long num = (long long)(2 * i + 1) * nc - nf, den = 2LL * nf;
+  long long J0 = num >= 0 ? num / den : -((-num + den - 1) / den);
+  const double w = (double)(num - J0 * den) / (double)den;
+  const long long J1 = J0 + 1;
+  if (J0 < 0) r.add(0, (1.0 - w) * slo); else r.add((int)J0, 1.0 - w);
+  if (J1 >= nc) r.add(nc - 1, w * shi); else r.add((int)J1, w);
+  return r;
+}
+
+richards_status build_axis_tables(richards_ctx* c, int l, int ax, double slo, double shi) {
+  HLevel& F = c->L[l];
+  HLevel& C = c->L[l + 1];
+  const int nf = F.n[ax], nc = C.n[ax];
+  std::vector<int> pc(nf), pj(2 * nf, 0), rc(nc, 0), ri((size_t)rich::RMAX * nc, 0);
+  std::vector<double> pw(2 * nf, 0.0), rw((size_t)rich::RMAX * nc, 0.0);
+  for (int i = 0; i < nf; ++i) {
+    Row r = interp(nf, nc, i, slo, shi);
+    pc[i] = r.cnt;
+    for (int k = 0; k < r.cnt; ++k) { pj[2 * i + k] = r.idx[k]; pw[2 * i + k] = r.w[k]; }
+  }
+  std::vector<Row> R(nc);
+  for (int i = 0; i < nf; ++i) {
+    Row p0 = interp(nf, nc, i, 1.0, 1.0);
+    for (int k = 0; k < p0.cnt; ++k)
+      if (!R[p0.idx[k]].add(i, p0.w[k])) return fail(c, RICH_EINVAL, "restriction stencil too wide");
+  }
+  for (int J = 0; J < nc; ++J) {
+    double s = 0.0;
+    for (int k = 0; k < R[J].cnt; ++k) s += R[J].w[k];
+    rc[J] = R[J].cnt;
+    for (int k = 0; k < R[J].cnt; ++k) {
+      ri[rich::RMAX * J + k] = R[J].idx[k];
+      rw[rich::RMAX * J + k] = R[J].w[k] / s;
+    }
+  }
+  std::vector<float> pwf(pw.begin(), pw.end()), rwf(rw.begin(), rw.end());
+  auto up = [&](auto** dst, const auto& src) -> richards_status {
+    using E = typename std::remove_reference<decltype(src)>::type::value_type;
+    E* p;
+    TRY(dalloc(c, &p, (long long)src.size(), &c->bc_allocs));
+    CK(cudaMemcpy(p, src.data(), sizeof(E) * src.size(), cudaMemcpyHostToDevice));
+    *dst = p;
+    return RICH_OK;
+  };
+  TRY(up(&F.pc[ax], pc));
+  TRY(up(&F.pj[ax], pj));
+  TRY(up(&F.pw[ax], pw));
+  TRY(up(&F.pwf[ax], pwf));
+  TRY(up(&F.rc[ax], rc));
+  TRY(up(&F.ri[ax], ri));
+  TRY(up(&F.rw[ax], rw));
+  TRY(up(&F.rwf[ax], rwf));
+  return RICH_OK;
+}
+
+rich::Geom geom(const richards_ctx* c, int l) {
+  rich::Geom G;
+  G.dim = c->grid.dim;
+  G.n0 = c->L[l].n[0];
+  G.n1 = c->L[l].n[1];
+  G.n2 = c->L[l].n[2];
+  for (int a = 0; a < 3; ++a) G.h[a] = c->L[l].h[a];
+  G.Lv = c->grid.L[c->grid.dim - 1];
+  return G;
+}
+
+Level<double> view64(const richards_ctx* c, int l) {
+  const HLevel& H = c->L[l];
+  Level<double> V{};
+  V.dim = c->grid.dim;
+  V.n0 = H.n[0]; V.n1 = H.n[1]; V.n2 = H.n[2];
+  V.ncell = H.ncell;
+  for (int a = 0; a < 3; ++a) V.ih2[a] = a < c->grid.dim ? 1.0 / (H.h[a] * H.h[a]) : 0.0;
+  V.u = H.u; V.ubar = H.ubar; V.g = H.g; V.d = H.d; V.Kc = H.Kc;
+  V.p1 = c->het_p1 ? H.p1 : nullptr;
+  V.p2 = c->het_p2 ? H.p2 : nullptr;
+  V.smax = c->sink.enabled ? H.smax : nullptr;
+  V.psi0 = nullptr;
+  for (int f = 0; f < 6; ++f) V.kb[f] = H.kb[f];
+  return V;
+}
+
+Level<float> view32(const richards_ctx* c, int l) {
+  const HLevel& H = c->L[l];
+  Level<float> V{};
+  V.dim = c->grid.dim;
+  V.n0 = H.n[0]; V.n1 = H.n[1]; V.n2 = H.n[2];
+  V.ncell = H.ncell;
+  for (int a = 0; a < 3; ++a) V.ih2[a] = a < c->grid.dim ? (float)(1.0 / (H.h[a] * H.h[a])) : 0.0f;
+  V.u = H.uf; V.ubar = H.ubarf; V.g = H.gf; V.d = H.df; V.Kc = H.Kcf;
+  V.p1 = c->het_p1 ? H.p1f : nullptr;
+  V.p2 = c->het_p2 ? H.p2f : nullptr;
+  V.smax = c->sink.enabled ? H.smaxf : nullptr;
+  V.psi0 = H.psi0f;
+  for (int f = 0; f < 6; ++f) V.kb[f] = H.kbf[f];
+  return V;
+}
+
+Xfer<double> xfer64(const richards_ctx* c, int l) {
+  const HLevel& H = c->L[l];
+  Xfer<double> X{};
+  for (int a = 0; a < 3; ++a) {
+    X.pc[a] = H.pc[a]; X.pj[a] = H.pj[a]; X.pw[a] = H.pw[a];
+    X.rc[a] = H.rc[a]; X.ri[a] = H.ri[a]; X.rw[a] = H.rw[a];
+  }
+  return X;
+}
+
+Xfer<float> xfer32(const richards_ctx* c, int l) {
+  const HLevel& H = c->L[l];
+  Xfer<float> X{};
+  for (int a = 0; a < 3; ++a) {
+    X.pc[a] = H.pc[a]; X.pj[a] = H.pj[a]; X.pw[a] = H.pwf[a];
+    X.rc[a] = H.rc[a]; X.ri[a] = H.ri[a]; X.rw[a] = H.rwf[a];
+  }
+  return X;
+}
+
+template <typename T>
+Phys<T> phys(const richards_ctx* c) {
+  Phys<T> P{};
+  P.a = (T)c->a;
+  P.xi = (T)c->opts.xi;
+  P.kappa = (T)(c->opts.kappa_mode == 0 ? c->opts.kappa : 0.0);
+  P.ts = (T)c->soil.theta_s;
+  P.tr = (T)c->soil.theta_r;
+  P.p1 = (T)c->soil.p1; P.p2 = (T)c->soil.p2; P.p3 = (T)c->soil.p3; P.p4 = (T)c->soil.p4;
+  P.h1 = (T)c->sink.h1; P.h2 = (T)c->sink.h2; P.h3 = (T)c->sink.h3; P.h4 = (T)c->sink.h4;
+  P.newton_k = c->opts.newton_iters;
+  P.sink = c->sink.enabled;
+  return P;
+}
+
+// upload the level views and transfer tables the coarse-tail kernel reads
+richards_status upload_views(richards_ctx* c) {
+  std::vector<Level<double>> v64(c->nlev);
+  std::vector<Xfer<double>> x64(c->nlev);
+  std::vector<Level<float>> v32(c->nlev);
+  std::vector<Xfer<float>> x32(c->nlev);
+  for (int l = 0; l < c->nlev; ++l) {
+    v64[l] = view64(c, l);
+    x64[l] = xfer64(c, l);
+    v32[l] = view32(c, l);
+    x32[l] = xfer32(c, l);
+  }
+  CK(cudaMemcpyAsync(c->dL64, v64.data(), sizeof(Level<double>) * c->nlev, cudaMemcpyHostToDevice, c->s));
+  CK(cudaMemcpyAsync(c->dX64, x64.data(), sizeof(Xfer<double>) * c->nlev, cudaMemcpyHostToDevice, c->s));
+  CK(cudaMemcpyAsync(c->dL32, v32.data(), sizeof(Level<float>) * c->nlev, cudaMemcpyHostToDevice, c->s));
+  CK(cudaMemcpyAsync(c->dX32, x32.data(), sizeof(Xfer<float>) * c->nlev, cudaMemcpyHostToDevice, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status check_launch(richards_ctx* c) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, RICH_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return RICH_OK;
+}
+
+// ||.||_inf of a freshly computed defect (slot k of the scratch area)
+richards_status read_norm(richards_ctx* c, int k, double* out, bool fp32) {
+  CK(cudaMemcpyAsync(c->hscratch + k, c->scratch + k, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  const unsigned long long b = c->hscratch[k];
+  if (fp32) {
+    unsigned u = (unsigned)b;
+    float f;
+    std::memcpy(&f, &u, 4);
+    *out = (double)f;
+  } else {
+    std::memcpy(out, &b, 8);
+  }
+  return RICH_OK;
+}
+
+richards_status norm64(richards_ctx* c, int l, double* out) {
+  CK(cudaMemsetAsync(c->scratch, 0, sizeof(unsigned long long), c->s));
+  {
+    Prof pr(c, "residual64", l, c->L[l].ncell);
+    rich::residual64(view64(c, l), phys<double>(c), c->soil.model, c->scratch, c->s);
+  }
+  TRY(check_launch(c));
+  return read_norm(c, 0, out, false);
+}
+
+// ------------------------------------------------------------------------
+// One V-cycle (Section 3.2, steps 1-7 with the coarse solve replaced by the
+// recursion) from level l: grid kernels down to the coarse tail, which runs
+// in one thread block.
+// ------------------------------------------------------------------------
+void vcycle64(richards_ctx* c, int l) {
+  const int model = c->soil.model;
+  const Phys<double> P = phys<double>(c);
+  if (l >= c->tail_start) {
+    Prof pr(c, "tail64", l, c->L[l].ncell);
+    rich::tail64(c->dL64, c->dX64, l, c->nlev, P, model, c->opts.nu1, c->opts.nu2, c->opts.coarse_max_sweeps,
+                 c->opts.coarse_rtol, c->scratch + 16, c->s);
+    return;
+  }
+  const Level<double> F = view64(c, l), C = view64(c, l + 1);
+  const long long half = (F.ncell + 1) / 2;
+  for (int k = 0; k < c->opts.nu1; ++k) {
+    { Prof pr(c, "sweep64", l, half); rich::sweep64(F, P, model, 0, c->s); }
+    { Prof pr(c, "sweep64", l, F.ncell - half); rich::sweep64(F, P, model, 1, c->s); }
+  }
+  c->updates_host += (long long)c->opts.nu1 * F.ncell;
+  { Prof pr(c, "residual64", l, F.ncell); rich::residual64(F, P, model, nullptr, c->s); }
+  { Prof pr(c, "restrict64", l, C.ncell); rich::restrict64(F, C, xfer64(c, l), F.u, F.d, C.ubar, C.d, c->s); }
+  { Prof pr(c, "tau64", l + 1, C.ncell); rich::tau64(C, P, model, c->s); }
+  vcycle64(c, l + 1);
+  { Prof pr(c, "prolong64", l, F.ncell); rich::prolong64(F, C, xfer64(c, l), c->s); }
+  for (int k = 0; k < c->opts.nu2; ++k) {
+    { Prof pr(c, "sweep64", l, half); rich::sweep64(F, P, model, 0, c->s); }
+    { Prof pr(c, "sweep64", l, F.ncell - half); rich::sweep64(F, P, model, 1, c->s); }
+  }
+  c->updates_host += (long long)c->opts.nu2 * F.ncell;
+}
+
+void vcycle32(richards_ctx* c, int l) {
+  const int model = c->soil.model;
+  const Phys<float> P = phys<float>(c);
+  if (l >= c->tail_start) {
+    Prof pr(c, "tail32", l, c->L[l].ncell);
+    rich::tail32(c->dL32, c->dX32, l, c->nlev, P, model, c->opts.nu1, c->opts.nu2, c->opts.coarse_max_sweeps,
+                 (float)c->opts.coarse_rtol, c->scratch + 16, c->s);
+    return;
+  }
+  const Level<float> F = view32(c, l), C = view32(c, l + 1);
+  const long long half = (F.ncell + 1) / 2;
+  for (int k = 0; k < c->opts.nu1; ++k) {
+    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->s); }
+    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->s); }
+  }
+  c->updates_host += (long long)c->opts.nu1 * F.ncell;
+  { Prof pr(c, "residual32", l, F.ncell); rich::residual32(F, P, model, nullptr, c->s); }
+  { Prof pr(c, "restrict32", l, C.ncell); rich::restrict32(F, C, xfer32(c, l), F.u, F.d, C.ubar, C.d, c->s); }
+  { Prof pr(c, "tau32", l + 1, C.ncell); rich::tau32(C, P, model, c->s); }
+  vcycle32(c, l + 1);
+  { Prof pr(c, "prolong32", l, F.ncell); rich::prolong32(F, C, xfer32(c, l), c->s); }
+  for (int k = 0; k < c->opts.nu2; ++k) {
+    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->s); }
+    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->s); }
+  }
+  c->updates_host += (long long)c->opts.nu2 * F.ncell;
+}
+
+// coarse copies of the lagged conductivity and boundary conductances
+richards_status restrict_coefficients(richards_ctx* c) {
+  Prof pr(c, "coefficients", 0, c->L[0].ncell);
+  for (int l = 0; l + 1 < c->nlev; ++l) {
+    const Level<double> F = view64(c, l), C = view64(c, l + 1);
+    rich::restrict64(F, C, xfer64(c, l), c->L[l].Kc, nullptr, c->L[l + 1].Kc, nullptr, c->s);
+    for (int f = 0; f < 2 * c->grid.dim; ++f)
+      rich::restrict_face64(geom(c, l), geom(c, l + 1), xfer64(c, l), f / 2, c->L[l].kb[f], c->L[l + 1].kb[f], c->s);
+  }
+  if (c->opts.precision == 1) {
+    for (int l = 0; l < c->nlev; ++l) {
+      rich::to_float(c->L[l].Kc, c->L[l].Kcf, c->L[l].ncell, c->s);
+      for (int f = 0; f < 2 * c->grid.dim; ++f) rich::to_float(c->L[l].kb[f], c->L[l].kbf[f], c->L[l].nface[f], c->s);
+    }
+  }
+  return check_launch(c);
+}
+
+richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
+  if (!c->soil_set) return fail(c, RICH_EINVAL, "soil not set");
+  if (!c->bc_set) return fail(c, RICH_EINVAL, "boundary conditions not set");
+  if (!c->have_state) return fail(c, RICH_EINVAL, "state not set");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, RICH_EINVAL, "dt must be positive and finite");
+  if (scheme != 1 && scheme != 2) return fail(c, RICH_EINVAL, "scheme must be 1 (BDF1) or 2 (BDF2)");
+  if (scheme == 2 && !c->have_prev) scheme = 1;
+  c->scheme_used = scheme;
+  c->dt = dt;
+  c->a = scheme == 1 ? 1.0 / dt : 1.5 / dt;
+  const Phys<double> P = phys<double>(c);
+  HLevel& F = c->L[0];
+  Prof pr(c, "prep", 0, F.ncell);
+  rich::prep_lagged(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
+                    c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, P, c->soil.model, scheme, dt, F.Kc, F.g,
+                    F.u, c->s);
+  double* kbw[6];
+  for (int f = 0; f < 6; ++f) kbw[f] = F.kb[f];
+  rich::prep_rhs(geom(c, 0), c->bcdev, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
+                 c->het_p2 ? F.p2 : nullptr, P, c->soil.model, F.Kc, F.g, kbw, c->s);
+  TRY(check_launch(c));
+  TRY(restrict_coefficients(c));
+  c->prepared = true;
+  return RICH_OK;
+}
+
+richards_status finish_step(richards_ctx* c, double r, richards_status st) {
+  if (std::isnan(r)) return fail(c, RICH_ENAN, "NaN in the iterate; state kept at psi^n");
+  std::swap(c->psi_n, c->psi_nm1);
+  CK(cudaMemcpyAsync(c->psi_n, c->L[0].u, sizeof(double) * c->L[0].ncell, cudaMemcpyDeviceToDevice, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  c->have_prev = true;
+  c->t += c->dt;
+  if (st != RICH_OK) return fail(c, st, "no convergence within the cycle limit");
+  return RICH_OK;
+}
+
+richards_status read_stats(richards_ctx* c, long long* tail_updates) {
+  CK(cudaMemcpyAsync(c->hscratch + 16, c->scratch + 16, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  *tail_updates = (long long)c->hscratch[16];
+  return RICH_OK;
+}
+
+richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
+  const double teff = 1.0 / c->a;
+  double nrm;
+  TRY(norm64(c, 0, &nrm));
+  double r = teff * nrm;
+  const double r0 = r;
+  int cycles = 0;
+  while (!(r <= c->opts.tol) && cycles < c->opts.max_cycles && !std::isnan(r)) {
+    vcycle64(c, 0);
+    TRY(check_launch(c));
+    ++cycles;
+    TRY(norm64(c, 0, &nrm));
+    r = teff * nrm;
+  }
+  long long tu = 0;
+  TRY(read_stats(c, &tu));
+  if (info) {
+    info->cycles = cycles;
+    info->outer_iters = 0;
+    info->scheme_used = c->scheme_used;
+    info->resid0 = r0;
+    info->resid = r;
+    info->cell_updates = c->updates_host + tu;
+  }
+  return finish_step(c, r, r <= c->opts.tol ? RICH_OK : RICH_ENOCONV);
+}
+
+// Mixed precision: FP64 defect r = g - N(psi); FP32 FAS V-cycles on the
+// correction equation N(psi + delta) - N(psi) = r; psi += delta; repeat until
+// the FP64 stop test holds.
+richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
+  const double teff = 1.0 / c->a;
+  const int model = c->soil.model;
+  const Phys<double> P64 = phys<double>(c);
+  const Phys<float> P32 = phys<float>(c);
+  HLevel& F = c->L[0];
+  double r = 0.0, r0 = 0.0;
+  int outer = 0, inner = 0;
+  richards_status st = RICH_OK;
+  for (;;) {
+    CK(cudaMemsetAsync(c->scratch, 0, sizeof(unsigned long long), c->s));
+    {
+      Prof pr(c, "outer_residual", 0, F.ncell);
+      rich::outer_residual(view64(c, 0), P64, model, F.gf, F.psi0f, F.uf, c->scratch, c->s);
+    }
+    TRY(check_launch(c));
+    double nrm;
+    TRY(read_norm(c, 0, &nrm, false));
+    r = teff * nrm;
+    if (outer == 0) r0 = r;
+    if (!(r > c->opts.tol) || std::isnan(r)) break;
+    if (outer >= c->opts.max_outer) { st = RICH_ENOCONV; break; }
+    for (int l = 0; l + 1 < c->nlev; ++l) {
+      Prof pr(c, "restrict_psi0", l, c->L[l + 1].ncell);
+      rich::restrict32(view32(c, l), view32(c, l + 1), xfer32(c, l), c->L[l].psi0f, nullptr, c->L[l + 1].psi0f,
+                       nullptr, c->s);
+    }
+    const double rin0 = nrm;
+    for (int k = 0; k < c->opts.inner_cycles; ++k) {
+      vcycle32(c, 0);
+      ++inner;
+      if (c->opts.inner_rtol > 0.0 && k + 1 < c->opts.inner_cycles) {
+        CK(cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s));
+        {
+          Prof pr(c, "residual32", 0, F.ncell);
+          rich::residual32(view32(c, 0), P32, model, c->scratch + 1, c->s);
+        }
+        double rin;
+        TRY(read_norm(c, 1, &rin, true));
+        if (rin <= c->opts.inner_rtol * rin0) break;
+      }
+    }
+    {
+      Prof pr(c, "apply_delta", 0, F.ncell);
+      rich::apply_delta(F.u, F.uf, F.ncell, c->s);
+    }
+    TRY(check_launch(c));
+    ++outer;
+  }
+  long long tu = 0;
+  TRY(read_stats(c, &tu));
+  if (info) {
+    info->cycles = inner;
+    info->outer_iters = outer;
+    info->scheme_used = c->scheme_used;
+    info->resid0 = r0;
+    info->resid = r;
+    info->cell_updates = c->updates_host + tu;
+  }
+  return finish_step(c, r, st);
+}
+
+richards_status check_ctx(const richards_ctx* c) { return c ? RICH_OK : RICH_EINVAL; }
+
+}  // namespace
+
+// ==========================================================================
+// extern "C" entry points
+// ==========================================================================
+extern "C" {
+
+richards_status richards_create(const richards_grid* grid, const richards_opts* opts, void* stream,
+                                richards_ctx** out) {
+  if (!grid || !opts || !out) return RICH_EINVAL;
+  *out = nullptr;
+  if (grid->dim < 1 || grid->dim > 3) return RICH_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    if (grid->n[a] < 1) return RICH_EINVAL;
+    if (a >= grid->dim && grid->n[a] != 1) return RICH_EINVAL;
+    if (a < grid->dim && !(grid->L[a] > 0.0 && std::isfinite(grid->L[a]))) return RICH_EINVAL;
+  }
+  const richards_opts& o = *opts;
+  if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max_sweeps < 1 || o.max_cycles < 0 || o.coarsest_max_n < 1 ||
+      !(o.tol > 0.0) || o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
+      o.ordering != 1 || (o.precision != 0 && o.precision != 1) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
+      o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0)
+    return RICH_EINVAL;
+  richards_ctx* c = new richards_ctx();
+  c->s = (cudaStream_t)stream;
+  c->grid = *grid;
+  c->opts = o;
+  // hierarchy: halve every axis with n > 1 while max n > coarsest_max_n
+  for (int a = 0; a < 3; ++a) {
+    c->L[0].n[a] = grid->n[a];
+    c->L[0].h[a] = a < grid->dim ? grid->L[a] / grid->n[a] : 1.0;
+  }
+  c->nlev = 1;
+  for (;;) {
+    const HLevel& F = c->L[c->nlev - 1];
+    const int mx = std::max(F.n[0], std::max(F.n[1], F.n[2]));
+    if (mx <= o.coarsest_max_n) break;
+    if (o.max_levels > 0 && c->nlev >= o.max_levels) break;
+    if (c->nlev >= MAXLEV) break;
+    HLevel& C = c->L[c->nlev];
+    for (int a = 0; a < 3; ++a) {
+      C.n[a] = F.n[a] > 1 ? (F.n[a] + 1) / 2 : 1;
+      C.h[a] = a < grid->dim ? grid->L[a] / C.n[a] : 1.0;
+    }
+    c->nlev++;
+  }
+  c->tail_start = c->nlev - 1;
+  for (int l = 0; l < c->nlev; ++l)
+    if ((long long)c->L[l].n[0] * c->L[l].n[1] * c->L[l].n[2] <= o.tail_cells) { c->tail_start = l; break; }
+  const bool mixed = o.precision == 1;
+  richards_status st = RICH_OK;
+  for (int l = 0; l < c->nlev && st == RICH_OK; ++l) {
+    HLevel& H = c->L[l];
+    H.ncell = (long long)H.n[0] * H.n[1] * H.n[2];
+    const long long n = H.ncell;
+    for (int f = 0; f < 6; ++f) H.nface[f] = (f / 2 < grid->dim) ? n / H.n[f / 2] : 0;
+    double** d64[] = {&H.u, &H.ubar, &H.g, &H.d, &H.Kc};
+    for (auto p : d64)
+      if (st == RICH_OK) st = dalloc(c, p, n);
+    for (int f = 0; f < 2 * grid->dim && st == RICH_OK; ++f) st = dalloc(c, &H.kb[f], H.nface[f]);
+    if (mixed) {
+      float** d32[] = {&H.uf, &H.ubarf, &H.gf, &H.df, &H.Kcf, &H.psi0f};
+      for (auto p : d32)
+        if (st == RICH_OK) st = dalloc(c, p, n);
+      for (int f = 0; f < 2 * grid->dim && st == RICH_OK; ++f) st = dalloc(c, &H.kbf[f], H.nface[f]);
+    }
+  }
+  const long long N = c->L[0].ncell;
+  if (st == RICH_OK) st = dalloc(c, &c->psi_n, N);
+  if (st == RICH_OK) st = dalloc(c, &c->psi_nm1, N);
+  if (st == RICH_OK) st = dalloc(c, &c->dL64, c->nlev);
+  if (st == RICH_OK) st = dalloc(c, &c->dX64, c->nlev);
+  if (st == RICH_OK) st = dalloc(c, &c->dL32, c->nlev);
+  if (st == RICH_OK) st = dalloc(c, &c->dX32, c->nlev);
+  if (st == RICH_OK) st = dalloc(c, &c->scratch, NSCRATCH);
+  if (st == RICH_OK && cudaMallocHost((void**)&c->hscratch, NSCRATCH * sizeof(unsigned long long)) != cudaSuccess)
+    st = fail(c, RICH_ENOMEM, "cudaMallocHost failed");
+  if (st == RICH_OK && cudaMemsetAsync(c->scratch, 0, NSCRATCH * sizeof(unsigned long long), c->s) != cudaSuccess)
+    st = fail(c, RICH_ECUDA, "cudaMemsetAsync failed");
+  if (st != RICH_OK) {
+    richards_destroy(c);
+    return st;
+  }
+  *out = c;
+  return RICH_OK;
+}
+
+void richards_destroy(richards_ctx* c) {
+  if (!c) return;
+  if (c->s) cudaStreamSynchronize(c->s); else cudaDeviceSynchronize();
+  for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->bc_allocs) cudaFree(p);
+  if (c->hscratch) cudaFreeHost(c->hscratch);
+  delete c;
+}
+
+const char* richards_last_error(const richards_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+double richards_time(const richards_ctx* c) { return c ? c->t : 0.0; }
+long long richards_ncell(const richards_ctx* c) { return c ? c->L[0].ncell : 0; }
+int richards_nlevels(const richards_ctx* c) { return c ? c->nlev : 0; }
+
+richards_status richards_level_dims(const richards_ctx* c, int level, int n_out[3]) {
+  if (!c || !n_out || level < 0 || level >= c->nlev) return RICH_EINVAL;
+  for (int a = 0; a < 3; ++a) n_out[a] = c->L[level].n[a];
+  return RICH_OK;
+}
+
+richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
+  if (!c || !s) return RICH_EINVAL;
+  const long long N = c->L[0].ncell;
+  const bool ok = s->model >= 0 && s->model <= 2 && std::isfinite(s->Ks) && s->Ks > 0.0 &&
+                  std::isfinite(s->theta_s) && std::isfinite(s->theta_r) && s->theta_r >= 0.0 &&
+                  s->theta_s > s->theta_r;
+  if (!ok) return fail(c, RICH_EINVAL, "invalid soil: need Ks > 0, theta_s > theta_r >= 0");
+  auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
+  if (s->model == RICH_HAVERKAMP && !(pos(s->p3) && pos(s->p4) && (s->p1_field || pos(s->p1)) &&
+                                      (s->p2_field || pos(s->p2))))
+    return fail(c, RICH_EINVAL, "Haverkamp needs alpha, beta, A, gamma > 0");
+  if (s->model == RICH_GARDNER && !(s->p1_field || pos(s->p1)))
+    return fail(c, RICH_EINVAL, "Gardner needs alpha > 0");
+  if (s->model == RICH_VANGENUCHTEN &&
+      !((s->p1_field || pos(s->p1)) && (s->p2_field || (std::isfinite(s->p2) && s->p2 > 1.0)) &&
+        std::isfinite(s->p3)))
+    return fail(c, RICH_EINVAL, "van Genuchten needs alpha > 0, n > 1, finite l");
+  if ((s->Ks_field && !finite_all(s->Ks_field, N)) || (s->p1_field && !finite_all(s->p1_field, N)) ||
+      (s->p2_field && !finite_all(s->p2_field, N)))
+    return fail(c, RICH_EINVAL, "non-finite value in a soil field");
+  if (s->Ks_field)
+    for (long long i = 0; i < N; ++i)
+      if (!(s->Ks_field[i] > 0.0)) return fail(c, RICH_EINVAL, "Ks field must be positive");
+  if (s->p2_field && s->model == RICH_VANGENUCHTEN)
+    for (long long i = 0; i < N; ++i)
+      if (!(s->p2_field[i] > 1.0)) return fail(c, RICH_EINVAL, "van Genuchten n field must exceed 1");
+  c->soil = *s;
+  c->soil.Ks_field = c->soil.p1_field = c->soil.p2_field = nullptr;
+  c->het_Ks = s->Ks_field != nullptr;
+  c->het_p1 = s->p1_field != nullptr;
+  c->het_p2 = s->p2_field != nullptr;
+  const bool mixed = c->opts.precision == 1;
+  if (c->het_Ks) {
+    if (!c->Ks) TRY(dalloc(c, &c->Ks, N));
+    CK(cudaMemcpyAsync(c->Ks, s->Ks_field, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
+  }
+  const double* fields[2] = {s->p1_field, s->p2_field};
+  for (int k = 0; k < 2; ++k) {
+    if (!fields[k]) continue;
+    for (int l = 0; l < c->nlev; ++l) {
+      HLevel& H = c->L[l];
+      double*& p = k == 0 ? H.p1 : H.p2;
+      float*& pf = k == 0 ? H.p1f : H.p2f;
+      if (!p) TRY(dalloc(c, &p, H.ncell));
+      if (mixed && !pf) TRY(dalloc(c, &pf, H.ncell));
+    }
+    CK(cudaMemcpyAsync(k == 0 ? c->L[0].p1 : c->L[0].p2, fields[k], sizeof(double) * N, cudaMemcpyHostToDevice,
+                       c->s));
+  }
+  CK(cudaStreamSynchronize(c->s));
+  c->soil_set = true;
+  if (c->bc_set) {
+    // coarse parameters need the transfer tables, built with the boundary conditions
+    for (int l = 0; l + 1 < c->nlev; ++l) {
+      const Level<double> F = view64(c, l), C = view64(c, l + 1);
+      if (c->het_p1) rich::restrict64(F, C, xfer64(c, l), c->L[l].p1, nullptr, c->L[l + 1].p1, nullptr, c->s);
+      if (c->het_p2) rich::restrict64(F, C, xfer64(c, l), c->L[l].p2, nullptr, c->L[l + 1].p2, nullptr, c->s);
+    }
+    if (mixed)
+      for (int l = 0; l < c->nlev; ++l) {
+        if (c->het_p1) rich::to_float(c->L[l].p1, c->L[l].p1f, c->L[l].ncell, c->s);
+        if (c->het_p2) rich::to_float(c->L[l].p2, c->L[l].p2f, c->L[l].ncell, c->s);
+      }
+    TRY(check_launch(c));
+    TRY(upload_views(c));
+  }
+  return RICH_OK;
+}
+
+static richards_status refresh_sink(richards_ctx* c) {
+  if (!c->sink.enabled || !c->bc_set) return RICH_OK;
+  const bool mixed = c->opts.precision == 1;
+  for (int l = 0; l < c->nlev; ++l) {
+    HLevel& H = c->L[l];
+    if (!H.smax) TRY(dalloc(c, &H.smax, H.ncell));
+    if (mixed && !H.smaxf) TRY(dalloc(c, &H.smaxf, H.ncell));
+  }
+  rich::sink_coef(geom(c, 0), c->sink.Tp, c->sink.root_depth, c->sink.root_decay, c->L[0].smax, c->s);
+  for (int l = 0; l + 1 < c->nlev; ++l)
+    rich::restrict64(view64(c, l), view64(c, l + 1), xfer64(c, l), c->L[l].smax, nullptr, c->L[l + 1].smax, nullptr,
+                     c->s);
+  if (mixed)
+    for (int l = 0; l < c->nlev; ++l) rich::to_float(c->L[l].smax, c->L[l].smaxf, c->L[l].ncell, c->s);
+  TRY(check_launch(c));
+  return upload_views(c);
+}
+
+richards_status richards_set_sink(richards_ctx* c, const richards_sink* k) {
+  if (!c || !k) return RICH_EINVAL;
+  if (k->enabled) {
+    const double v[] = {k->Tp, k->root_depth, k->root_decay, k->h1, k->h2, k->h3, k->h4};
+    for (double x : v)
+      if (!std::isfinite(x)) return fail(c, RICH_EINVAL, "non-finite sink parameter");
+    if (!(k->h4 < k->h3 && k->h3 <= k->h2 && k->h2 < k->h1) || !(k->Tp >= 0.0) || !(k->root_decay > 0.0) ||
+        !(k->root_depth > 0.0))
+      return fail(c, RICH_EINVAL, "sink needs h4 < h3 <= h2 < h1, Tp >= 0, root depth and decay > 0");
+  }
+  c->sink = *k;
+  return refresh_sink(c);
+}
+
+richards_status richards_set_bc(richards_ctx* c, const richards_bc* b) {
+  if (!c || !b) return RICH_EINVAL;
+  const int dim = c->grid.dim;
+  const HLevel& F = c->L[0];
+  for (int f = 0; f < 2 * dim; ++f) {
+    if (b->kind[f] < 0 || b->kind[f] > 3) return fail(c, RICH_EINVAL, "unknown boundary kind");
+    if (b->kind[f] == RICH_BC_FREE_DRAINAGE && f != 2 * (dim - 1))
+      return fail(c, RICH_EINVAL, "free drainage is only defined on the bottom face");
+    if (!std::isfinite(b->value[f])) return fail(c, RICH_EINVAL, "non-finite boundary value");
+    if (b->value_field[f] && !finite_all(b->value_field[f], F.nface[f]))
+      return fail(c, RICH_EINVAL, "non-finite boundary field");
+  }
+  // release tables and fields of an earlier call
+  cudaStreamSynchronize(c->s);
+  for (void* p : c->bc_allocs) cudaFree(p);
+  c->bc_allocs.clear();
+  c->bc = *b;
+  rich::BcDev bd{};
+  for (int f = 0; f < 6; ++f) {
+    bd.kind[f] = f < 2 * dim ? b->kind[f] : RICH_BC_NOFLUX;
+    bd.value[f] = f < 2 * dim ? b->value[f] : 0.0;
+    bd.vfield[f] = nullptr;
+    bd.mask[f] = nullptr;
+    c->bc.value_field[f] = nullptr;
+    c->bc.mask_field[f] = nullptr;
+    if (f >= 2 * dim) continue;
+    if (b->value_field[f]) {
+      double* p;
+      TRY(dalloc(c, &p, F.nface[f], &c->bc_allocs));
+      CK(cudaMemcpy(p, b->value_field[f], sizeof(double) * F.nface[f], cudaMemcpyHostToDevice));
+      bd.vfield[f] = p;
+    }
+    if (b->mask_field[f]) {
+      unsigned char* p;
+      TRY(dalloc(c, &p, F.nface[f], &c->bc_allocs));
+      CK(cudaMemcpy(p, b->mask_field[f], F.nface[f], cudaMemcpyHostToDevice));
+      bd.mask[f] = p;
+    }
+  }
+  c->bcdev = bd;
+  for (int l = 0; l + 1 < c->nlev; ++l)
+    for (int ax = 0; ax < 3; ++ax) {
+      double slo = 1.0, shi = 1.0;
+      if (ax < dim) {
+        if (b->kind[2 * ax] == RICH_BC_DIRICHLET && !b->mask_field[2 * ax]) slo = -1.0;
+        if (b->kind[2 * ax + 1] == RICH_BC_DIRICHLET && !b->mask_field[2 * ax + 1]) shi = -1.0;
+      }
+      TRY(build_axis_tables(c, l, ax, slo, shi));
+    }
+  c->bc_set = true;
+  TRY(upload_views(c));
+  if (c->soil_set) {
+    richards_soil s = c->soil;   // re-run the coarse parameter restriction with the new tables
+    (void)s;
+    for (int l = 0; l + 1 < c->nlev; ++l) {
+      const Level<double> Fv = view64(c, l), Cv = view64(c, l + 1);
+      if (c->het_p1) rich::restrict64(Fv, Cv, xfer64(c, l), c->L[l].p1, nullptr, c->L[l + 1].p1, nullptr, c->s);
+      if (c->het_p2) rich::restrict64(Fv, Cv, xfer64(c, l), c->L[l].p2, nullptr, c->L[l + 1].p2, nullptr, c->s);
+    }
+    if (c->opts.precision == 1)
+      for (int l = 0; l < c->nlev; ++l) {
+        if (c->het_p1) rich::to_float(c->L[l].p1, c->L[l].p1f, c->L[l].ncell, c->s);
+        if (c->het_p2) rich::to_float(c->L[l].p2, c->L[l].p2f, c->L[l].ncell, c->s);
+      }
+    TRY(check_launch(c));
+  }
+  return refresh_sink(c);
+}
+
+richards_status richards_set_state(richards_ctx* c, const double* psi, const double* psi_prev, double t) {
+  if (!c || !psi) return RICH_EINVAL;
+  const long long N = c->L[0].ncell;
+  if (!finite_all(psi, N) || (psi_prev && !finite_all(psi_prev, N)) || !std::isfinite(t))
+    return fail(c, RICH_EINVAL, "non-finite state");
+  CK(cudaMemcpyAsync(c->psi_n, psi, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
+  if (psi_prev) CK(cudaMemcpyAsync(c->psi_nm1, psi_prev, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  c->have_state = true;
+  c->have_prev = psi_prev != nullptr;
+  c->t = t;
+  return RICH_OK;
+}
+
+richards_status richards_get_state(richards_ctx* c, double* out, int on_device) {
+  if (!c || !out) return RICH_EINVAL;
+  if (!c->have_state) return fail(c, RICH_EINVAL, "state not set");
+  CK(cudaMemcpyAsync(out, c->psi_n, sizeof(double) * c->L[0].ncell,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status richards_prepare(richards_ctx* c, double dt, int scheme, int* scheme_used) {
+  if (!c) return RICH_EINVAL;
+  TRY(do_prepare(c, dt, scheme));
+  if (scheme_used) *scheme_used = c->scheme_used;
+  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status richards_step(richards_ctx* c, double dt, int scheme, richards_step_info* info) {
+  if (!c) return RICH_EINVAL;
+  c->updates_host = 0;
+  CK(cudaMemsetAsync(c->scratch + 16, 0, sizeof(unsigned long long), c->s));
+  TRY(do_prepare(c, dt, scheme));
+  return c->opts.precision == 1 ? step_mixed(c, info) : step_fp64(c, info);
+}
+
+richards_status richards_solve(richards_ctx* c, double dt, int nsteps, int scheme, richards_step_info* last) {
+  if (!c || nsteps < 0) return RICH_EINVAL;
+  for (int k = 0; k < nsteps; ++k) TRY(richards_step(c, dt, scheme, last));
+  return RICH_OK;
+}
+
+richards_status richards_get_level(richards_ctx* c, int level, int which, double* out, long long n) {
+  if (!c || !out || level < 0 || level >= c->nlev) return RICH_EINVAL;
+  HLevel& H = c->L[level];
+  const double* src = nullptr;
+  long long cnt = H.ncell;
+  switch (which) {
+    case 0: src = H.u; break;
+    case 1: src = H.g; break;
+    case 2: src = H.Kc; break;
+    case 3: src = c->het_p1 ? H.p1 : nullptr; break;
+    case 4: src = c->het_p2 ? H.p2 : nullptr; break;
+    case 5: src = c->sink.enabled ? H.smax : nullptr; break;
+    case 6: src = H.ubar; break;
+    case 7: src = H.d; break;
+    default:
+      if (which >= 10 && which < 16) { src = H.kb[which - 10]; cnt = H.nface[which - 10]; }
+  }
+  if (!src) return fail(c, RICH_EINVAL, "array not available");
+  if (n != cnt) return fail(c, RICH_EINVAL, "size mismatch");
+  CK(cudaMemcpyAsync(out, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status richards_set_level(richards_ctx* c, int level, int which, const double* in, long long n) {
+  if (!c || !in || level < 0 || level >= c->nlev || (which != 0 && which != 1)) return RICH_EINVAL;
+  HLevel& H = c->L[level];
+  if (n != H.ncell) return fail(c, RICH_EINVAL, "size mismatch");
+  CK(cudaMemcpyAsync(which == 0 ? H.u : H.g, in, sizeof(double) * n, cudaMemcpyHostToDevice, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status richards_sweep(richards_ctx* c, int level, int color) {
+  if (!c || level < 0 || level >= c->nlev || color < -1 || color > 1) return RICH_EINVAL;
+  if (!c->prepared) return fail(c, RICH_EINVAL, "call richards_prepare first");
+  const Level<double> L = view64(c, level);
+  const Phys<double> P = phys<double>(c);
+  if (color != 1) rich::sweep64(L, P, c->soil.model, 0, c->s);
+  if (color != 0) rich::sweep64(L, P, c->soil.model, 1, c->s);
+  TRY(check_launch(c));
+  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status richards_residual(richards_ctx* c, int level, double* norm) {
+  if (!c || level < 0 || level >= c->nlev) return RICH_EINVAL;
+  if (!c->prepared) return fail(c, RICH_EINVAL, "call richards_prepare first");
+  double nr;
+  TRY(norm64(c, level, &nr));
+  if (norm) *norm = nr;
+  return RICH_OK;
+}
+
+richards_status richards_restrict_tau(richards_ctx* c, int level) {
+  if (!c || level < 0 || level + 1 >= c->nlev) return RICH_EINVAL;
+  if (!c->prepared) return fail(c, RICH_EINVAL, "call richards_prepare first");
+  const Level<double> F = view64(c, level), C = view64(c, level + 1);
+  const Phys<double> P = phys<double>(c);
+  rich::residual64(F, P, c->soil.model, nullptr, c->s);
+  rich::restrict64(F, C, xfer64(c, level), F.u, F.d, C.ubar, C.d, c->s);
+  rich::tau64(C, P, c->soil.model, c->s);
+  TRY(check_launch(c));
+  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status richards_prolong(richards_ctx* c, int level) {
+  if (!c || level < 0 || level + 1 >= c->nlev) return RICH_EINVAL;
+  rich::prolong64(view64(c, level), view64(c, level + 1), xfer64(c, level), c->s);
+  TRY(check_launch(c));
+  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status richards_vcycle(richards_ctx* c) {
+  if (!c) return RICH_EINVAL;
+  if (!c->prepared) return fail(c, RICH_EINVAL, "call richards_prepare first");
+  vcycle64(c, 0);
+  TRY(check_launch(c));
+  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status richards_profile(richards_ctx* c, int enable) {
+  if (!c) return RICH_EINVAL;
+  if (enable) {
+    prof_flush(c);
+    c->prof_agg.clear();
+  }
+  c->prof = enable != 0;
+  return RICH_OK;
+}
+
+int richards_profile_read(richards_ctx* c, richards_kernel_stat* out, int max) {
+  if (!c || (!out && max > 0)) return -1;
+  prof_flush(c);
+  int k = 0;
+  for (const auto& kv : c->prof_agg) {
+    if (k >= max) break;
+    richards_kernel_stat& r = out[k++];
+    std::memset(&r, 0, sizeof(r));
+    std::strncpy(r.name, kv.first.first.c_str(), sizeof(r.name) - 1);
+    r.level = kv.first.second;
+    r.launches = kv.second.launches;
+    r.ms = kv.second.ms;
+    r.cells = kv.second.cells;
+  }
+  return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,474 @@
+// Device building blocks of the NGS-FAS solver: constitutive laws, the
+// conservative 7-point (2d+1) stencil, the bracketed Newton point update,
+// the nonlinear defect, and the transfer operators.  Grid kernels and the
+// single-block coarse tail both call these functions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rich {
+
+enum { HAVERKAMP = 0, GARDNER = 1, VANGENUCHTEN = 2 };
+
+// FORM_DIRECT: the unknown is psi (eq. point-update as written).
+// FORM_DELTA:  the unknown is the correction delta to a frozen psi0, and the
+//              storage/sink terms are the increments theta(psi0+delta) -
+//              theta(psi0), S(psi0+delta) - S(psi0) evaluated without
+//              cancellation (the FP32 inner problem of the mixed mode).
+enum { FORM_DIRECT = 0, FORM_DELTA = 1 };
+
+constexpr int RMAX = 6;     // max fine cells per coarse cell along one axis
+
+template <typename T>
+struct Level {
+  int dim, n0, n1, n2;
+  long long ncell;
+  T ih2[3];                      // 1/h^2 per axis (0 on unused axes)
+  T *u, *ubar, *g, *d;           // iterate, FAS restricted iterate, right side, defect
+  const T *Kc, *p1, *p2, *smax;  // lagged conductivity, soil params (nullable), sink coef (nullable)
+  const T *psi0;                 // FORM_DELTA: frozen state
+  const T *kb[6];                // boundary face conductances (per face cell)
+};
+
+template <typename T>
+struct Phys {
+  T a, xi, kappa;
+  T ts, tr;                      // theta_s, theta_r
+  T p1, p2, p3, p4;              // scalar soil parameters
+  T h1, h2, h3, h4;              // sink thresholds
+  int newton_k;                  // > 0: fixed steps; 0: to round-off
+  int sink;
+};
+
+template <typename T>
+struct Xfer {                    // fine level -> next coarser level
+  const int *pc[3];              // fine i: number of coarse contributors (1 or 2)
+  const int *pj[3];              // fine i: coarse indices [2 i + k]
+  const T *pw[3];                // fine i: weights [2 i + k]
+  const int *rc[3];              // coarse J: number of fine contributors
+  const int *ri[3];              // coarse J: fine indices [RMAX J + k]
+  const T *rw[3];                // coarse J: normalised weights
+};
+
+// ---------------------------------------------------------------------------
+// Constitutive laws (Table 1 of the paper); psi >= 0 gives theta_s, Ks and a
+// zero capacity for all three laws.
+// ---------------------------------------------------------------------------
+template <int MODEL>
+__device__ __forceinline__ void law_d(double psi, double p1, double p2, const Phys<double>& P,
+                                      double& th, double& dth) {
+  if (!(psi < 0.0)) { th = P.ts; dth = 0.0; return; }
+  const double h = -psi, ds = P.ts - P.tr;
+  if (MODEL == HAVERKAMP) {
+    // theta = theta_r + alpha ds / (alpha + h^beta)
+    const double u = exp(p2 * log(h));
+    const double den = p1 + u;
+    th = P.tr + p1 * ds / den;
+    dth = p1 * ds * p2 * (u / h) / (den * den);
+  } else if (MODEL == GARDNER) {
+    const double e = exp(p1 * psi);
+    th = P.tr + ds * e;
+    dth = p1 * ds * e;
+  } else {
+    // Se = (1 + t)^-m, t = (alpha h)^n, m = 1 - 1/n
+    const double n = p2, m = 1.0 - 1.0 / n;
+    const double t = exp(n * log(p1 * h));
+    const double Se = exp(-m * log1p(t));
+    th = P.tr + ds * Se;
+    dth = ds * m * n * (t / h) * Se / (1.0 + t);
+  }
+}
+
+template <int MODEL>
+__device__ __forceinline__ double theta_only_d(double psi, double p1, double p2, const Phys<double>& P) {
+  if (!(psi < 0.0)) return P.ts;
+  const double h = -psi, ds = P.ts - P.tr;
+  if (MODEL == HAVERKAMP) return P.tr + p1 * ds / (p1 + exp(p2 * log(h)));
+  if (MODEL == GARDNER) return P.tr + ds * exp(p1 * psi);
+  const double n = p2, m = 1.0 - 1.0 / n;
+  return P.tr + ds * exp(-m * log1p(exp(n * log(p1 * h))));
+}
+
+// Hydraulic conductivity.  For van Genuchten-Mualem, Se^{1/m} = 1/(1+t), so
+// 1 - (1 - Se^{1/m})^m = -expm1(m log(t/(1+t))), evaluated without
+// cancellation in both the wet (t < 1) and the dry (t > 1) range.
+template <int MODEL>
+__device__ __forceinline__ double cond_d(double psi, double p1, double p2, double Ks,
+                                         const Phys<double>& P) {
+  if (!(psi < 0.0)) return Ks;
+  const double h = -psi;
+  if (MODEL == HAVERKAMP) return Ks * P.p3 / (P.p3 + exp(P.p4 * log(h)));
+  if (MODEL == GARDNER) return Ks * exp(p1 * psi);
+  const double n = p2, m = 1.0 - 1.0 / n;
+  const double lt = n * log(p1 * h);
+  const double t = exp(lt);
+  const double L1 = log1p(t);
+  const double lr = t > 1.0 ? -log1p(1.0 / t) : lt - L1;     // log(t/(1+t))
+  const double inner = -expm1(m * lr);
+  return Ks * exp(-P.p3 * m * L1) * inner * inner;
+}
+
+__device__ __forceinline__ double cond_model_d(int model, double psi, double p1, double p2,
+                                               double Ks, const Phys<double>& P) {
+  if (model == HAVERKAMP) return cond_d<HAVERKAMP>(psi, p1, p2, Ks, P);
+  if (model == GARDNER) return cond_d<GARDNER>(psi, p1, p2, Ks, P);
+  return cond_d<VANGENUCHTEN>(psi, p1, p2, Ks, P);
+}
+__device__ __forceinline__ double theta_model_d(int model, double psi, double p1, double p2,
+                                                const Phys<double>& P) {
+  if (model == HAVERKAMP) return theta_only_d<HAVERKAMP>(psi, p1, p2, P);
+  if (model == GARDNER) return theta_only_d<GARDNER>(psi, p1, p2, P);
+  return theta_only_d<VANGENUCHTEN>(psi, p1, p2, P);
+}
+
+// Increment form in FP32: Dth = theta(psi0 + x) - theta(psi0) and
+// dth = theta'(psi0 + x), with the differences taken through expm1/log1p of
+// the ratio (psi0 + x)/psi0, so that Dth is accurate relative to itself.
+template <int MODEL>
+__device__ __forceinline__ void dlaw_f(float psi0, float x, float p1, float p2, const Phys<float>& P,
+                                       float& Dth, float& dth) {
+  const float ds = P.ts - P.tr;
+  const float psi1 = psi0 + x;
+  const bool wet0 = !(psi0 < 0.0f), wet1 = !(psi1 < 0.0f);
+  if (MODEL == GARDNER) {
+    const float al = p1;
+    if (!wet0) {
+      const float e0 = expf(al * psi0);
+      if (!wet1) {
+        const float em = expm1f(al * x);
+        Dth = ds * e0 * em;
+        dth = al * ds * e0 * (1.0f + em);
+      } else {
+        Dth = -ds * expm1f(al * psi0);
+        dth = 0.0f;
+      }
+    } else if (!wet1) {
+      Dth = ds * expm1f(al * psi1);
+      dth = al * ds * expf(al * psi1);
+    } else {
+      Dth = 0.0f; dth = 0.0f;
+    }
+  } else if (MODEL == HAVERKAMP) {
+    const float al = p1, be = p2;
+    if (!wet0) {
+      const float h0 = -psi0;
+      const float u0 = expf(be * logf(h0));
+      if (!wet1) {
+        const float du = u0 * expm1f(be * log1pf(x / psi0));
+        const float u1 = u0 + du, h1 = -psi1;
+        const float den1 = al + u1;
+        Dth = -al * ds * du / ((al + u0) * den1);
+        dth = al * ds * be * (u1 / h1) / (den1 * den1);
+      } else {
+        Dth = ds * u0 / (al + u0);
+        dth = 0.0f;
+      }
+    } else if (!wet1) {
+      const float h1 = -psi1;
+      const float u1 = expf(be * logf(h1));
+      const float den1 = al + u1;
+      Dth = -ds * u1 / den1;
+      dth = al * ds * be * (u1 / h1) / (den1 * den1);
+    } else {
+      Dth = 0.0f; dth = 0.0f;
+    }
+  } else {
+    const float al = p1, n = p2, m = 1.0f - 1.0f / n;
+    if (!wet0) {
+      const float h0 = -psi0;
+      const float t0 = expf(n * logf(al * h0));
+      const float L0 = log1pf(t0);
+      const float Se0 = expf(-m * L0);
+      if (!wet1) {
+        const float dt = t0 * expm1f(n * log1pf(x / psi0));      // t1 - t0
+        const float t1 = t0 + dt;
+        const float dL = log1pf(dt / (1.0f + t0));                // log(1+t1) - log(1+t0)
+        const float dSe = Se0 * expm1f(-m * dL);
+        const float Se1 = Se0 + dSe;
+        Dth = ds * dSe;
+        dth = ds * m * n * (t1 / (-psi1)) * Se1 / (1.0f + t1);
+      } else {
+        Dth = -ds * expm1f(-m * L0);
+        dth = 0.0f;
+      }
+    } else if (!wet1) {
+      const float h1 = -psi1;
+      const float t1 = expf(n * logf(al * h1));
+      const float L1 = log1pf(t1);
+      Dth = ds * expm1f(-m * L1);
+      dth = ds * m * n * (t1 / h1) * expf(-m * L1) / (1.0f + t1);
+    } else {
+      Dth = 0.0f; dth = 0.0f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sink reading: S = smax * alpha_F(psi), alpha_F piecewise linear through
+// (h4,0), (h3,1), (h2,1), (h1,0), zero outside; right derivatives at kinks.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ int feddes(T psi, const Phys<T>& P, T& a, T& da) {
+  if (psi >= P.h1) { a = T(0); da = T(0); return 0; }
+  if (psi < P.h4) { a = T(0); da = T(0); return 4; }
+  if (psi >= P.h2) { a = (P.h1 - psi) / (P.h1 - P.h2); da = T(-1) / (P.h1 - P.h2); return 1; }
+  if (psi >= P.h3) { a = T(1); da = T(0); return 2; }
+  a = (psi - P.h4) / (P.h3 - P.h4); da = T(1) / (P.h3 - P.h4); return 3;
+}
+
+template <typename T>
+__device__ __forceinline__ void sink_direct(T psi, T smax, const Phys<T>& P, T& S, T& dS) {
+  T a = T(0), da = T(0);
+  if (P.sink && smax > T(0)) feddes(psi, P, a, da);
+  S = a * smax;
+  dS = da * smax;
+}
+
+// S(psi0 + x) - S(psi0): exact slope * x on a common linear piece.
+template <typename T>
+__device__ __forceinline__ void sink_delta(T psi0, T x, T smax, const Phys<T>& P, T& DS, T& dS) {
+  if (!(P.sink && smax > T(0))) { DS = T(0); dS = T(0); return; }
+  T a0, da0, a1, da1;
+  const int k0 = feddes(psi0, P, a0, da0);
+  const int k1 = feddes(psi0 + x, P, a1, da1);
+  DS = (k0 == k1) ? smax * da1 * x : smax * (a1 - a0);
+  dS = smax * da1;
+}
+
+// ---------------------------------------------------------------------------
+// Stencil: m_ii and sum_j m_ij u_j for cell i (interior faces K_f/h^2 with
+// K_f = (Kc_i + Kc_j)/2; Dirichlet faces 2 kb/h^2 on the diagonal).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void stencil(const Level<T>& L, long long i, int i0, int i1, int i2,
+                                        const T* __restrict__ u, T& mii, T& off) {
+  const T Ki = L.Kc[i];
+  T dg = T(0), of = T(0);
+  {
+    const T s = L.ih2[0];
+    if (i0 > 0) { const T m = (Ki + L.Kc[i - 1]) * T(0.5) * s; dg += m; of += m * u[i - 1]; }
+    else dg += T(2) * L.kb[0][i1 + (long long)L.n1 * i2] * s;
+    if (i0 < L.n0 - 1) { const T m = (Ki + L.Kc[i + 1]) * T(0.5) * s; dg += m; of += m * u[i + 1]; }
+    else dg += T(2) * L.kb[1][i1 + (long long)L.n1 * i2] * s;
+  }
+  if (L.dim > 1) {
+    const T s = L.ih2[1];
+    const long long st = L.n0;
+    if (i1 > 0) { const T m = (Ki + L.Kc[i - st]) * T(0.5) * s; dg += m; of += m * u[i - st]; }
+    else dg += T(2) * L.kb[2][i0 + (long long)L.n0 * i2] * s;
+    if (i1 < L.n1 - 1) { const T m = (Ki + L.Kc[i + st]) * T(0.5) * s; dg += m; of += m * u[i + st]; }
+    else dg += T(2) * L.kb[3][i0 + (long long)L.n0 * i2] * s;
+  }
+  if (L.dim > 2) {
+    const T s = L.ih2[2];
+    const long long st = (long long)L.n0 * L.n1;
+    if (i2 > 0) { const T m = (Ki + L.Kc[i - st]) * T(0.5) * s; dg += m; of += m * u[i - st]; }
+    else dg += T(2) * L.kb[4][i0 + (long long)L.n0 * i1] * s;
+    if (i2 < L.n2 - 1) { const T m = (Ki + L.Kc[i + st]) * T(0.5) * s; dg += m; of += m * u[i + st]; }
+    else dg += T(2) * L.kb[5][i0 + (long long)L.n0 * i1] * s;
+  }
+  mii = dg;
+  off = of;
+}
+
+template <typename T>
+__device__ __forceinline__ T tol_of();
+template <>
+__device__ __forceinline__ double tol_of<double>() { return 1e-15; }
+template <>
+__device__ __forceinline__ float tol_of<float>() { return 1e-7f; }
+
+// Storage + sink part and its derivative at x for either form.
+template <typename T, int FORM, int MODEL>
+__device__ __forceinline__ void storage(T x, T psi0, T p1, T p2, T smax, const Phys<T>& P,
+                                        T& val, T& der) {
+  if constexpr (FORM == FORM_DIRECT) {
+    static_assert(sizeof(T) == 8, "direct form is FP64");
+    double th, dth, S, dS;
+    law_d<MODEL>(x, p1, p2, P, th, dth);
+    sink_direct(x, smax, P, S, dS);
+    val = P.a * th + S;
+    der = P.a * dth + dS;
+  } else {
+    static_assert(sizeof(T) == 4, "increment form is FP32");
+    float Dth, dth, DS, dS;
+    dlaw_f<MODEL>(psi0, x, p1, p2, P, Dth, dth);
+    sink_delta(psi0, x, smax, P, DS, dS);
+    val = P.a * Dth + DS;
+    der = P.a * dth + dS;
+  }
+}
+
+// Scalar solve of  storage(x) + cc x = f  (eq. point-update).  The left side
+// increases strictly (cc > 0), the root lies in [lo, hi]; Newton from x0,
+// bisection whenever a step leaves the current bracket.
+template <typename T, int FORM, int MODEL>
+__device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T smax,
+                                         const Phys<T>& P) {
+  if (!(cc > T(0))) return x0;
+  const T ds = P.ts - P.tr;
+  T lo, hi;
+  if constexpr (FORM == FORM_DIRECT) {
+    lo = (f - P.a * P.ts - smax) / cc;
+    hi = (f - P.a * P.tr) / cc;
+  } else {
+    lo = (f - P.a * ds - smax) / cc;
+    hi = (f + P.a * ds + smax) / cc;
+  }
+  T x = x0 < lo ? lo : (x0 > hi ? hi : x0);
+  const int maxit = P.newton_k > 0 ? P.newton_k : 200;
+  for (int it = 0; it < maxit; ++it) {
+    T val, der;
+    storage<T, FORM, MODEL>(x, psi0, p1, p2, smax, P, val, der);
+    const T F = val + cc * x - f;
+    const T dF = der + cc;
+    if (F == T(0)) break;
+    if (F > T(0)) hi = x; else lo = x;
+    T xn = x - F / dF;
+    // a step strictly inside the bracket, or below round-off, is kept;
+    // anything else (outside, or onto an end) is replaced by bisection
+    const T tiny = tol_of<T>() * (fabs(x) > T(1) ? fabs(x) : T(1));
+    if (!(xn > lo && xn < hi) && !(fabs(xn - x) <= tiny)) xn = T(0.5) * (lo + hi);
+    const T step = fabs(xn - x);
+    x = xn;
+    if (P.newton_k <= 0 && step <= tiny) break;
+  }
+  return x;
+}
+
+template <typename T, int FORM, int MODEL>
+__device__ __forceinline__ void point_update(const Level<T>& L, const Phys<T>& P, long long i,
+                                             int i0, int i1, int i2) {
+  T mii, off;
+  stencil(L, i, i0, i1, i2, L.u, mii, off);
+  const T ui = L.u[i];
+  const T cc = P.xi + P.kappa + mii;
+  const T f = L.g[i] + off + P.kappa * ui;
+  const T p1 = L.p1 ? L.p1[i] : P.p1;
+  const T p2 = L.p2 ? L.p2[i] : P.p2;
+  const T smax = L.smax ? L.smax[i] : T(0);
+  const T psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
+  L.u[i] = point_solve<T, FORM, MODEL>(cc, f, ui, psi0, p1, p2, smax, P);
+}
+
+// N(u)_i = storage(u_i) + xi u_i + m_ii u_i - sum_j m_ij u_j   (eq. Nh-def)
+template <typename T, int FORM, int MODEL>
+__device__ __forceinline__ T apply_N(const Level<T>& L, const Phys<T>& P, const T* __restrict__ u,
+                                     long long i, int i0, int i1, int i2) {
+  T mii, off;
+  stencil(L, i, i0, i1, i2, u, mii, off);
+  const T p1 = L.p1 ? L.p1[i] : P.p1;
+  const T p2 = L.p2 ? L.p2[i] : P.p2;
+  const T smax = L.smax ? L.smax[i] : T(0);
+  const T psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
+  T val, der;
+  storage<T, FORM, MODEL>(u[i], psi0, p1, p2, smax, P, val, der);
+  return val + P.xi * u[i] + mii * u[i] - off;
+}
+
+__device__ __forceinline__ void cell_coords(const int n0, const int n1, long long i, int& i0, int& i1,
+                                            int& i2) {
+  const long long r = i / n0;
+  i0 = (int)(i - r * n0);
+  i1 = (int)(r % n1);
+  i2 = (int)(r / n1);
+}
+
+// thread index t over one colour -> cell (x pairs, colour chosen per row)
+__device__ __forceinline__ bool color_cell(int n0, int n1, long long t, int color, int& i0, int& i1,
+                                           int& i2, long long& i) {
+  const int nh = (n0 + 1) >> 1;
+  const long long r = t / nh;
+  const int p = (int)(t - r * nh);
+  i1 = (int)(r % n1);
+  i2 = (int)(r / n1);
+  i0 = 2 * p + ((color + i1 + i2) & 1);
+  if (i0 >= n0) return false;
+  i = i0 + (long long)n0 * (i1 + (long long)n1 * i2);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Transfers (restriction: normalised full weighting; prolongation: linear).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T restrict_at(const Level<T>& F, const Xfer<T>& X, const T* __restrict__ fine,
+                                         int J0, int J1, int J2) {
+  T s = T(0);
+  const int c0 = X.rc[0][J0], c1 = X.rc[1][J1], c2 = X.rc[2][J2];
+  for (int a2 = 0; a2 < c2; ++a2) {
+    const int f2 = X.ri[2][RMAX * J2 + a2];
+    const T w2 = X.rw[2][RMAX * J2 + a2];
+    for (int a1 = 0; a1 < c1; ++a1) {
+      const int f1 = X.ri[1][RMAX * J1 + a1];
+      const T w1 = X.rw[1][RMAX * J1 + a1];
+      const long long row = (long long)F.n0 * (f1 + (long long)F.n1 * f2);
+      for (int a0 = 0; a0 < c0; ++a0) {
+        const T w0 = X.rw[0][RMAX * J0 + a0];
+        s += w0 * w1 * w2 * fine[row + X.ri[0][RMAX * J0 + a0]];
+      }
+    }
+  }
+  return s;
+}
+
+// sum_J P(i, J) (u_c - ubar_c)(J)
+template <typename T>
+__device__ __forceinline__ T prolong_at(const Level<T>& C, const Xfer<T>& X, int i0, int i1, int i2) {
+  T s = T(0);
+  const int c0 = X.pc[0][i0], c1 = X.pc[1][i1], c2 = X.pc[2][i2];
+  for (int a2 = 0; a2 < c2; ++a2) {
+    const int J2 = X.pj[2][2 * i2 + a2];
+    const T w2 = X.pw[2][2 * i2 + a2];
+    for (int a1 = 0; a1 < c1; ++a1) {
+      const int J1 = X.pj[1][2 * i1 + a1];
+      const T w1 = X.pw[1][2 * i1 + a1];
+      const long long row = (long long)C.n0 * (J1 + (long long)C.n1 * J2);
+      for (int a0 = 0; a0 < c0; ++a0) {
+        const T w0 = X.pw[0][2 * i0 + a0];
+        const long long J = row + X.pj[0][2 * i0 + a0];
+        s += w0 * w1 * w2 * (C.u[J] - C.ubar[J]);
+      }
+    }
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// max-norm reductions: |x| of finite or NaN values compares as its bit
+// pattern (NaN sorts above +inf, so a NaN anywhere survives the max).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long nbits(double x) {
+  return (unsigned long long)__double_as_longlong(fabs(x));
+}
+__device__ __forceinline__ unsigned long long nbits(float x) {
+  return (unsigned long long)__float_as_uint(fabsf(x));
+}
+
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// block-wide max of v; every thread gets the result (uses 33 words of smem)
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* sm) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    unsigned long long x = lane < nw ? sm[lane] : 0ull;
+    x = warp_max(x);
+    if (lane == 0) sm[32] = x;
+  }
+  __syncthreads();
+  return sm[32];
+}
+
+}  // namespace rich

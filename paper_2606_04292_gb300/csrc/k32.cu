@@ -1,0 +1,25 @@
+// FP32 instantiations: the inner correction problem of the mixed mode.
+#include "kernels.cuh"
+
+namespace rich {
+using D = Dispatch<float, FORM_DELTA>;
+void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, cudaStream_t s) {
+  D::sweep(L, P, model, color, s);
+}
+void residual32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,
+                cudaStream_t s) {
+  D::residual(L, P, model, norm, s);
+}
+void tau32(const Level<float>& C, const Phys<float>& P, int model, cudaStream_t s) { D::tau(C, P, model, s); }
+void restrict32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, const float* fa,
+                const float* fb, float* ca, float* cb, cudaStream_t s) {
+  D::restrict2(F, C, X, fa, fb, ca, cb, s);
+}
+void prolong32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, cudaStream_t s) {
+  D::prolong(F, C, X, s);
+}
+void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, const Phys<float>& P, int model,
+            int nu1, int nu2, int cmax, float crtol, unsigned long long* stats, cudaStream_t s) {
+  D::tail(dLs, dXs, l0, nl, P, model, nu1, nu2, cmax, crtol, stats, s);
+}
+}  // namespace rich

@@ -1,0 +1,232 @@
+// Grid kernels of one V-cycle level and the single-block coarse tail.
+// Included by the FP64 and FP32 translation units, which instantiate them.
+#pragma once
+
+#include "device.cuh"
+#include "launch.h"
+
+namespace rich {
+
+template <typename T>
+__device__ __forceinline__ T from_bits(unsigned long long b);
+template <>
+__device__ __forceinline__ double from_bits<double>(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+template <>
+__device__ __forceinline__ float from_bits<float>(unsigned long long b) {
+  return __uint_as_float((unsigned)b);
+}
+
+// ---------------------------------------------------------------------------
+// One colour of a red-black NGS sweep (eq. point-update for every cell of the
+// colour; cells of one colour do not couple, so the update is parallel).
+// ---------------------------------------------------------------------------
+template <typename T, int FORM, int MODEL>
+__global__ void __launch_bounds__(256) k_sweep(Level<T> L, Phys<T> P, int color) {
+  const long long nh = (long long)((L.n0 + 1) >> 1) * L.n1 * L.n2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nh;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i0, i1, i2;
+    long long i;
+    if (color_cell(L.n0, L.n1, t, color, i0, i1, i2, i)) point_update<T, FORM, MODEL>(L, P, i, i0, i1, i2);
+  }
+}
+
+// d = g - N(u) on a level, with ||d||_inf accumulated into *norm (bit max).
+template <typename T, int FORM, int MODEL>
+__global__ void __launch_bounds__(256) k_residual(Level<T> L, Phys<T> P, unsigned long long* norm) {
+  __shared__ unsigned long long sm[33];
+  unsigned long long mx = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.ncell;
+       i += (long long)gridDim.x * blockDim.x) {
+    int i0, i1, i2;
+    cell_coords(L.n0, L.n1, i, i0, i1, i2);
+    const T di = L.g[i] - apply_N<T, FORM, MODEL>(L, P, L.u, i, i0, i1, i2);
+    L.d[i] = di;
+    const unsigned long long b = nbits(di);
+    mx = b > mx ? b : mx;
+  }
+  mx = block_max(mx, sm);
+  if (threadIdx.x == 0 && norm) atomicMax(norm, mx);
+}
+
+// FAS step 3: psi_bar_H = R psi_h, d_H = R d_h (cb may be null).
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(Level<T> F, Level<T> C, Xfer<T> X, const T* fa, const T* fb,
+                                                  T* ca, T* cb) {
+  for (long long J = blockIdx.x * (long long)blockDim.x + threadIdx.x; J < C.ncell;
+       J += (long long)gridDim.x * blockDim.x) {
+    int J0, J1, J2;
+    cell_coords(C.n0, C.n1, J, J0, J1, J2);
+    ca[J] = restrict_at(F, X, fa, J0, J1, J2);
+    if (cb) cb[J] = restrict_at(F, X, fb, J0, J1, J2);
+  }
+}
+
+// FAS step 4 on the coarse level: g_H = N_H(psi_bar_H) + d_H, psi_H = psi_bar_H.
+template <typename T, int FORM, int MODEL>
+__global__ void __launch_bounds__(256) k_tau(Level<T> C, Phys<T> P) {
+  for (long long J = blockIdx.x * (long long)blockDim.x + threadIdx.x; J < C.ncell;
+       J += (long long)gridDim.x * blockDim.x) {
+    int J0, J1, J2;
+    cell_coords(C.n0, C.n1, J, J0, J1, J2);
+    C.g[J] = apply_N<T, FORM, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
+    C.u[J] = C.ubar[J];
+  }
+}
+
+// FAS step 6: u_h += P (u_H - psi_bar_H).
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong(Level<T> F, Level<T> C, Xfer<T> X) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < F.ncell;
+       i += (long long)gridDim.x * blockDim.x) {
+    int i0, i1, i2;
+    cell_coords(F.n0, F.n1, i, i0, i1, i2);
+    F.u[i] += prolong_at(C, X, i0, i1, i2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The coarse tail: the whole V-cycle from level l0 down to the coarsest level
+// in one thread block (levels small enough that launch latency would dominate
+// a kernel per stage).  Same arithmetic as the grid kernels, phase by phase,
+// separated by block barriers.
+// ---------------------------------------------------------------------------
+template <typename T, int FORM, int MODEL>
+__device__ __forceinline__ void block_sweep(const Level<T>& L, const Phys<T>& P) {
+  const long long nh = (long long)((L.n0 + 1) >> 1) * L.n1 * L.n2;
+  for (int color = 0; color < 2; ++color) {
+    for (long long t = threadIdx.x; t < nh; t += blockDim.x) {
+      int i0, i1, i2;
+      long long i;
+      if (color_cell(L.n0, L.n1, t, color, i0, i1, i2, i)) point_update<T, FORM, MODEL>(L, P, i, i0, i1, i2);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int FORM, int MODEL>
+__device__ __forceinline__ T block_defect_norm(const Level<T>& L, const Phys<T>& P, unsigned long long* sm) {
+  unsigned long long mx = 0;
+  for (long long i = threadIdx.x; i < L.ncell; i += blockDim.x) {
+    int i0, i1, i2;
+    cell_coords(L.n0, L.n1, i, i0, i1, i2);
+    const T di = L.g[i] - apply_N<T, FORM, MODEL>(L, P, L.u, i, i0, i1, i2);
+    const unsigned long long b = nbits(di);
+    mx = b > mx ? b : mx;
+  }
+  return from_bits<T>(block_max(mx, sm));
+}
+
+template <typename T, int FORM, int MODEL>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail(const Level<T>* __restrict__ Ls, const Xfer<T>* __restrict__ Xs,
+                                                       int l0, int nl, Phys<T> P, int nu1, int nu2, int cmax,
+                                                       T crtol, unsigned long long* stats) {
+  __shared__ unsigned long long sm[33];
+  unsigned long long updates = 0;
+  for (int l = l0; l < nl - 1; ++l) {
+    const Level<T> F = Ls[l];
+    for (int s = 0; s < nu1; ++s) block_sweep<T, FORM, MODEL>(F, P);
+    updates += (unsigned long long)nu1 * F.ncell;
+    for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
+      int i0, i1, i2;
+      cell_coords(F.n0, F.n1, i, i0, i1, i2);
+      F.d[i] = F.g[i] - apply_N<T, FORM, MODEL>(F, P, F.u, i, i0, i1, i2);
+    }
+    __syncthreads();
+    const Level<T> C = Ls[l + 1];
+    const Xfer<T> X = Xs[l];
+    for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
+      int J0, J1, J2;
+      cell_coords(C.n0, C.n1, J, J0, J1, J2);
+      C.ubar[J] = restrict_at(F, X, F.u, J0, J1, J2);
+      C.d[J] = restrict_at(F, X, F.d, J0, J1, J2);
+    }
+    __syncthreads();
+    for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
+      int J0, J1, J2;
+      cell_coords(C.n0, C.n1, J, J0, J1, J2);
+      C.g[J] = apply_N<T, FORM, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
+      C.u[J] = C.ubar[J];
+    }
+    __syncthreads();
+  }
+  {
+    const Level<T> C = Ls[nl - 1];
+    const T d0 = block_defect_norm<T, FORM, MODEL>(C, P, sm);
+    for (int s = 0; s < cmax; ++s) {
+      block_sweep<T, FORM, MODEL>(C, P);
+      updates += C.ncell;
+      const T dn = block_defect_norm<T, FORM, MODEL>(C, P, sm);
+      if (!(dn > crtol * d0)) break;
+    }
+  }
+  for (int l = nl - 2; l >= l0; --l) {
+    const Level<T> F = Ls[l];
+    const Level<T> C = Ls[l + 1];
+    const Xfer<T> X = Xs[l];
+    for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
+      int i0, i1, i2;
+      cell_coords(F.n0, F.n1, i, i0, i1, i2);
+      F.u[i] += prolong_at(C, X, i0, i1, i2);
+    }
+    __syncthreads();
+    for (int s = 0; s < nu2; ++s) block_sweep<T, FORM, MODEL>(F, P);
+    updates += (unsigned long long)nu2 * F.ncell;
+  }
+  if (threadIdx.x == 0 && stats) atomicAdd(stats, updates);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+inline int grid_for(long long n, int bs = 256) {
+  long long b = (n + bs - 1) / bs;
+  const long long cap = 152LL * 32;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename T, int FORM>
+struct Dispatch {
+  static void sweep(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
+    const long long nh = (long long)((L.n0 + 1) >> 1) * L.n1 * L.n2;
+    const int g = grid_for(nh);
+    if (model == HAVERKAMP) k_sweep<T, FORM, HAVERKAMP><<<g, 256, 0, s>>>(L, P, color);
+    else if (model == GARDNER) k_sweep<T, FORM, GARDNER><<<g, 256, 0, s>>>(L, P, color);
+    else k_sweep<T, FORM, VANGENUCHTEN><<<g, 256, 0, s>>>(L, P, color);
+  }
+  static void residual(const Level<T>& L, const Phys<T>& P, int model, unsigned long long* norm,
+                       cudaStream_t s) {
+    const int g = grid_for(L.ncell);
+    if (model == HAVERKAMP) k_residual<T, FORM, HAVERKAMP><<<g, 256, 0, s>>>(L, P, norm);
+    else if (model == GARDNER) k_residual<T, FORM, GARDNER><<<g, 256, 0, s>>>(L, P, norm);
+    else k_residual<T, FORM, VANGENUCHTEN><<<g, 256, 0, s>>>(L, P, norm);
+  }
+  static void tau(const Level<T>& C, const Phys<T>& P, int model, cudaStream_t s) {
+    const int g = grid_for(C.ncell);
+    if (model == HAVERKAMP) k_tau<T, FORM, HAVERKAMP><<<g, 256, 0, s>>>(C, P);
+    else if (model == GARDNER) k_tau<T, FORM, GARDNER><<<g, 256, 0, s>>>(C, P);
+    else k_tau<T, FORM, VANGENUCHTEN><<<g, 256, 0, s>>>(C, P);
+  }
+  static void restrict2(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, const T* fa, const T* fb,
+                        T* ca, T* cb, cudaStream_t s) {
+    k_restrict<T><<<grid_for(C.ncell), 256, 0, s>>>(F, C, X, fa, fb, ca, cb);
+  }
+  static void prolong(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, cudaStream_t s) {
+    k_prolong<T><<<grid_for(F.ncell), 256, 0, s>>>(F, C, X);
+  }
+  static void tail(const Level<T>* dLs, const Xfer<T>* dXs, int l0, int nl, const Phys<T>& P, int model,
+                   int nu1, int nu2, int cmax, T crtol, unsigned long long* stats, cudaStream_t s) {
+    if (model == HAVERKAMP)
+      k_tail<T, FORM, HAVERKAMP><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, stats);
+    else if (model == GARDNER)
+      k_tail<T, FORM, GARDNER><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, stats);
+    else
+      k_tail<T, FORM, VANGENUCHTEN><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, stats);
+  }
+};
+
+}  // namespace rich

@@ -1,0 +1,63 @@
+// Host-callable launchers of the device kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+#define TAIL_THREADS 512
+
+namespace rich {
+
+struct BcDev {
+  int kind[6];
+  double value[6];
+  const double* vfield[6];
+  const unsigned char* mask[6];
+};
+
+struct Geom {
+  int dim, n0, n1, n2;
+  double h[3];
+  double Lv;            // length of the vertical axis
+};
+
+// FP64, psi as unknown
+void sweep64(const Level<double>& L, const Phys<double>& P, int model, int color, cudaStream_t s);
+void residual64(const Level<double>& L, const Phys<double>& P, int model, unsigned long long* norm,
+                cudaStream_t s);
+void tau64(const Level<double>& C, const Phys<double>& P, int model, cudaStream_t s);
+void restrict64(const Level<double>& F, const Level<double>& C, const Xfer<double>& X, const double* fa,
+                const double* fb, double* ca, double* cb, cudaStream_t s);
+void prolong64(const Level<double>& F, const Level<double>& C, const Xfer<double>& X, cudaStream_t s);
+void tail64(const Level<double>* dLs, const Xfer<double>* dXs, int l0, int nl, const Phys<double>& P,
+            int model, int nu1, int nu2, int cmax, double crtol, unsigned long long* stats, cudaStream_t s);
+
+// FP32, correction delta as unknown
+void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, cudaStream_t s);
+void residual32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,
+                cudaStream_t s);
+void tau32(const Level<float>& C, const Phys<float>& P, int model, cudaStream_t s);
+void restrict32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, const float* fa,
+                const float* fb, float* ca, float* cb, cudaStream_t s);
+void prolong32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, cudaStream_t s);
+void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, const Phys<float>& P,
+            int model, int nu1, int nu2, int cmax, float crtol, unsigned long long* stats, cudaStream_t s);
+
+// per-step preparation (FP64)
+void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
+                 const double* p1, const double* p2, const Phys<double>& P, int model, int scheme, double dt,
+                 double* Kc, double* g, double* u, cudaStream_t s);
+void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
+              const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6], cudaStream_t s);
+void restrict_face64(const Geom& F, const Geom& C, const Xfer<double>& X, int axis, const double* fine,
+                     double* coarse, cudaStream_t s);
+void sink_coef(const Geom& G, double Tp, double depth, double decay, double* smax, cudaStream_t s);
+void to_float(const double* src, float* dst, long long n, cudaStream_t s);
+
+// mixed mode: r = g - N(u) in FP64 -> r32, psi0 = (float)u, delta = 0; ||r||_inf
+void outer_residual(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
+                    float* delta, unsigned long long* norm, cudaStream_t s);
+void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);
+
+}  // namespace rich

@@ -147,7 +147,7 @@ def gaussian_log_field(shape, corr_cells, seed):
     grids = np.meshgrid(*freqs, indexing="ij")
     k2 = sum(g * g for g in grids)
     F *= np.exp(-2.0 * (math.pi ** 2) * (s ** 2) * k2)
-    G = np.fft.irfftn(F, s=shape)
+    G = np.fft.irfftn(F, s=shape, axes=list(range(len(shape))))
     G = (G - G.mean()) / G.std()
     return G
 

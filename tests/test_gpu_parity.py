@@ -1,0 +1,299 @@
+"""CUDA path vs the CPU oracle, stage by stage and step by step (needs a GPU).
+
+Tolerances (FP64 mode): the two sides evaluate the same formulas with
+different libm routines, summation order and fused multiply-adds, so single
+stages agree to ~1e-13 relative; iterated results (V-cycles, steps) to the
+1e-10 norm-wise relative bound ||dpsi||_inf <= 1e-10 ||psi_ref||_inf.
+Mixed mode is checked against the a-posteriori bound
+||psi_mixed - psi_ref||_inf <= (||r_mixed|| + ||r_ref||) / min_i(a theta'_i + xi)
+(the diagonal-dominance argument of Lemma 3.1 applied to the whole Jacobian).
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import ORC_OK, Oracle
+from paper_2606_04292_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_04292_gb300 import richards as R  # noqa: E402
+
+STAGE_RTOL = 1e-12
+STEP_RTOL = 1e-10
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def pair(prob, **opts):
+    p = W.with_opts(prob, **opts) if opts else prob
+    return R.Solver(p), Oracle(p), p
+
+
+PROBLEMS = [
+    ("1d_haverkamp_dir", lambda: W.random_problem(1, 37, W.HAVERKAMP, 1,
+                                                   bc_kinds=[W.DIRICHLET, W.DIRICHLET], psi_range=(-1.5, -0.1))),
+    ("1d_vg_sink_flux", lambda: W.random_problem(1, 64, W.VANGENUCHTEN, 2, bc_kinds=[W.FREE_DRAINAGE, W.FLUX],
+                                                 hetero=True, sink=True)),
+    ("2d_vg_strip", lambda: W.strip_2d(n=33, dt=60.0)),
+    ("2d_gardner_mixed_bc", lambda: W.random_problem(2, (23, 18), W.GARDNER, 3,
+                                                     bc_kinds=[W.DIRICHLET, W.NOFLUX, W.FREE_DRAINAGE, W.FLUX],
+                                                     hetero=True)),
+    ("3d_vg_hetero_sink", lambda: W.random_problem(3, (17, 12, 9), W.VANGENUCHTEN, 4, hetero=True, sink=True)),
+    ("3d_haverkamp_dir", lambda: W.random_problem(3, (10, 11, 13), W.HAVERKAMP, 5,
+                                                   bc_kinds=[W.DIRICHLET] * 6)),
+    ("3d_drainage_16", lambda: W.drainage_3d(n=16, precision=0)),
+]
+IDS = [p[0] for p in PROBLEMS]
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_prepare_matches_oracle(mk, scheme):
+    prob = mk()
+    if scheme == 2:
+        rng = np.random.default_rng(9)
+        prob["psi_prev"] = prob["psi0"] + rng.uniform(-0.02, 0.02, len(prob["psi0"]))
+    gs, orc, p = pair(prob)
+    assert gs.prepare(p["dt"], scheme) == scheme
+    assert orc.prepare(p["dt"], scheme) == scheme
+    assert gs.nlevels == orc.nlevels
+    for lev in range(orc.nlevels):
+        assert gs.level_n(lev) == orc.level_n(lev)
+        assert rel(gs.get_level(lev, 2), orc.Kc(lev)) <= STAGE_RTOL, lev
+        for f in range(2 * p["dim"]):
+            kg, ko = gs.get_level(lev, 10 + f), orc.array(10 + f, lev)
+            assert np.max(np.abs(kg - ko)) <= STAGE_RTOL * max(np.max(np.abs(ko)), 1e-300), (lev, f)
+    assert rel(gs.get_level(0, 1), orc.g(0)) <= STAGE_RTOL
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
+@pytest.mark.parametrize("newton", [0, 2])
+def test_halfsweeps_match_oracle_on_every_level(mk, newton):
+    """Red then black half-sweep on every level.  With Newton run to round-off
+    the states are random; with the fixed two-step Newton of the solver they
+    are near the root, as inside a solve (far from it, two unconverged steps
+    can take different bracketing branches on a one-ulp difference)."""
+    prob = mk()
+    gs, orc, p = pair(prob, newton_iters=newton)
+    gs.prepare(p["dt"], 1)
+    orc.prepare(p["dt"], 1)
+    rng = np.random.default_rng(3)
+    for lev in range(orc.nlevels):
+        n = orc.ncell(lev)
+        if newton == 0:
+            psi = rng.uniform(-1.5, -0.05, n)
+            g = orc.apply_N(rng.uniform(-1.5, -0.05, n), lev)
+        else:
+            psi = rng.uniform(-1.5, -0.05, n)
+            g = orc.apply_N(psi + rng.uniform(-1e-3, 1e-3, n), lev)
+        gs.set_level(lev, 0, psi)
+        gs.set_level(lev, 1, g)
+        ref = psi
+        for color in (0, 1):
+            ref = orc.sweep(ref, g, lev, color)
+            gs.sweep(lev, color)
+            got = gs.get_level(lev, 0)
+            assert rel(got, ref) <= STAGE_RTOL, (lev, color, rel(got, ref))
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
+def test_residual_restrict_tau_prolong_match_oracle(mk):
+    prob = mk()
+    gs, orc, p = pair(prob)
+    gs.prepare(p["dt"], 1)
+    orc.prepare(p["dt"], 1)
+    rng = np.random.default_rng(4)
+    psi = p["psi0"] + rng.uniform(-0.05, 0.05, len(p["psi0"]))
+    gs.set_level(0, 0, psi)
+    nrm = gs.residual(0)
+    r, nrm_ref = orc.residual(psi)
+    d = gs.get_level(0, 7)
+    scale = np.max(np.abs(orc.g()))
+    assert np.max(np.abs(d - r)) <= 1e-12 * scale
+    assert abs(nrm - nrm_ref) <= 1e-12 * scale
+    if orc.nlevels < 2:
+        return
+    gs.restrict_tau(0)
+    pbar = orc.restrict(psi)
+    dH = orc.restrict(r)
+    gH = orc.apply_N(pbar, 1) + dH
+    assert rel(gs.get_level(1, 6), pbar) <= STAGE_RTOL
+    assert np.max(np.abs(gs.get_level(1, 7) - dH)) <= 1e-12 * scale
+    assert np.max(np.abs(gs.get_level(1, 1) - gH)) <= 1e-12 * np.max(np.abs(gH))
+    uH = pbar + rng.uniform(-0.01, 0.01, len(pbar))
+    gs.set_level(1, 0, uH)
+    gs.prolong(0)
+    ref = orc.prolong_add(uH - pbar, psi)
+    assert rel(gs.get_level(0, 0), ref) <= STAGE_RTOL
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
+def test_vcycle_matches_oracle(mk):
+    """Iterate-for-iterate V-cycles.  Point solves run to round-off and the
+    coarsest level does a fixed number of sweeps: with a fixed two-step Newton
+    the cycle map is discontinuous (whether a step bisects can flip on one
+    ulp; the oracle alone moves by ~1e-3 under a 1e-15 input perturbation on
+    the drainage case), and the coarse stop rule is a threshold decision."""
+    prob = mk()
+    gs, orc, p = pair(prob, coarse_rtol=0.0, coarse_max_sweeps=12, newton_iters=0)
+    gs.prepare(p["dt"], 1)
+    orc.prepare(p["dt"], 1)
+    ref = p["psi0"]
+    for _ in range(2):
+        gs.vcycle()
+        ref = orc.vcycle(ref)
+        assert rel(gs.get_level(0, 0), ref) <= STEP_RTOL
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
+def test_fp64_steps_match_oracle(mk):
+    """Whole steps, both sides cycling to a tight tolerance (1e-11) so that the
+    comparison is between two converged solutions of the same system."""
+    prob = mk()
+    gs, orc, p = pair(prob, tol=1e-11, max_cycles=200)
+    for k in range(3):
+        st, info = gs.step(p["dt"], p["scheme"], check=False)
+        sto, info_o = orc.step(p["dt"], p["scheme"])
+        assert st == sto, (k, info, info_o)
+        assert abs(info["cycles"] - info_o["cycles"]) <= 1, (k, info, info_o)
+        assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
+
+
+def test_celia_column_full_run():
+    """The paper's 1-d column (config: N=128, dt = 10 s, 36 BDF1 steps)."""
+    prob = W.celia_1d()
+    gs, orc, p = pair(prob)
+    for k in range(p["nsteps"]):
+        st, info = gs.step()
+        sto, info_o = orc.step()
+        assert st == R.RICH_OK and sto == ORC_OK
+        assert info["cycles"] == info_o["cycles"]
+    assert rel(gs.state(), orc.state()) <= STEP_RTOL
+
+
+def test_strip_2d_bdf2_steps():
+    prob = W.strip_2d(n=65, nsteps=6, tol=1e-11, max_cycles=200)
+    gs, orc, p = pair(prob)
+    for k in range(p["nsteps"]):
+        st, info = gs.step()
+        sto, info_o = orc.step()
+        assert st == sto
+        assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
+
+
+def _mixed_bound(orc, psi_m, psi_r):
+    """(||r_m|| + ||r_r||) / min_i a theta'(zeta_i), zeta_i on [psi_m, psi_r]."""
+    a = orc.a
+    xi = orc.prob["opts"]["xi"]
+    _, rm = orc.residual(psi_m)
+    _, rr = orc.residual(psi_r)
+    lo, hi = np.minimum(psi_m, psi_r), np.maximum(psi_m, psi_r)
+    dmin = np.inf
+    for i in range(len(psi_m)):
+        d = min(orc.soil(i, lo[i])[1], orc.soil(i, hi[i])[1])
+        dmin = min(dmin, a * d + xi)
+    if dmin <= 0:
+        return np.inf
+    return (rm + rr) / dmin
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS if "sink" not in p[0]],
+                         ids=[p[0] for p in PROBLEMS if "sink" not in p[0]])
+def test_mixed_precision_within_stated_bound(mk):
+    prob = mk()
+    prob = W.with_opts(prob, precision=1)
+    gs = R.Solver(prob)
+    orc = Oracle(W.with_opts(prob, tol=1e-13, newton_iters=0))
+    cur, prev = np.array(prob["psi0"], dtype=np.float64), None
+    for k in range(3):
+        st, info = gs.step(prob["dt"], prob["scheme"], check=False)
+        assert st == R.RICH_OK, info
+        assert info["resid"] <= prob["opts"]["tol"]
+        orc.set_state(cur, prev)           # same history as the GPU step
+        assert orc.step(prob["dt"], prob["scheme"])[0] == ORC_OK
+        psi_m, psi_r = gs.state(), orc.state()
+        orc.set_state(cur, prev)
+        orc.prepare(prob["dt"], info["scheme_used"])
+        _, rm = orc.residual(psi_m)        # the oracle re-derives the FP64 residual
+        assert rm / orc.a <= prob["opts"]["tol"] * (1 + 1e-6)
+        bound = _mixed_bound(orc, psi_m, psi_r)
+        err = np.max(np.abs(psi_m - psi_r))
+        assert err <= bound * (1 + 1e-6), (k, err, bound)
+        prev, cur = cur, psi_m
+
+
+def test_mixed_precision_reaches_fp64_solution_at_tight_tolerance():
+    """The FP64 outer correction is not limited by FP32: at tol 1e-13 the
+    mixed result equals the FP64 solution to 1e-9."""
+    prob = W.with_opts(W.random_problem(3, (15, 14, 13), W.VANGENUCHTEN, 6, hetero=True),
+                       precision=1, tol=1e-13, max_outer=40)
+    gs = R.Solver(prob)
+    orc = Oracle(W.with_opts(prob, tol=1e-14, newton_iters=0))
+    st, info = gs.step()
+    assert st == R.RICH_OK, info
+    assert orc.step()[0] == ORC_OK
+    assert rel(gs.state(), orc.state()) <= 1e-9
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_tiny_and_degenerate_grids(n):
+    for dim in (1, 2, 3):
+        prob = W.random_problem(dim, (n,) * dim, W.VANGENUCHTEN, 7,
+                                bc_kinds=[W.DIRICHLET] * (2 * dim), kappa=0.01)
+        gs, orc, p = pair(prob)
+        st, info = gs.step()
+        sto, _ = orc.step()
+        assert st == sto
+        assert rel(gs.state(), orc.state()) <= STEP_RTOL
+
+
+def test_hydrostatic_state_unchanged_on_gpu():
+    prob = W.random_problem(3, (9, 8, 7), W.VANGENUCHTEN, 8, hetero=True,
+                            bc_kinds=[W.NOFLUX] * 4 + [W.DIRICHLET, W.DIRICHLET])
+    H = 0.2
+    prob["bc"]["value"][4], prob["bc"]["value"][5] = H, H - 1.0
+    idx = np.arange(9 * 8 * 7)
+    z = (idx // 72 + 0.5) / 7
+    prob["psi0"] = H - z
+    gs = R.Solver(prob)
+    st, info = gs.step()
+    assert st == R.RICH_OK and info["cycles"] == 0
+    assert np.max(np.abs(gs.state() - prob["psi0"])) <= 1e-13
+
+
+def test_error_statuses():
+    prob = W.random_problem(2, (8, 8), W.VANGENUCHTEN, 9)
+    gs = R.Solver(prob)
+    bad = dict(prob["soil"], Ks=-1.0)
+    with pytest.raises(R.RichardsError) as e:
+        gs.set_soil(bad)
+    assert e.value.status == R.RICH_EINVAL
+    bad_bc = dict(prob["bc"], kind=[W.FREE_DRAINAGE] + list(prob["bc"]["kind"][1:]))
+    with pytest.raises(R.RichardsError):
+        gs.set_bc(bad_bc)
+    with pytest.raises(R.RichardsError):
+        gs.set_state(np.full(64, np.nan))
+    gs.set_state(prob["psi0"])
+    st, info = R.Solver(W.with_opts(prob, max_cycles=1, tol=1e-30)).step(check=False)
+    assert st == R.RICH_ENOCONV
+
+
+@pytest.mark.slow
+def test_full_size_drainage_step_solves_the_oracle_system():
+    """At the benchmark's size (256^3, mixed precision, BDF2 workload, first
+    step) the GPU result satisfies the oracle's own FP64 stop test."""
+    prob = W.drainage_3d(n=256)
+    gs = R.Solver(prob)
+    st, info = gs.step()
+    assert st == R.RICH_OK, info
+    psi = gs.state()
+    orc = Oracle(prob)
+    orc.prepare(prob["dt"], info["scheme_used"])
+    _, nrm = orc.residual(psi)
+    assert nrm / orc.a <= prob["opts"]["tol"] * (1 + 1e-6), (nrm / orc.a, info)
