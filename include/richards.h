@@ -250,6 +250,43 @@ richards_status richards_profile(richards_ctx *ctx, int enable);
    on error). */
 int richards_profile_read(richards_ctx *ctx, richards_kernel_stat *out, int max);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free step for small grids.  The paper has no counterpart: this
+ * is an interface for callers that may not allocate device memory while
+ * they run -- host code that executes during CUDA graph capture, programs
+ * whose memory pool already holds all of the device memory, real-time
+ * loops that forbid allocator calls, plug-ins that may only touch memory
+ * handed to them.
+ *
+ * One implicit step (same arithmetic as richards_step in FP64 mode) of a
+ * grid with at most RICHARDS_NOALLOC_MAX_CELLS cells, run in a single thread
+ * block.  psi_n, psi_prev (nullable: BDF1 is used) and psi_out are device
+ * arrays of ncell doubles; psi_out may alias psi_n.  In this call the
+ * optional soil fields (Ks_field, p1_field, p2_field) and boundary fields
+ * (value_field, mask_field) are DEVICE pointers.  Only opts->precision 0 is
+ * used (the step is FP64).  info (nullable, host) receives the statistics.
+ * stream: a cudaStream_t (NULL = default stream); the call synchronises it.
+ *
+ * Scratch: one fixed 2 MiB array in the library's device memory (every
+ * device that loads the library keeps it until the process exits); nothing
+ * is allocated.  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make the first
+ * call on a device before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (two streams, two host threads) race and
+ * must be serialised by the caller.  The array keeps the last call's
+ * contents; a call writes every value before reading it, so nothing has to
+ * start at zero.
+ *
+ * Errors: EINVAL for a grid above RICHARDS_NOALLOC_MAX_CELLS cells (its
+ * hierarchy would not fit the fixed scratch) or any invalid argument;
+ * ENOCONV / ENAN as for richards_step; ECUDA on a CUDA error. */
+#define RICHARDS_NOALLOC_MAX_CELLS 4096
+richards_status richards_step_small_noalloc(const richards_grid *grid, const richards_soil *soil,
+                                            const richards_bc *bc, const richards_sink *sink,
+                                            const richards_opts *opts, double dt, int scheme,
+                                            const double *psi_n, const double *psi_prev, double *psi_out,
+                                            richards_step_info *info, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,477 @@
+// One implicit time step of a small grid without any device allocation.
+//
+// Who needs this: code that must not call cudaMalloc in the middle of its
+// work -- a host routine that runs while a CUDA graph is being captured, an
+// application whose memory pool already owns all of the device memory, a
+// real-time loop that forbids allocator calls, or a plug-in inside another
+// GPU program that may only use memory handed to it.  Such callers pass
+// device pointers for the state in and the state out; everything else the
+// step needs (multigrid hierarchy, coefficients, transfer tables, norms)
+// lives in one fixed array in the library's own device memory.
+//
+// The whole step runs in one thread block (a variant of the coarse-tail
+// kernel that also does the per-step preparation and the stop loop), so the
+// grid is limited to RICHARDS_NOALLOC_MAX_CELLS cells.
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+#include "richards.h"
+
+namespace rich {
+namespace {
+
+constexpr int NA_MAXLEV = 14;
+constexpr long long NA_SCRATCH_DOUBLES = 262144;   // 2 MiB
+
+// The fixed scratch array.  Every device that loads the library holds it
+// until the process exits; all calls share it.
+static __device__ __align__(256) double g_noalloc_scratch[NA_SCRATCH_DOUBLES];
+
+struct NaLevel {
+  Level<double> L;
+  Xfer<double> X;          // tables to the next coarser level
+  int *pc[3], *pj[3], *rc[3], *ri[3];
+  double *pw[3], *rw[3];
+  double* Kcw;             // writable views of the coefficient arrays
+  double *p1w, *p2w, *smaxw;
+  double* kbw[6];
+};
+
+struct NaPlan {
+  int nlev, dim, model, scheme, max_cycles, nu1, nu2, cmax;
+  double crtol, tol, dt, Lv, h[3];
+  double slo[3], shi[3];           // prolongation ghost factors per axis
+  int het_p1, het_p2, het_Ks, sink;
+  double Ks, Tp, root_depth, root_decay;
+  const double *psin, *psinm1, *Ks_field, *p1_field, *p2_field;
+  double* psi_out;
+  BcDev bc;
+  Phys<double> P;
+  double* stats;                   // [cycles, resid0, resid, status, updates]
+  NaLevel lev[NA_MAXLEV];
+};
+
+// ---------------------------------------------------------------------------
+// device pieces
+// ---------------------------------------------------------------------------
+__device__ void na_interp(int nf, int nc, int i, double slo, double shi, int* idx, double* w, int& cnt) {
+  cnt = 0;
+  auto add = [&](int j, double wt) {
+    if (wt == 0.0) return;
+    for (int k = 0; k < cnt; ++k)
+      if (idx[k] == j) { w[k] += wt; return; }
+    idx[cnt] = j;
+    w[cnt] = wt;
+    ++cnt;
+  };
+  if (nf == 1) { add(0, 1.0); return; }
+  const long long num = (long long)(2 * i + 1) * nc - nf, den = 2LL * nf;
+  const long long J0 = num >= 0 ? num / den : -((-num + den - 1) / den);
+  const double wt = (double)(num - J0 * den) / (double)den;
+  const long long J1 = J0 + 1;
+  if (J0 < 0) add(0, (1.0 - wt) * slo); else add((int)J0, 1.0 - wt);
+  if (J1 >= nc) add(nc - 1, wt * shi); else add((int)J1, wt);
+}
+
+// transfer tables of every level, built by the block
+__device__ void na_tables(const NaPlan& p) {
+  for (int l = 0; l + 1 < p.nlev; ++l) {
+    const NaLevel& F = p.lev[l];
+    const NaLevel& C = p.lev[l + 1];
+    const int nfa[3] = {F.L.n0, F.L.n1, F.L.n2}, nca[3] = {C.L.n0, C.L.n1, C.L.n2};
+    for (int ax = 0; ax < 3; ++ax) {
+      const int nf = nfa[ax], nc = nca[ax];
+      for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        int idx[2];
+        double w[2];
+        int cnt;
+        na_interp(nf, nc, i, p.slo[ax], p.shi[ax], idx, w, cnt);
+        F.pc[ax][i] = cnt;
+        for (int k = 0; k < 2; ++k) {
+          F.pj[ax][2 * i + k] = k < cnt ? idx[k] : 0;
+          F.pw[ax][2 * i + k] = k < cnt ? w[k] : 0.0;
+        }
+      }
+      for (int J = threadIdx.x; J < nc; J += blockDim.x) {
+        int cnt = 0;
+        double s = 0.0;
+        const int lo = nf == 1 ? 0 : (2 * J - 4 > 0 ? 2 * J - 4 : 0);
+        const int hi = nf == 1 ? 0 : (2 * J + 4 < nf - 1 ? 2 * J + 4 : nf - 1);
+        for (int i = lo; i <= hi; ++i) {
+          int idx[2];
+          double w[2];
+          int c2;
+          na_interp(nf, nc, i, 1.0, 1.0, idx, w, c2);
+          for (int k = 0; k < c2; ++k)
+            if (idx[k] == J && cnt < RMAX) {
+              F.ri[ax][RMAX * J + cnt] = i;
+              F.rw[ax][RMAX * J + cnt] = w[k];
+              ++cnt;
+            }
+        }
+        for (int k = 0; k < cnt; ++k) s += F.rw[ax][RMAX * J + k];
+        for (int k = 0; k < cnt; ++k) F.rw[ax][RMAX * J + k] /= s;
+        F.rc[ax][J] = cnt;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// lagged state, Kc, history and the right side of the finest level
+template <int MODEL>
+__device__ void na_prepare(const NaPlan& p) {
+  const NaLevel& F = p.lev[0];
+  const Level<double>& L = F.L;
+  const Phys<double>& P = p.P;
+  for (long long i = threadIdx.x; i < L.ncell; i += blockDim.x) {
+    const double p1 = p.p1_field ? p.p1_field[i] : P.p1, p2 = p.p2_field ? p.p2_field[i] : P.p2;
+    if (F.p1w) F.p1w[i] = p1;
+    if (F.p2w) F.p2w[i] = p2;
+    const double pn = p.psin[i];
+    const double thn = theta_only_d<MODEL>(pn, p1, p2, P);
+    double ps, hist;
+    if (p.scheme == 1) {
+      ps = pn;
+      hist = thn / p.dt;
+    } else {
+      const double pm = p.psinm1[i];
+      ps = 2.0 * pn - pm;
+      hist = (4.0 * thn - theta_only_d<MODEL>(pm, p1, p2, P)) / (2.0 * p.dt);
+    }
+    F.Kcw[i] = cond_d<MODEL>(ps, p1, p2, p.Ks_field ? p.Ks_field[i] : p.Ks, P);
+    L.g[i] = hist + P.xi * ps;
+    L.u[i] = pn;
+    if (F.smaxw) {
+      int ii[3];
+      cell_coords(L.n0, L.n1, i, ii[0], ii[1], ii[2]);
+      const int v = p.dim - 1;
+      const double lam = p.root_decay, D = p.root_depth;
+      const double Z = lam * (1.0 - exp(-D / lam));
+      const double depth = p.Lv - (ii[v] + 0.5) * p.h[v];
+      F.smaxw[i] = depth <= D ? p.Tp * exp(-depth / lam) / Z : 0.0;
+    }
+  }
+  __syncthreads();
+  const int v = p.dim - 1;
+  const int nn[3] = {L.n0, L.n1, L.n2};
+  const long long stride[3] = {1, L.n0, (long long)L.n0 * L.n1};
+  for (long long i = threadIdx.x; i < L.ncell; i += blockDim.x) {
+    int ii[3];
+    cell_coords(L.n0, L.n1, i, ii[0], ii[1], ii[2]);
+    double gi = L.g[i];
+    const double Ki = L.Kc[i];
+    if (ii[v] + 1 < nn[v]) gi += 0.5 * (Ki + L.Kc[i + stride[v]]) / p.h[v];
+    if (ii[v] > 0) gi -= 0.5 * (Ki + L.Kc[i - stride[v]]) / p.h[v];
+    for (int ax = 0; ax < p.dim; ++ax)
+      for (int side = 0; side < 2; ++side) {
+        if (ii[ax] != (side ? nn[ax] - 1 : 0)) continue;
+        const int f = 2 * ax + side;
+        long long fc;
+        if (ax == 0) fc = ii[1] + (long long)L.n1 * ii[2];
+        else if (ax == 1) fc = ii[0] + (long long)L.n0 * ii[2];
+        else fc = ii[0] + (long long)L.n0 * ii[1];
+        const double h = p.h[ax];
+        const int kind = p.bc.kind[f];
+        const bool dir = kind == 0 && (!p.bc.mask[f] || p.bc.mask[f][fc]);
+        const double val = p.bc.vfield[f] ? p.bc.vfield[f][fc] : p.bc.value[f];
+        if (dir) {
+          const double p1 = p.p1_field ? p.p1_field[i] : P.p1, p2 = p.p2_field ? p.p2_field[i] : P.p2;
+          const double k = 0.5 * (Ki + cond_d<MODEL>(val, p1, p2, p.Ks_field ? p.Ks_field[i] : p.Ks, P));
+          F.kbw[f][fc] = k;
+          const double dz = (ax == v) ? (side ? 0.5 * h : -0.5 * h) : 0.0;
+          gi += 2.0 * k / (h * h) * (val + dz);
+        } else {
+          F.kbw[f][fc] = 0.0;
+          if (kind == 2) gi += val / h;
+          else if (kind == 3) gi -= Ki / h;
+        }
+      }
+    L.g[i] = gi;
+  }
+  __syncthreads();
+  // coarse coefficients: restricted Kc, soil parameters, sink, face conductances
+  for (int l = 0; l + 1 < p.nlev; ++l) {
+    const NaLevel& Fl = p.lev[l];
+    const NaLevel& Cl = p.lev[l + 1];
+    for (long long J = threadIdx.x; J < Cl.L.ncell; J += blockDim.x) {
+      int J0, J1, J2;
+      cell_coords(Cl.L.n0, Cl.L.n1, J, J0, J1, J2);
+      Cl.Kcw[J] = restrict_at(Fl.L, Fl.X, Fl.L.Kc, J0, J1, J2);
+      if (Cl.p1w) Cl.p1w[J] = restrict_at(Fl.L, Fl.X, Fl.L.p1, J0, J1, J2);
+      if (Cl.p2w) Cl.p2w[J] = restrict_at(Fl.L, Fl.X, Fl.L.p2, J0, J1, J2);
+      if (Cl.smaxw) Cl.smaxw[J] = restrict_at(Fl.L, Fl.X, Fl.L.smax, J0, J1, J2);
+    }
+    const int nF[3] = {Fl.L.n0, Fl.L.n1, Fl.L.n2}, nC[3] = {Cl.L.n0, Cl.L.n1, Cl.L.n2};
+    for (int f = 0; f < 2 * p.dim; ++f) {
+      const int ax = f / 2;
+      int oa[2], k = 0;
+      for (int a = 0; a < 3; ++a)
+        if (a != ax) oa[k++] = a;
+      const long long nc = (long long)nC[oa[0]] * nC[oa[1]];
+      for (long long J = threadIdx.x; J < nc; J += blockDim.x) {
+        const int J0 = (int)(J % nC[oa[0]]), J1 = (int)(J / nC[oa[0]]);
+        double s = 0.0;
+        for (int a1 = 0; a1 < Fl.X.rc[oa[1]][J1]; ++a1)
+          for (int a0 = 0; a0 < Fl.X.rc[oa[0]][J0]; ++a0)
+            s += Fl.X.rw[oa[0]][RMAX * J0 + a0] * Fl.X.rw[oa[1]][RMAX * J1 + a1] *
+                 Fl.L.kb[f][Fl.X.ri[oa[0]][RMAX * J0 + a0] + (long long)nF[oa[0]] * Fl.X.ri[oa[1]][RMAX * J1 + a1]];
+        Cl.kbw[f][J] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int MODEL>
+__global__ void __launch_bounds__(TAIL_THREADS) k_small_step(NaPlan p) {
+  __shared__ unsigned long long sm[33];
+  na_tables(p);
+  na_prepare<MODEL>(p);
+  const Phys<double>& P = p.P;
+  const double teff = 1.0 / P.a;
+  double r = teff * block_defect_norm<double, FORM_DIRECT, MODEL>(p.lev[0].L, P, sm);
+  const double r0 = r;
+  int cycles = 0;
+  unsigned long long updates = 0;
+  while (!(r <= p.tol) && cycles < p.max_cycles && !isnan(r)) {
+    // one V-cycle (Section 3.2, steps 1-7, recursion unrolled)
+    for (int l = 0; l < p.nlev - 1; ++l) {
+      const Level<double>& F = p.lev[l].L;
+      for (int s = 0; s < p.nu1; ++s) block_sweep<double, FORM_DIRECT, MODEL>(F, P);
+      updates += (unsigned long long)p.nu1 * F.ncell;
+      for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
+        int i0, i1, i2;
+        cell_coords(F.n0, F.n1, i, i0, i1, i2);
+        F.d[i] = F.g[i] - apply_N<double, FORM_DIRECT, MODEL>(F, P, F.u, i, i0, i1, i2);
+      }
+      __syncthreads();
+      const Level<double>& C = p.lev[l + 1].L;
+      const Xfer<double>& X = p.lev[l].X;
+      for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
+        int J0, J1, J2;
+        cell_coords(C.n0, C.n1, J, J0, J1, J2);
+        C.ubar[J] = restrict_at(F, X, F.u, J0, J1, J2);
+        C.d[J] = restrict_at(F, X, F.d, J0, J1, J2);
+      }
+      __syncthreads();
+      for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
+        int J0, J1, J2;
+        cell_coords(C.n0, C.n1, J, J0, J1, J2);
+        C.g[J] = apply_N<double, FORM_DIRECT, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
+        C.u[J] = C.ubar[J];
+      }
+      __syncthreads();
+    }
+    {
+      const Level<double>& C = p.lev[p.nlev - 1].L;
+      const double d0 = block_defect_norm<double, FORM_DIRECT, MODEL>(C, P, sm);
+      for (int s = 0; s < p.cmax; ++s) {
+        block_sweep<double, FORM_DIRECT, MODEL>(C, P);
+        updates += C.ncell;
+        const double dn = block_defect_norm<double, FORM_DIRECT, MODEL>(C, P, sm);
+        if (!(dn > p.crtol * d0)) break;
+      }
+    }
+    for (int l = p.nlev - 2; l >= 0; --l) {
+      const Level<double>& F = p.lev[l].L;
+      const Level<double>& C = p.lev[l + 1].L;
+      const Xfer<double>& X = p.lev[l].X;
+      for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
+        int i0, i1, i2;
+        cell_coords(F.n0, F.n1, i, i0, i1, i2);
+        F.u[i] += prolong_at(C, X, i0, i1, i2);
+      }
+      __syncthreads();
+      for (int s = 0; s < p.nu2; ++s) block_sweep<double, FORM_DIRECT, MODEL>(F, P);
+      updates += (unsigned long long)p.nu2 * F.ncell;
+    }
+    ++cycles;
+    r = teff * block_defect_norm<double, FORM_DIRECT, MODEL>(p.lev[0].L, P, sm);
+  }
+  const Level<double>& F = p.lev[0].L;
+  for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) p.psi_out[i] = F.u[i];
+  if (threadIdx.x == 0) {
+    p.stats[0] = cycles;
+    p.stats[1] = r0;
+    p.stats[2] = r;
+    p.stats[3] = isnan(r) ? (double)RICH_ENAN : (r <= p.tol ? (double)RICH_OK : (double)RICH_ENOCONV);
+    p.stats[4] = (double)updates;
+  }
+}
+
+// device address of the scratch array, looked up once per device
+constexpr int NA_MAXDEV = 64;
+double* g_scratch_addr[NA_MAXDEV] = {nullptr};
+
+}  // namespace
+}  // namespace rich
+
+extern "C" richards_status richards_step_small_noalloc(const richards_grid* grid, const richards_soil* soil,
+                                                       const richards_bc* bc, const richards_sink* sink,
+                                                       const richards_opts* opts, double dt, int scheme,
+                                                       const double* psi_n, const double* psi_prev, double* psi_out,
+                                                       richards_step_info* info, void* stream) {
+  using namespace rich;
+  if (!grid || !soil || !bc || !sink || !opts || !psi_n || !psi_out) return RICH_EINVAL;
+  if (grid->dim < 1 || grid->dim > 3) return RICH_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    if (grid->n[a] < 1 || (a >= grid->dim && grid->n[a] != 1)) return RICH_EINVAL;
+    if (a < grid->dim && !(grid->L[a] > 0.0 && std::isfinite(grid->L[a]))) return RICH_EINVAL;
+  }
+  const long long N = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+  if (N > RICHARDS_NOALLOC_MAX_CELLS) return RICH_EINVAL;          // grid larger than the fixed scratch
+  const richards_opts& o = *opts;
+  if (!(dt > 0.0) || !std::isfinite(dt) || (scheme != 1 && scheme != 2) || o.nu1 < 0 || o.nu2 < 0 ||
+      o.coarse_max_sweeps < 1 || o.max_cycles < 0 || o.coarsest_max_n < 1 || !(o.tol > 0.0) ||
+      o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
+      !(o.xi >= 0.0) || !(o.kappa >= 0.0))
+    return RICH_EINVAL;
+  if (soil->model < 0 || soil->model > 2 || !(soil->Ks > 0.0) || !(soil->theta_s > soil->theta_r) ||
+      !(soil->theta_r >= 0.0))
+    return RICH_EINVAL;
+  for (int f = 0; f < 2 * grid->dim; ++f) {
+    if (bc->kind[f] < 0 || bc->kind[f] > 3) return RICH_EINVAL;
+    if (bc->kind[f] == RICH_BC_FREE_DRAINAGE && f != 2 * (grid->dim - 1)) return RICH_EINVAL;
+  }
+  if (sink->enabled && !(sink->h4 < sink->h3 && sink->h3 <= sink->h2 && sink->h2 < sink->h1 &&
+                         sink->root_decay > 0.0 && sink->root_depth > 0.0))
+    return RICH_EINVAL;
+
+  // set-up, once per device: the device address of the scratch array
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAXDEV) return RICH_ECUDA;
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return RICH_ECUDA;
+    g_scratch_addr[dev] = (double*)ptr;
+  }
+  double* base = g_scratch_addr[dev];
+
+  // carve the hierarchy out of the scratch array
+  NaPlan p;
+  std::memset(&p, 0, sizeof(p));
+  long long used = 0;
+  bool overflow = false;
+  auto take = [&](long long ndoubles) -> double* {
+    const long long n = (ndoubles + 31) / 32 * 32;   // keep 256-byte alignment
+    if (used + n > NA_SCRATCH_DOUBLES) { overflow = true; return base; }
+    double* q = base + used;
+    used += n;
+    return q;
+  };
+  p.stats = take(8);
+  int n[NA_MAXLEV][3];
+  for (int a = 0; a < 3; ++a) n[0][a] = grid->n[a];
+  int nlev = 1;
+  for (;;) {
+    const int mx = n[nlev - 1][0] > n[nlev - 1][1] ? (n[nlev - 1][0] > n[nlev - 1][2] ? n[nlev - 1][0] : n[nlev - 1][2])
+                                                   : (n[nlev - 1][1] > n[nlev - 1][2] ? n[nlev - 1][1] : n[nlev - 1][2]);
+    if (mx <= o.coarsest_max_n || (o.max_levels > 0 && nlev >= o.max_levels) || nlev >= NA_MAXLEV) break;
+    for (int a = 0; a < 3; ++a) n[nlev][a] = n[nlev - 1][a] > 1 ? (n[nlev - 1][a] + 1) / 2 : 1;
+    ++nlev;
+  }
+  p.nlev = nlev;
+  p.dim = grid->dim;
+  const bool het_p1 = soil->p1_field != nullptr, het_p2 = soil->p2_field != nullptr;
+  for (int l = 0; l < nlev; ++l) {
+    NaLevel& H = p.lev[l];
+    Level<double>& L = H.L;
+    L.dim = grid->dim;
+    L.n0 = n[l][0]; L.n1 = n[l][1]; L.n2 = n[l][2];
+    L.ncell = (long long)L.n0 * L.n1 * L.n2;
+    for (int a = 0; a < 3; ++a) {
+      const double h = a < grid->dim ? grid->L[a] / n[l][a] : 1.0;
+      L.ih2[a] = a < grid->dim ? 1.0 / (h * h) : 0.0;
+    }
+    L.u = take(L.ncell); L.ubar = take(L.ncell); L.g = take(L.ncell); L.d = take(L.ncell);
+    H.Kcw = take(L.ncell);
+    L.Kc = H.Kcw;
+    H.p1w = het_p1 ? take(L.ncell) : nullptr;
+    H.p2w = het_p2 ? take(L.ncell) : nullptr;
+    H.smaxw = sink->enabled ? take(L.ncell) : nullptr;
+    L.p1 = H.p1w; L.p2 = H.p2w; L.smax = H.smaxw;
+    L.psi0 = nullptr;
+    for (int f = 0; f < 6; ++f) {
+      H.kbw[f] = f < 2 * grid->dim ? take(L.ncell / n[l][f / 2]) : nullptr;
+      L.kb[f] = H.kbw[f];
+    }
+    if (l + 1 < nlev)
+      for (int a = 0; a < 3; ++a) {
+        const int nf = n[l][a], nc = n[l + 1][a];
+        H.pc[a] = (int*)take((nf + 1) / 2);
+        H.pj[a] = (int*)take(nf);
+        H.pw[a] = take(2LL * nf);
+        H.rc[a] = (int*)take((nc + 1) / 2);
+        H.ri[a] = (int*)take((RMAX * (long long)nc + 1) / 2);
+        H.rw[a] = take(RMAX * (long long)nc);
+        H.X.pc[a] = H.pc[a]; H.X.pj[a] = H.pj[a]; H.X.pw[a] = H.pw[a];
+        H.X.rc[a] = H.rc[a]; H.X.ri[a] = H.ri[a]; H.X.rw[a] = H.rw[a];
+      }
+  }
+  if (overflow) return RICH_EINVAL;   // hierarchy larger than the fixed scratch
+
+  p.model = soil->model;
+  p.scheme = (scheme == 2 && psi_prev) ? 2 : 1;
+  p.max_cycles = o.max_cycles;
+  p.nu1 = o.nu1;
+  p.nu2 = o.nu2;
+  p.cmax = o.coarse_max_sweeps;
+  p.crtol = o.coarse_rtol;
+  p.tol = o.tol;
+  p.dt = dt;
+  for (int a = 0; a < 3; ++a) {
+    p.h[a] = a < grid->dim ? grid->L[a] / grid->n[a] : 1.0;
+    p.slo[a] = p.shi[a] = 1.0;
+    if (a < grid->dim) {
+      if (bc->kind[2 * a] == RICH_BC_DIRICHLET && !bc->mask_field[2 * a]) p.slo[a] = -1.0;
+      if (bc->kind[2 * a + 1] == RICH_BC_DIRICHLET && !bc->mask_field[2 * a + 1]) p.shi[a] = -1.0;
+    }
+  }
+  p.Lv = grid->L[grid->dim - 1];
+  p.Ks = soil->Ks;
+  p.Tp = sink->Tp;
+  p.root_depth = sink->root_depth;
+  p.root_decay = sink->root_decay;
+  p.psin = psi_n;
+  p.psinm1 = psi_prev;
+  p.Ks_field = soil->Ks_field;
+  p.p1_field = soil->p1_field;
+  p.p2_field = soil->p2_field;
+  p.psi_out = psi_out;
+  for (int f = 0; f < 6; ++f) {
+    p.bc.kind[f] = f < 2 * grid->dim ? bc->kind[f] : RICH_BC_NOFLUX;
+    p.bc.value[f] = f < 2 * grid->dim ? bc->value[f] : 0.0;
+    p.bc.vfield[f] = f < 2 * grid->dim ? bc->value_field[f] : nullptr;
+    p.bc.mask[f] = f < 2 * grid->dim ? bc->mask_field[f] : nullptr;
+  }
+  Phys<double>& P = p.P;
+  P.a = p.scheme == 1 ? 1.0 / dt : 1.5 / dt;
+  P.xi = o.xi;
+  P.kappa = o.kappa_mode == 0 ? o.kappa : 0.0;
+  P.ts = soil->theta_s;
+  P.tr = soil->theta_r;
+  P.p1 = soil->p1; P.p2 = soil->p2; P.p3 = soil->p3; P.p4 = soil->p4;
+  P.h1 = sink->h1; P.h2 = sink->h2; P.h3 = sink->h3; P.h4 = sink->h4;
+  P.newton_k = o.newton_iters;
+  P.sink = sink->enabled;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  if (soil->model == RICH_HAVERKAMP) k_small_step<HAVERKAMP><<<1, TAIL_THREADS, 0, s>>>(p);
+  else if (soil->model == RICH_GARDNER) k_small_step<GARDNER><<<1, TAIL_THREADS, 0, s>>>(p);
+  else k_small_step<VANGENUCHTEN><<<1, TAIL_THREADS, 0, s>>>(p);
+  if (cudaGetLastError() != cudaSuccess) return RICH_ECUDA;
+  double stats[5];
+  if (cudaMemcpyAsync(stats, p.stats, sizeof(stats), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RICH_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RICH_ECUDA;
+  if (info) {
+    info->cycles = (int)stats[0];
+    info->outer_iters = 0;
+    info->scheme_used = p.scheme;
+    info->resid0 = stats[1];
+    info->resid = stats[2];
+    info->cell_updates = (long long)stats[4];
+  }
+  return (richards_status)(int)stats[3];
+}

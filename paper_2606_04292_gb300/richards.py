@@ -99,6 +99,10 @@ _SIGS = {
     "richards_vcycle": (C.c_int, [_VP]),
     "richards_profile": (C.c_int, [_VP, C.c_int]),
     "richards_profile_read": (C.c_int, [_VP, C.POINTER(richards_kernel_stat), C.c_int]),
+    "richards_step_small_noalloc": (C.c_int, [C.POINTER(richards_grid), C.POINTER(richards_soil),
+                                              C.POINTER(richards_bc), C.POINTER(richards_sink),
+                                              C.POINTER(richards_opts), C.c_double, C.c_int, _DP, _DP, _DP,
+                                              C.POINTER(richards_step_info), _VP]),
 }
 
 

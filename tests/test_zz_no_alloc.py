@@ -1,0 +1,105 @@
+"""The allocation-free small-grid step against the regular step (needs a GPU).
+
+richards_step_small_noalloc serves callers that may not allocate device
+memory while they run (graph capture, a memory pool that owns the device, a
+real-time loop, a plug-in limited to the memory handed to it).  It must give
+the same state as richards_step on a context, call after call, within the
+step tolerance of the other GPU tests.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2606_04292_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_04292_gb300 import richards as R  # noqa: E402
+
+STEP_RTOL = 1e-10
+
+
+def _dptr(t):
+    return C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_double)) if t is not None else None
+
+
+def _structs(prob, keep):
+    """C structs for the call; per-cell and per-face fields as device arrays."""
+    grid = R.richards_grid(prob["dim"], (C.c_int * 3)(*prob["n"]), (C.c_double * 3)(*prob["L"]))
+    s = prob["soil"]
+    soil = R.richards_soil(s["model"], s["Ks"], s["theta_s"], s["theta_r"], s["p1"], s["p2"], s["p3"], s["p4"])
+    for key in ("Ks_field", "p1_field", "p2_field"):
+        if s.get(key) is not None:
+            t = torch.tensor(np.asarray(s[key], dtype=np.float64), device="cuda")
+            keep.append(t)
+            setattr(soil, key, _dptr(t))
+    b = prob["bc"]
+    bc = R.richards_bc()
+    for f in range(6):
+        bc.kind[f] = int(b["kind"][f])
+        bc.value[f] = float(b["value"][f])
+        if b["value_field"][f] is not None:
+            t = torch.tensor(np.asarray(b["value_field"][f], dtype=np.float64), device="cuda")
+            keep.append(t)
+            bc.value_field[f] = _dptr(t)
+        if b["mask_field"][f] is not None:
+            t = torch.tensor(np.asarray(b["mask_field"][f], dtype=np.uint8), device="cuda")
+            keep.append(t)
+            bc.mask_field[f] = C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_ubyte))
+    k = prob["sink"]
+    sink = R.richards_sink(int(k["enabled"]), k["Tp"], k["root_depth"], k["root_decay"], k["h1"], k["h2"], k["h3"],
+                           k["h4"])
+    opts = R.make_opts(prob["opts"])
+    return grid, soil, bc, sink, opts
+
+
+def _noalloc_step(prob, psi_n, psi_prev, keep):
+    L = R.lib()
+    grid, soil, bc, sink, opts = _structs(prob, keep)
+    out = torch.empty_like(psi_n)
+    info = R.richards_step_info()
+    st = L.richards_step_small_noalloc(C.byref(grid), C.byref(soil), C.byref(bc), C.byref(sink), C.byref(opts),
+                                       float(prob["dt"]), int(prob["scheme"]), _dptr(psi_n), _dptr(psi_prev),
+                                       _dptr(out), C.byref(info),
+                                       C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st, info.as_dict(), out
+
+
+CASES = [
+    ("3d_vg_fields_sink_bdf2", lambda: W.random_problem(3, (16, 16, 16), W.VANGENUCHTEN, 31, hetero=True, sink=True,
+                                                        scheme=2)),
+    ("2d_strip_mask_bdf2", lambda: W.strip_2d(n=63)),
+    ("1d_celia_bdf1", lambda: W.celia_1d(n=128)),
+]
+
+
+@pytest.mark.parametrize("mk", [c[1] for c in CASES], ids=[c[0] for c in CASES])
+def test_noalloc_step_matches_regular_step_twice(mk):
+    prob = W.with_opts(mk(), precision=0)
+    ref = R.Solver(prob)
+    keep = []
+    psi = torch.tensor(np.asarray(prob["psi0"], dtype=np.float64), device="cuda")
+    prev = None
+    for call in range(2):
+        st_ref, info_ref = ref.step(check=False)
+        st, info, out = _noalloc_step(prob, psi, prev, keep)
+        assert st == st_ref == R.RICH_OK, (call, st, st_ref)
+        assert info["cycles"] == info_ref["cycles"], (call, info, info_ref)
+        got, want = out.cpu().numpy(), ref.state()
+        err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+        assert err <= STEP_RTOL, (call, err)
+        prev, psi = psi, out
+
+
+def test_noalloc_rejects_grid_above_maximum():
+    prob = W.random_problem(3, (17, 16, 16), W.VANGENUCHTEN, 32)
+    assert 17 * 16 * 16 > 4096
+    keep = []
+    psi = torch.zeros(17 * 16 * 16, dtype=torch.float64, device="cuda")
+    st, _, _ = _noalloc_step(prob, psi, None, keep)
+    assert st == R.RICH_EINVAL
