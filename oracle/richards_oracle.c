@@ -680,7 +680,11 @@ void orc_vcycle(orc_ctx *c, int lev, double *psi, const double *g) {
   orc_restrict(c, lev, F->d, C->d);
   orc_apply_N(c, lev + 1, C->psibar, C->g);                                 /* 4 */
   for (long I = 0; I < C->ncell; ++I) { C->g[I] += C->d[I]; C->psi[I] = C->psibar[I]; }
-  orc_vcycle(c, lev + 1, C->psi, C->g);                                     /* 5 */
+  /* 5: the coarse solve is the recursion itself, done cycle_gamma times
+     (1: V-cycle, Section 3.2; 2: W-cycle) */
+  int gam = c->opts.cycle_gamma > 1 ? c->opts.cycle_gamma : 1;
+  if (c->opts.gamma_levels > 0 && lev >= c->opts.gamma_levels) gam = 1;
+  for (int q = 0; q < gam; ++q) orc_vcycle(c, lev + 1, C->psi, C->g);
   for (long I = 0; I < C->ncell; ++I) C->tmp[I] = C->psi[I] - C->psibar[I]; /* 6 */
   orc_prolong_add(c, lev, C->tmp, psi);
   for (int s = 0; s < c->opts.nu2; ++s) orc_sweep(c, lev, psi, g, -1);      /* 7 */

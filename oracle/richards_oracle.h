@@ -70,6 +70,8 @@ typedef struct {
   int max_cycles;
   int ordering;        /* 0 lexicographic, 1 red-black */
   int newton_iters;    /* 0: to tolerance; k > 0: exactly k safeguarded steps */
+  int cycle_gamma;     /* coarse-grid visits per level: 1 V-cycle, 2 W-cycle */
+  int gamma_levels;    /* cycle_gamma applies on levels < gamma_levels (0: all) */
 } orc_opts;
 
 typedef struct {
