@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=None,
                     help="steps with kernel timing (default: all timed steps)")
+    ap.add_argument("--gamma", type=int, default=2, help="1 = V-cycles, 2 = W-cycles")
+    ap.add_argument("--profile-json", default=None, help="write the per-kernel timing records here")
     return ap.parse_args()
 
 
@@ -234,7 +236,7 @@ def main():
     from paper_2606_04292_gb300 import richards as R
     from paper_2606_04292_gb300 import workloads as W
 
-    prob = W.drainage_3d(n=args.n)
+    prob = W.drainage_3d(n=args.n, cycle_gamma=args.gamma)
     N = W.ncells(prob)
     stream = torch.cuda.current_stream()
     gs = R.Solver(prob, stream=stream.cuda_stream)
@@ -268,6 +270,9 @@ def main():
     gs.profile(False)
     ms = e0.elapsed_time(e1)
     prof = gs.profile_read()
+    if args.profile_json and rank == 0:
+        with open(args.profile_json, "w") as f:
+            json.dump({"steps": prof_steps, "records": prof}, f, indent=1)
     updates = sum(i["cell_updates"] for i in infos)
     ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     up_t = torch.tensor([float(updates)], dtype=torch.float64, device="cuda")
@@ -349,6 +354,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": N, "levels": gs.nlevels, "l2": "inputs larger than L2",
+                       "cycle": "W(2,2)" if args.gamma == 2 else "V(2,2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "time_steps_per_s": steps_per_s,
             "v_cycles_per_step": statistics.mean(i["cycles"] for i in infos),

@@ -44,7 +44,8 @@ typedef enum {
 } richards_status;
 
 /* Grid (Section 2, reading: cell-centred, h = L/n per axis).  dim in 1..3;
-   n[a] >= 1 cells on axis a; axes a >= dim must have n[a] = 1. */
+   n[a] >= 1 cells on axis a; axes a >= dim must have n[a] = 1; n[1] and
+   n[2] at most 65535 and fewer than 2^31 cells in all. */
 typedef struct {
   int dim;
   int n[3];
@@ -112,7 +113,11 @@ typedef struct {
      inner_cycles,        mixed mode: FP32 V-cycles per outer iteration, stop
      inner_rtol, max_outer  early below inner_rtol x initial inner defect
      tail_cells           levels with at most this many cells run in one
-                          thread block (the coarse tail of the V-cycle) */
+                          thread block (the coarse tail of the V-cycle)
+     cycle_gamma          coarse-grid visits per level: 1 = V-cycle (the
+                          paper's), 2 = W-cycle
+     gamma_levels         cycle_gamma applies on the levels above this one
+                          (0: on every level); coarser levels use V-cycles */
 typedef struct {
   int nu1, nu2, coarse_max_sweeps;
   double coarse_rtol;
@@ -122,7 +127,7 @@ typedef struct {
   int max_cycles, ordering, newton_iters, precision;
   int inner_cycles;
   double inner_rtol;
-  int max_outer, tail_cells;
+  int max_outer, tail_cells, cycle_gamma, gamma_levels;
 } richards_opts;
 
 typedef struct {

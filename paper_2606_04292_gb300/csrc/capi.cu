@@ -11,6 +11,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.h"
 #include "richards.h"
 
@@ -56,6 +58,10 @@ struct richards_ctx {
   richards_sink sink{};
   double *psi_n = nullptr, *psi_nm1 = nullptr, *Ks = nullptr;
   bool have_state = false, have_prev = false;
+  // mixed mode: FP64 theta of psi^n, psi^{n-1} and of the latest iterate,
+  // kept so that no step evaluates theta twice at the same state
+  double *th_n = nullptr, *th_nm1 = nullptr, *th_cur = nullptr;
+  bool th_n_valid = false, th_nm1_valid = false;
   double t = 0.0, a = 0.0, dt = 0.0;
   int scheme_used = 1;
   bool prepared = false;
@@ -380,6 +386,19 @@ richards_status norm64(richards_ctx* c, int l, double* out) {
   return read_norm(c, 0, out, false);
 }
 
+// NVTX range per level around that level's own launches (a profiler can then
+// select the kernels of one level)
+const char* level_range(int l) {
+  static const char* names[] = {"L0", "L1", "L2", "L3", "L4", "L5", "L6", "L7", "L8", "L9", "L10", "L11",
+                                "L12", "L13", "L14", "L15", "L16", "L17", "L18", "L19", "L20", "L21", "L22", "L23"};
+  return names[l < 24 ? l : 23];
+}
+
+// coarse-grid visits from level l (cycle_gamma above gamma_levels, else 1)
+int gamma_at(const richards_ctx* c, int l) {
+  return (c->opts.gamma_levels <= 0 || l < c->opts.gamma_levels) ? c->opts.cycle_gamma : 1;
+}
+
 // ------------------------------------------------------------------------
 // One V-cycle (Section 3.2, steps 1-7 with the coarse solve replaced by the
 // recursion) from level l: grid kernels down to the coarse tail, which runs
@@ -391,11 +410,12 @@ void vcycle64(richards_ctx* c, int l) {
   if (l >= c->tail_start) {
     Prof pr(c, "tail64", l, c->L[l].ncell);
     rich::tail64(c->dL64, c->dX64, l, c->nlev, P, model, c->opts.nu1, c->opts.nu2, c->opts.coarse_max_sweeps,
-                 c->opts.coarse_rtol, c->scratch + 16, c->s);
+                 c->opts.coarse_rtol, c->opts.cycle_gamma, c->opts.gamma_levels, c->scratch + 16, c->s);
     return;
   }
   const Level<double> F = view64(c, l), C = view64(c, l + 1);
   const long long half = (F.ncell + 1) / 2;
+  nvtxRangePushA(level_range(l));
   for (int k = 0; k < c->opts.nu1; ++k) {
     { Prof pr(c, "sweep64", l, half); rich::sweep64(F, P, model, 0, c->s); }
     { Prof pr(c, "sweep64", l, F.ncell - half); rich::sweep64(F, P, model, 1, c->s); }
@@ -404,12 +424,15 @@ void vcycle64(richards_ctx* c, int l) {
   { Prof pr(c, "residual64", l, F.ncell); rich::residual64(F, P, model, nullptr, c->s); }
   { Prof pr(c, "restrict64", l, C.ncell); rich::restrict64(F, C, xfer64(c, l), F.u, F.d, C.ubar, C.d, c->s); }
   { Prof pr(c, "tau64", l + 1, C.ncell); rich::tau64(C, P, model, c->s); }
-  vcycle64(c, l + 1);
+  nvtxRangePop();
+  for (int q = 0; q < gamma_at(c, l); ++q) vcycle64(c, l + 1);
+  nvtxRangePushA(level_range(l));
   { Prof pr(c, "prolong64", l, F.ncell); rich::prolong64(F, C, xfer64(c, l), c->s); }
   for (int k = 0; k < c->opts.nu2; ++k) {
     { Prof pr(c, "sweep64", l, half); rich::sweep64(F, P, model, 0, c->s); }
     { Prof pr(c, "sweep64", l, F.ncell - half); rich::sweep64(F, P, model, 1, c->s); }
   }
+  nvtxRangePop();
   c->updates_host += (long long)c->opts.nu2 * F.ncell;
 }
 
@@ -419,11 +442,12 @@ void vcycle32(richards_ctx* c, int l) {
   if (l >= c->tail_start) {
     Prof pr(c, "tail32", l, c->L[l].ncell);
     rich::tail32(c->dL32, c->dX32, l, c->nlev, P, model, c->opts.nu1, c->opts.nu2, c->opts.coarse_max_sweeps,
-                 (float)c->opts.coarse_rtol, c->scratch + 16, c->s);
+                 (float)c->opts.coarse_rtol, c->opts.cycle_gamma, c->opts.gamma_levels, c->scratch + 16, c->s);
     return;
   }
   const Level<float> F = view32(c, l), C = view32(c, l + 1);
   const long long half = (F.ncell + 1) / 2;
+  nvtxRangePushA(level_range(l));
   for (int k = 0; k < c->opts.nu1; ++k) {
     { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->s); }
     { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->s); }
@@ -432,12 +456,15 @@ void vcycle32(richards_ctx* c, int l) {
   { Prof pr(c, "residual32", l, F.ncell); rich::residual32(F, P, model, nullptr, c->s); }
   { Prof pr(c, "restrict32", l, C.ncell); rich::restrict32(F, C, xfer32(c, l), F.u, F.d, C.ubar, C.d, c->s); }
   { Prof pr(c, "tau32", l + 1, C.ncell); rich::tau32(C, P, model, c->s); }
-  vcycle32(c, l + 1);
+  nvtxRangePop();
+  for (int q = 0; q < gamma_at(c, l); ++q) vcycle32(c, l + 1);
+  nvtxRangePushA(level_range(l));
   { Prof pr(c, "prolong32", l, F.ncell); rich::prolong32(F, C, xfer32(c, l), c->s); }
   for (int k = 0; k < c->opts.nu2; ++k) {
     { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->s); }
     { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->s); }
   }
+  nvtxRangePop();
   c->updates_host += (long long)c->opts.nu2 * F.ncell;
 }
 
@@ -472,9 +499,16 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   const Phys<double> P = phys<double>(c);
   HLevel& F = c->L[0];
   Prof pr(c, "prep", 0, F.ncell);
+  const bool cache = c->opts.precision == 1;
   rich::prep_lagged(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
                     c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, P, c->soil.model, scheme, dt, F.Kc, F.g,
-                    F.u, c->s);
+                    F.u, cache && c->th_n_valid ? c->th_n : nullptr, cache && c->th_nm1_valid ? c->th_nm1 : nullptr,
+                    cache && !c->th_n_valid ? c->th_n : nullptr, cache && !c->th_nm1_valid ? c->th_nm1 : nullptr,
+                    c->s);
+  if (cache) {
+    c->th_n_valid = true;
+    if (scheme == 2) c->th_nm1_valid = true;
+  }
   double* kbw[6];
   for (int f = 0; f < 6; ++f) kbw[f] = F.kb[f];
   rich::prep_rhs(geom(c, 0), c->bcdev, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
@@ -485,8 +519,18 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   return RICH_OK;
 }
 
-richards_status finish_step(richards_ctx* c, double r, richards_status st) {
+richards_status finish_step(richards_ctx* c, double r, richards_status st, int theta_fresh = -1) {
   if (std::isnan(r)) return fail(c, RICH_ENAN, "NaN in the iterate; state kept at psi^n");
+  if (theta_fresh == 1) {            // th_cur = theta(psi^{n+1})
+    double* t = c->th_nm1;
+    c->th_nm1 = c->th_n;
+    c->th_n = c->th_cur;
+    c->th_cur = t;
+    c->th_nm1_valid = true;
+  } else if (theta_fresh == 0) {     // psi^{n+1} = psi^n
+    CK(cudaMemcpyAsync(c->th_nm1, c->th_n, sizeof(double) * c->L[0].ncell, cudaMemcpyDeviceToDevice, c->s));
+    c->th_nm1_valid = true;
+  }
   std::swap(c->psi_n, c->psi_nm1);
   CK(cudaMemcpyAsync(c->psi_n, c->L[0].u, sizeof(double) * c->L[0].ncell, cudaMemcpyDeviceToDevice, c->s));
   CK(cudaStreamSynchronize(c->s));
@@ -546,7 +590,8 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
     CK(cudaMemsetAsync(c->scratch, 0, sizeof(unsigned long long), c->s));
     {
       Prof pr(c, "outer_residual", 0, F.ncell);
-      rich::outer_residual(view64(c, 0), P64, model, F.gf, F.psi0f, F.uf, c->scratch, c->s);
+      rich::outer_residual(view64(c, 0), P64, model, F.gf, F.psi0f, F.uf, c->scratch, outer == 0 ? c->th_n : nullptr,
+                           outer == 0 ? nullptr : c->th_cur, c->s);
     }
     TRY(check_launch(c));
     double nrm;
@@ -592,7 +637,7 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
     info->resid = r;
     info->cell_updates = c->updates_host + tu;
   }
-  return finish_step(c, r, st);
+  return finish_step(c, r, st, outer > 0 ? 1 : 0);
 }
 
 richards_status check_ctx(const richards_ctx* c) { return c ? RICH_OK : RICH_EINVAL; }
@@ -614,11 +659,17 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
     if (a >= grid->dim && grid->n[a] != 1) return RICH_EINVAL;
     if (a < grid->dim && !(grid->L[a] > 0.0 && std::isfinite(grid->L[a]))) return RICH_EINVAL;
   }
+  // launch grids put rows and planes on grid y/z (< 65536) and index a
+  // level with 32-bit coordinates (< 2^31 cells)
+  if (grid->n[1] > 65535 || grid->n[2] > 65535 ||
+      (long long)grid->n[0] * grid->n[1] * grid->n[2] >= (1LL << 31))
+    return RICH_EINVAL;
   const richards_opts& o = *opts;
   if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max_sweeps < 1 || o.max_cycles < 0 || o.coarsest_max_n < 1 ||
       !(o.tol > 0.0) || o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
       o.ordering != 1 || (o.precision != 0 && o.precision != 1) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
-      o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0)
+      o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0 || o.cycle_gamma < 1 || o.cycle_gamma > 3 ||
+      o.gamma_levels < 0)
     return RICH_EINVAL;
   richards_ctx* c = new richards_ctx();
   c->s = (cudaStream_t)stream;
@@ -667,6 +718,11 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
   const long long N = c->L[0].ncell;
   if (st == RICH_OK) st = dalloc(c, &c->psi_n, N);
   if (st == RICH_OK) st = dalloc(c, &c->psi_nm1, N);
+  if (mixed) {
+    if (st == RICH_OK) st = dalloc(c, &c->th_n, N);
+    if (st == RICH_OK) st = dalloc(c, &c->th_nm1, N);
+    if (st == RICH_OK) st = dalloc(c, &c->th_cur, N);
+  }
   if (st == RICH_OK) st = dalloc(c, &c->dL64, c->nlev);
   if (st == RICH_OK) st = dalloc(c, &c->dX64, c->nlev);
   if (st == RICH_OK) st = dalloc(c, &c->dL32, c->nlev);
@@ -887,6 +943,7 @@ richards_status richards_set_state(richards_ctx* c, const double* psi, const dou
   CK(cudaStreamSynchronize(c->s));
   c->have_state = true;
   c->have_prev = psi_prev != nullptr;
+  c->th_n_valid = c->th_nm1_valid = false;
   c->t = t;
   return RICH_OK;
 }

@@ -205,6 +205,116 @@ __device__ __forceinline__ void dlaw_f(float psi0, float x, float p1, float p2, 
 }
 
 // ---------------------------------------------------------------------------
+// Fast single-precision pieces for the inner correction problem.  The inner
+// FP32 solve only has to be accurate to ~1e-5 relative (the FP64 outer
+// defect correction removes the rest), but the increments must stay free of
+// cancellation: log1p and expm1 of small arguments come from their Taylor
+// series (truncation below 1e-10 relative for |x| < 1/32), larger arguments
+// use the hardware approximations __logf / __expf (relative error ~1e-6 of a
+// result that is then not small).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fast_log1p(float x) {
+  if (fabsf(x) < 0.03125f) {
+    // x - x^2/2 + x^3/3 - x^4/4 + x^5/5 - x^6/6
+    const float p = fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f), -0.5f), 1.0f);
+    return x * p;
+  }
+  return __logf(1.0f + x);
+}
+
+__device__ __forceinline__ float fast_expm1(float x) {
+  if (fabsf(x) < 0.03125f) {
+    // x + x^2/2 + x^3/6 + x^4/24 + x^5/120 + x^6/720
+    const float p = fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f),
+                                             1.0f / 6.0f), 0.5f), 1.0f);
+    return x * p;
+  }
+  return __expf(x) - 1.0f;
+}
+
+// x^y for x > 0 through the hardware approximations
+__device__ __forceinline__ float fast_pow(float x, float y) { return __expf(y * __logf(x)); }
+
+// Same increments as dlaw_f, built from the fast pieces above.
+template <int MODEL>
+__device__ __forceinline__ void dlaw_fast(float psi0, float x, float p1, float p2, const Phys<float>& P,
+                                          float& Dth, float& dth) {
+  const float ds = P.ts - P.tr;
+  const float psi1 = psi0 + x;
+  const bool wet0 = !(psi0 < 0.0f), wet1 = !(psi1 < 0.0f);
+  if (MODEL == GARDNER) {
+    const float al = p1;
+    if (!wet0) {
+      const float e0 = __expf(al * psi0);
+      if (!wet1) {
+        const float em = fast_expm1(al * x);
+        Dth = ds * e0 * em;
+        dth = al * ds * e0 * (1.0f + em);
+      } else {
+        Dth = -ds * fast_expm1(al * psi0);
+        dth = 0.0f;
+      }
+    } else if (!wet1) {
+      Dth = ds * fast_expm1(al * psi1);
+      dth = al * ds * __expf(al * psi1);
+    } else {
+      Dth = 0.0f; dth = 0.0f;
+    }
+  } else if (MODEL == HAVERKAMP) {
+    const float al = p1, be = p2;
+    if (!wet0) {
+      const float h0 = -psi0;
+      const float u0 = fast_pow(h0, be);
+      if (!wet1) {
+        const float du = u0 * fast_expm1(be * fast_log1p(__fdividef(x, psi0)));
+        const float u1 = u0 + du, h1 = -psi1;
+        const float den1 = al + u1;
+        Dth = __fdividef(-al * ds * du, (al + u0) * den1);
+        dth = __fdividef(al * ds * be * __fdividef(u1, h1), den1 * den1);
+      } else {
+        Dth = __fdividef(ds * u0, al + u0);
+        dth = 0.0f;
+      }
+    } else if (!wet1) {
+      const float h1 = -psi1;
+      const float u1 = fast_pow(h1, be);
+      const float den1 = al + u1;
+      Dth = __fdividef(-ds * u1, den1);
+      dth = __fdividef(al * ds * be * __fdividef(u1, h1), den1 * den1);
+    } else {
+      Dth = 0.0f; dth = 0.0f;
+    }
+  } else {
+    const float al = p1, n = p2, m = 1.0f - __fdividef(1.0f, n);
+    if (!wet0) {
+      const float h0 = -psi0;
+      const float t0 = fast_pow(al * h0, n);
+      const float L0 = fast_log1p(t0);
+      const float Se0 = __expf(-m * L0);
+      if (!wet1) {
+        const float dt = t0 * fast_expm1(n * fast_log1p(__fdividef(x, psi0)));
+        const float t1 = t0 + dt;
+        const float dSe = Se0 * fast_expm1(-m * fast_log1p(__fdividef(dt, 1.0f + t0)));
+        const float Se1 = Se0 + dSe;
+        Dth = ds * dSe;
+        dth = ds * m * n * __fdividef(t1, -psi1) * __fdividef(Se1, 1.0f + t1);
+      } else {
+        Dth = -ds * fast_expm1(-m * L0);
+        dth = 0.0f;
+      }
+    } else if (!wet1) {
+      const float h1 = -psi1;
+      const float t1 = fast_pow(al * h1, n);
+      const float L1 = fast_log1p(t1);
+      Dth = ds * fast_expm1(-m * L1);
+      dth = ds * m * n * __fdividef(t1, h1) * __fdividef(__expf(-m * L1), 1.0f + t1);
+    } else {
+      Dth = 0.0f; dth = 0.0f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Sink reading: S = smax * alpha_F(psi), alpha_F piecewise linear through
 // (h4,0), (h3,1), (h2,1), (h1,0), zero outside; right derivatives at kinks.
 // ---------------------------------------------------------------------------
@@ -293,7 +403,7 @@ __device__ __forceinline__ void storage(T x, T psi0, T p1, T p2, T smax, const P
   } else {
     static_assert(sizeof(T) == 4, "increment form is FP32");
     float Dth, dth, DS, dS;
-    dlaw_f<MODEL>(psi0, x, p1, p2, P, Dth, dth);
+    dlaw_fast<MODEL>(psi0, x, p1, p2, P, Dth, dth);
     sink_delta(psi0, x, smax, P, DS, dS);
     val = P.a * Dth + DS;
     der = P.a * dth + dS;
@@ -367,22 +477,25 @@ __device__ __forceinline__ T apply_N(const Level<T>& L, const Phys<T>& P, const 
   return val + P.xi * u[i] + mii * u[i] - off;
 }
 
+// (levels hold fewer than 2^31 cells: 32-bit division suffices)
 __device__ __forceinline__ void cell_coords(const int n0, const int n1, long long i, int& i0, int& i1,
                                             int& i2) {
-  const long long r = i / n0;
-  i0 = (int)(i - r * n0);
-  i1 = (int)(r % n1);
-  i2 = (int)(r / n1);
+  const unsigned ui = (unsigned)i;
+  const unsigned r = ui / (unsigned)n0;
+  i0 = (int)(ui - r * (unsigned)n0);
+  i1 = (int)(r % (unsigned)n1);
+  i2 = (int)(r / (unsigned)n1);
 }
 
 // thread index t over one colour -> cell (x pairs, colour chosen per row)
 __device__ __forceinline__ bool color_cell(int n0, int n1, long long t, int color, int& i0, int& i1,
                                            int& i2, long long& i) {
-  const int nh = (n0 + 1) >> 1;
-  const long long r = t / nh;
-  const int p = (int)(t - r * nh);
-  i1 = (int)(r % n1);
-  i2 = (int)(r / n1);
+  const unsigned nh = (unsigned)((n0 + 1) >> 1);
+  const unsigned ut = (unsigned)t;
+  const unsigned r = ut / nh;
+  const int p = (int)(ut - r * nh);
+  i1 = (int)(r % (unsigned)n1);
+  i2 = (int)(r / (unsigned)n1);
   i0 = 2 * p + ((color + i1 + i2) & 1);
   if (i0 >= n0) return false;
   i = i0 + (long long)n0 * (i1 + (long long)n1 * i2);

@@ -20,8 +20,9 @@ void prolong64(const Level<double>& F, const Level<double>& C, const Xfer<double
   D::prolong(F, C, X, s);
 }
 void tail64(const Level<double>* dLs, const Xfer<double>* dXs, int l0, int nl, const Phys<double>& P, int model,
-            int nu1, int nu2, int cmax, double crtol, unsigned long long* stats, cudaStream_t s) {
-  D::tail(dLs, dXs, l0, nl, P, model, nu1, nu2, cmax, crtol, stats, s);
+            int nu1, int nu2, int cmax, double crtol, int gamma, int gamma_levels, unsigned long long* stats,
+            cudaStream_t s) {
+  D::tail(dLs, dXs, l0, nl, P, model, nu1, nu2, cmax, crtol, gamma, gamma_levels, stats, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -34,19 +35,35 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
                                                      const double* __restrict__ psinm1, const double* __restrict__ Ks,
                                                      double Ks_s, const double* __restrict__ p1f,
                                                      const double* __restrict__ p2f, Phys<double> P, int scheme,
-                                                     double dt, double* Kc, double* g, double* u) {
+                                                     double dt, double* Kc, double* g, double* u,
+                                                     const double* thn_in, const double* thm_in, double* thn_out,
+                                                     double* thm_out) {
+  // thn_in / thm_in: theta(psi^n), theta(psi^{n-1}) kept from earlier FP64
+  // evaluations (nullable: evaluate here, and keep them in *_out if given)
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double p1 = p1f ? p1f[i] : P.p1, p2 = p2f ? p2f[i] : P.p2;
     const double ks = Ks ? Ks[i] : Ks_s;
     const double pn = psin[i];
-    const double thn = theta_only_d<MODEL>(pn, p1, p2, P);
+    double thn;
+    if (thn_in) {
+      thn = thn_in[i];
+    } else {
+      thn = theta_only_d<MODEL>(pn, p1, p2, P);
+      if (thn_out) thn_out[i] = thn;
+    }
     double ps, hist;
     if (scheme == 1) {
       ps = pn;
       hist = thn / dt;
     } else {
       const double pm = psinm1[i];
-      const double thm = theta_only_d<MODEL>(pm, p1, p2, P);
+      double thm;
+      if (thm_in) {
+        thm = thm_in[i];
+      } else {
+        thm = theta_only_d<MODEL>(pm, p1, p2, P);
+        if (thm_out) thm_out[i] = thm;
+      }
       ps = 2.0 * pn - pm;
       hist = (4.0 * thn - thm) / (2.0 * dt);
     }
@@ -150,16 +167,31 @@ __global__ void __launch_bounds__(256) k_to_float(const double* src, float* dst,
 
 // FP64 defect of the outer correction loop; hands the FP32 inner problem its
 // right side r, its frozen state psi0 and a zero initial correction.
+// th_in: theta(u) known already (the iterate is psi^n); otherwise theta(u) is
+// evaluated and kept in th_out for the next step's history.
 template <int MODEL>
 __global__ void __launch_bounds__(256) k_outer_residual(Level<double> L, Phys<double> P, float* r32, float* psi0f,
-                                                        float* delta, unsigned long long* norm) {
+                                                        float* delta, unsigned long long* norm,
+                                                        const double* __restrict__ th_in, double* th_out) {
   __shared__ unsigned long long sm[33];
   unsigned long long mx = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.ncell;
        i += (long long)gridDim.x * blockDim.x) {
     int i0, i1, i2;
     cell_coords(L.n0, L.n1, i, i0, i1, i2);
-    const double di = L.g[i] - apply_N<double, FORM_DIRECT, MODEL>(L, P, L.u, i, i0, i1, i2);
+    double mii, off;
+    stencil(L, i, i0, i1, i2, L.u, mii, off);
+    const double ui = L.u[i];
+    double th;
+    if (th_in) {
+      th = th_in[i];
+    } else {
+      th = theta_only_d<MODEL>(ui, L.p1 ? L.p1[i] : P.p1, L.p2 ? L.p2[i] : P.p2, P);
+      th_out[i] = th;
+    }
+    double S, dS;
+    sink_direct(ui, L.smax ? L.smax[i] : 0.0, P, S, dS);
+    const double di = L.g[i] - (P.a * th + S + P.xi * ui + mii * ui - off);
     r32[i] = (float)di;
     psi0f[i] = (float)L.u[i];
     delta[i] = 0.0f;
@@ -177,15 +209,19 @@ __global__ void __launch_bounds__(256) k_apply_delta(double* u, const float* del
 
 void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
                  const double* p1, const double* p2, const Phys<double>& P, int model, int scheme, double dt,
-                 double* Kc, double* g, double* u, cudaStream_t s) {
+                 double* Kc, double* g, double* u, const double* thn_in, const double* thm_in, double* thn_out,
+                 double* thm_out, cudaStream_t s) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
   const int b = grid_for(n);
   if (model == HAVERKAMP)
-    k_prep_lagged<HAVERKAMP><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, P, scheme, dt, Kc, g, u);
+    k_prep_lagged<HAVERKAMP><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, P, scheme, dt, Kc, g, u, thn_in,
+                                               thm_in, thn_out, thm_out);
   else if (model == GARDNER)
-    k_prep_lagged<GARDNER><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, P, scheme, dt, Kc, g, u);
+    k_prep_lagged<GARDNER><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, P, scheme, dt, Kc, g, u, thn_in,
+                                             thm_in, thn_out, thm_out);
   else
-    k_prep_lagged<VANGENUCHTEN><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, P, scheme, dt, Kc, g, u);
+    k_prep_lagged<VANGENUCHTEN><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, P, scheme, dt, Kc, g, u, thn_in,
+                                                  thm_in, thn_out, thm_out);
 }
 
 void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
@@ -219,11 +255,11 @@ void to_float(const double* src, float* dst, long long n, cudaStream_t s) {
 }
 
 void outer_residual(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
-                    float* delta, unsigned long long* norm, cudaStream_t s) {
+                    float* delta, unsigned long long* norm, const double* th_in, double* th_out, cudaStream_t s) {
   const int b = grid_for(L.ncell);
-  if (model == HAVERKAMP) k_outer_residual<HAVERKAMP><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm);
-  else if (model == GARDNER) k_outer_residual<GARDNER><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm);
-  else k_outer_residual<VANGENUCHTEN><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm);
+  if (model == HAVERKAMP) k_outer_residual<HAVERKAMP><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
+  else if (model == GARDNER) k_outer_residual<GARDNER><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
+  else k_outer_residual<VANGENUCHTEN><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
 }
 
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s) {

@@ -22,69 +22,68 @@ __device__ __forceinline__ float from_bits<float>(unsigned long long b) {
 // One colour of a red-black NGS sweep (eq. point-update for every cell of the
 // colour; cells of one colour do not couple, so the update is parallel).
 // ---------------------------------------------------------------------------
+// Launch grid: x = pairs of cells along a row, y = row, z = plane.
 template <typename T, int FORM, int MODEL>
 __global__ void __launch_bounds__(256) k_sweep(Level<T> L, Phys<T> P, int color) {
-  const long long nh = (long long)((L.n0 + 1) >> 1) * L.n1 * L.n2;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nh;
-       t += (long long)gridDim.x * blockDim.x) {
-    int i0, i1, i2;
-    long long i;
-    if (color_cell(L.n0, L.n1, t, color, i0, i1, i2, i)) point_update<T, FORM, MODEL>(L, P, i, i0, i1, i2);
-  }
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i2 = blockIdx.z;
+  const int i0 = 2 * p + ((color + i1 + i2) & 1);
+  if (i0 >= L.n0) return;
+  const long long i = i0 + (long long)L.n0 * (i1 + L.n1 * i2);
+  point_update<T, FORM, MODEL>(L, P, i, i0, i1, i2);
 }
 
 // d = g - N(u) on a level, with ||d||_inf accumulated into *norm (bit max).
+// Launch grid: x = cells along a row, y = row, z = plane.
 template <typename T, int FORM, int MODEL>
 __global__ void __launch_bounds__(256) k_residual(Level<T> L, Phys<T> P, unsigned long long* norm) {
   __shared__ unsigned long long sm[33];
   unsigned long long mx = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.ncell;
-       i += (long long)gridDim.x * blockDim.x) {
-    int i0, i1, i2;
-    cell_coords(L.n0, L.n1, i, i0, i1, i2);
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i2 = blockIdx.z;
+  if (i0 < L.n0) {
+    const long long i = i0 + (long long)L.n0 * (i1 + L.n1 * i2);
     const T di = L.g[i] - apply_N<T, FORM, MODEL>(L, P, L.u, i, i0, i1, i2);
     L.d[i] = di;
-    const unsigned long long b = nbits(di);
-    mx = b > mx ? b : mx;
+    mx = nbits(di);
   }
-  mx = block_max(mx, sm);
-  if (threadIdx.x == 0 && norm) atomicMax(norm, mx);
+  if (norm) {
+    mx = block_max(mx, sm);
+    if (threadIdx.x == 0) atomicMax(norm, mx);
+  }
 }
 
 // FAS step 3: psi_bar_H = R psi_h, d_H = R d_h (cb may be null).
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(Level<T> F, Level<T> C, Xfer<T> X, const T* fa, const T* fb,
                                                   T* ca, T* cb) {
-  for (long long J = blockIdx.x * (long long)blockDim.x + threadIdx.x; J < C.ncell;
-       J += (long long)gridDim.x * blockDim.x) {
-    int J0, J1, J2;
-    cell_coords(C.n0, C.n1, J, J0, J1, J2);
-    ca[J] = restrict_at(F, X, fa, J0, J1, J2);
-    if (cb) cb[J] = restrict_at(F, X, fb, J0, J1, J2);
-  }
+  const int J0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J1 = blockIdx.y, J2 = blockIdx.z;
+  if (J0 >= C.n0) return;
+  const long long J = J0 + (long long)C.n0 * (J1 + C.n1 * J2);
+  ca[J] = restrict_at(F, X, fa, J0, J1, J2);
+  if (cb) cb[J] = restrict_at(F, X, fb, J0, J1, J2);
 }
 
 // FAS step 4 on the coarse level: g_H = N_H(psi_bar_H) + d_H, psi_H = psi_bar_H.
 template <typename T, int FORM, int MODEL>
 __global__ void __launch_bounds__(256) k_tau(Level<T> C, Phys<T> P) {
-  for (long long J = blockIdx.x * (long long)blockDim.x + threadIdx.x; J < C.ncell;
-       J += (long long)gridDim.x * blockDim.x) {
-    int J0, J1, J2;
-    cell_coords(C.n0, C.n1, J, J0, J1, J2);
-    C.g[J] = apply_N<T, FORM, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
-    C.u[J] = C.ubar[J];
-  }
+  const int J0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J1 = blockIdx.y, J2 = blockIdx.z;
+  if (J0 >= C.n0) return;
+  const long long J = J0 + (long long)C.n0 * (J1 + C.n1 * J2);
+  C.g[J] = apply_N<T, FORM, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
+  C.u[J] = C.ubar[J];
 }
 
 // FAS step 6: u_h += P (u_H - psi_bar_H).
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong(Level<T> F, Level<T> C, Xfer<T> X) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < F.ncell;
-       i += (long long)gridDim.x * blockDim.x) {
-    int i0, i1, i2;
-    cell_coords(F.n0, F.n1, i, i0, i1, i2);
-    F.u[i] += prolong_at(C, X, i0, i1, i2);
-  }
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i2 = blockIdx.z;
+  if (i0 >= F.n0) return;
+  const long long i = i0 + (long long)F.n0 * (i1 + F.n1 * i2);
+  F.u[i] += prolong_at(C, X, i0, i1, i2);
 }
 
 // ---------------------------------------------------------------------------
@@ -119,53 +118,73 @@ __device__ __forceinline__ T block_defect_norm(const Level<T>& L, const Phys<T>&
   return from_bits<T>(block_max(mx, sm));
 }
 
-template <typename T, int FORM, int MODEL>
-__global__ void __launch_bounds__(TAIL_THREADS) k_tail(const Level<T>* __restrict__ Ls, const Xfer<T>* __restrict__ Xs,
-                                                       int l0, int nl, Phys<T> P, int nu1, int nu2, int cmax,
-                                                       T crtol, unsigned long long* stats) {
-  __shared__ unsigned long long sm[33];
-  unsigned long long updates = 0;
-  for (int l = l0; l < nl - 1; ++l) {
-    const Level<T> F = Ls[l];
-    for (int s = 0; s < nu1; ++s) block_sweep<T, FORM, MODEL>(F, P);
-    updates += (unsigned long long)nu1 * F.ncell;
-    for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
-      int i0, i1, i2;
-      cell_coords(F.n0, F.n1, i, i0, i1, i2);
-      F.d[i] = F.g[i] - apply_N<T, FORM, MODEL>(F, P, F.u, i, i0, i1, i2);
+// Levels l0..nl-1 of one multigrid cycle in one thread block, with the
+// recursion of Section 3.2 unrolled: pre-smoothing, defect, restriction and
+// the FAS right side on the way down; gamma visits of each coarser level
+// (1: V-cycle, 2: W-cycle); the coarsest level sweeps until its defect drops
+// by crtol or cmax sweeps are done; prolongation and post-smoothing on the
+// way up.  LV gives the level views (L(l)) and transfer tables (X(l)).
+template <typename T, int FORM, int MODEL, typename LV>
+__device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const Phys<T>& P, int nu1, int nu2, int cmax, T crtol,
+                            int gamma, int gamma_levels, unsigned long long* sm, unsigned long long& updates) {
+  int visits[24];
+  int l = l0;
+  bool down = true;
+  for (;;) {
+    if (down) {
+      if (l == nl - 1) {
+        const Level<T>& C = lv.L(l);
+        const T d0 = block_defect_norm<T, FORM, MODEL>(C, P, sm);
+        for (int s = 0; s < cmax; ++s) {
+          block_sweep<T, FORM, MODEL>(C, P);
+          updates += C.ncell;
+          const T dn = block_defect_norm<T, FORM, MODEL>(C, P, sm);
+          if (!(dn > crtol * d0)) break;
+        }
+        down = false;
+        continue;
+      }
+      const Level<T>& F = lv.L(l);
+      for (int s = 0; s < nu1; ++s) block_sweep<T, FORM, MODEL>(F, P);
+      updates += (unsigned long long)nu1 * F.ncell;
+      for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
+        int i0, i1, i2;
+        cell_coords(F.n0, F.n1, i, i0, i1, i2);
+        F.d[i] = F.g[i] - apply_N<T, FORM, MODEL>(F, P, F.u, i, i0, i1, i2);
+      }
+      __syncthreads();
+      const Level<T>& C = lv.L(l + 1);
+      const Xfer<T>& X = lv.X(l);
+      for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
+        int J0, J1, J2;
+        cell_coords(C.n0, C.n1, J, J0, J1, J2);
+        C.ubar[J] = restrict_at(F, X, F.u, J0, J1, J2);
+        C.d[J] = restrict_at(F, X, F.d, J0, J1, J2);
+      }
+      __syncthreads();
+      for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
+        int J0, J1, J2;
+        cell_coords(C.n0, C.n1, J, J0, J1, J2);
+        C.g[J] = apply_N<T, FORM, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
+        C.u[J] = C.ubar[J];
+      }
+      __syncthreads();
+      visits[l] = 0;
+      ++l;
+      continue;
     }
-    __syncthreads();
-    const Level<T> C = Ls[l + 1];
-    const Xfer<T> X = Xs[l];
-    for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
-      int J0, J1, J2;
-      cell_coords(C.n0, C.n1, J, J0, J1, J2);
-      C.ubar[J] = restrict_at(F, X, F.u, J0, J1, J2);
-      C.d[J] = restrict_at(F, X, F.d, J0, J1, J2);
+    // level l is finished: back to its parent
+    if (l == l0) break;
+    const int pl = l - 1;
+    const int g = (gamma_levels <= 0 || pl < gamma_levels) ? gamma : 1;
+    if (++visits[pl] < g) {           // visit the coarser level again (same right side)
+      l = pl + 1;
+      down = true;
+      continue;
     }
-    __syncthreads();
-    for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
-      int J0, J1, J2;
-      cell_coords(C.n0, C.n1, J, J0, J1, J2);
-      C.g[J] = apply_N<T, FORM, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
-      C.u[J] = C.ubar[J];
-    }
-    __syncthreads();
-  }
-  {
-    const Level<T> C = Ls[nl - 1];
-    const T d0 = block_defect_norm<T, FORM, MODEL>(C, P, sm);
-    for (int s = 0; s < cmax; ++s) {
-      block_sweep<T, FORM, MODEL>(C, P);
-      updates += C.ncell;
-      const T dn = block_defect_norm<T, FORM, MODEL>(C, P, sm);
-      if (!(dn > crtol * d0)) break;
-    }
-  }
-  for (int l = nl - 2; l >= l0; --l) {
-    const Level<T> F = Ls[l];
-    const Level<T> C = Ls[l + 1];
-    const Xfer<T> X = Xs[l];
+    const Level<T>& F = lv.L(pl);
+    const Level<T>& C = lv.L(pl + 1);
+    const Xfer<T>& X = lv.X(pl);
     for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
       int i0, i1, i2;
       cell_coords(F.n0, F.n1, i, i0, i1, i2);
@@ -174,7 +193,26 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const Level<T>* __restric
     __syncthreads();
     for (int s = 0; s < nu2; ++s) block_sweep<T, FORM, MODEL>(F, P);
     updates += (unsigned long long)nu2 * F.ncell;
+    l = pl;
   }
+}
+
+template <typename T>
+struct DeviceLevels {
+  const Level<T>* Ls;
+  const Xfer<T>* Xs;
+  __device__ const Level<T>& L(int l) const { return Ls[l]; }
+  __device__ const Xfer<T>& X(int l) const { return Xs[l]; }
+};
+
+template <typename T, int FORM, int MODEL>
+__global__ void __launch_bounds__(TAIL_THREADS, 1) k_tail(const Level<T>* __restrict__ Ls, const Xfer<T>* __restrict__ Xs,
+                                                       int l0, int nl, Phys<T> P, int nu1, int nu2, int cmax,
+                                                       T crtol, int gamma, int gamma_levels, unsigned long long* stats) {
+  __shared__ unsigned long long sm[33];
+  unsigned long long updates = 0;
+  block_cycle<T, FORM, MODEL>(DeviceLevels<T>{Ls, Xs}, l0, nl, P, nu1, nu2, cmax, crtol, gamma, gamma_levels, sm,
+                              updates);
   if (threadIdx.x == 0 && stats) atomicAdd(stats, updates);
 }
 
@@ -189,43 +227,62 @@ inline int grid_for(long long n, int bs = 256) {
   return (int)b;
 }
 
+// 3D launch over (units along x, n1 rows, n2 planes): block x-size is a
+// power of two between 32 and 128 covering the row
+struct Launch3 {
+  dim3 grid, block;
+};
+inline Launch3 launch3(int nx, int n1, int n2) {
+  int bx = 32;
+  while (bx < nx && bx < 128) bx <<= 1;
+  Launch3 L;
+  L.block = dim3(bx, 1, 1);
+  L.grid = dim3((nx + bx - 1) / bx, n1, n2);
+  return L;
+}
+
 template <typename T, int FORM>
 struct Dispatch {
   static void sweep(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
-    const long long nh = (long long)((L.n0 + 1) >> 1) * L.n1 * L.n2;
-    const int g = grid_for(nh);
-    if (model == HAVERKAMP) k_sweep<T, FORM, HAVERKAMP><<<g, 256, 0, s>>>(L, P, color);
-    else if (model == GARDNER) k_sweep<T, FORM, GARDNER><<<g, 256, 0, s>>>(L, P, color);
-    else k_sweep<T, FORM, VANGENUCHTEN><<<g, 256, 0, s>>>(L, P, color);
+    const Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
+    if (model == HAVERKAMP) k_sweep<T, FORM, HAVERKAMP><<<g.grid, g.block, 0, s>>>(L, P, color);
+    else if (model == GARDNER) k_sweep<T, FORM, GARDNER><<<g.grid, g.block, 0, s>>>(L, P, color);
+    else k_sweep<T, FORM, VANGENUCHTEN><<<g.grid, g.block, 0, s>>>(L, P, color);
   }
   static void residual(const Level<T>& L, const Phys<T>& P, int model, unsigned long long* norm,
                        cudaStream_t s) {
-    const int g = grid_for(L.ncell);
-    if (model == HAVERKAMP) k_residual<T, FORM, HAVERKAMP><<<g, 256, 0, s>>>(L, P, norm);
-    else if (model == GARDNER) k_residual<T, FORM, GARDNER><<<g, 256, 0, s>>>(L, P, norm);
-    else k_residual<T, FORM, VANGENUCHTEN><<<g, 256, 0, s>>>(L, P, norm);
+    const Launch3 g = launch3(L.n0, L.n1, L.n2);
+    if (model == HAVERKAMP) k_residual<T, FORM, HAVERKAMP><<<g.grid, g.block, 0, s>>>(L, P, norm);
+    else if (model == GARDNER) k_residual<T, FORM, GARDNER><<<g.grid, g.block, 0, s>>>(L, P, norm);
+    else k_residual<T, FORM, VANGENUCHTEN><<<g.grid, g.block, 0, s>>>(L, P, norm);
   }
   static void tau(const Level<T>& C, const Phys<T>& P, int model, cudaStream_t s) {
-    const int g = grid_for(C.ncell);
-    if (model == HAVERKAMP) k_tau<T, FORM, HAVERKAMP><<<g, 256, 0, s>>>(C, P);
-    else if (model == GARDNER) k_tau<T, FORM, GARDNER><<<g, 256, 0, s>>>(C, P);
-    else k_tau<T, FORM, VANGENUCHTEN><<<g, 256, 0, s>>>(C, P);
+    const Launch3 g = launch3(C.n0, C.n1, C.n2);
+    if (model == HAVERKAMP) k_tau<T, FORM, HAVERKAMP><<<g.grid, g.block, 0, s>>>(C, P);
+    else if (model == GARDNER) k_tau<T, FORM, GARDNER><<<g.grid, g.block, 0, s>>>(C, P);
+    else k_tau<T, FORM, VANGENUCHTEN><<<g.grid, g.block, 0, s>>>(C, P);
   }
   static void restrict2(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, const T* fa, const T* fb,
                         T* ca, T* cb, cudaStream_t s) {
-    k_restrict<T><<<grid_for(C.ncell), 256, 0, s>>>(F, C, X, fa, fb, ca, cb);
+    const Launch3 g = launch3(C.n0, C.n1, C.n2);
+    k_restrict<T><<<g.grid, g.block, 0, s>>>(F, C, X, fa, fb, ca, cb);
   }
   static void prolong(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, cudaStream_t s) {
-    k_prolong<T><<<grid_for(F.ncell), 256, 0, s>>>(F, C, X);
+    const Launch3 g = launch3(F.n0, F.n1, F.n2);
+    k_prolong<T><<<g.grid, g.block, 0, s>>>(F, C, X);
   }
   static void tail(const Level<T>* dLs, const Xfer<T>* dXs, int l0, int nl, const Phys<T>& P, int model,
-                   int nu1, int nu2, int cmax, T crtol, unsigned long long* stats, cudaStream_t s) {
+                   int nu1, int nu2, int cmax, T crtol, int gamma, int gamma_levels, unsigned long long* stats,
+                   cudaStream_t s) {
     if (model == HAVERKAMP)
-      k_tail<T, FORM, HAVERKAMP><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, stats);
+      k_tail<T, FORM, HAVERKAMP><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, gamma,
+                                                             gamma_levels, stats);
     else if (model == GARDNER)
-      k_tail<T, FORM, GARDNER><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, stats);
+      k_tail<T, FORM, GARDNER><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, gamma,
+                                                           gamma_levels, stats);
     else
-      k_tail<T, FORM, VANGENUCHTEN><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, stats);
+      k_tail<T, FORM, VANGENUCHTEN><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, gamma,
+                                                                gamma_levels, stats);
   }
 };
 

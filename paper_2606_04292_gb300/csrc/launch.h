@@ -31,7 +31,9 @@ void restrict64(const Level<double>& F, const Level<double>& C, const Xfer<doubl
                 const double* fb, double* ca, double* cb, cudaStream_t s);
 void prolong64(const Level<double>& F, const Level<double>& C, const Xfer<double>& X, cudaStream_t s);
 void tail64(const Level<double>* dLs, const Xfer<double>* dXs, int l0, int nl, const Phys<double>& P,
-            int model, int nu1, int nu2, int cmax, double crtol, unsigned long long* stats, cudaStream_t s);
+            int model, int nu1, int nu2, int cmax, double crtol, int gamma, int gamma_levels,
+            unsigned long long* stats,
+            cudaStream_t s);
 
 // FP32, correction delta as unknown
 void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, cudaStream_t s);
@@ -42,12 +44,15 @@ void restrict32(const Level<float>& F, const Level<float>& C, const Xfer<float>&
                 const float* fb, float* ca, float* cb, cudaStream_t s);
 void prolong32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, cudaStream_t s);
 void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, const Phys<float>& P,
-            int model, int nu1, int nu2, int cmax, float crtol, unsigned long long* stats, cudaStream_t s);
+            int model, int nu1, int nu2, int cmax, float crtol, int gamma, int gamma_levels,
+            unsigned long long* stats,
+            cudaStream_t s);
 
 // per-step preparation (FP64)
 void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
                  const double* p1, const double* p2, const Phys<double>& P, int model, int scheme, double dt,
-                 double* Kc, double* g, double* u, cudaStream_t s);
+                 double* Kc, double* g, double* u, const double* thn_in, const double* thm_in, double* thn_out,
+                 double* thm_out, cudaStream_t s);
 void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
               const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6], cudaStream_t s);
 void restrict_face64(const Geom& F, const Geom& C, const Xfer<double>& X, int axis, const double* fine,
@@ -57,7 +62,7 @@ void to_float(const double* src, float* dst, long long n, cudaStream_t s);
 
 // mixed mode: r = g - N(u) in FP64 -> r32, psi0 = (float)u, delta = 0; ||r||_inf
 void outer_residual(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
-                    float* delta, unsigned long long* norm, cudaStream_t s);
+                    float* delta, unsigned long long* norm, const double* th_in, double* th_out, cudaStream_t s);
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);
 
 }  // namespace rich

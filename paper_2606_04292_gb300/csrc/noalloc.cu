@@ -39,7 +39,7 @@ struct NaLevel {
 };
 
 struct NaPlan {
-  int nlev, dim, model, scheme, max_cycles, nu1, nu2, cmax;
+  int nlev, dim, model, scheme, max_cycles, nu1, nu2, cmax, gamma, gamma_levels;
   double crtol, tol, dt, Lv, h[3];
   double slo[3], shi[3];           // prolongation ghost factors per axis
   int het_p1, het_p2, het_Ks, sink;
@@ -224,8 +224,14 @@ __device__ void na_prepare(const NaPlan& p) {
   }
 }
 
+struct PlanLevels {
+  const NaLevel* lev;
+  __device__ const Level<double>& L(int l) const { return lev[l].L; }
+  __device__ const Xfer<double>& X(int l) const { return lev[l].X; }
+};
+
 template <int MODEL>
-__global__ void __launch_bounds__(TAIL_THREADS) k_small_step(NaPlan p) {
+__global__ void __launch_bounds__(TAIL_THREADS) k_small_step(const __grid_constant__ NaPlan p) {
   __shared__ unsigned long long sm[33];
   na_tables(p);
   na_prepare<MODEL>(p);
@@ -236,57 +242,8 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_small_step(NaPlan p) {
   int cycles = 0;
   unsigned long long updates = 0;
   while (!(r <= p.tol) && cycles < p.max_cycles && !isnan(r)) {
-    // one V-cycle (Section 3.2, steps 1-7, recursion unrolled)
-    for (int l = 0; l < p.nlev - 1; ++l) {
-      const Level<double>& F = p.lev[l].L;
-      for (int s = 0; s < p.nu1; ++s) block_sweep<double, FORM_DIRECT, MODEL>(F, P);
-      updates += (unsigned long long)p.nu1 * F.ncell;
-      for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
-        int i0, i1, i2;
-        cell_coords(F.n0, F.n1, i, i0, i1, i2);
-        F.d[i] = F.g[i] - apply_N<double, FORM_DIRECT, MODEL>(F, P, F.u, i, i0, i1, i2);
-      }
-      __syncthreads();
-      const Level<double>& C = p.lev[l + 1].L;
-      const Xfer<double>& X = p.lev[l].X;
-      for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
-        int J0, J1, J2;
-        cell_coords(C.n0, C.n1, J, J0, J1, J2);
-        C.ubar[J] = restrict_at(F, X, F.u, J0, J1, J2);
-        C.d[J] = restrict_at(F, X, F.d, J0, J1, J2);
-      }
-      __syncthreads();
-      for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
-        int J0, J1, J2;
-        cell_coords(C.n0, C.n1, J, J0, J1, J2);
-        C.g[J] = apply_N<double, FORM_DIRECT, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
-        C.u[J] = C.ubar[J];
-      }
-      __syncthreads();
-    }
-    {
-      const Level<double>& C = p.lev[p.nlev - 1].L;
-      const double d0 = block_defect_norm<double, FORM_DIRECT, MODEL>(C, P, sm);
-      for (int s = 0; s < p.cmax; ++s) {
-        block_sweep<double, FORM_DIRECT, MODEL>(C, P);
-        updates += C.ncell;
-        const double dn = block_defect_norm<double, FORM_DIRECT, MODEL>(C, P, sm);
-        if (!(dn > p.crtol * d0)) break;
-      }
-    }
-    for (int l = p.nlev - 2; l >= 0; --l) {
-      const Level<double>& F = p.lev[l].L;
-      const Level<double>& C = p.lev[l + 1].L;
-      const Xfer<double>& X = p.lev[l].X;
-      for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
-        int i0, i1, i2;
-        cell_coords(F.n0, F.n1, i, i0, i1, i2);
-        F.u[i] += prolong_at(C, X, i0, i1, i2);
-      }
-      __syncthreads();
-      for (int s = 0; s < p.nu2; ++s) block_sweep<double, FORM_DIRECT, MODEL>(F, P);
-      updates += (unsigned long long)p.nu2 * F.ncell;
-    }
+    block_cycle<double, FORM_DIRECT, MODEL>(PlanLevels{p.lev}, 0, p.nlev, P, p.nu1, p.nu2, p.cmax, p.crtol, p.gamma,
+                                            p.gamma_levels, sm, updates);
     ++cycles;
     r = teff * block_defect_norm<double, FORM_DIRECT, MODEL>(p.lev[0].L, P, sm);
   }
@@ -326,7 +283,7 @@ extern "C" richards_status richards_step_small_noalloc(const richards_grid* grid
   if (!(dt > 0.0) || !std::isfinite(dt) || (scheme != 1 && scheme != 2) || o.nu1 < 0 || o.nu2 < 0 ||
       o.coarse_max_sweeps < 1 || o.max_cycles < 0 || o.coarsest_max_n < 1 || !(o.tol > 0.0) ||
       o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
-      !(o.xi >= 0.0) || !(o.kappa >= 0.0))
+      !(o.xi >= 0.0) || !(o.kappa >= 0.0) || o.cycle_gamma < 1 || o.cycle_gamma > 3 || o.gamma_levels < 0)
     return RICH_EINVAL;
   if (soil->model < 0 || soil->model > 2 || !(soil->Ks > 0.0) || !(soil->theta_s > soil->theta_r) ||
       !(soil->theta_r >= 0.0))
@@ -418,6 +375,8 @@ extern "C" richards_status richards_step_small_noalloc(const richards_grid* grid
   p.nu1 = o.nu1;
   p.nu2 = o.nu2;
   p.cmax = o.coarse_max_sweeps;
+  p.gamma = o.cycle_gamma;
+  p.gamma_levels = o.gamma_levels;
   p.crtol = o.coarse_rtol;
   p.tol = o.tol;
   p.dt = dt;

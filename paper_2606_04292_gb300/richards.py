@@ -54,7 +54,7 @@ class richards_opts(C.Structure):
                 ("kappa", C.c_double), ("xi", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("ordering", C.c_int), ("newton_iters", C.c_int), ("precision", C.c_int),
                 ("inner_cycles", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int),
-                ("tail_cells", C.c_int)]
+                ("tail_cells", C.c_int), ("cycle_gamma", C.c_int), ("gamma_levels", C.c_int)]
 
 
 class richards_step_info(C.Structure):
@@ -148,7 +148,7 @@ def make_opts(o):
     return richards_opts(o["nu1"], o["nu2"], o["coarse_max_sweeps"], o["coarse_rtol"], o["coarsest_max_n"],
                          o["max_levels"], o["kappa_mode"], o["kappa"], o["xi"], o["tol"], o["max_cycles"],
                          o["ordering"], o["newton_iters"], o["precision"], o["inner_cycles"], o["inner_rtol"],
-                         o["max_outer"], o["tail_cells"])
+                         o["max_outer"], o["tail_cells"], o.get("cycle_gamma", 1), o.get("gamma_levels", 0))
 
 
 def current_stream():

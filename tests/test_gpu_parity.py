@@ -134,14 +134,16 @@ def test_residual_restrict_tau_prolong_match_oracle(mk):
 
 
 @pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
-def test_vcycle_matches_oracle(mk):
+@pytest.mark.parametrize("gamma,glev", [(1, 0), (2, 0), (2, 1)])
+def test_vcycle_matches_oracle(mk, gamma, glev):
     """Iterate-for-iterate V-cycles.  Point solves run to round-off and the
     coarsest level does a fixed number of sweeps: with a fixed two-step Newton
     the cycle map is discontinuous (whether a step bisects can flip on one
     ulp; the oracle alone moves by ~1e-3 under a 1e-15 input perturbation on
     the drainage case), and the coarse stop rule is a threshold decision."""
     prob = mk()
-    gs, orc, p = pair(prob, coarse_rtol=0.0, coarse_max_sweeps=12, newton_iters=0)
+    gs, orc, p = pair(prob, coarse_rtol=0.0, coarse_max_sweeps=12, newton_iters=0, cycle_gamma=gamma,
+                       gamma_levels=glev)
     gs.prepare(p["dt"], 1)
     orc.prepare(p["dt"], 1)
     ref = p["psi0"]

@@ -75,6 +75,7 @@ CASES = [
                                                         scheme=2)),
     ("2d_strip_mask_bdf2", lambda: W.strip_2d(n=63)),
     ("1d_celia_bdf1", lambda: W.celia_1d(n=128)),
+    ("3d_vg_wcycle", lambda: W.random_problem(3, (15, 14, 13), W.VANGENUCHTEN, 33, hetero=True, cycle_gamma=2)),
 ]
 
 
