@@ -343,8 +343,10 @@ orc_ctx *orc_create(const orc_grid *g, const orc_soil *s, const orc_bc *b,
     const double Z = lam * (1.0 - exp(-D / lam));
     for (long i = 0; i < N; ++i) {
       int ii[3]; cpos(L0, i, ii);
-      double z = (ii[v] + 0.5) * L0->h[v];
-      double depth = g->L[v] - z;
+      /* depth of the cell centre below the top face, L (2 (n-1-i) + 1) / (2 n):
+         one product and one quotient, so every implementation rounds it the
+         same way at the edge of the root zone */
+      double depth = g->L[v] * (double)(2 * (L0->n[v] - 1 - ii[v]) + 1) / (double)(2 * L0->n[v]);
       L0->smax[i] = depth <= D ? k->Tp * exp(-depth / lam) / Z : 0.0;
     }
   }
@@ -590,7 +592,14 @@ static double point_solve(const orc_ctx *c, const level *L, long i, double cc, d
                           double x0, int kfixed, int *iters) {
   const double a = c->a;
   const double smax = c->sink.enabled ? L->smax[i] : 0.0;
-  if (!(cc > 0.0)) { if (iters) *iters = 0; return x0; }
+  if (!(cc > 0.0)) {
+    /* a cell with no coupling and no shift (c = 0): add the shift
+       kappa (x - x0) with kappa = 1e-6 a, which leaves the root unchanged
+       and gives the bracket below */
+    const double k = 1e-6 * a;
+    f += (k - cc) * x0;
+    cc = k;
+  }
   double lo = (f - a * c->soil.theta_s - smax) / cc;
   double hi = (f - a * c->soil.theta_r) / cc;
   double x = x0 < lo ? lo : (x0 > hi ? hi : x0);
