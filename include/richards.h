@@ -292,6 +292,59 @@ richards_status richards_step_small_noalloc(const richards_grid *grid, const ric
                                             const double *psi_n, const double *psi_prev, double *psi_out,
                                             richards_step_info *info, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Batched soil columns: many independent 1D columns of uneven length solved
+ * in one persistent launch (a device work queue, longest column first; each
+ * thread block runs all time steps of one column with the column's whole
+ * multigrid hierarchy in shared memory).  Mixed precision as for
+ * richards_step with opts->precision 1: FP64 preparation, defect and stop
+ * test, FP32 FAS cycles on the correction equation.
+ * --------------------------------------------------------------------- */
+#define RICHARDS_COLUMN_MAX_CELLS 2048
+typedef struct richards_columns richards_columns;   /* opaque; owns its device memory */
+
+/* One column: n cells over length L (axis 0 is vertical, face 0 the bottom,
+   face 1 the top); scalar soil (fields are ignored; every column of a batch
+   uses the same soil law); boundary kinds/values as in richards_bc. */
+typedef struct {
+  int n;
+  double L;
+  richards_soil soil;
+  int bc_kind[2];
+  double bc_value[2];
+} richards_column;
+
+/* Create a batch; the sink (reading of (A2)) and the options are shared.
+   EINVAL: a column above RICHARDS_COLUMN_MAX_CELLS cells, mixed soil laws,
+   invalid parameters; ENOMEM; ECUDA. */
+richards_status richards_columns_create(int ncol, const richards_column *cols, const richards_sink *sink,
+                                        const richards_opts *opts, void *stream, richards_columns **out);
+void richards_columns_destroy(richards_columns *batch);
+long long richards_columns_ncell(const richards_columns *batch);
+
+/* States of all columns, packed in column order (host arrays of ncell
+   doubles); psi_prev nullable (the next BDF2 step falls back to BDF1). */
+richards_status richards_columns_set_state(richards_columns *batch, const double *psi, const double *psi_prev);
+
+/* nsteps implicit steps of every column in one launch (scheme 1 = BDF1,
+   2 = BDF2).  Per-column outcomes are read with richards_columns_stats. */
+richards_status richards_columns_run(richards_columns *batch, double dt, int nsteps, int scheme);
+
+richards_status richards_columns_get_state(richards_columns *batch, double *psi, int on_device);
+
+/* Per column (host arrays of ncol entries, each nullable): status of the
+   last run (RICH_OK / ENOCONV / ENAN), FP32 inner cycles, FP64 outer
+   iterations, last tau_eff ||g - N(psi)||_inf, NGS point updates. */
+richards_status richards_columns_stats(richards_columns *batch, int *status, int *cycles, int *outer,
+                                       double *resid, long long *updates);
+
+/* Threads per block (64, 128, 256 or 512). */
+richards_status richards_columns_set_threads(richards_columns *batch, int threads);
+
+/* Time one step of every column for each block size and keep the fastest;
+   the state is restored afterwards.  *threads_out (nullable) gets it. */
+richards_status richards_columns_autotune(richards_columns *batch, double dt, int scheme, int *threads_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -416,7 +416,13 @@ __device__ __forceinline__ void storage(T x, T psi0, T p1, T p2, T smax, const P
 template <typename T, int FORM, int MODEL>
 __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T smax,
                                          const Phys<T>& P) {
-  if (!(cc > T(0))) return x0;
+  if (!(cc > T(0))) {
+    // no coupling and no shift (c = 0): shift kappa (x - x0), kappa = 1e-6 a,
+    // which keeps the root and provides the bracket
+    const T k = T(1e-6) * P.a;
+    f += (k - cc) * x0;
+    cc = k;
+  }
   const T ds = P.ts - P.tr;
   T lo, hi;
   if constexpr (FORM == FORM_DIRECT) {
@@ -500,6 +506,33 @@ __device__ __forceinline__ bool color_cell(int n0, int n1, long long t, int colo
   if (i0 >= n0) return false;
   i = i0 + (long long)n0 * (i1 + (long long)n1 * i2);
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// One row of the linear interpolation from a coarse axis (nc cells) to fine
+// cell i of a fine axis (nf cells): the coarse coordinate of the fine centre
+// is ((2i+1) nc - nf) / (2 nf); a ghost beyond either end folds into the end
+// cell with factor slo / shi (+1 constant extrapolation, -1 zero on a
+// Dirichlet face).  Entries with zero weight are dropped, equal indices merged.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void interp_row(int nf, int nc, int i, double slo, double shi, int* idx, double* w,
+                                           int& cnt) {
+  cnt = 0;
+  auto add = [&](int j, double wt) {
+    if (wt == 0.0) return;
+    for (int k = 0; k < cnt; ++k)
+      if (idx[k] == j) { w[k] += wt; return; }
+    idx[cnt] = j;
+    w[cnt] = wt;
+    ++cnt;
+  };
+  if (nf == 1) { add(0, 1.0); return; }
+  const long long num = (long long)(2 * i + 1) * nc - nf, den = 2LL * nf;
+  const long long J0 = num >= 0 ? num / den : -((-num + den - 1) / den);
+  const double wt = (double)(num - J0 * den) / (double)den;
+  const long long J1 = J0 + 1;
+  if (J0 < 0) add(0, (1.0 - wt) * slo); else add((int)J0, 1.0 - wt);
+  if (J1 >= nc) add(nc - 1, wt * shi); else add((int)J1, wt);
 }
 
 // ---------------------------------------------------------------------------

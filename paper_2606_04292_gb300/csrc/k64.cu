@@ -154,8 +154,10 @@ __global__ void __launch_bounds__(256) k_sink_coef(Geom G, double Tp, double D, 
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     int ii[3];
     cell_coords(G.n0, G.n1, i, ii[0], ii[1], ii[2]);
-    const double z = (ii[v] + 0.5) * G.h[v];
-    const double depth = G.Lv - z;
+    // centre depth below the top face as one product and one quotient, so the
+    // root-zone edge is decided identically whatever the compiler fuses
+    const int nv = v == 0 ? G.n0 : (v == 1 ? G.n1 : G.n2);
+    const double depth = G.Lv * (double)(2 * (nv - 1 - ii[v]) + 1) / (double)(2 * nv);
     smax[i] = depth <= D ? Tp * exp(-depth / lam) / Z : 0.0;
   }
 }

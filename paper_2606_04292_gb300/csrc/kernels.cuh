@@ -123,7 +123,8 @@ __device__ __forceinline__ T block_defect_norm(const Level<T>& L, const Phys<T>&
 // the FAS right side on the way down; gamma visits of each coarser level
 // (1: V-cycle, 2: W-cycle); the coarsest level sweeps until its defect drops
 // by crtol or cmax sweeps are done; prolongation and post-smoothing on the
-// way up.  LV gives the level views (L(l)) and transfer tables (X(l)).
+// way up.  LV gives the level views (L(l)) and the transfers from level l:
+// restrict(l, fine array, coarse coords) and prolong(l, fine coords).
 template <typename T, int FORM, int MODEL, typename LV>
 __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const Phys<T>& P, int nu1, int nu2, int cmax, T crtol,
                             int gamma, int gamma_levels, unsigned long long* sm, unsigned long long& updates) {
@@ -154,12 +155,11 @@ __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const 
       }
       __syncthreads();
       const Level<T>& C = lv.L(l + 1);
-      const Xfer<T>& X = lv.X(l);
       for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
         int J0, J1, J2;
         cell_coords(C.n0, C.n1, J, J0, J1, J2);
-        C.ubar[J] = restrict_at(F, X, F.u, J0, J1, J2);
-        C.d[J] = restrict_at(F, X, F.d, J0, J1, J2);
+        C.ubar[J] = lv.restrict(l, F.u, J0, J1, J2);
+        C.d[J] = lv.restrict(l, F.d, J0, J1, J2);
       }
       __syncthreads();
       for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
@@ -183,12 +183,10 @@ __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const 
       continue;
     }
     const Level<T>& F = lv.L(pl);
-    const Level<T>& C = lv.L(pl + 1);
-    const Xfer<T>& X = lv.X(pl);
     for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
       int i0, i1, i2;
       cell_coords(F.n0, F.n1, i, i0, i1, i2);
-      F.u[i] += prolong_at(C, X, i0, i1, i2);
+      F.u[i] += lv.prolong(pl, i0, i1, i2);
     }
     __syncthreads();
     for (int s = 0; s < nu2; ++s) block_sweep<T, FORM, MODEL>(F, P);
@@ -202,7 +200,10 @@ struct DeviceLevels {
   const Level<T>* Ls;
   const Xfer<T>* Xs;
   __device__ const Level<T>& L(int l) const { return Ls[l]; }
-  __device__ const Xfer<T>& X(int l) const { return Xs[l]; }
+  __device__ T restrict(int l, const T* fine, int J0, int J1, int J2) const {
+    return restrict_at(Ls[l], Xs[l], fine, J0, J1, J2);
+  }
+  __device__ T prolong(int l, int i0, int i1, int i2) const { return prolong_at(Ls[l + 1], Xs[l], i0, i1, i2); }
 };
 
 template <typename T, int FORM, int MODEL>

@@ -55,25 +55,6 @@ struct NaPlan {
 // ---------------------------------------------------------------------------
 // device pieces
 // ---------------------------------------------------------------------------
-__device__ void na_interp(int nf, int nc, int i, double slo, double shi, int* idx, double* w, int& cnt) {
-  cnt = 0;
-  auto add = [&](int j, double wt) {
-    if (wt == 0.0) return;
-    for (int k = 0; k < cnt; ++k)
-      if (idx[k] == j) { w[k] += wt; return; }
-    idx[cnt] = j;
-    w[cnt] = wt;
-    ++cnt;
-  };
-  if (nf == 1) { add(0, 1.0); return; }
-  const long long num = (long long)(2 * i + 1) * nc - nf, den = 2LL * nf;
-  const long long J0 = num >= 0 ? num / den : -((-num + den - 1) / den);
-  const double wt = (double)(num - J0 * den) / (double)den;
-  const long long J1 = J0 + 1;
-  if (J0 < 0) add(0, (1.0 - wt) * slo); else add((int)J0, 1.0 - wt);
-  if (J1 >= nc) add(nc - 1, wt * shi); else add((int)J1, wt);
-}
-
 // transfer tables of every level, built by the block
 __device__ void na_tables(const NaPlan& p) {
   for (int l = 0; l + 1 < p.nlev; ++l) {
@@ -86,7 +67,7 @@ __device__ void na_tables(const NaPlan& p) {
         int idx[2];
         double w[2];
         int cnt;
-        na_interp(nf, nc, i, p.slo[ax], p.shi[ax], idx, w, cnt);
+        interp_row(nf, nc, i, p.slo[ax], p.shi[ax], idx, w, cnt);
         F.pc[ax][i] = cnt;
         for (int k = 0; k < 2; ++k) {
           F.pj[ax][2 * i + k] = k < cnt ? idx[k] : 0;
@@ -102,7 +83,7 @@ __device__ void na_tables(const NaPlan& p) {
           int idx[2];
           double w[2];
           int c2;
-          na_interp(nf, nc, i, 1.0, 1.0, idx, w, c2);
+          interp_row(nf, nc, i, 1.0, 1.0, idx, w, c2);
           for (int k = 0; k < c2; ++k)
             if (idx[k] == J && cnt < RMAX) {
               F.ri[ax][RMAX * J + cnt] = i;
@@ -149,7 +130,8 @@ __device__ void na_prepare(const NaPlan& p) {
       const int v = p.dim - 1;
       const double lam = p.root_decay, D = p.root_depth;
       const double Z = lam * (1.0 - exp(-D / lam));
-      const double depth = p.Lv - (ii[v] + 0.5) * p.h[v];
+      const int nv = v == 0 ? L.n0 : (v == 1 ? L.n1 : L.n2);
+      const double depth = p.Lv * (double)(2 * (nv - 1 - ii[v]) + 1) / (double)(2 * nv);
       F.smaxw[i] = depth <= D ? p.Tp * exp(-depth / lam) / Z : 0.0;
     }
   }
@@ -227,7 +209,12 @@ __device__ void na_prepare(const NaPlan& p) {
 struct PlanLevels {
   const NaLevel* lev;
   __device__ const Level<double>& L(int l) const { return lev[l].L; }
-  __device__ const Xfer<double>& X(int l) const { return lev[l].X; }
+  __device__ double restrict(int l, const double* fine, int J0, int J1, int J2) const {
+    return restrict_at(lev[l].L, lev[l].X, fine, J0, J1, J2);
+  }
+  __device__ double prolong(int l, int i0, int i1, int i2) const {
+    return prolong_at(lev[l + 1].L, lev[l].X, i0, i1, i2);
+  }
 };
 
 template <int MODEL>

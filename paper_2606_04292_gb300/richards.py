@@ -65,6 +65,11 @@ class richards_step_info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class richards_column(C.Structure):
+    _fields_ = [("n", C.c_int), ("L", C.c_double), ("soil", richards_soil), ("bc_kind", C.c_int * 2),
+                ("bc_value", C.c_double * 2)]
+
+
 class richards_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("level", C.c_int), ("launches", C.c_longlong), ("ms", C.c_double),
                 ("cells", C.c_longlong)]
@@ -99,6 +104,17 @@ _SIGS = {
     "richards_vcycle": (C.c_int, [_VP]),
     "richards_profile": (C.c_int, [_VP, C.c_int]),
     "richards_profile_read": (C.c_int, [_VP, C.POINTER(richards_kernel_stat), C.c_int]),
+    "richards_columns_create": (C.c_int, [C.c_int, C.POINTER(richards_column), C.POINTER(richards_sink),
+                                          C.POINTER(richards_opts), _VP, C.POINTER(_VP)]),
+    "richards_columns_destroy": (None, [_VP]),
+    "richards_columns_ncell": (C.c_longlong, [_VP]),
+    "richards_columns_set_state": (C.c_int, [_VP, _DP, _DP]),
+    "richards_columns_run": (C.c_int, [_VP, C.c_double, C.c_int, C.c_int]),
+    "richards_columns_get_state": (C.c_int, [_VP, _DP, C.c_int]),
+    "richards_columns_stats": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _DP,
+                                         C.POINTER(C.c_longlong)]),
+    "richards_columns_set_threads": (C.c_int, [_VP, C.c_int]),
+    "richards_columns_autotune": (C.c_int, [_VP, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     "richards_step_small_noalloc": (C.c_int, [C.POINTER(richards_grid), C.POINTER(richards_soil),
                                               C.POINTER(richards_bc), C.POINTER(richards_sink),
                                               C.POINTER(richards_opts), C.c_double, C.c_int, _DP, _DP, _DP,
@@ -319,3 +335,94 @@ class Solver:
             raise RichardsError(RICH_EINVAL, "profile_read failed")
         return [dict(name=buf[i].name.decode(), level=buf[i].level, launches=buf[i].launches, ms=buf[i].ms,
                      cells=buf[i].cells) for i in range(n)]
+
+
+class Columns:
+    """A batch of independent 1D columns (``richards_columns_*``).
+
+    ``probs``: list of 1D problem dicts (``workloads.columns()`` or
+    ``random_problem(1, ...)``); soil fields are not used (scalar soil per
+    column); the sink and the options of the first problem apply to all.
+    """
+
+    def __init__(self, probs, stream=None, opts=None):
+        L = lib()
+        self.probs = probs
+        o = dict(probs[0]["opts"])
+        if opts:
+            o.update(opts)
+        self.opts = o
+        arr = (richards_column * len(probs))()
+        for k, p in enumerate(probs):
+            s = p["soil"]
+            arr[k].n = int(p["n"][0])
+            arr[k].L = float(p["L"][0])
+            arr[k].soil = richards_soil(s["model"], s["Ks"], s["theta_s"], s["theta_r"], s["p1"], s["p2"],
+                                        s["p3"], s["p4"])
+            for f in range(2):
+                arr[k].bc_kind[f] = int(p["bc"]["kind"][f])
+                arr[k].bc_value[f] = float(p["bc"]["value"][f])
+        k0 = probs[0]["sink"]
+        sink = richards_sink(int(k0["enabled"]), k0["Tp"], k0["root_depth"], k0["root_decay"], k0["h1"],
+                             k0["h2"], k0["h3"], k0["h4"])
+        h = C.c_void_p()
+        st = L.richards_columns_create(len(probs), arr, C.byref(sink), C.byref(make_opts(o)),
+                                       C.c_void_p(current_stream() if stream is None else stream), C.byref(h))
+        if st != RICH_OK:
+            raise RichardsError(st, "richards_columns_create failed")
+        self.h = h
+        self.ncol = len(probs)
+        self.N = int(L.richards_columns_ncell(h))
+        self.offsets = np.cumsum([0] + [int(p["n"][0]) for p in probs])
+        psi = np.concatenate([np.asarray(p["psi0"], dtype=np.float64) for p in probs])
+        self.set_state(psi)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().richards_columns_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_state(self, psi, psi_prev=None):
+        psi = _f64(psi)
+        pp = None if psi_prev is None else _f64(psi_prev)
+        st = lib().richards_columns_set_state(self.h, _dp(psi), None if pp is None else _dp(pp))
+        if st != RICH_OK:
+            raise RichardsError(st, "richards_columns_set_state failed")
+
+    def run(self, dt, nsteps, scheme=1):
+        return lib().richards_columns_run(self.h, float(dt), int(nsteps), int(scheme))
+
+    def state(self):
+        out = np.empty(self.N)
+        st = lib().richards_columns_get_state(self.h, _dp(out), 0)
+        if st != RICH_OK:
+            raise RichardsError(st, "richards_columns_get_state failed")
+        return out
+
+    def column(self, psi, k):
+        return psi[self.offsets[k]:self.offsets[k + 1]]
+
+    def stats(self):
+        n = self.ncol
+        status = (C.c_int * n)()
+        cycles = (C.c_int * n)()
+        outer = (C.c_int * n)()
+        resid = np.empty(n)
+        upd = (C.c_longlong * n)()
+        st = lib().richards_columns_stats(self.h, status, cycles, outer, _dp(resid), upd)
+        if st != RICH_OK:
+            raise RichardsError(st, "richards_columns_stats failed")
+        return dict(status=np.array(status[:]), cycles=np.array(cycles[:]), outer=np.array(outer[:]),
+                    resid=resid, updates=np.array(upd[:], dtype=np.int64))
+
+    def set_threads(self, t):
+        return lib().richards_columns_set_threads(self.h, int(t))
+
+    def autotune(self, dt, scheme=1):
+        t = C.c_int()
+        st = lib().richards_columns_autotune(self.h, float(dt), int(scheme), C.byref(t))
+        if st != RICH_OK:
+            raise RichardsError(st, "richards_columns_autotune failed")
+        return t.value

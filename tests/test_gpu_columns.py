@@ -1,0 +1,133 @@
+"""Batched columns (persistent launch, device work queue) against the CPU
+oracle, column by column (needs a GPU).
+
+Each column is its own 1D problem; the batch solves all of them in one launch
+with FP32 inner cycles inside an FP64 defect correction.  At a tight tolerance
+every column must equal the oracle's FP64 solution; at the default tolerance
+the oracle's own FP64 stop test must hold for every column's result.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import ORC_OK, Oracle
+from paper_2606_04292_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_04292_gb300 import richards as R  # noqa: E402
+
+
+def mixed_columns(ncol, seed, nmin=5, nmax=300, **optkw):
+    """Columns of uneven length, per-column soil, every boundary kind."""
+    rng = np.random.default_rng(seed)
+    base = W.columns(ncol=ncol, seed=seed, nmin=nmin, nmax=nmax, **optkw)
+    kinds = [(W.FREE_DRAINAGE, W.FLUX), (W.DIRICHLET, W.DIRICHLET), (W.FREE_DRAINAGE, W.DIRICHLET),
+             (W.NOFLUX, W.FLUX)]
+    for k, p in enumerate(base):
+        kb, kt = kinds[k % len(kinds)]
+        p["bc"]["kind"][0], p["bc"]["kind"][1] = kb, kt
+        p["bc"]["value"][0] = -1.2 if kb == W.DIRICHLET else 0.0
+        p["bc"]["value"][1] = (-0.3 if kt == W.DIRICHLET else float(rng.uniform(0, 3e-7)))
+        n = p["n"][0]
+        p["psi0"] = -1.0 + 0.3 * np.sin(np.arange(n) / max(n, 1) * 3.0)
+    return base
+
+
+def oracle_column(p, **kw):
+    return Oracle(W.with_opts(p, **kw))
+
+
+def test_columns_match_oracle_at_tight_tolerance():
+    probs = mixed_columns(24, 11, tol=1e-12, max_outer=40)
+    cols = R.Columns(probs)
+    assert cols.run(probs[0]["dt"], 3, 1) == R.RICH_OK
+    st = cols.stats()
+    assert np.all(st["status"] == R.RICH_OK), st["status"]
+    psi = cols.state()
+    for k, p in enumerate(probs):
+        o = oracle_column(p, tol=1e-13, newton_iters=0)
+        for _ in range(3):
+            assert o.step()[0] == ORC_OK
+        ref = o.state()
+        got = cols.column(psi, k)
+        err = np.max(np.abs(got - ref))
+        assert err <= 1e-9 * max(1.0, np.max(np.abs(ref))), (k, p["n"][0], err, int(st["outer"][k]))
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_columns_satisfy_oracle_stop_test(scheme):
+    probs = mixed_columns(40, 12 + scheme)
+    cols = R.Columns(probs)
+    prev_all = None
+    cur_all = cols.state()
+    for step in range(2):
+        assert cols.run(probs[0]["dt"], 1, scheme) == R.RICH_OK
+        st = cols.stats()
+        assert np.all(st["status"] == R.RICH_OK)
+        new_all = cols.state()
+        for k, p in enumerate(probs):
+            o = oracle_column(p)
+            o.set_state(cols.column(cur_all, k), None if prev_all is None else cols.column(prev_all, k))
+            used = o.prepare(p["dt"], scheme)
+            _, nrm = o.residual(cols.column(new_all, k))
+            assert nrm / o.a <= p["opts"]["tol"] * (1 + 1e-6), (k, used, nrm / o.a)
+        prev_all, cur_all = cur_all, new_all
+
+
+def test_queue_with_many_more_columns_than_blocks():
+    """3000 short columns through the work queue (far more than the resident
+    blocks): every column is done, and sampled ones meet the oracle's stop test."""
+    probs = mixed_columns(3000, 13, nmin=1, nmax=40)
+    cols = R.Columns(probs)
+    psi0 = cols.state()
+    assert cols.run(probs[0]["dt"], 1, 1) == R.RICH_OK
+    st = cols.stats()
+    bad = np.nonzero(st["status"] != R.RICH_OK)[0]
+    assert len(bad) == 0, [(int(k), int(st["status"][k]), probs[k]["n"][0], float(st["resid"][k])) for k in bad[:10]]
+    psi = cols.state()
+    assert np.all(np.isfinite(psi))
+    for k in (0, 1, 2, 999, 1500, 2998, 2999):
+        o = oracle_column(probs[k])
+        o.set_state(cols.column(psi0, k))
+        o.prepare(probs[k]["dt"], 1)
+        _, nrm = o.residual(cols.column(psi, k))
+        assert nrm / o.a <= probs[k]["opts"]["tol"] * (1 + 1e-6), k
+
+
+def test_autotune_restores_state_and_matches_plain_run():
+    probs = mixed_columns(64, 14)
+    a = R.Columns(probs)
+    b = R.Columns(probs)
+    t = a.autotune(probs[0]["dt"], 1)
+    assert t in (128, 256, 512)
+    assert a.run(probs[0]["dt"], 2, 1) == R.RICH_OK
+    assert b.set_threads(t) == R.RICH_OK
+    assert b.run(probs[0]["dt"], 2, 1) == R.RICH_OK
+    assert np.array_equal(a.state(), b.state())
+
+
+def test_degenerate_and_limits():
+    probs = mixed_columns(6, 15, nmin=1, nmax=3)
+    cols = R.Columns(probs)
+    assert cols.run(probs[0]["dt"], 2, 1) == R.RICH_OK
+    psi = cols.state()
+    for k, p in enumerate(probs):
+        o = oracle_column(p)
+        for _ in range(2):
+            o.step()
+        ref = o.state()
+        got = cols.column(psi, k)
+        o2 = oracle_column(p)
+        o2.set_state(got)
+        # a 1-3 cell column is solved to the oracle's tolerance as well
+        assert np.max(np.abs(got - ref)) <= 1e-6 * max(1.0, np.max(np.abs(ref))), (k, p["n"])
+    big = mixed_columns(2, 16, nmin=2049, nmax=2049)
+    with pytest.raises(R.RichardsError):
+        R.Columns(big)
+    ok = mixed_columns(1, 17, nmin=2048, nmax=2048)
+    c2 = R.Columns(ok)
+    assert c2.run(ok[0]["dt"], 1, 1) == R.RICH_OK
