@@ -238,7 +238,10 @@ def main():
 
     prob = W.drainage_3d(n=args.n, cycle_gamma=args.gamma)
     N = W.ncells(prob)
-    stream = torch.cuda.current_stream()
+    # a stream of its own: the inner cycles are captured into CUDA graphs,
+    # which the legacy default stream does not allow
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     gs = R.Solver(prob, stream=stream.cuda_stream)
 
     def barrier():

@@ -117,7 +117,11 @@ typedef struct {
      cycle_gamma          coarse-grid visits per level: 1 = V-cycle (the
                           paper's), 2 = W-cycle
      gamma_levels         cycle_gamma applies on the levels above this one
-                          (0: on every level); coarser levels use V-cycles */
+                          (0: on every level); coarser levels use V-cycles
+     graphs               1: capture the FP32 inner cycle of the mixed mode
+                          into a CUDA graph and replay it (needs a stream
+                          other than the legacy default stream; falls back
+                          to direct launches otherwise) */
 typedef struct {
   int nu1, nu2, coarse_max_sweeps;
   double coarse_rtol;
@@ -127,7 +131,7 @@ typedef struct {
   int max_cycles, ordering, newton_iters, precision;
   int inner_cycles;
   double inner_rtol;
-  int max_outer, tail_cells, cycle_gamma, gamma_levels;
+  int max_outer, tail_cells, cycle_gamma, gamma_levels, graphs;
 } richards_opts;
 
 typedef struct {
@@ -179,6 +183,17 @@ richards_status richards_solve(richards_ctx *ctx, double dt, int nsteps, int sch
    1: a device pointer (ordered on the context's stream). */
 richards_status richards_get_state(richards_ctx *ctx, double *psi_out, int on_device);
 
+/* Water content and conductivity (Table 1, with each cell's own soil
+   parameters) at given pressure heads: theta_out[i] = theta(psi[i]),
+   K_out[i] = K(psi[i]) for the ncell cells of the finest level; theta_out or
+   K_out may be NULL.  on_device = 0: host arrays; 1: device arrays (ordered
+   on the context's stream).  arith 0: FP64, as every step computes them;
+   1: float-float (~1e-12 relative), the arithmetic of the mixed mode's
+   steering defects.  Returns RICH_EINVAL for a bad arith or before the soil
+   is set.  Useful for water-volume (mass balance) accounting. */
+richards_status richards_soil_eval(richards_ctx *ctx, const double *psi, double *theta_out,
+                                   double *K_out, int arith, int on_device);
+
 /* Model time and number of cells of the finest level. */
 double richards_time(const richards_ctx *ctx);
 long long richards_ncell(const richards_ctx *ctx);
@@ -189,6 +204,29 @@ const char *richards_last_error(const richards_ctx *ctx);
 
 /* Release the context and all its device memory.  NULL is accepted. */
 void richards_destroy(richards_ctx *ctx);
+
+/* ---------------------------------------------------------------------
+ * Concurrent requests.  richards_batch_submit starts, for each context, a
+ * host worker thread that runs nsteps steps on the context's stream; the
+ * contexts' work overlaps on the device when they have distinct streams.
+ * While a context runs, every other call on it returns RICH_EBUSY.
+ * --------------------------------------------------------------------- */
+
+/* EINVAL on a NULL or repeated context or bad arguments; EBUSY if one is
+   already running (nothing is started then). */
+richards_status richards_batch_submit(richards_ctx *const *ctxs, int n, double dt, int nsteps, int scheme);
+
+/* done[k] = 1 when context k has finished (0 while running); for finished
+   contexts status[k] and info[k] (both nullable) receive the outcome of the
+   run and its statistics: cycles, outer_iters and cell_updates summed over
+   the steps, resid0 of the first step, resid and scheme_used of the last. */
+richards_status richards_batch_poll(richards_ctx *const *ctxs, int n, int *done, richards_status *status,
+                                    richards_step_info *info);
+
+/* Device memory a context for this grid and these options allocates
+   (upper estimate, bytes; no device is touched): soil_fields != 0 when the
+   soil has per-cell fields, sink != 0 with a sink.  -1 on invalid input. */
+long long richards_device_bytes(const richards_grid *grid, const richards_opts *opts, int soil_fields, int sink);
 
 /* ---------------------------------------------------------------------
  * Inspection and kernel-level entry points.  They run single stages of the

@@ -3,11 +3,13 @@
 // kernels in k64.cu / k32.cu; the host only sequences launches and reads the
 // 8-byte residual norms that drive the stop tests.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -82,6 +84,26 @@ struct richards_ctx {
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
   std::map<std::pair<std::string, int>, ProfAgg> prof_agg;
+  // richards_batch_submit: a worker thread runs the steps; the context is
+  // busy (every other call returns EBUSY) until richards_batch_poll sees it done
+  std::atomic<int> busy{0};
+  std::thread worker;
+  int device = 0;
+  // CUDA graphs of the FP32 inner cycle, one per scheme (1: BDF1, 2: BDF2)
+  struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    double a = 0.0;
+    bool with_prof = false;
+    long long updates = 0;
+    std::vector<ProfRec> prof;
+  };
+  GraphRec graphs[3];
+  bool graphs_ok = true, capturing = false;
+  std::string graph_err;
+  GraphRec* harvest = nullptr;
+  std::vector<ProfRec> capture_recs;
+  richards_status batch_status = RICH_OK;
+  richards_step_info batch_info{};
 };
 
 namespace {
@@ -153,20 +175,54 @@ struct Prof {
   int level;
   long long cells;
   cudaEvent_t a = nullptr;
+  // while a graph is captured the events become external event-record nodes,
+  // so that their times can be read after each replay
+  static void record(richards_ctx* c, cudaEvent_t e) {
+    if (c->capturing) cudaEventRecordWithFlags(e, c->s, cudaEventRecordExternal);
+    else cudaEventRecord(e, c->s);
+  }
   Prof(richards_ctx* c_, const char* n, int l, long long cells_) : c(c_), name(n), level(l), cells(cells_) {
     if (c->prof) {
       a = prof_event(c);
-      cudaEventRecord(a, c->s);
+      record(c, a);
     }
   }
   ~Prof() {
     if (!a) return;
     cudaEvent_t b = prof_event(c);
-    cudaEventRecord(b, c->s);
+    record(c, b);
+    if (c->capturing) {                 // event nodes of a graph being captured
+      c->capture_recs.push_back({name, level, cells, a, b});
+      return;
+    }
     c->prof_pending.push_back({name, level, cells, a, b});
     if (c->prof_pending.size() > 8192) prof_flush(c);
   }
 };
+
+// times of the event nodes of the graph replayed last (after a stream sync)
+void graph_harvest(richards_ctx* c) {
+  if (!c->harvest) return;
+  for (auto& r : c->harvest->prof) {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto& g = c->prof_agg[{std::string(r.name), r.level}];
+    g.launches += 1;
+    g.ms += ms;
+    g.cells += r.cells;
+  }
+  c->harvest = nullptr;
+}
+
+void graphs_reset(richards_ctx* c) {
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    for (auto& r : g.prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    g.prof.clear();
+  }
+  c->harvest = nullptr;
+}
 
 bool finite_all(const double* a, long long n) {
   for (long long i = 0; i < n; ++i)
@@ -356,7 +412,9 @@ richards_status upload_views(richards_ctx* c) {
 
 richards_status check_launch(richards_ctx* c) {
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(c, RICH_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    return fail(c, RICH_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e) +
+                                   (c->graph_err.empty() ? "" : " (graphs: " + c->graph_err + ")"));
   return RICH_OK;
 }
 
@@ -364,6 +422,7 @@ richards_status check_launch(richards_ctx* c) {
 richards_status read_norm(richards_ctx* c, int k, double* out, bool fp32) {
   CK(cudaMemcpyAsync(c->hscratch + k, c->scratch + k, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
+  graph_harvest(c);
   const unsigned long long b = c->hscratch[k];
   if (fp32) {
     unsigned u = (unsigned)b;
@@ -466,6 +525,62 @@ void vcycle32(richards_ctx* c, int l) {
   }
   nvtxRangePop();
   c->updates_host += (long long)c->opts.nu2 * F.ncell;
+}
+
+// One FP32 inner cycle, replayed from a CUDA graph when the options ask for it
+// and the stream can be captured; the graph is captured again when a, the
+// profiling state or any set-up call changed what its launches bake in.
+void run_cycle32(richards_ctx* c) {
+  if (c->opts.graphs && c->graphs_ok && c->s != nullptr) {
+    richards_ctx::GraphRec& G = c->graphs[c->scheme_used];
+    if (!G.exec || G.a != c->a || G.with_prof != c->prof) {
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+      for (auto& r : G.prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+      G.prof.clear();
+      const long long before = c->updates_host;
+      c->capture_recs.clear();
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal);
+      const char* where = "cudaStreamBeginCapture";
+      if (e == cudaSuccess) {
+        c->capturing = true;
+        vcycle32(c, 0);
+        c->capturing = false;
+        const cudaError_t el = cudaGetLastError();
+        e = cudaStreamEndCapture(c->s, &g);
+        where = "cudaStreamEndCapture";
+        if (e == cudaSuccess && el != cudaSuccess) { e = el; where = "launch during capture"; }
+      }
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&G.exec, g, 0);
+        where = "cudaGraphInstantiate";
+      }
+      if (g) cudaGraphDestroy(g);
+      const bool ok = e == cudaSuccess;
+      if (!ok) c->graph_err = std::string(where) + ": " + cudaGetErrorString(e);
+      G.updates = c->updates_host - before;
+      c->updates_host = before;
+      G.prof.swap(c->capture_recs);
+      if (!ok) {                        // no graphs on this context: launch directly
+        cudaGetLastError();
+        for (auto& r : G.prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        G.prof.clear();
+        G.exec = nullptr;
+        c->graphs_ok = false;
+        vcycle32(c, 0);
+        return;
+      }
+      G.a = c->a;
+      G.with_prof = c->prof;
+    }
+    const cudaError_t e = cudaGraphLaunch(G.exec, c->s);
+    if (e != cudaSuccess) c->graph_err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
+    c->updates_host += G.updates;
+    if (c->prof && !G.prof.empty()) c->harvest = &G;
+    return;
+  }
+  vcycle32(c, 0);
 }
 
 // coarse copies of the lagged conductivity and boundary conductances
@@ -576,7 +691,11 @@ richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
 
 // Mixed precision: FP64 defect r = g - N(psi); FP32 FAS V-cycles on the
 // correction equation N(psi + delta) - N(psi) = r; psi += delta; repeat until
-// the FP64 stop test holds.
+// the FP64 stop test holds.  Defects that only steer the next correction take
+// theta(psi) in float-float arithmetic (~1e-13 relative, a small fraction of
+// the FP64 cost); a defect that would stop the iteration, or end it at the
+// outer limit, is re-taken in FP64, so every accept/reject decision and the
+// theta(psi^{n+1}) kept for the next step are FP64.
 richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   const double teff = 1.0 / c->a;
   const int model = c->soil.model;
@@ -586,17 +705,23 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   double r = 0.0, r0 = 0.0;
   int outer = 0, inner = 0;
   richards_status st = RICH_OK;
-  for (;;) {
+  // mode 0: theta from the cache of theta(psi^n); 1: float-float; 2: FP64
+  auto defect = [&](int mode, double* out) -> richards_status {
     CK(cudaMemsetAsync(c->scratch, 0, sizeof(unsigned long long), c->s));
     {
-      Prof pr(c, "outer_residual", 0, F.ncell);
-      rich::outer_residual(view64(c, 0), P64, model, F.gf, F.psi0f, F.uf, c->scratch, outer == 0 ? c->th_n : nullptr,
-                           outer == 0 ? nullptr : c->th_cur, c->s);
+      Prof pr(c, mode == 1 ? "outer_residual_dd" : "outer_residual", 0, F.ncell);
+      rich::outer_residual(view64(c, 0), P64, model, F.gf, F.psi0f, F.uf, c->scratch,
+                           mode == 0 ? c->th_n : nullptr, mode == 2 ? c->th_cur : nullptr, mode == 1, c->s);
     }
     TRY(check_launch(c));
     double nrm;
     TRY(read_norm(c, 0, &nrm, false));
-    r = teff * nrm;
+    *out = teff * nrm;
+    return RICH_OK;
+  };
+  for (;;) {
+    TRY(defect(outer == 0 ? 0 : 1, &r));
+    if (outer > 0 && (!(r > c->opts.tol) || outer >= c->opts.max_outer) && !std::isnan(r)) TRY(defect(2, &r));
     if (outer == 0) r0 = r;
     if (!(r > c->opts.tol) || std::isnan(r)) break;
     if (outer >= c->opts.max_outer) { st = RICH_ENOCONV; break; }
@@ -605,9 +730,9 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
       rich::restrict32(view32(c, l), view32(c, l + 1), xfer32(c, l), c->L[l].psi0f, nullptr, c->L[l + 1].psi0f,
                        nullptr, c->s);
     }
-    const double rin0 = nrm;
+    const double rin0 = r / teff;       // ||g - N(psi)||_inf of this defect
     for (int k = 0; k < c->opts.inner_cycles; ++k) {
-      vcycle32(c, 0);
+      run_cycle32(c);
       ++inner;
       if (c->opts.inner_rtol > 0.0 && k + 1 < c->opts.inner_cycles) {
         CK(cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s));
@@ -669,10 +794,11 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
       !(o.tol > 0.0) || o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
       o.ordering != 1 || (o.precision != 0 && o.precision != 1) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
       o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0 || o.cycle_gamma < 1 || o.cycle_gamma > 3 ||
-      o.gamma_levels < 0)
+      o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1))
     return RICH_EINVAL;
   richards_ctx* c = new richards_ctx();
   c->s = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
   c->grid = *grid;
   c->opts = o;
   // hierarchy: halve every axis with n > 1 while max n > coarsest_max_n
@@ -742,7 +868,9 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
 
 void richards_destroy(richards_ctx* c) {
   if (!c) return;
+  if (c->worker.joinable()) c->worker.join();
   if (c->s) cudaStreamSynchronize(c->s); else cudaDeviceSynchronize();
+  graphs_reset(c);
   for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
@@ -765,6 +893,9 @@ richards_status richards_level_dims(const richards_ctx* c, int level, int n_out[
 
 richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
   if (!c || !s) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  cudaStreamSynchronize(c->s);
+  graphs_reset(c);
   const long long N = c->L[0].ncell;
   const bool ok = s->model >= 0 && s->model <= 2 && std::isfinite(s->Ks) && s->Ks > 0.0 &&
                   std::isfinite(s->theta_s) && std::isfinite(s->theta_r) && s->theta_r >= 0.0 &&
@@ -852,6 +983,9 @@ static richards_status refresh_sink(richards_ctx* c) {
 
 richards_status richards_set_sink(richards_ctx* c, const richards_sink* k) {
   if (!c || !k) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  cudaStreamSynchronize(c->s);
+  graphs_reset(c);
   if (k->enabled) {
     const double v[] = {k->Tp, k->root_depth, k->root_decay, k->h1, k->h2, k->h3, k->h4};
     for (double x : v)
@@ -866,6 +1000,9 @@ richards_status richards_set_sink(richards_ctx* c, const richards_sink* k) {
 
 richards_status richards_set_bc(richards_ctx* c, const richards_bc* b) {
   if (!c || !b) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  cudaStreamSynchronize(c->s);
+  graphs_reset(c);
   const int dim = c->grid.dim;
   const HLevel& F = c->L[0];
   for (int f = 0; f < 2 * dim; ++f) {
@@ -935,6 +1072,7 @@ richards_status richards_set_bc(richards_ctx* c, const richards_bc* b) {
 
 richards_status richards_set_state(richards_ctx* c, const double* psi, const double* psi_prev, double t) {
   if (!c || !psi) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   const long long N = c->L[0].ncell;
   if (!finite_all(psi, N) || (psi_prev && !finite_all(psi_prev, N)) || !std::isfinite(t))
     return fail(c, RICH_EINVAL, "non-finite state");
@@ -950,6 +1088,7 @@ richards_status richards_set_state(richards_ctx* c, const double* psi, const dou
 
 richards_status richards_get_state(richards_ctx* c, double* out, int on_device) {
   if (!c || !out) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   if (!c->have_state) return fail(c, RICH_EINVAL, "state not set");
   CK(cudaMemcpyAsync(out, c->psi_n, sizeof(double) * c->L[0].ncell,
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
@@ -957,30 +1096,149 @@ richards_status richards_get_state(richards_ctx* c, double* out, int on_device) 
   return RICH_OK;
 }
 
+richards_status richards_soil_eval(richards_ctx* c, const double* psi, double* theta, double* K, int arith,
+                                   int on_device) {
+  if (!c || !psi || (arith != 0 && arith != 1)) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  if (!c->soil_set) return fail(c, RICH_EINVAL, "soil not set");
+  const long long n = c->L[0].ncell;
+  const size_t bytes = sizeof(double) * n;
+  const double* dpsi = psi;
+  double *dth = theta, *dK = K, *tmp = nullptr;
+  if (!on_device) {
+    CK(cudaMallocAsync((void**)&tmp, 3 * bytes, c->s));
+    CK(cudaMemcpyAsync(tmp, psi, bytes, cudaMemcpyHostToDevice, c->s));
+    dpsi = tmp;
+    dth = theta ? tmp + n : nullptr;
+    dK = K ? tmp + 2 * n : nullptr;
+  }
+  HLevel& F = c->L[0];
+  rich::soil_eval(n, dpsi, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
+                  c->het_p2 ? F.p2 : nullptr, phys<double>(c), c->soil.model, arith == 1, dth, dK, c->s);
+  richards_status st = check_launch(c);
+  if (!on_device) {
+    if (st == RICH_OK && theta) st = cudaMemcpyAsync(theta, dth, bytes, cudaMemcpyDeviceToHost, c->s) == cudaSuccess
+                                         ? RICH_OK : fail(c, RICH_ECUDA, "cudaMemcpyAsync failed");
+    if (st == RICH_OK && K) st = cudaMemcpyAsync(K, dK, bytes, cudaMemcpyDeviceToHost, c->s) == cudaSuccess
+                                     ? RICH_OK : fail(c, RICH_ECUDA, "cudaMemcpyAsync failed");
+    cudaFreeAsync(tmp, c->s);
+  }
+  CK(cudaStreamSynchronize(c->s));
+  return st;
+}
+
 richards_status richards_prepare(richards_ctx* c, double dt, int scheme, int* scheme_used) {
   if (!c) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   TRY(do_prepare(c, dt, scheme));
   if (scheme_used) *scheme_used = c->scheme_used;
   CK(cudaStreamSynchronize(c->s));
   return RICH_OK;
 }
 
+static richards_status step_impl(richards_ctx* c, double dt, int scheme, richards_step_info* info);
+
 richards_status richards_step(richards_ctx* c, double dt, int scheme, richards_step_info* info) {
   if (!c) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  return step_impl(c, dt, scheme, info);
+}
+
+static richards_status step_impl(richards_ctx* c, double dt, int scheme, richards_step_info* info) {
   c->updates_host = 0;
   CK(cudaMemsetAsync(c->scratch + 16, 0, sizeof(unsigned long long), c->s));
   TRY(do_prepare(c, dt, scheme));
   return c->opts.precision == 1 ? step_mixed(c, info) : step_fp64(c, info);
 }
 
+static richards_status solve_impl(richards_ctx* c, double dt, int nsteps, int scheme, richards_step_info* last) {
+  for (int k = 0; k < nsteps; ++k) TRY(step_impl(c, dt, scheme, last));
+  return RICH_OK;
+}
+
 richards_status richards_solve(richards_ctx* c, double dt, int nsteps, int scheme, richards_step_info* last) {
   if (!c || nsteps < 0) return RICH_EINVAL;
-  for (int k = 0; k < nsteps; ++k) TRY(richards_step(c, dt, scheme, last));
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  return solve_impl(c, dt, nsteps, scheme, last);
+}
+
+richards_status richards_batch_submit(richards_ctx* const* ctxs, int n, double dt, int nsteps, int scheme) {
+  if (!ctxs || n < 0 || nsteps < 0 || !(dt > 0.0) || (scheme != 1 && scheme != 2)) return RICH_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    if (!ctxs[k]) return RICH_EINVAL;
+    if (ctxs[k]->busy.load()) return RICH_EBUSY;
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return RICH_EINVAL;
+  }
+  for (int k = 0; k < n; ++k) {
+    richards_ctx* c = ctxs[k];
+    if (c->worker.joinable()) c->worker.join();
+    c->busy.store(1);
+    c->batch_info = richards_step_info{};
+    c->worker = std::thread([c, dt, nsteps, scheme]() {
+      cudaSetDevice(c->device);
+      richards_step_info acc{}, last{};
+      richards_status st = RICH_OK;
+      for (int k = 0; k < nsteps && st == RICH_OK; ++k) {
+        st = step_impl(c, dt, scheme, &last);
+        acc.cycles += last.cycles;
+        acc.outer_iters += last.outer_iters;
+        acc.cell_updates += last.cell_updates;
+        acc.scheme_used = last.scheme_used;
+        acc.resid = last.resid;
+        if (k == 0) acc.resid0 = last.resid0;
+      }
+      c->batch_info = acc;
+      c->batch_status = st;
+      c->busy.store(0);
+    });
+  }
   return RICH_OK;
+}
+
+richards_status richards_batch_poll(richards_ctx* const* ctxs, int n, int* done, richards_status* status,
+                                    richards_step_info* info) {
+  if (!ctxs || n < 0 || !done) return RICH_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    richards_ctx* c = ctxs[k];
+    if (!c) return RICH_EINVAL;
+    done[k] = c->busy.load() ? 0 : 1;
+    if (done[k]) {
+      if (c->worker.joinable()) c->worker.join();
+      if (status) status[k] = c->batch_status;
+      if (info) info[k] = c->batch_info;
+    }
+  }
+  return RICH_OK;
+}
+
+long long richards_device_bytes(const richards_grid* grid, const richards_opts* opts, int soil_fields, int sink) {
+  if (!grid || !opts || grid->dim < 1 || grid->dim > 3) return -1;
+  long long n[3] = {grid->n[0], grid->n[1], grid->n[2]};
+  for (int a = 0; a < 3; ++a)
+    if (n[a] < 1) return -1;
+  const bool mixed = opts->precision == 1;
+  const long long N = n[0] * n[1] * n[2];
+  long long bytes = 2 * N * 8 + (mixed ? 3 * N * 8 : 0) + (soil_fields > 0 ? N * 8 : 0);   // psi^n, psi^{n-1}, caches, Ks
+  int levels = 0;
+  for (;;) {
+    const long long cells = n[0] * n[1] * n[2];
+    long long faces = 0;
+    for (int a = 0; a < grid->dim; ++a) faces += 2 * (cells / n[a]);
+    bytes += cells * 8 * (5 + (soil_fields > 0 ? 2 : 0) + (sink ? 1 : 0)) + faces * 8;
+    if (mixed) bytes += cells * 4 * (6 + (soil_fields > 0 ? 2 : 0) + (sink ? 1 : 0)) + faces * 4;
+    for (int a = 0; a < 3; ++a) bytes += (n[a] * 5 + 13 * ((n[a] + 1) / 2)) * 8;   // transfer tables (bound)
+    ++levels;
+    const long long mx = std::max(n[0], std::max(n[1], n[2]));
+    if (mx <= opts->coarsest_max_n || (opts->max_levels > 0 && levels >= opts->max_levels) || levels >= MAXLEV) break;
+    for (int a = 0; a < 3; ++a) n[a] = n[a] > 1 ? (n[a] + 1) / 2 : 1;
+  }
+  return bytes;
 }
 
 richards_status richards_get_level(richards_ctx* c, int level, int which, double* out, long long n) {
   if (!c || !out || level < 0 || level >= c->nlev) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   HLevel& H = c->L[level];
   const double* src = nullptr;
   long long cnt = H.ncell;
@@ -1005,6 +1263,7 @@ richards_status richards_get_level(richards_ctx* c, int level, int which, double
 
 richards_status richards_set_level(richards_ctx* c, int level, int which, const double* in, long long n) {
   if (!c || !in || level < 0 || level >= c->nlev || (which != 0 && which != 1)) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   HLevel& H = c->L[level];
   if (n != H.ncell) return fail(c, RICH_EINVAL, "size mismatch");
   CK(cudaMemcpyAsync(which == 0 ? H.u : H.g, in, sizeof(double) * n, cudaMemcpyHostToDevice, c->s));
@@ -1014,6 +1273,7 @@ richards_status richards_set_level(richards_ctx* c, int level, int which, const 
 
 richards_status richards_sweep(richards_ctx* c, int level, int color) {
   if (!c || level < 0 || level >= c->nlev || color < -1 || color > 1) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   if (!c->prepared) return fail(c, RICH_EINVAL, "call richards_prepare first");
   const Level<double> L = view64(c, level);
   const Phys<double> P = phys<double>(c);
@@ -1026,6 +1286,7 @@ richards_status richards_sweep(richards_ctx* c, int level, int color) {
 
 richards_status richards_residual(richards_ctx* c, int level, double* norm) {
   if (!c || level < 0 || level >= c->nlev) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   if (!c->prepared) return fail(c, RICH_EINVAL, "call richards_prepare first");
   double nr;
   TRY(norm64(c, level, &nr));
@@ -1035,6 +1296,7 @@ richards_status richards_residual(richards_ctx* c, int level, double* norm) {
 
 richards_status richards_restrict_tau(richards_ctx* c, int level) {
   if (!c || level < 0 || level + 1 >= c->nlev) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   if (!c->prepared) return fail(c, RICH_EINVAL, "call richards_prepare first");
   const Level<double> F = view64(c, level), C = view64(c, level + 1);
   const Phys<double> P = phys<double>(c);
@@ -1048,6 +1310,7 @@ richards_status richards_restrict_tau(richards_ctx* c, int level) {
 
 richards_status richards_prolong(richards_ctx* c, int level) {
   if (!c || level < 0 || level + 1 >= c->nlev) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   rich::prolong64(view64(c, level), view64(c, level + 1), xfer64(c, level), c->s);
   TRY(check_launch(c));
   CK(cudaStreamSynchronize(c->s));
@@ -1056,6 +1319,7 @@ richards_status richards_prolong(richards_ctx* c, int level) {
 
 richards_status richards_vcycle(richards_ctx* c) {
   if (!c) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   if (!c->prepared) return fail(c, RICH_EINVAL, "call richards_prepare first");
   vcycle64(c, 0);
   TRY(check_launch(c));
@@ -1065,10 +1329,12 @@ richards_status richards_vcycle(richards_ctx* c) {
 
 richards_status richards_profile(richards_ctx* c, int enable) {
   if (!c) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   if (enable) {
     prof_flush(c);
     c->prof_agg.clear();
   }
+  c->harvest = nullptr;
   c->prof = enable != 0;
   return RICH_OK;
 }
@@ -1076,6 +1342,8 @@ richards_status richards_profile(richards_ctx* c, int enable) {
 int richards_profile_read(richards_ctx* c, richards_kernel_stat* out, int max) {
   if (!c || (!out && max > 0)) return -1;
   prof_flush(c);
+  cudaStreamSynchronize(c->s);
+  graph_harvest(c);
   int k = 0;
   for (const auto& kv : c->prof_agg) {
     if (k >= max) break;

@@ -1,0 +1,219 @@
+// Float-float ("double-float") evaluation of the constitutive laws.
+//
+// GB300's FP64 pipe issues about 1/64 of the FP32 rate, so the FP64 special
+// functions of theta(psi) and K(psi) dominate every FP64 kernel.  Here a value
+// is an unevaluated sum hi + lo of two floats (~48 significant bits), built
+// from the error-free transformations two-sum and two-product (Dekker 1971,
+// Knuth): the results agree with FP64 evaluation to ~1e-14 relative, far
+// inside the 1e-8 stop test and the 1e-12 stage tolerance, at a small
+// fraction of the FP64 cost.
+//
+//   exp:  Cody-Waite reduction x = k ln2 + r with ln2 split in three floats
+//         (k c1 exact), r scaled by 1/16, expm1 by its Taylor series to degree
+//         7, then four doublings y <- y (y + 2) and the exact scaling by 2^k;
+//   log:  one Newton step on exp from the single-precision logf:
+//         log x = y0 + log1p(x e^{-y0} - 1), the log1p of a ~1e-7 argument
+//         taken to second order;
+//   log1p: the same Newton step on expm1 from log1pf.
+#pragma once
+
+#include "device.cuh"
+
+namespace rich {
+
+struct dd {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dd mk(float h, float l = 0.0f) {
+  dd r;
+  r.hi = h;
+  r.lo = l;
+  return r;
+}
+
+// s + e = a + b exactly
+__device__ __forceinline__ dd two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return mk(s, e);
+}
+
+// s + e = a + b exactly, for |a| >= |b|
+__device__ __forceinline__ dd quick_two_sum(float a, float b) {
+  const float s = a + b;
+  return mk(s, b - (s - a));
+}
+
+// p + e = a b exactly
+__device__ __forceinline__ dd two_prod(float a, float b) {
+  const float p = a * b;
+  return mk(p, fmaf(a, b, -p));
+}
+
+__device__ __forceinline__ dd dd_add(dd x, dd y) {
+  dd s = two_sum(x.hi, y.hi);
+  const dd t = two_sum(x.lo, y.lo);
+  s = quick_two_sum(s.hi, s.lo + t.hi);
+  return quick_two_sum(s.hi, s.lo + t.lo);
+}
+
+__device__ __forceinline__ dd dd_neg(dd x) { return mk(-x.hi, -x.lo); }
+
+__device__ __forceinline__ dd dd_mul(dd x, dd y) {
+  const dd p = two_prod(x.hi, y.hi);
+  return quick_two_sum(p.hi, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
+}
+
+__device__ __forceinline__ dd dd_mul_f(dd x, float f) {
+  const dd p = two_prod(x.hi, f);
+  return quick_two_sum(p.hi, fmaf(x.lo, f, p.lo));
+}
+
+__device__ __forceinline__ dd dd_from(double x) {
+  const float h = __double2float_rn(x);
+  return mk(h, __double2float_rn(x - (double)h));
+}
+
+__device__ __forceinline__ double dd_to(dd x) { return (double)x.hi + (double)x.lo; }
+
+// ln 2 = C1 + C2 + C3 (C1 with 12 trailing zero bits: k C1 exact for |k| < 4096)
+#define RICH_LN2_C1 0x1.62e000p-1f
+#define RICH_LN2_C2 0x1.0bfbe8p-15f
+#define RICH_LN2_C3 0x1.cf79acp-40f
+#define RICH_INV_LN2 0x1.715476p+0f
+#define RICH_INV6_HI 0x1.555556p-3f
+#define RICH_INV6_LO -0x1.555556p-28f
+#define RICH_INV24_HI 0x1.555556p-5f
+#define RICH_INV24_LO -0x1.555556p-30f
+
+// expm1(r) for |r| <= ln2/32: Taylor series, degree 7
+__device__ __forceinline__ dd dd_expm1_reduced(dd r) {
+  const float rf = r.hi;
+  const float T = fmaf(rf, fmaf(rf, 1.0f / 5040.0f, 1.0f / 720.0f), 1.0f / 120.0f);   // r^5 coefficient tail
+  dd c = dd_add(mk(RICH_INV24_HI, RICH_INV24_LO), dd_mul_f(r, T));
+  c = dd_add(mk(RICH_INV6_HI, RICH_INV6_LO), dd_mul(r, c));
+  c = dd_add(mk(0.5f), dd_mul(r, c));
+  c = dd_add(mk(1.0f), dd_mul(r, c));
+  return dd_mul(r, c);
+}
+
+// expm1 of x / 2^k-reduced argument, doubled back four times
+__device__ __forceinline__ dd dd_expm1_core(dd r) {
+  dd y = dd_expm1_reduced(mk(r.hi * 0.0625f, r.lo * 0.0625f));
+  for (int k = 0; k < 4; ++k) y = dd_mul(y, dd_add(y, mk(2.0f)));    // e^{2s} - 1 = y (y + 2)
+  return y;
+}
+
+// e^x for |x| <= DD_EXP_MAX (the scale 2^k and the low word stay normal floats)
+__device__ __forceinline__ dd dd_exp(dd x) {
+  const float k = rintf(x.hi * RICH_INV_LN2);
+  dd r = dd_add(x, mk(-k * RICH_LN2_C1));
+  r = dd_add(r, dd_neg(two_prod(k, RICH_LN2_C2)));
+  r = dd_add(r, mk(-k * RICH_LN2_C3));
+  const dd e = dd_add(mk(1.0f), dd_expm1_core(r));
+  const float s = __int_as_float((127 + (int)k) << 23);   // 2^k; |k| <= 100 for the arguments used here
+  return mk(e.hi * s, e.lo * s);
+}
+
+// e^x - 1, accurate relative to itself also for small |x|
+__device__ __forceinline__ dd dd_expm1(dd x) {
+  if (fabsf(x.hi) < 0.34657359f) return dd_expm1_core(x);
+  return dd_add(dd_exp(x), mk(-1.0f));
+}
+
+// log x for x > 0
+__device__ __forceinline__ dd dd_log(dd x) {
+  const float y0 = logf(x.hi);
+  const dd t = dd_mul(x, dd_exp(mk(-y0)));
+  const dd d = dd_add(t, mk(-1.0f));                    // |d| ~ 1e-7
+  const dd corr = dd_add(d, mk(-0.5f * d.hi * d.hi));
+  return dd_add(mk(y0), corr);
+}
+
+// log(1 + t) for t > -1, accurate relative to itself also for small |t|:
+// one Newton step on expm1 from the single-precision log1pf,
+//   log1p t = y0 + log1p((t - expm1 y0) / (1 + expm1 y0)),
+// the correction d ~ 1e-7 relative taken to second order (its float factor
+// 1/(1 + expm1 y0) costs ~1e-7 of d, i.e. ~1e-14 of the result).
+__device__ __forceinline__ dd dd_log1p(dd t) {
+  const float y0 = log1pf(t.hi);
+  const dd E = dd_expm1(mk(y0));
+  const dd d = dd_mul_f(dd_add(t, dd_neg(E)), 1.0f / (1.0f + E.hi));
+  return dd_add(mk(y0), dd_add(d, mk(-0.5f * d.hi * d.hi)));
+}
+
+// 1 / t (one Newton step from the float reciprocal)
+__device__ __forceinline__ dd dd_recip(dd t) {
+  const float r0 = 1.0f / t.hi;
+  const dd e = dd_add(mk(1.0f), dd_neg(dd_mul_f(t, r0)));
+  return dd_add(mk(r0), dd_mul_f(e, r0));
+}
+
+// ---------------------------------------------------------------------------
+// Constitutive laws (Table 1) in float-float; same branches as law_d/cond_d.
+// Arguments outside the float range the routines are written for (a log of
+// a value outside [1e-30, 1e30], an exponent beyond +-DD_EXP_MAX) take the
+// FP64 routine instead; those are the far dry or far wet tails, where the
+// results are at or below 1e-26 of theta_s - theta_r or of Ks.
+// ---------------------------------------------------------------------------
+#define DD_EXP_MAX 60.0f
+
+__device__ __forceinline__ bool dd_log_ok(double x) { return x > 1e-30 && x < 1e30; }
+__device__ __forceinline__ bool dd_exp_ok(dd x) { return fabsf(x.hi) <= DD_EXP_MAX; }
+
+template <int MODEL>
+__device__ __forceinline__ double theta_dd(double psi, double p1, double p2, const Phys<double>& P) {
+  if (!(psi < 0.0)) return P.ts;
+  const double h = -psi, ds = P.ts - P.tr;
+  if (MODEL == HAVERKAMP) {
+    if (dd_log_ok(h)) {
+      const dd e = dd_mul(dd_log(dd_from(h)), dd_from(p2));
+      if (dd_exp_ok(e)) return P.tr + p1 * ds / (p1 + dd_to(dd_exp(e)));
+    }
+  } else if (MODEL == GARDNER) {
+    const dd e = dd_from(p1 * psi);
+    if (dd_exp_ok(e)) return P.tr + ds * dd_to(dd_exp(e));
+  } else if (dd_log_ok(p1 * h)) {
+    const double m = 1.0 - 1.0 / p2;
+    const dd lt = dd_mul(dd_log(dd_from(p1 * h)), dd_from(p2));
+    if (dd_exp_ok(lt)) {
+      const dd e = dd_mul(dd_log1p(dd_exp(lt)), dd_from(-m));
+      if (dd_exp_ok(e)) return P.tr + ds * dd_to(dd_exp(e));
+    }
+  }
+  return theta_only_d<MODEL>(psi, p1, p2, P);
+}
+
+template <int MODEL>
+__device__ __forceinline__ double cond_dd(double psi, double p1, double p2, double Ks, const Phys<double>& P) {
+  if (!(psi < 0.0)) return Ks;
+  const double h = -psi;
+  if (MODEL == HAVERKAMP) {
+    if (dd_log_ok(h)) {
+      const dd e = dd_mul(dd_log(dd_from(h)), dd_from(P.p4));
+      if (dd_exp_ok(e)) return Ks * P.p3 / (P.p3 + dd_to(dd_exp(e)));
+    }
+  } else if (MODEL == GARDNER) {
+    const dd e = dd_from(p1 * psi);
+    if (dd_exp_ok(e)) return Ks * dd_to(dd_exp(e));
+  } else if (dd_log_ok(p1 * h)) {
+    const double m = 1.0 - 1.0 / p2;
+    const dd lt = dd_mul(dd_log(dd_from(p1 * h)), dd_from(p2));   // log t
+    if (dd_exp_ok(lt)) {
+      const dd t = dd_exp(lt);
+      const dd L1 = dd_log1p(t);                                  // log(1 + t)
+      const dd eK = dd_mul(L1, dd_from(-P.p3 * m));
+      if (dd_exp_ok(eK)) {
+        // log(t / (1 + t)) without cancellation
+        const dd lr = t.hi > 1.0f ? dd_neg(dd_log1p(dd_recip(t))) : dd_add(lt, dd_neg(L1));
+        const double inner = -dd_to(dd_expm1(dd_mul(lr, dd_from(m))));
+        return Ks * dd_to(dd_exp(eK)) * inner * inner;
+      }
+    }
+  }
+  return cond_d<MODEL>(psi, p1, p2, Ks, P);
+}
+
+}  // namespace rich

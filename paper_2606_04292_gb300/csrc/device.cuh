@@ -235,23 +235,53 @@ __device__ __forceinline__ float fast_expm1(float x) {
 // x^y for x > 0 through the hardware approximations
 __device__ __forceinline__ float fast_pow(float x, float y) { return __expf(y * __logf(x)); }
 
-// Same increments as dlaw_f, built from the fast pieces above.
+// Same increments as dlaw_f, built from the fast pieces above, split into
+// the part that depends on psi0 only (once per point update) and the part
+// that depends on the correction x (once per Newton step).
+struct DBase {
+  float psi0, inv_psi0;
+  bool wet0;
+  float a0, b0, c0;      // VG: t0, log1p(t0), Se0; Haverkamp: u0; Gardner: e0
+};
+
 template <int MODEL>
-__device__ __forceinline__ void dlaw_fast(float psi0, float x, float p1, float p2, const Phys<float>& P,
-                                          float& Dth, float& dth) {
+__device__ __forceinline__ DBase dbase(float psi0, float p1, float p2) {
+  DBase B;
+  B.psi0 = psi0;
+  B.wet0 = !(psi0 < 0.0f);
+  B.inv_psi0 = B.wet0 ? 0.0f : __fdividef(1.0f, psi0);
+  B.a0 = B.b0 = B.c0 = 0.0f;
+  if (!B.wet0) {
+    if (MODEL == GARDNER) {
+      B.a0 = __expf(p1 * psi0);
+    } else if (MODEL == HAVERKAMP) {
+      B.a0 = fast_pow(-psi0, p2);
+    } else {
+      const float m = 1.0f - __fdividef(1.0f, p2);
+      B.a0 = fast_pow(p1 * -psi0, p2);
+      B.b0 = fast_log1p(B.a0);
+      B.c0 = __expf(-m * B.b0);
+    }
+  }
+  return B;
+}
+
+template <int MODEL>
+__device__ __forceinline__ void dincr(const DBase& B, float x, float p1, float p2, const Phys<float>& P,
+                                      float& Dth, float& dth) {
   const float ds = P.ts - P.tr;
-  const float psi1 = psi0 + x;
-  const bool wet0 = !(psi0 < 0.0f), wet1 = !(psi1 < 0.0f);
+  const float psi1 = B.psi0 + x;
+  const bool wet1 = !(psi1 < 0.0f);
   if (MODEL == GARDNER) {
     const float al = p1;
-    if (!wet0) {
-      const float e0 = __expf(al * psi0);
+    if (!B.wet0) {
+      const float e0 = B.a0;
       if (!wet1) {
         const float em = fast_expm1(al * x);
         Dth = ds * e0 * em;
         dth = al * ds * e0 * (1.0f + em);
       } else {
-        Dth = -ds * fast_expm1(al * psi0);
+        Dth = -ds * fast_expm1(al * B.psi0);
         dth = 0.0f;
       }
     } else if (!wet1) {
@@ -262,11 +292,10 @@ __device__ __forceinline__ void dlaw_fast(float psi0, float x, float p1, float p
     }
   } else if (MODEL == HAVERKAMP) {
     const float al = p1, be = p2;
-    if (!wet0) {
-      const float h0 = -psi0;
-      const float u0 = fast_pow(h0, be);
+    if (!B.wet0) {
+      const float u0 = B.a0;
       if (!wet1) {
-        const float du = u0 * fast_expm1(be * fast_log1p(__fdividef(x, psi0)));
+        const float du = u0 * fast_expm1(be * fast_log1p(x * B.inv_psi0));
         const float u1 = u0 + du, h1 = -psi1;
         const float den1 = al + u1;
         Dth = __fdividef(-al * ds * du, (al + u0) * den1);
@@ -286,13 +315,10 @@ __device__ __forceinline__ void dlaw_fast(float psi0, float x, float p1, float p
     }
   } else {
     const float al = p1, n = p2, m = 1.0f - __fdividef(1.0f, n);
-    if (!wet0) {
-      const float h0 = -psi0;
-      const float t0 = fast_pow(al * h0, n);
-      const float L0 = fast_log1p(t0);
-      const float Se0 = __expf(-m * L0);
+    if (!B.wet0) {
+      const float t0 = B.a0, L0 = B.b0, Se0 = B.c0;
       if (!wet1) {
-        const float dt = t0 * fast_expm1(n * fast_log1p(__fdividef(x, psi0)));
+        const float dt = t0 * fast_expm1(n * fast_log1p(x * B.inv_psi0));
         const float t1 = t0 + dt;
         const float dSe = Se0 * fast_expm1(-m * fast_log1p(__fdividef(dt, 1.0f + t0)));
         const float Se1 = Se0 + dSe;
@@ -312,6 +338,12 @@ __device__ __forceinline__ void dlaw_fast(float psi0, float x, float p1, float p
       Dth = 0.0f; dth = 0.0f;
     }
   }
+}
+
+template <int MODEL>
+__device__ __forceinline__ void dlaw_fast(float psi0, float x, float p1, float p2, const Phys<float>& P,
+                                          float& Dth, float& dth) {
+  dincr<MODEL>(dbase<MODEL>(psi0, p1, p2), x, p1, p2, P, Dth, dth);
 }
 
 // ---------------------------------------------------------------------------
@@ -434,9 +466,30 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
   }
   T x = x0 < lo ? lo : (x0 > hi ? hi : x0);
   const int maxit = P.newton_k > 0 ? P.newton_k : 200;
+  DBase B;
+  T sa0 = T(0), sda0 = T(0);
+  int sk0 = 0;
+  if constexpr (FORM == FORM_DELTA) {
+    B = dbase<MODEL>(psi0, p1, p2);
+    if (P.sink && smax > T(0)) sk0 = feddes(psi0, P, sa0, sda0);
+  }
   for (int it = 0; it < maxit; ++it) {
     T val, der;
-    storage<T, FORM, MODEL>(x, psi0, p1, p2, smax, P, val, der);
+    if constexpr (FORM == FORM_DELTA) {
+      float Dth, dth;
+      dincr<MODEL>(B, x, p1, p2, P, Dth, dth);
+      T DS = T(0), dS = T(0);
+      if (P.sink && smax > T(0)) {
+        T a1, da1;
+        const int k1 = feddes(psi0 + x, P, a1, da1);
+        DS = (k1 == sk0) ? smax * da1 * x : smax * (a1 - sa0);
+        dS = smax * da1;
+      }
+      val = P.a * Dth + DS;
+      der = P.a * dth + dS;
+    } else {
+      storage<T, FORM, MODEL>(x, psi0, p1, p2, smax, P, val, der);
+    }
     const T F = val + cc * x - f;
     const T dF = der + cc;
     if (F == T(0)) break;

@@ -1,4 +1,5 @@
 // FP64 instantiations and the per-step preparation kernels.
+#include "ddmath.cuh"
 #include "kernels.cuh"
 
 namespace rich {
@@ -171,7 +172,9 @@ __global__ void __launch_bounds__(256) k_to_float(const double* src, float* dst,
 // right side r, its frozen state psi0 and a zero initial correction.
 // th_in: theta(u) known already (the iterate is psi^n); otherwise theta(u) is
 // evaluated and kept in th_out for the next step's history.
-template <int MODEL>
+// theta(u) from th_in when given; else in FP64 (kept in th_out), or, with DD,
+// in float-float arithmetic (accurate to ~1e-13, nothing kept).
+template <int MODEL, bool DD>
 __global__ void __launch_bounds__(256) k_outer_residual(Level<double> L, Phys<double> P, float* r32, float* psi0f,
                                                         float* delta, unsigned long long* norm,
                                                         const double* __restrict__ th_in, double* th_out) {
@@ -187,6 +190,8 @@ __global__ void __launch_bounds__(256) k_outer_residual(Level<double> L, Phys<do
     double th;
     if (th_in) {
       th = th_in[i];
+    } else if (DD) {
+      th = theta_dd<MODEL>(ui, L.p1 ? L.p1[i] : P.p1, L.p2 ? L.p2[i] : P.p2, P);
     } else {
       th = theta_only_d<MODEL>(ui, L.p1 ? L.p1[i] : P.p1, L.p2 ? L.p2[i] : P.p2, P);
       th_out[i] = th;
@@ -256,12 +261,55 @@ void to_float(const double* src, float* dst, long long n, cudaStream_t s) {
   k_to_float<<<grid_for(n), 256, 0, s>>>(src, dst, n);
 }
 
-void outer_residual(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
-                    float* delta, unsigned long long* norm, const double* th_in, double* th_out, cudaStream_t s) {
+template <bool DD>
+static void outer_residual_t(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
+                             float* delta, unsigned long long* norm, const double* th_in, double* th_out,
+                             cudaStream_t s) {
   const int b = grid_for(L.ncell);
-  if (model == HAVERKAMP) k_outer_residual<HAVERKAMP><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
-  else if (model == GARDNER) k_outer_residual<GARDNER><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
-  else k_outer_residual<VANGENUCHTEN><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
+  if (model == HAVERKAMP)
+    k_outer_residual<HAVERKAMP, DD><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
+  else if (model == GARDNER)
+    k_outer_residual<GARDNER, DD><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
+  else
+    k_outer_residual<VANGENUCHTEN, DD><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
+}
+
+void outer_residual(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
+                    float* delta, unsigned long long* norm, const double* th_in, double* th_out, bool dd,
+                    cudaStream_t s) {
+  if (dd) outer_residual_t<true>(L, P, model, r32, psi0f, delta, norm, th_in, th_out, s);
+  else outer_residual_t<false>(L, P, model, r32, psi0f, delta, norm, th_in, th_out, s);
+}
+
+template <int MODEL, bool DD>
+__global__ void __launch_bounds__(256) k_soil_eval(long long n, const double* __restrict__ psi,
+                                                   const double* __restrict__ Ks, double Ks_s,
+                                                   const double* __restrict__ p1f, const double* __restrict__ p2f,
+                                                   Phys<double> P, double* theta, double* K) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double p1 = p1f ? p1f[i] : P.p1, p2 = p2f ? p2f[i] : P.p2, x = psi[i];
+    if (theta) theta[i] = DD ? theta_dd<MODEL>(x, p1, p2, P) : theta_only_d<MODEL>(x, p1, p2, P);
+    if (K) {
+      const double ks = Ks ? Ks[i] : Ks_s;
+      K[i] = DD ? cond_dd<MODEL>(x, p1, p2, ks, P) : cond_d<MODEL>(x, p1, p2, ks, P);
+    }
+  }
+}
+
+template <bool DD>
+static void soil_eval_t(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1,
+                        const double* p2, const Phys<double>& P, int model, double* theta, double* K,
+                        cudaStream_t s) {
+  const int b = grid_for(n);
+  if (model == HAVERKAMP) k_soil_eval<HAVERKAMP, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, theta, K);
+  else if (model == GARDNER) k_soil_eval<GARDNER, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, theta, K);
+  else k_soil_eval<VANGENUCHTEN, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, theta, K);
+}
+
+void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1, const double* p2,
+               const Phys<double>& P, int model, bool dd, double* theta, double* K, cudaStream_t s) {
+  if (dd) soil_eval_t<true>(n, psi, Ks, Ks_s, p1, p2, P, model, theta, K, s);
+  else soil_eval_t<false>(n, psi, Ks, Ks_s, p1, p2, P, model, theta, K, s);
 }
 
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s) {

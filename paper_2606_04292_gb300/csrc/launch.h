@@ -60,9 +60,15 @@ void restrict_face64(const Geom& F, const Geom& C, const Xfer<double>& X, int ax
 void sink_coef(const Geom& G, double Tp, double depth, double decay, double* smax, cudaStream_t s);
 void to_float(const double* src, float* dst, long long n, cudaStream_t s);
 
-// mixed mode: r = g - N(u) in FP64 -> r32, psi0 = (float)u, delta = 0; ||r||_inf
+// mixed mode: r = g - N(u) in FP64 -> r32, psi0 = (float)u, delta = 0; ||r||_inf.
+// theta(u) from th_in if given, else FP64 (written to th_out) or, with dd,
+// float-float (not written).
 void outer_residual(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
-                    float* delta, unsigned long long* norm, const double* th_in, double* th_out, cudaStream_t s);
+                    float* delta, unsigned long long* norm, const double* th_in, double* th_out, bool dd,
+                    cudaStream_t s);
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);
+// theta(psi) and K(psi) per cell (FP64 or float-float); outputs nullable
+void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1, const double* p2,
+               const Phys<double>& P, int model, bool dd, double* theta, double* K, cudaStream_t s);
 
 }  // namespace rich

@@ -54,7 +54,8 @@ class richards_opts(C.Structure):
                 ("kappa", C.c_double), ("xi", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("ordering", C.c_int), ("newton_iters", C.c_int), ("precision", C.c_int),
                 ("inner_cycles", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int),
-                ("tail_cells", C.c_int), ("cycle_gamma", C.c_int), ("gamma_levels", C.c_int)]
+                ("tail_cells", C.c_int), ("cycle_gamma", C.c_int), ("gamma_levels", C.c_int),
+                ("graphs", C.c_int)]
 
 
 class richards_step_info(C.Structure):
@@ -95,6 +96,7 @@ _SIGS = {
     "richards_prepare": (C.c_int, [_VP, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     "richards_nlevels": (C.c_int, [_VP]),
     "richards_level_dims": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int)]),
+    "richards_soil_eval": (C.c_int, [_VP, _DP, _DP, _DP, C.c_int, C.c_int]),
     "richards_get_level": (C.c_int, [_VP, C.c_int, C.c_int, _DP, C.c_longlong]),
     "richards_set_level": (C.c_int, [_VP, C.c_int, C.c_int, _DP, C.c_longlong]),
     "richards_sweep": (C.c_int, [_VP, C.c_int, C.c_int]),
@@ -104,6 +106,10 @@ _SIGS = {
     "richards_vcycle": (C.c_int, [_VP]),
     "richards_profile": (C.c_int, [_VP, C.c_int]),
     "richards_profile_read": (C.c_int, [_VP, C.POINTER(richards_kernel_stat), C.c_int]),
+    "richards_batch_submit": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_double, C.c_int, C.c_int]),
+    "richards_batch_poll": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(richards_step_info)]),
+    "richards_device_bytes": (C.c_longlong, [C.POINTER(richards_grid), C.POINTER(richards_opts), C.c_int, C.c_int]),
     "richards_columns_create": (C.c_int, [C.c_int, C.POINTER(richards_column), C.POINTER(richards_sink),
                                           C.POINTER(richards_opts), _VP, C.POINTER(_VP)]),
     "richards_columns_destroy": (None, [_VP]),
@@ -164,7 +170,8 @@ def make_opts(o):
     return richards_opts(o["nu1"], o["nu2"], o["coarse_max_sweeps"], o["coarse_rtol"], o["coarsest_max_n"],
                          o["max_levels"], o["kappa_mode"], o["kappa"], o["xi"], o["tol"], o["max_cycles"],
                          o["ordering"], o["newton_iters"], o["precision"], o["inner_cycles"], o["inner_rtol"],
-                         o["max_outer"], o["tail_cells"], o.get("cycle_gamma", 1), o.get("gamma_levels", 0))
+                         o["max_outer"], o["tail_cells"], o.get("cycle_gamma", 1), o.get("gamma_levels", 0),
+                         o.get("graphs", 1))
 
 
 def current_stream():
@@ -291,6 +298,13 @@ class Solver:
     def level_ncell(self, lev):
         n = self.level_n(lev)
         return n[0] * n[1] * n[2]
+
+    def soil_eval(self, psi, arith=0):
+        """(theta, K) at the heads psi, one per fine cell; arith 1: float-float."""
+        psi = _f64(psi)
+        th, K = np.empty(self.N), np.empty(self.N)
+        _check(lib().richards_soil_eval(self.h, _dp(psi), _dp(th), _dp(K), int(arith), 0), self.h)
+        return th, K
 
     def get_level(self, lev, which):
         n = self.level_n(lev)

@@ -1,0 +1,113 @@
+"""Continuous-batching request loop for Richards solves on one GPU.
+
+Requests (problem dicts with an ``arrival`` time in seconds) are admitted in
+arrival order as soon as a slot is free and their device memory fits the
+budget (``richards_device_bytes``).  Each admitted request gets its own
+context on its own CUDA stream, keeps its state resident on the device for
+all of its time steps, and runs on a native worker thread
+(``richards_batch_submit``); the kernels of all running requests overlap on
+the device.  Finished requests free their slot and memory at once, so later
+arrivals are admitted while others are still running.  Latency = completion
+time minus arrival time.
+"""
+from __future__ import annotations
+
+import collections
+import ctypes as C
+import time
+
+import numpy as np
+
+from . import richards as R
+
+
+def request_bytes(prob, opts=None):
+    o = dict(prob["opts"])
+    if opts:
+        o.update(opts)
+    grid = R.richards_grid(prob["dim"], (C.c_int * 3)(*prob["n"]), (C.c_double * 3)(*prob["L"]))
+    s = prob["soil"]
+    fields = int(any(s.get(k) is not None for k in ("Ks_field", "p1_field", "p2_field")))
+    return int(R.lib().richards_device_bytes(C.byref(grid), C.byref(R.make_opts(o)), fields,
+                                             int(prob["sink"]["enabled"])))
+
+
+class Server:
+    def __init__(self, budget_bytes=None, max_active=16, keep_states=False, opts=None, poll_s=2e-4):
+        import torch
+        self.torch = torch
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info()
+            budget_bytes = int(0.8 * free)
+        self.budget = int(budget_bytes)
+        self.max_active = int(max_active)
+        self.keep_states = keep_states
+        self.opts = opts
+        self.poll_s = poll_s
+
+    def run(self, requests, realtime=True):
+        """Serve ``requests``; returns (results, summary)."""
+        lib = R.lib()
+        reqs = sorted(enumerate(requests), key=lambda kv: kv[1].get("arrival", 0.0))
+        pending = collections.deque(reqs)
+        waiting = collections.deque()
+        active = {}
+        results = {}
+        used = 0
+        t0 = time.perf_counter()
+        while pending or waiting or active:
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0][1].get("arrival", 0.0) <= now):
+                waiting.append(pending.popleft())
+            # admission: arrival order, slot and memory permitting
+            while waiting and len(active) < self.max_active:
+                rid, prob = waiting[0]
+                need = request_bytes(prob, self.opts)
+                if need > self.budget:
+                    waiting.popleft()
+                    results[rid] = dict(id=rid, status="rejected", bytes=need)
+                    continue
+                if used + need > self.budget:
+                    break
+                waiting.popleft()
+                stream = self.torch.cuda.Stream()
+                solver = R.Solver(prob, stream=stream.cuda_stream, opts=self.opts)
+                h = (C.c_void_p * 1)(solver.h.value)
+                st = lib.richards_batch_submit(h, 1, float(prob["dt"]), int(prob["nsteps"]), int(prob["scheme"]))
+                if st != R.RICH_OK:
+                    raise R.RichardsError(st, "richards_batch_submit failed")
+                used += need
+                arrival = prob.get("arrival", 0.0) if realtime else 0.0
+                active[rid] = dict(solver=solver, stream=stream, handle=h, bytes=need, arrival=arrival,
+                                   start=time.perf_counter() - t0, prob=prob)
+            # completions
+            for rid in list(active):
+                a = active[rid]
+                done = (C.c_int * 1)()
+                status = (C.c_int * 1)()
+                info = (R.richards_step_info * 1)()
+                lib.richards_batch_poll(a["handle"], 1, done, status, info)
+                if not done[0]:
+                    continue
+                end = time.perf_counter() - t0
+                res = dict(id=rid, status=R.STATUS_NAMES[status[0]], arrival=a["arrival"], start=a["start"], end=end,
+                           latency=end - a["arrival"], queue=a["start"] - a["arrival"], steps=a["prob"]["nsteps"],
+                           cells=int(np.prod(a["prob"]["n"])), info=info[0].as_dict(), bytes=a["bytes"])
+                if self.keep_states:
+                    res["state"] = a["solver"].state()
+                a["solver"].close()
+                used -= a["bytes"]
+                results[rid] = res
+                del active[rid]
+            if not (waiting and len(active) < self.max_active):
+                time.sleep(self.poll_s)
+        makespan = time.perf_counter() - t0
+        done_ok = [r for r in results.values() if r.get("status") == "OK"]
+        lat = np.array([r["latency"] for r in done_ok]) if done_ok else np.array([np.nan])
+        summary = dict(requests=len(requests), completed=len(done_ok),
+                       rejected=sum(1 for r in results.values() if r.get("status") == "rejected"),
+                       makespan_s=makespan, solves_per_s=len(done_ok) / makespan,
+                       cell_updates_per_s=sum(r["info"]["cell_updates"] for r in done_ok) / makespan,
+                       p50_latency_s=float(np.percentile(lat, 50)), p99_latency_s=float(np.percentile(lat, 99)),
+                       max_active=self.max_active, budget_bytes=self.budget)
+        return [results[k] for k in sorted(results)], summary

@@ -62,7 +62,7 @@ def default_opts(**kw):
              newton_iters=2,      # 0 = to tolerance; k > 0 = exactly k steps
              precision=0,         # 0 = FP64 plain, 1 = FP32 inner / FP64 outer
              inner_cycles=8, inner_rtol=1e-3, max_outer=20,
-             tail_cells=4096, cycle_gamma=1, gamma_levels=0)
+             tail_cells=4096, cycle_gamma=1, gamma_levels=0, graphs=1)
     o.update(kw)
     return o
 
@@ -205,6 +205,19 @@ def columns(ncol=4096, seed=5, dt=600.0, nsteps=144, nmin=64, nmax=1024, **optkw
 # ---------------------------------------------------------------------------
 # Serving trace: Poisson arrivals of mixed 2D/3D solves.
 # ---------------------------------------------------------------------------
+def head_at_saturation(soil, Se):
+    """Pressure head (m, < 0) at effective saturation Se of a uniform soil
+    (the inverse of theta(psi) of Table 1)."""
+    a = soil["p1"]
+    if soil["model"] == HAVERKAMP:           # Se = alpha / (alpha + h^beta)
+        return -float((a * (1.0 / Se - 1.0)) ** (1.0 / soil["p2"]))
+    if soil["model"] == GARDNER:             # Se = exp(alpha psi)
+        return float(math.log(Se) / a)
+    n = soil["p2"]
+    m = 1.0 - 1.0 / n                        # Se = (1 + (alpha h)^n)^-m
+    return -float((Se ** (-1.0 / m) - 1.0) ** (1.0 / n) / a)
+
+
 def serving_trace(rate=200.0, seconds=60.0, seed=6, sizes2d=(129, 257, 513, 1025),
                   sizes3d=(65, 129, 257), max_requests=None):
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -232,18 +245,23 @@ def serving_trace(rate=200.0, seconds=60.0, seed=6, sizes2d=(129, 257, 513, 1025
                          p2=float(rng.uniform(1.2, 3.0)), p3=0.5)
         steps = int(rng.integers(20, 201))
         sink = feddes_sink() if rng.random() < 0.5 else no_sink()
+        # initial (and lower boundary) head at an effective saturation of
+        # 0.1-0.3 of this soil: dry, but not so dry that K(psi*) underflows
+        # to 0 where theta' is 0 too (with xi = 0 that system is singular)
+        dry = head_at_saturation(soil, float(rng.uniform(0.1, 0.3)))
+        wet = head_at_saturation(soil, 0.95)
         if is3d:
             bc = _bc([NOFLUX, NOFLUX, NOFLUX, NOFLUX, FREE_DRAINAGE, DIRICHLET],
-                     [0, 0, 0, 0, 0, -0.1])
+                     [0, 0, 0, 0, 0, wet])
             prob = dict(name=f"req{len(reqs)}_3d_n{n}", dim=3, n=(n, n, n), L=(1.0, 1.0, 1.0),
-                        psi0=np.full(n ** 3, -1.0), dt=300.0)
+                        psi0=np.full(n ** 3, dry), dt=300.0)
         else:
-            bc = _bc([NOFLUX, NOFLUX, DIRICHLET, DIRICHLET], [0, 0, -10.0, -0.1])
+            bc = _bc([NOFLUX, NOFLUX, DIRICHLET, DIRICHLET], [0, 0, dry, wet])
             h = 1.0 / n
             xc = (np.arange(n) + 0.5) * h
             bc["mask_field"][3] = (np.abs(xc - 0.5) <= 0.1).astype(np.uint8)
             prob = dict(name=f"req{len(reqs)}_2d_n{n}", dim=2, n=(n, n, 1), L=(1.0, 1.0, 1.0),
-                        psi0=np.full(n * n, -10.0 if not sink["enabled"] else -1.0), dt=60.0)
+                        psi0=np.full(n * n, dry), dt=60.0)
         prob.update(soil=soil, bc=bc, sink=sink, psi_prev=None, nsteps=steps, scheme=2,
                     opts=default_opts(precision=1), arrival=t)
         reqs.append(prob)

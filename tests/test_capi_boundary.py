@@ -51,3 +51,15 @@ def test_null_context_calls_are_rejected():
     assert L.richards_get_state(None, None, 0) == R.RICH_EINVAL
     assert L.richards_nlevels(None) == 0
     L.richards_destroy(None)
+
+
+def test_device_bytes_estimate_is_host_only_and_monotone():
+    from paper_2606_04292_gb300 import serve
+    a = serve.request_bytes(W.drainage_3d(n=32, precision=0))
+    b = serve.request_bytes(W.drainage_3d(n=32))            # mixed keeps FP32 copies too
+    c = serve.request_bytes(W.drainage_3d(n=64))
+    assert 0 < a < b < c
+    assert c > 7 * b                                        # ~8x the cells
+    L = R.lib()
+    g = R.richards_grid(0, (C.c_int * 3)(4, 1, 1), (C.c_double * 3)(1, 1, 1))
+    assert L.richards_device_bytes(C.byref(g), C.byref(R.make_opts(W.default_opts())), 0, 0) == -1

@@ -299,3 +299,22 @@ def test_full_size_drainage_step_solves_the_oracle_system():
     orc.prepare(prob["dt"], info["scheme_used"])
     _, nrm = orc.residual(psi)
     assert nrm / orc.a <= prob["opts"]["tol"] * (1 + 1e-6), (nrm / orc.a, info)
+
+
+def test_graph_replay_matches_direct_launches():
+    """The captured FP32 inner cycle replays exactly the launches it replaced."""
+    prob = W.with_opts(W.random_problem(3, (40, 36, 33), W.VANGENUCHTEN, 12, hetero=True, sink=True, scheme=2),
+                       precision=1)
+    stream = torch.cuda.Stream()
+    a = R.Solver(prob, stream=stream.cuda_stream, opts=dict(graphs=1))
+    b = R.Solver(prob, stream=stream.cuda_stream, opts=dict(graphs=0))
+    for _ in range(3):
+        sa, ia = a.step()
+        sb, ib = b.step()
+        assert sa == sb == R.RICH_OK
+        assert ia["cycles"] == ib["cycles"] and ia["cell_updates"] == ib["cell_updates"]
+    assert np.array_equal(a.state(), b.state())
+    a.profile(True)
+    a.step()
+    prof = a.profile_read()
+    assert any(r["name"] == "sweep32" and r["launches"] > 0 for r in prof)
