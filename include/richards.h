@@ -272,10 +272,11 @@ richards_status richards_prolong(richards_ctx *ctx, int level);
 richards_status richards_vcycle(richards_ctx *ctx);
 
 /* ---------------------------------------------------------------------
- * Kernel timing.  While enabled, every kernel launch of the context is
- * bracketed by CUDA events on the context's stream; richards_profile_read
- * synchronises the stream and returns, per kernel name and level, the number
- * of launches, their summed device time and the cells they covered (a
+ * Kernel timing.  While enabled, kernel launches of the context are counted
+ * and, depending on the mode, bracketed by CUDA events on the context's
+ * stream; richards_profile_read synchronises the stream and returns, per
+ * kernel name and level, the number of launches, their summed device time
+ * (0 for launches that were only counted) and the cells they covered (a
  * half-sweep covers the cells of one colour).
  * --------------------------------------------------------------------- */
 typedef struct {
@@ -286,7 +287,9 @@ typedef struct {
   long long cells;
 } richards_kernel_stat;
 
-/* enable = 1: clear the records and start recording; 0: stop. */
+/* enable = 0: stop; otherwise clear the records and start recording:
+   1 time every launch; 2 time the finest level's launches and count the
+   others; 3 count only (no events, so no timing overhead). */
 richards_status richards_profile(richards_ctx *ctx, int enable);
 
 /* Writes up to max records into out; returns the number of records (or -1

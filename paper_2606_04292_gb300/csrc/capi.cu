@@ -80,7 +80,7 @@ struct richards_ctx {
   // kernel timing (richards_profile)
   struct ProfRec { const char* name; int level; long long cells; cudaEvent_t a, b; };
   struct ProfAgg { long long launches = 0; double ms = 0.0; long long cells = 0; };
-  bool prof = false;
+  int prof = 0;          // 0 off, 1 time every launch, 2 time level 0 and count the rest, 3 count only
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
   std::map<std::pair<std::string, int>, ProfAgg> prof_agg;
@@ -93,7 +93,7 @@ struct richards_ctx {
   struct GraphRec {
     cudaGraphExec_t exec = nullptr;
     double a = 0.0;
-    bool with_prof = false;
+    int with_prof = 0;
     long long updates = 0;
     std::vector<ProfRec> prof;
   };
@@ -153,6 +153,12 @@ cudaEvent_t prof_event(richards_ctx* c) {
   return e;
 }
 
+void prof_count(richards_ctx* c, const char* name, int level, long long cells) {
+  auto& g = c->prof_agg[{std::string(name), level}];
+  g.launches += 1;
+  g.cells += cells;
+}
+
 void prof_flush(richards_ctx* c) {
   if (c->prof_pending.empty()) return;
   cudaStreamSynchronize(c->s);
@@ -182,13 +188,18 @@ struct Prof {
     else cudaEventRecord(e, c->s);
   }
   Prof(richards_ctx* c_, const char* n, int l, long long cells_) : c(c_), name(n), level(l), cells(cells_) {
-    if (c->prof) {
+    if (c->prof == 1 || (c->prof == 2 && level == 0)) {
       a = prof_event(c);
       record(c, a);
     }
   }
   ~Prof() {
-    if (!a) return;
+    if (!c->prof) return;
+    if (!a) {                           // counted, not timed
+      if (c->capturing) c->capture_recs.push_back({name, level, cells, nullptr, nullptr});
+      else prof_count(c, name, level, cells);
+      return;
+    }
     cudaEvent_t b = prof_event(c);
     record(c, b);
     if (c->capturing) {                 // event nodes of a graph being captured
@@ -205,7 +216,7 @@ void graph_harvest(richards_ctx* c) {
   if (!c->harvest) return;
   for (auto& r : c->harvest->prof) {
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, r.a, r.b);
+    if (r.a) cudaEventElapsedTime(&ms, r.a, r.b);
     auto& g = c->prof_agg[{std::string(r.name), r.level}];
     g.launches += 1;
     g.ms += ms;
@@ -218,7 +229,8 @@ void graphs_reset(richards_ctx* c) {
   for (auto& g : c->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     g.exec = nullptr;
-    for (auto& r : g.prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto& r : g.prof)
+      if (r.a) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     g.prof.clear();
   }
   c->harvest = nullptr;
@@ -536,7 +548,8 @@ void run_cycle32(richards_ctx* c) {
     if (!G.exec || G.a != c->a || G.with_prof != c->prof) {
       if (G.exec) cudaGraphExecDestroy(G.exec);
       G.exec = nullptr;
-      for (auto& r : G.prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+      for (auto& r : G.prof)
+        if (r.a) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
       G.prof.clear();
       const long long before = c->updates_host;
       c->capture_recs.clear();
@@ -564,7 +577,8 @@ void run_cycle32(richards_ctx* c) {
       G.prof.swap(c->capture_recs);
       if (!ok) {                        // no graphs on this context: launch directly
         cudaGetLastError();
-        for (auto& r : G.prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto& r : G.prof)
+          if (r.a) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         G.prof.clear();
         G.exec = nullptr;
         c->graphs_ok = false;
@@ -573,6 +587,10 @@ void run_cycle32(richards_ctx* c) {
       }
       G.a = c->a;
       G.with_prof = c->prof;
+    }
+    if (c->harvest) {                   // the replay reuses the event nodes: read the last one first
+      cudaStreamSynchronize(c->s);
+      graph_harvest(c);
     }
     const cudaError_t e = cudaGraphLaunch(G.exec, c->s);
     if (e != cudaSuccess) c->graph_err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
@@ -584,19 +602,26 @@ void run_cycle32(richards_ctx* c) {
 }
 
 // coarse copies of the lagged conductivity and boundary conductances
+// (mixed mode: the coarse coefficients only feed the FP32 inner cycles, so
+// they are restricted in FP32 from the finest level's FP32 copies)
 richards_status restrict_coefficients(richards_ctx* c) {
   Prof pr(c, "coefficients", 0, c->L[0].ncell);
+  if (c->opts.precision == 1) {
+    for (int f = 0; f < 2 * c->grid.dim; ++f) rich::to_float(c->L[0].kb[f], c->L[0].kbf[f], c->L[0].nface[f], c->s);
+    for (int l = 0; l + 1 < c->nlev; ++l) {
+      const Level<float> F = view32(c, l), C = view32(c, l + 1);
+      rich::restrict32(F, C, xfer32(c, l), c->L[l].Kcf, nullptr, c->L[l + 1].Kcf, nullptr, c->s);
+      for (int f = 0; f < 2 * c->grid.dim; ++f)
+        rich::restrict_face32(geom(c, l), geom(c, l + 1), xfer32(c, l), f / 2, c->L[l].kbf[f], c->L[l + 1].kbf[f],
+                              c->s);
+    }
+    return check_launch(c);
+  }
   for (int l = 0; l + 1 < c->nlev; ++l) {
     const Level<double> F = view64(c, l), C = view64(c, l + 1);
     rich::restrict64(F, C, xfer64(c, l), c->L[l].Kc, nullptr, c->L[l + 1].Kc, nullptr, c->s);
     for (int f = 0; f < 2 * c->grid.dim; ++f)
       rich::restrict_face64(geom(c, l), geom(c, l + 1), xfer64(c, l), f / 2, c->L[l].kb[f], c->L[l + 1].kb[f], c->s);
-  }
-  if (c->opts.precision == 1) {
-    for (int l = 0; l < c->nlev; ++l) {
-      rich::to_float(c->L[l].Kc, c->L[l].Kcf, c->L[l].ncell, c->s);
-      for (int f = 0; f < 2 * c->grid.dim; ++f) rich::to_float(c->L[l].kb[f], c->L[l].kbf[f], c->L[l].nface[f], c->s);
-    }
   }
   return check_launch(c);
 }
@@ -615,11 +640,16 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   HLevel& F = c->L[0];
   Prof pr(c, "prep", 0, F.ncell);
   const bool cache = c->opts.precision == 1;
-  rich::prep_lagged(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
-                    c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, P, c->soil.model, scheme, dt, F.Kc, F.g,
-                    F.u, cache && c->th_n_valid ? c->th_n : nullptr, cache && c->th_nm1_valid ? c->th_nm1 : nullptr,
-                    cache && !c->th_n_valid ? c->th_n : nullptr, cache && !c->th_nm1_valid ? c->th_nm1 : nullptr,
-                    c->s);
+  if (cache)    // mixed mode: float-float arithmetic, theta caches
+    rich::prep_lagged_dd(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
+                         c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, P, rich::make_ddphys(P),
+                         c->soil.model, scheme, dt, F.Kc, F.Kcf, F.g, F.u, c->th_n_valid ? c->th_n : nullptr,
+                         c->th_nm1_valid ? c->th_nm1 : nullptr, c->th_n_valid ? nullptr : c->th_n,
+                         c->th_nm1_valid ? nullptr : c->th_nm1, c->s);
+  else
+    rich::prep_lagged(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
+                      c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, P, c->soil.model, scheme, dt, F.Kc,
+                      F.g, F.u, nullptr, nullptr, nullptr, nullptr, c->s);
   if (cache) {
     c->th_n_valid = true;
     if (scheme == 2) c->th_nm1_valid = true;
@@ -689,39 +719,37 @@ richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
   return finish_step(c, r, r <= c->opts.tol ? RICH_OK : RICH_ENOCONV);
 }
 
-// Mixed precision: FP64 defect r = g - N(psi); FP32 FAS V-cycles on the
-// correction equation N(psi + delta) - N(psi) = r; psi += delta; repeat until
-// the FP64 stop test holds.  Defects that only steer the next correction take
-// theta(psi) in float-float arithmetic (~1e-13 relative, a small fraction of
-// the FP64 cost); a defect that would stop the iteration, or end it at the
-// outer limit, is re-taken in FP64, so every accept/reject decision and the
-// theta(psi^{n+1}) kept for the next step are FP64.
+// Mixed precision: defect r = g - N(psi) in float-float arithmetic (~1e-14
+// relative, no FP64 instruction); FP32 FAS cycles on the correction
+// equation N(psi + delta) - N(psi) = r; psi += delta (FP64); repeat until the
+// stop test on ||r|| holds.
 richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   const double teff = 1.0 / c->a;
   const int model = c->soil.model;
   const Phys<double> P64 = phys<double>(c);
+  const rich::DDPhys Q = rich::make_ddphys(P64);
   const Phys<float> P32 = phys<float>(c);
   HLevel& F = c->L[0];
   double r = 0.0, r0 = 0.0;
   int outer = 0, inner = 0;
   richards_status st = RICH_OK;
-  // mode 0: theta from the cache of theta(psi^n); 1: float-float; 2: FP64
-  auto defect = [&](int mode, double* out) -> richards_status {
+  // theta(psi) from the cache of theta(psi^n) before the first correction,
+  // else evaluated and kept in th_cur (theta(psi^{n+1}) once accepted)
+  auto defect = [&](bool cached, double* out) -> richards_status {
     CK(cudaMemsetAsync(c->scratch, 0, sizeof(unsigned long long), c->s));
     {
-      Prof pr(c, mode == 1 ? "outer_residual_dd" : "outer_residual", 0, F.ncell);
-      rich::outer_residual(view64(c, 0), P64, model, F.gf, F.psi0f, F.uf, c->scratch,
-                           mode == 0 ? c->th_n : nullptr, mode == 2 ? c->th_cur : nullptr, mode == 1, c->s);
+      Prof pr(c, "outer_residual", 0, F.ncell);
+      rich::outer_residual_dd(view64(c, 0), P64, Q, model, F.gf, F.psi0f, F.uf, c->scratch,
+                              cached ? c->th_n : nullptr, cached ? nullptr : c->th_cur, c->s);
     }
     TRY(check_launch(c));
     double nrm;
-    TRY(read_norm(c, 0, &nrm, false));
+    TRY(read_norm(c, 0, &nrm, true));
     *out = teff * nrm;
     return RICH_OK;
   };
   for (;;) {
-    TRY(defect(outer == 0 ? 0 : 1, &r));
-    if (outer > 0 && (!(r > c->opts.tol) || outer >= c->opts.max_outer) && !std::isnan(r)) TRY(defect(2, &r));
+    TRY(defect(outer == 0, &r));
     if (outer == 0) r0 = r;
     if (!(r > c->opts.tol) || std::isnan(r)) break;
     if (outer >= c->opts.max_outer) { st = RICH_ENOCONV; break; }
@@ -1113,8 +1141,9 @@ richards_status richards_soil_eval(richards_ctx* c, const double* psi, double* t
     dK = K ? tmp + 2 * n : nullptr;
   }
   HLevel& F = c->L[0];
+  const Phys<double> P = phys<double>(c);
   rich::soil_eval(n, dpsi, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
-                  c->het_p2 ? F.p2 : nullptr, phys<double>(c), c->soil.model, arith == 1, dth, dK, c->s);
+                  c->het_p2 ? F.p2 : nullptr, P, rich::make_ddphys(P), c->soil.model, arith == 1, dth, dK, c->s);
   richards_status st = check_launch(c);
   if (!on_device) {
     if (st == RICH_OK && theta) st = cudaMemcpyAsync(theta, dth, bytes, cudaMemcpyDeviceToHost, c->s) == cudaSuccess
@@ -1335,7 +1364,7 @@ richards_status richards_profile(richards_ctx* c, int enable) {
     c->prof_agg.clear();
   }
   c->harvest = nullptr;
-  c->prof = enable != 0;
+  c->prof = enable;
   return RICH_OK;
 }
 

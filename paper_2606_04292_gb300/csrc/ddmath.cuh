@@ -152,6 +152,78 @@ __device__ __forceinline__ dd dd_recip(dd t) {
 }
 
 // ---------------------------------------------------------------------------
+// FP64 <-> float-float.  FP64 arithmetic and FP32/FP64 conversions both issue
+// at ~1/64 of the FP32 rate here, so a double is split with integer
+// operations: hi = x truncated to 24 significant bits, lo = the next 23 bits
+// (x - hi - lo < 2^-46 |x|).  |x| outside [2^-103, 2^128) (zero included)
+// takes the conversion instead.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dd dd_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023 + 127;     // FP32 biased exponent of hi
+  if (e >= 24 && e <= 254) {
+    const unsigned fhi = ((hw & 0xfffffu) << 3) | (lw >> 29);  // fraction bits 51..29
+    const unsigned flo = (lw >> 6) & 0x7fffffu;                // fraction bits 28..6
+    const unsigned elo = (unsigned)(e - 23) << 23;
+    const float one = __uint_as_float(sign | elo);
+    return mk(__uint_as_float(sign | ((unsigned)e << 23) | fhi), __uint_as_float(sign | elo | flo) - one);
+  }
+  if ((b << 1) == 0ull) return mk(__uint_as_float(sign), 0.0f);  // +-0
+  return mk(__double2float_rn(x), 0.0f);
+}
+
+// back to FP64 (two conversions and one add)
+__device__ __forceinline__ double dd_join(dd x) { return (double)x.hi + (double)x.lo; }
+
+// rounded to float
+__device__ __forceinline__ float dd_float(dd x) { return x.hi + x.lo; }
+
+__device__ __forceinline__ dd dd_sub(dd x, dd y) { return dd_add(x, dd_neg(y)); }
+
+// x < y, for normalised pairs
+__device__ __forceinline__ bool dd_lt(dd x, dd y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); }
+__device__ __forceinline__ bool dd_neg_p(dd x) { return x.hi < 0.0f; }
+
+inline dd host_split(double x) {
+  dd r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+
+// host-side split of the constants a kernel needs
+struct DDPhys {
+  dd a, xi;
+  dd ts, tr, ds;                 // theta_s, theta_r, theta_s - theta_r
+  dd p1, p2, p3, p4;             // uniform soil parameters
+  dd h1, h2, h3, h4, r12, r34;   // sink thresholds, 1/(h1 - h2), 1/(h3 - h4)
+  int sink;
+};
+
+inline DDPhys make_ddphys(const Phys<double>& P) {
+  DDPhys Q;
+  Q.a = host_split(P.a);
+  Q.xi = host_split(P.xi);
+  Q.ts = host_split(P.ts);
+  Q.tr = host_split(P.tr);
+  Q.ds = host_split(P.ts - P.tr);
+  Q.p1 = host_split(P.p1);
+  Q.p2 = host_split(P.p2);
+  Q.p3 = host_split(P.p3);
+  Q.p4 = host_split(P.p4);
+  Q.h1 = host_split(P.h1);
+  Q.h2 = host_split(P.h2);
+  Q.h3 = host_split(P.h3);
+  Q.h4 = host_split(P.h4);
+  Q.r12 = host_split(P.h1 != P.h2 ? 1.0 / (P.h1 - P.h2) : 0.0);
+  Q.r34 = host_split(P.h3 != P.h4 ? 1.0 / (P.h3 - P.h4) : 0.0);
+  Q.sink = P.sink;
+  return Q;
+}
+
+// ---------------------------------------------------------------------------
 // Constitutive laws (Table 1) in float-float; same branches as law_d/cond_d.
 // Arguments outside the float range the routines are written for (a log of
 // a value outside [1e-30, 1e30], an exponent beyond +-DD_EXP_MAX) take the
@@ -160,60 +232,91 @@ __device__ __forceinline__ dd dd_recip(dd t) {
 // ---------------------------------------------------------------------------
 #define DD_EXP_MAX 60.0f
 
-__device__ __forceinline__ bool dd_log_ok(double x) { return x > 1e-30 && x < 1e30; }
+__device__ __forceinline__ bool dd_log_ok(dd x) { return x.hi > 1e-30f && x.hi < 1e30f; }
 __device__ __forceinline__ bool dd_exp_ok(dd x) { return fabsf(x.hi) <= DD_EXP_MAX; }
 
-template <int MODEL>
-__device__ __forceinline__ double theta_dd(double psi, double p1, double p2, const Phys<double>& P) {
-  if (!(psi < 0.0)) return P.ts;
-  const double h = -psi, ds = P.ts - P.tr;
-  if (MODEL == HAVERKAMP) {
-    if (dd_log_ok(h)) {
-      const dd e = dd_mul(dd_log(dd_from(h)), dd_from(p2));
-      if (dd_exp_ok(e)) return P.tr + p1 * ds / (p1 + dd_to(dd_exp(e)));
-    }
-  } else if (MODEL == GARDNER) {
-    const dd e = dd_from(p1 * psi);
-    if (dd_exp_ok(e)) return P.tr + ds * dd_to(dd_exp(e));
-  } else if (dd_log_ok(p1 * h)) {
-    const double m = 1.0 - 1.0 / p2;
-    const dd lt = dd_mul(dd_log(dd_from(p1 * h)), dd_from(p2));
-    if (dd_exp_ok(lt)) {
-      const dd e = dd_mul(dd_log1p(dd_exp(lt)), dd_from(-m));
-      if (dd_exp_ok(e)) return P.tr + ds * dd_to(dd_exp(e));
-    }
-  }
-  return theta_only_d<MODEL>(psi, p1, p2, P);
-}
+// van Genuchten m = 1 - 1/n
+__device__ __forceinline__ dd vg_m(dd n) { return dd_sub(mk(1.0f), dd_recip(n)); }
 
 template <int MODEL>
-__device__ __forceinline__ double cond_dd(double psi, double p1, double p2, double Ks, const Phys<double>& P) {
-  if (!(psi < 0.0)) return Ks;
-  const double h = -psi;
-  if (MODEL == HAVERKAMP) {
+__device__ __forceinline__ dd theta_x(dd psi, dd p1, dd p2, const DDPhys& Q, const Phys<double>& P) {
+  if (!dd_neg_p(psi)) return Q.ts;
+  const dd h = dd_neg(psi);
+  if (MODEL == HAVERKAMP) {                     // theta_r + alpha ds / (alpha + h^beta)
     if (dd_log_ok(h)) {
-      const dd e = dd_mul(dd_log(dd_from(h)), dd_from(P.p4));
-      if (dd_exp_ok(e)) return Ks * P.p3 / (P.p3 + dd_to(dd_exp(e)));
+      const dd e = dd_mul(dd_log(h), p2);
+      if (dd_exp_ok(e)) return dd_add(Q.tr, dd_mul(dd_mul(p1, Q.ds), dd_recip(dd_add(p1, dd_exp(e)))));
     }
-  } else if (MODEL == GARDNER) {
-    const dd e = dd_from(p1 * psi);
-    if (dd_exp_ok(e)) return Ks * dd_to(dd_exp(e));
-  } else if (dd_log_ok(p1 * h)) {
-    const double m = 1.0 - 1.0 / p2;
-    const dd lt = dd_mul(dd_log(dd_from(p1 * h)), dd_from(p2));   // log t
-    if (dd_exp_ok(lt)) {
-      const dd t = dd_exp(lt);
-      const dd L1 = dd_log1p(t);                                  // log(1 + t)
-      const dd eK = dd_mul(L1, dd_from(-P.p3 * m));
-      if (dd_exp_ok(eK)) {
-        // log(t / (1 + t)) without cancellation
-        const dd lr = t.hi > 1.0f ? dd_neg(dd_log1p(dd_recip(t))) : dd_add(lt, dd_neg(L1));
-        const double inner = -dd_to(dd_expm1(dd_mul(lr, dd_from(m))));
-        return Ks * dd_to(dd_exp(eK)) * inner * inner;
+  } else if (MODEL == GARDNER) {                // theta_r + ds e^{alpha psi}
+    const dd e = dd_mul(p1, psi);
+    if (dd_exp_ok(e)) return dd_add(Q.tr, dd_mul(Q.ds, dd_exp(e)));
+  } else {                                      // theta_r + ds (1 + t)^-m, t = (alpha h)^n
+    const dd ah = dd_mul(p1, h);
+    if (dd_log_ok(ah)) {
+      const dd lt = dd_mul(dd_log(ah), p2);
+      if (dd_exp_ok(lt)) {
+        const dd e = dd_neg(dd_mul(dd_log1p(dd_exp(lt)), vg_m(p2)));
+        if (dd_exp_ok(e)) return dd_add(Q.tr, dd_mul(Q.ds, dd_exp(e)));
       }
     }
   }
-  return cond_d<MODEL>(psi, p1, p2, Ks, P);
+  return dd_split(theta_only_d<MODEL>(dd_join(psi), dd_join(p1), dd_join(p2), P));
+}
+
+template <int MODEL>
+__device__ __forceinline__ dd cond_x(dd psi, dd p1, dd p2, dd Ks, const DDPhys& Q, const Phys<double>& P) {
+  if (!dd_neg_p(psi)) return Ks;
+  const dd h = dd_neg(psi);
+  if (MODEL == HAVERKAMP) {                     // Ks A / (A + h^gamma)
+    if (dd_log_ok(h)) {
+      const dd e = dd_mul(dd_log(h), Q.p4);
+      if (dd_exp_ok(e)) return dd_mul(dd_mul(Ks, Q.p3), dd_recip(dd_add(Q.p3, dd_exp(e))));
+    }
+  } else if (MODEL == GARDNER) {                // Ks e^{alpha psi}
+    const dd e = dd_mul(p1, psi);
+    if (dd_exp_ok(e)) return dd_mul(Ks, dd_exp(e));
+  } else {                                      // Ks Se^l (1 - (1 - Se^{1/m})^m)^2
+    const dd ah = dd_mul(p1, h);
+    if (dd_log_ok(ah)) {
+      const dd m = vg_m(p2);
+      const dd lt = dd_mul(dd_log(ah), p2);     // log t
+      if (dd_exp_ok(lt)) {
+        const dd t = dd_exp(lt);
+        const dd L1 = dd_log1p(t);              // log(1 + t)
+        const dd eK = dd_neg(dd_mul(dd_mul(L1, Q.p3), m));
+        if (dd_exp_ok(eK)) {
+          // log(t / (1 + t)) without cancellation; inner = 1 - (t/(1+t))^m
+          const dd lr = t.hi > 1.0f ? dd_neg(dd_log1p(dd_recip(t))) : dd_sub(lt, L1);
+          const dd inner = dd_neg(dd_expm1(dd_mul(lr, m)));
+          return dd_mul(dd_mul(Ks, dd_exp(eK)), dd_mul(inner, inner));
+        }
+      }
+    }
+  }
+  return dd_split(cond_d<MODEL>(dd_join(psi), dd_join(p1), dd_join(p2), dd_join(Ks), P));
+}
+
+// double in, double out (richards_soil_eval)
+template <int MODEL>
+__device__ __forceinline__ double theta_dd(double psi, double p1, double p2, const DDPhys& Q,
+                                           const Phys<double>& P) {
+  return dd_join(theta_x<MODEL>(dd_split(psi), dd_split(p1), dd_split(p2), Q, P));
+}
+template <int MODEL>
+__device__ __forceinline__ double cond_dd(double psi, double p1, double p2, double Ks, const DDPhys& Q,
+                                          const Phys<double>& P) {
+  return dd_join(cond_x<MODEL>(dd_split(psi), dd_split(p1), dd_split(p2), dd_split(Ks), Q, P));
+}
+
+// Feddes sink S = smax alpha_F(psi) (same pieces as feddes()); thresholds
+// are compared in float-float, so a psi within 2^-46 of a kink may take the
+// neighbouring piece, where alpha_F agrees to that order (it is continuous)
+__device__ __forceinline__ dd sink_x(dd psi, dd smax, const DDPhys& Q) {
+  if (!Q.sink || !(smax.hi > 0.0f)) return mk(0.0f);
+  if (!dd_lt(psi, Q.h1) || dd_lt(psi, Q.h4)) return mk(0.0f);
+  if (!dd_lt(psi, Q.h2)) return dd_mul(smax, dd_mul(dd_sub(Q.h1, psi), Q.r12));
+  if (!dd_lt(psi, Q.h3)) return smax;
+  return dd_mul(smax, dd_mul(dd_sub(psi, Q.h4), Q.r34));
 }
 
 }  // namespace rich

@@ -387,27 +387,29 @@ __device__ __forceinline__ void stencil(const Level<T>& L, long long i, int i0, 
                                         const T* __restrict__ u, T& mii, T& off) {
   const T Ki = L.Kc[i];
   T dg = T(0), of = T(0);
+  // K_f / h^2 = (Kc_i + Kc_j) * (s/2): halving s is exact, so this equals
+  // ((Kc_i + Kc_j) / 2) * s bit for bit
   {
-    const T s = L.ih2[0];
-    if (i0 > 0) { const T m = (Ki + L.Kc[i - 1]) * T(0.5) * s; dg += m; of += m * u[i - 1]; }
+    const T s = L.ih2[0], hs = T(0.5) * s;
+    if (i0 > 0) { const T m = (Ki + L.Kc[i - 1]) * hs; dg += m; of += m * u[i - 1]; }
     else dg += T(2) * L.kb[0][i1 + (long long)L.n1 * i2] * s;
-    if (i0 < L.n0 - 1) { const T m = (Ki + L.Kc[i + 1]) * T(0.5) * s; dg += m; of += m * u[i + 1]; }
+    if (i0 < L.n0 - 1) { const T m = (Ki + L.Kc[i + 1]) * hs; dg += m; of += m * u[i + 1]; }
     else dg += T(2) * L.kb[1][i1 + (long long)L.n1 * i2] * s;
   }
   if (L.dim > 1) {
-    const T s = L.ih2[1];
+    const T s = L.ih2[1], hs = T(0.5) * s;
     const long long st = L.n0;
-    if (i1 > 0) { const T m = (Ki + L.Kc[i - st]) * T(0.5) * s; dg += m; of += m * u[i - st]; }
+    if (i1 > 0) { const T m = (Ki + L.Kc[i - st]) * hs; dg += m; of += m * u[i - st]; }
     else dg += T(2) * L.kb[2][i0 + (long long)L.n0 * i2] * s;
-    if (i1 < L.n1 - 1) { const T m = (Ki + L.Kc[i + st]) * T(0.5) * s; dg += m; of += m * u[i + st]; }
+    if (i1 < L.n1 - 1) { const T m = (Ki + L.Kc[i + st]) * hs; dg += m; of += m * u[i + st]; }
     else dg += T(2) * L.kb[3][i0 + (long long)L.n0 * i2] * s;
   }
   if (L.dim > 2) {
-    const T s = L.ih2[2];
+    const T s = L.ih2[2], hs = T(0.5) * s;
     const long long st = (long long)L.n0 * L.n1;
-    if (i2 > 0) { const T m = (Ki + L.Kc[i - st]) * T(0.5) * s; dg += m; of += m * u[i - st]; }
+    if (i2 > 0) { const T m = (Ki + L.Kc[i - st]) * hs; dg += m; of += m * u[i - st]; }
     else dg += T(2) * L.kb[4][i0 + (long long)L.n0 * i1] * s;
-    if (i2 < L.n2 - 1) { const T m = (Ki + L.Kc[i + st]) * T(0.5) * s; dg += m; of += m * u[i + st]; }
+    if (i2 < L.n2 - 1) { const T m = (Ki + L.Kc[i + st]) * hs; dg += m; of += m * u[i + st]; }
     else dg += T(2) * L.kb[5][i0 + (long long)L.n0 * i1] * s;
   }
   mii = dg;
@@ -461,8 +463,11 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
     lo = (f - P.a * P.ts - smax) / cc;
     hi = (f - P.a * P.tr) / cc;
   } else {
-    lo = (f - P.a * ds - smax) / cc;
-    hi = (f + P.a * ds + smax) / cc;
+    // FP32: both ends through one approximate reciprocal; each end has a
+    // slack of (a ds + smax)/cc beyond the root, far above its 2^-22 error
+    const T rc = __fdividef(1.0f, cc);
+    lo = (f - P.a * ds - smax) * rc;
+    hi = (f + P.a * ds + smax) * rc;
   }
   T x = x0 < lo ? lo : (x0 > hi ? hi : x0);
   const int maxit = P.newton_k > 0 ? P.newton_k : 200;
@@ -494,7 +499,9 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
     const T dF = der + cc;
     if (F == T(0)) break;
     if (F > T(0)) hi = x; else lo = x;
-    T xn = x - F / dF;
+    T xn;
+    if constexpr (sizeof(T) == 4) xn = x - __fdividef(F, dF);    // dF > 0; a 2-ulp step error is harmless
+    else xn = x - F / dF;
     // a step strictly inside the bracket, or below round-off, is kept;
     // anything else (outside, or onto an end) is replaced by bisection
     const T tiny = tol_of<T>() * (fabs(x) > T(1) ? fabs(x) : T(1));

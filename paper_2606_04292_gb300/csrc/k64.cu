@@ -74,6 +74,54 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
   }
 }
 
+// The same lagged state in float-float arithmetic (mixed mode): Kc = K(psi*)
+// to FP64 (Kc) and FP32 (Kcf), g = history + xi psi* to FP64; theta(psi^n)
+// and theta(psi^{n-1}) from the caches when given, else evaluated and kept.
+template <int MODEL>
+__global__ void __launch_bounds__(256) k_prep_lagged_dd(long long n, const double* __restrict__ psin,
+                                                        const double* __restrict__ psinm1,
+                                                        const double* __restrict__ Ks, dd Ks_s,
+                                                        const double* __restrict__ p1f,
+                                                        const double* __restrict__ p2f, Phys<double> P, DDPhys Q,
+                                                        int scheme, dd hist_scale, double* Kc, float* Kcf, double* g,
+                                                        double* u, const double* thn_in, const double* thm_in,
+                                                        double* thn_out, double* thm_out) {
+  // hist_scale: 1/tau (BDF1) or 1/(2 tau) (BDF2)
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const dd p1 = p1f ? dd_split(p1f[i]) : Q.p1, p2 = p2f ? dd_split(p2f[i]) : Q.p2;
+    const double pnd = psin[i];
+    const dd pn = dd_split(pnd);
+    dd thn;
+    if (thn_in) {
+      thn = dd_split(thn_in[i]);
+    } else {
+      thn = theta_x<MODEL>(pn, p1, p2, Q, P);
+      if (thn_out) thn_out[i] = dd_join(thn);
+    }
+    dd ps, hist;
+    if (scheme == 1) {
+      ps = pn;
+      hist = dd_mul(thn, hist_scale);
+    } else {
+      const dd pm = dd_split(psinm1[i]);
+      dd thm;
+      if (thm_in) {
+        thm = dd_split(thm_in[i]);
+      } else {
+        thm = theta_x<MODEL>(pm, p1, p2, Q, P);
+        if (thm_out) thm_out[i] = dd_join(thm);
+      }
+      ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
+      hist = dd_mul(dd_sub(mk(4.0f * thn.hi, 4.0f * thn.lo), thm), hist_scale);
+    }
+    const dd K = cond_x<MODEL>(ps, p1, p2, Ks ? dd_split(Ks[i]) : Ks_s, Q, P);
+    Kc[i] = dd_join(K);
+    Kcf[i] = dd_float(K);
+    g[i] = dd_join(dd_add(hist, dd_mul(Q.xi, ps)));
+    u[i] = pnd;
+  }
+}
+
 // Gravity and boundary terms of g, and boundary face conductances:
 //   gravity  -(M z)_i = (K_{i+e_z/2} - K_{i-e_z/2}) / h_z over interior faces,
 //   Dirichlet (reading)  kb = (Kc_i + K(psi_b))/2,  g += 2 kb / h^2 (psi_b + z_b - z_i),
@@ -127,8 +175,8 @@ __global__ void __launch_bounds__(256) k_prep_rhs(Geom G, BcDev bc, const double
 }
 
 // restriction of a boundary-face array over the face's two in-plane axes
-__global__ void __launch_bounds__(256) k_restrict_face(Geom F, Geom C, Xfer<double> X, int ax, const double* fine,
-                                                       double* coarse) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_face(Geom F, Geom C, Xfer<T> X, int ax, const T* fine, T* coarse) {
   int oa[2], k = 0;
   for (int a = 0; a < 3; ++a)
     if (a != ax) oa[k++] = a;
@@ -137,7 +185,7 @@ __global__ void __launch_bounds__(256) k_restrict_face(Geom F, Geom C, Xfer<doub
   for (long long J = blockIdx.x * (long long)blockDim.x + threadIdx.x; J < nc; J += (long long)gridDim.x * blockDim.x) {
     const int J0 = (int)(J % nC[oa[0]]), J1 = (int)(J / nC[oa[0]]);
     const int c0 = X.rc[oa[0]][J0], c1 = X.rc[oa[1]][J1];
-    double s = 0.0;
+    T s = T(0);
     for (int a1 = 0; a1 < c1; ++a1)
       for (int a0 = 0; a0 < c0; ++a0)
         s += X.rw[oa[0]][RMAX * J0 + a0] * X.rw[oa[1]][RMAX * J1 + a1] *
@@ -168,42 +216,70 @@ __global__ void __launch_bounds__(256) k_to_float(const double* src, float* dst,
     dst[i] = (float)src[i];
 }
 
-// FP64 defect of the outer correction loop; hands the FP32 inner problem its
-// right side r, its frozen state psi0 and a zero initial correction.
-// th_in: theta(u) known already (the iterate is psi^n); otherwise theta(u) is
-// evaluated and kept in th_out for the next step's history.
-// theta(u) from th_in when given; else in FP64 (kept in th_out), or, with DD,
-// in float-float arithmetic (accurate to ~1e-13, nothing kept).
-template <int MODEL, bool DD>
-__global__ void __launch_bounds__(256) k_outer_residual(Level<double> L, Phys<double> P, float* r32, float* psi0f,
-                                                        float* delta, unsigned long long* norm,
-                                                        const double* __restrict__ th_in, double* th_out) {
+// Defect of the mixed mode's outer loop, d = g - N(u) (eq. Nh-def), in
+// float-float arithmetic (no FP64 instruction on the path: the FP64 arrays
+// are split with integer operations); hands the FP32 inner problem its right
+// side d, its frozen state psi0 = u and a zero initial correction, and
+// accumulates ||d||_inf (as float bits).  The interior fluxes are taken in
+// difference form m_f (u_i - u_j), so nothing cancels.  theta(u) comes from
+// th_in when given (u = psi^n), else it is evaluated and kept in th_out
+// (nullable) for the next step's history.
+template <int MODEL>
+__global__ void __launch_bounds__(128) k_outer_residual_dd(Level<double> L, Phys<double> P, DDPhys Q, float* r32,
+                                                           float* psi0f, float* delta, unsigned long long* norm,
+                                                           const double* __restrict__ th_in, double* th_out) {
   __shared__ unsigned long long sm[33];
   unsigned long long mx = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.ncell;
-       i += (long long)gridDim.x * blockDim.x) {
-    int i0, i1, i2;
-    cell_coords(L.n0, L.n1, i, i0, i1, i2);
-    double mii, off;
-    stencil(L, i, i0, i1, i2, L.u, mii, off);
-    const double ui = L.u[i];
-    double th;
-    if (th_in) {
-      th = th_in[i];
-    } else if (DD) {
-      th = theta_dd<MODEL>(ui, L.p1 ? L.p1[i] : P.p1, L.p2 ? L.p2[i] : P.p2, P);
-    } else {
-      th = theta_only_d<MODEL>(ui, L.p1 ? L.p1[i] : P.p1, L.p2 ? L.p2[i] : P.p2, P);
-      th_out[i] = th;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i2 = blockIdx.z;
+  if (i0 < L.n0) {
+    const long long i = i0 + (long long)L.n0 * (i1 + (long long)L.n1 * i2);
+    const double* __restrict__ u = L.u;
+    const double* __restrict__ K = L.Kc;
+    const dd ui = dd_split(u[i]);
+    const dd Ki = dd_split(K[i]);
+    dd flux = mk(0.0f), db = mk(0.0f);
+    const int nn[3] = {L.n0, L.n1, L.n2};
+    const int ii[3] = {i0, i1, i2};
+    const long long st[3] = {1, L.n0, (long long)L.n0 * L.n1};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= L.dim) break;
+      const dd s = dd_split(L.ih2[a]), hs = mk(0.5f * s.hi, 0.5f * s.lo), s2 = mk(2.0f * s.hi, 2.0f * s.lo);
+      long long fc;
+      if (a == 0) fc = i1 + (long long)L.n1 * i2;
+      else if (a == 1) fc = i0 + (long long)L.n0 * i2;
+      else fc = i0 + (long long)L.n0 * i1;
+      if (ii[a] > 0) {
+        const long long j = i - st[a];
+        flux = dd_add(flux, dd_mul(dd_mul(dd_add(Ki, dd_split(K[j])), hs), dd_sub(ui, dd_split(u[j]))));
+      } else {
+        db = dd_add(db, dd_mul(dd_split(L.kb[2 * a][fc]), s2));
+      }
+      if (ii[a] < nn[a] - 1) {
+        const long long j = i + st[a];
+        flux = dd_add(flux, dd_mul(dd_mul(dd_add(Ki, dd_split(K[j])), hs), dd_sub(ui, dd_split(u[j]))));
+      } else {
+        db = dd_add(db, dd_mul(dd_split(L.kb[2 * a + 1][fc]), s2));
+      }
     }
-    double S, dS;
-    sink_direct(ui, L.smax ? L.smax[i] : 0.0, P, S, dS);
-    const double di = L.g[i] - (P.a * th + S + P.xi * ui + mii * ui - off);
-    r32[i] = (float)di;
-    psi0f[i] = (float)L.u[i];
+    dd th;
+    if (th_in) {
+      th = dd_split(th_in[i]);
+    } else {
+      th = theta_x<MODEL>(ui, L.p1 ? dd_split(L.p1[i]) : Q.p1, L.p2 ? dd_split(L.p2[i]) : Q.p2, Q, P);
+      if (th_out) th_out[i] = dd_join(th);
+    }
+    const dd S = L.smax ? sink_x(ui, dd_split(L.smax[i]), Q) : mk(0.0f);
+    // N = a theta + S + xi u + sum_f m_f (u_i - u_j) + (sum of Dirichlet diagonals) u
+    dd N = dd_add(dd_mul(Q.a, th), S);
+    N = dd_add(N, dd_mul(dd_add(Q.xi, db), ui));
+    N = dd_add(N, flux);
+    const float di = dd_float(dd_sub(dd_split(L.g[i]), N));
+    r32[i] = di;
+    psi0f[i] = dd_float(ui);
     delta[i] = 0.0f;
-    const unsigned long long b = nbits(di);
-    mx = b > mx ? b : mx;
+    mx = nbits(di);
   }
   mx = block_max(mx, sm);
   if (threadIdx.x == 0) atomicMax(norm, mx);
@@ -231,6 +307,24 @@ void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const 
                                                   thm_in, thn_out, thm_out);
 }
 
+void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
+                    const double* p1, const double* p2, const Phys<double>& P, const DDPhys& Q, int model,
+                    int scheme, double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
+                    const double* thm_in, double* thn_out, double* thm_out, cudaStream_t s) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const int b = grid_for(n);
+  const dd ks = host_split(Ks_s), hs = host_split(scheme == 1 ? 1.0 / dt : 1.0 / (2.0 * dt));
+  if (model == HAVERKAMP)
+    k_prep_lagged_dd<HAVERKAMP><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, P, Q, scheme, hs, Kc, Kcf, g, u,
+                                                  thn_in, thm_in, thn_out, thm_out);
+  else if (model == GARDNER)
+    k_prep_lagged_dd<GARDNER><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, P, Q, scheme, hs, Kc, Kcf, g, u,
+                                                thn_in, thm_in, thn_out, thm_out);
+  else
+    k_prep_lagged_dd<VANGENUCHTEN><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, P, Q, scheme, hs, Kc, Kcf, g,
+                                                     u, thn_in, thm_in, thn_out, thm_out);
+}
+
 void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
               const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6], cudaStream_t s) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
@@ -250,7 +344,16 @@ void restrict_face64(const Geom& F, const Geom& C, const Xfer<double>& X, int ax
   long long nc = 1;
   for (int a = 0; a < 3; ++a)
     if (a != axis) nc *= nC[a];
-  k_restrict_face<<<grid_for(nc), 256, 0, s>>>(F, C, X, axis, fine, coarse);
+  k_restrict_face<double><<<grid_for(nc), 256, 0, s>>>(F, C, X, axis, fine, coarse);
+}
+
+void restrict_face32(const Geom& F, const Geom& C, const Xfer<float>& X, int axis, const float* fine, float* coarse,
+                     cudaStream_t s) {
+  const int nC[3] = {C.n0, C.n1, C.n2};
+  long long nc = 1;
+  for (int a = 0; a < 3; ++a)
+    if (a != axis) nc *= nC[a];
+  k_restrict_face<float><<<grid_for(nc), 256, 0, s>>>(F, C, X, axis, fine, coarse);
 }
 
 void sink_coef(const Geom& G, double Tp, double depth, double decay, double* smax, cudaStream_t s) {
@@ -261,55 +364,48 @@ void to_float(const double* src, float* dst, long long n, cudaStream_t s) {
   k_to_float<<<grid_for(n), 256, 0, s>>>(src, dst, n);
 }
 
-template <bool DD>
-static void outer_residual_t(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
-                             float* delta, unsigned long long* norm, const double* th_in, double* th_out,
-                             cudaStream_t s) {
-  const int b = grid_for(L.ncell);
+void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPhys& Q, int model, float* r32,
+                       float* psi0f, float* delta, unsigned long long* norm, const double* th_in, double* th_out,
+                       cudaStream_t s) {
+  const Launch3 g = launch3(L.n0, L.n1, L.n2);
   if (model == HAVERKAMP)
-    k_outer_residual<HAVERKAMP, DD><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
+    k_outer_residual_dd<HAVERKAMP><<<g.grid, g.block, 0, s>>>(L, P, Q, r32, psi0f, delta, norm, th_in, th_out);
   else if (model == GARDNER)
-    k_outer_residual<GARDNER, DD><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
+    k_outer_residual_dd<GARDNER><<<g.grid, g.block, 0, s>>>(L, P, Q, r32, psi0f, delta, norm, th_in, th_out);
   else
-    k_outer_residual<VANGENUCHTEN, DD><<<b, 256, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
-}
-
-void outer_residual(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
-                    float* delta, unsigned long long* norm, const double* th_in, double* th_out, bool dd,
-                    cudaStream_t s) {
-  if (dd) outer_residual_t<true>(L, P, model, r32, psi0f, delta, norm, th_in, th_out, s);
-  else outer_residual_t<false>(L, P, model, r32, psi0f, delta, norm, th_in, th_out, s);
+    k_outer_residual_dd<VANGENUCHTEN><<<g.grid, g.block, 0, s>>>(L, P, Q, r32, psi0f, delta, norm, th_in, th_out);
 }
 
 template <int MODEL, bool DD>
 __global__ void __launch_bounds__(256) k_soil_eval(long long n, const double* __restrict__ psi,
                                                    const double* __restrict__ Ks, double Ks_s,
                                                    const double* __restrict__ p1f, const double* __restrict__ p2f,
-                                                   Phys<double> P, double* theta, double* K) {
+                                                   Phys<double> P, DDPhys Q, double* theta, double* K) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double p1 = p1f ? p1f[i] : P.p1, p2 = p2f ? p2f[i] : P.p2, x = psi[i];
-    if (theta) theta[i] = DD ? theta_dd<MODEL>(x, p1, p2, P) : theta_only_d<MODEL>(x, p1, p2, P);
+    if (theta) theta[i] = DD ? theta_dd<MODEL>(x, p1, p2, Q, P) : theta_only_d<MODEL>(x, p1, p2, P);
     if (K) {
       const double ks = Ks ? Ks[i] : Ks_s;
-      K[i] = DD ? cond_dd<MODEL>(x, p1, p2, ks, P) : cond_d<MODEL>(x, p1, p2, ks, P);
+      K[i] = DD ? cond_dd<MODEL>(x, p1, p2, ks, Q, P) : cond_d<MODEL>(x, p1, p2, ks, P);
     }
   }
 }
 
 template <bool DD>
 static void soil_eval_t(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1,
-                        const double* p2, const Phys<double>& P, int model, double* theta, double* K,
-                        cudaStream_t s) {
+                        const double* p2, const Phys<double>& P, const DDPhys& Q, int model, double* theta,
+                        double* K, cudaStream_t s) {
   const int b = grid_for(n);
-  if (model == HAVERKAMP) k_soil_eval<HAVERKAMP, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, theta, K);
-  else if (model == GARDNER) k_soil_eval<GARDNER, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, theta, K);
-  else k_soil_eval<VANGENUCHTEN, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, theta, K);
+  if (model == HAVERKAMP) k_soil_eval<HAVERKAMP, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, Q, theta, K);
+  else if (model == GARDNER) k_soil_eval<GARDNER, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, Q, theta, K);
+  else k_soil_eval<VANGENUCHTEN, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, Q, theta, K);
 }
 
 void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1, const double* p2,
-               const Phys<double>& P, int model, bool dd, double* theta, double* K, cudaStream_t s) {
-  if (dd) soil_eval_t<true>(n, psi, Ks, Ks_s, p1, p2, P, model, theta, K, s);
-  else soil_eval_t<false>(n, psi, Ks, Ks_s, p1, p2, P, model, theta, K, s);
+               const Phys<double>& P, const DDPhys& Q, int model, bool dd, double* theta, double* K,
+               cudaStream_t s) {
+  if (dd) soil_eval_t<true>(n, psi, Ks, Ks_s, p1, p2, P, Q, model, theta, K, s);
+  else soil_eval_t<false>(n, psi, Ks, Ks_s, p1, p2, P, Q, model, theta, K, s);
 }
 
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s) {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "ddmath.cuh"
 #include "device.cuh"
 
 #define TAIL_THREADS 512
@@ -60,15 +61,23 @@ void restrict_face64(const Geom& F, const Geom& C, const Xfer<double>& X, int ax
 void sink_coef(const Geom& G, double Tp, double depth, double decay, double* smax, cudaStream_t s);
 void to_float(const double* src, float* dst, long long n, cudaStream_t s);
 
-// mixed mode: r = g - N(u) in FP64 -> r32, psi0 = (float)u, delta = 0; ||r||_inf.
-// theta(u) from th_in if given, else FP64 (written to th_out) or, with dd,
-// float-float (not written).
-void outer_residual(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
-                    float* delta, unsigned long long* norm, const double* th_in, double* th_out, bool dd,
-                    cudaStream_t s);
+// mixed mode: r = g - N(u) in float-float -> r32, psi0 = (float)u, delta = 0;
+// ||r||_inf as float bits.  theta(u) from th_in if given, else evaluated and
+// written to th_out (nullable).
+void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPhys& Q, int model, float* r32,
+                       float* psi0f, float* delta, unsigned long long* norm, const double* th_in, double* th_out,
+                       cudaStream_t s);
+// mixed mode: the lagged state in float-float (Kc to FP64 and FP32)
+void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
+                    const double* p1, const double* p2, const Phys<double>& P, const DDPhys& Q, int model,
+                    int scheme, double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
+                    const double* thm_in, double* thn_out, double* thm_out, cudaStream_t s);
+void restrict_face32(const Geom& F, const Geom& C, const Xfer<float>& X, int axis, const float* fine, float* coarse,
+                     cudaStream_t s);
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);
 // theta(psi) and K(psi) per cell (FP64 or float-float); outputs nullable
 void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1, const double* p2,
-               const Phys<double>& P, int model, bool dd, double* theta, double* K, cudaStream_t s);
+               const Phys<double>& P, const DDPhys& Q, int model, bool dd, double* theta, double* K,
+               cudaStream_t s);
 
 }  // namespace rich

@@ -339,8 +339,10 @@ class Solver:
         _check(lib().richards_vcycle(self.h), self.h)
 
     # -- kernel timing ---------------------------------------------------
-    def profile(self, enable=True):
-        _check(lib().richards_profile(self.h, 1 if enable else 0), self.h)
+    def profile(self, enable=True, mode=1):
+        """mode 1: time every launch; 2: time the finest level, count the rest;
+        3: count only."""
+        _check(lib().richards_profile(self.h, int(mode) if enable else 0), self.h)
 
     def profile_read(self):
         buf = (richards_kernel_stat * 256)()

@@ -168,9 +168,12 @@ def drainage_3d(n=256, dt=300.0, nsteps=50, seed_ks=3, seed_vg=4, **optkw):
     bc = _bc([NOFLUX, NOFLUX, NOFLUX, NOFLUX, FREE_DRAINAGE, NOFLUX])
     # W(2,2) cycles on the two finest levels (V below): on this heterogeneous,
     # partly saturated field they need ~2.4x fewer cycles than V(2,2), as many
-    # as full W-cycles, and two coarsest sweeps are enough.
+    # as full W-cycles, and two coarsest sweeps are enough.  Each FP32 inner
+    # solve reduces its defect 1e4-fold (two outer corrections reach tol
+    # 1e-8; 1e3 takes three), and levels of up to 512 cells run in the
+    # single-block tail.
     opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0, precision=1, cycle_gamma=2, gamma_levels=2,
-                        coarse_max_sweeps=2)
+                        coarse_max_sweeps=2, inner_rtol=1e-4, tail_cells=512)
     opts.update(optkw)
     return dict(name=f"drainage3d_n{n}", dim=3, n=(n, n, n), L=(1.0, 1.0, 1.0),
                 soil=soil, bc=bc, sink=no_sink(),

@@ -7,6 +7,11 @@ stages agree to ~1e-13 relative; iterated results (V-cycles, steps) to the
 Mixed mode is checked against the a-posteriori bound
 ||psi_mixed - psi_ref||_inf <= (||r_mixed|| + ||r_ref||) / min_i(a theta'_i + xi)
 (the diagonal-dominance argument of Lemma 3.1 applied to the whole Jacobian).
+Mixed mode evaluates K(psi*), theta and the defect in float-float arithmetic
+(laws within DD_EPS = 6e-12 relative, the bound of the soil-law tests), so its
+discrete system differs from the oracle's by at most DD_EPS times the size of
+each term; the oracle's residual of a mixed result may exceed the GPU's own by
+that much (_law_allowance), on top of the stop tolerance.
 """
 import numpy as np
 import pytest
@@ -24,6 +29,7 @@ from paper_2606_04292_gb300 import richards as R  # noqa: E402
 
 STAGE_RTOL = 1e-12
 STEP_RTOL = 1e-10
+DD_EPS = 6e-12
 
 
 def rel(a, b):
@@ -70,6 +76,25 @@ def test_prepare_matches_oracle(mk, scheme):
             kg, ko = gs.get_level(lev, 10 + f), orc.array(10 + f, lev)
             assert np.max(np.abs(kg - ko)) <= STAGE_RTOL * max(np.max(np.abs(ko)), 1e-300), (lev, f)
     assert rel(gs.get_level(0, 1), orc.g(0)) <= STAGE_RTOL
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_mixed_prepare_matches_oracle_within_float_float_bound(mk, scheme):
+    """Mixed mode takes K(psi*), theta(psi^n), theta(psi^{n-1}) and g in
+    float-float: the finest level's Kc and g agree with the oracle to DD_EPS."""
+    prob = W.with_opts(mk(), precision=1)
+    if scheme == 2:
+        rng = np.random.default_rng(9)
+        prob["psi_prev"] = prob["psi0"] + rng.uniform(-0.02, 0.02, len(prob["psi0"]))
+    gs, orc, p = pair(prob)
+    assert gs.prepare(p["dt"], scheme) == scheme
+    assert orc.prepare(p["dt"], scheme) == scheme
+    assert rel(gs.get_level(0, 2), orc.Kc(0)) <= DD_EPS
+    for f in range(2 * p["dim"]):
+        kg, ko = gs.get_level(0, 10 + f), orc.array(10 + f, 0)
+        assert np.max(np.abs(kg - ko)) <= DD_EPS * max(np.max(np.abs(ko)), 1e-300), f
+    assert rel(gs.get_level(0, 1), orc.g(0)) <= DD_EPS
 
 
 @pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
@@ -189,6 +214,39 @@ def test_strip_2d_bdf2_steps():
         assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
 
 
+def _law_allowance(orc, prob, psi):
+    """DD_EPS times, per cell, the magnitudes of the terms of g - N(psi) that
+    depend on K or theta (interior fluxes |m_f (psi_i - psi_j)|, Dirichlet
+    diagonals, gravity fluxes, |g|, a theta_s, |S|), max over cells, in theta
+    units (divided by a)."""
+    n0, n1, n2 = prob["n"]
+    dim = prob["dim"]
+    Kc = orc.Kc(0).reshape(n2, n1, n0)
+    P = np.asarray(psi, dtype=np.float64).reshape(n2, n1, n0)
+    h = [prob["L"][a] / prob["n"][a] for a in range(dim)]
+    tot = np.abs(orc.g(0)).reshape(n2, n1, n0) + orc.a * prob["soil"]["theta_s"]
+    for a in range(dim):
+        ax = 2 - a
+        sl_lo = [slice(None)] * 3
+        sl_hi = [slice(None)] * 3
+        sl_lo[ax], sl_hi[ax] = slice(0, -1), slice(1, None)
+        Kf = 0.5 * (Kc[tuple(sl_lo)] + Kc[tuple(sl_hi)])
+        flux = Kf / h[a] ** 2 * np.abs(P[tuple(sl_hi)] - P[tuple(sl_lo)])
+        if a == dim - 1:
+            flux = flux + Kf / h[a]                     # gravity
+        tot[tuple(sl_lo)] += flux
+        tot[tuple(sl_hi)] += flux
+        for side in range(2):
+            kb = orc.array(10 + 2 * a + side, 0)
+            edge = [slice(None)] * 3
+            edge[ax] = -1 if side else 0
+            bval = abs(prob["bc"]["value"][2 * a + side])
+            tot[tuple(edge)] += 2.0 * kb.reshape(tot[tuple(edge)].shape) / h[a] ** 2 * (np.abs(P[tuple(edge)]) + bval)
+    if prob["sink"]["enabled"]:
+        tot += orc.array(4, 0).reshape(n2, n1, n0)
+    return DD_EPS * float(np.max(tot)) / orc.a
+
+
 def _mixed_bound(orc, psi_m, psi_r):
     """(||r_m|| + ||r_r||) / min_i a theta'(zeta_i), zeta_i on [psi_m, psi_r]."""
     a = orc.a
@@ -223,7 +281,7 @@ def test_mixed_precision_within_stated_bound(mk):
         orc.set_state(cur, prev)
         orc.prepare(prob["dt"], info["scheme_used"])
         _, rm = orc.residual(psi_m)        # the oracle re-derives the FP64 residual
-        assert rm / orc.a <= prob["opts"]["tol"] * (1 + 1e-6)
+        assert rm / orc.a <= prob["opts"]["tol"] * (1 + 1e-6) + _law_allowance(orc, prob, psi_m)
         bound = _mixed_bound(orc, psi_m, psi_r)
         err = np.max(np.abs(psi_m - psi_r))
         assert err <= bound * (1 + 1e-6), (k, err, bound)
@@ -298,7 +356,8 @@ def test_full_size_drainage_step_solves_the_oracle_system():
     orc = Oracle(prob)
     orc.prepare(prob["dt"], info["scheme_used"])
     _, nrm = orc.residual(psi)
-    assert nrm / orc.a <= prob["opts"]["tol"] * (1 + 1e-6), (nrm / orc.a, info)
+    allow = _law_allowance(orc, prob, psi)
+    assert nrm / orc.a <= prob["opts"]["tol"] * (1 + 1e-6) + allow, (nrm / orc.a, allow, info)
 
 
 def test_graph_replay_matches_direct_launches():
