@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=None,
                     help="steps with kernel timing (default: all timed steps)")
+    ap.add_argument("--no-columns", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--gamma", type=int, default=2, help="1 = V-cycles, 2 = W-cycles")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel timing records here")
     return ap.parse_args()
@@ -166,6 +168,55 @@ def roofline(prof, steps, ms_pass):
     else:
         out.update({"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": None,
                     "traffic": None})
+    return out
+
+
+# ---------------------------------------------------------------------------
+def columns_bench(stream, steps=10):
+    """Batched root-uptake columns: 4096 columns of U{64..1024} cells, per-column
+    van Genuchten soil, Feddes sink, BDF1 dt = 600 s; every column advances
+    `steps` steps in one persistent launch (block size autotuned first)."""
+    import numpy as np
+    import torch
+    from paper_2606_04292_gb300 import richards as R
+    from paper_2606_04292_gb300 import workloads as W
+    probs = W.columns()
+    cols = R.Columns(probs, stream=stream.cuda_stream)
+    dt = probs[0]["dt"]
+    threads = cols.autotune(dt)
+    cols.run(dt, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = cols.run(dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stt = cols.stats()
+    out = {"workload": "4096 columns U{64..1024} cells, VG per column, Feddes sink, BDF1 dt=600 s, mixed",
+           "columns": len(probs), "cells": int(cols.N), "steps": steps, "threads": threads,
+           "status": R.STATUS_NAMES[st], "all_columns_ok": bool(np.all(stt["status"] == R.RICH_OK)),
+           "column_steps_per_s": len(probs) * steps / (ms * 1e-3),
+           "cell_updates_per_s": float(np.sum(stt["updates"])) / (ms * 1e-3), "ms": ms}
+    cols.close()
+    return out
+
+
+def serving_bench(nreq=24, max_steps=20):
+    """Served stream, reduced: Poisson arrivals at 200/s of 2D 129^2/257^2 and
+    3D 65^3 requests (three soil laws, half with a sink, BDF2), at most
+    `max_steps` steps each; mixed precision and FP64 plain on the same trace."""
+    from paper_2606_04292_gb300 import serve
+    from paper_2606_04292_gb300 import workloads as W
+    out = {"workload": f"{nreq} Poisson requests (200/s), 2D 129^2-257^2 and 3D 65^3, <= {max_steps} BDF2 steps"}
+    for label, opts in (("mixed", None), ("fp64_plain", {"precision": 0})):
+        trace = W.serving_trace(rate=200.0, seconds=60.0, seed=6, sizes2d=(129, 257), sizes3d=(65,),
+                                max_requests=nreq)
+        for p in trace:
+            p["nsteps"] = min(p["nsteps"], max_steps)
+        results, summary = serve.Server(max_active=8, opts=opts).run(trace, realtime=True)
+        out[label] = {k: summary[k] for k in ("completed", "makespan_s", "solves_per_s", "cell_updates_per_s",
+                                              "p50_latency_s", "p99_latency_s")}
     return out
 
 
@@ -363,6 +414,13 @@ def main():
         gf.close()
         gm.close()
 
+    columns = None
+    if rank == 0 and not args.no_columns:
+        columns = columns_bench(stream)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_bench()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob, gs.state())
@@ -385,6 +443,8 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "fp64_plain": fp64,
+            "columns": columns,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

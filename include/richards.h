@@ -121,7 +121,10 @@ typedef struct {
      graphs               1: capture the FP32 inner cycle of the mixed mode
                           into a CUDA graph and replay it (needs a stream
                           other than the legacy default stream; falls back
-                          to direct launches otherwise) */
+                          to direct launches otherwise)
+     sweep_planes         FP32 half-sweeps: cells per thread along z (1, 2,
+                          4 or 8); above 1 a thread loads the operands of
+                          its next cell before it solves the current one */
 typedef struct {
   int nu1, nu2, coarse_max_sweeps;
   double coarse_rtol;
@@ -131,7 +134,7 @@ typedef struct {
   int max_cycles, ordering, newton_iters, precision;
   int inner_cycles;
   double inner_rtol;
-  int max_outer, tail_cells, cycle_gamma, gamma_levels, graphs;
+  int max_outer, tail_cells, cycle_gamma, gamma_levels, graphs, sweep_planes;
 } richards_opts;
 
 typedef struct {
@@ -140,6 +143,15 @@ typedef struct {
   int scheme_used;       /* 1 or 2 (BDF2 falls back to BDF1 on a first step) */
   double resid0, resid;  /* tau_eff ||g - N(psi)||_inf at start / at exit    */
   long long cell_updates;/* NGS point updates over all levels this step     */
+  /* Water balance of the step (conservation, Section 2): tau_eff times
+     sum_i V_i (a theta_i - hist_i + S_i + xi (psi_i - psi*_i)) minus the
+     net boundary inflow, i.e. the water volume the unconverged residual
+     leaves unaccounted (-tau_eff sum_i V_i r_i), summed in float-float. */
+  double mass_defect;
+  /* ||N(psi) - g||_inf / min_i (a theta'(psi_i) + S'(psi_i) + xi): bound on
+     ||psi - psi_exact||_inf by the diagonal dominance of the Jacobian
+     (Lemma 3.1); +inf where that minimum is 0 (saturated cells, xi = 0). */
+  double err_bound;
 } richards_step_info;
 
 /* Create a context for one grid; allocates the multigrid hierarchy on the

@@ -26,6 +26,7 @@ namespace {
 
 constexpr int MAXLEV = 24;
 constexpr int NSCRATCH = 32;   // norm slots + statistics
+constexpr int MASS_PARTS = 152 * 32;   // water-balance blocks (grid_for's cap)
 
 struct HLevel {
   int n[3] = {1, 1, 1};
@@ -73,6 +74,8 @@ struct richards_ctx {
   Xfer<float>* dX32 = nullptr;
   unsigned long long* scratch = nullptr;
   unsigned long long* hscratch = nullptr;    // pinned
+  double* mass_part = nullptr;               // water-balance partial sums (+ the min bits)
+  double* hmass = nullptr;                   // pinned
   std::vector<void*> allocs;
   std::vector<void*> bc_allocs;
   std::string err;
@@ -520,8 +523,8 @@ void vcycle32(richards_ctx* c, int l) {
   const long long half = (F.ncell + 1) / 2;
   nvtxRangePushA(level_range(l));
   for (int k = 0; k < c->opts.nu1; ++k) {
-    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->s); }
-    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->s); }
+    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->opts.sweep_planes, c->s); }
+    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->opts.sweep_planes, c->s); }
   }
   c->updates_host += (long long)c->opts.nu1 * F.ncell;
   { Prof pr(c, "residual32", l, F.ncell); rich::residual32(F, P, model, nullptr, c->s); }
@@ -532,8 +535,8 @@ void vcycle32(richards_ctx* c, int l) {
   nvtxRangePushA(level_range(l));
   { Prof pr(c, "prolong32", l, F.ncell); rich::prolong32(F, C, xfer32(c, l), c->s); }
   for (int k = 0; k < c->opts.nu2; ++k) {
-    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->s); }
-    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->s); }
+    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->opts.sweep_planes, c->s); }
+    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->opts.sweep_planes, c->s); }
   }
   nvtxRangePop();
   c->updates_host += (long long)c->opts.nu2 * F.ncell;
@@ -692,6 +695,41 @@ richards_status read_stats(richards_ctx* c, long long* tail_updates) {
   return RICH_OK;
 }
 
+// Water balance and error bound of the iterate about to be accepted (before
+// the history shift); r = tau_eff ||g - N(psi)||_inf.  th_*: theta caches
+// (nullable: evaluated in float-float).
+richards_status water_balance(richards_ctx* c, double r, richards_step_info* info, const double* th_new,
+                              const double* th_n, const double* th_nm1) {
+  if (!info) return RICH_OK;
+  info->mass_defect = NAN;
+  info->err_bound = NAN;
+  if (!std::isfinite(r)) return RICH_OK;
+  unsigned* dmin = (unsigned*)(c->mass_part + MASS_PARTS);
+  CK(cudaMemsetAsync(dmin, 0xff, sizeof(unsigned), c->s));
+  int nb;
+  {
+    Prof pr(c, "mass_balance", 0, c->L[0].ncell);
+    nb = rich::mass_balance(view64(c, 0), geom(c, 0), c->bcdev, phys<double>(c), phys<float>(c), c->soil.model,
+                            c->psi_n, c->psi_nm1, c->scheme_used, c->dt, th_new, th_n,
+                            c->scheme_used == 2 ? th_nm1 : nullptr, c->mass_part, dmin, c->s);
+  }
+  TRY(check_launch(c));
+  if (nb > MASS_PARTS) return fail(c, RICH_ECUDA, "water balance: too many blocks");
+  CK(cudaMemcpyAsync(c->hmass, c->mass_part, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaMemcpyAsync(c->hmass + MASS_PARTS, dmin, sizeof(unsigned), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  long double sum = 0.0L;
+  for (int b = 0; b < nb; ++b) sum += (long double)c->hmass[b];
+  info->mass_defect = (double)(sum / (long double)c->a);
+  unsigned bits;
+  std::memcpy(&bits, c->hmass + MASS_PARTS, sizeof(unsigned));
+  float dm;
+  std::memcpy(&dm, &bits, sizeof(float));
+  const double nrm = r * c->a;      // ||N(psi) - g||_inf
+  info->err_bound = (bits < 0x7f800000u && dm > 0.0f) ? nrm / (double)dm : INFINITY;
+  return RICH_OK;
+}
+
 richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
   const double teff = 1.0 / c->a;
   double nrm;
@@ -716,6 +754,7 @@ richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
     info->resid = r;
     info->cell_updates = c->updates_host + tu;
   }
+  TRY(water_balance(c, r, info, nullptr, nullptr, nullptr));
   return finish_step(c, r, r <= c->opts.tol ? RICH_OK : RICH_ENOCONV);
 }
 
@@ -790,6 +829,7 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
     info->resid = r;
     info->cell_updates = c->updates_host + tu;
   }
+  TRY(water_balance(c, r, info, outer > 0 ? c->th_cur : c->th_n, c->th_n, c->th_nm1_valid ? c->th_nm1 : nullptr));
   return finish_step(c, r, st, outer > 0 ? 1 : 0);
 }
 
@@ -822,7 +862,8 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
       !(o.tol > 0.0) || o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
       o.ordering != 1 || (o.precision != 0 && o.precision != 1) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
       o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0 || o.cycle_gamma < 1 || o.cycle_gamma > 3 ||
-      o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1))
+      o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1) ||
+      (o.sweep_planes != 1 && o.sweep_planes != 2 && o.sweep_planes != 4 && o.sweep_planes != 8))
     return RICH_EINVAL;
   richards_ctx* c = new richards_ctx();
   c->s = (cudaStream_t)stream;
@@ -882,6 +923,9 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
   if (st == RICH_OK) st = dalloc(c, &c->dL32, c->nlev);
   if (st == RICH_OK) st = dalloc(c, &c->dX32, c->nlev);
   if (st == RICH_OK) st = dalloc(c, &c->scratch, NSCRATCH);
+  if (st == RICH_OK) st = dalloc(c, &c->mass_part, MASS_PARTS + 1);
+  if (st == RICH_OK && cudaMallocHost((void**)&c->hmass, (MASS_PARTS + 1) * sizeof(double)) != cudaSuccess)
+    st = fail(c, RICH_ENOMEM, "cudaMallocHost failed");
   if (st == RICH_OK && cudaMallocHost((void**)&c->hscratch, NSCRATCH * sizeof(unsigned long long)) != cudaSuccess)
     st = fail(c, RICH_ENOMEM, "cudaMallocHost failed");
   if (st == RICH_OK && cudaMemsetAsync(c->scratch, 0, NSCRATCH * sizeof(unsigned long long), c->s) != cudaSuccess)
@@ -904,6 +948,7 @@ void richards_destroy(richards_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   for (void* p : c->bc_allocs) cudaFree(p);
   if (c->hscratch) cudaFreeHost(c->hscratch);
+  if (c->hmass) cudaFreeHost(c->hmass);
   delete c;
 }
 
@@ -1215,6 +1260,8 @@ richards_status richards_batch_submit(richards_ctx* const* ctxs, int n, double d
         acc.cell_updates += last.cell_updates;
         acc.scheme_used = last.scheme_used;
         acc.resid = last.resid;
+        acc.mass_defect = last.mass_defect;
+        acc.err_bound = last.err_bound;
         if (k == 0) acc.resid0 = last.resid0;
       }
       c->batch_info = acc;

@@ -385,32 +385,36 @@ __device__ __forceinline__ void sink_delta(T psi0, T x, T smax, const Phys<T>& P
 template <typename T>
 __device__ __forceinline__ void stencil(const Level<T>& L, long long i, int i0, int i1, int i2,
                                         const T* __restrict__ u, T& mii, T& off) {
-  const T Ki = L.Kc[i];
+  // neighbours through base pointers and 32-bit strides (levels hold fewer
+  // than 2^31 cells)
+  const T* __restrict__ Kp = L.Kc + i;
+  const T* __restrict__ up = u + i;
+  const T Ki = Kp[0];
   T dg = T(0), of = T(0);
   // K_f / h^2 = (Kc_i + Kc_j) * (s/2): halving s is exact, so this equals
   // ((Kc_i + Kc_j) / 2) * s bit for bit
   {
     const T s = L.ih2[0], hs = T(0.5) * s;
-    if (i0 > 0) { const T m = (Ki + L.Kc[i - 1]) * hs; dg += m; of += m * u[i - 1]; }
-    else dg += T(2) * L.kb[0][i1 + (long long)L.n1 * i2] * s;
-    if (i0 < L.n0 - 1) { const T m = (Ki + L.Kc[i + 1]) * hs; dg += m; of += m * u[i + 1]; }
-    else dg += T(2) * L.kb[1][i1 + (long long)L.n1 * i2] * s;
+    if (i0 > 0) { const T m = (Ki + Kp[-1]) * hs; dg += m; of += m * up[-1]; }
+    else dg += T(2) * L.kb[0][i1 + L.n1 * i2] * s;
+    if (i0 < L.n0 - 1) { const T m = (Ki + Kp[1]) * hs; dg += m; of += m * up[1]; }
+    else dg += T(2) * L.kb[1][i1 + L.n1 * i2] * s;
   }
   if (L.dim > 1) {
     const T s = L.ih2[1], hs = T(0.5) * s;
-    const long long st = L.n0;
-    if (i1 > 0) { const T m = (Ki + L.Kc[i - st]) * hs; dg += m; of += m * u[i - st]; }
-    else dg += T(2) * L.kb[2][i0 + (long long)L.n0 * i2] * s;
-    if (i1 < L.n1 - 1) { const T m = (Ki + L.Kc[i + st]) * hs; dg += m; of += m * u[i + st]; }
-    else dg += T(2) * L.kb[3][i0 + (long long)L.n0 * i2] * s;
+    const int st = L.n0;
+    if (i1 > 0) { const T m = (Ki + Kp[-st]) * hs; dg += m; of += m * up[-st]; }
+    else dg += T(2) * L.kb[2][i0 + L.n0 * i2] * s;
+    if (i1 < L.n1 - 1) { const T m = (Ki + Kp[st]) * hs; dg += m; of += m * up[st]; }
+    else dg += T(2) * L.kb[3][i0 + L.n0 * i2] * s;
   }
   if (L.dim > 2) {
     const T s = L.ih2[2], hs = T(0.5) * s;
-    const long long st = (long long)L.n0 * L.n1;
-    if (i2 > 0) { const T m = (Ki + L.Kc[i - st]) * hs; dg += m; of += m * u[i - st]; }
-    else dg += T(2) * L.kb[4][i0 + (long long)L.n0 * i1] * s;
-    if (i2 < L.n2 - 1) { const T m = (Ki + L.Kc[i + st]) * hs; dg += m; of += m * u[i + st]; }
-    else dg += T(2) * L.kb[5][i0 + (long long)L.n0 * i1] * s;
+    const int st = L.n0 * L.n1;
+    if (i2 > 0) { const T m = (Ki + Kp[-st]) * hs; dg += m; of += m * up[-st]; }
+    else dg += T(2) * L.kb[4][i0 + L.n0 * i1] * s;
+    if (i2 < L.n2 - 1) { const T m = (Ki + Kp[st]) * hs; dg += m; of += m * up[st]; }
+    else dg += T(2) * L.kb[5][i0 + L.n0 * i1] * s;
   }
   mii = dg;
   off = of;
@@ -509,6 +513,11 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
     const T step = fabs(xn - x);
     x = xn;
     if (P.newton_k <= 0 && step <= tiny) break;
+    // FP32 increment form: a step below 2^-20 of |x| leaves nothing for the
+    // next one to change at this precision (quadratic convergence)
+    if constexpr (FORM == FORM_DELTA) {
+      if (step <= 9.5367431640625e-7f * fabsf(x)) break;
+    }
   }
   return x;
 }
@@ -526,6 +535,74 @@ __device__ __forceinline__ void point_update(const Level<T>& L, const Phys<T>& P
   const T smax = L.smax ? L.smax[i] : T(0);
   const T psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
   L.u[i] = point_solve<T, FORM, MODEL>(cc, f, ui, psi0, p1, p2, smax, P);
+}
+
+// Operands of one point update, gathered before any of them is used, so that
+// a thread can issue the loads of its next cell before it solves the current
+// one (the sweep is bound by load latency, not by bandwidth).  Face f =
+// 2 axis + side; on a boundary face Kn holds the face conductance kb; on an
+// axis the grid does not have, Kn = un = 0 and 1/h^2 = 0, so m_f = 0.
+template <typename T>
+struct CellOps {
+  unsigned i;
+  bool valid;
+  unsigned bmask;                // bit f: face f lies on the boundary
+  T ui, Ki, g, psi0, p1, p2, smax;
+  T Kn[6], un[6];
+};
+
+template <typename T, int FORM>
+__device__ __forceinline__ void gather(const Level<T>& L, const Phys<T>& P, int i0, int i1, int i2, CellOps<T>& c) {
+  const unsigned i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
+  c.i = i;
+  const T* __restrict__ Kp = L.Kc + i;
+  const T* __restrict__ up = L.u + i;
+  c.Ki = Kp[0];
+  c.ui = up[0];
+  c.g = L.g[i];
+  c.psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
+  c.p1 = L.p1 ? L.p1[i] : P.p1;
+  c.p2 = L.p2 ? L.p2[i] : P.p2;
+  c.smax = L.smax ? L.smax[i] : T(0);
+  unsigned bm = 0;
+  const int ii[3] = {i0, i1, i2};
+  const int nn[3] = {L.n0, L.n1, L.n2};
+  const int st[3] = {1, L.n0, L.n0 * L.n1};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int fc = a == 0 ? i1 + L.n1 * i2 : (a == 1 ? i0 + L.n0 * i2 : i0 + L.n0 * i1);
+    if (a >= L.dim) {
+      c.Kn[2 * a] = c.Kn[2 * a + 1] = T(0);
+      c.un[2 * a] = c.un[2 * a + 1] = T(0);
+      continue;
+    }
+    if (ii[a] > 0) { c.Kn[2 * a] = Kp[-st[a]]; c.un[2 * a] = up[-st[a]]; }
+    else { c.Kn[2 * a] = L.kb[2 * a][fc]; c.un[2 * a] = T(0); bm |= 1u << (2 * a); }
+    if (ii[a] < nn[a] - 1) { c.Kn[2 * a + 1] = Kp[st[a]]; c.un[2 * a + 1] = up[st[a]]; }
+    else { c.Kn[2 * a + 1] = L.kb[2 * a + 1][fc]; c.un[2 * a + 1] = T(0); bm |= 1u << (2 * a + 1); }
+  }
+  c.bmask = bm;
+}
+
+// the point update of a gathered cell (same sums, in the same order, as
+// stencil() and point_update())
+template <typename T, int FORM, int MODEL>
+__device__ __forceinline__ T solve_cell(const Level<T>& L, const Phys<T>& P, const CellOps<T>& c) {
+  T dg = T(0), of = T(0);
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const T s = L.ih2[f >> 1];
+    if (c.bmask & (1u << f)) {
+      dg += T(2) * c.Kn[f] * s;
+    } else {
+      const T m = (c.Ki + c.Kn[f]) * (T(0.5) * s);
+      dg += m;
+      of += m * c.un[f];
+    }
+  }
+  const T cc = P.xi + P.kappa + dg;
+  const T f = c.g + of + P.kappa * c.ui;
+  return point_solve<T, FORM, MODEL>(cc, f, c.ui, c.psi0, c.p1, c.p2, c.smax, P);
 }
 
 // N(u)_i = storage(u_i) + xi u_i + m_ii u_i - sum_j m_ij u_j   (eq. Nh-def)

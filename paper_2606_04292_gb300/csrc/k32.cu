@@ -3,8 +3,8 @@
 
 namespace rich {
 using D = Dispatch<float, FORM_DELTA>;
-void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, cudaStream_t s) {
-  D::sweep(L, P, model, color, s);
+void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, int planes, cudaStream_t s) {
+  D::sweep_pipe(L, P, model, color, planes, s);
 }
 void residual32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,
                 cudaStream_t s) {

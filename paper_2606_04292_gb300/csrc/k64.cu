@@ -408,6 +408,135 @@ void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, co
   else soil_eval_t<false>(n, psi, Ks, Ks_s, p1, p2, P, Q, model, theta, K, s);
 }
 
+// ---------------------------------------------------------------------------
+// Water balance of a step (float-float, per block partial sums).  Per cell,
+//   V (a theta(psi) - hist + S(psi) + xi (psi - psi*)) - (boundary inflow of the cell),
+// whose sum is -V sum_i r_i (r = g - N(psi)): interior fluxes telescope and
+// the gravity and boundary terms of g are the boundary inflow.  Also the
+// minimum over cells of a theta'(psi) + S'(psi) + xi (FP32), for the error
+// bound ||psi - psi_exact|| <= ||N(psi) - g|| / min(...).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dd warp_sum_dd(dd v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    dd w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = dd_add(v, w);
+  }
+  return v;
+}
+
+template <int MODEL>
+__global__ void __launch_bounds__(256) k_mass_balance(Level<double> L, Geom G, BcDev bc, Phys<double> P, DDPhys Q,
+                                                      Phys<float> Pf, const double* __restrict__ psin,
+                                                      const double* __restrict__ psinm1, int scheme, dd hist_scale,
+                                                      const double* th_new, const double* th_n, const double* th_nm1,
+                                                      double* part, unsigned* dmin_bits) {
+  __shared__ float sh[2][32];
+  dd acc = mk(0.0f);
+  float dmin = __int_as_float(0x7f800000);
+  const int v = G.dim - 1;
+  const int nn[3] = {G.n0, G.n1, G.n2};
+  double Vd = 1.0;
+  for (int a = 0; a < G.dim; ++a) Vd *= G.h[a];
+  const dd V = dd_split(Vd);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.ncell;
+       i += (long long)gridDim.x * blockDim.x) {
+    int ii[3];
+    cell_coords(G.n0, G.n1, i, ii[0], ii[1], ii[2]);
+    const dd p1 = L.p1 ? dd_split(L.p1[i]) : Q.p1, p2 = L.p2 ? dd_split(L.p2[i]) : Q.p2;
+    const dd psi = dd_split(L.u[i]), pn = dd_split(psin[i]);
+    const dd th1 = th_new ? dd_split(th_new[i]) : theta_x<MODEL>(psi, p1, p2, Q, P);
+    const dd thn = th_n ? dd_split(th_n[i]) : theta_x<MODEL>(pn, p1, p2, Q, P);
+    dd hist, ps;
+    if (scheme == 1) {
+      hist = dd_mul(thn, hist_scale);
+      ps = pn;
+    } else {
+      const dd pm = dd_split(psinm1[i]);
+      const dd thm = th_nm1 ? dd_split(th_nm1[i]) : theta_x<MODEL>(pm, p1, p2, Q, P);
+      hist = dd_mul(dd_sub(mk(4.0f * thn.hi, 4.0f * thn.lo), thm), hist_scale);
+      ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
+    }
+    const dd smax = L.smax ? dd_split(L.smax[i]) : mk(0.0f);
+    dd cell = dd_sub(dd_mul(Q.a, th1), hist);
+    cell = dd_add(cell, sink_x(psi, smax, Q));
+    cell = dd_add(cell, dd_mul(Q.xi, dd_sub(psi, ps)));
+    cell = dd_mul(V, cell);
+    // inflow through this cell's boundary faces (face area A = V / h)
+    for (int ax = 0; ax < G.dim; ++ax)
+      for (int side = 0; side < 2; ++side) {
+        if (ii[ax] != (side ? nn[ax] - 1 : 0)) continue;
+        const int f = 2 * ax + side;
+        long long fc;
+        if (ax == 0) fc = ii[1] + (long long)G.n1 * ii[2];
+        else if (ax == 1) fc = ii[0] + (long long)G.n0 * ii[2];
+        else fc = ii[0] + (long long)G.n0 * ii[1];
+        const dd A = dd_split(Vd / G.h[ax]);
+        const int kind = bc.kind[f];
+        const bool dir = kind == 0 && (!bc.mask[f] || bc.mask[f][fc]);
+        dd qin = mk(0.0f);
+        if (dir) {
+          const double zi = (ii[v] + 0.5) * G.h[v];
+          const double zb = (ax == v) ? (side ? G.Lv : 0.0) : zi;
+          const double val = bc.vfield[f] ? bc.vfield[f][fc] : bc.value[f];
+          const dd head = dd_sub(dd_add(dd_split(val), dd_split(zb)), dd_add(psi, dd_split(zi)));
+          qin = dd_mul(dd_mul(A, dd_split(L.kb[f][fc])), dd_mul(head, dd_split(2.0 / G.h[ax])));
+        } else if (kind == 2) {
+          qin = dd_mul(A, dd_split(bc.vfield[f] ? bc.vfield[f][fc] : bc.value[f]));
+        } else if (kind == 3) {
+          qin = dd_neg(dd_mul(A, dd_split(L.Kc[i])));
+        }
+        cell = dd_sub(cell, qin);
+      }
+    acc = dd_add(acc, cell);
+    // a theta' + S' + xi at psi (FP32 increment laws with a zero increment)
+    const float psif = dd_float(psi), p1f = dd_float(p1), p2f = dd_float(p2);
+    float Dth, dth;
+    dincr<MODEL>(dbase<MODEL>(psif, p1f, p2f), 0.0f, p1f, p2f, Pf, Dth, dth);
+    const float smf = dd_float(smax);
+    float sa = 0.0f, sda = 0.0f;
+    if (Pf.sink && smf > 0.0f) feddes(psif, Pf, sa, sda);
+    dmin = fminf(dmin, Pf.a * dth + sda * smf + Pf.xi);
+  }
+  acc = warp_sum_dd(acc);
+  for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sh[0][wid] = acc.hi; sh[1][wid] = acc.lo; }
+  __shared__ float smin[32];
+  if (lane == 0) smin[wid] = dmin;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    dd x = lane < nw ? mk(sh[0][lane], sh[1][lane]) : mk(0.0f);
+    float m = lane < nw ? smin[lane] : __int_as_float(0x7f800000);
+    x = warp_sum_dd(x);
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+      part[blockIdx.x] = dd_join(x);
+      atomicMin(dmin_bits, __float_as_uint(fmaxf(m, 0.0f)));
+    }
+  }
+}
+
+int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const Phys<double>& P, const Phys<float>& Pf,
+                 int model, const double* psin, const double* psinm1, int scheme, double dt, const double* th_new,
+                 const double* th_n, const double* th_nm1, double* part, unsigned* dmin_bits, cudaStream_t s) {
+  const int b = grid_for(L.ncell);
+  const DDPhys Q = make_ddphys(P);
+  const dd hs = host_split(scheme == 1 ? 1.0 / dt : 1.0 / (2.0 * dt));
+  if (model == HAVERKAMP)
+    k_mass_balance<HAVERKAMP><<<b, 256, 0, s>>>(L, G, bc, P, Q, Pf, psin, psinm1, scheme, hs, th_new, th_n, th_nm1,
+                                                part, dmin_bits);
+  else if (model == GARDNER)
+    k_mass_balance<GARDNER><<<b, 256, 0, s>>>(L, G, bc, P, Q, Pf, psin, psinm1, scheme, hs, th_new, th_n, th_nm1,
+                                              part, dmin_bits);
+  else
+    k_mass_balance<VANGENUCHTEN><<<b, 256, 0, s>>>(L, G, bc, P, Q, Pf, psin, psinm1, scheme, hs, th_new, th_n,
+                                                   th_nm1, part, dmin_bits);
+  return b;
+}
+
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s) {
   k_apply_delta<<<grid_for(n), 256, 0, s>>>(u, delta, n);
 }

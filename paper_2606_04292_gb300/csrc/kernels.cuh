@@ -29,8 +29,37 @@ __global__ void __launch_bounds__(256) k_sweep(Level<T> L, Phys<T> P, int color)
   const int i1 = blockIdx.y, i2 = blockIdx.z;
   const int i0 = 2 * p + ((color + i1 + i2) & 1);
   if (i0 >= L.n0) return;
-  const long long i = i0 + (long long)L.n0 * (i1 + L.n1 * i2);
+  const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
   point_update<T, FORM, MODEL>(L, P, i, i0, i1, i2);
+}
+
+// The same half-sweep with ZC planes per thread, software-pipelined: the
+// operands of the next plane's cell are loaded before the current cell is
+// solved.  Launch grid: x = pairs of cells along a row, y = row, z = chunk
+// of ZC planes.
+template <typename T, int FORM, int MODEL, int ZC>
+__global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int color) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y;
+  const int z0 = blockIdx.z * ZC;
+  CellOps<T> c[2];
+  {
+    const int i0 = 2 * p + ((color + i1 + z0) & 1);
+    c[0].valid = z0 < L.n2 && i0 < L.n0;
+    if (c[0].valid) gather<T, FORM>(L, P, i0, i1, z0, c[0]);
+  }
+#pragma unroll
+  for (int k = 0; k < ZC; ++k) {
+    if (k + 1 < ZC) {
+      const int i2 = z0 + k + 1;
+      const int i0 = 2 * p + ((color + i1 + i2) & 1);
+      CellOps<T>& nx = c[(k + 1) & 1];
+      nx.valid = i2 < L.n2 && i0 < L.n0;
+      if (nx.valid) gather<T, FORM>(L, P, i0, i1, i2, nx);
+    }
+    const CellOps<T>& cur = c[k & 1];
+    if (cur.valid) L.u[cur.i] = solve_cell<T, FORM, MODEL>(L, P, cur);
+  }
 }
 
 // d = g - N(u) on a level, with ||d||_inf accumulated into *norm (bit max).
@@ -42,7 +71,7 @@ __global__ void __launch_bounds__(256) k_residual(Level<T> L, Phys<T> P, unsigne
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int i1 = blockIdx.y, i2 = blockIdx.z;
   if (i0 < L.n0) {
-    const long long i = i0 + (long long)L.n0 * (i1 + L.n1 * i2);
+    const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
     const T di = L.g[i] - apply_N<T, FORM, MODEL>(L, P, L.u, i, i0, i1, i2);
     L.d[i] = di;
     mx = nbits(di);
@@ -84,6 +113,129 @@ __global__ void __launch_bounds__(256) k_prolong(Level<T> F, Level<T> C, Xfer<T>
   if (i0 >= F.n0) return;
   const long long i = i0 + (long long)F.n0 * (i1 + F.n1 * i2);
   F.u[i] += prolong_at(C, X, i0, i1, i2);
+}
+
+// ---------------------------------------------------------------------------
+// Nested levels (n_fine = 2 n_coarse on every axis the grid has): the same
+// transfer operators with their weights written out, so a thread reads no
+// tables.  Restriction taps per axis at fine 2J-1 .. 2J+2 with weights
+// (1,3,3,1)/8, at the ends (0,4,3,1)/8 and (1,3,4,0)/8 (the normalised
+// transpose of the constant-extrapolation interpolation); an axis of one
+// cell is a single tap of weight 1.  Interpolation of an interior fine cell
+// i: 3/4 of coarse floor(i/2) and 1/4 of the coarse neighbour on i's side;
+// fine end cells take their weights from the tables (they fold the ghost).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void restrict_taps(int J, int nc, int nf, int* idx, T* w) {
+  if (nf == 1) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) { idx[t] = 0; w[t] = T(0); }
+    w[1] = T(1);
+    return;
+  }
+  w[0] = T(0.125); w[1] = T(0.375); w[2] = T(0.375); w[3] = T(0.125);
+  if (J == 0) { w[0] = T(0); w[1] = T(0.5); }
+  if (J == nc - 1) { w[2] = T(0.5); w[3] = T(0); }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int f = 2 * J - 1 + t;
+    idx[t] = f < 0 ? 0 : (f >= nf ? nf - 1 : f);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_nested(Level<T> F, Level<T> C, const T* fa, const T* fb, T* ca,
+                                                         T* cb) {
+  const int J0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J1 = blockIdx.y, J2 = blockIdx.z;
+  if (J0 >= C.n0) return;
+  int x[4], y[4], z[4];
+  T wx[4], wy[4], wz[4];
+  restrict_taps<T>(J0, C.n0, F.n0, x, wx);
+  restrict_taps<T>(J1, C.n1, F.n1, y, wy);
+  restrict_taps<T>(J2, C.n2, F.n2, z, wz);
+  T sa = T(0), sb = T(0);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (wz[c] == T(0)) continue;
+    T ya = T(0), yb = T(0);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (wy[b] == T(0)) continue;
+      const unsigned row = (unsigned)F.n0 * ((unsigned)y[b] + (unsigned)F.n1 * (unsigned)z[c]);
+      const T* ra = fa + row;
+      T xa = T(0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xa += wx[a] * ra[x[a]];
+      ya += wy[b] * xa;
+      if (fb) {
+        const T* rb = fb + row;
+        T xb = T(0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xb += wx[a] * rb[x[a]];
+        yb += wy[b] * xb;
+      }
+    }
+    sa += wz[c] * ya;
+    sb += wz[c] * yb;
+  }
+  const unsigned J = (unsigned)(J0 + C.n0 * (J1 + C.n1 * J2));
+  ca[J] = sa;
+  if (cb) cb[J] = sb;
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_taps(const Xfer<T>& X, int a, int i, int nf, int* j, T* w) {
+  if (i > 0 && i < nf - 1) {
+    const int J = i >> 1;
+    j[0] = J;
+    w[0] = T(0.75);
+    j[1] = (i & 1) ? J + 1 : J - 1;
+    w[1] = T(0.25);
+    return;
+  }
+  const int c = X.pc[a][i];
+  j[0] = X.pj[a][2 * i];
+  w[0] = X.pw[a][2 * i];
+  j[1] = c > 1 ? X.pj[a][2 * i + 1] : j[0];
+  w[1] = c > 1 ? X.pw[a][2 * i + 1] : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_nested(Level<T> F, Level<T> C, Xfer<T> X) {
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i2 = blockIdx.z;
+  if (i0 >= F.n0) return;
+  int jx[2], jy[2], jz[2];
+  T wx[2], wy[2], wz[2];
+  prolong_taps<T>(X, 0, i0, F.n0, jx, wx);
+  prolong_taps<T>(X, 1, i1, F.n1, jy, wy);
+  prolong_taps<T>(X, 2, i2, F.n2, jz, wz);
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (wz[c] == T(0)) continue;
+    T sy = T(0);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (wy[b] == T(0)) continue;
+      const unsigned row = (unsigned)C.n0 * ((unsigned)jy[b] + (unsigned)C.n1 * (unsigned)jz[c]);
+      T sx = T(0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) sx += wx[a] * (C.u[row + jx[a]] - C.ubar[row + jx[a]]);
+      sy += wy[b] * sx;
+    }
+    s += wz[c] * sy;
+  }
+  const unsigned i = (unsigned)(i0 + F.n0 * (i1 + F.n1 * i2));
+  F.u[i] += s;
+}
+
+inline bool nested_levels(int fn0, int fn1, int fn2, int cn0, int cn1, int cn2) {
+  const int f[3] = {fn0, fn1, fn2}, c[3] = {cn0, cn1, cn2};
+  for (int a = 0; a < 3; ++a)
+    if (!(f[a] == 2 * c[a] || (f[a] == 1 && c[a] == 1))) return false;
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -250,6 +402,20 @@ struct Dispatch {
     else if (model == GARDNER) k_sweep<T, FORM, GARDNER><<<g.grid, g.block, 0, s>>>(L, P, color);
     else k_sweep<T, FORM, VANGENUCHTEN><<<g.grid, g.block, 0, s>>>(L, P, color);
   }
+  template <int ZC>
+  static void sweep_pipe_z(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
+    Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
+    g.grid.z = (L.n2 + ZC - 1) / ZC;
+    if (model == HAVERKAMP) k_sweep_pipe<T, FORM, HAVERKAMP, ZC><<<g.grid, g.block, 0, s>>>(L, P, color);
+    else if (model == GARDNER) k_sweep_pipe<T, FORM, GARDNER, ZC><<<g.grid, g.block, 0, s>>>(L, P, color);
+    else k_sweep_pipe<T, FORM, VANGENUCHTEN, ZC><<<g.grid, g.block, 0, s>>>(L, P, color);
+  }
+  static void sweep_pipe(const Level<T>& L, const Phys<T>& P, int model, int color, int planes, cudaStream_t s) {
+    if (planes <= 1 || L.n2 < 2) sweep(L, P, model, color, s);
+    else if (planes == 2) sweep_pipe_z<2>(L, P, model, color, s);
+    else if (planes == 4) sweep_pipe_z<4>(L, P, model, color, s);
+    else sweep_pipe_z<8>(L, P, model, color, s);
+  }
   static void residual(const Level<T>& L, const Phys<T>& P, int model, unsigned long long* norm,
                        cudaStream_t s) {
     const Launch3 g = launch3(L.n0, L.n1, L.n2);
@@ -266,11 +432,17 @@ struct Dispatch {
   static void restrict2(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, const T* fa, const T* fb,
                         T* ca, T* cb, cudaStream_t s) {
     const Launch3 g = launch3(C.n0, C.n1, C.n2);
-    k_restrict<T><<<g.grid, g.block, 0, s>>>(F, C, X, fa, fb, ca, cb);
+    if (nested_levels(F.n0, F.n1, F.n2, C.n0, C.n1, C.n2))
+      k_restrict_nested<T><<<g.grid, g.block, 0, s>>>(F, C, fa, fb, ca, cb);
+    else
+      k_restrict<T><<<g.grid, g.block, 0, s>>>(F, C, X, fa, fb, ca, cb);
   }
   static void prolong(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, cudaStream_t s) {
     const Launch3 g = launch3(F.n0, F.n1, F.n2);
-    k_prolong<T><<<g.grid, g.block, 0, s>>>(F, C, X);
+    if (nested_levels(F.n0, F.n1, F.n2, C.n0, C.n1, C.n2))
+      k_prolong_nested<T><<<g.grid, g.block, 0, s>>>(F, C, X);
+    else
+      k_prolong<T><<<g.grid, g.block, 0, s>>>(F, C, X);
   }
   static void tail(const Level<T>* dLs, const Xfer<T>* dXs, int l0, int nl, const Phys<T>& P, int model,
                    int nu1, int nu2, int cmax, T crtol, int gamma, int gamma_levels, unsigned long long* stats,

@@ -37,7 +37,7 @@ void tail64(const Level<double>* dLs, const Xfer<double>* dXs, int l0, int nl, c
             cudaStream_t s);
 
 // FP32, correction delta as unknown
-void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, cudaStream_t s);
+void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, int planes, cudaStream_t s);
 void residual32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,
                 cudaStream_t s);
 void tau32(const Level<float>& C, const Phys<float>& P, int model, cudaStream_t s);
@@ -72,6 +72,11 @@ void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, con
                     const double* p1, const double* p2, const Phys<double>& P, const DDPhys& Q, int model,
                     int scheme, double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
                     const double* thm_in, double* thn_out, double* thm_out, cudaStream_t s);
+// water balance of a step: per-block partial sums into part (returns the
+// block count) and min_i(a theta' + S' + xi) as float bits into *dmin_bits
+int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const Phys<double>& P, const Phys<float>& Pf,
+                 int model, const double* psin, const double* psinm1, int scheme, double dt, const double* th_new,
+                 const double* th_n, const double* th_nm1, double* part, unsigned* dmin_bits, cudaStream_t s);
 void restrict_face32(const Geom& F, const Geom& C, const Xfer<float>& X, int axis, const float* fine, float* coarse,
                      cudaStream_t s);
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);

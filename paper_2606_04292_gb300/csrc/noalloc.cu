@@ -418,6 +418,8 @@ extern "C" richards_status richards_step_small_noalloc(const richards_grid* grid
     info->resid0 = stats[1];
     info->resid = stats[2];
     info->cell_updates = (long long)stats[4];
+    info->mass_defect = NAN;    // not computed on this path
+    info->err_bound = NAN;
   }
   return (richards_status)(int)stats[3];
 }

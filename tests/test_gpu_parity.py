@@ -288,6 +288,50 @@ def test_mixed_precision_within_stated_bound(mk):
         prev, cur = cur, psi_m
 
 
+WATER_PROBLEMS = [
+    ("1d_vg_sink_flux_xi", lambda: W.with_opts(W.random_problem(1, 64, W.VANGENUCHTEN, 2, bc_kinds=[W.FREE_DRAINAGE,
+                                                                                                  W.FLUX],
+                                                              hetero=True, sink=True, scheme=2), xi=3e-4)),
+    ("2d_gardner_mixed_bc", lambda: W.random_problem(2, (23, 18), W.GARDNER, 3,
+                                                     bc_kinds=[W.DIRICHLET, W.NOFLUX, W.FREE_DRAINAGE, W.FLUX],
+                                                     hetero=True, scheme=2)),
+    ("3d_vg_hetero_sink", lambda: W.random_problem(3, (17, 12, 9), W.VANGENUCHTEN, 4, hetero=True, sink=True)),
+]
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in WATER_PROBLEMS], ids=[p[0] for p in WATER_PROBLEMS])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_water_balance_and_error_bound_of_each_step(mk, precision):
+    """info.mass_defect equals the oracle's water balance of the GPU state
+    (sum V (a theta - hist + S + xi (psi - psi*)) - boundary inflow, over a);
+    info.err_bound bounds the distance to the oracle's tight solution."""
+    prob = W.with_opts(mk(), precision=precision)
+    gs = R.Solver(prob)
+    orc = Oracle(W.with_opts(prob, tol=1e-13, newton_iters=0))
+    xi = prob["opts"]["xi"]
+    cur, prev = np.array(prob["psi0"], dtype=np.float64), None
+    for k in range(3):
+        st, info = gs.step(prob["dt"], prob["scheme"], check=False)
+        assert st == R.RICH_OK, info
+        psi = gs.state()
+        orc.set_state(cur, prev)
+        orc.prepare(prob["dt"], info["scheme_used"])
+        V, a = orc.cell_volume(), orc.a
+        hist, pstar = orc.array(7), orc.array(6)
+        th = np.array([orc.soil(i, x)[0] for i, x in enumerate(psi)])
+        S = np.array([orc.sink(i, x)[0] for i, x in enumerate(psi)])
+        Q = orc.boundary_inflow(psi)
+        want = (V * np.sum(a * th - hist) + V * np.sum(S) + xi * V * np.sum(psi - pstar) - Q) / a
+        scale = (V * (np.sum(np.abs(a * th)) + np.sum(np.abs(hist))) + abs(Q)) / a
+        assert abs(info["mass_defect"] - want) <= 1e-11 * scale, (k, info["mass_defect"], want, scale)
+        orc.set_state(cur, prev)
+        assert orc.step(prob["dt"], info["scheme_used"])[0] == ORC_OK
+        err = np.max(np.abs(psi - orc.state()))
+        if np.isfinite(info["err_bound"]):
+            assert err <= info["err_bound"] * (1 + 1e-6) + 1e-15, (k, err, info["err_bound"])
+        prev, cur = cur, psi
+
+
 def test_mixed_precision_reaches_fp64_solution_at_tight_tolerance():
     """The FP64 outer correction is not limited by FP32: at tol 1e-13 the
     mixed result equals the FP64 solution to 1e-9."""
