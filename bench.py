@@ -36,6 +36,11 @@ WORKLOAD = "3D drainage 256^3, heterogeneous VG (lognormal Ks, sigma_lnK=1, corr
 # launch covers; a half-sweep covers the cells of one colour).  The NGS
 # figure is the mixed-mode inner update of the heterogeneous workload:
 # delta read+write, Kc, r, psi0, alpha, n (7 x 4 B).
+# DRAM bytes (read + write) per launch of the finest level's half-sweep of
+# 256^3 (8,388,608 cells), from an ncu capture of this kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum); the roofline's traffic.
+TRAFFIC_PER_LAUNCH = {("sweep32", 8388608): 459.2e6}
+
 BYTES_PER_CELL = {
     "sweep32": 28.0,
     "residual32": 28.0,
@@ -164,7 +169,8 @@ def roofline(prof, steps, ms_pass):
         achieved = bytes_per_launch / (ms / max(launches, 1) * 1e-3) / 1e9
         out.update({"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / pk["hbm_gbs"], "peak_source": src + " hbm_gbs",
-                    "algorithmic_bytes_per_launch": bytes_per_launch, "traffic": None})
+                    "algorithmic_bytes_per_launch": bytes_per_launch,
+                    "traffic": TRAFFIC_PER_LAUNCH.get((dom, round(cells / max(launches, 1))))})
     else:
         out.update({"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": None,
                     "traffic": None})

@@ -410,8 +410,10 @@ struct Dispatch {
     else if (model == GARDNER) k_sweep_pipe<T, FORM, GARDNER, ZC><<<g.grid, g.block, 0, s>>>(L, P, color);
     else k_sweep_pipe<T, FORM, VANGENUCHTEN, ZC><<<g.grid, g.block, 0, s>>>(L, P, color);
   }
+  // (levels below 2^20 cells keep one cell per thread: latency, not load
+  // throughput, bounds them)
   static void sweep_pipe(const Level<T>& L, const Phys<T>& P, int model, int color, int planes, cudaStream_t s) {
-    if (planes <= 1 || L.n2 < 2) sweep(L, P, model, color, s);
+    if (planes <= 1 || L.n2 < 2 || L.ncell < (1LL << 20)) sweep(L, P, model, color, s);
     else if (planes == 2) sweep_pipe_z<2>(L, P, model, color, s);
     else if (planes == 4) sweep_pipe_z<4>(L, P, model, color, s);
     else sweep_pipe_z<8>(L, P, model, color, s);
