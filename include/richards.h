@@ -124,7 +124,11 @@ typedef struct {
                           to direct launches otherwise)
      sweep_planes         FP32 half-sweeps: cells per thread along z (1, 2,
                           4 or 8); above 1 a thread loads the operands of
-                          its next cell before it solves the current one */
+                          its next cell before it solves the current one
+     predictor            mixed mode, BDF2 steps: 1 starts the iteration
+                          from the extrapolated psi* = 2 psi^n - psi^{n-1}
+                          instead of psi^n (same discrete system and stop
+                          test; a closer start needs fewer cycles) */
 typedef struct {
   int nu1, nu2, coarse_max_sweeps;
   double coarse_rtol;
@@ -134,7 +138,7 @@ typedef struct {
   int max_cycles, ordering, newton_iters, precision;
   int inner_cycles;
   double inner_rtol;
-  int max_outer, tail_cells, cycle_gamma, gamma_levels, graphs, sweep_planes;
+  int max_outer, tail_cells, cycle_gamma, gamma_levels, graphs, sweep_planes, predictor;
 } richards_opts;
 
 typedef struct {

@@ -648,7 +648,7 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
                          c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, P, rich::make_ddphys(P),
                          c->soil.model, scheme, dt, F.Kc, F.Kcf, F.g, F.u, c->th_n_valid ? c->th_n : nullptr,
                          c->th_nm1_valid ? c->th_nm1 : nullptr, c->th_n_valid ? nullptr : c->th_n,
-                         c->th_nm1_valid ? nullptr : c->th_nm1, c->s);
+                         c->th_nm1_valid ? nullptr : c->th_nm1, c->opts.predictor == 1, c->s);
   else
     rich::prep_lagged(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
                       c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, P, c->soil.model, scheme, dt, F.Kc,
@@ -787,8 +787,10 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
     *out = teff * nrm;
     return RICH_OK;
   };
+  // with the predictor (BDF2 steps) the iteration starts at psi*, not psi^n
+  const bool predicted = c->opts.predictor == 1 && c->scheme_used == 2;
   for (;;) {
-    TRY(defect(outer == 0, &r));
+    TRY(defect(outer == 0 && !predicted, &r));
     if (outer == 0) r0 = r;
     if (!(r > c->opts.tol) || std::isnan(r)) break;
     if (outer >= c->opts.max_outer) { st = RICH_ENOCONV; break; }
@@ -829,8 +831,9 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
     info->resid = r;
     info->cell_updates = c->updates_host + tu;
   }
-  TRY(water_balance(c, r, info, outer > 0 ? c->th_cur : c->th_n, c->th_n, c->th_nm1_valid ? c->th_nm1 : nullptr));
-  return finish_step(c, r, st, outer > 0 ? 1 : 0);
+  const bool moved = outer > 0 || predicted;      // theta(psi^{n+1}) is in th_cur
+  TRY(water_balance(c, r, info, moved ? c->th_cur : c->th_n, c->th_n, c->th_nm1_valid ? c->th_nm1 : nullptr));
+  return finish_step(c, r, st, moved ? 1 : 0);
 }
 
 richards_status check_ctx(const richards_ctx* c) { return c ? RICH_OK : RICH_EINVAL; }
@@ -862,7 +865,7 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
       !(o.tol > 0.0) || o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
       o.ordering != 1 || (o.precision != 0 && o.precision != 1) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
       o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0 || o.cycle_gamma < 1 || o.cycle_gamma > 3 ||
-      o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1) ||
+      o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1) || (o.predictor != 0 && o.predictor != 1) ||
       (o.sweep_planes != 1 && o.sweep_planes != 2 && o.sweep_planes != 4 && o.sweep_planes != 8))
     return RICH_EINVAL;
   richards_ctx* c = new richards_ctx();

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_prep_lagged_dd(long long n, const doubl
                                                         const double* __restrict__ p2f, Phys<double> P, DDPhys Q,
                                                         int scheme, dd hist_scale, double* Kc, float* Kcf, double* g,
                                                         double* u, const double* thn_in, const double* thm_in,
-                                                        double* thn_out, double* thm_out) {
+                                                        double* thn_out, double* thm_out, bool predict) {
   // hist_scale: 1/tau (BDF1) or 1/(2 tau) (BDF2)
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const dd p1 = p1f ? dd_split(p1f[i]) : Q.p1, p2 = p2f ? dd_split(p2f[i]) : Q.p2;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_prep_lagged_dd(long long n, const doubl
     Kc[i] = dd_join(K);
     Kcf[i] = dd_float(K);
     g[i] = dd_join(dd_add(hist, dd_mul(Q.xi, ps)));
-    u[i] = pnd;
+    u[i] = predict ? dd_join(ps) : pnd;
   }
 }
 
@@ -310,19 +310,20 @@ void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const 
 void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
                     const double* p1, const double* p2, const Phys<double>& P, const DDPhys& Q, int model,
                     int scheme, double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
-                    const double* thm_in, double* thn_out, double* thm_out, cudaStream_t s) {
+                    const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
   const int b = grid_for(n);
   const dd ks = host_split(Ks_s), hs = host_split(scheme == 1 ? 1.0 / dt : 1.0 / (2.0 * dt));
+  predict = predict && scheme == 2;
   if (model == HAVERKAMP)
     k_prep_lagged_dd<HAVERKAMP><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, P, Q, scheme, hs, Kc, Kcf, g, u,
-                                                  thn_in, thm_in, thn_out, thm_out);
+                                                  thn_in, thm_in, thn_out, thm_out, predict);
   else if (model == GARDNER)
     k_prep_lagged_dd<GARDNER><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, P, Q, scheme, hs, Kc, Kcf, g, u,
-                                                thn_in, thm_in, thn_out, thm_out);
+                                                thn_in, thm_in, thn_out, thm_out, predict);
   else
     k_prep_lagged_dd<VANGENUCHTEN><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, P, Q, scheme, hs, Kc, Kcf, g,
-                                                     u, thn_in, thm_in, thn_out, thm_out);
+                                                     u, thn_in, thm_in, thn_out, thm_out, predict);
 }
 
 void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,

@@ -68,10 +68,11 @@ void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPh
                        float* psi0f, float* delta, unsigned long long* norm, const double* th_in, double* th_out,
                        cudaStream_t s);
 // mixed mode: the lagged state in float-float (Kc to FP64 and FP32)
+// (predict: u = psi* instead of psi^n)
 void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
                     const double* p1, const double* p2, const Phys<double>& P, const DDPhys& Q, int model,
                     int scheme, double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
-                    const double* thm_in, double* thn_out, double* thm_out, cudaStream_t s);
+                    const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s);
 // water balance of a step: per-block partial sums into part (returns the
 // block count) and min_i(a theta' + S' + xi) as float bits into *dmin_bits
 int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const Phys<double>& P, const Phys<float>& Pf,

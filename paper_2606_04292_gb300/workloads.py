@@ -62,7 +62,7 @@ def default_opts(**kw):
              newton_iters=2,      # 0 = to tolerance; k > 0 = exactly k steps
              precision=0,         # 0 = FP64 plain, 1 = FP32 inner / FP64 outer
              inner_cycles=8, inner_rtol=1e-3, max_outer=20,
-             tail_cells=4096, cycle_gamma=1, gamma_levels=0, graphs=1, sweep_planes=2)
+             tail_cells=4096, cycle_gamma=1, gamma_levels=0, graphs=1, sweep_planes=2, predictor=0)
     o.update(kw)
     return o
 
@@ -171,9 +171,10 @@ def drainage_3d(n=256, dt=300.0, nsteps=50, seed_ks=3, seed_vg=4, **optkw):
     # as full W-cycles, and two coarsest sweeps are enough.  Each FP32 inner
     # solve reduces its defect 1e4-fold (two outer corrections reach tol
     # 1e-8; 1e3 takes three), and levels of up to 512 cells run in the
-    # single-block tail.
+    # single-block tail.  One safeguarded Newton step per point update gives
+    # the same cycles per step here as two (10.5 vs 10.3) in 8% less time.
     opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0, precision=1, cycle_gamma=2, gamma_levels=2,
-                        coarse_max_sweeps=2, inner_rtol=1e-4, tail_cells=512)
+                        coarse_max_sweeps=2, inner_rtol=1e-4, tail_cells=512, newton_iters=1)
     opts.update(optkw)
     return dict(name=f"drainage3d_n{n}", dim=3, n=(n, n, n), L=(1.0, 1.0, 1.0),
                 soil=soil, bc=bc, sink=no_sink(),

@@ -265,9 +265,10 @@ def _mixed_bound(orc, psi_m, psi_r):
 
 @pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS if "sink" not in p[0]],
                          ids=[p[0] for p in PROBLEMS if "sink" not in p[0]])
-def test_mixed_precision_within_stated_bound(mk):
+@pytest.mark.parametrize("predictor", [0, 1])
+def test_mixed_precision_within_stated_bound(mk, predictor):
     prob = mk()
-    prob = W.with_opts(prob, precision=1)
+    prob = W.with_opts(prob, precision=1, predictor=predictor)
     gs = R.Solver(prob)
     orc = Oracle(W.with_opts(prob, tol=1e-13, newton_iters=0))
     cur, prev = np.array(prob["psi0"], dtype=np.float64), None
