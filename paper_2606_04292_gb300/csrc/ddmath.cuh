@@ -8,9 +8,10 @@
 // inside the 1e-8 stop test and the 1e-12 stage tolerance, at a small
 // fraction of the FP64 cost.
 //
-//   exp:  Cody-Waite reduction x = k ln2 + r with ln2 split in three floats
-//         (k c1 exact), r scaled by 1/16, expm1 by its Taylor series to degree
-//         7, then four doublings y <- y (y + 2) and the exact scaling by 2^k;
+//   exp:  table-driven reduction by ln2/32 (Tang's method), a short Taylor
+//         series for the remainder, then the exact scaling by 2^m;
+//   expm1 of a small argument: the remainder scaled by 1/16, Taylor to
+//         degree 7, four doublings y <- y (y + 2);
 //   log:  one Newton step on exp from the single-precision logf:
 //         log x = y0 + log1p(x e^{-y0} - 1), the log1p of a ~1e-7 argument
 //         taken to second order;
@@ -106,14 +107,45 @@ __device__ __forceinline__ dd dd_expm1_core(dd r) {
   return y;
 }
 
-// e^x for |x| <= DD_EXP_MAX (the scale 2^k and the low word stay normal floats)
+// 2^(j/32), j = 0..31, as float pairs (hi + lo within 1.5e-15 relative)
+static __device__ const float2 kExp2Frac[32] = {
+    {0x1.000000p+0f, 0x0.0p+0f},          {0x1.059b0ep+0f, -0x1.9d4f52p-25f},
+    {0x1.0b5586p+0f, 0x1.9f3122p-25f},    {0x1.11301ep+0f, -0x1.fdb496p-25f},
+    {0x1.172b84p+0f, -0x1.c15742p-27f},   {0x1.1d4874p+0f, -0x1.d2e8cap-25f},
+    {0x1.2387a6p+0f, 0x1.ceac48p-25f},    {0x1.29e9e0p+0f, -0x1.5c0424p-25f},
+    {0x1.306fe0p+0f, 0x1.4636e2p-25f},    {0x1.371a74p+0f, -0x1.18aac6p-25f},
+    {0x1.3dea64p+0f, 0x1.824684p-25f},    {0x1.44e086p+0f, 0x1.8624b4p-30f},
+    {0x1.4bfdaep+0f, -0x1.593abcp-25f},   {0x1.5342b6p+0f, -0x1.2c5610p-25f},
+    {0x1.5ab07ep+0f, -0x1.5bd5ecp-27f},   {0x1.6247ecp+0f, -0x1.f8b550p-25f},
+    {0x1.6a09e6p+0f, 0x1.9fcef4p-26f},    {0x1.71f75ep+0f, 0x1.1d8beep-25f},
+    {0x1.7a1148p+0f, -0x1.829fd0p-25f},   {0x1.82589ap+0f, -0x1.accc7cp-26f},
+    {0x1.8ace54p+0f, 0x1.15506ep-27f},    {0x1.93737cp+0f, -0x1.e64744p-25f},
+    {0x1.9c4918p+0f, 0x1.51f848p-27f},    {0x1.a5503cp+0f, -0x1.b83b54p-25f},
+    {0x1.ae89fap+0f, -0x1.a94b14p-26f},   {0x1.b7f770p+0f, -0x1.a09438p-25f},
+    {0x1.c199bep+0f, -0x1.3d56b2p-27f},   {0x1.cb720ep+0f, -0x1.8837ccp-27f},
+    {0x1.d5818ep+0f, -0x1.822dbcp-27f},   {0x1.dfc974p+0f, -0x1.908c94p-25f},
+    {0x1.ea4afap+0f, 0x1.52486cp-27f},    {0x1.f50766p+0f, -0x1.246eb0p-26f}};
+
+// e^x for |x| <= ~70 (the scale and the low word stay normal floats):
+// table-driven reduction (Tang's method) x = (32 m + j) ln2/32 + r,
+// |r| <= ln2/64, with ln2/32 in three floats (the first with 12 significant
+// bits, so k times it is exact for |k| < 4096); e^r - 1 by its Taylor series
+// (terms to r^3 in float-float, r^4 .. r^6 in float); e^x = 2^m 2^(j/32)(1 + p).
 __device__ __forceinline__ dd dd_exp(dd x) {
-  const float k = rintf(x.hi * RICH_INV_LN2);
-  dd r = dd_add(x, mk(-k * RICH_LN2_C1));
-  r = dd_add(r, dd_neg(two_prod(k, RICH_LN2_C2)));
-  r = dd_add(r, mk(-k * RICH_LN2_C3));
-  const dd e = dd_add(mk(1.0f), dd_expm1_core(r));
-  const float s = __int_as_float((127 + (int)k) << 23);   // 2^k; |k| <= 100 for the arguments used here
+  const float kf = rintf(x.hi * (32.0f * RICH_INV_LN2));
+  const int k = (int)kf;
+  dd r = dd_add(x, mk(-kf * (RICH_LN2_C1 * 0.03125f)));
+  r = dd_add(r, dd_neg(two_prod(kf, RICH_LN2_C2 * 0.03125f)));
+  r = dd_add(r, mk(-kf * (RICH_LN2_C3 * 0.03125f)));
+  const float rf = r.hi;
+  const float q = rf * rf * fmaf(rf, fmaf(rf, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f);
+  dd b = dd_add(mk(0.5f), dd_mul(r, mk(RICH_INV6_HI, RICH_INV6_LO)));
+  b = dd_add(b, mk(q));
+  const dd p = dd_add(r, dd_mul(dd_mul(r, r), b));       // e^r - 1
+  const float2 t = kExp2Frac[k & 31];
+  const dd T = mk(t.x, t.y);
+  const dd e = dd_add(T, dd_mul(T, p));
+  const float s = __int_as_float((127 + (k >> 5)) << 23);   // 2^m, m = floor(k/32)
   return mk(e.hi * s, e.lo * s);
 }
 
