@@ -451,7 +451,9 @@ __device__ __forceinline__ void storage(T x, T psi0, T p1, T p2, T smax, const P
 // Scalar solve of  storage(x) + cc x = f  (eq. point-update).  The left side
 // increases strictly (cc > 0), the root lies in [lo, hi]; Newton from x0,
 // bisection whenever a step leaves the current bracket.
-template <typename T, int FORM, int MODEL>
+// NK > 0: exactly NK steps fixed at compile time (must equal P.newton_k);
+// NK = 0: P.newton_k steps (0: to round-off).
+template <typename T, int FORM, int MODEL, int NK = 0>
 __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T smax,
                                          const Phys<T>& P) {
   if (!(cc > T(0))) {
@@ -474,7 +476,7 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
     hi = (f + P.a * ds + smax) * rc;
   }
   T x = x0 < lo ? lo : (x0 > hi ? hi : x0);
-  const int maxit = P.newton_k > 0 ? P.newton_k : 200;
+  const int maxit = NK > 0 ? NK : (P.newton_k > 0 ? P.newton_k : 200);
   DBase B;
   T sa0 = T(0), sda0 = T(0);
   int sk0 = 0;
@@ -482,6 +484,7 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
     B = dbase<MODEL>(psi0, p1, p2);
     if (P.sink && smax > T(0)) sk0 = feddes(psi0, P, sa0, sda0);
   }
+#pragma unroll(NK > 0 ? NK : 1)
   for (int it = 0; it < maxit; ++it) {
     T val, der;
     if constexpr (FORM == FORM_DELTA) {
@@ -522,7 +525,7 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
   return x;
 }
 
-template <typename T, int FORM, int MODEL>
+template <typename T, int FORM, int MODEL, int NK = 0>
 __device__ __forceinline__ void point_update(const Level<T>& L, const Phys<T>& P, long long i,
                                              int i0, int i1, int i2) {
   T mii, off;
@@ -534,7 +537,7 @@ __device__ __forceinline__ void point_update(const Level<T>& L, const Phys<T>& P
   const T p2 = L.p2 ? L.p2[i] : P.p2;
   const T smax = L.smax ? L.smax[i] : T(0);
   const T psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
-  L.u[i] = point_solve<T, FORM, MODEL>(cc, f, ui, psi0, p1, p2, smax, P);
+  L.u[i] = point_solve<T, FORM, MODEL, NK>(cc, f, ui, psi0, p1, p2, smax, P);
 }
 
 // Operands of one point update, gathered before any of them is used, so that
@@ -586,7 +589,7 @@ __device__ __forceinline__ void gather(const Level<T>& L, const Phys<T>& P, int 
 
 // the point update of a gathered cell (same sums, in the same order, as
 // stencil() and point_update())
-template <typename T, int FORM, int MODEL>
+template <typename T, int FORM, int MODEL, int NK = 0>
 __device__ __forceinline__ T solve_cell(const Level<T>& L, const Phys<T>& P, const CellOps<T>& c) {
   T dg = T(0), of = T(0);
 #pragma unroll
@@ -602,7 +605,7 @@ __device__ __forceinline__ T solve_cell(const Level<T>& L, const Phys<T>& P, con
   }
   const T cc = P.xi + P.kappa + dg;
   const T f = c.g + of + P.kappa * c.ui;
-  return point_solve<T, FORM, MODEL>(cc, f, c.ui, c.psi0, c.p1, c.p2, c.smax, P);
+  return point_solve<T, FORM, MODEL, NK>(cc, f, c.ui, c.psi0, c.p1, c.p2, c.smax, P);
 }
 
 // N(u)_i = storage(u_i) + xi u_i + m_ii u_i - sum_j m_ij u_j   (eq. Nh-def)

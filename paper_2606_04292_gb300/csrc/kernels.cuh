@@ -23,21 +23,21 @@ __device__ __forceinline__ float from_bits<float>(unsigned long long b) {
 // colour; cells of one colour do not couple, so the update is parallel).
 // ---------------------------------------------------------------------------
 // Launch grid: x = pairs of cells along a row, y = row, z = plane.
-template <typename T, int FORM, int MODEL>
+template <typename T, int FORM, int MODEL, int NK = 0>
 __global__ void __launch_bounds__(256) k_sweep(Level<T> L, Phys<T> P, int color) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int i1 = blockIdx.y, i2 = blockIdx.z;
   const int i0 = 2 * p + ((color + i1 + i2) & 1);
   if (i0 >= L.n0) return;
   const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
-  point_update<T, FORM, MODEL>(L, P, i, i0, i1, i2);
+  point_update<T, FORM, MODEL, NK>(L, P, i, i0, i1, i2);
 }
 
 // The same half-sweep with ZC planes per thread, software-pipelined: the
 // operands of the next plane's cell are loaded before the current cell is
 // solved.  Launch grid: x = pairs of cells along a row, y = row, z = chunk
 // of ZC planes.
-template <typename T, int FORM, int MODEL, int ZC>
+template <typename T, int FORM, int MODEL, int ZC, int NK = 0>
 __global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int color) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int i1 = blockIdx.y;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int c
       if (nx.valid) gather<T, FORM>(L, P, i0, i1, i2, nx);
     }
     const CellOps<T>& cur = c[k & 1];
-    if (cur.valid) L.u[cur.i] = solve_cell<T, FORM, MODEL>(L, P, cur);
+    if (cur.valid) L.u[cur.i] = solve_cell<T, FORM, MODEL, NK>(L, P, cur);
   }
 }
 
@@ -396,19 +396,33 @@ inline Launch3 launch3(int nx, int n1, int n2) {
 
 template <typename T, int FORM>
 struct Dispatch {
-  static void sweep(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
+  template <int NK>
+  static void sweep_nk(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
     const Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
-    if (model == HAVERKAMP) k_sweep<T, FORM, HAVERKAMP><<<g.grid, g.block, 0, s>>>(L, P, color);
-    else if (model == GARDNER) k_sweep<T, FORM, GARDNER><<<g.grid, g.block, 0, s>>>(L, P, color);
-    else k_sweep<T, FORM, VANGENUCHTEN><<<g.grid, g.block, 0, s>>>(L, P, color);
+    if (model == HAVERKAMP) k_sweep<T, FORM, HAVERKAMP, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+    else if (model == GARDNER) k_sweep<T, FORM, GARDNER, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+    else k_sweep<T, FORM, VANGENUCHTEN, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+  }
+  // the FP32 increment form compiles the common fixed step counts 1 and 2
+  static void sweep(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
+    if (FORM == FORM_DELTA && P.newton_k == 1) sweep_nk<(FORM == FORM_DELTA ? 1 : 0)>(L, P, model, color, s);
+    else if (FORM == FORM_DELTA && P.newton_k == 2) sweep_nk<(FORM == FORM_DELTA ? 2 : 0)>(L, P, model, color, s);
+    else sweep_nk<0>(L, P, model, color, s);
+  }
+  template <int ZC, int NK>
+  static void sweep_pipe_zk(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
+    Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
+    g.grid.z = (L.n2 + ZC - 1) / ZC;
+    if (model == HAVERKAMP) k_sweep_pipe<T, FORM, HAVERKAMP, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+    else if (model == GARDNER) k_sweep_pipe<T, FORM, GARDNER, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+    else k_sweep_pipe<T, FORM, VANGENUCHTEN, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
   }
   template <int ZC>
   static void sweep_pipe_z(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
-    Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
-    g.grid.z = (L.n2 + ZC - 1) / ZC;
-    if (model == HAVERKAMP) k_sweep_pipe<T, FORM, HAVERKAMP, ZC><<<g.grid, g.block, 0, s>>>(L, P, color);
-    else if (model == GARDNER) k_sweep_pipe<T, FORM, GARDNER, ZC><<<g.grid, g.block, 0, s>>>(L, P, color);
-    else k_sweep_pipe<T, FORM, VANGENUCHTEN, ZC><<<g.grid, g.block, 0, s>>>(L, P, color);
+    if (FORM == FORM_DELTA && P.newton_k == 1) sweep_pipe_zk<ZC, (FORM == FORM_DELTA ? 1 : 0)>(L, P, model, color, s);
+    else if (FORM == FORM_DELTA && P.newton_k == 2)
+      sweep_pipe_zk<ZC, (FORM == FORM_DELTA ? 2 : 0)>(L, P, model, color, s);
+    else sweep_pipe_zk<ZC, 0>(L, P, model, color, s);
   }
   // (levels below 2^20 cells keep one cell per thread: latency, not load
   // throughput, bounds them)
