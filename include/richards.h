@@ -107,11 +107,14 @@ typedef struct {
      ordering             1 = red-black (the only GPU ordering)
      newton_iters         k > 0: exactly k safeguarded Newton steps per point
                           update; 0: to round-off
-     precision            0 = FP64 throughout; 1 = FP32 inner V-cycles on the
-                          correction equation inside an FP64 defect
-                          correction (residual, stop test in FP64)
-     inner_cycles,        mixed mode: FP32 V-cycles per outer iteration, stop
-     inner_rtol, max_outer  early below inner_rtol x initial inner defect
+     precision            0 = FP64 throughout; 1 = FP32 inner cycles on the
+                          correction equation inside an outer defect
+                          correction (defect, laws and stop test in
+                          float-float arithmetic, ~1e-12 relative)
+     inner_cycles,        mixed mode: FP32 cycles per outer iteration, stop
+     inner_rtol, max_outer  early below max(inner_rtol, 0.3 tol / r) x the
+                          initial inner defect (r: the outer defect in theta
+                          units); at most max_outer outer iterations
      tail_cells           levels with at most this many cells run in one
                           thread block (the coarse tail of the V-cycle)
      cycle_gamma          coarse-grid visits per level: 1 = V-cycle (the
