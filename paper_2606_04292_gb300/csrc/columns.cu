@@ -2,10 +2,10 @@
 //
 // Each thread block takes columns from a device work queue (one atomic
 // counter over a longest-first order) and runs every time step of its column:
-// per-step preparation and the FP64 defect of the outer correction loop on
-// the column's slices of global arrays, and the FP32 FAS cycles of the inner
-// correction problem with the whole multigrid hierarchy of the column in
-// shared memory.  Columns are 1D (axis 0 is the vertical), of any length up
+// per-step preparation and the defect of the outer correction loop in
+// float-float arithmetic on the column's slices of global arrays, and the
+// FP32 FAS cycles of the inner correction problem with the whole multigrid
+// hierarchy of the column in shared memory.  Columns are 1D (axis 0 is the vertical), of any length up
 // to RICHARDS_COLUMN_MAX_CELLS, each with its own scalar soil parameters and
 // boundary conditions; one soil law for the whole batch.
 #include <algorithm>
@@ -49,41 +49,67 @@ struct ColArgs {
       model;
 };
 
+// The interpolation row of fine cell i (the same reading as the tables of the
+// multi-dimensional path: coarse coordinate ((2i+1) nc - nf)/(2 nf), a ghost
+// beyond an end folded into the end cell with factor slo/shi) in FP32 and
+// 32-bit integers: columns have at most RICHARDS_COLUMN_MAX_CELLS cells.
+__device__ __forceinline__ void interp_row_f(int nf, int nc, int i, float slo, float shi, int* idx, float* w,
+                                             int& cnt) {
+  cnt = 0;
+  auto add = [&](int j, float wt) {
+    if (wt == 0.0f) return;
+    for (int k = 0; k < cnt; ++k)
+      if (idx[k] == j) { w[k] += wt; return; }
+    idx[cnt] = j;
+    w[cnt] = wt;
+    ++cnt;
+  };
+  if (nf == 1) { add(0, 1.0f); return; }
+  const int num = (2 * i + 1) * nc - nf, den = 2 * nf;
+  const int J0 = num >= 0 ? num / den : -((-num + den - 1) / den);
+  const float wt = (float)(num - J0 * den) / (float)den;
+  const int J1 = J0 + 1;
+  if (J0 < 0) add(0, (1.0f - wt) * slo); else add(J0, 1.0f - wt);
+  if (J1 >= nc) add(nc - 1, wt * shi); else add(J1, wt);
+}
+
 // 1D hierarchy of one column in shared memory; transfer weights computed on
-// the fly (columns have arbitrary lengths), in the same order and precision
-// as the tables of the multi-dimensional path.
+// the fly (columns have arbitrary lengths) in FP32: R is the transpose of the
+// constant-extrapolation P with rows normalised to 1, P folds the ghost with
+// slo/shi (-1 on a Dirichlet end).
 struct ColumnLevels {
   const Level<float>* Ls;
-  double slo, shi;
+  float slo, shi;
   __device__ const Level<float>& L(int l) const { return Ls[l]; }
   __device__ float restrict(int l, const float* fine, int J0, int, int) const {
     const int nf = Ls[l].n0, nc = Ls[l + 1].n0;
     int ri[RMAX];
-    double rw[RMAX];
+    float rw[RMAX];
     int cnt = 0;
     const int lo = nf == 1 ? 0 : max(0, 2 * J0 - 4), hi = nf == 1 ? 0 : min(nf - 1, 2 * J0 + 4);
     for (int i = lo; i <= hi; ++i) {
       int idx[2];
-      double w[2];
+      float w[2];
       int c2;
-      interp_row(nf, nc, i, 1.0, 1.0, idx, w, c2);
+      interp_row_f(nf, nc, i, 1.0f, 1.0f, idx, w, c2);
       for (int k = 0; k < c2; ++k)
         if (idx[k] == J0 && cnt < RMAX) { ri[cnt] = i; rw[cnt] = w[k]; ++cnt; }
     }
-    double s = 0.0;
+    float s = 0.0f;
     for (int k = 0; k < cnt; ++k) s += rw[k];
+    const float inv = 1.0f / s;
     float acc = 0.0f;
-    for (int k = 0; k < cnt; ++k) acc += (float)(rw[k] / s) * 1.0f * 1.0f * fine[ri[k]];
+    for (int k = 0; k < cnt; ++k) acc += rw[k] * inv * fine[ri[k]];
     return acc;
   }
   __device__ float prolong(int l, int i0, int, int) const {
     const Level<float>& C = Ls[l + 1];
     int idx[2];
-    double w[2];
+    float w[2];
     int cnt;
-    interp_row(Ls[l].n0, C.n0, i0, slo, shi, idx, w, cnt);
+    interp_row_f(Ls[l].n0, C.n0, i0, slo, shi, idx, w, cnt);
     float acc = 0.0f;
-    for (int k = 0; k < cnt; ++k) acc += (float)w[k] * 1.0f * 1.0f * (C.u[idx[k]] - C.ubar[idx[k]]);
+    for (int k = 0; k < cnt; ++k) acc += w[k] * (C.u[idx[k]] - C.ubar[idx[k]]);
     return acc;
   }
 };
@@ -119,8 +145,8 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
   }
   __syncthreads();
   const int nl = *s_nl;
-  const ColumnLevels lv{Ls, (D.bc_kind[0] == RICH_BC_DIRICHLET) ? -1.0 : 1.0,
-                        (D.bc_kind[1] == RICH_BC_DIRICHLET) ? -1.0 : 1.0};
+  const ColumnLevels lv{Ls, (D.bc_kind[0] == RICH_BC_DIRICHLET) ? -1.0f : 1.0f,
+                        (D.bc_kind[1] == RICH_BC_DIRICHLET) ? -1.0f : 1.0f};
   // FP64 view of the finest level on the column's slices of global memory
   Level<double> G{};
   G.dim = 1; G.n0 = n; G.n1 = 1; G.n2 = 1; G.ncell = n;
@@ -162,23 +188,32 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
     const double a = scheme == 1 ? 1.0 / A.dt : 1.5 / A.dt;
     P64.a = a;
     P32.a = (float)a;
-    // ---- per-step preparation (FP64): lagged K, history, u = psi^n
+    const DDPhys Q = make_ddphys_dev(P64);
+    const dd Ks = dd_split(D.Ks);
+    const dd hist_scale = dd_split(scheme == 1 ? 1.0 / A.dt : 1.0 / (2.0 * A.dt));
+    // ---- per-step preparation (float-float): lagged K, history, u = psi^n
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const double pn = psin[i];
-      double th = th_valid ? thn[i] : theta_only_d<MODEL>(pn, D.p1, D.p2, P64);
-      if (!th_valid) thn[i] = th;
-      double ps, hist;
+      const double pnd = psin[i];
+      const dd pn = dd_split(pnd);
+      dd th;
+      if (th_valid) {
+        th = dd_split(thn[i]);
+      } else {
+        th = theta_x<MODEL>(pn, Q.p1, Q.p2, Q, P64);
+        thn[i] = dd_join(th);
+      }
+      dd ps, hist;
       if (scheme == 1) {
         ps = pn;
-        hist = th / A.dt;
+        hist = dd_mul(th, hist_scale);
       } else {
-        const double pm = psinm1[i];
-        ps = 2.0 * pn - pm;
-        hist = (4.0 * th - theta_only_d<MODEL>(pm, D.p1, D.p2, P64)) / (2.0 * A.dt);
+        const dd pm = dd_split(psinm1[i]);
+        ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
+        hist = dd_mul(dd_sub(mk(4.0f * th.hi, 4.0f * th.lo), theta_x<MODEL>(pm, Q.p1, Q.p2, Q, P64)), hist_scale);
       }
-      A.Kc[off + i] = cond_d<MODEL>(ps, D.p1, D.p2, D.Ks, P64);
-      G.g[i] = hist + A.xi * ps;
-      G.u[i] = pn;
+      A.Kc[off + i] = dd_join(cond_x<MODEL>(ps, Q.p1, Q.p2, Ks, Q, P64));
+      G.g[i] = dd_join(dd_add(hist, dd_mul(Q.xi, ps)));
+      G.u[i] = pnd;
     }
     th_valid = 1;
     __syncthreads();
@@ -215,34 +250,46 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
       if (threadIdx.x < 2) const_cast<float*>(Ls[l + 1].kb[threadIdx.x])[0] = Ls[l].kb[threadIdx.x][0];
       __syncthreads();
     }
-    // ---- FP64 defect correction around FP32 cycles
+    // ---- defect correction around FP32 cycles; the defect in float-float,
+    // interior fluxes in difference form m_f (u_i - u_j)
     const double teff = 1.0 / a;
+    const dd hs = dd_split(0.5 / (h * h)), s2 = dd_split(2.0 / (h * h));
+    const dd db0 = dd_mul(dd_split(kb64[0]), s2), db1 = dd_mul(dd_split(kb64[1]), s2);
     int outer = 0;
     bool fresh = false;
     for (;;) {
       unsigned long long mx = 0;
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double mii, offs;
-        stencil(G, i, i, 0, 0, G.u, mii, offs);
-        const double ui = G.u[i];
-        double th;
+        const dd ui = dd_split(G.u[i]), Ki = dd_split(G.Kc[i]);
+        dd flux = mk(0.0f), db = mk(0.0f);
+        if (i > 0)
+          flux = dd_add(flux, dd_mul(dd_mul(dd_add(Ki, dd_split(G.Kc[i - 1])), hs), dd_sub(ui, dd_split(G.u[i - 1]))));
+        else
+          db = dd_add(db, db0);
+        if (i + 1 < n)
+          flux = dd_add(flux, dd_mul(dd_mul(dd_add(Ki, dd_split(G.Kc[i + 1])), hs), dd_sub(ui, dd_split(G.u[i + 1]))));
+        else
+          db = dd_add(db, db1);
+        dd th;
         if (outer == 0) {
-          th = thn[i];
+          th = dd_split(thn[i]);
         } else {
-          th = theta_only_d<MODEL>(ui, D.p1, D.p2, P64);
-          thcur[i] = th;
+          th = theta_x<MODEL>(ui, Q.p1, Q.p2, Q, P64);
+          thcur[i] = dd_join(th);
         }
-        double S, dS;
-        sink_direct(ui, G.smax ? G.smax[i] : 0.0, P64, S, dS);
-        const double r = G.g[i] - (a * th + S + A.xi * ui + mii * ui - offs);
-        Ls[0].g[i] = (float)r;
-        const_cast<float*>(Ls[0].psi0)[i] = (float)ui;
+        const dd S = G.smax ? sink_x(ui, dd_split(G.smax[i]), Q) : mk(0.0f);
+        dd N = dd_add(dd_mul(Q.a, th), S);
+        N = dd_add(N, dd_mul(dd_add(Q.xi, db), ui));
+        N = dd_add(N, flux);
+        const float r = dd_float(dd_sub(dd_split(G.g[i]), N));
+        Ls[0].g[i] = r;
+        const_cast<float*>(Ls[0].psi0)[i] = dd_float(ui);
         Ls[0].u[i] = 0.0f;
         const unsigned long long b = nbits(r);
         mx = b > mx ? b : mx;
       }
       fresh = outer > 0;
-      const double nrm = __longlong_as_double((long long)block_max(mx, sm));
+      const double nrm = (double)__uint_as_float((unsigned)block_max(mx, sm));
       resid = teff * nrm;
       if (!(resid > A.tol) || isnan(resid)) break;
       if (outer >= A.max_outer) { status = RICH_ENOCONV; break; }

@@ -255,6 +255,28 @@ inline DDPhys make_ddphys(const Phys<double>& P) {
   return Q;
 }
 
+// the same split on the device (per-column soil parameters)
+__device__ __forceinline__ DDPhys make_ddphys_dev(const Phys<double>& P) {
+  DDPhys Q;
+  Q.a = dd_split(P.a);
+  Q.xi = dd_split(P.xi);
+  Q.ts = dd_split(P.ts);
+  Q.tr = dd_split(P.tr);
+  Q.ds = dd_split(P.ts - P.tr);
+  Q.p1 = dd_split(P.p1);
+  Q.p2 = dd_split(P.p2);
+  Q.p3 = dd_split(P.p3);
+  Q.p4 = dd_split(P.p4);
+  Q.h1 = dd_split(P.h1);
+  Q.h2 = dd_split(P.h2);
+  Q.h3 = dd_split(P.h3);
+  Q.h4 = dd_split(P.h4);
+  Q.r12 = dd_split(P.h1 != P.h2 ? 1.0 / (P.h1 - P.h2) : 0.0);
+  Q.r34 = dd_split(P.h3 != P.h4 ? 1.0 / (P.h3 - P.h4) : 0.0);
+  Q.sink = P.sink;
+  return Q;
+}
+
 // ---------------------------------------------------------------------------
 // Constitutive laws (Table 1) in float-float; same branches as law_d/cond_d.
 // Arguments outside the float range the routines are written for (a log of

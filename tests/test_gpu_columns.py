@@ -2,13 +2,15 @@
 oracle, column by column (needs a GPU).
 
 Each column is its own 1D problem; the batch solves all of them in one launch
-with FP32 inner cycles inside an FP64 defect correction.  At a tight tolerance
-every column must equal the oracle's FP64 solution; at the default tolerance
-the oracle's own FP64 stop test must hold for every column's result.
+with FP32 inner cycles inside a float-float defect correction.  At a tight
+tolerance every column must equal the oracle's FP64 solution; at the default
+tolerance the oracle's own FP64 stop test must hold for every column's result,
+up to the float-float law allowance (law_allowance).
 """
 import numpy as np
 import pytest
 
+from law_allowance import law_allowance
 from oracle.oracle import ORC_OK, Oracle
 from paper_2606_04292_gb300 import workloads as W
 
@@ -19,6 +21,8 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_2606_04292_gb300 import richards as R  # noqa: E402
+
+DD_EPS = 6e-12      # float-float laws and defect (the bound of the soil-law tests)
 
 
 def mixed_columns(ncol, seed, nmin=5, nmax=300, **optkw):
@@ -73,8 +77,10 @@ def test_columns_satisfy_oracle_stop_test(scheme):
             o = oracle_column(p)
             o.set_state(cols.column(cur_all, k), None if prev_all is None else cols.column(prev_all, k))
             used = o.prepare(p["dt"], scheme)
-            _, nrm = o.residual(cols.column(new_all, k))
-            assert nrm / o.a <= p["opts"]["tol"] * (1 + 1e-6), (k, used, nrm / o.a)
+            psi_k = cols.column(new_all, k)
+            _, nrm = o.residual(psi_k)
+            allow = law_allowance(o, p, psi_k, DD_EPS)
+            assert nrm / o.a <= p["opts"]["tol"] * (1 + 1e-6) + allow, (k, used, nrm / o.a, allow)
         prev_all, cur_all = cur_all, new_all
 
 
@@ -94,8 +100,9 @@ def test_queue_with_many_more_columns_than_blocks():
         o = oracle_column(probs[k])
         o.set_state(cols.column(psi0, k))
         o.prepare(probs[k]["dt"], 1)
-        _, nrm = o.residual(cols.column(psi, k))
-        assert nrm / o.a <= probs[k]["opts"]["tol"] * (1 + 1e-6), k
+        psi_k = cols.column(psi, k)
+        _, nrm = o.residual(psi_k)
+        assert nrm / o.a <= probs[k]["opts"]["tol"] * (1 + 1e-6) + law_allowance(o, probs[k], psi_k, DD_EPS), k
 
 
 def test_autotune_restores_state_and_matches_plain_run():

@@ -16,6 +16,7 @@ that much (_law_allowance), on top of the stop tolerance.
 import numpy as np
 import pytest
 
+from law_allowance import law_allowance
 from oracle.oracle import ORC_OK, Oracle
 from paper_2606_04292_gb300 import workloads as W
 
@@ -30,6 +31,10 @@ from paper_2606_04292_gb300 import richards as R  # noqa: E402
 STAGE_RTOL = 1e-12
 STEP_RTOL = 1e-10
 DD_EPS = 6e-12
+
+
+def _law_allowance(orc, prob, psi):
+    return law_allowance(orc, prob, psi, DD_EPS)
 
 
 def rel(a, b):
@@ -212,39 +217,6 @@ def test_strip_2d_bdf2_steps():
         sto, info_o = orc.step()
         assert st == sto
         assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
-
-
-def _law_allowance(orc, prob, psi):
-    """DD_EPS times, per cell, the magnitudes of the terms of g - N(psi) that
-    depend on K or theta (interior fluxes |m_f (psi_i - psi_j)|, Dirichlet
-    diagonals, gravity fluxes, |g|, a theta_s, |S|), max over cells, in theta
-    units (divided by a)."""
-    n0, n1, n2 = prob["n"]
-    dim = prob["dim"]
-    Kc = orc.Kc(0).reshape(n2, n1, n0)
-    P = np.asarray(psi, dtype=np.float64).reshape(n2, n1, n0)
-    h = [prob["L"][a] / prob["n"][a] for a in range(dim)]
-    tot = np.abs(orc.g(0)).reshape(n2, n1, n0) + orc.a * prob["soil"]["theta_s"]
-    for a in range(dim):
-        ax = 2 - a
-        sl_lo = [slice(None)] * 3
-        sl_hi = [slice(None)] * 3
-        sl_lo[ax], sl_hi[ax] = slice(0, -1), slice(1, None)
-        Kf = 0.5 * (Kc[tuple(sl_lo)] + Kc[tuple(sl_hi)])
-        flux = Kf / h[a] ** 2 * np.abs(P[tuple(sl_hi)] - P[tuple(sl_lo)])
-        if a == dim - 1:
-            flux = flux + Kf / h[a]                     # gravity
-        tot[tuple(sl_lo)] += flux
-        tot[tuple(sl_hi)] += flux
-        for side in range(2):
-            kb = orc.array(10 + 2 * a + side, 0)
-            edge = [slice(None)] * 3
-            edge[ax] = -1 if side else 0
-            bval = abs(prob["bc"]["value"][2 * a + side])
-            tot[tuple(edge)] += 2.0 * kb.reshape(tot[tuple(edge)].shape) / h[a] ** 2 * (np.abs(P[tuple(edge)]) + bval)
-    if prob["sink"]["enabled"]:
-        tot += orc.array(4, 0).reshape(n2, n1, n0)
-    return DD_EPS * float(np.max(tot)) / orc.a
 
 
 def _mixed_bound(orc, psi_m, psi_r):
