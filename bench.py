@@ -241,7 +241,8 @@ def cpu_baseline(prob, psi, nsweeps=3):
     dt = time.perf_counter() - t0
     n = len(psi)
     return {"value": nsweeps * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsweeps} red-black NGS sweeps (Newton k=2) of the {round(n ** (1 / 3))}^3 fine level "
+            "sample": f"{nsweeps} red-black NGS sweeps (Newton k={prob['opts']['newton_iters']}) of the "
+                      f"{round(n ** (1 / 3))}^3 fine level "
                       f"at the benchmark state, single-threaded C oracle, {dt:.1f} s"}
 
 
