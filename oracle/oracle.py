@@ -63,7 +63,7 @@ class _Opts(C.Structure):
                 ("max_levels", C.c_int), ("kappa_mode", C.c_int), ("kappa", C.c_double),
                 ("xi", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("ordering", C.c_int), ("newton_iters", C.c_int), ("cycle_gamma", C.c_int),
-                ("gamma_levels", C.c_int)]
+                ("gamma_levels", C.c_int), ("fmg_cycles", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -104,6 +104,7 @@ def lib():
         L.orc_vcycle.argtypes = [C.c_void_p, C.c_int, _DP, _DP]
         L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(_Info)]
         L.orc_solve_current.argtypes = [C.c_void_p, _DP, C.POINTER(_Info)]
+        L.orc_fmg.argtypes = [C.c_void_p, _DP]
         L.orc_get_array.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
         L.orc_set_g.argtypes = [C.c_void_p, _DP]
         L.orc_soil_eval.argtypes = [C.c_void_p, C.c_int, C.c_long, C.c_double, _DP, _DP, _DP]
@@ -164,7 +165,7 @@ class Oracle:
         opts = _Opts(o["nu1"], o["nu2"], o["coarse_max_sweeps"], o["coarse_rtol"],
                      o["coarsest_max_n"], o["max_levels"], o["kappa_mode"], o["kappa"],
                      o["xi"], o["tol"], o["max_cycles"], o["ordering"], o["newton_iters"],
-                     o.get("cycle_gamma", 1), o.get("gamma_levels", 0))
+                     o.get("cycle_gamma", 1), o.get("gamma_levels", 0), o.get("fmg_cycles", 0))
         self.h = L.orc_create(C.byref(g), C.byref(soil), C.byref(bc), C.byref(sink),
                               C.byref(opts))
         if not self.h:
@@ -282,6 +283,12 @@ class Oracle:
                             int(scheme if scheme is not None else self.prob["scheme"]),
                             C.byref(info))
         return st, dict(cycles=info.cycles, resid=info.resid, resid0=info.resid0)
+
+    def fmg(self, psi):
+        """Full multigrid pass (fmg_cycles per level) from psi on the prepared step."""
+        psi = _f64(psi).copy()
+        lib().orc_fmg(self.h, _dp(psi))
+        return psi
 
     def solve_current(self, psi):
         psi = _f64(psi).copy()

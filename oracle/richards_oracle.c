@@ -699,6 +699,33 @@ void orc_vcycle(orc_ctx *c, int lev, double *psi, const double *g) {
   for (int s = 0; s < c->opts.nu2; ++s) orc_sweep(c, lev, psi, g, -1);      /* 7 */
 }
 
+/* Full multigrid (Section 3.2: start from the coarsest grid, interpolate the
+   solution to successively finer grids, one or several cycles on each).
+   Reading: level l solves N_l(psi_l) = g_l with g_{l+1} = R g_l (full
+   weighting of the right side) and the coarse operators of the cycle; every
+   level starts from the restricted iterate, psi_{l+1} = R psi_l, and the
+   interpolation corrects the finer iterate, psi_l += P(psi_{l+1} - R psi_l),
+   so that the time step's initial guess is kept on every scale. */
+void orc_fmg(orc_ctx *c, double *psi) {
+  const int nl = c->nlev;
+  if (nl < 2 || c->opts.fmg_cycles <= 0) return;
+  for (int l = 0; l + 1 < nl; ++l) {
+    level *F = &c->lev[l], *C = &c->lev[l + 1];
+    const double *fpsi = l == 0 ? psi : F->psi;
+    orc_restrict(c, l, fpsi, C->psibar);
+    orc_restrict(c, l, F->g, C->g);
+    memcpy(C->psi, C->psibar, sizeof(double) * (size_t)C->ncell);
+  }
+  for (int k = 0; k < c->opts.fmg_cycles; ++k) orc_vcycle(c, nl - 1, c->lev[nl - 1].psi, c->lev[nl - 1].g);
+  for (int l = nl - 2; l >= 0; --l) {
+    level *F = &c->lev[l], *C = &c->lev[l + 1];
+    double *fpsi = l == 0 ? psi : F->psi;
+    for (long I = 0; I < C->ncell; ++I) C->tmp[I] = C->psi[I] - C->psibar[I];
+    orc_prolong_add(c, l, C->tmp, fpsi);
+    for (int k = 0; k < c->opts.fmg_cycles; ++k) orc_vcycle(c, l, fpsi, F->g);
+  }
+}
+
 /* cycle until tau_eff ||g - N(psi)||_inf <= tol, tau_eff = 1/a (reading of
    the "prescribed tolerance") */
 int orc_solve_current(orc_ctx *c, double *psi, orc_info *info) {
@@ -721,7 +748,17 @@ int orc_step(orc_ctx *c, double dt, int scheme, orc_info *info) {
   orc_prepare(c, dt, scheme);
   double *psi = dalloc(N);
   memcpy(psi, c->psi_n, sizeof(double) * (size_t)N);   /* psi^(0) = psi^n */
+  const int fmg = c->nlev > 1 && c->opts.fmg_cycles > 0;
+  double r0 = 0.0;
+  if (fmg) {                                             /* full multigrid start */
+    r0 = orc_residual(c, 0, psi, c->lev[0].g, NULL) / c->a;
+    orc_fmg(c, psi);
+  }
   int st = orc_solve_current(c, psi, info);
+  if (fmg && info) {                                     /* count the pass's finest cycles */
+    info->cycles += c->opts.fmg_cycles;
+    info->resid0 = r0;
+  }
   if (st != ORC_ENAN) {
     memcpy(c->psi_nm1, c->psi_n, sizeof(double) * (size_t)N);
     memcpy(c->psi_n, psi, sizeof(double) * (size_t)N);

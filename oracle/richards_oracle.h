@@ -72,6 +72,7 @@ typedef struct {
   int newton_iters;    /* 0: to tolerance; k > 0: exactly k safeguarded steps */
   int cycle_gamma;     /* coarse-grid visits per level: 1 V-cycle, 2 W-cycle */
   int gamma_levels;    /* cycle_gamma applies on levels < gamma_levels (0: all) */
+  int fmg_cycles;      /* > 0: full multigrid pass first, this many cycles per level */
 } orc_opts;
 
 typedef struct {
@@ -121,6 +122,9 @@ int orc_step(orc_ctx *c, double dt, int scheme, orc_info *info);
 /* same, but starting from and returning the caller's iterate, without shifting
    the history (for studies of a single implicit solve). */
 int orc_solve_current(orc_ctx *c, double *psi, orc_info *info);
+/* Full multigrid pass on the prepared step from the iterate psi (level 0):
+   fmg_cycles cycles per level, coarsest first. */
+void orc_fmg(orc_ctx *c, double *psi);
 
 /* inspection: which = 0 Kc, 1 g, 2 p1, 3 p2, 4 smax, 5 kappa, 6 psi_star,
    7 hist (a * history part of g), 10+face: boundary conductance on a face */
