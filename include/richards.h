@@ -131,7 +131,13 @@ typedef struct {
      predictor            mixed mode, BDF2 steps: 1 starts the iteration
                           from the extrapolated psi* = 2 psi^n - psi^{n-1}
                           instead of psi^n (same discrete system and stop
-                          test; a closer start needs fewer cycles) */
+                          test; a closer start needs fewer cycles)
+     fmg_cycles           > 0: a full multigrid pass (Section 3.2) starts the
+                          step (FP64) or each inner solve (mixed): right
+                          sides and iterates restricted to every level, the
+                          coarsest solved first, each finer iterate corrected
+                          by the interpolated coarse change, then fmg_cycles
+                          cycles on it; counted in cycles */
 typedef struct {
   int nu1, nu2, coarse_max_sweeps;
   double coarse_rtol;
@@ -141,7 +147,7 @@ typedef struct {
   int max_cycles, ordering, newton_iters, precision;
   int inner_cycles;
   double inner_rtol;
-  int max_outer, tail_cells, cycle_gamma, gamma_levels, graphs, sweep_planes, predictor;
+  int max_outer, tail_cells, cycle_gamma, gamma_levels, graphs, sweep_planes, predictor, fmg_cycles;
 } richards_opts;
 
 typedef struct {

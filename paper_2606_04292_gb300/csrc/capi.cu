@@ -730,13 +730,69 @@ richards_status water_balance(richards_ctx* c, double r, richards_step_info* inf
   return RICH_OK;
 }
 
+// Full multigrid pass (Section 3.2: coarsest grid first, the solution
+// interpolated to successively finer grids, fmg_cycles cycles on each).
+// Coarse right sides and starting iterates are the restricted finer ones
+// (ubar keeps the restricted iterate); prolong() then adds
+// P(coarse iterate - ubar) to the finer iterate.  FP64 levels (FP64 mode).
+void fmg64(richards_ctx* c) {
+  const int nl = c->nlev;
+  if (nl < 2 || c->opts.fmg_cycles <= 0) return;
+  for (int l = 0; l + 1 < nl; ++l) {
+    HLevel &F = c->L[l], &C = c->L[l + 1];
+    {
+      Prof pr(c, "fmg_restrict64", l, C.ncell);
+      rich::restrict64(view64(c, l), view64(c, l + 1), xfer64(c, l), F.u, F.g, C.ubar, C.g, c->s);
+    }
+    cudaMemcpyAsync(C.u, C.ubar, sizeof(double) * C.ncell, cudaMemcpyDeviceToDevice, c->s);
+  }
+  for (int k = 0; k < c->opts.fmg_cycles; ++k) vcycle64(c, nl - 1);
+  for (int l = nl - 2; l >= 0; --l) {
+    {
+      Prof pr(c, "prolong64", l, c->L[l].ncell);
+      rich::prolong64(view64(c, l), view64(c, l + 1), xfer64(c, l), c->s);
+    }
+    for (int k = 0; k < c->opts.fmg_cycles; ++k) vcycle64(c, l);
+  }
+}
+
+// The same pass on the FP32 correction problem of the mixed mode (finest
+// level: delta = 0, right side the outer defect).
+void fmg32(richards_ctx* c) {
+  const int nl = c->nlev;
+  if (nl < 2 || c->opts.fmg_cycles <= 0) return;
+  for (int l = 0; l + 1 < nl; ++l) {
+    HLevel &F = c->L[l], &C = c->L[l + 1];
+    {
+      Prof pr(c, "fmg_restrict32", l, C.ncell);
+      rich::restrict32(view32(c, l), view32(c, l + 1), xfer32(c, l), F.uf, F.gf, C.ubarf, C.gf, c->s);
+    }
+    cudaMemcpyAsync(C.uf, C.ubarf, sizeof(float) * C.ncell, cudaMemcpyDeviceToDevice, c->s);
+  }
+  for (int k = 0; k < c->opts.fmg_cycles; ++k) vcycle32(c, nl - 1);
+  for (int l = nl - 2; l >= 0; --l) {
+    {
+      Prof pr(c, "prolong32", l, c->L[l].ncell);
+      rich::prolong32(view32(c, l), view32(c, l + 1), xfer32(c, l), c->s);
+    }
+    for (int k = 0; k < c->opts.fmg_cycles; ++k) vcycle32(c, l);
+  }
+}
+
 richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
   const double teff = 1.0 / c->a;
   double nrm;
   TRY(norm64(c, 0, &nrm));
   double r = teff * nrm;
   const double r0 = r;
-  int cycles = 0;
+  int cycles = 0, fmg = 0;                            // cycles after / in the FMG pass
+  if (c->opts.fmg_cycles > 0 && c->nlev > 1) {      // full multigrid start
+    fmg64(c);
+    TRY(check_launch(c));
+    fmg = c->opts.fmg_cycles;
+    TRY(norm64(c, 0, &nrm));
+    r = teff * nrm;
+  }
   while (!(r <= c->opts.tol) && cycles < c->opts.max_cycles && !std::isnan(r)) {
     vcycle64(c, 0);
     TRY(check_launch(c));
@@ -747,7 +803,7 @@ richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
   long long tu = 0;
   TRY(read_stats(c, &tu));
   if (info) {
-    info->cycles = cycles;
+    info->cycles = cycles + fmg;
     info->outer_iters = 0;
     info->scheme_used = c->scheme_used;
     info->resid0 = r0;
@@ -804,7 +860,22 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
     // asks of the next outer defect (with a margin of 0.3 for the FP32 and
     // nonlinear remainder): close to tol it stops early
     const double rtol_in = std::max(c->opts.inner_rtol, 0.3 * c->opts.tol / r);
-    for (int k = 0; k < c->opts.inner_cycles; ++k) {
+    bool done_in = false;
+    if (c->opts.fmg_cycles > 0 && c->nlev > 1) {    // full multigrid start of the inner solve
+      fmg32(c);
+      inner += c->opts.fmg_cycles;
+      if (c->opts.inner_rtol > 0.0) {
+        CK(cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s));
+        {
+          Prof pr(c, "residual32", 0, F.ncell);
+          rich::residual32(view32(c, 0), P32, model, c->scratch + 1, c->s);
+        }
+        double rin;
+        TRY(read_norm(c, 1, &rin, true));
+        done_in = rin <= rtol_in * rin0;
+      }
+    }
+    for (int k = 0; k < c->opts.inner_cycles && !done_in; ++k) {
       run_cycle32(c);
       ++inner;
       if (c->opts.inner_rtol > 0.0 && k + 1 < c->opts.inner_cycles) {
@@ -870,6 +941,7 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
       o.ordering != 1 || (o.precision != 0 && o.precision != 1) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
       o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0 || o.cycle_gamma < 1 || o.cycle_gamma > 3 ||
       o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1) || (o.predictor != 0 && o.predictor != 1) ||
+      o.fmg_cycles < 0 || o.fmg_cycles > 16 ||
       (o.sweep_planes != 1 && o.sweep_planes != 2 && o.sweep_planes != 4 && o.sweep_planes != 8))
     return RICH_EINVAL;
   richards_ctx* c = new richards_ctx();

@@ -183,6 +183,59 @@ def test_vcycle_matches_oracle(mk, gamma, glev):
         assert rel(gs.get_level(0, 0), ref) <= STEP_RTOL
 
 
+FMG_IDS = ["1d_haverkamp_dir", "2d_gardner_mixed_bc", "3d_vg_hetero_sink", "3d_drainage_16"]
+FMG_PROBLEMS = [p for p in PROBLEMS if p[0] in FMG_IDS]
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in FMG_PROBLEMS], ids=[p[0] for p in FMG_PROBLEMS])
+@pytest.mark.parametrize("fmg", [1, 2])
+def test_fmg_pass_matches_oracle(mk, fmg):
+    """The full multigrid pass alone (max_cycles = 0), iterate for iterate."""
+    prob = mk()
+    gs, orc, p = pair(prob, coarse_rtol=0.0, coarse_max_sweeps=12, newton_iters=0, fmg_cycles=fmg, max_cycles=0)
+    gs.step(p["dt"], 1, check=False)
+    orc.prepare(p["dt"], 1)
+    ref = orc.fmg(p["psi0"])
+    assert rel(gs.state(), ref) <= STEP_RTOL
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in FMG_PROBLEMS], ids=[p[0] for p in FMG_PROBLEMS])
+def test_fmg_steps_match_oracle(mk):
+    """Whole FMG-started steps (Newton to round-off and a fixed coarsest sweep
+    count, as in the cycle tests: with the sink the system need not be
+    monotone, and iterates that part on one ulp may reach another root)."""
+    prob = mk()
+    gs, orc, p = pair(prob, tol=1e-11, max_cycles=200, fmg_cycles=1, newton_iters=0, coarse_rtol=0.0,
+                      coarse_max_sweeps=12)
+    for k in range(2):
+        st, info = gs.step(p["dt"], p["scheme"], check=False)
+        sto, info_o = orc.step(p["dt"], p["scheme"])
+        assert st == sto, (k, info, info_o)
+        assert abs(info["cycles"] - info_o["cycles"]) <= 1, (k, info, info_o)
+        assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in FMG_PROBLEMS], ids=[p[0] for p in FMG_PROBLEMS])
+def test_mixed_fmg_within_stated_bound(mk):
+    """Mixed mode with a full multigrid start of every inner solve."""
+    prob = W.with_opts(mk(), precision=1, fmg_cycles=1)
+    gs = R.Solver(prob)
+    orc = Oracle(W.with_opts(prob, tol=1e-13, newton_iters=0, fmg_cycles=0))
+    cur, prev = np.array(prob["psi0"], dtype=np.float64), None
+    for k in range(2):
+        st, info = gs.step(prob["dt"], prob["scheme"], check=False)
+        assert st == R.RICH_OK, info
+        psi_m = gs.state()
+        orc.set_state(cur, prev)
+        assert orc.step(prob["dt"], prob["scheme"])[0] == ORC_OK
+        psi_r = orc.state()
+        orc.set_state(cur, prev)
+        orc.prepare(prob["dt"], info["scheme_used"])
+        bound = _mixed_bound(orc, psi_m, psi_r)
+        assert np.max(np.abs(psi_m - psi_r)) <= bound * (1 + 1e-6) + 1e-15, k
+        prev, cur = cur, psi_m
+
+
 @pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
 def test_fp64_steps_match_oracle(mk):
     """Whole steps, both sides cycling to a tight tolerance (1e-11) so that the
