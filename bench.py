@@ -69,6 +69,7 @@ def parse():
                     help="steps with kernel timing (default: all timed steps)")
     ap.add_argument("--no-columns", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-gardner", action="store_true")
     ap.add_argument("--gamma", type=int, default=2, help="1 = V-cycles, 2 = W-cycles")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel timing records here")
     return ap.parse_args()
@@ -224,6 +225,51 @@ def serving_bench(nreq=24, max_steps=20):
         out[label] = {k: summary[k] for k in ("completed", "makespan_s", "solves_per_s", "cell_updates_per_s",
                                               "p50_latency_s", "p99_latency_s")}
     return out
+
+
+def gardner_bench(stream):
+    """The paper's 2D Gardner infiltration test in full (Section 4.2: 128^2,
+    tau = 0.1 day, 3 days = 30 steps), FP64 plain and mixed, wall time of the
+    whole run beside the CPU oracle's and the paper's 2.216 s (its hardware
+    unstated).  Returns the summary and the final states (the CPU-baseline
+    leg times the oracle on the same run and compares)."""
+    import torch
+    from paper_2606_04292_gb300 import richards as R
+    from paper_2606_04292_gb300 import workloads as W
+    out = {"workload": "2D Gardner infiltration 128^2, tau 0.1 day x 30 steps, tol 1e-8",
+           "paper_total_cpu_s": 2.216}
+    states = {}
+    for label, prec in (("fp64_plain", 0), ("mixed", 1)):
+        prob = W.gardner_2d(precision=prec)
+        gs = R.Solver(prob, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cyc = 0
+        for _ in range(prob["nsteps"]):
+            st, info = gs.step(check=False)
+            cyc += info["cycles"]
+        torch.cuda.synchronize()
+        out[label] = {"total_s": time.perf_counter() - t0, "status_last": R.STATUS_NAMES[st],
+                      "cycles_per_step": cyc / prob["nsteps"]}
+        states[label] = gs.state()
+        gs.close()
+    return out, states
+
+
+def gardner_cpu(states):
+    """The oracle on the whole 2D Gardner run (single thread), and its distance
+    to the GPU results."""
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_2606_04292_gb300 import workloads as W
+    prob = W.gardner_2d()
+    o = Oracle(prob)
+    t0 = time.perf_counter()
+    for _ in range(prob["nsteps"]):
+        o.step()
+    ref = o.state()
+    return {"total_s": time.perf_counter() - t0, "cores": 1,
+            "max_abs_dpsi_gpu_vs_oracle": {k: float(np.max(np.abs(v - ref))) for k, v in states.items()}}
 
 
 # ---------------------------------------------------------------------------
@@ -428,9 +474,15 @@ def main():
     if rank == 0 and not args.no_serving:
         serving = serving_bench()
 
+    gardner = gstates = None
+    if rank == 0 and not args.no_gardner:
+        gardner, gstates = gardner_bench(stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob, gs.state())
+        if gardner is not None:
+            gardner["cpu_oracle"] = gardner_cpu(gstates)
 
     if rank == 0:
         line = {
@@ -452,6 +504,7 @@ def main():
             "fp64_plain": fp64,
             "columns": columns,
             "serving": serving,
+            "paper_gardner_2d": gardner,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -133,6 +133,29 @@ def strip_2d(n=513, dt=60.0, nsteps=100, **optkw):
                 dt=dt, nsteps=nsteps, scheme=2, opts=opts)
 
 
+# ---------------------------------------------------------------------------
+# The paper's 2D infiltration test (Section 4.2): Gardner soil on (0, 10)^2 m,
+# time in days, h = -10 m initially and on every boundary but the top, where
+# eq. top-bc prescribes h(x) = ln(e^{-10 alpha} + (1 - e^{-10 alpha})
+# sin(pi x / 10)) / alpha (0 at x = 5, -10 at the corners); 3 days at
+# tau = 0.1 day on 128^2 cells.
+# ---------------------------------------------------------------------------
+def gardner_2d(n=128, dt=0.1, nsteps=30, **optkw):
+    alpha = 0.164
+    soil = _soil(GARDNER, Ks=0.1, theta_s=0.45, theta_r=0.15, p1=alpha)
+    # faces: 0 x-low, 1 x-high, 2 bottom, 3 top (axis 1 vertical)
+    bc = _bc([DIRICHLET, DIRICHLET, DIRICHLET, DIRICHLET], [-10.0, -10.0, -10.0, 0.0])
+    xc = (np.arange(n) + 0.5) * (10.0 / n)
+    e = math.exp(-10.0 * alpha)
+    bc["value_field"][3] = np.log(e + (1.0 - e) * np.sin(np.pi * xc / 10.0)) / alpha
+    opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0)
+    opts.update(optkw)
+    return dict(name=f"gardner2d_n{n}", dim=2, n=(n, n, 1), L=(10.0, 10.0, 1.0),
+                soil=soil, bc=bc, sink=no_sink(),
+                psi0=np.full(n * n, -10.0), psi_prev=None,
+                dt=dt, nsteps=nsteps, scheme=1, opts=opts)
+
+
 def gaussian_log_field(shape, corr_cells, seed):
     """Standardised Gaussian random field with covariance ~ exp(-r^2/corr^2).
 

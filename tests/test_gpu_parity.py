@@ -59,6 +59,7 @@ PROBLEMS = [
     ("3d_haverkamp_dir", lambda: W.random_problem(3, (10, 11, 13), W.HAVERKAMP, 5,
                                                    bc_kinds=[W.DIRICHLET] * 6)),
     ("3d_drainage_16", lambda: W.drainage_3d(n=16, precision=0)),
+    ("2d_gardner_paper_32", lambda: W.gardner_2d(n=32)),
 ]
 IDS = [p[0] for p in PROBLEMS]
 
