@@ -45,6 +45,12 @@ class _Soil(C.Structure):
                 ("p2_field", C.POINTER(C.c_double))]
 
 
+class _Material(C.Structure):
+    _fields_ = [("model", C.c_int), ("Ks", C.c_double), ("theta_s", C.c_double),
+                ("theta_r", C.c_double), ("p1", C.c_double), ("p2", C.c_double),
+                ("p3", C.c_double), ("p4", C.c_double)]
+
+
 class _BC(C.Structure):
     _fields_ = [("kind", C.c_int * 6), ("value", C.c_double * 6),
                 ("value_field", C.POINTER(C.c_double) * 6),
@@ -105,6 +111,10 @@ def lib():
         L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(_Info)]
         L.orc_solve_current.argtypes = [C.c_void_p, _DP, C.POINTER(_Info)]
         L.orc_fmg.argtypes = [C.c_void_p, _DP]
+        L.orc_set_materials.restype = C.c_int
+        L.orc_set_materials.argtypes = [C.c_void_p, C.POINTER(_Material), C.c_int, C.POINTER(C.c_ubyte)]
+        L.orc_level_material.restype = None
+        L.orc_level_material.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_ubyte)]
         L.orc_get_array.argtypes = [C.c_void_p, C.c_int, C.c_int, _DP]
         L.orc_set_g.argtypes = [C.c_void_p, _DP]
         L.orc_soil_eval.argtypes = [C.c_void_p, C.c_int, C.c_long, C.c_double, _DP, _DP, _DP]
@@ -170,6 +180,14 @@ class Oracle:
                               C.byref(opts))
         if not self.h:
             raise ValueError("oracle rejected the problem")
+        if s.get("materials"):
+            mats = (_Material * len(s["materials"]))(*[
+                _Material(m["model"], m["Ks"], m["theta_s"], m["theta_r"], m["p1"], m["p2"], m["p3"], m["p4"])
+                for m in s["materials"]])
+            idx = np.ascontiguousarray(s["material_index"], dtype=np.uint8)
+            if L.orc_set_materials(self.h, mats, len(s["materials"]),
+                                   idx.ctypes.data_as(C.POINTER(C.c_ubyte))) != ORC_OK:
+                raise ValueError("oracle rejected the materials")
         self.N = int(L.orc_level_ncell(self.h, 0))
         self.set_state(prob["psi0"], prob.get("psi_prev"))
 
@@ -323,6 +341,11 @@ class Oracle:
     def boundary_inflow(self, psi):
         psi = _f64(psi)
         return lib().orc_boundary_inflow(self.h, _dp(psi))
+
+    def material_map(self, lev=0):
+        out = np.zeros(self.ncell(lev), dtype=np.uint8)
+        lib().orc_level_material(self.h, lev, out.ctypes.data_as(C.POINTER(C.c_ubyte)))
+        return out
 
     def cell_volume(self, lev=0):
         return lib().orc_cell_volume(self.h, lev)

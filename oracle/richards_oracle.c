@@ -23,6 +23,7 @@ typedef struct {
   double h[3];
   long ncell;
   double *Kc, *p1, *p2, *smax, *kappa;
+  unsigned char *mat;   /* layered soil: material per cell (NULL otherwise) */
   double *kb[6];
   long nface[6];
   double *g, *psi, *psibar, *d, *tmp;
@@ -34,6 +35,8 @@ typedef struct {
 struct orc_ctx {
   orc_grid grid;
   orc_soil soil;          /* scalars; fields copied below */
+  int nmat;               /* layered soil: materials as soils (scalars only) */
+  orc_soil msoil[ORC_MAXMAT];
   orc_bc bc;              /* kinds/values; fields copied below */
   orc_sink sink;
   orc_opts opts;
@@ -76,6 +79,11 @@ static long fidx(const level *L, int ax, const int ii[3]) {
 /* K = Ks, theta' = 0 (Gardner's explicit saturated branch, applied to  */
 /* all three laws).                                                    */
 /* ------------------------------------------------------------------ */
+/* the law of cell i of a level: its material's, else the soil's */
+static const orc_soil *soil_of(const orc_ctx *c, const level *L, long i) {
+  return L->mat ? &c->msoil[L->mat[i]] : &c->soil;
+}
+
 static void soil_law(const orc_soil *s, double p1, double p2, double Ks, double psi,
                      double *th, double *dth, double *K) {
   const double ts = s->theta_s, tr = s->theta_r;
@@ -366,12 +374,71 @@ void orc_destroy(orc_ctx *c) {
     level *L = &c->lev[l];
     free(L->Kc); free(L->p1); free(L->p2); free(L->smax); free(L->kappa);
     free(L->g); free(L->psi); free(L->psibar); free(L->d); free(L->tmp);
+    free(L->mat);
     for (int f = 0; f < 6; ++f) free(L->kb[f]);
     for (int a = 0; a < 3; ++a) { free(L->R[a]); free(L->P[a]); }
   }
   for (int f = 0; f < 6; ++f) { free(c->bcval[f]); free(c->bcmask[f]); }
   free(c->Ks); free(c->psi_n); free(c->psi_nm1); free(c->psistar); free(c->hist);
   free(c);
+}
+
+/* Layered soil (reading for the coarse levels: the material of largest
+   total restriction weight among a coarse cell's fine cells, ties to the
+   lower index; every cell uses its material's law and parameters). */
+int orc_set_materials(orc_ctx *c, const orc_material *mats, int nmat, const unsigned char *index) {
+  if (nmat < 1 || nmat > ORC_MAXMAT || !mats || !index) return ORC_EINVAL;
+  level *L0 = &c->lev[0];
+  for (long i = 0; i < L0->ncell; ++i)
+    if (index[i] >= nmat) return ORC_EINVAL;
+  c->nmat = nmat;
+  for (int m = 0; m < nmat; ++m) {
+    orc_soil *S = &c->msoil[m];
+    memset(S, 0, sizeof(*S));
+    S->model = mats[m].model;
+    S->Ks = mats[m].Ks; S->theta_s = mats[m].theta_s; S->theta_r = mats[m].theta_r;
+    S->p1 = mats[m].p1; S->p2 = mats[m].p2; S->p3 = mats[m].p3; S->p4 = mats[m].p4;
+  }
+  for (int l = 0; l < c->nlev; ++l) {
+    level *L = &c->lev[l];
+    free(L->mat);
+    L->mat = (unsigned char *)malloc((size_t)L->ncell);
+  }
+  memcpy(L0->mat, index, (size_t)L0->ncell);
+  for (int l = 0; l + 1 < c->nlev; ++l) {
+    const level *F = &c->lev[l];
+    level *C = &c->lev[l + 1];
+    for (long J = 0; J < C->ncell; ++J) {
+      int jj[3]; cpos(C, J, jj);
+      double w[ORC_MAXMAT] = {0};
+      const wrow *r0 = &F->R[0][jj[0]], *r1 = &F->R[1][jj[1]], *r2 = &F->R[2][jj[2]];
+      for (int a2 = 0; a2 < r2->cnt; ++a2)
+        for (int a1 = 0; a1 < r1->cnt; ++a1)
+          for (int a0 = 0; a0 < r0->cnt; ++a0) {
+            long i = cidx(F, r0->idx[a0], r1->idx[a1], r2->idx[a2]);
+            w[F->mat[i]] += r0->w[a0] * r1->w[a1] * r2->w[a2];
+          }
+      int best = 0;
+      for (int m = 1; m < nmat; ++m)
+        if (w[m] > w[best]) best = m;
+      C->mat[J] = (unsigned char)best;
+    }
+  }
+  for (int l = 0; l < c->nlev; ++l) {
+    level *L = &c->lev[l];
+    for (long i = 0; i < L->ncell; ++i) {
+      const orc_soil *S = &c->msoil[L->mat[i]];
+      L->p1[i] = S->p1;
+      L->p2[i] = S->p2;
+      if (l == 0) c->Ks[i] = S->Ks;
+    }
+  }
+  return ORC_OK;
+}
+
+void orc_level_material(const orc_ctx *c, int lev, unsigned char *out) {
+  const level *L = &c->lev[lev];
+  for (long i = 0; i < L->ncell; ++i) out[i] = L->mat ? L->mat[i] : 0;
 }
 
 int orc_nlevels(const orc_ctx *c) { return c->nlev; }
@@ -441,7 +508,7 @@ void orc_apply_N(const orc_ctx *c, int lev, const double *psi, double *out) {
   const level *L = &c->lev[lev];
   for (long i = 0; i < L->ncell; ++i) {
     double th, S, mii, off;
-    soil_law(&c->soil, L->p1[i], L->p2[i], 0.0, psi[i], &th, NULL, NULL);
+    soil_law(soil_of(c, L, i), L->p1[i], L->p2[i], 0.0, psi[i], &th, NULL, NULL);
     sink_law(&c->sink, L->smax[i], psi[i], &S, NULL);
     stencil(c, L, i, psi, &mii, &off);
     out[i] = c->a * th + S + c->opts.xi * psi[i] + mii * psi[i] - off;
@@ -505,16 +572,16 @@ int orc_prepare(orc_ctx *c, double dt, int scheme) {
   c->a = scheme == 1 ? 1.0 / dt : 1.5 / dt;
   for (long i = 0; i < N; ++i) {
     double thn, thm = 0.0;
-    soil_law(&c->soil, L->p1[i], L->p2[i], c->Ks[i], c->psi_n[i], &thn, NULL, NULL);
+    soil_law(soil_of(c, L, i), L->p1[i], L->p2[i], c->Ks[i], c->psi_n[i], &thn, NULL, NULL);
     if (scheme == 1) {
       c->psistar[i] = c->psi_n[i];
       c->hist[i] = thn / dt;
     } else {
-      soil_law(&c->soil, L->p1[i], L->p2[i], c->Ks[i], c->psi_nm1[i], &thm, NULL, NULL);
+      soil_law(soil_of(c, L, i), L->p1[i], L->p2[i], c->Ks[i], c->psi_nm1[i], &thm, NULL, NULL);
       c->psistar[i] = 2.0 * c->psi_n[i] - c->psi_nm1[i];
       c->hist[i] = (4.0 * thn - thm) / (2.0 * dt);
     }
-    soil_law(&c->soil, L->p1[i], L->p2[i], c->Ks[i], c->psistar[i], NULL, NULL, &L->Kc[i]);
+    soil_law(soil_of(c, L, i), L->p1[i], L->p2[i], c->Ks[i], c->psistar[i], NULL, NULL, &L->Kc[i]);
   }
   /* boundary face conductances of the fine level */
   for (int f = 0; f < 2 * c->grid.dim; ++f) {
@@ -525,7 +592,7 @@ int orc_prepare(orc_ctx *c, double dt, int scheme) {
       long fc = fidx(L, ax, ii);
       if (face_is_dirichlet(c, f, fc)) {
         double Kb;
-        soil_law(&c->soil, L->p1[i], L->p2[i], c->Ks[i], face_value(c, f, fc), NULL, NULL, &Kb);
+        soil_law(soil_of(c, L, i), L->p1[i], L->p2[i], c->Ks[i], face_value(c, f, fc), NULL, NULL, &Kb);
         L->kb[f][fc] = 0.5 * (L->Kc[i] + Kb);
       } else {
         L->kb[f][fc] = 0.0;
@@ -600,14 +667,15 @@ static double point_solve(const orc_ctx *c, const level *L, long i, double cc, d
     f += (k - cc) * x0;
     cc = k;
   }
-  double lo = (f - a * c->soil.theta_s - smax) / cc;
-  double hi = (f - a * c->soil.theta_r) / cc;
+  const orc_soil *SL = soil_of(c, L, i);
+  double lo = (f - a * SL->theta_s - smax) / cc;
+  double hi = (f - a * SL->theta_r) / cc;
   double x = x0 < lo ? lo : (x0 > hi ? hi : x0);
   const int maxit = kfixed > 0 ? kfixed : 200;
   int it = 0;
   while (it < maxit) {
     double th, dth, S, dS;
-    soil_law(&c->soil, L->p1[i], L->p2[i], 0.0, x, &th, &dth, NULL);
+    soil_law(SL, L->p1[i], L->p2[i], 0.0, x, &th, &dth, NULL);
     sink_law(&c->sink, L->smax[i], x, &S, &dS);
     const double F = a * th + S + cc * x - f;
     const double dF = a * dth + dS + cc;
@@ -794,7 +862,7 @@ void orc_soil_eval(const orc_ctx *c, int lev, long cell, double psi,
                    double *theta, double *dtheta, double *K) {
   const level *L = &c->lev[lev];
   double Ks = lev == 0 ? c->Ks[cell] : 0.0;
-  soil_law(&c->soil, L->p1[cell], L->p2[cell], Ks, psi, theta, dtheta, K);
+  soil_law(soil_of(c, L, cell), L->p1[cell], L->p2[cell], Ks, psi, theta, dtheta, K);
 }
 
 void orc_sink_eval(const orc_ctx *c, int lev, long cell, double psi, double *S, double *dS) {

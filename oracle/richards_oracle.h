@@ -47,6 +47,14 @@ typedef struct {
   const double *Ks_field, *p1_field, *p2_field;   /* nullable, per cell */
 } orc_soil;
 
+/* A material of a layered soil (spatially varying law, Section 4.1's
+   composite column and Section 4.2's two-layer field). */
+#define ORC_MAXMAT 8
+typedef struct {
+  int model;
+  double Ks, theta_s, theta_r, p1, p2, p3, p4;
+} orc_material;
+
 typedef struct {
   int kind[6];                        /* face 2*axis+side */
   double value[6];
@@ -122,6 +130,14 @@ int orc_step(orc_ctx *c, double dt, int scheme, orc_info *info);
 /* same, but starting from and returning the caller's iterate, without shifting
    the history (for studies of a single implicit solve). */
 int orc_solve_current(orc_ctx *c, double *psi, orc_info *info);
+/* Layered soil: nmat (1..ORC_MAXMAT) materials and a material index per
+   fine cell (host array, copied).  Each cell then takes its material's law
+   and parameters (the soil's scalars and fields no longer apply); a coarse
+   cell takes the material with the largest restriction weight among its
+   fine cells (ties: the lower index).  Returns ORC_OK or ORC_EINVAL. */
+int orc_set_materials(orc_ctx *c, const orc_material *mats, int nmat, const unsigned char *index);
+/* Material index of every cell of level lev (0 everywhere without materials). */
+void orc_level_material(const orc_ctx *c, int lev, unsigned char *out);
 /* Full multigrid pass on the prepared step from the iterate psi (level 0):
    fmg_cycles cycles per level, coarsest first. */
 void orc_fmg(orc_ctx *c, double *psi);

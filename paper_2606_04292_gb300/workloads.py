@@ -156,6 +156,97 @@ def gardner_2d(n=128, dt=0.1, nsteps=30, **optkw):
                 dt=dt, nsteps=nsteps, scheme=1, opts=opts)
 
 
+# ---------------------------------------------------------------------------
+# Layered soils (spatially varying laws).  A soil dict may carry
+# "materials" (list of per-material laws and parameters) and
+# "material_index" (uint8 per cell); each cell then uses its material.
+# ---------------------------------------------------------------------------
+def material(model, Ks, theta_s, theta_r, p1=0.0, p2=0.0, p3=0.0, p4=0.0):
+    return dict(model=int(model), Ks=float(Ks), theta_s=float(theta_s), theta_r=float(theta_r),
+                p1=float(p1), p2=float(p2), p3=float(p3), p4=float(p4))
+
+
+def celia_composite_1d(n=128, dt=10.0, nsteps=36, **optkw):
+    """Section 4.1's composite column (cm, s): Gardner for 30 <= z < 40,
+    Haverkamp for 20 <= z < 30, van Genuchten-Mualem elsewhere, with the
+    shared Ks, theta_s, theta_r of Table 2 and the parameters of Table 4."""
+    prob = celia_1d(n=n, dt=dt, nsteps=nsteps, **optkw)
+    Ks, ts, tr = 0.00944, 0.287, 0.075
+    mats = [material(VANGENUCHTEN, Ks, ts, tr, p1=0.03165, p2=3.349, p3=0.5),
+            material(HAVERKAMP, Ks, ts, tr, p1=1.611e6, p2=3.96, p3=1.175e6, p4=4.74),
+            material(GARDNER, Ks, ts, tr, p1=0.01877)]
+    z = (np.arange(n) + 0.5) * (40.0 / n)
+    idx = np.zeros(n, dtype=np.uint8)
+    idx[(z >= 20.0) & (z < 30.0)] = 1
+    idx[(z >= 30.0) & (z < 40.0)] = 2
+    prob["soil"] = dict(prob["soil"], materials=mats, material_index=idx)
+    prob["name"] = f"celia_composite1d_n{n}"
+    return prob
+
+
+def two_layer_2d(n=256, dt=0.01, nsteps=100, **optkw):
+    """Section 4.2's two-layer van Genuchten-Mualem field (cm, hours) on
+    (0, 100)^2: the interface zeta(x) = 100 (0.1 (1 - cos(pi x / 100)) + 0.45),
+    psi = -z initially, psi = 0 on the top and bottom, no flux on the sides;
+    FMG with 10 pre- and 10 post-smoothing sweeps, kappa = 0.1, xi = 0."""
+    upper = material(VANGENUCHTEN, 0.25, 0.50, 0.120, p1=0.025, p2=3.00, p3=0.5)
+    lower = material(VANGENUCHTEN, 2.00, 0.46, 0.034, p1=0.016, p2=1.37, p3=0.5)
+    h = 100.0 / n
+    xc = (np.arange(n) + 0.5) * h
+    zc = (np.arange(n) + 0.5) * h
+    zeta = 100.0 * (0.1 * (1.0 - np.cos(np.pi * xc / 100.0)) + 0.45)
+    idx = (zc[:, None] < zeta[None, :]).astype(np.uint8).reshape(-1)     # [z, x], x fastest
+    soil = _soil(VANGENUCHTEN, Ks=upper["Ks"], theta_s=upper["theta_s"], theta_r=upper["theta_r"],
+                 p1=upper["p1"], p2=upper["p2"], p3=0.5)
+    soil.update(materials=[upper, lower], material_index=idx)
+    bc = _bc([NOFLUX, NOFLUX, DIRICHLET, DIRICHLET], [0.0, 0.0, 0.0, 0.0])
+    opts = default_opts(kappa_mode=0, kappa=0.1, xi=0.0, nu1=10, nu2=10, fmg_cycles=1)
+    opts.update(optkw)
+    psi0 = -np.repeat(zc, n)
+    return dict(name=f"two_layer2d_n{n}", dim=2, n=(n, n, 1), L=(100.0, 100.0, 1.0),
+                soil=soil, bc=bc, sink=no_sink(), psi0=psi0, psi_prev=None,
+                dt=dt, nsteps=nsteps, scheme=1, opts=opts)
+
+
+def test_materials():
+    """Three materials in m and s, one per law, with distinct Ks, theta_s and
+    theta_r (parameters exact in float)."""
+    f = lambda x: float(np.float32(x))
+    return [material(VANGENUCHTEN, f(1e-5), f(0.368), f(0.102), p1=f(3.35), p2=f(2.0), p3=0.5),
+            material(HAVERKAMP, f(2.5e-5), f(0.287), f(0.075), p1=f(1.611e6 * 100.0 ** -3.96),
+                     p2=f(3.96), p3=f(1.175e6 * 100.0 ** -4.74), p4=f(4.74)),
+            material(GARDNER, f(4e-6), f(0.45), f(0.15), p1=f(2.0))]
+
+
+def with_materials(prob, mats, index):
+    """A copy of prob whose soil carries the given materials and per-cell index."""
+    p = copy.copy(prob)
+    p["soil"] = dict(prob["soil"], materials=list(mats),
+                     material_index=np.ascontiguousarray(index, dtype=np.uint8))
+    return p
+
+
+def material_pattern(prob, kind, nmat, seed):
+    """A material index for prob's grid: "random" (independent per cell) or
+    "layers" (bands in the vertical axis bounded by wavy interfaces)."""
+    nn = prob["n"]
+    N = nn[0] * nn[1] * nn[2]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if kind == "random":
+        return rng.integers(0, nmat, N).astype(np.uint8)
+    dim = prob["dim"]
+    idx = np.arange(N)
+    pos = [idx % nn[0], (idx // nn[0]) % nn[1], idx // (nn[0] * nn[1])]
+    z = (pos[dim - 1] + 0.5) / nn[dim - 1]
+    x = (pos[0] + 0.5) / nn[0] if dim > 1 else np.zeros(N)
+    cuts = np.sort(rng.uniform(0.15, 0.85, nmat - 1))
+    amp = rng.uniform(0.0, 0.1, nmat - 1)
+    out = np.zeros(N, dtype=np.uint8)
+    for k in range(nmat - 1):
+        out += (z >= cuts[k] + amp[k] * np.sin(2.0 * np.pi * x)).astype(np.uint8)
+    return out
+
+
 def gaussian_log_field(shape, corr_cells, seed):
     """Standardised Gaussian random field with covariance ~ exp(-r^2/corr^2).
 
