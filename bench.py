@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-columns", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-gardner", action="store_true")
+    ap.add_argument("--no-layered", action="store_true")
     ap.add_argument("--gamma", type=int, default=2, help="1 = V-cycles, 2 = W-cycles")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel timing records here")
     return ap.parse_args()
@@ -270,6 +271,69 @@ def gardner_cpu(states):
     ref = o.state()
     return {"total_s": time.perf_counter() - t0, "cores": 1,
             "max_abs_dpsi_gpu_vs_oracle": {k: float(np.max(np.abs(v - ref))) for k, v in states.items()}}
+
+
+LAYERED_STEPS = 100       # two-layer field: 1 h at tau = 0.01 h
+LAYERED_CPU_STEPS = 3
+
+
+def layered_bench(stream):
+    """The paper's layered workloads: Section 4.1's composite column (128
+    cells, 36 steps of 10 s, FP64) and Section 4.2's two-layer field (256^2,
+    tau = 0.01 h, FMG(10,10), kappa = 0.1) for LAYERED_STEPS steps, FP64
+    plain and mixed; wall time of each whole run.  Returns the summary and
+    the states the CPU leg compares with."""
+    import torch
+    from paper_2606_04292_gb300 import richards as R
+    from paper_2606_04292_gb300 import workloads as W
+    out = {"workload": f"composite column 128 x 36 steps; two-layer 256^2 x {LAYERED_STEPS} steps, tol 1e-8"}
+    states = {}
+    runs = [("composite_column_fp64", W.celia_composite_1d(), None),
+            ("two_layer_fp64_plain", W.two_layer_2d(nsteps=LAYERED_STEPS, precision=0), LAYERED_CPU_STEPS),
+            ("two_layer_mixed", W.two_layer_2d(nsteps=LAYERED_STEPS, precision=1), LAYERED_CPU_STEPS)]
+    for label, prob, keep in runs:
+        gs = R.Solver(prob, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cyc, worst = 0, 0
+        for k in range(prob["nsteps"]):
+            st, info = gs.step(check=False)
+            cyc += info["cycles"]
+            worst = max(worst, st)
+            if keep is not None and k + 1 == keep:
+                states[label] = gs.state()
+        torch.cuda.synchronize()
+        out[label] = {"total_s": time.perf_counter() - t0, "steps": prob["nsteps"],
+                      "worst_status": R.STATUS_NAMES[worst], "cycles_per_step": cyc / prob["nsteps"]}
+        if keep is None:
+            states[label] = gs.state()
+        gs.close()
+    return out, states
+
+
+def layered_cpu(states):
+    """The oracle on the composite column (whole run) and on the first
+    LAYERED_CPU_STEPS steps of the two-layer field (single thread, seconds
+    per step), with the distance of the GPU states at the same points."""
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_2606_04292_gb300 import workloads as W
+    res = {"cores": 1}
+    o = Oracle(W.celia_composite_1d())
+    t0 = time.perf_counter()
+    for _ in range(o.prob["nsteps"]):
+        o.step()
+    res["composite_column_total_s"] = time.perf_counter() - t0
+    res["composite_column_max_abs_dpsi"] = float(np.max(np.abs(states["composite_column_fp64"] - o.state())))
+    o = Oracle(W.two_layer_2d())
+    t0 = time.perf_counter()
+    for _ in range(LAYERED_CPU_STEPS):
+        o.step()
+    res["two_layer_s_per_step"] = (time.perf_counter() - t0) / LAYERED_CPU_STEPS
+    res["two_layer_sample"] = f"first {LAYERED_CPU_STEPS} steps"
+    for k in ("two_layer_fp64_plain", "two_layer_mixed"):
+        res[k + "_max_abs_dpsi"] = float(np.max(np.abs(states[k] - o.state())))
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -477,12 +541,17 @@ def main():
     gardner = gstates = None
     if rank == 0 and not args.no_gardner:
         gardner, gstates = gardner_bench(stream)
+    layered = lstates = None
+    if rank == 0 and not args.no_layered:
+        layered, lstates = layered_bench(stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob, gs.state())
         if gardner is not None:
             gardner["cpu_oracle"] = gardner_cpu(gstates)
+        if layered is not None:
+            layered["cpu_oracle"] = layered_cpu(lstates)
 
     if rank == 0:
         line = {
@@ -505,6 +574,7 @@ def main():
             "columns": columns,
             "serving": serving,
             "paper_gardner_2d": gardner,
+            "paper_layered": layered,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

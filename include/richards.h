@@ -178,6 +178,25 @@ richards_status richards_create(const richards_grid *grid, const richards_opts *
    <= 0, or a non-finite value in a field. */
 richards_status richards_set_soil(richards_ctx *ctx, const richards_soil *soil);
 
+/* Layered soil (Section 4.1's composite law; Section 4.2's two layers): up
+   to 8 materials, each a Table 1 law (model, Ks, theta_s, theta_r and p1..p4
+   as in richards_soil), and a material index per cell of the finest level
+   (host array of ncell bytes, copied; layout as psi).  Every cell then takes
+   its material's law and parameters everywhere (theta, theta', K, the point
+   solve's bracket, K(psi_b) on a Dirichlet face); conductivities stay
+   cell-centred and faces take the mean of the two cell values.  A coarse
+   cell takes the material with the largest total restriction weight among
+   its fine cells (ties: the lower index) and that material's parameters.
+   Replaces the soil set by richards_set_soil (and is replaced by the next
+   such call).  Ownership: nothing is retained.  EINVAL: nmat outside 1..8, a
+   material failing richards_set_soil's checks, or an index >= nmat. */
+typedef struct {
+  int model;
+  double Ks, theta_s, theta_r, p1, p2, p3, p4;
+} richards_material;
+richards_status richards_set_materials(richards_ctx *ctx, const richards_material *mats, int nmat,
+                                       const unsigned char *index);
+
 /* Boundary conditions (see richards_bc).  EINVAL: unknown kind, free
    drainage off the bottom face, non-finite value. */
 richards_status richards_set_bc(richards_ctx *ctx, const richards_bc *bc);
@@ -270,8 +289,9 @@ richards_status richards_level_dims(const richards_ctx *ctx, int level, int n_ou
 
 /* Arrays of a level (FP64 copies, host buffers):
      0 iterate psi, 1 right side g, 2 Kc, 3 p1, 4 p2, 5 sink coefficient,
-     6 FAS restricted iterate psi_bar, 7 defect d, 10+f boundary conductance
-     of face f (face cells).  set accepts 0 (iterate) and 1 (right side). */
+     6 FAS restricted iterate psi_bar, 7 defect d, 8 material index (layered
+     soils only, as doubles), 10+f boundary conductance of face f (face
+     cells).  set accepts 0 (iterate) and 1 (right side). */
 richards_status richards_get_level(richards_ctx *ctx, int level, int which, double *out,
                                    long long n);
 richards_status richards_set_level(richards_ctx *ctx, int level, int which, const double *in,

@@ -10,6 +10,7 @@
 #include <map>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -39,6 +40,7 @@ struct HLevel {
   float *uf = nullptr, *ubarf = nullptr, *gf = nullptr, *df = nullptr, *Kcf = nullptr;
   float *p1f = nullptr, *p2f = nullptr, *smaxf = nullptr, *psi0f = nullptr;
   float* kbf[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  uint8_t* mat = nullptr;        // layered soil: material of each cell
   // transfer tables to the next coarser level
   int *pc[3] = {}, *pj[3] = {}, *rc[3] = {}, *ri[3] = {};
   double *pw[3] = {}, *rw[3] = {};
@@ -55,6 +57,13 @@ struct richards_ctx {
   HLevel L[MAXLEV];
   richards_soil soil{};
   bool soil_set = false, het_p1 = false, het_p2 = false, het_Ks = false;
+  // layered soil (richards_set_materials): soil.model is then rich::COMPOSITE
+  bool layered = false;
+  int nmat = 0;
+  richards_material mats[rich::MAXMAT] = {};
+  rich::MatLaw<double>* dmat64 = nullptr;
+  rich::MatLaw<float>* dmat32 = nullptr;
+  rich::DDMat* dmatdd = nullptr;
   richards_bc bc{};
   bool bc_set = false;
   rich::BcDev bcdev{};
@@ -281,6 +290,23 @@ Row interp(int nf, int nc, int i, double slo, double shi) {
   return r;
 }
 
+// Rows of the restriction along one axis: the transpose of the
+// constant-extrapolation interpolation, each row normalised to sum 1.
+bool restriction_rows(int nf, int nc, std::vector<Row>& R) {
+  R.assign(nc, Row());
+  for (int i = 0; i < nf; ++i) {
+    Row p0 = interp(nf, nc, i, 1.0, 1.0);
+    for (int k = 0; k < p0.cnt; ++k)
+      if (!R[p0.idx[k]].add(i, p0.w[k])) return false;
+  }
+  for (int J = 0; J < nc; ++J) {
+    double s = 0.0;
+    for (int k = 0; k < R[J].cnt; ++k) s += R[J].w[k];
+    for (int k = 0; k < R[J].cnt; ++k) R[J].w[k] /= s;
+  }
+  return true;
+}
+
 richards_status build_axis_tables(richards_ctx* c, int l, int ax, double slo, double shi) {
   HLevel& F = c->L[l];
   HLevel& C = c->L[l + 1];
@@ -292,19 +318,13 @@ richards_status build_axis_tables(richards_ctx* c, int l, int ax, double slo, do
     pc[i] = r.cnt;
     for (int k = 0; k < r.cnt; ++k) { pj[2 * i + k] = r.idx[k]; pw[2 * i + k] = r.w[k]; }
   }
-  std::vector<Row> R(nc);
-  for (int i = 0; i < nf; ++i) {
-    Row p0 = interp(nf, nc, i, 1.0, 1.0);
-    for (int k = 0; k < p0.cnt; ++k)
-      if (!R[p0.idx[k]].add(i, p0.w[k])) return fail(c, RICH_EINVAL, "restriction stencil too wide");
-  }
+  std::vector<Row> R;
+  if (!restriction_rows(nf, nc, R)) return fail(c, RICH_EINVAL, "restriction stencil too wide");
   for (int J = 0; J < nc; ++J) {
-    double s = 0.0;
-    for (int k = 0; k < R[J].cnt; ++k) s += R[J].w[k];
     rc[J] = R[J].cnt;
     for (int k = 0; k < R[J].cnt; ++k) {
       ri[rich::RMAX * J + k] = R[J].idx[k];
-      rw[rich::RMAX * J + k] = R[J].w[k] / s;
+      rw[rich::RMAX * J + k] = R[J].w[k];
     }
   }
   std::vector<float> pwf(pw.begin(), pw.end()), rwf(rw.begin(), rw.end());
@@ -351,6 +371,7 @@ Level<double> view64(const richards_ctx* c, int l) {
   V.smax = c->sink.enabled ? H.smax : nullptr;
   V.psi0 = nullptr;
   for (int f = 0; f < 6; ++f) V.kb[f] = H.kb[f];
+  V.mat = c->layered ? H.mat : nullptr;
   return V;
 }
 
@@ -367,6 +388,7 @@ Level<float> view32(const richards_ctx* c, int l) {
   V.smax = c->sink.enabled ? H.smaxf : nullptr;
   V.psi0 = H.psi0f;
   for (int f = 0; f < 6; ++f) V.kb[f] = H.kbf[f];
+  V.mat = c->layered ? H.mat : nullptr;
   return V;
 }
 
@@ -402,8 +424,16 @@ Phys<T> phys(const richards_ctx* c) {
   P.h1 = (T)c->sink.h1; P.h2 = (T)c->sink.h2; P.h3 = (T)c->sink.h3; P.h4 = (T)c->sink.h4;
   P.newton_k = c->opts.newton_iters;
   P.sink = c->sink.enabled;
+  if (c->layered) {
+    if constexpr (std::is_same<T, double>::value) P.mats = c->dmat64;
+    else P.mats = c->dmat32;
+    P.ddmats = c->dmatdd;
+  }
   return P;
 }
+
+// fine material index for the preparation kernels (null unless layered)
+const uint8_t* fine_mat(const richards_ctx* c) { return c->layered ? c->L[0].mat : nullptr; }
 
 // upload the level views and transfer tables the coarse-tail kernel reads
 richards_status upload_views(richards_ctx* c) {
@@ -645,13 +675,14 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   const bool cache = c->opts.precision == 1;
   if (cache)    // mixed mode: float-float arithmetic, theta caches
     rich::prep_lagged_dd(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
-                         c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, P, rich::make_ddphys(P),
+                         c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, rich::make_ddphys(P),
                          c->soil.model, scheme, dt, F.Kc, F.Kcf, F.g, F.u, c->th_n_valid ? c->th_n : nullptr,
                          c->th_nm1_valid ? c->th_nm1 : nullptr, c->th_n_valid ? nullptr : c->th_n,
                          c->th_nm1_valid ? nullptr : c->th_nm1, c->opts.predictor == 1, c->s);
   else
     rich::prep_lagged(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
-                      c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, P, c->soil.model, scheme, dt, F.Kc,
+                      c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, c->soil.model, scheme,
+                      dt, F.Kc,
                       F.g, F.u, nullptr, nullptr, nullptr, nullptr, c->s);
   if (cache) {
     c->th_n_valid = true;
@@ -660,7 +691,7 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   double* kbw[6];
   for (int f = 0; f < 6; ++f) kbw[f] = F.kb[f];
   rich::prep_rhs(geom(c, 0), c->bcdev, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
-                 c->het_p2 ? F.p2 : nullptr, P, c->soil.model, F.Kc, F.g, kbw, c->s);
+                 c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, c->soil.model, F.Kc, F.g, kbw, c->s);
   TRY(check_launch(c));
   TRY(restrict_coefficients(c));
   c->prepared = true;
@@ -1043,26 +1074,32 @@ richards_status richards_level_dims(const richards_ctx* c, int level, int n_out[
   return RICH_OK;
 }
 
+// Validity of one law's parameters (Table 1); p1/p2 given by fields are
+// checked separately.  Returns nullptr or the complaint.
+const char* law_error(int model, double Ks, double ts, double tr, double p1, double p2, double p3, double p4,
+                      bool p1_field, bool p2_field) {
+  const bool ok = model >= 0 && model <= 2 && std::isfinite(Ks) && Ks > 0.0 && std::isfinite(ts) &&
+                  std::isfinite(tr) && tr >= 0.0 && ts > tr;
+  if (!ok) return "invalid soil: need a known law, Ks > 0, theta_s > theta_r >= 0";
+  auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
+  if (model == RICH_HAVERKAMP && !(pos(p3) && pos(p4) && (p1_field || pos(p1)) && (p2_field || pos(p2))))
+    return "Haverkamp needs alpha, beta, A, gamma > 0";
+  if (model == RICH_GARDNER && !(p1_field || pos(p1))) return "Gardner needs alpha > 0";
+  if (model == RICH_VANGENUCHTEN &&
+      !((p1_field || pos(p1)) && (p2_field || (std::isfinite(p2) && p2 > 1.0)) && std::isfinite(p3)))
+    return "van Genuchten needs alpha > 0, n > 1, finite l";
+  return nullptr;
+}
+
 richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
   if (!c || !s) return RICH_EINVAL;
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   cudaStreamSynchronize(c->s);
   graphs_reset(c);
   const long long N = c->L[0].ncell;
-  const bool ok = s->model >= 0 && s->model <= 2 && std::isfinite(s->Ks) && s->Ks > 0.0 &&
-                  std::isfinite(s->theta_s) && std::isfinite(s->theta_r) && s->theta_r >= 0.0 &&
-                  s->theta_s > s->theta_r;
-  if (!ok) return fail(c, RICH_EINVAL, "invalid soil: need Ks > 0, theta_s > theta_r >= 0");
-  auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
-  if (s->model == RICH_HAVERKAMP && !(pos(s->p3) && pos(s->p4) && (s->p1_field || pos(s->p1)) &&
-                                      (s->p2_field || pos(s->p2))))
-    return fail(c, RICH_EINVAL, "Haverkamp needs alpha, beta, A, gamma > 0");
-  if (s->model == RICH_GARDNER && !(s->p1_field || pos(s->p1)))
-    return fail(c, RICH_EINVAL, "Gardner needs alpha > 0");
-  if (s->model == RICH_VANGENUCHTEN &&
-      !((s->p1_field || pos(s->p1)) && (s->p2_field || (std::isfinite(s->p2) && s->p2 > 1.0)) &&
-        std::isfinite(s->p3)))
-    return fail(c, RICH_EINVAL, "van Genuchten needs alpha > 0, n > 1, finite l");
+  if (const char* e = law_error(s->model, s->Ks, s->theta_s, s->theta_r, s->p1, s->p2, s->p3, s->p4,
+                                s->p1_field != nullptr, s->p2_field != nullptr))
+    return fail(c, RICH_EINVAL, e);
   if ((s->Ks_field && !finite_all(s->Ks_field, N)) || (s->p1_field && !finite_all(s->p1_field, N)) ||
       (s->p2_field && !finite_all(s->p2_field, N)))
     return fail(c, RICH_EINVAL, "non-finite value in a soil field");
@@ -1074,6 +1111,9 @@ richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
       if (!(s->p2_field[i] > 1.0)) return fail(c, RICH_EINVAL, "van Genuchten n field must exceed 1");
   c->soil = *s;
   c->soil.Ks_field = c->soil.p1_field = c->soil.p2_field = nullptr;
+  c->layered = false;
+  c->nmat = 0;
+  c->th_n_valid = c->th_nm1_valid = false;   // cached theta belongs to the old soil
   c->het_Ks = s->Ks_field != nullptr;
   c->het_p1 = s->p1_field != nullptr;
   c->het_p2 = s->p2_field != nullptr;
@@ -1113,6 +1153,116 @@ richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
     TRY(upload_views(c));
   }
   return RICH_OK;
+}
+
+richards_status richards_set_materials(richards_ctx* c, const richards_material* mats, int nmat,
+                                       const unsigned char* index) {
+  if (!c || !mats || !index) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  if (nmat < 1 || nmat > rich::MAXMAT) return fail(c, RICH_EINVAL, "need 1 to 8 materials");
+  for (int m = 0; m < nmat; ++m) {
+    const richards_material& M = mats[m];
+    if (const char* e = law_error(M.model, M.Ks, M.theta_s, M.theta_r, M.p1, M.p2, M.p3, M.p4, false, false))
+      return fail(c, RICH_EINVAL, std::string("material ") + std::to_string(m) + ": " + e);
+  }
+  const long long N = c->L[0].ncell;
+  for (long long i = 0; i < N; ++i)
+    if (index[i] >= nmat) return fail(c, RICH_EINVAL, "material index out of range");
+  cudaStreamSynchronize(c->s);
+  graphs_reset(c);
+  // material of every cell of every level: the fine index as given; a coarse
+  // cell takes the material with the largest total restriction weight among
+  // its fine cells (per-axis rows, weight (w0 w1) w2, summed over a2, a1, a0;
+  // ties: the lower index)
+  std::vector<std::vector<uint8_t>> mat(c->nlev);
+  mat[0].assign(index, index + N);
+  for (int l = 0; l + 1 < c->nlev; ++l) {
+    const HLevel& F = c->L[l];
+    const HLevel& C = c->L[l + 1];
+    std::vector<Row> R[3];
+    for (int a = 0; a < 3; ++a)
+      if (!restriction_rows(F.n[a], C.n[a], R[a])) return fail(c, RICH_EINVAL, "restriction stencil too wide");
+    mat[l + 1].resize(C.ncell);
+    for (int J2 = 0; J2 < C.n[2]; ++J2)
+      for (int J1 = 0; J1 < C.n[1]; ++J1)
+        for (int J0 = 0; J0 < C.n[0]; ++J0) {
+          const Row &r0 = R[0][J0], &r1 = R[1][J1], &r2 = R[2][J2];
+          double w[rich::MAXMAT] = {0.0};
+          for (int a2 = 0; a2 < r2.cnt; ++a2)
+            for (int a1 = 0; a1 < r1.cnt; ++a1)
+              for (int a0 = 0; a0 < r0.cnt; ++a0) {
+                const long long i = r0.idx[a0] + (long long)F.n[0] * (r1.idx[a1] + (long long)F.n[1] * r2.idx[a2]);
+                w[mat[l][i]] += r0.w[a0] * r1.w[a1] * r2.w[a2];
+              }
+          int best = 0;
+          for (int m = 1; m < nmat; ++m)
+            if (w[m] > w[best]) best = m;
+          mat[l + 1][J0 + (long long)C.n[0] * (J1 + (long long)C.n[1] * J2)] = (uint8_t)best;
+        }
+  }
+  // per-level arrays: material index, and p1, p2 (and the fine Ks) of each
+  // cell's material, not restricted
+  const bool mixed = c->opts.precision == 1;
+  if (!c->Ks) TRY(dalloc(c, &c->Ks, N));
+  std::vector<double> hKs(N);
+  for (long long i = 0; i < N; ++i) hKs[i] = mats[index[i]].Ks;
+  CK(cudaMemcpyAsync(c->Ks, hKs.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
+  std::vector<std::vector<double>> hp(2 * c->nlev);
+  for (int l = 0; l < c->nlev; ++l) {
+    HLevel& H = c->L[l];
+    if (!H.mat) TRY(dalloc(c, &H.mat, H.ncell));
+    if (!H.p1) TRY(dalloc(c, &H.p1, H.ncell));
+    if (!H.p2) TRY(dalloc(c, &H.p2, H.ncell));
+    if (mixed && !H.p1f) TRY(dalloc(c, &H.p1f, H.ncell));
+    if (mixed && !H.p2f) TRY(dalloc(c, &H.p2f, H.ncell));
+    std::vector<double>& q1 = hp[2 * l];
+    std::vector<double>& q2 = hp[2 * l + 1];
+    q1.resize(H.ncell);
+    q2.resize(H.ncell);
+    for (long long i = 0; i < H.ncell; ++i) {
+      q1[i] = mats[mat[l][i]].p1;
+      q2[i] = mats[mat[l][i]].p2;
+    }
+    CK(cudaMemcpyAsync(H.mat, mat[l].data(), H.ncell, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(H.p1, q1.data(), sizeof(double) * H.ncell, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(H.p2, q2.data(), sizeof(double) * H.ncell, cudaMemcpyHostToDevice, c->s));
+    if (mixed) {
+      rich::to_float(H.p1, H.p1f, H.ncell, c->s);
+      rich::to_float(H.p2, H.p2f, H.ncell, c->s);
+    }
+  }
+  // material tables (FP64, FP32, float-float)
+  if (!c->dmat64) TRY(dalloc(c, &c->dmat64, rich::MAXMAT));
+  if (!c->dmat32) TRY(dalloc(c, &c->dmat32, rich::MAXMAT));
+  if (!c->dmatdd) TRY(dalloc(c, &c->dmatdd, rich::MAXMAT));
+  rich::MatLaw<double> t64[rich::MAXMAT] = {};
+  rich::MatLaw<float> t32[rich::MAXMAT] = {};
+  rich::DDMat tdd[rich::MAXMAT] = {};
+  for (int m = 0; m < nmat; ++m) {
+    const richards_material& M = mats[m];
+    t64[m] = rich::MatLaw<double>{M.model, M.theta_s, M.theta_r, M.p3, M.p4};
+    t32[m] = rich::MatLaw<float>{M.model, (float)M.theta_s, (float)M.theta_r, (float)M.p3, (float)M.p4};
+    tdd[m] = rich::make_ddmat(t64[m]);
+  }
+  CK(cudaMemcpyAsync(c->dmat64, t64, sizeof(t64), cudaMemcpyHostToDevice, c->s));
+  CK(cudaMemcpyAsync(c->dmat32, t32, sizeof(t32), cudaMemcpyHostToDevice, c->s));
+  CK(cudaMemcpyAsync(c->dmatdd, tdd, sizeof(tdd), cudaMemcpyHostToDevice, c->s));
+  TRY(check_launch(c));
+  CK(cudaStreamSynchronize(c->s));
+  c->nmat = nmat;
+  for (int m = 0; m < nmat; ++m) c->mats[m] = mats[m];
+  richards_soil s0{};
+  s0.model = rich::COMPOSITE;
+  s0.Ks = mats[0].Ks;
+  s0.theta_s = mats[0].theta_s;
+  s0.theta_r = mats[0].theta_r;
+  s0.p1 = mats[0].p1; s0.p2 = mats[0].p2; s0.p3 = mats[0].p3; s0.p4 = mats[0].p4;
+  c->soil = s0;
+  c->layered = true;
+  c->het_Ks = c->het_p1 = c->het_p2 = true;
+  c->th_n_valid = c->th_nm1_valid = false;
+  c->soil_set = true;
+  return upload_views(c);
 }
 
 static richards_status refresh_sink(richards_ctx* c) {
@@ -1204,9 +1354,9 @@ richards_status richards_set_bc(richards_ctx* c, const richards_bc* b) {
     }
   c->bc_set = true;
   TRY(upload_views(c));
-  if (c->soil_set) {
-    richards_soil s = c->soil;   // re-run the coarse parameter restriction with the new tables
-    (void)s;
+  if (c->soil_set && !c->layered) {
+    // re-run the coarse parameter restriction with the new tables (a
+    // layered soil's coarse parameters come from the coarse materials)
     for (int l = 0; l + 1 < c->nlev; ++l) {
       const Level<double> Fv = view64(c, l), Cv = view64(c, l + 1);
       if (c->het_p1) rich::restrict64(Fv, Cv, xfer64(c, l), c->L[l].p1, nullptr, c->L[l + 1].p1, nullptr, c->s);
@@ -1267,7 +1417,8 @@ richards_status richards_soil_eval(richards_ctx* c, const double* psi, double* t
   HLevel& F = c->L[0];
   const Phys<double> P = phys<double>(c);
   rich::soil_eval(n, dpsi, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
-                  c->het_p2 ? F.p2 : nullptr, P, rich::make_ddphys(P), c->soil.model, arith == 1, dth, dK, c->s);
+                  c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, rich::make_ddphys(P), c->soil.model, arith == 1, dth,
+                  dK, c->s);
   richards_status st = check_launch(c);
   if (!on_device) {
     if (st == RICH_OK && theta) st = cudaMemcpyAsync(theta, dth, bytes, cudaMemcpyDeviceToHost, c->s) == cudaSuccess
@@ -1406,6 +1557,15 @@ richards_status richards_get_level(richards_ctx* c, int level, int which, double
     case 5: src = c->sink.enabled ? H.smax : nullptr; break;
     case 6: src = H.ubar; break;
     case 7: src = H.d; break;
+    case 8: {                         // material index (layered soils)
+      if (!c->layered) return fail(c, RICH_EINVAL, "array not available");
+      if (n != H.ncell) return fail(c, RICH_EINVAL, "size mismatch");
+      std::vector<uint8_t> m(H.ncell);
+      CK(cudaMemcpyAsync(m.data(), H.mat, H.ncell, cudaMemcpyDeviceToHost, c->s));
+      CK(cudaStreamSynchronize(c->s));
+      for (long long i = 0; i < H.ncell; ++i) out[i] = m[i];
+      return RICH_OK;
+    }
     default:
       if (which >= 10 && which < 16) { src = H.kb[which - 10]; cnt = H.nface[which - 10]; }
   }

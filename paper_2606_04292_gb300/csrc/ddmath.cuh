@@ -255,6 +255,50 @@ inline DDPhys make_ddphys(const Phys<double>& P) {
   return Q;
 }
 
+// float-float copy of one material of a layered soil (MatLaw<double>)
+struct DDMat {
+  int model;
+  dd ts, tr, ds, p3, p4;
+};
+
+inline DDMat make_ddmat(const MatLaw<double>& M) {
+  DDMat D;
+  D.model = M.model;
+  D.ts = host_split(M.ts);
+  D.tr = host_split(M.tr);
+  D.ds = host_split(M.ts - M.tr);
+  D.p3 = host_split(M.p3);
+  D.p4 = host_split(M.p4);
+  return D;
+}
+
+// with_law for the float-float kernels: fn(LawTag<law>{}, phys, ddphys) with
+// both records carrying the cell's theta_s, theta_r, p3, p4
+template <int MODEL, typename Fn>
+__device__ __forceinline__ auto with_law_dd(const Phys<double>& P, const DDPhys& Q, unsigned m, Fn&& fn) {
+  if constexpr (MODEL == COMPOSITE) {
+    const MatLaw<double>* __restrict__ M = P.mats + m;
+    const DDMat* __restrict__ D = P.ddmats + m;
+    Phys<double> Pc = P;
+    Pc.ts = M->ts;
+    Pc.tr = M->tr;
+    Pc.p3 = M->p3;
+    Pc.p4 = M->p4;
+    DDPhys Qc = Q;
+    Qc.ts = D->ts;
+    Qc.tr = D->tr;
+    Qc.ds = D->ds;
+    Qc.p3 = D->p3;
+    Qc.p4 = D->p4;
+    const int law = D->model;
+    if (law == HAVERKAMP) return fn(LawTag<HAVERKAMP>{}, (const Phys<double>&)Pc, (const DDPhys&)Qc);
+    if (law == GARDNER) return fn(LawTag<GARDNER>{}, (const Phys<double>&)Pc, (const DDPhys&)Qc);
+    return fn(LawTag<VANGENUCHTEN>{}, (const Phys<double>&)Pc, (const DDPhys&)Qc);
+  } else {
+    return fn(LawTag<MODEL>{}, P, Q);
+  }
+}
+
 // the same split on the device (per-column soil parameters)
 __device__ __forceinline__ DDPhys make_ddphys_dev(const Phys<double>& P) {
   DDPhys Q;

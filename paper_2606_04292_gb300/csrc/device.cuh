@@ -7,9 +7,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace rich {
 
-enum { HAVERKAMP = 0, GARDNER = 1, VANGENUCHTEN = 2 };
+// COMPOSITE: a layered soil (Section 4.1's composite law, Section 4.2's two
+// layers); every cell takes the law of its own material.
+enum { HAVERKAMP = 0, GARDNER = 1, VANGENUCHTEN = 2, COMPOSITE = 3 };
+constexpr int MAXMAT = 8;      // materials of a layered soil
 
 // FORM_DIRECT: the unknown is psi (eq. point-update as written).
 // FORM_DELTA:  the unknown is the correction delta to a frozen psi0, and the
@@ -29,7 +34,19 @@ struct Level {
   const T *Kc, *p1, *p2, *smax;  // lagged conductivity, soil params (nullable), sink coef (nullable)
   const T *psi0;                 // FORM_DELTA: frozen state
   const T *kb[6];                // boundary face conductances (per face cell)
+  const uint8_t *mat;            // COMPOSITE: material of each cell of this level
 };
+
+// One material of a layered soil: its law and the parameters that are not
+// per-cell arrays (p1 and p2 are: the level's p1/p2 hold each cell's
+// material values on every level).
+template <typename T>
+struct MatLaw {
+  int model;
+  T ts, tr, p3, p4;
+};
+
+struct DDMat;                    // float-float copy of a MatLaw (ddmath.cuh)
 
 template <typename T>
 struct Phys {
@@ -39,7 +56,45 @@ struct Phys {
   T h1, h2, h3, h4;              // sink thresholds
   int newton_k;                  // > 0: fixed steps; 0: to round-off
   int sink;
+  const MatLaw<T> *mats;         // COMPOSITE: material table (device, MAXMAT entries at most)
+  const DDMat *ddmats;           // COMPOSITE, float-float outer layer: the same table as pairs
 };
+
+template <int M>
+using LawTag = std::integral_constant<int, M>;
+
+// Calls fn(LawTag<law>{}, phys) with the law of a cell and the physics
+// record that carries its theta_s, theta_r, p3, p4: MODEL and P themselves,
+// or, for a layered soil (MODEL == COMPOSITE), the law and parameters of
+// material m.  Cells of one warp with different laws take the branches in turn.
+template <int MODEL, typename T, typename Fn>
+__device__ __forceinline__ auto with_law(const Phys<T>& P, unsigned m, Fn&& fn) {
+  if constexpr (MODEL == COMPOSITE) {
+    const MatLaw<T>* __restrict__ M = P.mats + m;
+    Phys<T> Q = P;
+    Q.ts = M->ts;
+    Q.tr = M->tr;
+    Q.p3 = M->p3;
+    Q.p4 = M->p4;
+    const int law = M->model;
+    if (law == HAVERKAMP) return fn(LawTag<HAVERKAMP>{}, (const Phys<T>&)Q);
+    if (law == GARDNER) return fn(LawTag<GARDNER>{}, (const Phys<T>&)Q);
+    return fn(LawTag<VANGENUCHTEN>{}, (const Phys<T>&)Q);
+  } else {
+    return fn(LawTag<MODEL>{}, P);
+  }
+}
+
+// material index of cell i (0, and no load, when the soil is not layered)
+template <int MODEL>
+__device__ __forceinline__ unsigned mat_at(const uint8_t* __restrict__ mat, long long i) {
+  if constexpr (MODEL == COMPOSITE) return mat[i];
+  else return 0u;
+}
+template <int MODEL, typename T>
+__device__ __forceinline__ unsigned mat_of(const Level<T>& L, long long i) {
+  return mat_at<MODEL>(L.mat, i);
+}
 
 template <typename T>
 struct Xfer {                    // fine level -> next coarser level
@@ -537,7 +592,9 @@ __device__ __forceinline__ void point_update(const Level<T>& L, const Phys<T>& P
   const T p2 = L.p2 ? L.p2[i] : P.p2;
   const T smax = L.smax ? L.smax[i] : T(0);
   const T psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
-  L.u[i] = point_solve<T, FORM, MODEL, NK>(cc, f, ui, psi0, p1, p2, smax, P);
+  L.u[i] = with_law<MODEL>(P, mat_of<MODEL>(L, i), [&](auto law, const Phys<T>& Q) {
+    return point_solve<T, FORM, decltype(law)::value, NK>(cc, f, ui, psi0, p1, p2, smax, Q);
+  });
 }
 
 // Operands of one point update, gathered before any of them is used, so that
@@ -550,14 +607,16 @@ struct CellOps {
   unsigned i;
   bool valid;
   unsigned bmask;                // bit f: face f lies on the boundary
+  unsigned mat;                  // COMPOSITE: the cell's material
   T ui, Ki, g, psi0, p1, p2, smax;
   T Kn[6], un[6];
 };
 
-template <typename T, int FORM>
+template <typename T, int FORM, int MODEL>
 __device__ __forceinline__ void gather(const Level<T>& L, const Phys<T>& P, int i0, int i1, int i2, CellOps<T>& c) {
   const unsigned i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
   c.i = i;
+  c.mat = mat_of<MODEL>(L, i);
   const T* __restrict__ Kp = L.Kc + i;
   const T* __restrict__ up = L.u + i;
   c.Ki = Kp[0];
@@ -605,7 +664,9 @@ __device__ __forceinline__ T solve_cell(const Level<T>& L, const Phys<T>& P, con
   }
   const T cc = P.xi + P.kappa + dg;
   const T f = c.g + of + P.kappa * c.ui;
-  return point_solve<T, FORM, MODEL, NK>(cc, f, c.ui, c.psi0, c.p1, c.p2, c.smax, P);
+  return with_law<MODEL>(P, c.mat, [&](auto law, const Phys<T>& Q) {
+    return point_solve<T, FORM, decltype(law)::value, NK>(cc, f, c.ui, c.psi0, c.p1, c.p2, c.smax, Q);
+  });
 }
 
 // N(u)_i = storage(u_i) + xi u_i + m_ii u_i - sum_j m_ij u_j   (eq. Nh-def)
@@ -619,7 +680,10 @@ __device__ __forceinline__ T apply_N(const Level<T>& L, const Phys<T>& P, const 
   const T smax = L.smax ? L.smax[i] : T(0);
   const T psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
   T val, der;
-  storage<T, FORM, MODEL>(u[i], psi0, p1, p2, smax, P, val, der);
+  with_law<MODEL>(P, mat_of<MODEL>(L, i), [&](auto law, const Phys<T>& Q) {
+    storage<T, FORM, decltype(law)::value>(u[i], psi0, p1, p2, smax, Q, val, der);
+    return 0;
+  });
   return val + P.xi * u[i] + mii * u[i] - off;
 }
 

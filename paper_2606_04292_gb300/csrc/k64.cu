@@ -35,41 +35,45 @@ template <int MODEL>
 __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* __restrict__ psin,
                                                      const double* __restrict__ psinm1, const double* __restrict__ Ks,
                                                      double Ks_s, const double* __restrict__ p1f,
-                                                     const double* __restrict__ p2f, Phys<double> P, int scheme,
-                                                     double dt, double* Kc, double* g, double* u,
-                                                     const double* thn_in, const double* thm_in, double* thn_out,
-                                                     double* thm_out) {
+                                                     const double* __restrict__ p2f, const uint8_t* __restrict__ mat,
+                                                     Phys<double> P, int scheme, double dt, double* Kc, double* g,
+                                                     double* u, const double* thn_in, const double* thm_in,
+                                                     double* thn_out, double* thm_out) {
   // thn_in / thm_in: theta(psi^n), theta(psi^{n-1}) kept from earlier FP64
   // evaluations (nullable: evaluate here, and keep them in *_out if given)
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double p1 = p1f ? p1f[i] : P.p1, p2 = p2f ? p2f[i] : P.p2;
     const double ks = Ks ? Ks[i] : Ks_s;
     const double pn = psin[i];
-    double thn;
-    if (thn_in) {
-      thn = thn_in[i];
-    } else {
-      thn = theta_only_d<MODEL>(pn, p1, p2, P);
-      if (thn_out) thn_out[i] = thn;
-    }
-    double ps, hist;
-    if (scheme == 1) {
-      ps = pn;
-      hist = thn / dt;
-    } else {
-      const double pm = psinm1[i];
-      double thm;
-      if (thm_in) {
-        thm = thm_in[i];
+    with_law<MODEL>(P, mat_at<MODEL>(mat, i), [&](auto law, const Phys<double>& Q) {
+      constexpr int ML = decltype(law)::value;
+      double thn;
+      if (thn_in) {
+        thn = thn_in[i];
       } else {
-        thm = theta_only_d<MODEL>(pm, p1, p2, P);
-        if (thm_out) thm_out[i] = thm;
+        thn = theta_only_d<ML>(pn, p1, p2, Q);
+        if (thn_out) thn_out[i] = thn;
       }
-      ps = 2.0 * pn - pm;
-      hist = (4.0 * thn - thm) / (2.0 * dt);
-    }
-    Kc[i] = cond_d<MODEL>(ps, p1, p2, ks, P);
-    g[i] = hist + P.xi * ps;
+      double ps, hist;
+      if (scheme == 1) {
+        ps = pn;
+        hist = thn / dt;
+      } else {
+        const double pm = psinm1[i];
+        double thm;
+        if (thm_in) {
+          thm = thm_in[i];
+        } else {
+          thm = theta_only_d<ML>(pm, p1, p2, Q);
+          if (thm_out) thm_out[i] = thm;
+        }
+        ps = 2.0 * pn - pm;
+        hist = (4.0 * thn - thm) / (2.0 * dt);
+      }
+      Kc[i] = cond_d<ML>(ps, p1, p2, ks, Q);
+      g[i] = hist + P.xi * ps;
+      return 0;
+    });
     u[i] = pn;
   }
 }
@@ -82,7 +86,8 @@ __global__ void __launch_bounds__(256) k_prep_lagged_dd(long long n, const doubl
                                                         const double* __restrict__ psinm1,
                                                         const double* __restrict__ Ks, dd Ks_s,
                                                         const double* __restrict__ p1f,
-                                                        const double* __restrict__ p2f, Phys<double> P, DDPhys Q,
+                                                        const double* __restrict__ p2f,
+                                                        const uint8_t* __restrict__ mat, Phys<double> P, DDPhys Q,
                                                         int scheme, dd hist_scale, double* Kc, float* Kcf, double* g,
                                                         double* u, const double* thn_in, const double* thm_in,
                                                         double* thn_out, double* thm_out, bool predict) {
@@ -91,34 +96,38 @@ __global__ void __launch_bounds__(256) k_prep_lagged_dd(long long n, const doubl
     const dd p1 = p1f ? dd_split(p1f[i]) : Q.p1, p2 = p2f ? dd_split(p2f[i]) : Q.p2;
     const double pnd = psin[i];
     const dd pn = dd_split(pnd);
-    dd thn;
-    if (thn_in) {
-      thn = dd_split(thn_in[i]);
-    } else {
-      thn = theta_x<MODEL>(pn, p1, p2, Q, P);
-      if (thn_out) thn_out[i] = dd_join(thn);
-    }
-    dd ps, hist;
-    if (scheme == 1) {
-      ps = pn;
-      hist = dd_mul(thn, hist_scale);
-    } else {
-      const dd pm = dd_split(psinm1[i]);
-      dd thm;
-      if (thm_in) {
-        thm = dd_split(thm_in[i]);
+    with_law_dd<MODEL>(P, Q, mat_at<MODEL>(mat, i), [&](auto law, const Phys<double>& Pc, const DDPhys& Qc) {
+      constexpr int ML = decltype(law)::value;
+      dd thn;
+      if (thn_in) {
+        thn = dd_split(thn_in[i]);
       } else {
-        thm = theta_x<MODEL>(pm, p1, p2, Q, P);
-        if (thm_out) thm_out[i] = dd_join(thm);
+        thn = theta_x<ML>(pn, p1, p2, Qc, Pc);
+        if (thn_out) thn_out[i] = dd_join(thn);
       }
-      ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
-      hist = dd_mul(dd_sub(mk(4.0f * thn.hi, 4.0f * thn.lo), thm), hist_scale);
-    }
-    const dd K = cond_x<MODEL>(ps, p1, p2, Ks ? dd_split(Ks[i]) : Ks_s, Q, P);
-    Kc[i] = dd_join(K);
-    Kcf[i] = dd_float(K);
-    g[i] = dd_join(dd_add(hist, dd_mul(Q.xi, ps)));
-    u[i] = predict ? dd_join(ps) : pnd;
+      dd ps, hist;
+      if (scheme == 1) {
+        ps = pn;
+        hist = dd_mul(thn, hist_scale);
+      } else {
+        const dd pm = dd_split(psinm1[i]);
+        dd thm;
+        if (thm_in) {
+          thm = dd_split(thm_in[i]);
+        } else {
+          thm = theta_x<ML>(pm, p1, p2, Qc, Pc);
+          if (thm_out) thm_out[i] = dd_join(thm);
+        }
+        ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
+        hist = dd_mul(dd_sub(mk(4.0f * thn.hi, 4.0f * thn.lo), thm), hist_scale);
+      }
+      const dd K = cond_x<ML>(ps, p1, p2, Ks ? dd_split(Ks[i]) : Ks_s, Qc, Pc);
+      Kc[i] = dd_join(K);
+      Kcf[i] = dd_float(K);
+      g[i] = dd_join(dd_add(hist, dd_mul(Q.xi, ps)));
+      u[i] = predict ? dd_join(ps) : pnd;
+      return 0;
+    });
   }
 }
 
@@ -129,7 +138,8 @@ __global__ void __launch_bounds__(256) k_prep_lagged_dd(long long n, const doubl
 template <int MODEL>
 __global__ void __launch_bounds__(256) k_prep_rhs(Geom G, BcDev bc, const double* __restrict__ Ks, double Ks_s,
                                                   const double* __restrict__ p1f, const double* __restrict__ p2f,
-                                                  Phys<double> P, const double* __restrict__ Kc, double* g,
+                                                  const uint8_t* __restrict__ mat, Phys<double> P,
+                                                  const double* __restrict__ Kc, double* g,
                                                   double* kb0, double* kb1, double* kb2, double* kb3, double* kb4,
                                                   double* kb5) {
   double* kb[6] = {kb0, kb1, kb2, kb3, kb4, kb5};
@@ -158,7 +168,10 @@ __global__ void __launch_bounds__(256) k_prep_rhs(Geom G, BcDev bc, const double
         const double val = bc.vfield[f] ? bc.vfield[f][fc] : bc.value[f];
         if (dir) {
           const double p1 = p1f ? p1f[i] : P.p1, p2 = p2f ? p2f[i] : P.p2;
-          const double Kb = cond_d<MODEL>(val, p1, p2, Ks ? Ks[i] : Ks_s, P);
+          const double ks = Ks ? Ks[i] : Ks_s;
+          const double Kb = with_law<MODEL>(P, mat_at<MODEL>(mat, i), [&](auto law, const Phys<double>& Q) {
+            return cond_d<decltype(law)::value>(val, p1, p2, ks, Q);
+          });
           const double k = 0.5 * (Ki + Kb);
           kb[f][fc] = k;
           const double dz = (ax == v) ? (side ? 0.5 * h : -0.5 * h) : 0.0;
@@ -267,7 +280,10 @@ __global__ void __launch_bounds__(128) k_outer_residual_dd(Level<double> L, Phys
     if (th_in) {
       th = dd_split(th_in[i]);
     } else {
-      th = theta_x<MODEL>(ui, L.p1 ? dd_split(L.p1[i]) : Q.p1, L.p2 ? dd_split(L.p2[i]) : Q.p2, Q, P);
+      const dd p1 = L.p1 ? dd_split(L.p1[i]) : Q.p1, p2 = L.p2 ? dd_split(L.p2[i]) : Q.p2;
+      th = with_law_dd<MODEL>(P, Q, mat_of<MODEL>(L, i), [&](auto law, const Phys<double>& Pc, const DDPhys& Qc) {
+        return theta_x<decltype(law)::value>(ui, p1, p2, Qc, Pc);
+      });
       if (th_out) th_out[i] = dd_join(th);
     }
     const dd S = L.smax ? sink_x(ui, dd_split(L.smax[i]), Q) : mk(0.0f);
@@ -291,52 +307,41 @@ __global__ void __launch_bounds__(256) k_apply_delta(double* u, const float* del
 }
 
 void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
-                 const double* p1, const double* p2, const Phys<double>& P, int model, int scheme, double dt,
-                 double* Kc, double* g, double* u, const double* thn_in, const double* thm_in, double* thn_out,
-                 double* thm_out, cudaStream_t s) {
+                 const double* p1, const double* p2, const uint8_t* mat, const Phys<double>& P, int model, int scheme,
+                 double dt, double* Kc, double* g, double* u, const double* thn_in, const double* thm_in,
+                 double* thn_out, double* thm_out, cudaStream_t s) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
   const int b = grid_for(n);
-  if (model == HAVERKAMP)
-    k_prep_lagged<HAVERKAMP><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, P, scheme, dt, Kc, g, u, thn_in,
-                                               thm_in, thn_out, thm_out);
-  else if (model == GARDNER)
-    k_prep_lagged<GARDNER><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, P, scheme, dt, Kc, g, u, thn_in,
-                                             thm_in, thn_out, thm_out);
-  else
-    k_prep_lagged<VANGENUCHTEN><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, P, scheme, dt, Kc, g, u, thn_in,
-                                                  thm_in, thn_out, thm_out);
+  by_model(model, [&](auto m) {
+    k_prep_lagged<decltype(m)::value><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, mat, P, scheme, dt, Kc, g,
+                                                        u, thn_in, thm_in, thn_out, thm_out);
+  });
 }
 
 void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
-                    const double* p1, const double* p2, const Phys<double>& P, const DDPhys& Q, int model,
-                    int scheme, double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
-                    const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s) {
+                    const double* p1, const double* p2, const uint8_t* mat, const Phys<double>& P, const DDPhys& Q,
+                    int model, int scheme, double dt, double* Kc, float* Kcf, double* g, double* u,
+                    const double* thn_in, const double* thm_in, double* thn_out, double* thm_out, bool predict,
+                    cudaStream_t s) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
   const int b = grid_for(n);
   const dd ks = host_split(Ks_s), hs = host_split(scheme == 1 ? 1.0 / dt : 1.0 / (2.0 * dt));
   predict = predict && scheme == 2;
-  if (model == HAVERKAMP)
-    k_prep_lagged_dd<HAVERKAMP><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, P, Q, scheme, hs, Kc, Kcf, g, u,
-                                                  thn_in, thm_in, thn_out, thm_out, predict);
-  else if (model == GARDNER)
-    k_prep_lagged_dd<GARDNER><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, P, Q, scheme, hs, Kc, Kcf, g, u,
-                                                thn_in, thm_in, thn_out, thm_out, predict);
-  else
-    k_prep_lagged_dd<VANGENUCHTEN><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, P, Q, scheme, hs, Kc, Kcf, g,
-                                                     u, thn_in, thm_in, thn_out, thm_out, predict);
+  by_model(model, [&](auto m) {
+    k_prep_lagged_dd<decltype(m)::value><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, ks, p1, p2, mat, P, Q, scheme, hs, Kc,
+                                                           Kcf, g, u, thn_in, thm_in, thn_out, thm_out, predict);
+  });
 }
 
 void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
-              const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6], cudaStream_t s) {
+              const uint8_t* mat, const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6],
+              cudaStream_t s) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
   const int b = grid_for(n);
-  if (model == HAVERKAMP)
-    k_prep_rhs<HAVERKAMP><<<b, 256, 0, s>>>(G, bc, Ks, Ks_s, p1, p2, P, Kc, g, kb[0], kb[1], kb[2], kb[3], kb[4], kb[5]);
-  else if (model == GARDNER)
-    k_prep_rhs<GARDNER><<<b, 256, 0, s>>>(G, bc, Ks, Ks_s, p1, p2, P, Kc, g, kb[0], kb[1], kb[2], kb[3], kb[4], kb[5]);
-  else
-    k_prep_rhs<VANGENUCHTEN><<<b, 256, 0, s>>>(G, bc, Ks, Ks_s, p1, p2, P, Kc, g, kb[0], kb[1], kb[2], kb[3], kb[4],
-                                               kb[5]);
+  by_model(model, [&](auto m) {
+    k_prep_rhs<decltype(m)::value><<<b, 256, 0, s>>>(G, bc, Ks, Ks_s, p1, p2, mat, P, Kc, g, kb[0], kb[1], kb[2], kb[3],
+                                                     kb[4], kb[5]);
+  });
 }
 
 void restrict_face64(const Geom& F, const Geom& C, const Xfer<double>& X, int axis, const double* fine,
@@ -369,44 +374,45 @@ void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPh
                        float* psi0f, float* delta, unsigned long long* norm, const double* th_in, double* th_out,
                        cudaStream_t s) {
   const Launch3 g = launch3(L.n0, L.n1, L.n2);
-  if (model == HAVERKAMP)
-    k_outer_residual_dd<HAVERKAMP><<<g.grid, g.block, 0, s>>>(L, P, Q, r32, psi0f, delta, norm, th_in, th_out);
-  else if (model == GARDNER)
-    k_outer_residual_dd<GARDNER><<<g.grid, g.block, 0, s>>>(L, P, Q, r32, psi0f, delta, norm, th_in, th_out);
-  else
-    k_outer_residual_dd<VANGENUCHTEN><<<g.grid, g.block, 0, s>>>(L, P, Q, r32, psi0f, delta, norm, th_in, th_out);
+  by_model(model, [&](auto m) {
+    k_outer_residual_dd<decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, Q, r32, psi0f, delta, norm, th_in,
+                                                                       th_out);
+  });
 }
 
 template <int MODEL, bool DD>
 __global__ void __launch_bounds__(256) k_soil_eval(long long n, const double* __restrict__ psi,
                                                    const double* __restrict__ Ks, double Ks_s,
                                                    const double* __restrict__ p1f, const double* __restrict__ p2f,
-                                                   Phys<double> P, DDPhys Q, double* theta, double* K) {
+                                                   const uint8_t* __restrict__ mat, Phys<double> P, DDPhys Q,
+                                                   double* theta, double* K) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double p1 = p1f ? p1f[i] : P.p1, p2 = p2f ? p2f[i] : P.p2, x = psi[i];
-    if (theta) theta[i] = DD ? theta_dd<MODEL>(x, p1, p2, Q, P) : theta_only_d<MODEL>(x, p1, p2, P);
-    if (K) {
-      const double ks = Ks ? Ks[i] : Ks_s;
-      K[i] = DD ? cond_dd<MODEL>(x, p1, p2, ks, Q, P) : cond_d<MODEL>(x, p1, p2, ks, P);
-    }
+    const double ks = Ks ? Ks[i] : Ks_s;
+    with_law_dd<MODEL>(P, Q, mat_at<MODEL>(mat, i), [&](auto law, const Phys<double>& Pc, const DDPhys& Qc) {
+      constexpr int ML = decltype(law)::value;
+      if (theta) theta[i] = DD ? theta_dd<ML>(x, p1, p2, Qc, Pc) : theta_only_d<ML>(x, p1, p2, Pc);
+      if (K) K[i] = DD ? cond_dd<ML>(x, p1, p2, ks, Qc, Pc) : cond_d<ML>(x, p1, p2, ks, Pc);
+      return 0;
+    });
   }
 }
 
 template <bool DD>
 static void soil_eval_t(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1,
-                        const double* p2, const Phys<double>& P, const DDPhys& Q, int model, double* theta,
-                        double* K, cudaStream_t s) {
+                        const double* p2, const uint8_t* mat, const Phys<double>& P, const DDPhys& Q, int model,
+                        double* theta, double* K, cudaStream_t s) {
   const int b = grid_for(n);
-  if (model == HAVERKAMP) k_soil_eval<HAVERKAMP, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, Q, theta, K);
-  else if (model == GARDNER) k_soil_eval<GARDNER, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, Q, theta, K);
-  else k_soil_eval<VANGENUCHTEN, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, P, Q, theta, K);
+  by_model(model, [&](auto m) {
+    k_soil_eval<decltype(m)::value, DD><<<b, 256, 0, s>>>(n, psi, Ks, Ks_s, p1, p2, mat, P, Q, theta, K);
+  });
 }
 
 void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1, const double* p2,
-               const Phys<double>& P, const DDPhys& Q, int model, bool dd, double* theta, double* K,
-               cudaStream_t s) {
-  if (dd) soil_eval_t<true>(n, psi, Ks, Ks_s, p1, p2, P, Q, model, theta, K, s);
-  else soil_eval_t<false>(n, psi, Ks, Ks_s, p1, p2, P, Q, model, theta, K, s);
+               const uint8_t* mat, const Phys<double>& P, const DDPhys& Q, int model, bool dd, double* theta,
+               double* K, cudaStream_t s) {
+  if (dd) soil_eval_t<true>(n, psi, Ks, Ks_s, p1, p2, mat, P, Q, model, theta, K, s);
+  else soil_eval_t<false>(n, psi, Ks, Ks_s, p1, p2, mat, P, Q, model, theta, K, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -447,18 +453,23 @@ __global__ void __launch_bounds__(256) k_mass_balance(Level<double> L, Geom G, B
     cell_coords(G.n0, G.n1, i, ii[0], ii[1], ii[2]);
     const dd p1 = L.p1 ? dd_split(L.p1[i]) : Q.p1, p2 = L.p2 ? dd_split(L.p2[i]) : Q.p2;
     const dd psi = dd_split(L.u[i]), pn = dd_split(psin[i]);
-    const dd th1 = th_new ? dd_split(th_new[i]) : theta_x<MODEL>(psi, p1, p2, Q, P);
-    const dd thn = th_n ? dd_split(th_n[i]) : theta_x<MODEL>(pn, p1, p2, Q, P);
-    dd hist, ps;
-    if (scheme == 1) {
-      hist = dd_mul(thn, hist_scale);
-      ps = pn;
-    } else {
-      const dd pm = dd_split(psinm1[i]);
-      const dd thm = th_nm1 ? dd_split(th_nm1[i]) : theta_x<MODEL>(pm, p1, p2, Q, P);
-      hist = dd_mul(dd_sub(mk(4.0f * thn.hi, 4.0f * thn.lo), thm), hist_scale);
-      ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
-    }
+    const unsigned mi = mat_of<MODEL>(L, i);
+    dd th1, thn, hist, ps;
+    with_law_dd<MODEL>(P, Q, mi, [&](auto law, const Phys<double>& Pc, const DDPhys& Qc) {
+      constexpr int ML = decltype(law)::value;
+      th1 = th_new ? dd_split(th_new[i]) : theta_x<ML>(psi, p1, p2, Qc, Pc);
+      thn = th_n ? dd_split(th_n[i]) : theta_x<ML>(pn, p1, p2, Qc, Pc);
+      if (scheme == 1) {
+        hist = dd_mul(thn, hist_scale);
+        ps = pn;
+      } else {
+        const dd pm = dd_split(psinm1[i]);
+        const dd thm = th_nm1 ? dd_split(th_nm1[i]) : theta_x<ML>(pm, p1, p2, Qc, Pc);
+        hist = dd_mul(dd_sub(mk(4.0f * thn.hi, 4.0f * thn.lo), thm), hist_scale);
+        ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
+      }
+      return 0;
+    });
     const dd smax = L.smax ? dd_split(L.smax[i]) : mk(0.0f);
     dd cell = dd_sub(dd_mul(Q.a, th1), hist);
     cell = dd_add(cell, sink_x(psi, smax, Q));
@@ -494,7 +505,11 @@ __global__ void __launch_bounds__(256) k_mass_balance(Level<double> L, Geom G, B
     // a theta' + S' + xi at psi (FP32 increment laws with a zero increment)
     const float psif = dd_float(psi), p1f = dd_float(p1), p2f = dd_float(p2);
     float Dth, dth;
-    dincr<MODEL>(dbase<MODEL>(psif, p1f, p2f), 0.0f, p1f, p2f, Pf, Dth, dth);
+    with_law<MODEL>(Pf, mi, [&](auto law, const Phys<float>& Qf) {
+      constexpr int ML = decltype(law)::value;
+      dincr<ML>(dbase<ML>(psif, p1f, p2f), 0.0f, p1f, p2f, Qf, Dth, dth);
+      return 0;
+    });
     const float smf = dd_float(smax);
     float sa = 0.0f, sda = 0.0f;
     if (Pf.sink && smf > 0.0f) feddes(psif, Pf, sa, sda);
@@ -526,15 +541,10 @@ int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const P
   const int b = grid_for(L.ncell);
   const DDPhys Q = make_ddphys(P);
   const dd hs = host_split(scheme == 1 ? 1.0 / dt : 1.0 / (2.0 * dt));
-  if (model == HAVERKAMP)
-    k_mass_balance<HAVERKAMP><<<b, 256, 0, s>>>(L, G, bc, P, Q, Pf, psin, psinm1, scheme, hs, th_new, th_n, th_nm1,
-                                                part, dmin_bits);
-  else if (model == GARDNER)
-    k_mass_balance<GARDNER><<<b, 256, 0, s>>>(L, G, bc, P, Q, Pf, psin, psinm1, scheme, hs, th_new, th_n, th_nm1,
-                                              part, dmin_bits);
-  else
-    k_mass_balance<VANGENUCHTEN><<<b, 256, 0, s>>>(L, G, bc, P, Q, Pf, psin, psinm1, scheme, hs, th_new, th_n,
-                                                   th_nm1, part, dmin_bits);
+  by_model(model, [&](auto m) {
+    k_mass_balance<decltype(m)::value><<<b, 256, 0, s>>>(L, G, bc, P, Q, Pf, psin, psinm1, scheme, hs, th_new, th_n,
+                                                         th_nm1, part, dmin_bits);
+  });
   return b;
 }
 

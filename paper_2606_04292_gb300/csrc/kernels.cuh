@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int c
   {
     const int i0 = 2 * p + ((color + i1 + z0) & 1);
     c[0].valid = z0 < L.n2 && i0 < L.n0;
-    if (c[0].valid) gather<T, FORM>(L, P, i0, i1, z0, c[0]);
+    if (c[0].valid) gather<T, FORM, MODEL>(L, P, i0, i1, z0, c[0]);
   }
 #pragma unroll
   for (int k = 0; k < ZC; ++k) {
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int c
       const int i0 = 2 * p + ((color + i1 + i2) & 1);
       CellOps<T>& nx = c[(k + 1) & 1];
       nx.valid = i2 < L.n2 && i0 < L.n0;
-      if (nx.valid) gather<T, FORM>(L, P, i0, i1, i2, nx);
+      if (nx.valid) gather<T, FORM, MODEL>(L, P, i0, i1, i2, nx);
     }
     const CellOps<T>& cur = c[k & 1];
     if (cur.valid) L.u[cur.i] = solve_cell<T, FORM, MODEL, NK>(L, P, cur);
@@ -394,14 +394,23 @@ inline Launch3 launch3(int nx, int n1, int n2) {
   return L;
 }
 
+// host: calls fn(LawTag<model>{}) for a runtime law (COMPOSITE included)
+template <typename Fn>
+inline void by_model(int model, Fn&& fn) {
+  if (model == HAVERKAMP) fn(LawTag<HAVERKAMP>{});
+  else if (model == GARDNER) fn(LawTag<GARDNER>{});
+  else if (model == COMPOSITE) fn(LawTag<COMPOSITE>{});
+  else fn(LawTag<VANGENUCHTEN>{});
+}
+
 template <typename T, int FORM>
 struct Dispatch {
   template <int NK>
   static void sweep_nk(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
     const Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
-    if (model == HAVERKAMP) k_sweep<T, FORM, HAVERKAMP, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
-    else if (model == GARDNER) k_sweep<T, FORM, GARDNER, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
-    else k_sweep<T, FORM, VANGENUCHTEN, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+    by_model(model, [&](auto m) {
+      k_sweep<T, FORM, decltype(m)::value, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+    });
   }
   // the FP32 increment form compiles the common fixed step counts 1 and 2
   static void sweep(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
@@ -413,9 +422,9 @@ struct Dispatch {
   static void sweep_pipe_zk(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
     Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
     g.grid.z = (L.n2 + ZC - 1) / ZC;
-    if (model == HAVERKAMP) k_sweep_pipe<T, FORM, HAVERKAMP, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
-    else if (model == GARDNER) k_sweep_pipe<T, FORM, GARDNER, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
-    else k_sweep_pipe<T, FORM, VANGENUCHTEN, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+    by_model(model, [&](auto m) {
+      k_sweep_pipe<T, FORM, decltype(m)::value, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+    });
   }
   template <int ZC>
   static void sweep_pipe_z(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
@@ -435,15 +444,13 @@ struct Dispatch {
   static void residual(const Level<T>& L, const Phys<T>& P, int model, unsigned long long* norm,
                        cudaStream_t s) {
     const Launch3 g = launch3(L.n0, L.n1, L.n2);
-    if (model == HAVERKAMP) k_residual<T, FORM, HAVERKAMP><<<g.grid, g.block, 0, s>>>(L, P, norm);
-    else if (model == GARDNER) k_residual<T, FORM, GARDNER><<<g.grid, g.block, 0, s>>>(L, P, norm);
-    else k_residual<T, FORM, VANGENUCHTEN><<<g.grid, g.block, 0, s>>>(L, P, norm);
+    by_model(model, [&](auto m) {
+      k_residual<T, FORM, decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, norm);
+    });
   }
   static void tau(const Level<T>& C, const Phys<T>& P, int model, cudaStream_t s) {
     const Launch3 g = launch3(C.n0, C.n1, C.n2);
-    if (model == HAVERKAMP) k_tau<T, FORM, HAVERKAMP><<<g.grid, g.block, 0, s>>>(C, P);
-    else if (model == GARDNER) k_tau<T, FORM, GARDNER><<<g.grid, g.block, 0, s>>>(C, P);
-    else k_tau<T, FORM, VANGENUCHTEN><<<g.grid, g.block, 0, s>>>(C, P);
+    by_model(model, [&](auto m) { k_tau<T, FORM, decltype(m)::value><<<g.grid, g.block, 0, s>>>(C, P); });
   }
   static void restrict2(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, const T* fa, const T* fb,
                         T* ca, T* cb, cudaStream_t s) {
@@ -463,15 +470,10 @@ struct Dispatch {
   static void tail(const Level<T>* dLs, const Xfer<T>* dXs, int l0, int nl, const Phys<T>& P, int model,
                    int nu1, int nu2, int cmax, T crtol, int gamma, int gamma_levels, unsigned long long* stats,
                    cudaStream_t s) {
-    if (model == HAVERKAMP)
-      k_tail<T, FORM, HAVERKAMP><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, gamma,
-                                                             gamma_levels, stats);
-    else if (model == GARDNER)
-      k_tail<T, FORM, GARDNER><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, gamma,
-                                                           gamma_levels, stats);
-    else
-      k_tail<T, FORM, VANGENUCHTEN><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol, gamma,
-                                                                gamma_levels, stats);
+    by_model(model, [&](auto m) {
+      k_tail<T, FORM, decltype(m)::value><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol,
+                                                                      gamma, gamma_levels, stats);
+    });
   }
 };
 

@@ -49,13 +49,15 @@ void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, con
             unsigned long long* stats,
             cudaStream_t s);
 
-// per-step preparation (FP64)
+// per-step preparation (FP64).  mat: the fine level's material index (read
+// only when model == COMPOSITE; nullable otherwise)
 void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
-                 const double* p1, const double* p2, const Phys<double>& P, int model, int scheme, double dt,
-                 double* Kc, double* g, double* u, const double* thn_in, const double* thm_in, double* thn_out,
-                 double* thm_out, cudaStream_t s);
+                 const double* p1, const double* p2, const uint8_t* mat, const Phys<double>& P, int model, int scheme,
+                 double dt, double* Kc, double* g, double* u, const double* thn_in, const double* thm_in,
+                 double* thn_out, double* thm_out, cudaStream_t s);
 void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
-              const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6], cudaStream_t s);
+              const uint8_t* mat, const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6],
+              cudaStream_t s);
 void restrict_face64(const Geom& F, const Geom& C, const Xfer<double>& X, int axis, const double* fine,
                      double* coarse, cudaStream_t s);
 void sink_coef(const Geom& G, double Tp, double depth, double decay, double* smax, cudaStream_t s);
@@ -70,9 +72,10 @@ void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPh
 // mixed mode: the lagged state in float-float (Kc to FP64 and FP32)
 // (predict: u = psi* instead of psi^n)
 void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
-                    const double* p1, const double* p2, const Phys<double>& P, const DDPhys& Q, int model,
-                    int scheme, double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
-                    const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s);
+                    const double* p1, const double* p2, const uint8_t* mat, const Phys<double>& P, const DDPhys& Q,
+                    int model, int scheme, double dt, double* Kc, float* Kcf, double* g, double* u,
+                    const double* thn_in, const double* thm_in, double* thn_out, double* thm_out, bool predict,
+                    cudaStream_t s);
 // water balance of a step: per-block partial sums into part (returns the
 // block count) and min_i(a theta' + S' + xi) as float bits into *dmin_bits
 int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const Phys<double>& P, const Phys<float>& Pf,
@@ -83,7 +86,7 @@ void restrict_face32(const Geom& F, const Geom& C, const Xfer<float>& X, int axi
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);
 // theta(psi) and K(psi) per cell (FP64 or float-float); outputs nullable
 void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1, const double* p2,
-               const Phys<double>& P, const DDPhys& Q, int model, bool dd, double* theta, double* K,
-               cudaStream_t s);
+               const uint8_t* mat, const Phys<double>& P, const DDPhys& Q, int model, bool dd, double* theta,
+               double* K, cudaStream_t s);
 
 }  // namespace rich

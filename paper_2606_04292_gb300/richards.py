@@ -37,6 +37,11 @@ class richards_soil(C.Structure):
                 ("p2_field", C.POINTER(C.c_double))]
 
 
+class richards_material(C.Structure):
+    _fields_ = [("model", C.c_int), ("Ks", C.c_double), ("theta_s", C.c_double), ("theta_r", C.c_double),
+                ("p1", C.c_double), ("p2", C.c_double), ("p3", C.c_double), ("p4", C.c_double)]
+
+
 class richards_bc(C.Structure):
     _fields_ = [("kind", C.c_int * 6), ("value", C.c_double * 6),
                 ("value_field", C.POINTER(C.c_double) * 6), ("mask_field", C.POINTER(C.c_ubyte) * 6)]
@@ -85,6 +90,7 @@ _lib = None
 _SIGS = {
     "richards_create": (C.c_int, [C.POINTER(richards_grid), C.POINTER(richards_opts), _VP, C.POINTER(_VP)]),
     "richards_set_soil": (C.c_int, [_VP, C.POINTER(richards_soil)]),
+    "richards_set_materials": (C.c_int, [_VP, C.POINTER(richards_material), C.c_int, C.POINTER(C.c_ubyte)]),
     "richards_set_bc": (C.c_int, [_VP, C.POINTER(richards_bc)]),
     "richards_set_sink": (C.c_int, [_VP, C.POINTER(richards_sink)]),
     "richards_set_state": (C.c_int, [_VP, _DP, _DP, C.c_double]),
@@ -227,6 +233,9 @@ class Solver:
 
     # -- set-up ----------------------------------------------------------
     def set_soil(self, s):
+        if s.get("materials"):
+            self.set_materials(s["materials"], s["material_index"])
+            return
         soil = richards_soil(s["model"], s["Ks"], s["theta_s"], s["theta_r"], s["p1"], s["p2"], s["p3"], s["p4"])
         for key in ("Ks_field", "p1_field", "p2_field"):
             if s.get(key) is not None:
@@ -234,6 +243,17 @@ class Solver:
                 self._keep.append(arr)
                 setattr(soil, key, _dp(arr))
         _check(lib().richards_set_soil(self.h, C.byref(soil)), self.h)
+
+    def set_materials(self, mats, index):
+        """Layered soil: a list of per-material law dicts and a uint8 index per cell."""
+        arr = (richards_material * len(mats))(*[
+            richards_material(m["model"], m["Ks"], m["theta_s"], m["theta_r"], m["p1"], m["p2"], m["p3"], m["p4"])
+            for m in mats])
+        idx = np.ascontiguousarray(index, dtype=np.uint8)
+        if idx.size != self.N:
+            raise RichardsError(RICH_EINVAL, "material index size mismatch")
+        _check(lib().richards_set_materials(self.h, arr, len(mats), idx.ctypes.data_as(C.POINTER(C.c_ubyte))),
+               self.h)
 
     def set_bc(self, b):
         bc = richards_bc()

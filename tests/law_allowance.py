@@ -18,7 +18,9 @@ def law_allowance(orc, prob, psi, eps):
     Kc = orc.Kc(0).reshape(n2, n1, n0)
     P = np.asarray(psi, dtype=np.float64).reshape(n2, n1, n0)
     h = [prob["L"][a] / prob["n"][a] for a in range(dim)]
-    tot = np.abs(orc.g(0)).reshape(n2, n1, n0) + orc.a * prob["soil"]["theta_s"]
+    mats = prob["soil"].get("materials")
+    ts = max(m["theta_s"] for m in mats) if mats else prob["soil"]["theta_s"]
+    tot = np.abs(orc.g(0)).reshape(n2, n1, n0) + orc.a * ts
     for a in range(dim):
         ax = 2 - a
         sl_lo = [slice(None)] * 3
