@@ -273,24 +273,29 @@ def gardner_cpu(states):
             "max_abs_dpsi_gpu_vs_oracle": {k: float(np.max(np.abs(v - ref))) for k, v in states.items()}}
 
 
-LAYERED_STEPS = 100       # two-layer field: 1 h at tau = 0.01 h
+LAYERED_STEPS = 100       # two-layer field, FP64 plain: 1 h at tau = 0.01 h
+LAYERED_FULL_STEPS = 4200  # the paper's whole two-layer run: 1.75 days = 42 h at tau = 0.01 h
 LAYERED_CPU_STEPS = 3
 
 
 def layered_bench(stream):
     """The paper's layered workloads: Section 4.1's composite column (128
     cells, 36 steps of 10 s, FP64) and Section 4.2's two-layer field (256^2,
-    tau = 0.01 h, FMG(10,10), kappa = 0.1) for LAYERED_STEPS steps, FP64
-    plain and mixed; wall time of each whole run.  Returns the summary and
+    tau = 0.01 h, FMG(10,10), kappa = 0.1): the paper's whole run (1.75
+    days, LAYERED_FULL_STEPS steps) mixed, beside the paper's total CPU time
+    of 2320 s (its hardware unstated), and LAYERED_STEPS steps FP64 plain;
+    wall time of each run.  Returns the summary and
     the states the CPU leg compares with."""
     import torch
     from paper_2606_04292_gb300 import richards as R
     from paper_2606_04292_gb300 import workloads as W
-    out = {"workload": f"composite column 128 x 36 steps; two-layer 256^2 x {LAYERED_STEPS} steps, tol 1e-8"}
+    out = {"workload": f"composite column 128 x 36 steps; two-layer 256^2 x {LAYERED_FULL_STEPS} steps (mixed) "
+                       f"and x {LAYERED_STEPS} steps (FP64 plain), tol 1e-8",
+           "paper_two_layer_total_cpu_s": 2320.0}
     states = {}
     runs = [("composite_column_fp64", W.celia_composite_1d(), None),
             ("two_layer_fp64_plain", W.two_layer_2d(nsteps=LAYERED_STEPS, precision=0), LAYERED_CPU_STEPS),
-            ("two_layer_mixed", W.two_layer_2d(nsteps=LAYERED_STEPS, precision=1), LAYERED_CPU_STEPS)]
+            ("two_layer_mixed", W.two_layer_2d(nsteps=LAYERED_FULL_STEPS, precision=1), LAYERED_CPU_STEPS)]
     for label, prob, keep in runs:
         gs = R.Solver(prob, stream=stream.cuda_stream)
         torch.cuda.synchronize()

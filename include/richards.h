@@ -104,7 +104,11 @@ typedef struct {
      tol                  stop when tau_eff ||N(psi) - g||_inf <= tol,
                           tau_eff = 1/a (residual in theta units)
      max_cycles           V-cycles per step (FP64) / inner cycles (mixed)
-     ordering             1 = red-black (the only GPU ordering)
+     ordering             1 = red-black; 0 = lexicographic, the paper's order
+                          (Section 3.1), run hyperplane by hyperplane
+                          (i0 + i1 + i2 = const, one launch each): the same
+                          iterates as the sequential sweep, for studies and
+                          parity, not speed.  Batched columns: 1 only.
      newton_iters         k > 0: exactly k safeguarded Newton steps per point
                           update; 0: to round-off
      precision            0 = FP64 throughout; 1 = FP32 inner cycles on the
@@ -298,7 +302,8 @@ richards_status richards_set_level(richards_ctx *ctx, int level, int which, cons
                                    long long n);
 
 /* One red (color 0) or black (color 1) half-sweep of eq. (point-update) on
-   a level's iterate with its right side (FP64); color -1: both. */
+   a level's iterate with its right side (FP64); color -1: both.  With
+   ordering 0 only color -1 is accepted: one lexicographic sweep. */
 richards_status richards_sweep(richards_ctx *ctx, int level, int color);
 
 /* d = g - N(psi) on a level (FP64) into the level's defect; *norm gets
@@ -355,7 +360,8 @@ int richards_profile_read(richards_ctx *ctx, richards_kernel_stat *out, int max)
  * arrays of ncell doubles; psi_out may alias psi_n.  In this call the
  * optional soil fields (Ks_field, p1_field, p2_field) and boundary fields
  * (value_field, mask_field) are DEVICE pointers.  Only opts->precision 0 is
- * used (the step is FP64).  info (nullable, host) receives the statistics.
+ * used (the step is FP64), and the sweeps are red-black whatever
+ * opts->ordering says.  info (nullable, host) receives the statistics.
  * stream: a cudaStream_t (NULL = default stream); the call synchronises it.
  *
  * Scratch: one fixed 2 MiB array in the library's device memory (every

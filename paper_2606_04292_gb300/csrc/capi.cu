@@ -503,6 +503,39 @@ int gamma_at(const richards_ctx* c, int l) {
   return (c->opts.gamma_levels <= 0 || l < c->opts.gamma_levels) ? c->opts.cycle_gamma : 1;
 }
 
+// nu NGS sweeps on a grid level: red then black half-sweeps, or, with
+// ordering 0, the paper's lexicographic sweep (one launch per hyperplane;
+// timed as one record per sweep)
+void smooth64(richards_ctx* c, const Level<double>& F, const Phys<double>& P, int l, int nu) {
+  const int model = c->soil.model;
+  const long long half = (F.ncell + 1) / 2;
+  for (int k = 0; k < nu; ++k) {
+    if (c->opts.ordering == 0) {
+      Prof pr(c, "sweep_lex64", l, F.ncell);
+      rich::sweep_lex64(F, P, model, c->s);
+      continue;
+    }
+    { Prof pr(c, "sweep64", l, half); rich::sweep64(F, P, model, 0, c->s); }
+    { Prof pr(c, "sweep64", l, F.ncell - half); rich::sweep64(F, P, model, 1, c->s); }
+  }
+  c->updates_host += (long long)nu * F.ncell;
+}
+
+void smooth32(richards_ctx* c, const Level<float>& F, const Phys<float>& P, int l, int nu) {
+  const int model = c->soil.model;
+  const long long half = (F.ncell + 1) / 2;
+  for (int k = 0; k < nu; ++k) {
+    if (c->opts.ordering == 0) {
+      Prof pr(c, "sweep_lex32", l, F.ncell);
+      rich::sweep_lex32(F, P, model, c->s);
+      continue;
+    }
+    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->opts.sweep_planes, c->s); }
+    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->opts.sweep_planes, c->s); }
+  }
+  c->updates_host += (long long)nu * F.ncell;
+}
+
 // ------------------------------------------------------------------------
 // One V-cycle (Section 3.2, steps 1-7 with the coarse solve replaced by the
 // recursion) from level l: grid kernels down to the coarse tail, which runs
@@ -514,17 +547,13 @@ void vcycle64(richards_ctx* c, int l) {
   if (l >= c->tail_start) {
     Prof pr(c, "tail64", l, c->L[l].ncell);
     rich::tail64(c->dL64, c->dX64, l, c->nlev, P, model, c->opts.nu1, c->opts.nu2, c->opts.coarse_max_sweeps,
-                 c->opts.coarse_rtol, c->opts.cycle_gamma, c->opts.gamma_levels, c->scratch + 16, c->s);
+                 c->opts.coarse_rtol, c->opts.cycle_gamma, c->opts.gamma_levels, c->scratch + 16, c->opts.ordering,
+                 c->s);
     return;
   }
   const Level<double> F = view64(c, l), C = view64(c, l + 1);
-  const long long half = (F.ncell + 1) / 2;
   nvtxRangePushA(level_range(l));
-  for (int k = 0; k < c->opts.nu1; ++k) {
-    { Prof pr(c, "sweep64", l, half); rich::sweep64(F, P, model, 0, c->s); }
-    { Prof pr(c, "sweep64", l, F.ncell - half); rich::sweep64(F, P, model, 1, c->s); }
-  }
-  c->updates_host += (long long)c->opts.nu1 * F.ncell;
+  smooth64(c, F, P, l, c->opts.nu1);
   { Prof pr(c, "residual64", l, F.ncell); rich::residual64(F, P, model, nullptr, c->s); }
   { Prof pr(c, "restrict64", l, C.ncell); rich::restrict64(F, C, xfer64(c, l), F.u, F.d, C.ubar, C.d, c->s); }
   { Prof pr(c, "tau64", l + 1, C.ncell); rich::tau64(C, P, model, c->s); }
@@ -532,12 +561,8 @@ void vcycle64(richards_ctx* c, int l) {
   for (int q = 0; q < gamma_at(c, l); ++q) vcycle64(c, l + 1);
   nvtxRangePushA(level_range(l));
   { Prof pr(c, "prolong64", l, F.ncell); rich::prolong64(F, C, xfer64(c, l), c->s); }
-  for (int k = 0; k < c->opts.nu2; ++k) {
-    { Prof pr(c, "sweep64", l, half); rich::sweep64(F, P, model, 0, c->s); }
-    { Prof pr(c, "sweep64", l, F.ncell - half); rich::sweep64(F, P, model, 1, c->s); }
-  }
+  smooth64(c, F, P, l, c->opts.nu2);
   nvtxRangePop();
-  c->updates_host += (long long)c->opts.nu2 * F.ncell;
 }
 
 void vcycle32(richards_ctx* c, int l) {
@@ -546,17 +571,13 @@ void vcycle32(richards_ctx* c, int l) {
   if (l >= c->tail_start) {
     Prof pr(c, "tail32", l, c->L[l].ncell);
     rich::tail32(c->dL32, c->dX32, l, c->nlev, P, model, c->opts.nu1, c->opts.nu2, c->opts.coarse_max_sweeps,
-                 (float)c->opts.coarse_rtol, c->opts.cycle_gamma, c->opts.gamma_levels, c->scratch + 16, c->s);
+                 (float)c->opts.coarse_rtol, c->opts.cycle_gamma, c->opts.gamma_levels, c->scratch + 16,
+                 c->opts.ordering, c->s);
     return;
   }
   const Level<float> F = view32(c, l), C = view32(c, l + 1);
-  const long long half = (F.ncell + 1) / 2;
   nvtxRangePushA(level_range(l));
-  for (int k = 0; k < c->opts.nu1; ++k) {
-    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->opts.sweep_planes, c->s); }
-    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->opts.sweep_planes, c->s); }
-  }
-  c->updates_host += (long long)c->opts.nu1 * F.ncell;
+  smooth32(c, F, P, l, c->opts.nu1);
   { Prof pr(c, "residual32", l, F.ncell); rich::residual32(F, P, model, nullptr, c->s); }
   { Prof pr(c, "restrict32", l, C.ncell); rich::restrict32(F, C, xfer32(c, l), F.u, F.d, C.ubar, C.d, c->s); }
   { Prof pr(c, "tau32", l + 1, C.ncell); rich::tau32(C, P, model, c->s); }
@@ -564,12 +585,8 @@ void vcycle32(richards_ctx* c, int l) {
   for (int q = 0; q < gamma_at(c, l); ++q) vcycle32(c, l + 1);
   nvtxRangePushA(level_range(l));
   { Prof pr(c, "prolong32", l, F.ncell); rich::prolong32(F, C, xfer32(c, l), c->s); }
-  for (int k = 0; k < c->opts.nu2; ++k) {
-    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->opts.sweep_planes, c->s); }
-    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->opts.sweep_planes, c->s); }
-  }
+  smooth32(c, F, P, l, c->opts.nu2);
   nvtxRangePop();
-  c->updates_host += (long long)c->opts.nu2 * F.ncell;
 }
 
 // One FP32 inner cycle, replayed from a CUDA graph when the options ask for it
@@ -969,7 +986,7 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
   const richards_opts& o = *opts;
   if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max_sweeps < 1 || o.max_cycles < 0 || o.coarsest_max_n < 1 ||
       !(o.tol > 0.0) || o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
-      o.ordering != 1 || (o.precision != 0 && o.precision != 1) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
+      (o.ordering != 0 && o.ordering != 1) || (o.precision != 0 && o.precision != 1) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
       o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0 || o.cycle_gamma < 1 || o.cycle_gamma > 3 ||
       o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1) || (o.predictor != 0 && o.predictor != 1) ||
       o.fmg_cycles < 0 || o.fmg_cycles > 16 ||
@@ -1592,8 +1609,13 @@ richards_status richards_sweep(richards_ctx* c, int level, int color) {
   if (!c->prepared) return fail(c, RICH_EINVAL, "call richards_prepare first");
   const Level<double> L = view64(c, level);
   const Phys<double> P = phys<double>(c);
-  if (color != 1) rich::sweep64(L, P, c->soil.model, 0, c->s);
-  if (color != 0) rich::sweep64(L, P, c->soil.model, 1, c->s);
+  if (c->opts.ordering == 0) {
+    if (color != -1) return fail(c, RICH_EINVAL, "lexicographic ordering: only whole sweeps (color -1)");
+    rich::sweep_lex64(L, P, c->soil.model, c->s);
+  } else {
+    if (color != 1) rich::sweep64(L, P, c->soil.model, 0, c->s);
+    if (color != 0) rich::sweep64(L, P, c->soil.model, 1, c->s);
+  }
   TRY(check_launch(c));
   CK(cudaStreamSynchronize(c->s));
   return RICH_OK;

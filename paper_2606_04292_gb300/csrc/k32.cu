@@ -20,7 +20,8 @@ void prolong32(const Level<float>& F, const Level<float>& C, const Xfer<float>& 
 }
 void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, const Phys<float>& P, int model,
             int nu1, int nu2, int cmax, float crtol, int gamma, int gamma_levels, unsigned long long* stats,
-            cudaStream_t s) {
-  D::tail(dLs, dXs, l0, nl, P, model, nu1, nu2, cmax, crtol, gamma, gamma_levels, stats, s);
+            int ordering, cudaStream_t s) {
+  D::tail(dLs, dXs, l0, nl, P, model, nu1, nu2, cmax, crtol, gamma, gamma_levels, stats, ordering, s);
 }
+void sweep_lex32(const Level<float>& L, const Phys<float>& P, int model, cudaStream_t s) { D::sweep_lex(L, P, model, s); }
 }  // namespace rich

@@ -22,9 +22,10 @@ void prolong64(const Level<double>& F, const Level<double>& C, const Xfer<double
 }
 void tail64(const Level<double>* dLs, const Xfer<double>* dXs, int l0, int nl, const Phys<double>& P, int model,
             int nu1, int nu2, int cmax, double crtol, int gamma, int gamma_levels, unsigned long long* stats,
-            cudaStream_t s) {
-  D::tail(dLs, dXs, l0, nl, P, model, nu1, nu2, cmax, crtol, gamma, gamma_levels, stats, s);
+            int ordering, cudaStream_t s) {
+  D::tail(dLs, dXs, l0, nl, P, model, nu1, nu2, cmax, crtol, gamma, gamma_levels, stats, ordering, s);
 }
+void sweep_lex64(const Level<double>& L, const Phys<double>& P, int model, cudaStream_t s) { D::sweep_lex(L, P, model, s); }
 
 // ---------------------------------------------------------------------------
 // Lagged state and history (eq. fully-bdf1; BDF2 reading: a = 3/(2 tau),

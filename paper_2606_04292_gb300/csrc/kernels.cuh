@@ -2,6 +2,8 @@
 // Included by the FP64 and FP32 translation units, which instantiate them.
 #pragma once
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "launch.h"
 
@@ -60,6 +62,23 @@ __global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int c
     const CellOps<T>& cur = c[k & 1];
     if (cur.valid) L.u[cur.i] = solve_cell<T, FORM, MODEL, NK>(L, P, cur);
   }
+}
+
+// One hyperplane i0 + i1 + i2 = s of a lexicographic NGS sweep (the
+// paper's ordering, Section 3.1: cells in the order of the flattened index).
+// Cells of one hyperplane do not couple; each reads the updated values of its
+// lower neighbours (plane s - 1) and the old values of its upper ones (plane
+// s + 1), exactly what the sequential sweep reads.  Planes s = 0 .. n0+n1+n2-3
+// in turn make one sweep.  Launch grid: x = i1, y = i2 - i2lo.
+template <typename T, int FORM, int MODEL, int NK = 0>
+__global__ void __launch_bounds__(128) k_sweep_plane(Level<T> L, Phys<T> P, int s, int i2lo) {
+  const int i1 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i2 = i2lo + blockIdx.y;
+  if (i1 >= L.n1) return;
+  const int i0 = s - i1 - i2;
+  if (i0 < 0 || i0 >= L.n0) return;
+  const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
+  point_update<T, FORM, MODEL, NK>(L, P, i, i0, i1, i2);
 }
 
 // d = g - N(u) on a level, with ||d||_inf accumulated into *norm (bit max).
@@ -244,8 +263,24 @@ inline bool nested_levels(int fn0, int fn1, int fn2, int cn0, int cn1, int cn2) 
 // a kernel per stage).  Same arithmetic as the grid kernels, phase by phase,
 // separated by block barriers.
 // ---------------------------------------------------------------------------
+// one NGS sweep of a level by one thread block: red then black half-sweeps
+// (ordering 1), or the lexicographic order hyperplane by hyperplane (0)
 template <typename T, int FORM, int MODEL>
-__device__ __forceinline__ void block_sweep(const Level<T>& L, const Phys<T>& P) {
+__device__ __forceinline__ void block_sweep(const Level<T>& L, const Phys<T>& P, int ordering = 1) {
+  if (ordering == 0) {
+    const int nplanes = L.n0 + L.n1 + L.n2 - 2;
+    const int nrows = L.n1 * L.n2;
+    for (int s = 0; s < nplanes; ++s) {
+      for (int t = threadIdx.x; t < nrows; t += blockDim.x) {
+        const int i1 = t % L.n1, i2 = t / L.n1;
+        const int i0 = s - i1 - i2;
+        if (i0 >= 0 && i0 < L.n0)
+          point_update<T, FORM, MODEL>(L, P, (unsigned)(i0 + L.n0 * t), i0, i1, i2);
+      }
+      __syncthreads();
+    }
+    return;
+  }
   const long long nh = (long long)((L.n0 + 1) >> 1) * L.n1 * L.n2;
   for (int color = 0; color < 2; ++color) {
     for (long long t = threadIdx.x; t < nh; t += blockDim.x) {
@@ -279,7 +314,8 @@ __device__ __forceinline__ T block_defect_norm(const Level<T>& L, const Phys<T>&
 // restrict(l, fine array, coarse coords) and prolong(l, fine coords).
 template <typename T, int FORM, int MODEL, typename LV>
 __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const Phys<T>& P, int nu1, int nu2, int cmax, T crtol,
-                            int gamma, int gamma_levels, unsigned long long* sm, unsigned long long& updates) {
+                            int gamma, int gamma_levels, unsigned long long* sm, unsigned long long& updates,
+                            int ordering = 1) {
   int visits[24];
   int l = l0;
   bool down = true;
@@ -289,7 +325,7 @@ __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const 
         const Level<T>& C = lv.L(l);
         const T d0 = block_defect_norm<T, FORM, MODEL>(C, P, sm);
         for (int s = 0; s < cmax; ++s) {
-          block_sweep<T, FORM, MODEL>(C, P);
+          block_sweep<T, FORM, MODEL>(C, P, ordering);
           updates += C.ncell;
           const T dn = block_defect_norm<T, FORM, MODEL>(C, P, sm);
           if (!(dn > crtol * d0)) break;
@@ -298,7 +334,7 @@ __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const 
         continue;
       }
       const Level<T>& F = lv.L(l);
-      for (int s = 0; s < nu1; ++s) block_sweep<T, FORM, MODEL>(F, P);
+      for (int s = 0; s < nu1; ++s) block_sweep<T, FORM, MODEL>(F, P, ordering);
       updates += (unsigned long long)nu1 * F.ncell;
       for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
         int i0, i1, i2;
@@ -341,7 +377,7 @@ __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const 
       F.u[i] += lv.prolong(pl, i0, i1, i2);
     }
     __syncthreads();
-    for (int s = 0; s < nu2; ++s) block_sweep<T, FORM, MODEL>(F, P);
+    for (int s = 0; s < nu2; ++s) block_sweep<T, FORM, MODEL>(F, P, ordering);
     updates += (unsigned long long)nu2 * F.ncell;
     l = pl;
   }
@@ -361,11 +397,12 @@ struct DeviceLevels {
 template <typename T, int FORM, int MODEL>
 __global__ void __launch_bounds__(TAIL_THREADS, 1) k_tail(const Level<T>* __restrict__ Ls, const Xfer<T>* __restrict__ Xs,
                                                        int l0, int nl, Phys<T> P, int nu1, int nu2, int cmax,
-                                                       T crtol, int gamma, int gamma_levels, unsigned long long* stats) {
+                                                       T crtol, int gamma, int gamma_levels, unsigned long long* stats,
+                                                       int ordering) {
   __shared__ unsigned long long sm[33];
   unsigned long long updates = 0;
   block_cycle<T, FORM, MODEL>(DeviceLevels<T>{Ls, Xs}, l0, nl, P, nu1, nu2, cmax, crtol, gamma, gamma_levels, sm,
-                              updates);
+                              updates, ordering);
   if (threadIdx.x == 0 && stats) atomicAdd(stats, updates);
 }
 
@@ -441,6 +478,26 @@ struct Dispatch {
     else if (planes == 4) sweep_pipe_z<4>(L, P, model, color, s);
     else sweep_pipe_z<8>(L, P, model, color, s);
   }
+  // one lexicographic sweep: a launch per hyperplane, rows of the plane's
+  // i2 range only
+  template <int NK>
+  static void sweep_lex_nk(const Level<T>& L, const Phys<T>& P, int model, cudaStream_t s) {
+    int bx = 32;
+    while (bx < L.n1 && bx < 128) bx <<= 1;
+    const int nplanes = L.n0 + L.n1 + L.n2 - 2;
+    by_model(model, [&](auto m) {
+      for (int p = 0; p < nplanes; ++p) {
+        const int i2lo = std::max(0, p - (L.n0 - 1) - (L.n1 - 1)), i2hi = std::min(L.n2 - 1, p);
+        const dim3 grid((L.n1 + bx - 1) / bx, i2hi - i2lo + 1, 1);
+        k_sweep_plane<T, FORM, decltype(m)::value, NK><<<grid, bx, 0, s>>>(L, P, p, i2lo);
+      }
+    });
+  }
+  static void sweep_lex(const Level<T>& L, const Phys<T>& P, int model, cudaStream_t s) {
+    if (FORM == FORM_DELTA && P.newton_k == 1) sweep_lex_nk<(FORM == FORM_DELTA ? 1 : 0)>(L, P, model, s);
+    else if (FORM == FORM_DELTA && P.newton_k == 2) sweep_lex_nk<(FORM == FORM_DELTA ? 2 : 0)>(L, P, model, s);
+    else sweep_lex_nk<0>(L, P, model, s);
+  }
   static void residual(const Level<T>& L, const Phys<T>& P, int model, unsigned long long* norm,
                        cudaStream_t s) {
     const Launch3 g = launch3(L.n0, L.n1, L.n2);
@@ -469,10 +526,10 @@ struct Dispatch {
   }
   static void tail(const Level<T>* dLs, const Xfer<T>* dXs, int l0, int nl, const Phys<T>& P, int model,
                    int nu1, int nu2, int cmax, T crtol, int gamma, int gamma_levels, unsigned long long* stats,
-                   cudaStream_t s) {
+                   int ordering, cudaStream_t s) {
     by_model(model, [&](auto m) {
       k_tail<T, FORM, decltype(m)::value><<<1, TAIL_THREADS, 0, s>>>(dLs, dXs, l0, nl, P, nu1, nu2, cmax, crtol,
-                                                                      gamma, gamma_levels, stats);
+                                                                      gamma, gamma_levels, stats, ordering);
     });
   }
 };

@@ -31,10 +31,12 @@ void tau64(const Level<double>& C, const Phys<double>& P, int model, cudaStream_
 void restrict64(const Level<double>& F, const Level<double>& C, const Xfer<double>& X, const double* fa,
                 const double* fb, double* ca, double* cb, cudaStream_t s);
 void prolong64(const Level<double>& F, const Level<double>& C, const Xfer<double>& X, cudaStream_t s);
+// ordering: 1 red-black, 0 lexicographic (hyperplane by hyperplane)
 void tail64(const Level<double>* dLs, const Xfer<double>* dXs, int l0, int nl, const Phys<double>& P,
             int model, int nu1, int nu2, int cmax, double crtol, int gamma, int gamma_levels,
-            unsigned long long* stats,
-            cudaStream_t s);
+            unsigned long long* stats, int ordering, cudaStream_t s);
+// one lexicographic NGS sweep (a launch per hyperplane i0 + i1 + i2 = const)
+void sweep_lex64(const Level<double>& L, const Phys<double>& P, int model, cudaStream_t s);
 
 // FP32, correction delta as unknown
 void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, int planes, cudaStream_t s);
@@ -46,8 +48,8 @@ void restrict32(const Level<float>& F, const Level<float>& C, const Xfer<float>&
 void prolong32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, cudaStream_t s);
 void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, const Phys<float>& P,
             int model, int nu1, int nu2, int cmax, float crtol, int gamma, int gamma_levels,
-            unsigned long long* stats,
-            cudaStream_t s);
+            unsigned long long* stats, int ordering, cudaStream_t s);
+void sweep_lex32(const Level<float>& L, const Phys<float>& P, int model, cudaStream_t s);
 
 // per-step preparation (FP64).  mat: the fine level's material index (read
 // only when model == COMPOSITE; nullable otherwise)

@@ -37,7 +37,7 @@ def test_create_rejects_invalid_arguments_without_a_device():
     for g in bad_grids:
         assert L.richards_create(C.byref(g), C.byref(o), None, C.byref(h)) == R.RICH_EINVAL
     g = R.richards_grid(2, (C.c_int * 3)(4, 4, 1), (C.c_double * 3)(1, 1, 1))
-    for key, val in [("ordering", 0), ("kappa_mode", 1), ("precision", 3), ("tol", 0.0), ("nu1", -1),
+    for key, val in [("ordering", 2), ("ordering", -1), ("kappa_mode", 1), ("precision", 3), ("tol", 0.0), ("nu1", -1),
                      ("newton_iters", -2), ("xi", -1.0), ("sweep_planes", 3), ("sweep_planes", 0), ("predictor", 2), ("fmg_cycles", -1)]:
         oo = R.make_opts(W.default_opts(**{key: val}))
         assert L.richards_create(C.byref(g), C.byref(oo), None, C.byref(h)) == R.RICH_EINVAL, key

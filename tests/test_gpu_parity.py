@@ -488,3 +488,111 @@ def test_graph_replay_matches_direct_launches():
     a.step()
     prof = a.profile_read()
     assert any(r["name"] == "sweep32" and r["launches"] > 0 for r in prof)
+
+
+# ---------------------------------------------------------------------------
+# The paper's lexicographic ordering on the GPU (ordering 0: hyperplanes
+# i0 + i1 + i2 = const in turn), iterate for iterate against the oracle's
+# sequential sweep.
+# ---------------------------------------------------------------------------
+LEX_IDS = ["1d_haverkamp_dir", "2d_gardner_mixed_bc", "3d_vg_hetero_sink", "3d_haverkamp_dir",
+           "1d_celia_composite_40", "2d_layers_3mat"]
+LEX_PROBLEMS = [p for p in PROBLEMS if p[0] in LEX_IDS]
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in LEX_PROBLEMS], ids=[p[0] for p in LEX_PROBLEMS])
+@pytest.mark.parametrize("newton", [0, 2])
+def test_lexicographic_sweeps_match_oracle_on_every_level(mk, newton):
+    """One lexicographic sweep on every level (Newton to round-off on random
+    states; the fixed two-step Newton near the root)."""
+    prob = W.with_opts(mk(), ordering=0)
+    gs, orc, p = pair(prob, newton_iters=newton)
+    gs.prepare(p["dt"], 1)
+    orc.prepare(p["dt"], 1)
+    rng = np.random.default_rng(13)
+    for lev in range(orc.nlevels):
+        n = orc.ncell(lev)
+        psi = rng.uniform(-1.5, -0.05, n)
+        g = orc.apply_N(rng.uniform(-1.5, -0.05, n) if newton == 0 else psi + rng.uniform(-1e-3, 1e-3, n), lev)
+        gs.set_level(lev, 0, psi)
+        gs.set_level(lev, 1, g)
+        ref = orc.sweep(psi, g, lev, -1, ordering=0)
+        gs.sweep(lev, -1)
+        got = gs.get_level(lev, 0)
+        assert sweep_agrees(orc, p, lev, got, ref, psi, g), (lev, rel(got, ref))
+    with pytest.raises(R.RichardsError):
+        gs.sweep(0, 0)                    # half-sweeps belong to the red-black ordering
+
+
+def test_lexicographic_differs_from_red_black():
+    """The two orderings are different smoothers (same fixed point): one
+    sweep from the same state gives different iterates."""
+    prob = W.random_problem(2, (12, 10), W.VANGENUCHTEN, 21)
+    lex, rb = R.Solver(W.with_opts(prob, ordering=0)), R.Solver(prob)
+    for gs in (lex, rb):
+        gs.prepare(prob["dt"], 1)
+        gs.sweep(0, -1)
+    assert rel(lex.get_level(0, 0), rb.get_level(0, 0)) > 1e-6
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in LEX_PROBLEMS], ids=[p[0] for p in LEX_PROBLEMS])
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_lexicographic_cycles_match_oracle(mk, gamma):
+    prob = W.with_opts(mk(), ordering=0)
+    gs, orc, p = pair(prob, coarse_rtol=0.0, coarse_max_sweeps=12, newton_iters=0, cycle_gamma=gamma,
+                      gamma_levels=0)
+    gs.prepare(p["dt"], 1)
+    orc.prepare(p["dt"], 1)
+    ref = p["psi0"]
+    for _ in range(2):
+        gs.vcycle()
+        ref = orc.vcycle(ref)
+        assert rel(gs.get_level(0, 0), ref) <= STEP_RTOL
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in LEX_PROBLEMS], ids=[p[0] for p in LEX_PROBLEMS])
+def test_lexicographic_fp64_steps_match_oracle(mk):
+    prob = W.with_opts(mk(), ordering=0)
+    gs, orc, p = pair(prob, tol=1e-11, max_cycles=200)
+    for k in range(3):
+        st, info = gs.step(p["dt"], p["scheme"], check=False)
+        sto, info_o = orc.step(p["dt"], p["scheme"])
+        assert st == sto, (k, info, info_o)
+        assert abs(info["cycles"] - info_o["cycles"]) <= 1, (k, info, info_o)
+        assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in LEX_PROBLEMS if "sink" not in p[0]],
+                         ids=[p[0] for p in LEX_PROBLEMS if "sink" not in p[0]])
+def test_lexicographic_mixed_within_stated_bound(mk):
+    """Mixed mode with the lexicographic FP32 inner smoother."""
+    prob = W.with_opts(mk(), precision=1, ordering=0)
+    gs = R.Solver(prob)
+    orc = Oracle(W.with_opts(prob, tol=1e-13, newton_iters=0))
+    cur, prev = np.array(prob["psi0"], dtype=np.float64), None
+    for k in range(2):
+        st, info = gs.step(prob["dt"], prob["scheme"], check=False)
+        assert st == R.RICH_OK, info
+        psi_m = gs.state()
+        orc.set_state(cur, prev)
+        assert orc.step(prob["dt"], prob["scheme"])[0] == ORC_OK
+        psi_r = orc.state()
+        orc.set_state(cur, prev)
+        orc.prepare(prob["dt"], info["scheme_used"])
+        _, rm = orc.residual(psi_m)
+        assert rm / orc.a <= prob["opts"]["tol"] * (1 + 1e-6) + _law_allowance(orc, prob, psi_m)
+        assert np.max(np.abs(psi_m - psi_r)) <= _mixed_bound(orc, psi_m, psi_r) * (1 + 1e-6), k
+        prev, cur = cur, psi_m
+
+
+def test_celia_column_lexicographic_full_run():
+    """Section 4.1's column with the paper's own sweep order: cycle counts
+    and the final state as the oracle's lexicographic run."""
+    prob = W.with_opts(W.celia_1d(), ordering=0)
+    gs, orc, p = pair(prob)
+    for k in range(p["nsteps"]):
+        st, info = gs.step()
+        sto, info_o = orc.step()
+        assert st == R.RICH_OK and sto == ORC_OK
+        assert info["cycles"] == info_o["cycles"], k
+    assert rel(gs.state(), orc.state()) <= STEP_RTOL
