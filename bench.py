@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-gardner", action="store_true")
     ap.add_argument("--no-layered", action="store_true")
+    ap.add_argument("--temporal-study", action="store_true",
+                    help="add Section 4.1's temporal-convergence study (N=1024 vs N=2048, tau_ref=1e-4; ~4 min)")
     ap.add_argument("--gamma", type=int, default=2, help="1 = V-cycles, 2 = W-cycles")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel timing records here")
     return ap.parse_args()
@@ -550,6 +552,13 @@ def main():
     if rank == 0 and not args.no_layered:
         layered, lstates = layered_bench(stream)
 
+    temporal = None
+    if rank == 0 and args.temporal_study:
+        from paper_2606_04292_gb300 import studies
+        t_study = time.perf_counter()
+        temporal = studies.temporal_convergence()
+        temporal["total_wall_s"] = time.perf_counter() - t_study
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob, gs.state())
@@ -580,6 +589,7 @@ def main():
             "serving": serving,
             "paper_gardner_2d": gardner,
             "paper_layered": layered,
+            "paper_temporal_study": temporal,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
