@@ -573,7 +573,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": N, "levels": gs.nlevels, "l2": "inputs larger than L2",
-                       "cycle": "W(2,2)" if args.gamma == 2 else "V(2,2)",
+                       "cycle": f"{'W' if args.gamma == 2 else 'V'}({prob['opts']['nu1']},{prob['opts']['nu2']})",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "time_steps_per_s": steps_per_s,
             "v_cycles_per_step": statistics.mean(i["cycles"] for i in infos),

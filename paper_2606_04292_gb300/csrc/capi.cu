@@ -541,7 +541,8 @@ void smooth32(richards_ctx* c, const Level<float>& F, const Phys<float>& P, int 
 // recursion) from level l: grid kernels down to the coarse tail, which runs
 // in one thread block.
 // ------------------------------------------------------------------------
-void vcycle64(richards_ctx* c, int l) {
+// d_ready: as for vcycle32 (nu1 = 0 and the finest defect already current)
+void vcycle64(richards_ctx* c, int l, bool d_ready = false) {
   const int model = c->soil.model;
   const Phys<double> P = phys<double>(c);
   if (l >= c->tail_start) {
@@ -554,7 +555,10 @@ void vcycle64(richards_ctx* c, int l) {
   const Level<double> F = view64(c, l), C = view64(c, l + 1);
   nvtxRangePushA(level_range(l));
   smooth64(c, F, P, l, c->opts.nu1);
-  { Prof pr(c, "residual64", l, F.ncell); rich::residual64(F, P, model, nullptr, c->s); }
+  if (!(d_ready && c->opts.nu1 == 0)) {
+    Prof pr(c, "residual64", l, F.ncell);
+    rich::residual64(F, P, model, nullptr, c->s);
+  }
   { Prof pr(c, "restrict64", l, C.ncell); rich::restrict64(F, C, xfer64(c, l), F.u, F.d, C.ubar, C.d, c->s); }
   { Prof pr(c, "tau64", l + 1, C.ncell); rich::tau64(C, P, model, c->s); }
   nvtxRangePop();
@@ -565,7 +569,10 @@ void vcycle64(richards_ctx* c, int l) {
   nvtxRangePop();
 }
 
-void vcycle32(richards_ctx* c, int l) {
+// d_ready: the finest level's defect array already holds g - N(u) for the
+// current u (only used with nu1 = 0, where no pre-smoothing changes u
+// between the inner stop test's defect and this cycle's restriction)
+void vcycle32(richards_ctx* c, int l, bool d_ready = false) {
   const int model = c->soil.model;
   const Phys<float> P = phys<float>(c);
   if (l >= c->tail_start) {
@@ -578,7 +585,10 @@ void vcycle32(richards_ctx* c, int l) {
   const Level<float> F = view32(c, l), C = view32(c, l + 1);
   nvtxRangePushA(level_range(l));
   smooth32(c, F, P, l, c->opts.nu1);
-  { Prof pr(c, "residual32", l, F.ncell); rich::residual32(F, P, model, nullptr, c->s); }
+  if (!(d_ready && c->opts.nu1 == 0)) {
+    Prof pr(c, "residual32", l, F.ncell);
+    rich::residual32(F, P, model, nullptr, c->s);
+  }
   { Prof pr(c, "restrict32", l, C.ncell); rich::restrict32(F, C, xfer32(c, l), F.u, F.d, C.ubar, C.d, c->s); }
   { Prof pr(c, "tau32", l + 1, C.ncell); rich::tau32(C, P, model, c->s); }
   nvtxRangePop();
@@ -592,7 +602,15 @@ void vcycle32(richards_ctx* c, int l) {
 // One FP32 inner cycle, replayed from a CUDA graph when the options ask for it
 // and the stream can be captured; the graph is captured again when a, the
 // profiling state or any set-up call changed what its launches bake in.
+// With nu1 = 0 and the inner stop test on, every inner cycle starts from a
+// finest-level defect that is already in place: the stop test's after each
+// cycle, and g itself before the first one (N(0) = 0 exactly: every
+// increment of the correction equation vanishes at delta = 0).  The cycle
+// then skips recomputing it.
+bool top_defect_ready(const richards_ctx* c) { return c->opts.nu1 == 0 && c->opts.inner_rtol > 0.0; }
+
 void run_cycle32(richards_ctx* c) {
+  const bool ready = top_defect_ready(c);
   if (c->opts.graphs && c->graphs_ok && c->s != nullptr) {
     richards_ctx::GraphRec& G = c->graphs[c->scheme_used];
     if (!G.exec || G.a != c->a || G.with_prof != c->prof) {
@@ -608,7 +626,7 @@ void run_cycle32(richards_ctx* c) {
       const char* where = "cudaStreamBeginCapture";
       if (e == cudaSuccess) {
         c->capturing = true;
-        vcycle32(c, 0);
+        vcycle32(c, 0, ready);
         c->capturing = false;
         const cudaError_t el = cudaGetLastError();
         e = cudaStreamEndCapture(c->s, &g);
@@ -632,7 +650,7 @@ void run_cycle32(richards_ctx* c) {
         G.prof.clear();
         G.exec = nullptr;
         c->graphs_ok = false;
-        vcycle32(c, 0);
+        vcycle32(c, 0, ready);
         return;
       }
       G.a = c->a;
@@ -648,7 +666,7 @@ void run_cycle32(richards_ctx* c) {
     if (c->prof && !G.prof.empty()) c->harvest = &G;
     return;
   }
-  vcycle32(c, 0);
+  vcycle32(c, 0, ready);
 }
 
 // coarse copies of the lagged conductivity and boundary conductances
@@ -841,8 +859,10 @@ richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
     TRY(norm64(c, 0, &nrm));
     r = teff * nrm;
   }
+  // every cycle follows a norm64 of the current iterate, whose defect the
+  // cycle reuses when there is no pre-smoothing
   while (!(r <= c->opts.tol) && cycles < c->opts.max_cycles && !std::isnan(r)) {
-    vcycle64(c, 0);
+    vcycle64(c, 0, true);
     TRY(check_launch(c));
     ++cycles;
     TRY(norm64(c, 0, &nrm));
@@ -909,7 +929,10 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
     // nonlinear remainder): close to tol it stops early
     const double rtol_in = std::max(c->opts.inner_rtol, 0.3 * c->opts.tol / r);
     bool done_in = false;
-    if (c->opts.fmg_cycles > 0 && c->nlev > 1) {    // full multigrid start of the inner solve
+    const bool fmg_start = c->opts.fmg_cycles > 0 && c->nlev > 1;
+    if (top_defect_ready(c) && !fmg_start)          // the defect at delta = 0 is g
+      CK(cudaMemcpyAsync(F.df, F.gf, sizeof(float) * F.ncell, cudaMemcpyDeviceToDevice, c->s));
+    if (fmg_start) {                                // full multigrid start of the inner solve
       fmg32(c);
       inner += c->opts.fmg_cycles;
       if (c->opts.inner_rtol > 0.0) {
