@@ -612,7 +612,9 @@ struct CellOps {
   T Kn[6], un[6];
 };
 
-template <typename T, int FORM, int MODEL>
+// YZI: the caller knows that the cell is interior along axes 1 and 2 of a
+// 3-d level (no boundary face there), so only axis 0 is tested
+template <typename T, int FORM, int MODEL, bool YZI = false>
 __device__ __forceinline__ void gather(const Level<T>& L, const Phys<T>& P, int i0, int i1, int i2, CellOps<T>& c) {
   const unsigned i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
   c.i = i;
@@ -632,6 +634,11 @@ __device__ __forceinline__ void gather(const Level<T>& L, const Phys<T>& P, int 
   const int st[3] = {1, L.n0, L.n0 * L.n1};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
+    if (YZI && a > 0) {
+      c.Kn[2 * a] = Kp[-st[a]]; c.un[2 * a] = up[-st[a]];
+      c.Kn[2 * a + 1] = Kp[st[a]]; c.un[2 * a + 1] = up[st[a]];
+      continue;
+    }
     const int fc = a == 0 ? i1 + L.n1 * i2 : (a == 1 ? i0 + L.n0 * i2 : i0 + L.n0 * i1);
     if (a >= L.dim) {
       c.Kn[2 * a] = c.Kn[2 * a + 1] = T(0);
@@ -648,13 +655,13 @@ __device__ __forceinline__ void gather(const Level<T>& L, const Phys<T>& P, int 
 
 // the point update of a gathered cell (same sums, in the same order, as
 // stencil() and point_update())
-template <typename T, int FORM, int MODEL, int NK = 0>
+template <typename T, int FORM, int MODEL, int NK = 0, bool YZI = false>
 __device__ __forceinline__ T solve_cell(const Level<T>& L, const Phys<T>& P, const CellOps<T>& c) {
   T dg = T(0), of = T(0);
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     const T s = L.ih2[f >> 1];
-    if (c.bmask & (1u << f)) {
+    if ((!YZI || f < 2) && (c.bmask & (1u << f))) {
       dg += T(2) * c.Kn[f] * s;
     } else {
       const T m = (c.Ki + c.Kn[f]) * (T(0.5) * s);

@@ -39,16 +39,13 @@ __global__ void __launch_bounds__(256) k_sweep(Level<T> L, Phys<T> P, int color)
 // operands of the next plane's cell are loaded before the current cell is
 // solved.  Launch grid: x = pairs of cells along a row, y = row, z = chunk
 // of ZC planes.
-template <typename T, int FORM, int MODEL, int ZC, int NK = 0>
-__global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int color) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y;
-  const int z0 = blockIdx.z * ZC;
+template <typename T, int FORM, int MODEL, int ZC, int NK, bool YZI>
+__device__ __forceinline__ void sweep_pipe_body(const Level<T>& L, const Phys<T>& P, int color, int p, int i1, int z0) {
   CellOps<T> c[2];
   {
     const int i0 = 2 * p + ((color + i1 + z0) & 1);
     c[0].valid = z0 < L.n2 && i0 < L.n0;
-    if (c[0].valid) gather<T, FORM, MODEL>(L, P, i0, i1, z0, c[0]);
+    if (c[0].valid) gather<T, FORM, MODEL, YZI>(L, P, i0, i1, z0, c[0]);
   }
 #pragma unroll
   for (int k = 0; k < ZC; ++k) {
@@ -57,11 +54,23 @@ __global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int c
       const int i0 = 2 * p + ((color + i1 + i2) & 1);
       CellOps<T>& nx = c[(k + 1) & 1];
       nx.valid = i2 < L.n2 && i0 < L.n0;
-      if (nx.valid) gather<T, FORM, MODEL>(L, P, i0, i1, i2, nx);
+      if (nx.valid) gather<T, FORM, MODEL, YZI>(L, P, i0, i1, i2, nx);
     }
     const CellOps<T>& cur = c[k & 1];
-    if (cur.valid) L.u[cur.i] = solve_cell<T, FORM, MODEL, NK>(L, P, cur);
+    if (cur.valid) L.u[cur.i] = solve_cell<T, FORM, MODEL, NK, YZI>(L, P, cur);
   }
+}
+
+template <typename T, int FORM, int MODEL, int ZC, int NK = 0>
+__global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int color) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y;
+  const int z0 = blockIdx.z * ZC;
+  // blocks away from the y and z boundaries (all but a thin shell) skip
+  // those boundary tests; the branch is uniform over the block
+  const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && z0 > 0 && z0 + ZC < L.n2;
+  if (yzi) sweep_pipe_body<T, FORM, MODEL, ZC, NK, true>(L, P, color, p, i1, z0);
+  else sweep_pipe_body<T, FORM, MODEL, ZC, NK, false>(L, P, color, p, i1, z0);
 }
 
 // One hyperplane i0 + i1 + i2 = s of a lexicographic NGS sweep (the

@@ -544,6 +544,25 @@ def test_fp64_steps_without_presmoothing_match_oracle(mk):
         assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
 
 
+def test_pipelined_half_sweeps_equal_one_cell_per_thread():
+    """Levels of >= 2^20 cells take the pipelined half-sweep (sweep_planes
+    cells along z per thread, blocks away from the y/z boundaries without
+    those tests); the same point updates in the same order per cell, so the
+    mixed steps are bit for bit those of one cell per thread.  Odd sizes
+    leave a partial row pair and a partial plane chunk."""
+    prob = W.drainage_3d(n=103)
+    states = []
+    for planes in (1, 2, 4, 8):
+        gs = R.Solver(prob, opts=dict(sweep_planes=planes))
+        for _ in range(2):
+            st, info = gs.step(check=False)
+            assert st == R.RICH_OK, (planes, info)
+        states.append(gs.state())
+        gs.close()
+    for st in states[1:]:
+        assert np.array_equal(st, states[0])
+
+
 # ---------------------------------------------------------------------------
 # The paper's lexicographic ordering on the GPU (ordering 0: hyperplanes
 # i0 + i1 + i2 = const in turn), iterate for iterate against the oracle's
