@@ -725,8 +725,13 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   }
   double* kbw[6];
   for (int f = 0; f < 6; ++f) kbw[f] = F.kb[f];
-  rich::prep_rhs(geom(c, 0), c->bcdev, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
-                 c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, c->soil.model, F.Kc, F.g, kbw, c->s);
+  if (cache)
+    rich::prep_rhs_dd(geom(c, 0), c->bcdev, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
+                      c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, rich::make_ddphys(P), c->soil.model, F.Kc, F.g, kbw,
+                      c->s);
+  else
+    rich::prep_rhs(geom(c, 0), c->bcdev, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
+                   c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, c->soil.model, F.Kc, F.g, kbw, c->s);
   TRY(check_launch(c));
   TRY(restrict_coefficients(c));
   c->prepared = true;

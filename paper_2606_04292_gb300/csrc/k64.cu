@@ -188,6 +188,67 @@ __global__ void __launch_bounds__(256) k_prep_rhs(Geom G, BcDev bc, const double
   }
 }
 
+// The same gravity and boundary terms in float-float (mixed mode: no FP64
+// arithmetic on the path; FP64 arrays split and joined with integer bit
+// operations).  Per-axis constants split on the host: 0.5/h, 1/h, 2/h^2, h/2.
+struct RhsConstDD {
+  dd half_ih[3], ih[3], two_ih2[3], half_h[3];
+};
+
+template <int MODEL>
+__global__ void __launch_bounds__(256) k_prep_rhs_dd(Geom G, BcDev bc, const double* __restrict__ Ks, dd Ks_s,
+                                                     const double* __restrict__ p1f, const double* __restrict__ p2f,
+                                                     const uint8_t* __restrict__ mat, Phys<double> P, DDPhys Q,
+                                                     RhsConstDD H, const double* __restrict__ Kc, double* g,
+                                                     double* kb0, double* kb1, double* kb2, double* kb3, double* kb4,
+                                                     double* kb5) {
+  double* kb[6] = {kb0, kb1, kb2, kb3, kb4, kb5};
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const int v = G.dim - 1;
+  const int nn[3] = {G.n0, G.n1, G.n2};
+  const long long stride[3] = {1, G.n0, (long long)G.n0 * G.n1};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    int ii[3];
+    cell_coords(G.n0, G.n1, i, ii[0], ii[1], ii[2]);
+    dd gi = dd_split(g[i]);
+    const dd Ki = dd_split(Kc[i]);
+    if (ii[v] + 1 < nn[v]) gi = dd_add(gi, dd_mul(dd_add(Ki, dd_split(Kc[i + stride[v]])), H.half_ih[v]));
+    if (ii[v] > 0) gi = dd_sub(gi, dd_mul(dd_add(Ki, dd_split(Kc[i - stride[v]])), H.half_ih[v]));
+    for (int ax = 0; ax < G.dim; ++ax) {
+      for (int side = 0; side < 2; ++side) {
+        if (ii[ax] != (side ? nn[ax] - 1 : 0)) continue;
+        const int f = 2 * ax + side;
+        long long fc;
+        if (ax == 0) fc = ii[1] + (long long)G.n1 * ii[2];
+        else if (ax == 1) fc = ii[0] + (long long)G.n0 * ii[2];
+        else fc = ii[0] + (long long)G.n0 * ii[1];
+        const int kind = bc.kind[f];
+        const bool dir = kind == 0 && (!bc.mask[f] || bc.mask[f][fc]);
+        const dd val = dd_split(bc.vfield[f] ? bc.vfield[f][fc] : bc.value[f]);
+        if (dir) {
+          const dd p1 = p1f ? dd_split(p1f[i]) : Q.p1, p2 = p2f ? dd_split(p2f[i]) : Q.p2;
+          const dd ks = Ks ? dd_split(Ks[i]) : Ks_s;
+          const dd Kb = with_law_dd<MODEL>(P, Q, mat_at<MODEL>(mat, i),
+                                           [&](auto law, const Phys<double>& Pc, const DDPhys& Qc) {
+                                             return cond_x<decltype(law)::value>(val, p1, p2, ks, Qc, Pc);
+                                           });
+          const dd ksum = dd_add(Ki, Kb);
+          const dd k = mk(0.5f * ksum.hi, 0.5f * ksum.lo);
+          kb[f][fc] = dd_join(k);
+          dd head = val;
+          if (ax == v) head = side ? dd_add(val, H.half_h[ax]) : dd_sub(val, H.half_h[ax]);
+          gi = dd_add(gi, dd_mul(dd_mul(k, H.two_ih2[ax]), head));
+        } else {
+          kb[f][fc] = 0.0;
+          if (kind == 2) gi = dd_add(gi, dd_mul(val, H.ih[ax]));
+          else if (kind == 3) gi = dd_sub(gi, dd_mul(Ki, H.ih[ax]));
+        }
+      }
+    }
+    g[i] = dd_join(gi);
+  }
+}
+
 // restriction of a boundary-face array over the face's two in-plane axes
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_face(Geom F, Geom C, Xfer<T> X, int ax, const T* fine, T* coarse) {
@@ -342,6 +403,26 @@ void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, con
   by_model(model, [&](auto m) {
     k_prep_rhs<decltype(m)::value><<<b, 256, 0, s>>>(G, bc, Ks, Ks_s, p1, p2, mat, P, Kc, g, kb[0], kb[1], kb[2], kb[3],
                                                      kb[4], kb[5]);
+  });
+}
+
+void prep_rhs_dd(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
+                 const uint8_t* mat, const Phys<double>& P, const DDPhys& Q, int model, const double* Kc, double* g,
+                 double* const kb[6], cudaStream_t s) {
+  const long long n = (long long)G.n0 * G.n1 * G.n2;
+  const int b = grid_for(n);
+  RhsConstDD H;
+  for (int a = 0; a < 3; ++a) {
+    const double h = G.h[a];
+    H.half_ih[a] = host_split(0.5 / h);
+    H.ih[a] = host_split(1.0 / h);
+    H.two_ih2[a] = host_split(2.0 / (h * h));
+    H.half_h[a] = host_split(0.5 * h);
+  }
+  const dd ks = host_split(Ks_s);
+  by_model(model, [&](auto m) {
+    k_prep_rhs_dd<decltype(m)::value><<<b, 256, 0, s>>>(G, bc, Ks, ks, p1, p2, mat, P, Q, H, Kc, g, kb[0], kb[1], kb[2],
+                                                        kb[3], kb[4], kb[5]);
   });
 }
 

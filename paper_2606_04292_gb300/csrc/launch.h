@@ -60,6 +60,10 @@ void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const 
 void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
               const uint8_t* mat, const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6],
               cudaStream_t s);
+// mixed mode: the same terms in float-float
+void prep_rhs_dd(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
+                 const uint8_t* mat, const Phys<double>& P, const DDPhys& Q, int model, const double* Kc, double* g,
+                 double* const kb[6], cudaStream_t s);
 void restrict_face64(const Geom& F, const Geom& C, const Xfer<double>& X, int axis, const double* fine,
                      double* coarse, cudaStream_t s);
 void sink_coef(const Geom& G, double Tp, double depth, double decay, double* smax, cudaStream_t s);
