@@ -411,6 +411,7 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
+    from paper_2606_04292_gb300 import replicas
     from paper_2606_04292_gb300 import richards as R
     from paper_2606_04292_gb300 import workloads as W
 
@@ -469,13 +470,8 @@ def main():
         with open(args.profile_json, "w") as f:
             json.dump({"steps": prof_steps, "records": prof}, f, indent=1)
     updates = sum(i["cell_updates"] for i in infos)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    up_t = torch.tensor([float(updates)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(up_t, op=dist.ReduceOp.SUM)
-    ms_max, updates_all = ms_t.item(), up_t.item()
-    value = updates_all / (ms_max * 1e-3)
+    ms_max, updates_all = replicas.aggregate(ms, updates, device="cuda")
+    value = replicas.throughput(ms_max, updates_all)
     steps_per_s = world * args.steps / (ms_max * 1e-3)
 
     # end to end through the C ABI: inputs from pinned host memory each step,
