@@ -1421,10 +1421,23 @@ richards_status richards_set_state(richards_ctx* c, const double* psi, const dou
   if (!c || !psi) return RICH_EINVAL;
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   const long long N = c->L[0].ncell;
-  if (!finite_all(psi, N) || (psi_prev && !finite_all(psi_prev, N)) || !std::isfinite(t))
-    return fail(c, RICH_EINVAL, "non-finite state");
-  CK(cudaMemcpyAsync(c->psi_n, psi, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
-  if (psi_prev) CK(cudaMemcpyAsync(c->psi_nm1, psi_prev, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
+  if (!std::isfinite(t)) return fail(c, RICH_EINVAL, "non-finite time");
+  // the values are staged in two finest-level work arrays (FAS restricted
+  // iterate and defect, rewritten by every step) and checked there on the
+  // device, so that a rejected state leaves the context as it was
+  HLevel& F = c->L[0];
+  CK(cudaMemcpyAsync(F.ubar, psi, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
+  if (psi_prev) CK(cudaMemcpyAsync(F.d, psi_prev, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
+  unsigned* bad = (unsigned*)(c->scratch + 17);
+  CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), c->s));
+  rich::flag_nonfinite(F.ubar, N, bad, c->s);
+  if (psi_prev) rich::flag_nonfinite(F.d, N, bad, c->s);
+  TRY(check_launch(c));
+  CK(cudaMemcpyAsync(c->hscratch + 17, c->scratch + 17, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  if ((unsigned)c->hscratch[17] != 0u) return fail(c, RICH_EINVAL, "non-finite state");
+  CK(cudaMemcpyAsync(c->psi_n, F.ubar, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->s));
+  if (psi_prev) CK(cudaMemcpyAsync(c->psi_nm1, F.d, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->s));
   CK(cudaStreamSynchronize(c->s));
   c->have_state = true;
   c->have_prev = psi_prev != nullptr;

@@ -630,6 +630,21 @@ int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const P
   return b;
 }
 
+// *bad = 1 if any of x[0..n) is not finite (the exponent field all ones:
+// integer test, so no FP64 instruction)
+__global__ void __launch_bounds__(256) k_nonfinite(const double* __restrict__ x, long long n, unsigned* bad) {
+  bool any = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x[i]);
+    any |= ((b >> 52) & 0x7ffull) == 0x7ffull;
+  }
+  if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
+void flag_nonfinite(const double* x, long long n, unsigned* bad, cudaStream_t s) {
+  k_nonfinite<<<grid_for(n), 256, 0, s>>>(x, n, bad);
+}
+
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s) {
   k_apply_delta<<<grid_for(n), 256, 0, s>>>(u, delta, n);
 }

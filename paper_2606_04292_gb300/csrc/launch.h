@@ -90,6 +90,8 @@ int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const P
 void restrict_face32(const Geom& F, const Geom& C, const Xfer<float>& X, int axis, const float* fine, float* coarse,
                      cudaStream_t s);
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);
+// sets *bad to 1 if any of x[0..n) is NaN or infinite (device arrays)
+void flag_nonfinite(const double* x, long long n, unsigned* bad, cudaStream_t s);
 // theta(psi) and K(psi) per cell (FP64 or float-float); outputs nullable
 void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1, const double* p2,
                const uint8_t* mat, const Phys<double>& P, const DDPhys& Q, int model, bool dd, double* theta,

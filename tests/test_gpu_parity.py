@@ -544,6 +544,25 @@ def test_fp64_steps_without_presmoothing_match_oracle(mk):
         assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
 
 
+def test_rejected_state_leaves_the_context_unchanged():
+    """A state with a NaN or an infinity (in psi or psi_prev) is rejected
+    with EINVAL after the device check, and the previous state stays."""
+    prob = W.random_problem(3, (9, 8, 7), W.GARDNER, 16, scheme=2)
+    gs = R.Solver(prob)
+    gs.step()
+    before = gs.state()
+    for bad, prev in [(np.nan, None), (np.inf, None), (0.0, -np.inf)]:
+        psi = before.copy()
+        psi[17] = bad if bad != 0.0 else psi[17]
+        pp = None if prev is None else np.full_like(before, prev)
+        with pytest.raises(R.RichardsError) as e:
+            gs.set_state(psi, pp)
+        assert e.value.status == R.RICH_EINVAL
+        assert np.array_equal(gs.state(), before)
+    st, info = gs.step()
+    assert st == R.RICH_OK
+
+
 def test_pipelined_half_sweeps_equal_one_cell_per_thread():
     """Levels of >= 2^20 cells take the pipelined half-sweep (sweep_planes
     cells along z per thread, blocks away from the y/z boundaries without
