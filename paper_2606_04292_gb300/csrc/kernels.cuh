@@ -259,6 +259,76 @@ __global__ void __launch_bounds__(256) k_prolong_nested(Level<T> F, Level<T> C, 
   F.u[i] += s;
 }
 
+// ---------------------------------------------------------------------------
+// The interpolation of big 3-d levels through a shared-memory tile: a block
+// first stages, in coalesced rows, the coarse corrections u_H - psi_bar_H its
+// fine tile reads, with a one-cell halo (out-of-range halo cells repeat the
+// edge and are never weighted), then evaluates the taps of
+// k_prolong_nested, in the same order, from shared memory: same results,
+// fewer L1 requests (16 global loads per fine cell become 8 shared ones).
+// (The same staging for the restriction measured slower than its L1-cached
+// kernel: 64 taps per coarse cell reuse the cache well.)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct TransferTile {
+  static constexpr int PX = 64, PY = 4, PZ = 4;                         // fine tile of the interpolation
+};
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+template <typename T>
+__global__ void __launch_bounds__(TransferTile<T>::PX * TransferTile<T>::PY)
+k_prolong_tiled(Level<T> F, Level<T> C, Xfer<T> X) {
+  constexpr int PX = TransferTile<T>::PX, PY = TransferTile<T>::PY, PZ = TransferTile<T>::PZ;
+  constexpr int CX = PX / 2 + 2, CY = PY / 2 + 2, CZ = PZ / 2 + 2, NT = PX * PY;
+  __shared__ T se[CZ][CY][CX];
+  const int x0 = blockIdx.x * PX, y0 = blockIdx.y * PY, z0 = blockIdx.z * PZ;
+  const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1, cz0 = z0 / 2 - 1;
+  for (int t = threadIdx.x; t < CX * CY * CZ; t += NT) {
+    const int x = t % CX, y = (t / CX) % CY, z = t / (CX * CY);
+    const int gx = clampi(cx0 + x, 0, C.n0 - 1), gy = clampi(cy0 + y, 0, C.n1 - 1), gz = clampi(cz0 + z, 0, C.n2 - 1);
+    const unsigned gj = (unsigned)gx + (unsigned)C.n0 * ((unsigned)gy + (unsigned)C.n1 * (unsigned)gz);
+    se[z][y][x] = C.u[gj] - C.ubar[gj];
+  }
+  __syncthreads();
+  const int i0 = x0 + threadIdx.x % PX, i1 = y0 + threadIdx.x / PX;
+  if (i0 >= F.n0 || i1 >= F.n1) return;
+  int jx[2], jy[2];
+  T wx[2], wy[2];
+  prolong_taps<T>(X, 0, i0, F.n0, jx, wx);
+  prolong_taps<T>(X, 1, i1, F.n1, jy, wy);
+  for (int k = 0; k < PZ; ++k) {
+    const int i2 = z0 + k;
+    if (i2 >= F.n2) break;
+    int jz[2];
+    T wz[2];
+    prolong_taps<T>(X, 2, i2, F.n2, jz, wz);
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (wz[c] == T(0)) continue;
+      T sy = T(0);
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        if (wy[b] == T(0)) continue;
+        const T* row = &se[jz[c] - cz0][jy[b] - cy0][0];
+        T sx = T(0);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) sx += wx[a] * row[jx[a] - cx0];
+        sy += wy[b] * sx;
+      }
+      s += wz[c] * sy;
+    }
+    const unsigned i = (unsigned)(i0 + F.n0 * (i1 + F.n1 * i2));
+    F.u[i] += s;
+  }
+}
+
+// the tiles pay off on big 3-d levels
+inline bool tiled_transfer(int dim, int fn0, int fn1, int fn2) {
+  return dim == 3 && fn2 >= 4 && fn1 >= 4 && (long long)fn0 * fn1 * fn2 >= (1LL << 15);
+}
+
 inline bool nested_levels(int fn0, int fn1, int fn2, int cn0, int cn1, int cn2) {
   const int f[3] = {fn0, fn1, fn2}, c[3] = {cn0, cn1, cn2};
   for (int a = 0; a < 3; ++a)
@@ -528,7 +598,11 @@ struct Dispatch {
   }
   static void prolong(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, cudaStream_t s) {
     const Launch3 g = launch3(F.n0, F.n1, F.n2);
-    if (nested_levels(F.n0, F.n1, F.n2, C.n0, C.n1, C.n2))
+    if (nested_levels(F.n0, F.n1, F.n2, C.n0, C.n1, C.n2) && tiled_transfer(F.dim, F.n0, F.n1, F.n2)) {
+      using TT = TransferTile<T>;
+      const dim3 grid((F.n0 + TT::PX - 1) / TT::PX, (F.n1 + TT::PY - 1) / TT::PY, (F.n2 + TT::PZ - 1) / TT::PZ);
+      k_prolong_tiled<T><<<grid, TT::PX * TT::PY, 0, s>>>(F, C, X);
+    } else if (nested_levels(F.n0, F.n1, F.n2, C.n0, C.n1, C.n2))
       k_prolong_nested<T><<<g.grid, g.block, 0, s>>>(F, C, X);
     else
       k_prolong<T><<<g.grid, g.block, 0, s>>>(F, C, X);

@@ -174,7 +174,17 @@ def test_halfsweeps_match_oracle_on_every_level(mk, newton):
             assert sweep_agrees(orc, p, lev, got, ref, old, g), (lev, color, rel(got, ref))
 
 
-@pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS], ids=IDS)
+# big nested 3-d levels take the shared-memory tiled transfers (FP64 here,
+# the same template as the FP32 inner cycles), boundary tiles included
+TRANSFER_PROBLEMS = PROBLEMS + [
+    ("3d_vg_tiled_64x32x16", lambda: W.random_problem(3, (64, 32, 16), W.VANGENUCHTEN, 17, hetero=True,
+                                                      bc_kinds=[W.DIRICHLET, W.NOFLUX, W.NOFLUX, W.DIRICHLET,
+                                                                W.FREE_DRAINAGE, W.DIRICHLET])),
+    ("3d_vg_tiled_96x40x24", lambda: W.random_problem(3, (96, 40, 24), W.VANGENUCHTEN, 18, sink=True)),
+]
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in TRANSFER_PROBLEMS], ids=[p[0] for p in TRANSFER_PROBLEMS])
 def test_residual_restrict_tau_prolong_match_oracle(mk):
     prob = mk()
     gs, orc, p = pair(prob)
