@@ -437,7 +437,9 @@ __device__ __forceinline__ void sink_delta(T psi0, T x, T smax, const Phys<T>& P
 // Stencil: m_ii and sum_j m_ij u_j for cell i (interior faces K_f/h^2 with
 // K_f = (Kc_i + Kc_j)/2; Dirichlet faces 2 kb/h^2 on the diagonal).
 // ---------------------------------------------------------------------------
-template <typename T>
+// (YZI: the caller knows that the cell of a 3-d level is interior along axes
+// 1 and 2, so only axis 0 is tested for boundary faces)
+template <typename T, bool YZI = false>
 __device__ __forceinline__ void stencil(const Level<T>& L, long long i, int i0, int i1, int i2,
                                         const T* __restrict__ u, T& mii, T& off) {
   // neighbours through base pointers and 32-bit strides (levels hold fewer
@@ -454,6 +456,23 @@ __device__ __forceinline__ void stencil(const Level<T>& L, long long i, int i0, 
     else dg += T(2) * L.kb[0][i1 + L.n1 * i2] * s;
     if (i0 < L.n0 - 1) { const T m = (Ki + Kp[1]) * hs; dg += m; of += m * up[1]; }
     else dg += T(2) * L.kb[1][i1 + L.n1 * i2] * s;
+  }
+  if (YZI) {
+    {
+      const T s = L.ih2[1], hs = T(0.5) * s;
+      const int st = L.n0;
+      { const T m = (Ki + Kp[-st]) * hs; dg += m; of += m * up[-st]; }
+      { const T m = (Ki + Kp[st]) * hs; dg += m; of += m * up[st]; }
+    }
+    {
+      const T s = L.ih2[2], hs = T(0.5) * s;
+      const int st = L.n0 * L.n1;
+      { const T m = (Ki + Kp[-st]) * hs; dg += m; of += m * up[-st]; }
+      { const T m = (Ki + Kp[st]) * hs; dg += m; of += m * up[st]; }
+    }
+    mii = dg;
+    off = of;
+    return;
   }
   if (L.dim > 1) {
     const T s = L.ih2[1], hs = T(0.5) * s;
@@ -677,11 +696,11 @@ __device__ __forceinline__ T solve_cell(const Level<T>& L, const Phys<T>& P, con
 }
 
 // N(u)_i = storage(u_i) + xi u_i + m_ii u_i - sum_j m_ij u_j   (eq. Nh-def)
-template <typename T, int FORM, int MODEL>
+template <typename T, int FORM, int MODEL, bool YZI = false>
 __device__ __forceinline__ T apply_N(const Level<T>& L, const Phys<T>& P, const T* __restrict__ u,
                                      long long i, int i0, int i1, int i2) {
   T mii, off;
-  stencil(L, i, i0, i1, i2, u, mii, off);
+  stencil<T, YZI>(L, i, i0, i1, i2, u, mii, off);
   const T p1 = L.p1 ? L.p1[i] : P.p1;
   const T p2 = L.p2 ? L.p2[i] : P.p2;
   const T smax = L.smax ? L.smax[i] : T(0);

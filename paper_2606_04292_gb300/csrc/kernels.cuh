@@ -100,7 +100,10 @@ __global__ void __launch_bounds__(256) k_residual(Level<T> L, Phys<T> P, unsigne
   const int i1 = blockIdx.y, i2 = blockIdx.z;
   if (i0 < L.n0) {
     const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
-    const T di = L.g[i] - apply_N<T, FORM, MODEL>(L, P, L.u, i, i0, i1, i2);
+    // rows away from the y/z boundaries skip those tests (uniform over the block)
+    const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && i2 > 0 && i2 < L.n2 - 1;
+    const T di = L.g[i] - (yzi ? apply_N<T, FORM, MODEL, true>(L, P, L.u, i, i0, i1, i2)
+                               : apply_N<T, FORM, MODEL, false>(L, P, L.u, i, i0, i1, i2));
     L.d[i] = di;
     mx = nbits(di);
   }
