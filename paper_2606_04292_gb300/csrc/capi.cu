@@ -572,7 +572,10 @@ void vcycle64(richards_ctx* c, int l, bool d_ready = false) {
 // d_ready: the finest level's defect array already holds g - N(u) for the
 // current u (only used with nu1 = 0, where no pre-smoothing changes u
 // between the inner stop test's defect and this cycle's restriction)
-void vcycle32(richards_ctx* c, int l, bool d_ready = false) {
+// fuse (finest level only): the last half-sweep of the post-smoothing also
+// writes its cells' defects, a defect pass over the other colour completes
+// d, and ||d||_inf lands in scratch slot 1, ready for the inner stop test
+void vcycle32(richards_ctx* c, int l, bool d_ready = false, bool fuse = false) {
   const int model = c->soil.model;
   const Phys<float> P = phys<float>(c);
   if (l >= c->tail_start) {
@@ -595,7 +598,17 @@ void vcycle32(richards_ctx* c, int l, bool d_ready = false) {
   for (int q = 0; q < gamma_at(c, l); ++q) vcycle32(c, l + 1);
   nvtxRangePushA(level_range(l));
   { Prof pr(c, "prolong32", l, F.ncell); rich::prolong32(F, C, xfer32(c, l), c->s); }
-  smooth32(c, F, P, l, c->opts.nu2);
+  if (fuse && l == 0 && c->opts.nu2 >= 1) {
+    smooth32(c, F, P, l, c->opts.nu2 - 1);
+    const long long half = (F.ncell + 1) / 2;
+    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->opts.sweep_planes, c->s); }
+    cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s);
+    { Prof pr(c, "sweep_resid32", l, F.ncell - half); rich::sweep_resid32(F, P, model, c->scratch + 1, c->s); }
+    { Prof pr(c, "residual32", l, half); rich::residual_color32(F, P, model, 0, c->scratch + 1, c->s); }
+    c->updates_host += F.ncell;
+  } else {
+    smooth32(c, F, P, l, c->opts.nu2);
+  }
   nvtxRangePop();
 }
 
@@ -609,8 +622,15 @@ void vcycle32(richards_ctx* c, int l, bool d_ready = false) {
 // then skips recomputing it.
 bool top_defect_ready(const richards_ctx* c) { return c->opts.nu1 == 0 && c->opts.inner_rtol > 0.0; }
 
+// the stop test's defect then also comes from the cycle's last half-sweep
+// (see vcycle32), on levels the pipelined half-sweep serves
+bool fuse_defect(const richards_ctx* c) {
+  return top_defect_ready(c) && c->opts.ordering == 1 && c->opts.nu2 >= 1 && c->tail_start > 0 &&
+         rich::resid_fusable32(view32(c, 0), c->opts.sweep_planes);
+}
+
 void run_cycle32(richards_ctx* c) {
-  const bool ready = top_defect_ready(c);
+  const bool ready = top_defect_ready(c), fuse = fuse_defect(c);
   if (c->opts.graphs && c->graphs_ok && c->s != nullptr) {
     richards_ctx::GraphRec& G = c->graphs[c->scheme_used];
     if (!G.exec || G.a != c->a || G.with_prof != c->prof) {
@@ -626,7 +646,7 @@ void run_cycle32(richards_ctx* c) {
       const char* where = "cudaStreamBeginCapture";
       if (e == cudaSuccess) {
         c->capturing = true;
-        vcycle32(c, 0, ready);
+        vcycle32(c, 0, ready, fuse);
         c->capturing = false;
         const cudaError_t el = cudaGetLastError();
         e = cudaStreamEndCapture(c->s, &g);
@@ -650,7 +670,7 @@ void run_cycle32(richards_ctx* c) {
         G.prof.clear();
         G.exec = nullptr;
         c->graphs_ok = false;
-        vcycle32(c, 0, ready);
+        vcycle32(c, 0, ready, fuse);
         return;
       }
       G.a = c->a;
@@ -666,7 +686,7 @@ void run_cycle32(richards_ctx* c) {
     if (c->prof && !G.prof.empty()) c->harvest = &G;
     return;
   }
-  vcycle32(c, 0, ready);
+  vcycle32(c, 0, ready, fuse);
 }
 
 // coarse copies of the lagged conductivity and boundary conductances
@@ -951,12 +971,13 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
         done_in = rin <= rtol_in * rin0;
       }
     }
+    const bool fused = fuse_defect(c);           // the cycle leaves d and its norm
     for (int k = 0; k < c->opts.inner_cycles && !done_in; ++k) {
       run_cycle32(c);
       ++inner;
       if (c->opts.inner_rtol > 0.0 && k + 1 < c->opts.inner_cycles) {
-        CK(cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s));
-        {
+        if (!fused) {
+          CK(cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s));
           Prof pr(c, "residual32", 0, F.ncell);
           rich::residual32(view32(c, 0), P32, model, c->scratch + 1, c->s);
         }

@@ -674,9 +674,12 @@ __device__ __forceinline__ void gather(const Level<T>& L, const Phys<T>& P, int 
 
 // the point update of a gathered cell (same sums, in the same order, as
 // stencil() and point_update())
-template <typename T, int FORM, int MODEL, int NK = 0, bool YZI = false>
-__device__ __forceinline__ T solve_cell(const Level<T>& L, const Phys<T>& P, const CellOps<T>& c) {
-  T dg = T(0), of = T(0);
+// m_ii (dg) and sum_j m_ij u_j (of) of a gathered cell: the sums of
+// stencil(), in its order
+template <typename T, bool YZI = false>
+__device__ __forceinline__ void cell_sums(const Level<T>& L, const CellOps<T>& c, T& dg, T& of) {
+  dg = T(0);
+  of = T(0);
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     const T s = L.ih2[f >> 1];
@@ -688,11 +691,34 @@ __device__ __forceinline__ T solve_cell(const Level<T>& L, const Phys<T>& P, con
       of += m * c.un[f];
     }
   }
+}
+
+// g_i - N(u)_i of a gathered cell at the value x of u_i, with its sums dg, of
+// (the expression of apply_N(), so both give the same bits)
+template <typename T, int FORM, int MODEL>
+__device__ __forceinline__ T cell_defect(const Phys<T>& P, const CellOps<T>& c, T dg, T of, T x) {
+  T val, der;
+  with_law<MODEL>(P, c.mat, [&](auto law, const Phys<T>& Q) {
+    storage<T, FORM, decltype(law)::value>(x, c.psi0, c.p1, c.p2, c.smax, Q, val, der);
+    return 0;
+  });
+  return c.g - (val + P.xi * x + dg * x - of);
+}
+
+template <typename T, int FORM, int MODEL, int NK = 0, bool YZI = false>
+__device__ __forceinline__ T solve_cell_sums(const Level<T>& L, const Phys<T>& P, const CellOps<T>& c, T dg, T of) {
   const T cc = P.xi + P.kappa + dg;
   const T f = c.g + of + P.kappa * c.ui;
   return with_law<MODEL>(P, c.mat, [&](auto law, const Phys<T>& Q) {
     return point_solve<T, FORM, decltype(law)::value, NK>(cc, f, c.ui, c.psi0, c.p1, c.p2, c.smax, Q);
   });
+}
+
+template <typename T, int FORM, int MODEL, int NK = 0, bool YZI = false>
+__device__ __forceinline__ T solve_cell(const Level<T>& L, const Phys<T>& P, const CellOps<T>& c) {
+  T dg, of;
+  cell_sums<T, YZI>(L, c, dg, of);
+  return solve_cell_sums<T, FORM, MODEL, NK, YZI>(L, P, c, dg, of);
 }
 
 // N(u)_i = storage(u_i) + xi u_i + m_ii u_i - sum_j m_ij u_j   (eq. Nh-def)

@@ -1,11 +1,9 @@
-// FP32 instantiations: the inner correction problem of the mixed mode.
+// FP32 instantiations: the inner correction problem of the mixed mode (the
+// half-sweeps are in k32s.cu).
 #include "kernels.cuh"
 
 namespace rich {
 using D = Dispatch<float, FORM_DELTA>;
-void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, int planes, cudaStream_t s) {
-  D::sweep_pipe(L, P, model, color, planes, s);
-}
 void residual32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,
                 cudaStream_t s) {
   D::residual(L, P, model, norm, s);
@@ -23,5 +21,8 @@ void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, con
             int ordering, cudaStream_t s) {
   D::tail(dLs, dXs, l0, nl, P, model, nu1, nu2, cmax, crtol, gamma, gamma_levels, stats, ordering, s);
 }
-void sweep_lex32(const Level<float>& L, const Phys<float>& P, int model, cudaStream_t s) { D::sweep_lex(L, P, model, s); }
+void residual_color32(const Level<float>& L, const Phys<float>& P, int model, int color, unsigned long long* norm,
+                      cudaStream_t s) {
+  D::residual_color(L, P, model, color, norm, s);
+}
 }  // namespace rich

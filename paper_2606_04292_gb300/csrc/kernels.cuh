@@ -39,8 +39,13 @@ __global__ void __launch_bounds__(256) k_sweep(Level<T> L, Phys<T> P, int color)
 // operands of the next plane's cell are loaded before the current cell is
 // solved.  Launch grid: x = pairs of cells along a row, y = row, z = chunk
 // of ZC planes.
-template <typename T, int FORM, int MODEL, int ZC, int NK, bool YZI>
-__device__ __forceinline__ void sweep_pipe_body(const Level<T>& L, const Phys<T>& P, int color, int p, int i1, int z0) {
+// RESID: the half-sweep also writes the defect d = g - N(u) of each cell it
+// updates, at the new value (its neighbours, of the other colour, do not
+// change during the half-sweep), and returns the largest |d| (bits)
+template <typename T, int FORM, int MODEL, int ZC, int NK, bool YZI, bool RESID>
+__device__ __forceinline__ unsigned long long sweep_pipe_body(const Level<T>& L, const Phys<T>& P, int color, int p,
+                                                              int i1, int z0) {
+  unsigned long long mx = 0;
   CellOps<T> c[2];
   {
     const int i0 = 2 * p + ((color + i1 + z0) & 1);
@@ -57,20 +62,64 @@ __device__ __forceinline__ void sweep_pipe_body(const Level<T>& L, const Phys<T>
       if (nx.valid) gather<T, FORM, MODEL, YZI>(L, P, i0, i1, i2, nx);
     }
     const CellOps<T>& cur = c[k & 1];
-    if (cur.valid) L.u[cur.i] = solve_cell<T, FORM, MODEL, NK, YZI>(L, P, cur);
+    if (cur.valid) {
+      T dg, of;
+      cell_sums<T, YZI>(L, cur, dg, of);
+      const T x = solve_cell_sums<T, FORM, MODEL, NK, YZI>(L, P, cur, dg, of);
+      L.u[cur.i] = x;
+      if (RESID) {
+        const T di = cell_defect<T, FORM, MODEL>(P, cur, dg, of, x);
+        L.d[cur.i] = di;
+        const unsigned long long b = nbits(di);
+        mx = b > mx ? b : mx;
+      }
+    }
   }
+  return mx;
 }
 
-template <typename T, int FORM, int MODEL, int ZC, int NK = 0>
-__global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int color) {
+template <typename T, int FORM, int MODEL, int ZC, int NK = 0, bool RESID = false>
+__global__ void __launch_bounds__(128) k_sweep_pipe(Level<T> L, Phys<T> P, int color, unsigned long long* norm) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int i1 = blockIdx.y;
   const int z0 = blockIdx.z * ZC;
   // blocks away from the y and z boundaries (all but a thin shell) skip
   // those boundary tests; the branch is uniform over the block
-  const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && z0 > 0 && z0 + ZC < L.n2;
-  if (yzi) sweep_pipe_body<T, FORM, MODEL, ZC, NK, true>(L, P, color, p, i1, z0);
-  else sweep_pipe_body<T, FORM, MODEL, ZC, NK, false>(L, P, color, p, i1, z0);
+  // (the deeper pipelines, 4 and 8 planes, keep one body: compile time)
+  unsigned long long mx;
+  if constexpr (ZC == 2) {
+    const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && z0 > 0 && z0 + ZC < L.n2;
+    mx = yzi ? sweep_pipe_body<T, FORM, MODEL, ZC, NK, true, RESID>(L, P, color, p, i1, z0)
+             : sweep_pipe_body<T, FORM, MODEL, ZC, NK, false, RESID>(L, P, color, p, i1, z0);
+  } else {
+    mx = sweep_pipe_body<T, FORM, MODEL, ZC, NK, false, RESID>(L, P, color, p, i1, z0);
+  }
+  if (RESID) {
+    __shared__ unsigned long long sm[33];
+    mx = block_max(mx, sm);
+    if (threadIdx.x == 0) atomicMax(norm, mx);
+  }
+}
+
+// The defect of the cells of one colour (the other colour's defects come
+// from a RESID half-sweep).  Launch grid: as k_sweep.
+template <typename T, int FORM, int MODEL>
+__global__ void __launch_bounds__(256) k_residual_color(Level<T> L, Phys<T> P, int color, unsigned long long* norm) {
+  __shared__ unsigned long long sm[33];
+  unsigned long long mx = 0;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i2 = blockIdx.z;
+  const int i0 = 2 * p + ((color + i1 + i2) & 1);
+  if (i0 < L.n0) {
+    const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
+    const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && i2 > 0 && i2 < L.n2 - 1;
+    const T di = L.g[i] - (yzi ? apply_N<T, FORM, MODEL, true>(L, P, L.u, i, i0, i1, i2)
+                               : apply_N<T, FORM, MODEL, false>(L, P, L.u, i, i0, i1, i2));
+    L.d[i] = di;
+    mx = nbits(di);
+  }
+  mx = block_max(mx, sm);
+  if (threadIdx.x == 0) atomicMax(norm, mx);
 }
 
 // One hyperplane i0 + i1 + i2 = s of a lexicographic NGS sweep (the
@@ -542,7 +591,7 @@ struct Dispatch {
     Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
     g.grid.z = (L.n2 + ZC - 1) / ZC;
     by_model(model, [&](auto m) {
-      k_sweep_pipe<T, FORM, decltype(m)::value, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
+      k_sweep_pipe<T, FORM, decltype(m)::value, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color, nullptr);
     });
   }
   template <int ZC>
@@ -579,6 +628,33 @@ struct Dispatch {
     if (FORM == FORM_DELTA && P.newton_k == 1) sweep_lex_nk<(FORM == FORM_DELTA ? 1 : 0)>(L, P, model, s);
     else if (FORM == FORM_DELTA && P.newton_k == 2) sweep_lex_nk<(FORM == FORM_DELTA ? 2 : 0)>(L, P, model, s);
     else sweep_lex_nk<0>(L, P, model, s);
+  }
+  // whether sweep_resid applies to a level (the pipelined two-plane kernel)
+  static bool fusable(const Level<T>& L, int planes) {
+    return FORM == FORM_DELTA && planes == 2 && L.n2 >= 2 && L.ncell >= (1LL << 20);
+  }
+  // the last half-sweep of a smoothing (colour 1), writing the defects of
+  // its cells; residual_color(0) then gives colour 0's: d and ||d||_inf
+  // (into *norm) at the end of the smoothing, as one defect pass would
+  static void sweep_resid(const Level<T>& L, const Phys<T>& P, int model, unsigned long long* norm, cudaStream_t s) {
+    auto sweep_r = [&](auto nk) {
+      Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
+      g.grid.z = (L.n2 + 1) / 2;
+      by_model(model, [&](auto m) {
+        k_sweep_pipe<T, FORM, decltype(m)::value, 2, decltype(nk)::value, true><<<g.grid, g.block, 0, s>>>(L, P, 1,
+                                                                                                          norm);
+      });
+    };
+    if (FORM == FORM_DELTA && P.newton_k == 1) sweep_r(LawTag<(FORM == FORM_DELTA ? 1 : 0)>{});
+    else if (FORM == FORM_DELTA && P.newton_k == 2) sweep_r(LawTag<(FORM == FORM_DELTA ? 2 : 0)>{});
+    else sweep_r(LawTag<0>{});
+  }
+  static void residual_color(const Level<T>& L, const Phys<T>& P, int model, int color, unsigned long long* norm,
+                             cudaStream_t s) {
+    const Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
+    by_model(model, [&](auto m) {
+      k_residual_color<T, FORM, decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, color, norm);
+    });
   }
   static void residual(const Level<T>& L, const Phys<T>& P, int model, unsigned long long* norm,
                        cudaStream_t s) {

@@ -50,6 +50,13 @@ void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, con
             int model, int nu1, int nu2, int cmax, float crtol, int gamma, int gamma_levels,
             unsigned long long* stats, int ordering, cudaStream_t s);
 void sweep_lex32(const Level<float>& L, const Phys<float>& P, int model, cudaStream_t s);
+// the last (colour 1) half-sweep of a smoothing that also writes its cells' defects and their
+// max into *norm (pipelined two-plane levels only: resid_fusable32), and the defects of one colour
+bool resid_fusable32(const Level<float>& L, int planes);
+void sweep_resid32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,
+                   cudaStream_t s);
+void residual_color32(const Level<float>& L, const Phys<float>& P, int model, int color, unsigned long long* norm,
+                      cudaStream_t s);
 
 // per-step preparation (FP64).  mat: the fine level's material index (read
 // only when model == COMPOSITE; nullable otherwise)
