@@ -181,7 +181,10 @@ __global__ void __launch_bounds__(256) k_tau(Level<T> C, Phys<T> P) {
   const int J1 = blockIdx.y, J2 = blockIdx.z;
   if (J0 >= C.n0) return;
   const long long J = J0 + (long long)C.n0 * (J1 + C.n1 * J2);
-  C.g[J] = apply_N<T, FORM, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
+  // rows away from the y/z boundaries skip those tests (uniform over the block)
+  const bool yzi = C.dim == 3 && J1 > 0 && J1 < C.n1 - 1 && J2 > 0 && J2 < C.n2 - 1;
+  C.g[J] = (yzi ? apply_N<T, FORM, MODEL, true>(C, P, C.ubar, J, J0, J1, J2)
+                : apply_N<T, FORM, MODEL, false>(C, P, C.ubar, J, J0, J1, J2)) + C.d[J];
   C.u[J] = C.ubar[J];
 }
 
