@@ -290,9 +290,12 @@ def drainage_3d(n=256, dt=300.0, nsteps=50, seed_ks=3, seed_vg=4, **optkw):
     # FP32 inner solve reduces its defect 1e4-fold (two outer corrections
     # reach tol 1e-8; 1e3 takes three), and levels of up to 512 cells run in
     # the single-block tail.  One safeguarded Newton step per point update
-    # gives the same cycles per step here as two in 8% less time.
+    # gives the same cycles per step here as two in 8% less time.  Coarsening
+    # stops at 8^3 (two sweeps there): as many cycles as with a 4^3 level
+    # below it, 6% less time.
     opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0, precision=1, cycle_gamma=2, gamma_levels=2,
-                        nu1=0, nu2=2, coarse_max_sweeps=2, inner_rtol=1e-4, tail_cells=512, newton_iters=1)
+                        nu1=0, nu2=2, coarse_max_sweeps=2, coarsest_max_n=8, inner_rtol=1e-4, tail_cells=512,
+                        newton_iters=1)
     opts.update(optkw)
     return dict(name=f"drainage3d_n{n}", dim=3, n=(n, n, n), L=(1.0, 1.0, 1.0),
                 soil=soil, bc=bc, sink=no_sink(),

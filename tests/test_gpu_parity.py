@@ -89,11 +89,12 @@ PROBLEMS = [
     ("3d_vg_hetero_sink", lambda: W.random_problem(3, (17, 12, 9), W.VANGENUCHTEN, 4, hetero=True, sink=True)),
     ("3d_haverkamp_dir", lambda: W.random_problem(3, (10, 11, 13), W.HAVERKAMP, 5,
                                                    bc_kinds=[W.DIRICHLET] * 6)),
-    # (W(2,2): with one fixed Newton step and the adaptive coarse stop, the
-    # slower-converging W(0,2) default can part from the oracle by a few
-    # cycles on one-ulp differences; W(0,2) has its own test with Newton to
-    # round-off below)
-    ("3d_drainage_16", lambda: W.drainage_3d(n=16, precision=0, nu1=2)),
+    # (W(2,2) down to 4^3: with one fixed Newton step and the adaptive coarse
+    # stop, the slower-converging W(0,2) default can part from the oracle by a
+    # few cycles on one-ulp differences; W(0,2) has its own test with Newton to
+    # round-off below.  An 8^3 coarsest level, right for 256^3, leaves 16^3
+    # two levels, too few for the tight-tolerance oracle runs.)
+    ("3d_drainage_16", lambda: W.drainage_3d(n=16, precision=0, nu1=2, coarsest_max_n=4)),
     ("2d_gardner_paper_32", lambda: W.gardner_2d(n=32)),
     ("1d_celia_composite_40", lambda: W.celia_composite_1d(n=40)),
     ("2d_layers_3mat", lambda: layered(2, (23, 19), W.VANGENUCHTEN, 6, "layers",
@@ -512,7 +513,7 @@ def test_mixed_without_presmoothing_reuses_the_stop_test_defect(fmg, graphs):
     steps meet the stop test on the oracle's own FP64 residual, stay within
     the error bound, converge in as many cycles as a W(1,2) run needs at most
     1.6 times over, and graph replay equals direct launches."""
-    prob = W.with_opts(W.drainage_3d(n=32), nu1=0, nu2=2, fmg_cycles=fmg)
+    prob = W.with_opts(W.drainage_3d(n=32, coarsest_max_n=4), nu1=0, nu2=2, fmg_cycles=fmg)
     gs = R.Solver(prob, opts=dict(graphs=graphs))
     ref = R.Solver(W.with_opts(prob, nu1=1))
     orc = Oracle(W.with_opts(prob, tol=1e-13, newton_iters=0, fmg_cycles=0))
