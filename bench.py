@@ -39,7 +39,7 @@ WORKLOAD = "3D drainage 256^3, heterogeneous VG (lognormal Ks, sigma_lnK=1, corr
 # DRAM bytes (read + write) per launch of the finest level's half-sweep of
 # 256^3 (8,388,608 cells), from an ncu capture of this kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum); the roofline's traffic.
-TRAFFIC_PER_LAUNCH = {("sweep32", 8388608): 459.6e6}
+TRAFFIC_PER_LAUNCH = {("sweep32", 8388608): 459.4e6}
 
 BYTES_PER_CELL = {
     "sweep32": 28.0,
