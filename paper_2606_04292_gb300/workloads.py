@@ -283,18 +283,17 @@ def drainage_3d(n=256, dt=300.0, nsteps=50, seed_ks=3, seed_vg=4, **optkw):
     bc = _bc([NOFLUX, NOFLUX, NOFLUX, NOFLUX, FREE_DRAINAGE, NOFLUX])
     # W-cycles on the two finest levels (V below): on this heterogeneous,
     # partly saturated field they need ~2.4x fewer cycles than V-cycles, as
-    # many as full W-cycles, and two coarsest sweeps are enough.  Two post-
-    # and no pre-smoothing sweeps, W(0,2): 13.9 cycles per step against 10.6
-    # for W(2,2), but each cycle reuses the inner stop test's finest-level
-    # defect, so a step costs 13% less (28.9 against 33.3 ms at 256^3).  Each
-    # FP32 inner solve reduces its defect 1e4-fold (two outer corrections
-    # reach tol 1e-8; 1e3 takes three), and levels of up to 512 cells run in
-    # the single-block tail.  One safeguarded Newton step per point update
+    # many as full W-cycles.  Two post- and no pre-smoothing sweeps, W(0,2):
+    # 13.9 cycles per step against 10.6 for W(2,2), but each cycle reuses the
+    # inner stop test's finest-level defect, so a step costs 13% less (28.9
+    # against 33.3 ms at 256^3, when it was measured).  Each FP32 inner solve
+    # reduces its defect 5e3-fold (two or three outer corrections reach tol
+    # 1e-8), and levels of up to 512 cells run in the single-block tail.  One safeguarded Newton step per point update
     # gives the same cycles per step here as two in 8% less time.  Coarsening
-    # stops at 8^3 (two sweeps there): as many cycles as with a 4^3 level
-    # below it, 6% less time.
+    # stops at 8^3: as many cycles as with a 4^3 level below it, 6% less
+    # time; one sweep there and an inner target of 2e-4 save another 2%.
     opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0, precision=1, cycle_gamma=2, gamma_levels=2,
-                        nu1=0, nu2=2, coarse_max_sweeps=2, coarsest_max_n=8, inner_rtol=1e-4, tail_cells=512,
+                        nu1=0, nu2=2, coarse_max_sweeps=1, coarsest_max_n=8, inner_rtol=2e-4, tail_cells=512,
                         newton_iters=1)
     opts.update(optkw)
     return dict(name=f"drainage3d_n{n}", dim=3, n=(n, n, n), L=(1.0, 1.0, 1.0),

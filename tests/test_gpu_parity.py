@@ -92,9 +92,11 @@ PROBLEMS = [
     # (W(2,2) down to 4^3: with one fixed Newton step and the adaptive coarse
     # stop, the slower-converging W(0,2) default can part from the oracle by a
     # few cycles on one-ulp differences; W(0,2) has its own test with Newton to
-    # round-off below.  An 8^3 coarsest level, right for 256^3, leaves 16^3
-    # two levels, too few for the tight-tolerance oracle runs.)
-    ("3d_drainage_16", lambda: W.drainage_3d(n=16, precision=0, nu1=2, coarsest_max_n=4)),
+    # round-off below.  An 8^3 coarsest level with one sweep, right for
+    # 256^3, leaves 16^3 two levels, too few for the tight-tolerance oracle
+    # runs.)
+    ("3d_drainage_16", lambda: W.drainage_3d(n=16, precision=0, nu1=2, coarsest_max_n=4, coarse_max_sweeps=2,
+                                             inner_rtol=1e-4)),
     ("2d_gardner_paper_32", lambda: W.gardner_2d(n=32)),
     ("1d_celia_composite_40", lambda: W.celia_composite_1d(n=40)),
     ("2d_layers_3mat", lambda: layered(2, (23, 19), W.VANGENUCHTEN, 6, "layers",
