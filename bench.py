@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-gardner", action="store_true")
     ap.add_argument("--no-layered", action="store_true")
+    ap.add_argument("--no-table3", action="store_true")
     ap.add_argument("--temporal-study", action="store_true",
                     help="add Section 4.1's temporal-convergence study (N=1024 vs N=2048, tau_ref=1e-4; ~4 min)")
     ap.add_argument("--gamma", type=int, default=2, help="1 = V-cycles, 2 = W-cycles")
@@ -343,6 +344,24 @@ def layered_cpu(states):
     return res
 
 
+TABLE3_CPU_STEPS = 20
+
+
+def table3_cpu():
+    """The oracle on the first TABLE3_CPU_STEPS steps of Table 3's column
+    (single thread, red-black V(5,5)): seconds per step, and that rate over
+    the whole run."""
+    from oracle.oracle import Oracle
+    from paper_2606_04292_gb300 import workloads as W
+    o = Oracle(W.celia_1d(n=2048, dt=0.1, nu1=5, nu2=5, kappa=0.1))
+    t0 = time.perf_counter()
+    for _ in range(TABLE3_CPU_STEPS):
+        o.step()
+    per = (time.perf_counter() - t0) / TABLE3_CPU_STEPS
+    return {"cores": 1, "s_per_step": per, "whole_run_at_that_rate_s": per * 3600,
+            "sample": f"first {TABLE3_CPU_STEPS} steps"}
+
+
 # ---------------------------------------------------------------------------
 def cpu_baseline(prob, psi, nsweeps=3):
     """The CPU oracle, as it stands, on a bounded sample of the same workload:
@@ -548,6 +567,14 @@ def main():
     if rank == 0 and not args.no_layered:
         layered, lstates = layered_bench(stream)
 
+    table3 = None
+    if rank == 0 and not args.no_table3:
+        from paper_2606_04292_gb300 import studies
+        table3 = studies.table3_column()
+        table3.pop("state")
+        table3["paper_cpu_s_vcycle55"] = 20.0
+        table3["workload"] = "Section 4.1 column, N=2048, tau 0.1 s to t=360 s (3600 BDF1 steps), V(5,5), tol 1e-8"
+
     temporal = None
     if rank == 0 and args.temporal_study:
         from paper_2606_04292_gb300 import studies
@@ -562,6 +589,8 @@ def main():
             gardner["cpu_oracle"] = gardner_cpu(gstates)
         if layered is not None:
             layered["cpu_oracle"] = layered_cpu(lstates)
+        if table3 is not None:
+            table3["cpu_oracle"] = table3_cpu()
 
     if rank == 0:
         line = {
@@ -586,6 +615,7 @@ def main():
             "paper_gardner_2d": gardner,
             "paper_layered": layered,
             "paper_temporal_study": temporal,
+            "paper_table3": table3,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

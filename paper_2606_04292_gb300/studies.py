@@ -1,4 +1,4 @@
-"""The paper's temporal-convergence study re-run on the GPU.
+"""The paper's temporal-convergence study and Table 3's run on the GPU.
 
 Section 4.1 measures the time discretisation error of the Celia column:
 solutions on N = 1024 cells with tau = 0.1 * 2^-k (k = 0..5) at t = 10 s
@@ -11,6 +11,10 @@ thread so that the runs overlap on the device.
 The reference lives on twice the cells: a coarse cell centre is the face
 between fine cells 2j and 2j + 1, where the linear interpolant of the
 reference is the mean of those two values.
+
+``table3_column`` runs Table 3's configuration (the same column on 2048
+cells to t = 360 s at tau = 0.1 s, V(5,5)) through the same solver, for its
+wall time beside the paper's CPU times.
 
 Command line (prints one JSON object)::
 
@@ -80,6 +84,31 @@ def temporal_convergence(n=1024, n_ref=2048, tau0=0.1, ks=range(6), times=(10.0,
         errs = [float(np.max(np.abs(r[0][i] - ref))) for r in results[:-1]]
         out["errors"][str(t)] = errs
         out["orders"][str(t)] = [math.log2(errs[j] / errs[j + 1]) for j in range(len(errs) - 1)]
+    return out
+
+
+def table3_column(n=2048, tau=0.1, t_end=360.0, nu=5, kappa=0.1):
+    """Table 3's configuration (Section 4.1): the Celia column on n cells to
+    t_end with step tau and V(nu, nu) cycles, here through the batched-column
+    solver (mixed precision, every step in one launch).  Wall time of the
+    whole run, last status and cycles per step."""
+    import torch
+    nsteps = int(round(t_end / tau))
+    prob = W.celia_1d(n=n, dt=tau, nsteps=nsteps, nu1=nu, nu2=nu, kappa=kappa, precision=1)
+    stream = torch.cuda.Stream()
+    cols = R.Columns([prob], stream=stream.cuda_stream)
+    threads = cols.autotune(tau, 1)           # block size for this one column (state restored)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = cols.run(tau, nsteps, 1)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    stats = cols.stats()
+    out = {"n": n, "tau": tau, "steps": nsteps, "cycle": f"V({nu},{nu})", "threads": threads, "wall_s": wall,
+           "status": R.STATUS_NAMES.get(int(stats["status"][0]), str(int(stats["status"][0]))),
+           "run_status": R.STATUS_NAMES.get(st, str(st)), "cycles_per_step": float(stats["cycles"][0]) / nsteps,
+           "state": cols.state()}
+    cols.close()
     return out
 
 
