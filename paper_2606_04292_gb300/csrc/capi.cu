@@ -1008,8 +1008,6 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   return finish_step(c, r, st, moved ? 1 : 0);
 }
 
-richards_status check_ctx(const richards_ctx* c) { return c ? RICH_OK : RICH_EINVAL; }
-
 }  // namespace
 
 // ==========================================================================
