@@ -156,6 +156,31 @@ def test_sink_reading_shape():
     assert dS > 0          # rising branch (A2)
 
 
+@pytest.mark.parametrize("dim", [1, 3])
+def test_sink_total_uptake_is_midpoint_rule_of_tp(dim):
+    """On the Feddes plateau the whole column takes up Tp per unit area: the
+    cells sample beta(d) = exp(-d/lambda)/Z, normalised on [0, D], at their
+    centres, so the total is the midpoint rule of an integral equal to one.
+    With D on a face, Euler-Maclaurin gives the relative error
+    -h^2 (f'(D) - f'(0)) / 24 = -h^2 / (24 lambda^2) + O(h^4) (f = beta); a
+    wrong normaliser, depth measured from the wrong end or off the cell
+    centre breaks the constant or the order."""
+    k = W.feddes_sink()
+    lam, D = k["root_decay"], k["root_depth"]
+    for n in (40, 80, 160, 320):
+        h = 1.0 / n
+        assert abs(D / h - round(D / h)) < 1e-9          # root zone ends on a face
+        shape = (n,) if dim == 1 else (3, 2, n)
+        p = W.random_problem(dim, shape, W.GARDNER, 1, sink=True, L=1.0)
+        o = Oracle(p)
+        Tp = p["sink"]["Tp"]
+        ncol = int(np.prod(shape[:-1]))
+        total = sum(o.sink(i, -1.0)[0] for i in range(ncol * n)) * o.cell_volume()
+        rel = total / (Tp * 1.0 ** (dim - 1)) - 1.0
+        lead = -h * h / (24.0 * lam * lam)
+        assert abs(rel - lead) <= 7.0 * h ** 4 / (5760.0 * lam ** 4) * 1.2, (n, rel, lead)
+
+
 # ---------------------------------------------------------------------------
 # Operator assembly: Prop. 3.1 and closed-form discrete steady states.
 # ---------------------------------------------------------------------------
