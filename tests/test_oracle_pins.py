@@ -441,6 +441,48 @@ def test_point_solve_matches_bracketing_root(model):
 
 
 # ---------------------------------------------------------------------------
+# Coarse operators (Section 3.2, "complete analogy").
+# ---------------------------------------------------------------------------
+COARSE_CASES = [(1, (8,)), (1, (9,)), (2, (8, 6)), (2, (7, 10)), (3, (6, 4, 8)), (3, (5, 6, 7))]
+
+
+@pytest.mark.parametrize("dim,n", COARSE_CASES)
+@pytest.mark.parametrize("model", [W.HAVERKAMP, W.GARDNER, W.VANGENUCHTEN])
+def test_coarse_operator_is_rediscretisation_for_constant_coefficients(dim, n, model):
+    """Where "complete analogy" has one meaning: a homogeneous soil at a
+    uniform state psi0 (so every lagged conductivity, Dirichlet face value and
+    soil parameter is one constant).  The level-1 operator N_H must then be
+    the same discretisation on the grid of ceil(n/2) cells: equal to the
+    fine operator of that coarser problem applied to any vector, Dirichlet
+    faces included.  A wrong coarse spacing, a restriction that does not
+    preserve constants, or a face conductivity summed instead of averaged
+    breaks it."""
+    kinds = {1: [W.DIRICHLET, W.DIRICHLET],
+             2: [W.DIRICHLET, W.NOFLUX, W.FREE_DRAINAGE, W.DIRICHLET],
+             3: [W.NOFLUX, W.DIRICHLET, W.DIRICHLET, W.NOFLUX, W.FREE_DRAINAGE, W.DIRICHLET]}[dim]
+    nc = tuple((k + 1) // 2 for k in n)
+    psi0, dt = -0.3, 120.0
+
+    def build(shape):
+        p = W.random_problem(dim, shape, model, 21, bc_kinds=kinds, coarsest_max_n=2)
+        p["bc"]["value"] = [psi0 if k == W.DIRICHLET else 0.0 for k in p["bc"]["kind"]]
+        p["psi0"] = np.full(len(p["psi0"]), psi0)
+        o = Oracle(p)
+        o.prepare(dt, 1)
+        return o
+
+    fine, coarse = build(n), build(nc)
+    assert fine.nlevels >= 2 and fine.level_n(1)[:dim] == nc
+    assert np.max(np.abs(fine.Kc(1) - coarse.Kc(0))) <= 1e-15 * np.max(coarse.Kc(0))
+    M_H, M_c = fine.dense_M(1), coarse.dense_M(0)
+    assert np.max(np.abs(M_H - M_c)) <= 1e-13 * np.max(np.abs(M_c))
+    rng = np.random.default_rng(5)
+    x = psi0 + 0.2 * rng.standard_normal(coarse.ncell())
+    got, want = fine.apply_N(x, lev=1), coarse.apply_N(x)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+# ---------------------------------------------------------------------------
 # The implicit step: FAS-NGS reaches the plain solution of N_h(psi) = g_h.
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("dim,n", [(1, (9,)), (2, (5, 7)), (3, (4, 3, 5))])
