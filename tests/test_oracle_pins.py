@@ -500,6 +500,46 @@ def test_fas_solution_equals_dense_newton(dim, n, model):
     assert np.max(np.abs(psi_fas - psi_dn)) <= 1e-10 * max(1.0, np.max(np.abs(psi_dn)))
 
 
+@pytest.mark.parametrize("dim,n", [(1, (9,)), (2, (5, 7)), (3, (4, 3, 5))])
+@pytest.mark.parametrize("model", [W.HAVERKAMP, W.GARDNER, W.VANGENUCHTEN])
+def test_error_bound_of_the_defect(dim, n, model):
+    """The step's error bound (reading R14).  N(psi) - N(psi*) = D (psi - psi*)
+    + M (psi - psi*) exactly, D_i the secant slope of a theta + S + xi psi
+    between psi_i and psi*_i; M has non-positive off-diagonals and
+    non-negative row sums (Prop. 3.1), so at the cell i of the largest error
+    |r_i| >= D_i |e_i|.  That inequality holds for every iterate of the cycle;
+    the reported bound ||r|| / min_i (a theta'(psi_i) + S'(psi_i) + xi), its
+    point-slope form, holds on these iterates too.  psi* is the dense Newton
+    solution; iterates within 1e-8 of it are not compared (its own accuracy)."""
+    kinds = [W.NOFLUX] * (2 * dim - 2) + [W.FREE_DRAINAGE, W.DIRICHLET]
+    compared = 0
+    for seed in (70, 71):
+        p = W.random_problem(dim, n, model, seed, bc_kinds=kinds, hetero=True, sink=True, tol=1e-13,
+                             coarsest_max_n=2)
+        o = Oracle(p)
+        o.prepare(p["dt"], 1)
+        a, xi = o.a, p["opts"]["xi"]
+        ex, res = dense_newton(o, p["psi0"])
+        assert res <= 1e-13
+        psi = np.array(p["psi0"], dtype=np.float64)
+        for _ in range(6):
+            e = psi - ex
+            if np.max(np.abs(e)) < 1e-8:
+                break
+            r, _ = o.residual(psi)
+            i = int(np.argmax(np.abs(e)))
+            th_i, S_i = o.soil(i, psi[i])[0], o.sink(i, psi[i])[0]
+            th_x, S_x = o.soil(i, ex[i])[0], o.sink(i, ex[i])[0]
+            D_sec = (a * (th_i - th_x) + (S_i - S_x)) / (psi[i] - ex[i]) + xi
+            assert abs(e[i]) * D_sec <= abs(r[i]) * (1 + 1e-6), (abs(e[i]) * D_sec, abs(r[i]))
+            D_pt = np.array([a * o.soil(j, x)[1] + o.sink(j, x)[1] + xi for j, x in enumerate(psi)])
+            if D_pt.min() > 0:
+                assert np.max(np.abs(e)) <= np.max(np.abs(r)) / D_pt.min()
+            compared += 1
+            psi = o.vcycle(psi)
+    assert compared >= 2
+
+
 def test_fas_fixed_point_independent_of_hierarchy():
     """The converged FAS answer does not depend on restriction, prolongation
     or coarse operators: V-cycles, plain NGS and both orderings agree."""
