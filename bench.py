@@ -209,8 +209,41 @@ def columns_bench(stream, steps=10):
            "status": R.STATUS_NAMES[st], "all_columns_ok": bool(np.all(stt["status"] == R.RICH_OK)),
            "column_steps_per_s": len(probs) * steps / (ms * 1e-3),
            "cell_updates_per_s": float(np.sum(stt["updates"])) / (ms * 1e-3), "ms": ms}
+    psi = cols.state()
+    sample = {k: cols.column(psi, k).copy() for k in range(0, len(probs), COLUMN_CPU_EVERY)}
     cols.close()
-    return out
+    return out, sample
+
+
+COLUMN_CPU_EVERY = 64     # the CPU leg runs every 64th column: 64 columns across the length mix
+
+
+def columns_cpu(sample, steps):
+    """The oracle on the sampled columns of the batched-column workload: the
+    same 1 + steps BDF1 steps (the first untimed, as on the GPU), single
+    thread; column-steps/s over the timed steps, and the largest distance of
+    the GPU's mixed-precision states to the oracle's FP64 ones."""
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_2606_04292_gb300 import workloads as W
+    probs = W.columns()
+    total = 0.0
+    cells = 0
+    dmax = 0.0
+    failed = 0
+    for k, psi_gpu in sample.items():
+        o = Oracle(probs[k])
+        failed += o.step()[0] != 0
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            failed += o.step()[0] != 0
+        total += time.perf_counter() - t0
+        cells += len(psi_gpu)
+        dmax = max(dmax, float(np.max(np.abs(o.state() - psi_gpu))))
+    return {"cores": 1, "columns": len(sample), "steps": steps, "cells": cells, "failed_steps": int(failed),
+            "column_steps_per_s": len(sample) * steps / total, "cell_steps_per_s": cells * steps / total,
+            "max_abs_dpsi_gpu_vs_oracle": dmax,
+            "sample": f"every {COLUMN_CPU_EVERY}th column ({len(sample)} columns, {cells} cells), {steps} timed steps"}
 
 
 def serving_bench(nreq=24, max_steps=20):
@@ -229,6 +262,33 @@ def serving_bench(nreq=24, max_steps=20):
         out[label] = {k: summary[k] for k in ("completed", "makespan_s", "solves_per_s", "cell_updates_per_s",
                                               "p50_latency_s", "p99_latency_s")}
     return out
+
+
+SERVING_CPU_REQUESTS = 6   # the CPU leg times the first step of this many requests of the trace
+
+
+def serving_cpu(nreq=24, max_steps=20):
+    """The oracle on the served trace, bounded: the first step of each of the
+    first SERVING_CPU_REQUESTS requests (single thread), its time as measured;
+    the trace's serial solve rate at those per-step times is an estimate
+    (every step of a request is taken to cost its first step)."""
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_2606_04292_gb300 import workloads as W
+    trace = W.serving_trace(rate=200.0, seconds=60.0, seed=6, sizes2d=(129, 257), sizes3d=(65,),
+                            max_requests=nreq)
+    per_step, names, failed = [], [], 0
+    for p in trace[:SERVING_CPU_REQUESTS]:
+        o = Oracle(p)
+        t0 = time.perf_counter()
+        failed += o.step()[0] != 0
+        per_step.append(time.perf_counter() - t0)
+        names.append(f"{p['dim']}D {p['n'][0]}^{p['dim']}")
+    steps = [min(p["nsteps"], max_steps) for p in trace[:SERVING_CPU_REQUESTS]]
+    solve_s = float(np.sum(np.array(per_step) * np.array(steps)))
+    return {"cores": 1, "requests": names, "s_per_step": per_step, "failed_steps": int(failed),
+            "serial_solves_per_s_estimate": len(per_step) / solve_s,
+            "sample": f"first step of the first {len(per_step)} of {len(trace)} requests"}
 
 
 def gardner_bench(stream):
@@ -553,9 +613,9 @@ def main():
         gf.close()
         gm.close()
 
-    columns = None
+    columns = csample = None
     if rank == 0 and not args.no_columns:
-        columns = columns_bench(stream)
+        columns, csample = columns_bench(stream)
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_bench()
@@ -591,6 +651,10 @@ def main():
             layered["cpu_oracle"] = layered_cpu(lstates)
         if table3 is not None:
             table3["cpu_oracle"] = table3_cpu()
+        if columns is not None:
+            columns["cpu_oracle"] = columns_cpu(csample, columns["steps"])
+        if serving is not None:
+            serving["cpu_oracle"] = serving_cpu()
 
     if rank == 0:
         line = {
