@@ -2,8 +2,9 @@
 """Benchmark: NGS-FAS Richards solver on the 3D drainage workload (256^3).
 
 One bench step is one implicit BDF2 time step of the whole path (per-step
-preparation, FP64 defect correction around FP32 FAS V-cycles with red-black
-NGS, stop test in FP64, history shift) on 256^3 cells of heterogeneous van
+preparation, an outer defect correction of the FP64 state in float-float
+arithmetic around FP32 FAS cycles with red-black NGS, the stop test on that
+defect, water balance, history shift) on 256^3 cells of heterogeneous van
 Genuchten soil draining from saturation.  Inputs (16.8 M cells, 134 MB per
 FP64 array) are larger than L2, so no flush is needed between steps.
 
@@ -30,7 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "NGS cell-updates/s and time-steps/s at 256^3; p50/p99 solve latency, vs FP64 plain @1e-8"
 UNIT = "cell-updates/s"
 WORKLOAD = "3D drainage 256^3, heterogeneous VG (lognormal Ks, sigma_lnK=1, corr 8 cells; alpha U[2,5], n U[1.5,2.5]), " \
-           "psi0=0, free drainage bottom, BDF2 dt=300 s, mixed FP32 inner / FP64 outer, tol 1e-8"
+           "psi0=0, free drainage bottom, BDF2 dt=300 s, mixed: FP32 inner cycles, float-float outer defect " \
+           "on the FP64 state, tol 1e-8"
 
 # Algorithmic bytes per unit for the kernels that can dominate (per cell the
 # launch covers; a half-sweep covers the cells of one colour).  The NGS
@@ -660,7 +662,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / float-float (f32x2) outer, f64 state", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": N, "levels": gs.nlevels, "l2": "inputs larger than L2",
                        "cycle": f"{'W' if args.gamma == 2 else 'V'}({prob['opts']['nu1']},{prob['opts']['nu2']})",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -425,7 +425,7 @@ richards_status richards_columns_run(richards_columns *batch, double dt, int nst
 richards_status richards_columns_get_state(richards_columns *batch, double *psi, int on_device);
 
 /* Per column (host arrays of ncol entries, each nullable): status of the
-   last run (RICH_OK / ENOCONV / ENAN), FP32 inner cycles, FP64 outer
+   last run (RICH_OK / ENOCONV / ENAN), FP32 inner cycles, outer (float-float defect)
    iterations, last tau_eff ||g - N(psi)||_inf, NGS point updates. */
 richards_status richards_columns_stats(richards_columns *batch, int *status, int *cycles, int *outer,
                                        double *resid, long long *updates);

@@ -261,7 +261,7 @@ __device__ __forceinline__ void dlaw_f(float psi0, float x, float p1, float p2, 
 
 // ---------------------------------------------------------------------------
 // Fast single-precision pieces for the inner correction problem.  The inner
-// FP32 solve only has to be accurate to ~1e-5 relative (the FP64 outer
+// FP32 solve only has to be accurate to ~1e-5 relative (the float-float outer
 // defect correction removes the rest), but the increments must stay free of
 // cancellation: log1p and expm1 of small arguments come from their Taylor
 // series (truncation below 1e-10 relative for |x| < 1/32), larger arguments
