@@ -371,6 +371,72 @@ def test_lemma31_bounds(seed):
     assert inv_norm <= 1.0 / (al * mu.min() + be * lam_low) * (1 + 1e-12)
 
 
+def _changed_after_one_sweep(n, ordering, cell, dim):
+    kinds = [W.NOFLUX] * (2 * dim - 2) + [W.FREE_DRAINAGE, W.DIRICHLET]
+    # a long step, so that the coupling dominates the storage term and a
+    # perturbation decays slowly from cell to cell
+    p = W.random_problem(dim, n, W.VANGENUCHTEN, 41, hetero=True, ordering=ordering, newton_iters=0, dt=1e4,
+                         tol=1e-16, max_cycles=300, coarsest_max_n=2, bc_kinds=kinds)
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    star, st, info = o.solve_current(p["psi0"])
+    floor = np.max(np.abs(o.sweep(star) - star))        # what a sweep moves the converged state
+    assert floor <= 1e-12
+    psi = star.copy()
+    psi[cell] += 0.05
+    new = o.sweep(psi)
+    return set(np.flatnonzero(np.abs(new - psi) > 1e-10).tolist())
+
+
+def _expected_changes(n, order, cell):
+    """Cells that a Gauss-Seidel sweep in the given order changes when only
+    `cell` is off the solution: a visited cell lands off the solution iff a
+    neighbour is off it at that moment (else its point solve returns the
+    solution), and it changes iff it was off before or lands off now."""
+    dim = len(n)
+    off = np.zeros(int(np.prod(n)), dtype=bool)
+    off[cell] = True
+    changed = set()
+    for c in order:
+        ii = np.unravel_index(c, n[::-1])[::-1]          # x fastest
+        nb = []
+        for a in range(dim):
+            for s in (-1, 1):
+                jj = list(ii)
+                jj[a] += s
+                if 0 <= jj[a] < n[a]:
+                    nb.append(int(np.ravel_multi_index(tuple(jj[::-1]), n[::-1])))
+        now = any(off[j] for j in nb)
+        if off[c] or now:
+            changed.add(int(c))
+        off[c] = now
+    return changed
+
+
+SWEEP_CASES = [((9,), [4, 5, 8]), ((5, 4), [7, 12, 19]), ((3, 4, 3), [17, 22, 35])]
+
+
+@pytest.mark.parametrize("n,cells", SWEEP_CASES)
+def test_sweep_orders_by_where_a_perturbation_travels(n, cells):
+    """Which cells one sweep changes, starting from the solution with one
+    cell perturbed, fixes the order of the sweep: lexicographic, ascending
+    (Section 3.1), and red-black with the colour of cell 0 first.  A reversed
+    or recoloured order moves the perturbation elsewhere."""
+    N = int(np.prod(n))
+    lex = list(range(N))
+    idx = np.arange(N)
+    coords = np.stack(np.unravel_index(idx, n[::-1])[::-1])
+    colour = coords.sum(axis=0) % 2
+    rb = list(idx[colour == 0]) + list(idx[colour == 1])
+    for cell in cells:
+        assert _changed_after_one_sweep(n, 0, cell, len(n)) == _expected_changes(n, lex, cell), ("lex", cell)
+        assert _changed_after_one_sweep(n, 1, cell, len(n)) == _expected_changes(n, rb, cell), ("rb", cell)
+    # the rule tells these orders apart on these cells (it cannot tell which
+    # axis runs fastest: monotone paths reach the same cells either way)
+    assert any(_expected_changes(n, lex[::-1], c) != _expected_changes(n, lex, c) for c in cells)
+    assert all(_expected_changes(n, rb, c) != _expected_changes(n, lex, c) for c in cells)
+
+
 @pytest.mark.parametrize("ordering", [0, 1])
 @pytest.mark.parametrize("model", [W.HAVERKAMP, W.VANGENUCHTEN])
 def test_theorem31_contraction_per_sweep(ordering, model):
