@@ -249,6 +249,54 @@ def test_hydrostatic_state_is_exact_steady_state(dim, model):
     assert np.max(np.abs(o.state() - psi)) <= 1e-12
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_hydrostatic_state_with_face_fields_and_masks(dim):
+    """The hydrostatic state psi = H - z stays exact when the bottom head is
+    given per face cell (value_field) and the top is Dirichlet only where a
+    mask is set (no-flux elsewhere): pins the face indexing of value_field and
+    mask_field (lexicographic over the other axes, first fastest)."""
+    n = {2: (6, 7), 3: (4, 5, 6)}[dim]
+    kinds = [W.NOFLUX] * (2 * dim - 2) + [W.DIRICHLET, W.DIRICHLET]
+    p = W.random_problem(dim, n, W.VANGENUCHTEN, 14, bc_kinds=kinds, hetero=True)
+    H, Lz = 0.3, p["L"][dim - 1]
+    nface = int(np.prod(n[:-1]))
+    rng = np.random.default_rng(3)
+    p["bc"]["value_field"][2 * dim - 2] = np.full(nface, H)            # bottom: z = 0
+    p["bc"]["value"][2 * dim - 1] = H - Lz
+    mask = (rng.uniform(size=nface) < 0.5).astype(np.uint8)
+    mask[0] = 1
+    p["bc"]["mask_field"][2 * dim - 1] = mask
+    nn = p["n"]
+    hz = Lz / nn[dim - 1]
+    idx = np.arange(nn[0] * nn[1] * nn[2])
+    iz = [idx % nn[0], (idx // nn[0]) % nn[1], idx // (nn[0] * nn[1])][dim - 1]
+    psi = H - (iz + 0.5) * hz
+    p["psi0"] = psi
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    _, nrm = o.residual(psi)
+    assert nrm <= 1e-13 * np.max(np.abs(o.g()))
+    # a bottom head off by 0.1 m in one face cell leaves a defect in exactly the cell above it
+    vf = np.full(nface, H)
+    k = nface // 2 + 1
+    vf[k] = H + 0.1
+    p["bc"]["value_field"][2 * dim - 2] = vf
+    o2 = Oracle(p)
+    o2.prepare(p["dt"], 1)
+    r, nrm2 = o2.residual(psi)
+    big = np.flatnonzero(np.abs(r) > 1e-9 * np.max(np.abs(o2.g())))
+    assert big.tolist() == [k]                     # face cell k lies under fine cell k of the bottom layer
+    # a top head off by 0.1 m leaves defects in exactly the top cells whose mask is set
+    p["bc"]["value_field"][2 * dim - 2] = np.full(nface, H)
+    p["bc"]["value"][2 * dim - 1] = H - Lz + 0.1
+    o3 = Oracle(p)
+    o3.prepare(p["dt"], 1)
+    r, _ = o3.residual(psi)
+    big = np.flatnonzero(np.abs(r) > 1e-9 * np.max(np.abs(o3.g())))
+    top0 = len(psi) - nface
+    assert big.tolist() == (top0 + np.flatnonzero(mask)).tolist()
+
+
 @pytest.mark.parametrize("dim", [1, 2])
 def test_saturated_linear_head_is_exact(dim):
     """Saturated (psi >= 0, K = Ks) flow between two Dirichlet heads: the
