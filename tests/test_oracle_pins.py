@@ -351,6 +351,38 @@ def test_constant_flux_column_is_exact(dim):
     assert nrm2 > 1e6 * nrm
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_flux_face_field_column_is_exact(dim):
+    """The unit-gradient column with its inflow K(psi0) given per top face
+    cell (value_field of a FLUX face) has zero defect; raising one face
+    cell's inflow by q leaves the defect g - N = q/h (the inflow enters g) in
+    exactly the top cell under it."""
+    n = {2: (5, 6), 3: (3, 4, 5)}[dim]
+    kinds = [W.NOFLUX] * (2 * dim - 2) + [W.FREE_DRAINAGE, W.FLUX]
+    p = W.random_problem(dim, n, W.HAVERKAMP, 15, bc_kinds=kinds)
+    psi0 = -0.4
+    _, _, K0 = Oracle(p).soil(0, psi0)
+    nface = int(np.prod(n[:-1]))
+    p["bc"]["value_field"][2 * dim - 1] = np.full(nface, K0)
+    p["psi0"] = np.full(len(p["psi0"]), psi0)
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    _, nrm = o.residual(p["psi0"])
+    assert nrm <= 1e-13 * np.max(np.abs(o.g()))
+    k, q = nface - 2, 3.0 * K0
+    vf = np.full(nface, K0)
+    vf[k] += q
+    p["bc"]["value_field"][2 * dim - 1] = vf
+    o2 = Oracle(p)
+    o2.prepare(p["dt"], 1)
+    r, _ = o2.residual(p["psi0"])
+    hz = p["L"][dim - 1] / n[-1]
+    cell = len(r) - nface + k
+    assert abs(r[cell] - q / hz) <= 1e-12 * q / hz
+    r[cell] = 0.0
+    assert np.max(np.abs(r)) <= 1e-13 * np.max(np.abs(o2.g()))
+
+
 @pytest.mark.parametrize("scheme", [1, 2])
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_discrete_mass_balance_identity(scheme, dim):
