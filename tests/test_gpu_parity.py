@@ -369,6 +369,20 @@ def test_mixed_precision_within_stated_bound(mk, predictor):
         prev, cur = cur, psi_m
 
 
+def _face_field_problem():
+    """3-d problem whose boundary data are per face cell: inflow value_field on
+    the top (FLUX), a Dirichlet side with a mask and a head per face cell, free
+    drainage at the bottom, a sink."""
+    p = W.random_problem(3, (12, 10, 14), W.VANGENUCHTEN, 8, hetero=True, sink=True,
+                         bc_kinds=[W.DIRICHLET, W.NOFLUX, W.NOFLUX, W.NOFLUX, W.FREE_DRAINAGE, W.FLUX])
+    rng = np.random.default_rng(9)
+    n0, n1, n2 = p["n"]
+    p["bc"]["value_field"][5] = rng.uniform(0.0, 2e-6, n0 * n1)          # top: z-face cells over (x, y)
+    p["bc"]["value_field"][0] = rng.uniform(-1.5, -0.2, n1 * n2)         # x-low: face cells over (y, z)
+    p["bc"]["mask_field"][0] = (rng.uniform(size=n1 * n2) < 0.6).astype(np.uint8)
+    return p
+
+
 WATER_PROBLEMS = [
     ("1d_vg_sink_flux_xi", lambda: W.with_opts(W.random_problem(1, 64, W.VANGENUCHTEN, 2, bc_kinds=[W.FREE_DRAINAGE,
                                                                                                   W.FLUX],
@@ -380,6 +394,7 @@ WATER_PROBLEMS = [
     ("3d_layers_3mat_sink", lambda: layered(3, (12, 10, 11), W.GARDNER, 8, "layers", sink=True, scheme=2,
                                             bc_kinds=[W.NOFLUX, W.FLUX, W.DIRICHLET, W.NOFLUX, W.FREE_DRAINAGE,
                                                       W.DIRICHLET])),
+    ("3d_face_fields_sink", _face_field_problem),
 ]
 
 
@@ -701,3 +716,14 @@ def test_celia_column_lexicographic_full_run():
         assert st == R.RICH_OK and sto == ORC_OK
         assert info["cycles"] == info_o["cycles"], k
     assert rel(gs.state(), orc.state()) <= STEP_RTOL
+
+
+def test_face_fields_fp64_steps_match_oracle():
+    prob = _face_field_problem()
+    gs, orc, p = pair(prob, tol=1e-11, max_cycles=200)
+    for k in range(3):
+        st, info = gs.step(p["dt"], p["scheme"], check=False)
+        sto, info_o = orc.step(p["dt"], p["scheme"])
+        assert st == sto == R.RICH_OK, (k, info, info_o)
+        assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
+        assert abs(info["mass_defect"]) <= 1e-9
