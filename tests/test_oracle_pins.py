@@ -383,6 +383,47 @@ def test_flux_face_field_column_is_exact(dim):
     assert np.max(np.abs(r)) <= 1e-13 * np.max(np.abs(o2.g()))
 
 
+def test_gardner_2d_steady_state_converges_to_the_kirchhoff_solution():
+    """Section 4.2's 2D Gardner problem has a closed-form steady state.  With
+    K = Ks e^{alpha h} and u = e^{alpha h}, steady flow div(K grad(h + z)) = 0
+    (z up) becomes the linear equation lap u + alpha du/dz = 0.  With
+    u = e^{-10 alpha} =: u_r on the sides and the bottom and
+    u = u_r + (1 - u_r) sin(pi x / L) on the top (the paper's top head),
+    separation of variables gives
+        u = u_r + (1 - u_r) sin(pi x / L) e^{alpha (L - z) / 2} sinh(beta z) / sinh(beta L),
+        beta = sqrt(alpha^2 / 4 + pi^2 / L^2).
+    Long implicit steps with the lagged conductivity are a Picard iteration
+    whose fixed point is the discrete steady state; it approaches h = ln(u) /
+    alpha at second order in the cell size (a wrong gravity sign, Dirichlet
+    distance or face average stalls the error at O(1) or O(h))."""
+    alpha, L = 0.164, 10.0
+    ur = math.exp(-10.0 * alpha)
+    beta = math.sqrt(alpha ** 2 / 4.0 + (math.pi / L) ** 2)
+    dt = 1e9
+    errs = []
+    for n in (8, 16, 32):
+        p = W.gardner_2d(n=n, dt=dt, nsteps=1, tol=1e-14 * dt, max_cycles=400)
+        assert p["soil"]["p1"] == alpha and p["L"][:2] == (L, L)
+        c = (np.arange(n) + 0.5) * (L / n)
+        X, Z = np.meshgrid(c, c)                      # [z, x]: x fastest when flattened
+        u = ur + (1.0 - ur) * np.sin(np.pi * X / L) * np.exp(alpha * (L - Z) / 2.0) * np.sinh(beta * Z) \
+            / math.sinh(beta * L)
+        exact = (np.log(u) / alpha).reshape(-1)
+        o = Oracle(p)
+        last = o.state()
+        for _ in range(80):
+            assert o.step()[0] == ORC_OK
+            cur = o.state()
+            moved = np.max(np.abs(cur - last))
+            last = cur
+            if moved < 1e-11:
+                break
+        assert moved < 1e-11
+        errs.append(np.max(np.abs(cur - exact)))
+    assert errs[0] < 0.1
+    assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.3, errs
+
+
 @pytest.mark.parametrize("scheme", [1, 2])
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_discrete_mass_balance_identity(scheme, dim):
