@@ -383,6 +383,42 @@ def test_flux_face_field_column_is_exact(dim):
     assert np.max(np.abs(r)) <= 1e-13 * np.max(np.abs(o2.g()))
 
 
+@pytest.mark.parametrize("model", [W.HAVERKAMP, W.GARDNER, W.VANGENUCHTEN])
+def test_steady_flux_column_converges_to_the_ode_solution(model):
+    """A column with a Dirichlet head h_b at the bottom and a prescribed inflow
+    q at the top settles to the steady profile of K(h) (dh/dz + 1) = q, the
+    ODE dh/dz = q / K(h) - 1 from h(0) = h_b (integrated here by scipy's
+    DOP853 to 1e-13, with the law K(h) pinned by the paper's calibration).
+    Time steps of 1e5 s reach the discrete steady state; it converges to the
+    ODE's values at the cell centres at second order (error ratio -> 4 under
+    halving of the cells)."""
+    solve_ivp = pytest.importorskip("scipy.integrate").solve_ivp
+    dt, hb = 1e5, -1.0
+    errs = []
+    for n in (32, 64, 128, 256):
+        p = W.random_problem(1, (n,), model, 16, bc_kinds=[W.DIRICHLET, W.FLUX], dt=dt,
+                             tol=1e-14 * dt, max_cycles=400)
+        q = 3.0 * Oracle(p).soil(0, hb)[2]
+        p["bc"]["value"] = [hb, q] + [0.0] * 4
+        p["psi0"] = np.full(n, hb)
+        o = Oracle(p)
+        zc = (np.arange(n) + 0.5) / n * p["L"][0]
+        ode = solve_ivp(lambda z, h: [q / o.soil(0, h[0])[2] - 1.0], (0.0, zc[-1]), [hb], t_eval=zc,
+                        rtol=1e-13, atol=1e-15, method="DOP853")
+        last = o.state()
+        for _ in range(200):
+            assert o.step()[0] == ORC_OK
+            cur = o.state()
+            moved = np.max(np.abs(cur - last))
+            last = cur
+            if moved < 1e-12:
+                break
+        assert moved < 1e-12
+        errs.append(np.max(np.abs(cur - ode.y[0])))
+    ratios = [errs[k] / errs[k + 1] for k in range(3)]
+    assert errs[0] < 2e-4 and all(r > 3.0 for r in ratios[1:]) and ratios[-1] > 3.6, (errs, ratios)
+
+
 def test_gardner_2d_steady_state_converges_to_the_kirchhoff_solution():
     """Section 4.2's 2D Gardner problem has a closed-form steady state.  With
     K = Ks e^{alpha h} and u = e^{alpha h}, steady flow div(K grad(h + z)) = 0
