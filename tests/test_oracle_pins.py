@@ -460,6 +460,44 @@ def test_gardner_2d_steady_state_converges_to_the_kirchhoff_solution():
     assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.3, errs
 
 
+def test_gardner_3d_steady_state_converges_to_the_kirchhoff_solution():
+    """The same closed form in three dimensions: top head
+    ln(u_r + (1 - u_r) sin(pi x / L) sin(pi y / L)) / alpha per face cell,
+    -10 m on the other faces, beta = sqrt(alpha^2 / 4 + 2 pi^2 / L^2); the
+    discrete steady state approaches it at second order (pins the second
+    horizontal axis and the face-cell order of a 3-d value field)."""
+    alpha, L, dt = 0.164, 10.0, 1e9
+    ur = math.exp(-10.0 * alpha)
+    beta = math.sqrt(alpha ** 2 / 4.0 + 2.0 * (math.pi / L) ** 2)
+    errs = []
+    for n in (8, 16):
+        p = W.random_problem(3, (n, n, n), W.GARDNER, 0, bc_kinds=[W.DIRICHLET] * 6, L=L, dt=dt,
+                             tol=1e-14 * dt, max_cycles=400)
+        p["soil"] = W._soil(W.GARDNER, 0.1, 0.45, 0.15, p1=alpha)
+        c = (np.arange(n) + 0.5) * (L / n)
+        Y, X = np.meshgrid(c, c, indexing="ij")              # top face cells [y, x], x fastest
+        p["bc"]["value"] = [-10.0] * 6
+        p["bc"]["value_field"][5] = (np.log(ur + (1.0 - ur) * np.sin(np.pi * X / L) * np.sin(np.pi * Y / L))
+                                     / alpha).reshape(-1)
+        p["psi0"] = np.full(n ** 3, -10.0)
+        Z3, Y3, X3 = np.meshgrid(c, c, c, indexing="ij")
+        u = ur + (1.0 - ur) * np.sin(np.pi * X3 / L) * np.sin(np.pi * Y3 / L) * np.exp(alpha * (L - Z3) / 2.0) \
+            * np.sinh(beta * Z3) / math.sinh(beta * L)
+        exact = (np.log(u) / alpha).reshape(-1)
+        o = Oracle(p)
+        last = o.state()
+        for _ in range(80):
+            assert o.step()[0] == ORC_OK
+            cur = o.state()
+            moved = np.max(np.abs(cur - last))
+            last = cur
+            if moved < 1e-11:
+                break
+        assert moved < 1e-11
+        errs.append(np.max(np.abs(cur - exact)))
+    assert errs[0] < 0.2 and errs[0] / errs[1] > 3.2, errs
+
+
 @pytest.mark.parametrize("scheme", [1, 2])
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_discrete_mass_balance_identity(scheme, dim):
