@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--temporal-study", action="store_true",
                     help="add Section 4.1's temporal-convergence study (N=1024 vs N=2048, tau_ref=1e-4; ~4 min)")
     ap.add_argument("--gamma", type=int, default=2, help="1 = V-cycles, 2 = W-cycles")
+    ap.add_argument("--precision", type=int, default=2, choices=[1, 2],
+                    help="outer defect correction of the headline: 2 = FP64, 1 = float-float")
     ap.add_argument("--profile-json", default=None, help="write the per-kernel timing records here")
     return ap.parse_args()
 
@@ -496,7 +498,7 @@ def main():
     from paper_2606_04292_gb300 import richards as R
     from paper_2606_04292_gb300 import workloads as W
 
-    prob = W.drainage_3d(n=args.n, cycle_gamma=args.gamma)
+    prob = W.drainage_3d(n=args.n, cycle_gamma=args.gamma, precision=args.precision)
     N = W.ncells(prob)
     # a stream of its own: the inner cycles are captured into CUDA graphs,
     # which the legacy default stream does not allow

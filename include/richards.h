@@ -113,8 +113,14 @@ typedef struct {
                           update; 0: to round-off
      precision            0 = FP64 throughout; 1 = FP32 inner cycles on the
                           correction equation inside an outer defect
-                          correction (defect, laws and stop test in
-                          float-float arithmetic, ~1e-12 relative)
+                          correction whose lagged K, history, defect, water
+                          balance and stop test run in float-float
+                          arithmetic (laws ~1e-12 relative); 2 = the same
+                          FP32 inner cycles inside an FP64 outer defect
+                          correction: lagged K, history, right side, the
+                          defect that decides the stop test and the water
+                          balance in FP64 (float-float defects only steer
+                          the corrections in between)
      inner_cycles,        mixed mode: FP32 cycles per outer iteration, stop
      inner_rtol, max_outer  early below max(inner_rtol, 0.3 tol / r) x the
                           initial inner defect (r: the outer defect in theta
@@ -163,7 +169,8 @@ typedef struct {
   /* Water balance of the step (conservation, Section 2): tau_eff times
      sum_i V_i (a theta_i - hist_i + S_i + xi (psi_i - psi*_i)) minus the
      net boundary inflow, i.e. the water volume the unconverged residual
-     leaves unaccounted (-tau_eff sum_i V_i r_i), summed in float-float. */
+     leaves unaccounted (-tau_eff sum_i V_i r_i), summed in FP64 (in
+     float-float with precision 1). */
   double mass_defect;
   /* ||N(psi) - g||_inf / min_i (a theta'(psi_i) + S'(psi_i) + xi): bound on
      ||psi - psi_exact||_inf by the diagonal dominance of the Jacobian
@@ -171,9 +178,11 @@ typedef struct {
   double err_bound;
 } richards_step_info;
 
-/* Create a context for one grid; allocates the multigrid hierarchy on the
-   device.  stream: a cudaStream_t (NULL = default stream).  On success
-   *out receives the context.  Errors: EINVAL (bad grid/opts), ENOMEM, ECUDA. */
+/* Create a context for one grid (Section 2: the cell-centred grid of the
+   discrete problem; Section 3.2: its hierarchy of coarser grids); allocates
+   the multigrid hierarchy on the device.  stream: a cudaStream_t (NULL =
+   default stream).  On success *out receives the context.  Errors: EINVAL
+   (bad grid/opts), ENOMEM, ECUDA. */
 richards_status richards_create(const richards_grid *grid, const richards_opts *opts,
                                 void *stream, richards_ctx **out);
 
@@ -349,20 +358,24 @@ int richards_profile_read(richards_ctx *ctx, richards_kernel_stat *out, int max)
 /* ---------------------------------------------------------------------
  * Allocation-free step for small grids.  The paper has no counterpart: this
  * is an interface for callers that may not allocate device memory while
- * they run -- host code that executes during CUDA graph capture, programs
- * whose memory pool already holds all of the device memory, real-time
- * loops that forbid allocator calls, plug-ins that may only touch memory
+ * they run -- programs whose memory pool already holds all of the device
+ * memory, real-time loops that forbid allocator calls (an allocation can
+ * block and synchronise the device), plug-ins that may only touch memory
  * handed to them.
  *
  * One implicit step (same arithmetic as richards_step in FP64 mode) of a
  * grid with at most RICHARDS_NOALLOC_MAX_CELLS cells, run in a single thread
  * block.  psi_n, psi_prev (nullable: BDF1 is used) and psi_out are device
- * arrays of ncell doubles; psi_out may alias psi_n.  In this call the
- * optional soil fields (Ks_field, p1_field, p2_field) and boundary fields
- * (value_field, mask_field) are DEVICE pointers.  Only opts->precision 0 is
- * used (the step is FP64), and the sweeps are red-black whatever
- * opts->ordering says.  info (nullable, host) receives the statistics.
- * stream: a cudaStream_t (NULL = default stream); the call synchronises it.
+ * arrays of ncell doubles; psi_out may alias psi_n or psi_prev (both are
+ * read before anything is written).  In this call the optional soil fields
+ * (Ks_field, p1_field, p2_field) and boundary fields (value_field,
+ * mask_field) are DEVICE pointers.  The soil, boundary and sink parameters
+ * are checked as by richards_set_soil / set_bc / set_sink (fields
+ * excepted).  The step is FP64 and starts from psi_n with V/W-cycles:
+ * opts->precision, ordering (red-black is used), fmg_cycles, predictor,
+ * graphs, sweep_planes, tail_cells and the inner_* and max_outer options
+ * are ignored.  info (nullable, host) receives the statistics.  stream: a
+ * cudaStream_t (NULL = default stream); the call synchronises it.
  *
  * Scratch: one fixed 2 MiB array in the library's device memory (every
  * device that loads the library keeps it until the process exits); nothing
@@ -389,8 +402,9 @@ richards_status richards_step_small_noalloc(const richards_grid *grid, const ric
  * in one persistent launch (a device work queue, longest column first; each
  * thread block runs all time steps of one column with the column's whole
  * multigrid hierarchy in shared memory).  Mixed precision as for
- * richards_step with opts->precision 1: FP64 preparation, defect and stop
- * test, FP32 FAS cycles on the correction equation.
+ * richards_step with opts->precision 1: lagged K, history, defect and stop
+ * test in float-float arithmetic (laws ~1e-12 relative), FP32 FAS cycles on
+ * the correction equation.
  * --------------------------------------------------------------------- */
 #define RICHARDS_COLUMN_MAX_CELLS 2048
 typedef struct richards_columns richards_columns;   /* opaque; owns its device memory */

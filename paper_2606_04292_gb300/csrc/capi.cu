@@ -18,10 +18,12 @@
 
 #include "launch.h"
 #include "richards.h"
+#include "validate.h"
 
 using rich::Level;
 using rich::Phys;
 using rich::Xfer;
+using rich::law_error;
 
 namespace {
 
@@ -694,7 +696,7 @@ void run_cycle32(richards_ctx* c) {
 // they are restricted in FP32 from the finest level's FP32 copies)
 richards_status restrict_coefficients(richards_ctx* c) {
   Prof pr(c, "coefficients", 0, c->L[0].ncell);
-  if (c->opts.precision == 1) {
+  if (c->opts.precision >= 1) {
     for (int f = 0; f < 2 * c->grid.dim; ++f) rich::to_float(c->L[0].kb[f], c->L[0].kbf[f], c->L[0].nface[f], c->s);
     for (int l = 0; l + 1 < c->nlev; ++l) {
       const Level<float> F = view32(c, l), C = view32(c, l + 1);
@@ -727,8 +729,15 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   const Phys<double> P = phys<double>(c);
   HLevel& F = c->L[0];
   Prof pr(c, "prep", 0, F.ncell);
-  const bool cache = c->opts.precision == 1;
-  if (cache)    // mixed mode: float-float arithmetic, theta caches
+  const bool cache = c->opts.precision >= 1;
+  const bool dd = c->opts.precision == 1;   // float-float outer layer; else FP64
+  if (c->opts.precision == 2)   // FP64-outer mixed mode: FP64 laws, FP64 theta caches, FP32 copy of Kc
+    rich::prep_lagged(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
+                      c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, c->soil.model, scheme,
+                      dt, F.Kc, F.Kcf, F.g, F.u, c->th_n_valid ? c->th_n : nullptr,
+                      c->th_nm1_valid ? c->th_nm1 : nullptr, c->th_n_valid ? nullptr : c->th_n,
+                      c->th_nm1_valid ? nullptr : c->th_nm1, c->opts.predictor == 1, c->s);
+  else if (dd)    // mixed mode: float-float arithmetic, theta caches
     rich::prep_lagged_dd(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
                          c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, rich::make_ddphys(P),
                          c->soil.model, scheme, dt, F.Kc, F.Kcf, F.g, F.u, c->th_n_valid ? c->th_n : nullptr,
@@ -737,15 +746,14 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   else
     rich::prep_lagged(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
                       c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, c->soil.model, scheme,
-                      dt, F.Kc,
-                      F.g, F.u, nullptr, nullptr, nullptr, nullptr, c->s);
+                      dt, F.Kc, nullptr, F.g, F.u, nullptr, nullptr, nullptr, nullptr, false, c->s);
   if (cache) {
     c->th_n_valid = true;
     if (scheme == 2) c->th_nm1_valid = true;
   }
   double* kbw[6];
   for (int f = 0; f < 6; ++f) kbw[f] = F.kb[f];
-  if (cache)
+  if (dd)
     rich::prep_rhs_dd(geom(c, 0), c->bcdev, c->het_Ks ? c->Ks : nullptr, c->soil.Ks, c->het_p1 ? F.p1 : nullptr,
                       c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, rich::make_ddphys(P), c->soil.model, F.Kc, F.g, kbw,
                       c->s);
@@ -788,7 +796,8 @@ richards_status read_stats(richards_ctx* c, long long* tail_updates) {
 
 // Water balance and error bound of the iterate about to be accepted (before
 // the history shift); r = tau_eff ||g - N(psi)||_inf.  th_*: theta caches
-// (nullable: evaluated in float-float).
+// (nullable: evaluated).  FP64 laws and sums, except in the float-float
+// mixed mode (precision 1).
 richards_status water_balance(richards_ctx* c, double r, richards_step_info* info, const double* th_new,
                               const double* th_n, const double* th_nm1) {
   if (!info) return RICH_OK;
@@ -802,7 +811,7 @@ richards_status water_balance(richards_ctx* c, double r, richards_step_info* inf
     Prof pr(c, "mass_balance", 0, c->L[0].ncell);
     nb = rich::mass_balance(view64(c, 0), geom(c, 0), c->bcdev, phys<double>(c), phys<float>(c), c->soil.model,
                             c->psi_n, c->psi_nm1, c->scheme_used, c->dt, th_new, th_n,
-                            c->scheme_used == 2 ? th_nm1 : nullptr, c->mass_part, dmin, c->s);
+                            c->scheme_used == 2 ? th_nm1 : nullptr, c->mass_part, dmin, c->opts.precision != 1, c->s);
   }
   TRY(check_launch(c));
   if (nb > MASS_PARTS) return fail(c, RICH_ECUDA, "water balance: too many blocks");
@@ -907,10 +916,14 @@ richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
   return finish_step(c, r, r <= c->opts.tol ? RICH_OK : RICH_ENOCONV);
 }
 
-// Mixed precision: defect r = g - N(psi) in float-float arithmetic (~1e-14
+// Mixed precision: defect r = g - N(psi) in float-float arithmetic (~1e-12
 // relative, no FP64 instruction); FP32 FAS cycles on the correction
 // equation N(psi + delta) - N(psi) = r; psi += delta (FP64); repeat until the
-// stop test on ||r|| holds.
+// stop test on ||r|| holds.  precision 2 (FP64 outer): the system (lagged K,
+// history, right side) is the FP64 one, the float-float defects only steer
+// the corrections, and the defect that decides the stop test -- computed
+// whenever a float-float defect passes it, or the outer limit is reached --
+// is FP64; it also gives theta(psi^{n+1}) to the FP64 history cache.
 richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   const double teff = 1.0 / c->a;
   const int model = c->soil.model;
@@ -923,23 +936,33 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   richards_status st = RICH_OK;
   // theta(psi) from the cache of theta(psi^n) before the first correction,
   // else evaluated and kept in th_cur (theta(psi^{n+1}) once accepted)
-  auto defect = [&](bool cached, double* out) -> richards_status {
+  const bool outer64 = c->opts.precision == 2;
+  auto defect = [&](bool cached, bool fp64, double* out) -> richards_status {
     CK(cudaMemsetAsync(c->scratch, 0, sizeof(unsigned long long), c->s));
-    {
+    // (FP64 outer: only the FP64 defect writes the theta cache)
+    double* th_out = cached || (outer64 && !fp64) ? nullptr : c->th_cur;
+    if (fp64) {
+      Prof pr(c, "outer_residual64", 0, F.ncell);
+      rich::outer_residual64(view64(c, 0), P64, model, F.gf, F.psi0f, F.uf, c->scratch, cached ? c->th_n : nullptr,
+                             th_out, c->s);
+    } else {
       Prof pr(c, "outer_residual", 0, F.ncell);
       rich::outer_residual_dd(view64(c, 0), P64, Q, model, F.gf, F.psi0f, F.uf, c->scratch,
-                              cached ? c->th_n : nullptr, cached ? nullptr : c->th_cur, c->s);
+                              cached ? c->th_n : nullptr, th_out, c->s);
     }
     TRY(check_launch(c));
     double nrm;
-    TRY(read_norm(c, 0, &nrm, true));
+    TRY(read_norm(c, 0, &nrm, !fp64));
     *out = teff * nrm;
     return RICH_OK;
   };
   // with the predictor (BDF2 steps) the iteration starts at psi*, not psi^n
   const bool predicted = c->opts.predictor == 1 && c->scheme_used == 2;
   for (;;) {
-    TRY(defect(outer == 0 && !predicted, &r));
+    const bool cached = outer == 0 && !predicted;
+    TRY(defect(cached, false, &r));
+    if (outer64 && !std::isnan(r) && (!(r > c->opts.tol) || outer >= c->opts.max_outer))
+      TRY(defect(cached, true, &r));     // the FP64 defect decides
     if (outer == 0) r0 = r;
     if (!(r > c->opts.tol) || std::isnan(r)) break;
     if (outer >= c->opts.max_outer) { st = RICH_ENOCONV; break; }
@@ -1033,7 +1056,7 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
   const richards_opts& o = *opts;
   if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max_sweeps < 1 || o.max_cycles < 0 || o.coarsest_max_n < 1 ||
       !(o.tol > 0.0) || o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
-      (o.ordering != 0 && o.ordering != 1) || (o.precision != 0 && o.precision != 1) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
+      (o.ordering != 0 && o.ordering != 1) || (o.precision < 0 || o.precision > 2) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
       o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0 || o.cycle_gamma < 1 || o.cycle_gamma > 3 ||
       o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1) || (o.predictor != 0 && o.predictor != 1) ||
       o.fmg_cycles < 0 || o.fmg_cycles > 16 ||
@@ -1066,7 +1089,7 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
   c->tail_start = c->nlev - 1;
   for (int l = 0; l < c->nlev; ++l)
     if ((long long)c->L[l].n[0] * c->L[l].n[1] * c->L[l].n[2] <= o.tail_cells) { c->tail_start = l; break; }
-  const bool mixed = o.precision == 1;
+  const bool mixed = o.precision >= 1;
   richards_status st = RICH_OK;
   for (int l = 0; l < c->nlev && st == RICH_OK; ++l) {
     HLevel& H = c->L[l];
@@ -1138,23 +1161,6 @@ richards_status richards_level_dims(const richards_ctx* c, int level, int n_out[
   return RICH_OK;
 }
 
-// Validity of one law's parameters (Table 1); p1/p2 given by fields are
-// checked separately.  Returns nullptr or the complaint.
-const char* law_error(int model, double Ks, double ts, double tr, double p1, double p2, double p3, double p4,
-                      bool p1_field, bool p2_field) {
-  const bool ok = model >= 0 && model <= 2 && std::isfinite(Ks) && Ks > 0.0 && std::isfinite(ts) &&
-                  std::isfinite(tr) && tr >= 0.0 && ts > tr;
-  if (!ok) return "invalid soil: need a known law, Ks > 0, theta_s > theta_r >= 0";
-  auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
-  if (model == RICH_HAVERKAMP && !(pos(p3) && pos(p4) && (p1_field || pos(p1)) && (p2_field || pos(p2))))
-    return "Haverkamp needs alpha, beta, A, gamma > 0";
-  if (model == RICH_GARDNER && !(p1_field || pos(p1))) return "Gardner needs alpha > 0";
-  if (model == RICH_VANGENUCHTEN &&
-      !((p1_field || pos(p1)) && (p2_field || (std::isfinite(p2) && p2 > 1.0)) && std::isfinite(p3)))
-    return "van Genuchten needs alpha > 0, n > 1, finite l";
-  return nullptr;
-}
-
 richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
   if (!c || !s) return RICH_EINVAL;
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
@@ -1181,7 +1187,7 @@ richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
   c->het_Ks = s->Ks_field != nullptr;
   c->het_p1 = s->p1_field != nullptr;
   c->het_p2 = s->p2_field != nullptr;
-  const bool mixed = c->opts.precision == 1;
+  const bool mixed = c->opts.precision >= 1;
   if (c->het_Ks) {
     if (!c->Ks) TRY(dalloc(c, &c->Ks, N));
     CK(cudaMemcpyAsync(c->Ks, s->Ks_field, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
@@ -1266,7 +1272,7 @@ richards_status richards_set_materials(richards_ctx* c, const richards_material*
   }
   // per-level arrays: material index, and p1, p2 (and the fine Ks) of each
   // cell's material, not restricted
-  const bool mixed = c->opts.precision == 1;
+  const bool mixed = c->opts.precision >= 1;
   if (!c->Ks) TRY(dalloc(c, &c->Ks, N));
   std::vector<double> hKs(N);
   for (long long i = 0; i < N; ++i) hKs[i] = mats[index[i]].Ks;
@@ -1331,7 +1337,7 @@ richards_status richards_set_materials(richards_ctx* c, const richards_material*
 
 static richards_status refresh_sink(richards_ctx* c) {
   if (!c->sink.enabled || !c->bc_set) return RICH_OK;
-  const bool mixed = c->opts.precision == 1;
+  const bool mixed = c->opts.precision >= 1;
   for (int l = 0; l < c->nlev; ++l) {
     HLevel& H = c->L[l];
     if (!H.smax) TRY(dalloc(c, &H.smax, H.ncell));
@@ -1352,14 +1358,7 @@ richards_status richards_set_sink(richards_ctx* c, const richards_sink* k) {
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
   cudaStreamSynchronize(c->s);
   graphs_reset(c);
-  if (k->enabled) {
-    const double v[] = {k->Tp, k->root_depth, k->root_decay, k->h1, k->h2, k->h3, k->h4};
-    for (double x : v)
-      if (!std::isfinite(x)) return fail(c, RICH_EINVAL, "non-finite sink parameter");
-    if (!(k->h4 < k->h3 && k->h3 <= k->h2 && k->h2 < k->h1) || !(k->Tp >= 0.0) || !(k->root_decay > 0.0) ||
-        !(k->root_depth > 0.0))
-      return fail(c, RICH_EINVAL, "sink needs h4 < h3 <= h2 < h1, Tp >= 0, root depth and decay > 0");
-  }
+  if (const char* e = rich::sink_error(*k)) return fail(c, RICH_EINVAL, e);
   c->sink = *k;
   return refresh_sink(c);
 }
@@ -1371,14 +1370,10 @@ richards_status richards_set_bc(richards_ctx* c, const richards_bc* b) {
   graphs_reset(c);
   const int dim = c->grid.dim;
   const HLevel& F = c->L[0];
-  for (int f = 0; f < 2 * dim; ++f) {
-    if (b->kind[f] < 0 || b->kind[f] > 3) return fail(c, RICH_EINVAL, "unknown boundary kind");
-    if (b->kind[f] == RICH_BC_FREE_DRAINAGE && f != 2 * (dim - 1))
-      return fail(c, RICH_EINVAL, "free drainage is only defined on the bottom face");
-    if (!std::isfinite(b->value[f])) return fail(c, RICH_EINVAL, "non-finite boundary value");
+  if (const char* e = rich::bc_error(*b, dim)) return fail(c, RICH_EINVAL, e);
+  for (int f = 0; f < 2 * dim; ++f)
     if (b->value_field[f] && !finite_all(b->value_field[f], F.nface[f]))
       return fail(c, RICH_EINVAL, "non-finite boundary field");
-  }
   // release tables and fields of an earlier call
   cudaStreamSynchronize(c->s);
   for (void* p : c->bc_allocs) cudaFree(p);
@@ -1426,7 +1421,7 @@ richards_status richards_set_bc(richards_ctx* c, const richards_bc* b) {
       if (c->het_p1) rich::restrict64(Fv, Cv, xfer64(c, l), c->L[l].p1, nullptr, c->L[l + 1].p1, nullptr, c->s);
       if (c->het_p2) rich::restrict64(Fv, Cv, xfer64(c, l), c->L[l].p2, nullptr, c->L[l + 1].p2, nullptr, c->s);
     }
-    if (c->opts.precision == 1)
+    if (c->opts.precision >= 1)
       for (int l = 0; l < c->nlev; ++l) {
         if (c->het_p1) rich::to_float(c->L[l].p1, c->L[l].p1f, c->L[l].ncell, c->s);
         if (c->het_p2) rich::to_float(c->L[l].p2, c->L[l].p2f, c->L[l].ncell, c->s);
@@ -1529,7 +1524,7 @@ static richards_status step_impl(richards_ctx* c, double dt, int scheme, richard
   c->updates_host = 0;
   CK(cudaMemsetAsync(c->scratch + 16, 0, sizeof(unsigned long long), c->s));
   TRY(do_prepare(c, dt, scheme));
-  return c->opts.precision == 1 ? step_mixed(c, info) : step_fp64(c, info);
+  return c->opts.precision >= 1 ? step_mixed(c, info) : step_fp64(c, info);
 }
 
 static richards_status solve_impl(richards_ctx* c, double dt, int nsteps, int scheme, richards_step_info* last) {
@@ -1600,7 +1595,7 @@ long long richards_device_bytes(const richards_grid* grid, const richards_opts* 
   long long n[3] = {grid->n[0], grid->n[1], grid->n[2]};
   for (int a = 0; a < 3; ++a)
     if (n[a] < 1) return -1;
-  const bool mixed = opts->precision == 1;
+  const bool mixed = opts->precision >= 1;
   const long long N = n[0] * n[1] * n[2];
   long long bytes = 2 * N * 8 + (mixed ? 3 * N * 8 : 0) + (soil_fields > 0 ? N * 8 : 0);   // psi^n, psi^{n-1}, caches, Ks
   int levels = 0;

@@ -37,11 +37,14 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
                                                      const double* __restrict__ psinm1, const double* __restrict__ Ks,
                                                      double Ks_s, const double* __restrict__ p1f,
                                                      const double* __restrict__ p2f, const uint8_t* __restrict__ mat,
-                                                     Phys<double> P, int scheme, double dt, double* Kc, double* g,
-                                                     double* u, const double* thn_in, const double* thm_in,
-                                                     double* thn_out, double* thm_out) {
+                                                     Phys<double> P, int scheme, double dt, double* Kc, float* Kcf,
+                                                     double* g, double* u, const double* thn_in,
+                                                     const double* thm_in, double* thn_out, double* thm_out,
+                                                     bool predict) {
   // thn_in / thm_in: theta(psi^n), theta(psi^{n-1}) kept from earlier FP64
-  // evaluations (nullable: evaluate here, and keep them in *_out if given)
+  // evaluations (nullable: evaluate here, and keep them in *_out if given).
+  // Kcf (nullable): an FP32 copy of Kc for the inner cycles of the mixed
+  // mode; predict: the iterate starts at psi* instead of psi^n.
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double p1 = p1f ? p1f[i] : P.p1, p2 = p2f ? p2f[i] : P.p2;
     const double ks = Ks ? Ks[i] : Ks_s;
@@ -71,11 +74,13 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
         ps = 2.0 * pn - pm;
         hist = (4.0 * thn - thm) / (2.0 * dt);
       }
-      Kc[i] = cond_d<ML>(ps, p1, p2, ks, Q);
+      const double K = cond_d<ML>(ps, p1, p2, ks, Q);
+      Kc[i] = K;
+      if (Kcf) Kcf[i] = (float)K;
       g[i] = hist + P.xi * ps;
+      u[i] = predict ? ps : pn;
       return 0;
     });
-    u[i] = pn;
   }
 }
 
@@ -363,6 +368,50 @@ __global__ void __launch_bounds__(128) k_outer_residual_dd(Level<double> L, Phys
   if (threadIdx.x == 0) atomicMax(norm, mx);
 }
 
+// The same defect in FP64 (the FP64-outer mixed mode's accepting defect and
+// stop test): d = g - N(u) with the expression of the FP64 grid residual
+// (eq. Nh-def: a theta(u) + S(u) + xi u + m_ii u - sum_j m_ij u_j), theta in
+// FP64 from th_in when given (u = psi^n), else evaluated and kept in th_out
+// (nullable) for the next step's history.  Hands the FP32 inner problem r32,
+// psi0 and a zero correction like k_outer_residual_dd; ||d||_inf accumulates
+// as FP64 bits.
+template <int MODEL>
+__global__ void __launch_bounds__(256) k_outer_residual64(Level<double> L, Phys<double> P, float* r32, float* psi0f,
+                                                          float* delta, unsigned long long* norm,
+                                                          const double* __restrict__ th_in, double* th_out) {
+  __shared__ unsigned long long sm[33];
+  unsigned long long mx = 0;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y, i2 = blockIdx.z;
+  if (i0 < L.n0) {
+    const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
+    const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && i2 > 0 && i2 < L.n2 - 1;
+    double mii, off;
+    if (yzi) stencil<double, true>(L, i, i0, i1, i2, L.u, mii, off);
+    else stencil<double, false>(L, i, i0, i1, i2, L.u, mii, off);
+    const double ui = L.u[i];
+    double th;
+    if (th_in) {
+      th = th_in[i];
+    } else {
+      const double p1 = L.p1 ? L.p1[i] : P.p1, p2 = L.p2 ? L.p2[i] : P.p2;
+      th = with_law<MODEL>(P, mat_of<MODEL>(L, i), [&](auto law, const Phys<double>& Q) {
+        return theta_only_d<decltype(law)::value>(ui, p1, p2, Q);
+      });
+      if (th_out) th_out[i] = th;
+    }
+    double S, dS;
+    sink_direct(ui, L.smax ? L.smax[i] : 0.0, P, S, dS);
+    const double di = L.g[i] - ((P.a * th + S) + P.xi * ui + mii * ui - off);
+    r32[i] = (float)di;
+    psi0f[i] = (float)ui;
+    delta[i] = 0.0f;
+    mx = nbits(di);
+  }
+  mx = block_max(mx, sm);
+  if (threadIdx.x == 0) atomicMax(norm, mx);
+}
+
 __global__ void __launch_bounds__(256) k_apply_delta(double* u, const float* delta, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     u[i] += (double)delta[i];
@@ -370,13 +419,14 @@ __global__ void __launch_bounds__(256) k_apply_delta(double* u, const float* del
 
 void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
                  const double* p1, const double* p2, const uint8_t* mat, const Phys<double>& P, int model, int scheme,
-                 double dt, double* Kc, double* g, double* u, const double* thn_in, const double* thm_in,
-                 double* thn_out, double* thm_out, cudaStream_t s) {
+                 double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
+                 const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
   const int b = grid_for(n);
+  predict = predict && scheme == 2;
   by_model(model, [&](auto m) {
-    k_prep_lagged<decltype(m)::value><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, mat, P, scheme, dt, Kc, g,
-                                                        u, thn_in, thm_in, thn_out, thm_out);
+    k_prep_lagged<decltype(m)::value><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, mat, P, scheme, dt, Kc,
+                                                        Kcf, g, u, thn_in, thm_in, thn_out, thm_out, predict);
   });
 }
 
@@ -459,6 +509,14 @@ void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPh
   by_model(model, [&](auto m) {
     k_outer_residual_dd<decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, Q, r32, psi0f, delta, norm, th_in,
                                                                        th_out);
+  });
+}
+
+void outer_residual64(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
+                      float* delta, unsigned long long* norm, const double* th_in, double* th_out, cudaStream_t s) {
+  const Launch3 g = launch3(L.n0, L.n1, L.n2);
+  by_model(model, [&](auto m) {
+    k_outer_residual64<decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
   });
 }
 
@@ -617,10 +675,126 @@ __global__ void __launch_bounds__(256) k_mass_balance(Level<double> L, Geom G, B
   }
 }
 
+// The same water balance in FP64 (FP64 mode and the FP64-outer mixed mode):
+// theta from the FP64 caches where given, else FP64 laws; FP64 sums.  The
+// error bound's minimum stays the FP32 expression of k_mass_balance.
+template <int MODEL>
+__global__ void __launch_bounds__(256) k_mass_balance64(Level<double> L, Geom G, BcDev bc, Phys<double> P,
+                                                        Phys<float> Pf, const double* __restrict__ psin,
+                                                        const double* __restrict__ psinm1, int scheme,
+                                                        double hist_scale, const double* th_new, const double* th_n,
+                                                        const double* th_nm1, double* part, unsigned* dmin_bits) {
+  __shared__ double sh[32];
+  __shared__ float smin[32];
+  double acc = 0.0;
+  float dmin = __int_as_float(0x7f800000);
+  const int v = G.dim - 1;
+  const int nn[3] = {G.n0, G.n1, G.n2};
+  double V = 1.0;
+  for (int a = 0; a < G.dim; ++a) V *= G.h[a];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.ncell;
+       i += (long long)gridDim.x * blockDim.x) {
+    int ii[3];
+    cell_coords(G.n0, G.n1, i, ii[0], ii[1], ii[2]);
+    const double p1 = L.p1 ? L.p1[i] : P.p1, p2 = L.p2 ? L.p2[i] : P.p2;
+    const double psi = L.u[i], pn = psin[i];
+    const unsigned mi = mat_of<MODEL>(L, i);
+    double th1, hist, ps;
+    with_law<MODEL>(P, mi, [&](auto law, const Phys<double>& Q) {
+      constexpr int ML = decltype(law)::value;
+      th1 = th_new ? th_new[i] : theta_only_d<ML>(psi, p1, p2, Q);
+      const double thn = th_n ? th_n[i] : theta_only_d<ML>(pn, p1, p2, Q);
+      if (scheme == 1) {
+        hist = thn * hist_scale;
+        ps = pn;
+      } else {
+        const double pm = psinm1[i];
+        const double thm = th_nm1 ? th_nm1[i] : theta_only_d<ML>(pm, p1, p2, Q);
+        hist = (4.0 * thn - thm) * hist_scale;
+        ps = 2.0 * pn - pm;
+      }
+      return 0;
+    });
+    const double smax = L.smax ? L.smax[i] : 0.0;
+    double S, dS;
+    sink_direct(psi, smax, P, S, dS);
+    double cell = (P.a * th1 - hist) + S + P.xi * (psi - ps);
+    cell *= V;
+    // inflow through this cell's boundary faces (face area A = V / h)
+    for (int ax = 0; ax < G.dim; ++ax)
+      for (int side = 0; side < 2; ++side) {
+        if (ii[ax] != (side ? nn[ax] - 1 : 0)) continue;
+        const int f = 2 * ax + side;
+        long long fc;
+        if (ax == 0) fc = ii[1] + (long long)G.n1 * ii[2];
+        else if (ax == 1) fc = ii[0] + (long long)G.n0 * ii[2];
+        else fc = ii[0] + (long long)G.n0 * ii[1];
+        const double A = V / G.h[ax];
+        const int kind = bc.kind[f];
+        const bool dir = kind == 0 && (!bc.mask[f] || bc.mask[f][fc]);
+        double qin = 0.0;
+        if (dir) {
+          const double zi = (ii[v] + 0.5) * G.h[v];
+          const double zb = (ax == v) ? (side ? G.Lv : 0.0) : zi;
+          const double val = bc.vfield[f] ? bc.vfield[f][fc] : bc.value[f];
+          const double head = (val + zb) - (psi + zi);
+          qin = A * L.kb[f][fc] * (head * (2.0 / G.h[ax]));
+        } else if (kind == 2) {
+          qin = A * (bc.vfield[f] ? bc.vfield[f][fc] : bc.value[f]);
+        } else if (kind == 3) {
+          qin = -A * L.Kc[i];
+        }
+        cell -= qin;
+      }
+    acc += cell;
+    // a theta' + S' + xi at psi (FP32 increment laws with a zero increment)
+    const float psif = (float)psi, p1f = (float)p1, p2f = (float)p2;
+    float Dth, dth;
+    with_law<MODEL>(Pf, mi, [&](auto law, const Phys<float>& Qf) {
+      constexpr int ML = decltype(law)::value;
+      dincr<ML>(dbase<ML>(psif, p1f, p2f), 0.0f, p1f, p2f, Qf, Dth, dth);
+      return 0;
+    });
+    const float smf = (float)smax;
+    float sa = 0.0f, sda = 0.0f;
+    if (Pf.sink && smf > 0.0f) feddes(psif, Pf, sa, sda);
+    dmin = fminf(dmin, Pf.a * dth + sda * smf + Pf.xi);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sh[wid] = acc; smin[wid] = dmin; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double x = lane < nw ? sh[lane] : 0.0;
+    float m = lane < nw ? smin[lane] : __int_as_float(0x7f800000);
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) {
+      part[blockIdx.x] = x;
+      atomicMin(dmin_bits, __float_as_uint(fmaxf(m, 0.0f)));
+    }
+  }
+}
+
 int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const Phys<double>& P, const Phys<float>& Pf,
                  int model, const double* psin, const double* psinm1, int scheme, double dt, const double* th_new,
-                 const double* th_n, const double* th_nm1, double* part, unsigned* dmin_bits, cudaStream_t s) {
+                 const double* th_n, const double* th_nm1, double* part, unsigned* dmin_bits, bool fp64,
+                 cudaStream_t s) {
   const int b = grid_for(L.ncell);
+  if (fp64) {
+    const double hs = scheme == 1 ? 1.0 / dt : 1.0 / (2.0 * dt);
+    by_model(model, [&](auto m) {
+      k_mass_balance64<decltype(m)::value><<<b, 256, 0, s>>>(L, G, bc, P, Pf, psin, psinm1, scheme, hs, th_new, th_n,
+                                                             th_nm1, part, dmin_bits);
+    });
+    return b;
+  }
   const DDPhys Q = make_ddphys(P);
   const dd hs = host_split(scheme == 1 ? 1.0 / dt : 1.0 / (2.0 * dt));
   by_model(model, [&](auto m) {

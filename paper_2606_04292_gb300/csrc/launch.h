@@ -62,8 +62,8 @@ void residual_color32(const Level<float>& L, const Phys<float>& P, int model, in
 // only when model == COMPOSITE; nullable otherwise)
 void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
                  const double* p1, const double* p2, const uint8_t* mat, const Phys<double>& P, int model, int scheme,
-                 double dt, double* Kc, double* g, double* u, const double* thn_in, const double* thm_in,
-                 double* thn_out, double* thm_out, cudaStream_t s);
+                 double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
+                 const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s);
 void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
               const uint8_t* mat, const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6],
               cudaStream_t s);
@@ -82,6 +82,10 @@ void to_float(const double* src, float* dst, long long n, cudaStream_t s);
 void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPhys& Q, int model, float* r32,
                        float* psi0f, float* delta, unsigned long long* norm, const double* th_in, double* th_out,
                        cudaStream_t s);
+// FP64-outer mixed mode: r = g - N(u) in FP64 -> r32, psi0 = (float)u,
+// delta = 0; ||r||_inf as FP64 bits; theta caches as outer_residual_dd.
+void outer_residual64(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
+                      float* delta, unsigned long long* norm, const double* th_in, double* th_out, cudaStream_t s);
 // mixed mode: the lagged state in float-float (Kc to FP64 and FP32)
 // (predict: u = psi* instead of psi^n)
 void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
@@ -90,10 +94,12 @@ void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, con
                     const double* thn_in, const double* thm_in, double* thn_out, double* thm_out, bool predict,
                     cudaStream_t s);
 // water balance of a step: per-block partial sums into part (returns the
-// block count) and min_i(a theta' + S' + xi) as float bits into *dmin_bits
+// block count) and min_i(a theta' + S' + xi) as float bits into *dmin_bits;
+// fp64: FP64 laws and sums, else float-float
 int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const Phys<double>& P, const Phys<float>& Pf,
                  int model, const double* psin, const double* psinm1, int scheme, double dt, const double* th_new,
-                 const double* th_n, const double* th_nm1, double* part, unsigned* dmin_bits, cudaStream_t s);
+                 const double* th_n, const double* th_nm1, double* part, unsigned* dmin_bits, bool fp64,
+                 cudaStream_t s);
 void restrict_face32(const Geom& F, const Geom& C, const Xfer<float>& X, int axis, const float* fine, float* coarse,
                      cudaStream_t s);
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);

@@ -1,10 +1,10 @@
 // One implicit time step of a small grid without any device allocation.
 //
 // Who needs this: code that must not call cudaMalloc in the middle of its
-// work -- a host routine that runs while a CUDA graph is being captured, an
-// application whose memory pool already owns all of the device memory, a
-// real-time loop that forbids allocator calls, or a plug-in inside another
-// GPU program that may only use memory handed to it.  Such callers pass
+// work -- an application whose memory pool already owns all of the device
+// memory, a real-time loop that forbids allocator calls (they can block and
+// synchronise the device), or a plug-in inside another GPU program that may
+// only use memory handed to it.  Such callers pass
 // device pointers for the state in and the state out; everything else the
 // step needs (multigrid hierarchy, coefficients, transfer tables, norms)
 // lives in one fixed array in the library's own device memory.
@@ -17,6 +17,7 @@
 
 #include "kernels.cuh"
 #include "richards.h"
+#include "validate.h"
 
 namespace rich {
 namespace {
@@ -56,7 +57,9 @@ struct NaPlan {
 // device pieces
 // ---------------------------------------------------------------------------
 // transfer tables of every level, built by the block
-__device__ void na_tables(const NaPlan& p) {
+// (*overflow is set when a coarse cell would take more than RMAX fine
+// contributors along an axis; ceil(n/2) coarsening gives at most 4)
+__device__ void na_tables(const NaPlan& p, int* overflow) {
   for (int l = 0; l + 1 < p.nlev; ++l) {
     const NaLevel& F = p.lev[l];
     const NaLevel& C = p.lev[l + 1];
@@ -85,7 +88,8 @@ __device__ void na_tables(const NaPlan& p) {
           int c2;
           interp_row(nf, nc, i, 1.0, 1.0, idx, w, c2);
           for (int k = 0; k < c2; ++k)
-            if (idx[k] == J && cnt < RMAX) {
+            if (idx[k] == J) {
+              if (cnt == RMAX) { *overflow = 1; continue; }
               F.ri[ax][RMAX * J + cnt] = i;
               F.rw[ax][RMAX * J + cnt] = w[k];
               ++cnt;
@@ -220,7 +224,19 @@ struct PlanLevels {
 template <int MODEL>
 __global__ void __launch_bounds__(TAIL_THREADS) k_small_step(const __grid_constant__ NaPlan p) {
   __shared__ unsigned long long sm[33];
-  na_tables(p);
+  __shared__ int overflow;
+  if (threadIdx.x == 0) overflow = 0;
+  __syncthreads();
+  na_tables(p, &overflow);          // ends with a barrier
+  if (overflow) {                   // (uniform over the block)
+    if (threadIdx.x == 0) {
+      p.stats[0] = 0.0;
+      p.stats[1] = p.stats[2] = 0.0;
+      p.stats[3] = (double)RICH_EINVAL;
+      p.stats[4] = 0.0;
+    }
+    return;
+  }
   na_prepare<MODEL>(p);
   const Phys<double>& P = p.P;
   const double teff = 1.0 / P.a;
@@ -272,15 +288,11 @@ extern "C" richards_status richards_step_small_noalloc(const richards_grid* grid
       o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
       !(o.xi >= 0.0) || !(o.kappa >= 0.0) || o.cycle_gamma < 1 || o.cycle_gamma > 3 || o.gamma_levels < 0)
     return RICH_EINVAL;
-  if (soil->model < 0 || soil->model > 2 || !(soil->Ks > 0.0) || !(soil->theta_s > soil->theta_r) ||
-      !(soil->theta_r >= 0.0))
-    return RICH_EINVAL;
-  for (int f = 0; f < 2 * grid->dim; ++f) {
-    if (bc->kind[f] < 0 || bc->kind[f] > 3) return RICH_EINVAL;
-    if (bc->kind[f] == RICH_BC_FREE_DRAINAGE && f != 2 * (grid->dim - 1)) return RICH_EINVAL;
-  }
-  if (sink->enabled && !(sink->h4 < sink->h3 && sink->h3 <= sink->h2 && sink->h2 < sink->h1 &&
-                         sink->root_decay > 0.0 && sink->root_depth > 0.0))
+  // the same checks as richards_set_soil / set_bc / set_sink (the fields are
+  // device arrays here and are not read on the host)
+  if (law_error(soil->model, soil->Ks, soil->theta_s, soil->theta_r, soil->p1, soil->p2, soil->p3, soil->p4,
+                soil->p1_field != nullptr, soil->p2_field != nullptr) ||
+      bc_error(*bc, grid->dim) || sink_error(*sink))
     return RICH_EINVAL;
 
   // set-up, once per device: the device address of the scratch array

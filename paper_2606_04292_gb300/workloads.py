@@ -29,8 +29,8 @@ Problem layout (a plain ``dict``):
 * ``dt``, ``nsteps``, ``scheme`` (1 = BDF1, 2 = BDF2).
 * ``opts``: solver options (sweeps, kappa mode, xi, tolerance, ...).
 
-Per-cell soil fields are rounded to float32-representable doubles so that a
-float32 copy on the device is exact; the CPU oracle reads the same values.
+Every parameter and per-cell field is a plain float64 draw: the library makes
+whatever lower-precision copies it needs on the device itself.
 """
 from __future__ import annotations
 
@@ -46,11 +46,6 @@ MODEL_NAMES = {HAVERKAMP: "haverkamp", GARDNER: "gardner", VANGENUCHTEN: "vangen
 
 # 5 mm/day of potential transpiration, in m/s.
 TP_5MM_PER_DAY = 5.0e-3 / 86400.0
-
-
-def f32exact(x):
-    """Round to the nearest float32 and return float64 (exactly representable)."""
-    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
 
 
 def default_opts(**kw):
@@ -210,12 +205,11 @@ def two_layer_2d(n=256, dt=0.01, nsteps=100, **optkw):
 
 def test_materials():
     """Three materials in m and s, one per law, with distinct Ks, theta_s and
-    theta_r (parameters exact in float)."""
-    f = lambda x: float(np.float32(x))
-    return [material(VANGENUCHTEN, f(1e-5), f(0.368), f(0.102), p1=f(3.35), p2=f(2.0), p3=0.5),
-            material(HAVERKAMP, f(2.5e-5), f(0.287), f(0.075), p1=f(1.611e6 * 100.0 ** -3.96),
-                     p2=f(3.96), p3=f(1.175e6 * 100.0 ** -4.74), p4=f(4.74)),
-            material(GARDNER, f(4e-6), f(0.45), f(0.15), p1=f(2.0))]
+    theta_r."""
+    return [material(VANGENUCHTEN, 1e-5, 0.368, 0.102, p1=3.35, p2=2.0, p3=0.5),
+            material(HAVERKAMP, 2.5e-5, 0.287, 0.075, p1=1.611e6 * 100.0 ** -3.96,
+                     p2=3.96, p3=1.175e6 * 100.0 ** -4.74, p4=4.74),
+            material(GARDNER, 4e-6, 0.45, 0.15, p1=2.0)]
 
 
 def with_materials(prob, mats, index):
@@ -273,10 +267,10 @@ def gaussian_log_field(shape, corr_cells, seed):
 def drainage_3d(n=256, dt=300.0, nsteps=50, seed_ks=3, seed_vg=4, **optkw):
     shape_zyx = (n, n, n)
     G = gaussian_log_field(shape_zyx, 8.0, seed_ks)          # indexed [z, y, x]
-    Ks = f32exact(np.exp(math.log(1e-5) + 1.0 * G)).reshape(-1)   # x fastest
+    Ks = np.exp(math.log(1e-5) + 1.0 * G).reshape(-1)   # x fastest
     rng = np.random.Generator(np.random.PCG64(seed_vg))
-    alpha = f32exact(rng.uniform(2.0, 5.0, n ** 3))
-    nvg = f32exact(rng.uniform(1.5, 2.5, n ** 3))
+    alpha = rng.uniform(2.0, 5.0, n ** 3)
+    nvg = rng.uniform(1.5, 2.5, n ** 3)
     soil = _soil(VANGENUCHTEN, Ks=1e-5, theta_s=0.368, theta_r=0.102,
                  p1=3.5, p2=2.0, p3=0.5, Ks_field=Ks, p1_field=alpha, p2_field=nvg)
     # faces: x-low, x-high, y-low, y-high, bottom (free drainage), top (no flux)
@@ -308,9 +302,9 @@ def drainage_3d(n=256, dt=300.0, nsteps=50, seed_ks=3, seed_vg=4, **optkw):
 def columns(ncol=4096, seed=5, dt=600.0, nsteps=144, nmin=64, nmax=1024, **optkw):
     rng = np.random.Generator(np.random.PCG64(seed))
     lengths = rng.integers(nmin, nmax + 1, ncol)
-    alpha = f32exact(rng.uniform(0.5, 5.0, ncol))
-    nvg = f32exact(rng.uniform(1.2, 3.0, ncol))
-    Ks = f32exact(np.exp(rng.uniform(math.log(1e-7), math.log(1e-4), ncol)))
+    alpha = rng.uniform(0.5, 5.0, ncol)
+    nvg = rng.uniform(1.2, 3.0, ncol)
+    Ks = np.exp(rng.uniform(math.log(1e-7), math.log(1e-4), ncol))
     out = []
     for c in range(ncol):
         m = int(lengths[c])
@@ -356,7 +350,7 @@ def serving_trace(rate=200.0, seconds=60.0, seed=6, sizes2d=(129, 257, 513, 1025
         is3d = rng.random() < 0.5
         n = int(rng.choice(sizes3d if is3d else sizes2d))
         model = int(rng.integers(0, 3))
-        Ks = float(f32exact(math.exp(rng.uniform(math.log(1e-7), math.log(1e-4)))))
+        Ks = float(math.exp(rng.uniform(math.log(1e-7), math.log(1e-4))))
         if model == HAVERKAMP:
             s = rng.uniform(0.8, 1.2)
             # C1 parameters converted from cm to m: A*100^-gamma, alpha*100^-beta
@@ -406,19 +400,19 @@ def random_problem(dim, n, model, seed, bc_kinds=None, hetero=False, sink=False,
         soil = _soil(HAVERKAMP, 1e-5, 0.287, 0.075, p1=1.611e6 * 100.0 ** -3.96,
                      p2=3.96, p3=1.175e6 * 100.0 ** -4.74, p4=4.74)
         if hetero:
-            soil["p1_field"] = f32exact(soil["p1"] * rng.uniform(0.7, 1.3, N))
-            soil["p2_field"] = f32exact(rng.uniform(3.0, 4.5, N))
+            soil["p1_field"] = soil["p1"] * rng.uniform(0.7, 1.3, N)
+            soil["p2_field"] = rng.uniform(3.0, 4.5, N)
     elif model == GARDNER:
         soil = _soil(GARDNER, 1e-5, 0.45, 0.15, p1=2.0)
         if hetero:
-            soil["p1_field"] = f32exact(rng.uniform(1.0, 5.0, N))
+            soil["p1_field"] = rng.uniform(1.0, 5.0, N)
     else:
         soil = _soil(VANGENUCHTEN, 1e-5, 0.368, 0.102, p1=3.35, p2=2.0, p3=0.5)
         if hetero:
-            soil["p1_field"] = f32exact(rng.uniform(2.0, 5.0, N))
-            soil["p2_field"] = f32exact(rng.uniform(1.5, 2.5, N))
+            soil["p1_field"] = rng.uniform(2.0, 5.0, N)
+            soil["p2_field"] = rng.uniform(1.5, 2.5, N)
     if hetero:
-        soil["Ks_field"] = f32exact(np.exp(np.log(1e-5) + rng.standard_normal(N)))
+        soil["Ks_field"] = np.exp(np.log(1e-5) + rng.standard_normal(N))
     if bc_kinds is None:
         bc_kinds = [NOFLUX] * (2 * dim - 2) + [FREE_DRAINAGE, DIRICHLET]
     vals = []

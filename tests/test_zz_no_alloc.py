@@ -1,10 +1,11 @@
 """The allocation-free small-grid step against the regular step (needs a GPU).
 
 richards_step_small_noalloc serves callers that may not allocate device
-memory while they run (graph capture, a memory pool that owns the device, a
-real-time loop, a plug-in limited to the memory handed to it).  It must give
-the same state as richards_step on a context, call after call, within the
-step tolerance of the other GPU tests.
+memory while they run (a memory pool that owns the device, a real-time loop
+where an allocation may block, a plug-in limited to the memory handed to it).
+It must give the same state as richards_step on a context, call after call,
+within the step tolerance of the other GPU tests, and reject the inputs the
+regular set-up calls reject.
 """
 import ctypes as C
 
@@ -58,10 +59,10 @@ def _structs(prob, keep):
     return grid, soil, bc, sink, opts
 
 
-def _noalloc_step(prob, psi_n, psi_prev, keep):
+def _noalloc_step(prob, psi_n, psi_prev, keep, out=None):
     L = R.lib()
     grid, soil, bc, sink, opts = _structs(prob, keep)
-    out = torch.empty_like(psi_n)
+    out = torch.empty_like(psi_n) if out is None else out
     info = R.richards_step_info()
     st = L.richards_step_small_noalloc(C.byref(grid), C.byref(soil), C.byref(bc), C.byref(sink), C.byref(opts),
                                        float(prob["dt"]), int(prob["scheme"]), _dptr(psi_n), _dptr(psi_prev),
@@ -103,4 +104,63 @@ def test_noalloc_rejects_grid_above_maximum():
     keep = []
     psi = torch.zeros(17 * 16 * 16, dtype=torch.float64, device="cuda")
     st, _, _ = _noalloc_step(prob, psi, None, keep)
+    assert st == R.RICH_EINVAL
+
+
+@pytest.mark.parametrize("alias", ["psi_n", "psi_prev"])
+def test_noalloc_output_may_alias_an_input(alias):
+    """BDF2 with rotating buffers: the output written over psi^n or over
+    psi^{n-1} gives the regular step's state."""
+    prob = W.with_opts(W.random_problem(3, (12, 11, 10), W.VANGENUCHTEN, 34, hetero=True, scheme=2), precision=0)
+    ref = R.Solver(prob)
+    keep = []
+    psi = torch.tensor(np.asarray(prob["psi0"], dtype=np.float64), device="cuda")
+    prev = None
+    for call in range(3):
+        assert ref.step(check=False)[0] == R.RICH_OK
+        if prev is None:
+            out = torch.empty_like(psi)
+        else:
+            out = psi if alias == "psi_n" else prev
+        keep_prev = psi.clone()
+        st, _, out = _noalloc_step(prob, psi, prev, keep, out=out)
+        assert st == R.RICH_OK, (call, st)
+        got, want = out.cpu().numpy(), ref.state()
+        assert np.max(np.abs(got - want)) / np.max(np.abs(want)) <= STEP_RTOL, call
+        prev, psi = keep_prev, out
+
+
+BAD_SOILS = [
+    ("haverkamp_alpha", W.HAVERKAMP, dict(p1=0.0)),
+    ("haverkamp_beta", W.HAVERKAMP, dict(p2=-1.0)),
+    ("haverkamp_A", W.HAVERKAMP, dict(p3=0.0)),
+    ("haverkamp_gamma", W.HAVERKAMP, dict(p4=float("nan"))),
+    ("gardner_alpha", W.GARDNER, dict(p1=-2.0)),
+    ("vg_n", W.VANGENUCHTEN, dict(p2=1.0)),
+    ("vg_l", W.VANGENUCHTEN, dict(p3=float("inf"))),
+    ("vg_alpha", W.VANGENUCHTEN, dict(p1=0.0)),
+]
+
+
+@pytest.mark.parametrize("model,bad", [(b[1], b[2]) for b in BAD_SOILS], ids=[b[0] for b in BAD_SOILS])
+def test_noalloc_rejects_what_set_soil_rejects(model, bad):
+    prob = W.random_problem(2, (8, 8), model, 35)
+    prob["soil"] = dict(prob["soil"], **bad)
+    with pytest.raises(R.RichardsError) as e:
+        R.Solver(prob)
+    assert e.value.status == R.RICH_EINVAL
+    psi = torch.tensor(np.asarray(prob["psi0"], dtype=np.float64), device="cuda")
+    st, _, _ = _noalloc_step(prob, psi, None, [])
+    assert st == R.RICH_EINVAL
+
+
+def test_noalloc_rejects_bad_sink_and_boundary_values():
+    prob = W.random_problem(2, (8, 8), W.VANGENUCHTEN, 36, sink=True)
+    psi = torch.tensor(np.asarray(prob["psi0"], dtype=np.float64), device="cuda")
+    for sink in (dict(prob["sink"], Tp=-1.0), dict(prob["sink"], root_decay=float("nan"))):
+        st, _, _ = _noalloc_step(dict(prob, sink=sink), psi, None, [])
+        assert st == R.RICH_EINVAL
+    bc = dict(prob["bc"], value=list(prob["bc"]["value"]))
+    bc["value"][3] = float("nan")
+    st, _, _ = _noalloc_step(dict(prob, bc=bc), psi, None, [])
     assert st == R.RICH_EINVAL
