@@ -1,11 +1,12 @@
 #!/usr/bin/env python
 """Benchmark: NGS-FAS Richards solver on the 3D drainage workload (256^3).
 
-One bench step is one implicit BDF2 time step of the whole path (per-step
-preparation, an outer defect correction of the FP64 state in float-float
-arithmetic around FP32 FAS cycles with red-black NGS, the stop test on that
-defect, water balance, history shift) on 256^3 cells of heterogeneous van
-Genuchten soil draining from saturation.  Inputs (16.8 M cells, 134 MB per
+One bench step is one implicit BDF2 time step of the whole path (FP64
+per-step preparation, an FP64 outer defect correction of the FP64 state
+around FP32 FAS cycles with red-black NGS, the FP64 stop test, FP64 water
+balance, history shift) on 256^3 cells of heterogeneous van Genuchten soil
+draining from saturation.  --precision 1 times the float-float outer layer
+instead; the line carries the other one's figures beside the headline.  Inputs (16.8 M cells, 134 MB per
 FP64 array) are larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -30,9 +31,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "NGS cell-updates/s and time-steps/s at 256^3; p50/p99 solve latency, vs FP64 plain @1e-8"
 UNIT = "cell-updates/s"
-WORKLOAD = "3D drainage 256^3, heterogeneous VG (lognormal Ks, sigma_lnK=1, corr 8 cells; alpha U[2,5], n U[1.5,2.5]), " \
-           "psi0=0, free drainage bottom, BDF2 dt=300 s, mixed: FP32 inner cycles, float-float outer defect " \
-           "on the FP64 state, tol 1e-8"
+def workload_name(precision):
+    outer = ("FP64 outer defect correction (FP64 lagged K, history, deciding defect, stop test and water "
+             "balance; float-float steering defects)" if precision == 2 else
+             "float-float outer defect correction on the FP64 state")
+    return ("3D drainage 256^3, heterogeneous VG (lognormal Ks, sigma_lnK=1, corr 8 cells; alpha U[2,5], "
+            f"n U[1.5,2.5]), psi0=0, free drainage bottom, BDF2 dt=300 s, mixed: FP32 inner cycles, {outer}, "
+            "tol 1e-8")
+
+
+DTYPE = {2: "f32 inner / f64 outer, f64 state", 1: "f32 inner / float-float (f32x2) outer, f64 state"}
 
 # Algorithmic bytes per unit for the kernels that can dominate (per cell the
 # launch covers; a half-sweep covers the cells of one colour).  The NGS
@@ -67,6 +75,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-other-outer", action="store_true",
+                    help="skip timing the other outer layer (float-float beside FP64, or the reverse)")
     ap.add_argument("--profile-steps", type=int, default=None,
                     help="steps with kernel timing (default: all timed steps)")
     ap.add_argument("--no-columns", action="store_true")
@@ -74,6 +84,8 @@ def parse():
     ap.add_argument("--no-gardner", action="store_true")
     ap.add_argument("--no-layered", action="store_true")
     ap.add_argument("--no-table3", action="store_true")
+    ap.add_argument("--no-celia", action="store_true")
+    ap.add_argument("--no-strip", action="store_true")
     ap.add_argument("--temporal-study", action="store_true",
                     help="add Section 4.1's temporal-convergence study (N=1024 vs N=2048, tau_ref=1e-4; ~4 min)")
     ap.add_argument("--gamma", type=int, default=2, help="1 = V-cycles, 2 = W-cycles")
@@ -187,15 +199,20 @@ def roofline(prof, steps, ms_pass):
 
 
 # ---------------------------------------------------------------------------
-def columns_bench(stream, steps=10):
+def columns_bench(stream, steps=10, rank=0, world=1):
     """Batched root-uptake columns: 4096 columns of U{64..1024} cells, per-column
     van Genuchten soil, Feddes sink, BDF1 dt = 600 s; every column advances
-    `steps` steps in one persistent launch (block size autotuned first)."""
+    `steps` steps in one persistent launch (block size autotuned first).
+    Under torchrun each rank takes every world-th column (replicas.shard) and
+    the ranks' summaries are merged: the slowest rank's time, summed work."""
     import numpy as np
     import torch
+    from paper_2606_04292_gb300 import replicas
     from paper_2606_04292_gb300 import richards as R
     from paper_2606_04292_gb300 import workloads as W
-    probs = W.columns()
+    allp = W.columns()
+    ids = replicas.shard(range(len(allp)), rank, world)
+    probs = [allp[k] for k in ids]
     cols = R.Columns(probs, stream=stream.cuda_stream)
     dt = probs[0]["dt"]
     threads = cols.autotune(dt)
@@ -208,13 +225,19 @@ def columns_bench(stream, steps=10):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     stt = cols.stats()
-    out = {"workload": "4096 columns U{64..1024} cells, VG per column, Feddes sink, BDF1 dt=600 s, mixed",
-           "columns": len(probs), "cells": int(cols.N), "steps": steps, "threads": threads,
-           "status": R.STATUS_NAMES[st], "all_columns_ok": bool(np.all(stt["status"] == R.RICH_OK)),
-           "column_steps_per_s": len(probs) * steps / (ms * 1e-3),
-           "cell_updates_per_s": float(np.sum(stt["updates"])) / (ms * 1e-3), "ms": ms}
+    part = {"ids": ids, "ms": ms, "units": len(ids), "updates": float(np.sum(stt["updates"])),
+            "unit_steps": len(ids) * steps, "ok": bool(np.all(stt["status"] == R.RICH_OK) and st == R.RICH_OK)}
+    parts = replicas.gather(part)
+    allpart = replicas.combine(parts)
+    out = {"workload": "4096 columns U{64..1024} cells, VG per column, Feddes sink, BDF1 dt=600 s, mixed "
+                       "(float-float outer)",
+           "columns": len(allp), "cells": int(sum(p["n"][0] for p in allp)), "steps": steps, "threads": threads,
+           "ranks": world, "status": R.STATUS_NAMES[st], "all_columns_ok": all(p["ok"] for p in parts),
+           "column_steps_per_s": allpart["unit_steps"] / (allpart["ms"] * 1e-3),
+           "cell_updates_per_s": allpart["updates"] / (allpart["ms"] * 1e-3), "ms": allpart["ms"]}
     psi = cols.state()
-    sample = {k: cols.column(psi, k).copy() for k in range(0, len(probs), COLUMN_CPU_EVERY)}
+    # the CPU leg's sample: every COLUMN_CPU_EVERY-th column this rank took
+    sample = {k: cols.column(psi, j).copy() for j, k in enumerate(ids) if k % COLUMN_CPU_EVERY == 0}
     cols.close()
     return out, sample
 
@@ -250,21 +273,67 @@ def columns_cpu(sample, steps):
             "sample": f"every {COLUMN_CPU_EVERY}th column ({len(sample)} columns, {cells} cells), {steps} timed steps"}
 
 
-def serving_bench(nreq=24, max_steps=20):
-    """Served stream, reduced: Poisson arrivals at 200/s of 2D 129^2/257^2 and
-    3D 65^3 requests (three soil laws, half with a sink, BDF2), at most
-    `max_steps` steps each; mixed precision and FP64 plain on the same trace."""
+SERVING_MODES = {
+    # label: (precision, batched)
+    "batched_mixed_fp64_outer": (2, True),
+    "streams_mixed_fp64_outer": (2, False),
+    "streams_mixed_float_float_outer": (1, False),
+    "streams_fp64_plain": (0, False),
+}
+
+
+def _serve(trace, ids, precision, batched):
+    from paper_2606_04292_gb300 import replicas
     from paper_2606_04292_gb300 import serve
+    srv = serve.Server(max_active=16 if batched else 8, opts={"precision": precision}, batched=batched)
+    results, summary = srv.run([trace[k] for k in ids], realtime=True)
+    part = {"ids": ids, "ms": summary["makespan_s"] * 1e3, "completed": summary["completed"],
+            "rejected": summary.get("rejected", 0),
+            "updates": summary["cell_updates_per_s"] * summary["makespan_s"],
+            "latencies": [r["latency"] for r in results if r["status"] == "OK"]}
+    m = replicas.combine(replicas.gather(part))
+    mk = m["ms"] * 1e-3
+    return {"completed": m["completed"], "makespan_s": mk, "solves_per_s": m["completed"] / mk,
+            "cell_updates_per_s": m["updates"] / mk, "p50_latency_s": m["p50_latency_s"],
+            "p99_latency_s": m["p99_latency_s"]}
+
+
+def serving_bench(nreq=24, max_steps=20, rank=0, world=1):
+    """Served streams of Poisson arrivals at 200/s (three soil laws, half with a
+    sink, BDF2), at most `max_steps` steps each.  Two traces: a reduced size
+    mix (2D 129^2/257^2, 3D 65^3), served by lockstep batched cycles
+    (richards_batcher_step) and by per-request streams, in the FP64-outer and
+    float-float mixed modes and FP64 plain; and the configured size mix (2D
+    129^2-1025^2, 3D 65^3-257^3), mixed with the FP64 outer layer, batched and
+    per-stream.  Offered load is the arrival rate; served load the solve rate.
+    Under torchrun each rank serves every world-th request (replicas.shard);
+    completions and latencies are merged over the ranks."""
+    from paper_2606_04292_gb300 import replicas
     from paper_2606_04292_gb300 import workloads as W
-    out = {"workload": f"{nreq} Poisson requests (200/s), 2D 129^2-257^2 and 3D 65^3, <= {max_steps} BDF2 steps"}
-    for label, opts in (("mixed", None), ("fp64_plain", {"precision": 0})):
-        trace = W.serving_trace(rate=200.0, seconds=60.0, seed=6, sizes2d=(129, 257), sizes3d=(65,),
-                                max_requests=nreq)
-        for p in trace:
+
+    def trace_of(sizes2d, sizes3d):
+        tr = W.serving_trace(rate=200.0, seconds=60.0, seed=6, sizes2d=sizes2d, sizes3d=sizes3d, max_requests=nreq)
+        for p in tr:
             p["nsteps"] = min(p["nsteps"], max_steps)
-        results, summary = serve.Server(max_active=8, opts=opts).run(trace, realtime=True)
-        out[label] = {k: summary[k] for k in ("completed", "makespan_s", "solves_per_s", "cell_updates_per_s",
-                                              "p50_latency_s", "p99_latency_s")}
+        return tr
+
+    out = {"offered_requests_per_s": 200.0, "ranks": world, "max_steps": max_steps}
+    red = trace_of((129, 257), (65,))
+    ids = replicas.shard(range(len(red)), rank, world)
+    out["reduced_mix"] = {"workload": f"{len(red)} Poisson requests (200/s), 2D 129^2-257^2 and 3D 65^3, "
+                                      f"<= {max_steps} BDF2 steps"}
+    for label, (prec, batched) in SERVING_MODES.items():
+        out["reduced_mix"][label] = _serve(red, ids, prec, batched)
+    full = trace_of((129, 257, 513, 1025), (65, 129, 257))
+    ids = replicas.shard(range(len(full)), rank, world)
+    out["configured_mix"] = {
+        "workload": f"{len(full)} Poisson requests (200/s) of the configured size mix, 2D 129^2-1025^2 and 3D "
+                    f"65^3-257^3, <= {max_steps} BDF2 steps (FP64 plain not run on this mix: its 257^3 requests "
+                    "take ~0.6 s a step)",
+        "sizes": sorted({f"{p['dim']}D {p['n'][0]}" for p in full})}
+    for label in ("batched_mixed_fp64_outer", "streams_mixed_fp64_outer"):
+        prec, batched = SERVING_MODES[label]
+        out["configured_mix"][label] = _serve(full, ids, prec, batched)
     return out
 
 
@@ -338,6 +407,101 @@ def gardner_cpu(states):
     ref = o.state()
     return {"total_s": time.perf_counter() - t0, "cores": 1,
             "max_abs_dpsi_gpu_vs_oracle": {k: float(np.max(np.abs(v - ref))) for k, v in states.items()}}
+
+
+def celia_bench(stream):
+    """The 1-d infiltration column in full (128 cells over 40 cm, Haverkamp,
+    BDF1 dt = 10 s for 36 steps, V(2,2), FP64), red-black and the paper's
+    lexicographic order: wall time of the whole run and cycles per step."""
+    import torch
+    from paper_2606_04292_gb300 import richards as R
+    from paper_2606_04292_gb300 import workloads as W
+    out = {"workload": "1D Haverkamp column 128 cells, BDF1 dt=10 s x 36 steps, V(2,2), FP64, tol 1e-8"}
+    states = {}
+    for label, ordering in (("red_black_fp64", 1), ("lexicographic_fp64", 0)):
+        prob = W.celia_1d(ordering=ordering)
+        gs = R.Solver(prob, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cyc, worst = 0, 0
+        for _ in range(prob["nsteps"]):
+            st, info = gs.step(check=False)
+            cyc += info["cycles"]
+            worst = max(worst, st)
+        torch.cuda.synchronize()
+        out[label] = {"total_s": time.perf_counter() - t0, "steps": prob["nsteps"],
+                      "worst_status": R.STATUS_NAMES[worst], "cycles_per_step": cyc / prob["nsteps"]}
+        states[label] = gs.state()
+        gs.close()
+    return out, states
+
+
+def celia_cpu(states):
+    """The oracle on the whole column run, both orderings (single thread),
+    and the distance of the GPU states."""
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_2606_04292_gb300 import workloads as W
+    res = {"cores": 1}
+    for label, ordering in (("red_black_fp64", 1), ("lexicographic_fp64", 0)):
+        o = Oracle(W.celia_1d(ordering=ordering))
+        t0 = time.perf_counter()
+        for _ in range(o.prob["nsteps"]):
+            o.step()
+        res[label + "_total_s"] = time.perf_counter() - t0
+        res[label + "_max_abs_dpsi"] = float(np.max(np.abs(states[label] - o.state())))
+    return res
+
+
+STRIP_CPU_STEPS = 2
+
+
+def strip_bench(stream, nsteps=100):
+    """The 2-d infiltration workload in full (513^2 over 1 m^2, van Genuchten,
+    Dirichlet strip on the top, BDF2 dt = 60 s for 100 steps, V(2,2)): FP64
+    plain (as configured) and the FP64-outer mixed mode; wall time, steps/s,
+    cell-updates/s.  Returns the summary and the FP64 state after
+    STRIP_CPU_STEPS steps for the CPU leg."""
+    import torch
+    from paper_2606_04292_gb300 import richards as R
+    from paper_2606_04292_gb300 import workloads as W
+    out = {"workload": f"2D strip infiltration 513^2, VG, BDF2 dt=60 s x {nsteps} steps, V(2,2), tol 1e-8"}
+    states = {}
+    for label, prec in (("fp64_plain", 0), ("mixed_fp64_outer", 2)):
+        prob = W.strip_2d(n=513, nsteps=nsteps, precision=prec)
+        gs = R.Solver(prob, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cyc, worst, upd = 0, 0, 0
+        for k in range(nsteps):
+            st, info = gs.step(check=False)
+            cyc += info["cycles"]
+            upd += info["cell_updates"]
+            worst = max(worst, st)
+            if k + 1 == STRIP_CPU_STEPS:
+                states[label] = gs.state()
+        torch.cuda.synchronize()
+        tt = time.perf_counter() - t0
+        out[label] = {"total_s": tt, "steps": nsteps, "time_steps_per_s": nsteps / tt,
+                      "cell_updates_per_s": upd / tt, "cycles_per_step": cyc / nsteps,
+                      "worst_status": R.STATUS_NAMES[worst]}
+        gs.close()
+    return out, states
+
+
+def strip_cpu(states):
+    """The oracle on the first STRIP_CPU_STEPS steps of the 513^2 strip
+    (single thread): seconds per step, and the distance of the GPU states."""
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_2606_04292_gb300 import workloads as W
+    o = Oracle(W.strip_2d(n=513))
+    t0 = time.perf_counter()
+    for _ in range(STRIP_CPU_STEPS):
+        o.step()
+    per = (time.perf_counter() - t0) / STRIP_CPU_STEPS
+    return {"cores": 1, "s_per_step": per, "sample": f"first {STRIP_CPU_STEPS} steps",
+            **{k + "_max_abs_dpsi": float(np.max(np.abs(v - o.state()))) for k, v in states.items()}}
 
 
 LAYERED_STEPS = 100       # two-layer field, FP64 plain: 1 h at tau = 0.01 h
@@ -427,53 +591,94 @@ def table3_cpu():
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(prob, psi, nsweeps=3):
-    """The CPU oracle, as it stands, on a bounded sample of the same workload:
-    red-black NGS sweeps of the 256^3 fine level at the given state."""
+def host_info():
+    """The host the CPU legs run on: logical core count and CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"host_cores": os.cpu_count(), "cpu_model": model or "unknown", "machine": platform.machine()}
+
+
+def cpu_baseline(prob, psi, nsweeps_all=6, nsweeps_lex=2):
+    """The CPU oracle, as it stands, on a bounded sample of the same workload
+    at the given state of the 256^3 fine level: red-black NGS sweeps with each
+    colour's cells shared among all host cores (OpenMP; the same updates as
+    the serial sweep), and, beside it, the paper's single-threaded
+    lexicographic sweep."""
     from oracle.oracle import Oracle
     o = Oracle(prob)
     o.set_state(psi)
     o.prepare(prob["dt"], 1)
+    n = len(psi)
     cur = psi
     t0 = time.perf_counter()
-    for _ in range(nsweeps):
-        cur = o.sweep(cur)
-    dt = time.perf_counter() - t0
-    n = len(psi)
-    return {"value": nsweeps * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsweeps} red-black NGS sweeps (Newton k={prob['opts']['newton_iters']}) of the "
-                      f"{round(n ** (1 / 3))}^3 fine level "
-                      f"at the benchmark state, single-threaded C oracle, {dt:.1f} s"}
+    for _ in range(nsweeps_all):
+        cur, used = o.sweep_threads(cur, 0)
+    t_all = time.perf_counter() - t0
+    cur = psi
+    t0 = time.perf_counter()
+    for _ in range(nsweeps_lex):
+        cur = o.sweep(cur, ordering=0)
+    t_lex = time.perf_counter() - t0
+    k = prob["opts"]["newton_iters"]
+    side = round(n ** (1 / 3))
+    return dict({"value": nsweeps_all * n / t_all, "unit": UNIT, "cores": used, "kind": "oracle",
+                 "sample": f"{nsweeps_all} red-black NGS sweeps (Newton k={k}) of the {side}^3 fine level at the "
+                           f"benchmark state, C oracle with each colour's cells on {used} OpenMP threads, "
+                           f"{t_all:.1f} s",
+                 "single_thread_lexicographic": {
+                     "value": nsweeps_lex * n / t_lex, "unit": UNIT, "cores": 1,
+                     "sample": f"{nsweeps_lex} lexicographic NGS sweeps (the paper's order), same level and "
+                               f"state, {t_lex:.1f} s"}}, **host_info())
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle timed on the host, one fine-level
-    sweep of the same 256^3 workload per step."""
+    """--impl reference: the CPU oracle timed on the host's cores, one
+    fine-level red-black sweep of the same 256^3 workload per step (each
+    colour's cells on all cores, OpenMP)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import numpy as np
     from oracle.oracle import Oracle
     from paper_2606_04292_gb300 import workloads as W
-    prob = W.drainage_3d(n=args.n)
+    prob = W.drainage_3d(n=args.n, precision=args.precision)
     o = Oracle(prob)
     o.prepare(prob["dt"], 1)
     psi = np.array(prob["psi0"], dtype=np.float64)
     for _ in range(args.warmup):
-        psi = o.sweep(psi)
+        psi, used = o.sweep_threads(psi, 0)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        psi = o.sweep(psi)
+        psi, used = o.sweep_threads(psi, 0)
     dt = time.perf_counter() - t0
     n = len(psi)
     v = args.steps * n / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "one red-black NGS sweep of the "
-                                            "fine level of the first time step per step"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} fine-level NGS sweeps at {args.n}^3, single thread"},
+            "data": "synthetic", "config": {"workload": workload_name(args.precision),
+                                            "sample": "one red-black NGS sweep of the fine level of the first "
+                                                      "time step per step"},
+            "cpu_baseline": dict({"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+                                  "sample": f"{args.steps} fine-level red-black NGS sweeps at {args.n}^3, "
+                                            f"{used} OpenMP threads"}, **host_info()),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -514,6 +719,10 @@ def main():
     infos = []
     for _ in range(args.warmup):
         st, info = gs.step()
+    # launch shapes of the big FP32 grid levels, timed on this state (the
+    # choice never changes the arithmetic)
+    gs.prepare(prob["dt"], prob["scheme"])
+    tuned = gs.autotune()
     barrier()
     # timed region: the context counts its launches on the host (no events)
     gs.profile(True, mode=3)
@@ -569,6 +778,8 @@ def main():
         ge = R.Solver(prob, stream=stream.cuda_stream)
         ge.set_state(host_psi, host_prev)
         ge.step()
+        ge.prepare(prob["dt"], prob["scheme"])
+        ge.autotune()
         barrier()
         ke = max(1, min(args.steps, 5))
         upd = 0
@@ -585,6 +796,35 @@ def main():
         e2e = {"value": upd / te * world, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N,
                "steps": ke, "time_steps_per_s": ke / te}
         ge.close()
+
+    # the other outer layer on the same workload: float-float beside an FP64
+    # headline (or FP64 beside a float-float one), device time of a few steps
+    other = None
+    if not args.no_other_outer and rank == 0:
+        oprec = 1 if args.precision == 2 else 2
+        go = R.Solver(W.with_opts(prob, precision=oprec), stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            go.step()
+        go.prepare(prob["dt"], prob["scheme"])
+        go.autotune()
+        ko = max(1, min(args.steps, 5))
+        oi = []
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        q0.record(stream)
+        for _ in range(ko):
+            st, info = go.step(check=False)
+            oi.append(info)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        mo = q0.elapsed_time(q1)
+        other = {"precision": oprec, "dtype": DTYPE[oprec], "steps": ko, "warmup": args.warmup,
+                 "ms_per_step": mo / ko, "time_steps_per_s": ko / (mo * 1e-3),
+                 "cell_updates_per_s": sum(i["cell_updates"] for i in oi) / (mo * 1e-3),
+                 "v_cycles_per_step": statistics.mean(i["cycles"] for i in oi),
+                 "outer_iters_per_step": statistics.mean(i["outer_iters"] for i in oi),
+                 "status_last": R.STATUS_NAMES[st]}
+        go.close()
 
     fp64 = None
     if not args.no_fp64 and rank == 0:
@@ -617,12 +857,14 @@ def main():
         gf.close()
         gm.close()
 
+    # batched columns and served requests: every rank takes its share of the
+    # units (no data-path collective; the summaries are gathered)
     columns = csample = None
-    if rank == 0 and not args.no_columns:
-        columns, csample = columns_bench(stream)
+    if not args.no_columns:
+        columns, csample = columns_bench(stream, rank=rank, world=world)
     serving = None
-    if rank == 0 and not args.no_serving:
-        serving = serving_bench()
+    if not args.no_serving:
+        serving = serving_bench(rank=rank, world=world)
 
     gardner = gstates = None
     if rank == 0 and not args.no_gardner:
@@ -630,6 +872,13 @@ def main():
     layered = lstates = None
     if rank == 0 and not args.no_layered:
         layered, lstates = layered_bench(stream)
+
+    celia = cstates = None
+    if rank == 0 and not args.no_celia:
+        celia, cstates = celia_bench(stream)
+    strip = sstates = None
+    if rank == 0 and not args.no_strip:
+        strip, sstates = strip_bench(stream)
 
     table3 = None
     if rank == 0 and not args.no_table3:
@@ -655,6 +904,10 @@ def main():
             layered["cpu_oracle"] = layered_cpu(lstates)
         if table3 is not None:
             table3["cpu_oracle"] = table3_cpu()
+        if celia is not None:
+            celia["cpu_oracle"] = celia_cpu(cstates)
+        if strip is not None:
+            strip["cpu_oracle"] = strip_cpu(sstates)
         if columns is not None:
             columns["cpu_oracle"] = columns_cpu(csample, columns["steps"])
         if serving is not None:
@@ -664,8 +917,10 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / float-float (f32x2) outer, f64 state", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": N, "levels": gs.nlevels, "l2": "inputs larger than L2",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": workload_name(args.precision), "cells": N, "levels": gs.nlevels, "l2": "inputs larger than L2",
+                       "launch_shapes": {f"level{l}": {"planes": t[0], "block_x": t[1], "resid_block_x": t[2]}
+                                         for l, t in enumerate(tuned) if any(t)},
                        "cycle": f"{'W' if args.gamma == 2 else 'V'}({prob['opts']['nu1']},{prob['opts']['nu2']})",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "time_steps_per_s": steps_per_s,
@@ -677,9 +932,12 @@ def main():
             "roofline": roofline(prof, prof_steps, ms_prof) if prof else None,
             "clocks": clk.summary(),
             "e2e": e2e,
+            "other_outer": other,
             "fp64_plain": fp64,
             "columns": columns,
             "serving": serving,
+            "celia_column_c1": celia,
+            "strip_513_c2": strip,
             "paper_gardner_2d": gardner,
             "paper_layered": layered,
             "paper_temporal_study": temporal,

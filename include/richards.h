@@ -280,6 +280,63 @@ richards_status richards_batch_submit(richards_ctx *const *ctxs, int n, double d
 richards_status richards_batch_poll(richards_ctx *const *ctxs, int n, int *done, richards_status *status,
                                     richards_step_info *info);
 
+/* ---------------------------------------------------------------------
+ * Launch shapes of the FP32 grid kernels (mixed modes).  The paper has no
+ * counterpart: these choose how the kernels of a level are laid out on the
+ * GPU, never what they compute (one cell's arithmetic does not depend on the
+ * launch shape, so every choice gives the same bits).
+ * --------------------------------------------------------------------- */
+
+/* Time, on the context's current prepared state, every candidate shape of
+   each grid level with at least 2^15 cells -- cells per thread along z of
+   the half-sweeps (1, 2, 4, 8; the finest level keeps 2 where its last
+   half-sweep also writes the defects), their block x-size (32..256; 128 at
+   most with more than one plane) and the defect kernel's block x-size --
+   over reps red+black half-sweeps (defects) each, and keep the fastest; the
+   state is restored.  planes_out / bx_out / rbx_out (nullable, nlevels
+   entries) receive the choices (0: default).  Needs a mixed-mode context
+   (precision 1 or 2) with red-black sweeps after richards_prepare or a
+   step.  Errors: EINVAL, EBUSY, ENOMEM (the saved state), ECUDA. */
+richards_status richards_autotune(richards_ctx *ctx, int reps, int *planes_out, int *bx_out, int *rbx_out);
+
+/* Set a level's shapes by hand (0 restores a default).  EINVAL outside the
+   candidate sets above. */
+richards_status richards_set_launch(richards_ctx *ctx, int level, int planes, int block_x, int resid_block_x);
+
+/* ---------------------------------------------------------------------
+ * Lockstep batch of resident contexts (continuous batching of served
+ * requests, at the granularity of a time step).  richards_batcher_step takes
+ * one implicit step of each listed context: the outer defects, the FP64
+ * decisions and the inner stop tests of all contexts are taken together
+ * (one synchronisation for all per stage), and the FP32 inner V-cycles of
+ * all of them run together -- every stage of a cycle (half-sweep, defect,
+ * restriction, FAS right side, interpolation, coarse tail) is one launch
+ * over a device table of (context, level) descriptors (Section 3.2's cycle
+ * for each context; a context's arithmetic is the same as in richards_step,
+ * and no reduction mixes contexts).  The caller may change the list from one
+ * step to the next (admit new requests, retire finished ones).
+ * --------------------------------------------------------------------- */
+typedef struct richards_batcher richards_batcher;   /* opaque; owns its descriptor tables */
+
+/* stream: the cudaStream_t every batched step runs on (NULL = default
+   stream); max_contexts: the most contexts one step takes (1..4096).
+   Errors: EINVAL, ENOMEM. */
+richards_status richards_batcher_create(void *stream, int max_contexts, richards_batcher **out);
+void richards_batcher_destroy(richards_batcher *b);
+const char *richards_batcher_last_error(const richards_batcher *b);
+
+/* One step of each of the n contexts (dt[k], scheme[k]: as richards_step).
+   Every context must be in a mixed mode (precision 1 or 2) with red-black
+   sweeps and no FMG start, and all must share nu1, nu2, cycle_gamma,
+   gamma_levels, coarse_max_sweeps, coarse_rtol and inner_cycles; the calls
+   are ordered on the batcher's stream (each context's own stream is
+   synchronised first).  status[k] / info[k] (nullable) receive each
+   context's outcome as richards_step would return it.  Returns EINVAL /
+   EBUSY before doing anything when an argument or a context does not
+   qualify, ECUDA on a CUDA error, else RICH_OK. */
+richards_status richards_batcher_step(richards_batcher *b, richards_ctx *const *ctxs, int n, const double *dt,
+                                      const int *scheme, richards_status *status, richards_step_info *info);
+
 /* Device memory a context for this grid and these options allocates
    (upper estimate, bytes; no device is touched): soil_fields != 0 when the
    soil has per-cell fields, sink != 0 with a sink.  -1 on invalid input. */
@@ -402,9 +459,11 @@ richards_status richards_step_small_noalloc(const richards_grid *grid, const ric
  * in one persistent launch (a device work queue, longest column first; each
  * thread block runs all time steps of one column with the column's whole
  * multigrid hierarchy in shared memory).  Mixed precision as for
- * richards_step with opts->precision 1: lagged K, history, defect and stop
- * test in float-float arithmetic (laws ~1e-12 relative), FP32 FAS cycles on
- * the correction equation.
+ * richards_step: FP32 FAS cycles on the correction equation inside an outer
+ * defect correction whose lagged K, history, defect and stop test run in
+ * float-float arithmetic (laws ~1e-12 relative) with opts->precision 1, or
+ * in FP64 with opts->precision 2 (float-float defects steer, the FP64 defect
+ * decides the stop test); precision 0 is taken as 1.
  * --------------------------------------------------------------------- */
 #define RICHARDS_COLUMN_MAX_CELLS 2048
 typedef struct richards_columns richards_columns;   /* opaque; owns its device memory */

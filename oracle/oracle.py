@@ -27,8 +27,11 @@ def build(force=False):
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "richards_oracle.h"))):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", "-o", tmp, SRC, "-lm"])
+    base = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, SRC]
+    # OpenMP only shares the cells of one red-black colour among threads
+    # (orc_sweep_rb_threads); without it that sweep runs on one thread
+    if subprocess.run(base + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, LIB)
     return LIB
 
@@ -105,6 +108,8 @@ def lib():
         L.orc_residual.argtypes = [C.c_void_p, C.c_int, _DP, _DP, _DP]
         L.orc_sweep.argtypes = [C.c_void_p, C.c_int, _DP, _DP, C.c_int]
         L.orc_sweep_ordering.argtypes = [C.c_void_p, C.c_int, _DP, _DP, C.c_int]
+        L.orc_sweep_rb_threads.argtypes = [C.c_void_p, C.c_int, _DP, _DP, C.c_int]
+        L.orc_sweep_rb_threads.restype = C.c_int
         L.orc_restrict.argtypes = [C.c_void_p, C.c_int, _DP, _DP]
         L.orc_prolong_add.argtypes = [C.c_void_p, C.c_int, _DP, _DP]
         L.orc_vcycle.argtypes = [C.c_void_p, C.c_int, _DP, _DP]
@@ -276,6 +281,14 @@ class Oracle:
         else:
             lib().orc_sweep_ordering(self.h, lev, _dp(psi), _dp(g), int(ordering))
         return psi
+
+    def sweep_threads(self, psi, nthreads=0, g=None, lev=0):
+        """One red-black sweep on nthreads OpenMP threads (0: all); the same
+        result as sweep(psi, ordering=1).  Returns (psi, threads used)."""
+        psi = _f64(psi).copy()
+        g = self.g(lev) if g is None else _f64(g)
+        used = lib().orc_sweep_rb_threads(self.h, lev, _dp(psi), _dp(g), int(nthreads))
+        return psi, int(used)
 
     def restrict(self, fine, lev=0):
         fine = _f64(fine)

@@ -7,6 +7,9 @@
  * floating-point contraction.  Every function cites the passage of the paper
  * it follows; build-defined readings are marked "reading".
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "richards_oracle.h"
 
 #include <math.h>
@@ -724,6 +727,32 @@ void orc_sweep_ordering(orc_ctx *c, int lev, double *psi, const double *g, int o
         if (((ii[0] + ii[1] + ii[2]) & 1) == col) point_update(c, L, i, psi, g);
       }
   }
+}
+
+/* One red-black sweep with the cells of each colour shared among nthreads
+   OpenMP threads (nthreads <= 0: all of them).  Cells of one colour do not
+   couple -- each reads only cells of the other colour and its own old value
+   -- so every cell gets exactly the update of orc_sweep_ordering's
+   red-black sweep, whatever the thread count.  Returns the thread count
+   used (1 when the library was built without OpenMP).  Used to time the
+   oracle on all host cores. */
+int orc_sweep_rb_threads(orc_ctx *c, int lev, double *psi, const double *g, int nthreads) {
+  level *L = &c->lev[lev];
+  int used = 1;
+#ifdef _OPENMP
+  used = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+  for (int col = 0; col < 2; ++col) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(used)
+#endif
+    for (long i = 0; i < L->ncell; ++i) {
+      int ii[3]; cpos(L, i, ii);
+      if (((ii[0] + ii[1] + ii[2]) & 1) == col) point_update(c, L, i, psi, g);
+    }
+  }
+  (void)nthreads;
+  return used;
 }
 
 void orc_sweep(orc_ctx *c, int lev, double *psi, const double *g, int color) {

@@ -117,6 +117,9 @@ double orc_residual(const orc_ctx *c, int lev, const double *psi, const double *
    red/black half of a red-black sweep. */
 void orc_sweep(orc_ctx *c, int lev, double *psi, const double *g, int color);
 void orc_sweep_ordering(orc_ctx *c, int lev, double *psi, const double *g, int ordering);
+/* the red-black sweep on nthreads OpenMP threads (<= 0: all); same result as
+   orc_sweep_ordering(..., 1); returns the threads used */
+int orc_sweep_rb_threads(orc_ctx *c, int lev, double *psi, const double *g, int nthreads);
 
 /* transfers between lev (fine) and lev+1 (coarse) */
 void orc_restrict(const orc_ctx *c, int lev, const double *fine, double *coarse);

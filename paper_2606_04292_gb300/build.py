@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "librichards_gb300.so")
-SOURCES = ["k64.cu", "k32.cu", "k32s.cu", "capi.cu", "noalloc.cu", "columns.cu"]
+SOURCES = ["k64.cu", "k32.cu", "k32s.cu", "capi.cu", "noalloc.cu", "columns.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -118,6 +118,10 @@ struct richards_ctx {
   std::vector<ProfRec> capture_recs;
   richards_status batch_status = RICH_OK;
   richards_step_info batch_info{};
+  // launch shapes of the FP32 grid kernels per level (richards_autotune /
+  // richards_set_launch; 0 = the defaults): cells per thread along z of the
+  // half-sweeps, their block x-size, the defect kernel's block x-size
+  int tune_planes[MAXLEV] = {}, tune_bx[MAXLEV] = {}, tune_rbx[MAXLEV] = {};
 };
 
 namespace {
@@ -523,17 +527,20 @@ void smooth64(richards_ctx* c, const Level<double>& F, const Phys<double>& P, in
   c->updates_host += (long long)nu * F.ncell;
 }
 
+int planes_at(const richards_ctx* c, int l) { return c->tune_planes[l] > 0 ? c->tune_planes[l] : c->opts.sweep_planes; }
+
 void smooth32(richards_ctx* c, const Level<float>& F, const Phys<float>& P, int l, int nu) {
   const int model = c->soil.model;
   const long long half = (F.ncell + 1) / 2;
+  const int pl = planes_at(c, l), bx = c->tune_bx[l];
   for (int k = 0; k < nu; ++k) {
     if (c->opts.ordering == 0) {
       Prof pr(c, "sweep_lex32", l, F.ncell);
       rich::sweep_lex32(F, P, model, c->s);
       continue;
     }
-    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->opts.sweep_planes, c->s); }
-    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, c->opts.sweep_planes, c->s); }
+    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, pl, c->s, bx); }
+    { Prof pr(c, "sweep32", l, F.ncell - half); rich::sweep32(F, P, model, 1, pl, c->s, bx); }
   }
   c->updates_host += (long long)nu * F.ncell;
 }
@@ -592,7 +599,7 @@ void vcycle32(richards_ctx* c, int l, bool d_ready = false, bool fuse = false) {
   smooth32(c, F, P, l, c->opts.nu1);
   if (!(d_ready && c->opts.nu1 == 0)) {
     Prof pr(c, "residual32", l, F.ncell);
-    rich::residual32(F, P, model, nullptr, c->s);
+    rich::residual32(F, P, model, nullptr, c->s, c->tune_rbx[l]);
   }
   { Prof pr(c, "restrict32", l, C.ncell); rich::restrict32(F, C, xfer32(c, l), F.u, F.d, C.ubar, C.d, c->s); }
   { Prof pr(c, "tau32", l + 1, C.ncell); rich::tau32(C, P, model, c->s); }
@@ -603,7 +610,7 @@ void vcycle32(richards_ctx* c, int l, bool d_ready = false, bool fuse = false) {
   if (fuse && l == 0 && c->opts.nu2 >= 1) {
     smooth32(c, F, P, l, c->opts.nu2 - 1);
     const long long half = (F.ncell + 1) / 2;
-    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, c->opts.sweep_planes, c->s); }
+    { Prof pr(c, "sweep32", l, half); rich::sweep32(F, P, model, 0, planes_at(c, l), c->s, c->tune_bx[l]); }
     cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s);
     { Prof pr(c, "sweep_resid32", l, F.ncell - half); rich::sweep_resid32(F, P, model, c->scratch + 1, c->s); }
     { Prof pr(c, "residual32", l, half); rich::residual_color32(F, P, model, 0, c->scratch + 1, c->s); }
@@ -628,7 +635,7 @@ bool top_defect_ready(const richards_ctx* c) { return c->opts.nu1 == 0 && c->opt
 // (see vcycle32), on levels the pipelined half-sweep serves
 bool fuse_defect(const richards_ctx* c) {
   return top_defect_ready(c) && c->opts.ordering == 1 && c->opts.nu2 >= 1 && c->tail_start > 0 &&
-         rich::resid_fusable32(view32(c, 0), c->opts.sweep_planes);
+         rich::resid_fusable32(view32(c, 0), planes_at(c, 0));
 }
 
 void run_cycle32(richards_ctx* c) {
@@ -924,11 +931,40 @@ richards_status step_fp64(richards_ctx* c, richards_step_info* info) {
 // the corrections, and the defect that decides the stop test -- computed
 // whenever a float-float defect passes it, or the outer limit is reached --
 // is FP64; it also gives theta(psi^{n+1}) to the FP64 history cache.
+// The outer defect of the mixed mode (float-float, or FP64 with fp64) into
+// the inner problem's right side, frozen state and zero correction, with
+// ||d||_inf in scratch slot 0.  cached: the iterate is psi^n, whose theta is
+// cached; otherwise theta of the iterate goes to th_cur (FP64 outer: only
+// from the FP64 defect).
+richards_status outer_defect_launch(richards_ctx* c, bool cached, bool fp64) {
+  HLevel& F = c->L[0];
+  const Phys<double> P64 = phys<double>(c);
+  CK(cudaMemsetAsync(c->scratch, 0, sizeof(unsigned long long), c->s));
+  double* th_out = cached || (c->opts.precision == 2 && !fp64) ? nullptr : c->th_cur;
+  if (fp64) {
+    Prof pr(c, "outer_residual64", 0, F.ncell);
+    rich::outer_residual64(view64(c, 0), P64, c->soil.model, F.gf, F.psi0f, F.uf, c->scratch,
+                           cached ? c->th_n : nullptr, th_out, c->s);
+  } else {
+    Prof pr(c, "outer_residual", 0, F.ncell);
+    rich::outer_residual_dd(view64(c, 0), P64, rich::make_ddphys(P64), c->soil.model, F.gf, F.psi0f, F.uf,
+                            c->scratch, cached ? c->th_n : nullptr, th_out, c->s);
+  }
+  return check_launch(c);
+}
+
+// the coarse copies of the inner problem's frozen state psi0
+void restrict_psi0(richards_ctx* c) {
+  for (int l = 0; l + 1 < c->nlev; ++l) {
+    Prof pr(c, "restrict_psi0", l, c->L[l + 1].ncell);
+    rich::restrict32(view32(c, l), view32(c, l + 1), xfer32(c, l), c->L[l].psi0f, nullptr, c->L[l + 1].psi0f,
+                     nullptr, c->s);
+  }
+}
+
 richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   const double teff = 1.0 / c->a;
   const int model = c->soil.model;
-  const Phys<double> P64 = phys<double>(c);
-  const rich::DDPhys Q = rich::make_ddphys(P64);
   const Phys<float> P32 = phys<float>(c);
   HLevel& F = c->L[0];
   double r = 0.0, r0 = 0.0;
@@ -938,19 +974,7 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   // else evaluated and kept in th_cur (theta(psi^{n+1}) once accepted)
   const bool outer64 = c->opts.precision == 2;
   auto defect = [&](bool cached, bool fp64, double* out) -> richards_status {
-    CK(cudaMemsetAsync(c->scratch, 0, sizeof(unsigned long long), c->s));
-    // (FP64 outer: only the FP64 defect writes the theta cache)
-    double* th_out = cached || (outer64 && !fp64) ? nullptr : c->th_cur;
-    if (fp64) {
-      Prof pr(c, "outer_residual64", 0, F.ncell);
-      rich::outer_residual64(view64(c, 0), P64, model, F.gf, F.psi0f, F.uf, c->scratch, cached ? c->th_n : nullptr,
-                             th_out, c->s);
-    } else {
-      Prof pr(c, "outer_residual", 0, F.ncell);
-      rich::outer_residual_dd(view64(c, 0), P64, Q, model, F.gf, F.psi0f, F.uf, c->scratch,
-                              cached ? c->th_n : nullptr, th_out, c->s);
-    }
-    TRY(check_launch(c));
+    TRY(outer_defect_launch(c, cached, fp64));
     double nrm;
     TRY(read_norm(c, 0, &nrm, !fp64));
     *out = teff * nrm;
@@ -958,19 +982,26 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   };
   // with the predictor (BDF2 steps) the iteration starts at psi*, not psi^n
   const bool predicted = c->opts.predictor == 1 && c->scheme_used == 2;
+  // FP64 outer: a float-float defect that passes the stop test, or stops
+  // falling (less than halved by a correction: near tol it may sit on its own
+  // rounding floor), or the outer limit hands over to FP64 defects for the
+  // rest of the step
+  bool use64 = false;
+  double r_ff = INFINITY;
   for (;;) {
     const bool cached = outer == 0 && !predicted;
-    TRY(defect(cached, false, &r));
-    if (outer64 && !std::isnan(r) && (!(r > c->opts.tol) || outer >= c->opts.max_outer))
-      TRY(defect(cached, true, &r));     // the FP64 defect decides
+    if (!use64) {
+      const double prev = r_ff;
+      TRY(defect(cached, false, &r_ff));
+      r = r_ff;
+      use64 = outer64 && !std::isnan(r) &&
+              (!(r > c->opts.tol) || outer >= c->opts.max_outer || r > 0.5 * prev);
+    }
+    if (use64) TRY(defect(cached, true, &r));     // the FP64 defect decides
     if (outer == 0) r0 = r;
     if (!(r > c->opts.tol) || std::isnan(r)) break;
     if (outer >= c->opts.max_outer) { st = RICH_ENOCONV; break; }
-    for (int l = 0; l + 1 < c->nlev; ++l) {
-      Prof pr(c, "restrict_psi0", l, c->L[l + 1].ncell);
-      rich::restrict32(view32(c, l), view32(c, l + 1), xfer32(c, l), c->L[l].psi0f, nullptr, c->L[l + 1].psi0f,
-                       nullptr, c->s);
-    }
+    restrict_psi0(c);
     const double rin0 = r / teff;       // ||g - N(psi)||_inf of this defect
     // an inner solve need not reduce its defect below what the stop test
     // asks of the next outer defect (with a margin of 0.3 for the FP32 and
@@ -987,7 +1018,7 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
         CK(cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s));
         {
           Prof pr(c, "residual32", 0, F.ncell);
-          rich::residual32(view32(c, 0), P32, model, c->scratch + 1, c->s);
+          rich::residual32(view32(c, 0), P32, model, c->scratch + 1, c->s, c->tune_rbx[0]);
         }
         double rin;
         TRY(read_norm(c, 1, &rin, true));
@@ -1002,7 +1033,7 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
         if (!fused) {
           CK(cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s));
           Prof pr(c, "residual32", 0, F.ncell);
-          rich::residual32(view32(c, 0), P32, model, c->scratch + 1, c->s);
+          rich::residual32(view32(c, 0), P32, model, c->scratch + 1, c->s, c->tune_rbx[0]);
         }
         double rin;
         TRY(read_norm(c, 1, &rin, true));
@@ -1029,6 +1060,251 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
   const bool moved = outer > 0 || predicted;      // theta(psi^{n+1}) is in th_cur
   TRY(water_balance(c, r, info, moved ? c->th_cur : c->th_n, c->th_n, c->th_nm1_valid ? c->th_nm1 : nullptr));
   return finish_step(c, r, st, moved ? 1 : 0);
+}
+
+}  // namespace
+
+// ==========================================================================
+// Lockstep batch of mixed-precision contexts (served requests): every
+// context takes one implicit step; their outer defects, decisions and inner
+// stop tests are taken together (one synchronisation for all), and their
+// FP32 inner cycles run together, each stage of a cycle one launch over the
+// descriptors of all contexts that are at that stage (batch.cu).
+// ==========================================================================
+struct richards_batcher {
+  cudaStream_t s = nullptr;
+  int cap = 0;                               // contexts the tables hold
+  rich::BJob32* dtable = nullptr;            // cap x MAXLEV descriptors (device)
+  rich::BJob32* htable = nullptr;            // staging copy (pinned)
+  std::string err;
+};
+
+namespace {
+
+struct BatchCtx {
+  richards_ctx* c = nullptr;
+  cudaStream_t own = nullptr;                // the context's stream, restored at the end
+  int slot = 0;
+  bool ok = true;                            // prepared; takes part
+  bool outer_active = false, inner_active = false, predicted = false;
+  bool use64 = false;                        // FP64 outer: FP64 defects from here on (as step_mixed)
+  double r = 0.0, r0 = 0.0, rin0 = 0.0, rtol_in = 0.0, r_ff = INFINITY;
+  int outer = 0, inner = 0;
+  richards_status st = RICH_OK;
+};
+
+int batch_nk(const richards_ctx* c) {
+  const int k = c->opts.newton_iters;
+  return (k == 1 || k == 2) ? k : 0;
+}
+
+// one stage over the level-l descriptors of the listed contexts, grouped by
+// law and Newton count, at most BATCH_MAX descriptors per launch
+void batch_stage(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who, int op, int l,
+                 int color, bool with_norm) {
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  for (int k : who) groups[{B[k].c->soil.model, batch_nk(B[k].c)}].push_back(k);
+  for (auto& kv : groups) {
+    const std::vector<int>& ks = kv.second;
+    for (size_t a = 0; a < ks.size(); a += rich::BATCH_MAX) {
+      rich::BList list{};
+      list.n = 0;
+      int blocks = 0;
+      for (size_t q = a; q < ks.size() && q < a + rich::BATCH_MAX; ++q) {
+        const int j = B[ks[q]].slot * MAXLEV + l;
+        list.job[list.n] = j;
+        list.block0[list.n] = blocks;
+        blocks += rich::batch_blocks(op, b->htable[j]);
+        ++list.n;
+      }
+      list.block0[list.n] = blocks;
+      rich::batch32(op, kv.first.first, kv.first.second, b->dtable, list, color, with_norm, b->s);
+    }
+  }
+}
+
+void batch_tail(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who, int l) {
+  std::map<int, std::vector<int>> groups;
+  for (int k : who) groups[B[k].c->soil.model].push_back(k);
+  const richards_opts& o = B[who[0]].c->opts;
+  for (auto& kv : groups)
+    for (size_t a = 0; a < kv.second.size(); a += rich::BATCH_MAX) {
+      rich::BList list{};
+      for (size_t q = a; q < kv.second.size() && q < a + rich::BATCH_MAX; ++q)
+        list.job[list.n++] = B[kv.second[q]].slot * MAXLEV + l;
+      rich::batch_tail32(kv.first, b->dtable, list, o.nu1, o.nu2, o.coarse_max_sweeps, (float)o.coarse_rtol,
+                         o.cycle_gamma, o.gamma_levels, b->s);
+    }
+}
+
+void batch_smooth(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who, int l, int nu) {
+  for (int q = 0; q < nu; ++q) {
+    batch_stage(b, B, who, rich::BOP_SWEEP, l, 0, false);
+    batch_stage(b, B, who, rich::BOP_SWEEP, l, 1, false);
+  }
+  for (int k : who) B[k].c->updates_host += (long long)nu * B[k].c->L[l].ncell;
+}
+
+// vcycle32 for all listed contexts at once (top: level 0 of the inner
+// solve, where a context whose stop test left the defect in place skips it)
+void batch_vcycle(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who, int l, bool top) {
+  std::vector<int> tail, grid;
+  for (int k : who) (l >= B[k].c->tail_start ? tail : grid).push_back(k);
+  if (!tail.empty()) batch_tail(b, B, tail, l);
+  if (grid.empty()) return;
+  const richards_opts& o = B[grid[0]].c->opts;
+  batch_smooth(b, B, grid, l, o.nu1);
+  std::vector<int> need;
+  for (int k : grid)
+    if (!(top && top_defect_ready(B[k].c) && o.nu1 == 0)) need.push_back(k);
+  if (!need.empty()) batch_stage(b, B, need, rich::BOP_RESID, l, 0, false);
+  batch_stage(b, B, grid, rich::BOP_RESTRICT, l, 0, false);
+  batch_stage(b, B, grid, rich::BOP_TAU, l, 0, false);
+  for (int q = 0; q < gamma_at(B[grid[0]].c, l); ++q) batch_vcycle(b, B, grid, l + 1, false);
+  batch_stage(b, B, grid, rich::BOP_PROLONG, l, 0, false);
+  batch_smooth(b, B, grid, l, o.nu2);
+}
+
+double host_norm(const richards_ctx* c, int k, bool fp32) {
+  const unsigned long long bits = c->hscratch[k];
+  if (fp32) {
+    const unsigned u = (unsigned)bits;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+  }
+  double d;
+  std::memcpy(&d, &bits, 8);
+  return d;
+}
+
+richards_status bfail(richards_batcher* b, richards_status st, const std::string& msg) {
+  b->err = msg;
+  return st;
+}
+
+#define TRY_B(expr)                            \
+  do {                                         \
+    const richards_status s_ = (expr);         \
+    if (s_ != RICH_OK) return s_;              \
+  } while (0)
+
+#define BCK(call)                                                                                 \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return bfail(b, RICH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// launch the outer defects of the listed contexts, one synchronisation,
+// their norms (fp64: the FP64 defect) into B[k].r
+richards_status batch_defects(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who, bool fp64) {
+  for (int k : who) {
+    richards_ctx* c = B[k].c;
+    const bool cached = B[k].outer == 0 && !B[k].predicted;
+    richards_status st = outer_defect_launch(c, cached, fp64);
+    if (st != RICH_OK) return bfail(b, st, c->err);
+    BCK(cudaMemcpyAsync(c->hscratch, c->scratch, sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->s));
+  }
+  BCK(cudaStreamSynchronize(b->s));
+  for (int k : who) B[k].r = host_norm(B[k].c, 0, !fp64) / B[k].c->a;
+  return RICH_OK;
+}
+
+richards_status batch_step_impl(richards_batcher* b, std::vector<BatchCtx>& B, const double* dts,
+                                const int* schemes) {
+  const int n = (int)B.size();
+  // descriptors of every level of every context
+  for (int k = 0; k < n; ++k) {
+    richards_ctx* c = B[k].c;
+    for (int l = 0; l < c->nlev; ++l) {
+      rich::BJob32& J = b->htable[B[k].slot * MAXLEV + l];
+      J = rich::BJob32{};
+      J.F = view32(c, l);
+      if (l + 1 < c->nlev) {
+        J.C = view32(c, l + 1);
+        J.X = xfer32(c, l);
+      }
+      J.P = phys<float>(c);
+      J.dLs = c->dL32;
+      J.dXs = c->dX32;
+      J.level = l;
+      J.nlev = c->nlev;
+      J.norm = c->scratch + 1;
+      J.stats = c->scratch + 16;
+    }
+  }
+  (void)dts; (void)schemes;
+  BCK(cudaMemcpyAsync(b->dtable, b->htable, sizeof(rich::BJob32) * (size_t)n * MAXLEV, cudaMemcpyHostToDevice,
+                      b->s));
+  std::vector<int> act;
+  for (int k = 0; k < n; ++k)
+    if (B[k].ok) { B[k].outer_active = true; act.push_back(k); }
+  while (!act.empty()) {
+    std::vector<int> ff, need64;
+    for (int k : act) (B[k].use64 ? need64 : ff).push_back(k);
+    if (!ff.empty()) TRY_B(batch_defects(b, B, ff, false));
+    for (int k : ff) {
+      BatchCtx& X = B[k];
+      const richards_ctx* c = X.c;
+      const double prev = X.r_ff;
+      X.r_ff = X.r;
+      X.use64 = c->opts.precision == 2 && !std::isnan(X.r) &&
+                (!(X.r > c->opts.tol) || X.outer >= c->opts.max_outer || X.r > 0.5 * prev);
+      if (X.use64) need64.push_back(k);
+    }
+    if (!need64.empty()) TRY_B(batch_defects(b, B, need64, true));   // the FP64 defect decides
+    std::vector<int> go;
+    for (int k : act) {
+      BatchCtx& X = B[k];
+      if (X.outer == 0) X.r0 = X.r;
+      if (!(X.r > X.c->opts.tol) || std::isnan(X.r)) continue;
+      if (X.outer >= X.c->opts.max_outer) { X.st = RICH_ENOCONV; continue; }
+      go.push_back(k);
+    }
+    act.swap(go);
+    if (act.empty()) break;
+    for (int k : act) {
+      BatchCtx& X = B[k];
+      richards_ctx* c = X.c;
+      restrict_psi0(c);
+      X.rin0 = X.r * c->a;
+      X.rtol_in = std::max(c->opts.inner_rtol, 0.3 * c->opts.tol / X.r);
+      if (top_defect_ready(c))
+        BCK(cudaMemcpyAsync(c->L[0].df, c->L[0].gf, sizeof(float) * c->L[0].ncell, cudaMemcpyDeviceToDevice, b->s));
+    }
+    std::vector<int> in = act;
+    const int cycles = B[act[0]].c->opts.inner_cycles;
+    for (int q = 0; q < cycles && !in.empty(); ++q) {
+      batch_vcycle(b, B, in, 0, true);
+      for (int k : in) ++B[k].inner;
+      if (q + 1 >= cycles) break;
+      std::vector<int> test;
+      for (int k : in)
+        if (B[k].c->opts.inner_rtol > 0.0) test.push_back(k);
+      if (test.empty()) continue;
+      for (int k : test) BCK(cudaMemsetAsync(B[k].c->scratch + 1, 0, sizeof(unsigned long long), b->s));
+      batch_stage(b, B, test, rich::BOP_RESID, 0, 0, true);
+      for (int k : test)
+        BCK(cudaMemcpyAsync(B[k].c->hscratch + 1, B[k].c->scratch + 1, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, b->s));
+      BCK(cudaStreamSynchronize(b->s));
+      std::vector<int> keep;
+      for (int k : in) {
+        const bool tested = B[k].c->opts.inner_rtol > 0.0;
+        if (tested && host_norm(B[k].c, 1, true) <= B[k].rtol_in * B[k].rin0) continue;
+        keep.push_back(k);
+      }
+      in.swap(keep);
+    }
+    for (int k : act) {
+      richards_ctx* c = B[k].c;
+      rich::apply_delta(c->L[0].u, c->L[0].uf, c->L[0].ncell, b->s);
+      ++B[k].outer;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, RICH_ECUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+  }
+  return RICH_OK;
 }
 
 }  // namespace
@@ -1588,6 +1864,197 @@ richards_status richards_batch_poll(richards_ctx* const* ctxs, int n, int* done,
     }
   }
   return RICH_OK;
+}
+
+richards_status richards_set_launch(richards_ctx* c, int level, int planes, int block_x, int resid_block_x) {
+  if (!c || level < 0 || level >= c->nlev) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  auto bx_ok = [](int b) { return b == 0 || b == 32 || b == 64 || b == 128 || b == 256; };
+  if (!(planes == 0 || planes == 1 || planes == 2 || planes == 4 || planes == 8) || !bx_ok(block_x) ||
+      !bx_ok(resid_block_x) || (planes > 1 && block_x > 128))
+    return fail(c, RICH_EINVAL, "planes in {0,1,2,4,8}, block sizes in {0,32,64,128,256} (128 at most with planes > 1)");
+  if (level == 0 && planes > 0 && fuse_defect(c) && planes != 2)
+    return fail(c, RICH_EINVAL, "the finest level's defect-writing half-sweep needs two planes");
+  cudaStreamSynchronize(c->s);
+  graphs_reset(c);
+  c->tune_planes[level] = planes;
+  c->tune_bx[level] = block_x;
+  c->tune_rbx[level] = resid_block_x;
+  return RICH_OK;
+}
+
+richards_status richards_autotune(richards_ctx* c, int reps, int* planes_out, int* bx_out, int* rbx_out) {
+  if (!c || reps < 1 || reps > 100) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  if (!c->prepared || c->opts.precision < 1 || c->opts.ordering != 1)
+    return fail(c, RICH_EINVAL, "autotune needs a prepared mixed-mode context with red-black sweeps");
+  cudaStreamSynchronize(c->s);
+  graphs_reset(c);
+  const Phys<float> P = phys<float>(c);
+  const int model = c->soil.model;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  richards_status st = RICH_OK;
+  for (int l = 0; l < c->tail_start && st == RICH_OK; ++l) {
+    HLevel& H = c->L[l];
+    if (H.ncell < (1LL << 15)) continue;        // small levels: bound by their own latency
+    const Level<float> F = view32(c, l);
+    float* save = nullptr;
+    if (cudaMallocAsync((void**)&save, sizeof(float) * 2 * H.ncell, c->s) != cudaSuccess) {
+      st = fail(c, RICH_ENOMEM, "autotune: no room for the saved state");
+      break;
+    }
+    cudaMemcpyAsync(save, H.uf, sizeof(float) * H.ncell, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(save + H.ncell, H.df, sizeof(float) * H.ncell, cudaMemcpyDeviceToDevice, c->s);
+    // every candidate computes the same values (one cell's arithmetic does
+    // not depend on the launch shape); each starts from the saved state
+    auto time_it = [&](auto&& launch) -> float {
+      launch();                                 // warm-up
+      cudaEventRecord(e0, c->s);
+      for (int r = 0; r < reps; ++r) launch();
+      cudaEventRecord(e1, c->s);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaMemcpyAsync(H.uf, save, sizeof(float) * H.ncell, cudaMemcpyDeviceToDevice, c->s);
+      return ms;
+    };
+    const bool fixed2 = l == 0 && fuse_defect(c);
+    const int plist[4] = {1, 2, 4, 8}, blist[4] = {32, 64, 128, 256};
+    float best = INFINITY;
+    int bp = 0, bb = 0;
+    for (int pl : plist) {
+      if (fixed2 && pl != 2) continue;
+      if (pl > 1 && (F.dim < 3 || F.n2 < 2 * pl)) continue;
+      for (int bx : blist) {
+        if (pl > 1 && bx > 128) continue;
+        const float ms = time_it([&] {
+          rich::sweep32(F, P, model, 0, pl, c->s, bx);
+          rich::sweep32(F, P, model, 1, pl, c->s, bx);
+        });
+        if (ms < best) { best = ms; bp = pl; bb = bx; }
+      }
+    }
+    float bestr = INFINITY;
+    int br = 0;
+    for (int bx : blist) {
+      const float ms = time_it([&] { rich::residual32(F, P, model, nullptr, c->s, bx); });
+      if (ms < bestr) { bestr = ms; br = bx; }
+    }
+    c->tune_planes[l] = bp;
+    c->tune_bx[l] = bb;
+    c->tune_rbx[l] = br;
+    cudaMemcpyAsync(H.df, save + H.ncell, sizeof(float) * H.ncell, cudaMemcpyDeviceToDevice, c->s);
+    cudaFreeAsync(save, c->s);
+    if (cudaGetLastError() != cudaSuccess) st = fail(c, RICH_ECUDA, "autotune: a candidate launch failed");
+  }
+  cudaStreamSynchronize(c->s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int l = 0; l < c->nlev; ++l) {
+    if (planes_out) planes_out[l] = planes_at(c, l);
+    if (bx_out) bx_out[l] = c->tune_bx[l];
+    if (rbx_out) rbx_out[l] = c->tune_rbx[l];
+  }
+  return st;
+}
+
+richards_status richards_batcher_create(void* stream, int max_contexts, richards_batcher** out) {
+  if (!out || max_contexts < 1 || max_contexts > 4096) return RICH_EINVAL;
+  *out = nullptr;
+  richards_batcher* b = new richards_batcher();
+  b->s = (cudaStream_t)stream;
+  b->cap = max_contexts;
+  const size_t bytes = sizeof(rich::BJob32) * (size_t)max_contexts * MAXLEV;
+  if (cudaMalloc((void**)&b->dtable, bytes) != cudaSuccess ||
+      cudaMallocHost((void**)&b->htable, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    richards_batcher_destroy(b);
+    return RICH_ENOMEM;
+  }
+  *out = b;
+  return RICH_OK;
+}
+
+void richards_batcher_destroy(richards_batcher* b) {
+  if (!b) return;
+  if (b->s) cudaStreamSynchronize(b->s); else cudaDeviceSynchronize();
+  if (b->dtable) cudaFree(b->dtable);
+  if (b->htable) cudaFreeHost(b->htable);
+  delete b;
+}
+
+const char* richards_batcher_last_error(const richards_batcher* b) { return b ? b->err.c_str() : "null batcher"; }
+
+richards_status richards_batcher_step(richards_batcher* b, richards_ctx* const* ctxs, int n, const double* dt,
+                                      const int* scheme, richards_status* status, richards_step_info* info) {
+  if (!b || !ctxs || !dt || !scheme || n < 1) return RICH_EINVAL;
+  if (n > b->cap) return bfail(b, RICH_EINVAL, "more contexts than the batcher holds");
+  const richards_opts* o0 = ctxs[0] ? &ctxs[0]->opts : nullptr;
+  for (int k = 0; k < n; ++k) {
+    const richards_ctx* c = ctxs[k];
+    if (!c || !o0) return bfail(b, RICH_EINVAL, "null context");
+    for (int q = 0; q < k; ++q)
+      if (ctxs[q] == c) return bfail(b, RICH_EINVAL, "a context appears twice");
+    if (c->busy.load()) return bfail(b, RICH_EBUSY, "context busy: a batch is running on it");
+    const richards_opts& o = c->opts;
+    if (o.precision < 1 || o.ordering != 1 || o.fmg_cycles != 0)
+      return bfail(b, RICH_EINVAL, "batched steps need mixed precision, red-black sweeps and no FMG start");
+    if (o.nu1 != o0->nu1 || o.nu2 != o0->nu2 || o.cycle_gamma != o0->cycle_gamma ||
+        o.gamma_levels != o0->gamma_levels || o.coarse_max_sweeps != o0->coarse_max_sweeps ||
+        o.coarse_rtol != o0->coarse_rtol || o.inner_cycles != o0->inner_cycles)
+      return bfail(b, RICH_EINVAL, "batched contexts must share the cycle options");
+    if (!(dt[k] > 0.0) || !std::isfinite(dt[k]) || (scheme[k] != 1 && scheme[k] != 2))
+      return bfail(b, RICH_EINVAL, "bad dt or scheme");
+  }
+  std::vector<BatchCtx> B(n);
+  for (int k = 0; k < n; ++k) {
+    richards_ctx* c = ctxs[k];
+    B[k].c = c;
+    B[k].slot = k;
+    B[k].own = c->s;
+    c->busy.store(1);
+    cudaStreamSynchronize(c->s);               // earlier work of the context is done
+    c->s = b->s;
+  }
+  richards_status st = RICH_OK;
+  for (int k = 0; k < n; ++k) {
+    richards_ctx* c = B[k].c;
+    c->updates_host = 0;
+    cudaMemsetAsync(c->scratch + 16, 0, sizeof(unsigned long long), b->s);
+    B[k].st = do_prepare(c, dt[k], scheme[k]);
+    B[k].ok = B[k].st == RICH_OK;
+    B[k].predicted = c->opts.predictor == 1 && c->scheme_used == 2;
+  }
+  st = batch_step_impl(b, B, dt, scheme);
+  for (int k = 0; k < n; ++k) {
+    BatchCtx& X = B[k];
+    richards_ctx* c = X.c;
+    richards_status sk = st != RICH_OK ? st : X.st;
+    if (st == RICH_OK && X.ok) {
+      long long tu = 0;
+      richards_step_info inf{};
+      sk = read_stats(c, &tu);
+      inf.cycles = X.inner;
+      inf.outer_iters = X.outer;
+      inf.scheme_used = c->scheme_used;
+      inf.resid0 = X.r0;
+      inf.resid = X.r;
+      inf.cell_updates = c->updates_host + tu;
+      const bool moved = X.outer > 0 || X.predicted;
+      if (sk == RICH_OK)
+        sk = water_balance(c, X.r, &inf, moved ? c->th_cur : c->th_n, c->th_n, c->th_nm1_valid ? c->th_nm1 : nullptr);
+      if (sk == RICH_OK) sk = finish_step(c, X.r, X.st, moved ? 1 : 0);
+      if (info) info[k] = inf;
+    } else if (info) {
+      info[k] = richards_step_info{};
+    }
+    if (status) status[k] = sk;
+    c->s = X.own;
+    c->busy.store(0);
+  }
+  return st;
 }
 
 long long richards_device_bytes(const richards_grid* grid, const richards_opts* opts, int soil_fields, int sink) {

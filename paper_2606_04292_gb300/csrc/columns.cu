@@ -16,6 +16,7 @@
 
 #include "kernels.cuh"
 #include "richards.h"
+#include "validate.h"
 
 namespace rich {
 namespace {
@@ -44,6 +45,7 @@ struct ColArgs {
   double* st_resid;
   unsigned long long* st_updates;
   int sink;
+  int fp64;                        // outer layer: 1 FP64 (precision 2), 0 float-float
   double h1, h2, h3, h4, xi, kappa, tol, inner_rtol, crtol, dt;
   int newton_k, max_outer, inner_cycles, nu1, nu2, cmax, gamma, gamma_levels, coarsest_max_n, scheme, nsteps,
       model;
@@ -191,8 +193,31 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
     const DDPhys Q = make_ddphys_dev(P64);
     const dd Ks = dd_split(D.Ks);
     const dd hist_scale = dd_split(scheme == 1 ? 1.0 / A.dt : 1.0 / (2.0 * A.dt));
-    // ---- per-step preparation (float-float): lagged K, history, u = psi^n
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    // ---- per-step preparation (float-float, or FP64 with the FP64 outer
+    // layer): lagged K, history, u = psi^n
+    for (int i = threadIdx.x; i < n && A.fp64; i += blockDim.x) {
+      const double pnd = psin[i];
+      double th;
+      if (th_valid) {
+        th = thn[i];
+      } else {
+        th = theta_only_d<MODEL>(pnd, D.p1, D.p2, P64);
+        thn[i] = th;
+      }
+      double ps, hist;
+      if (scheme == 1) {
+        ps = pnd;
+        hist = th / A.dt;
+      } else {
+        const double pm = psinm1[i];
+        ps = 2.0 * pnd - pm;
+        hist = (4.0 * th - theta_only_d<MODEL>(pm, D.p1, D.p2, P64)) / (2.0 * A.dt);
+      }
+      A.Kc[off + i] = cond_d<MODEL>(ps, D.p1, D.p2, D.Ks, P64);
+      G.g[i] = hist + A.xi * ps;
+      G.u[i] = pnd;
+    }
+    for (int i = threadIdx.x; i < n && !A.fp64; i += blockDim.x) {
       const double pnd = psin[i];
       const dd pn = dd_split(pnd);
       dd th;
@@ -257,9 +282,42 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
     const dd db0 = dd_mul(dd_split(kb64[0]), s2), db1 = dd_mul(dd_split(kb64[1]), s2);
     int outer = 0;
     bool fresh = false;
+    // the FP64 outer layer's deciding defect: the expression of the grid
+    // path's FP64 defect (interior fluxes in difference form), theta(u) kept
+    // for the history when u moved
+    auto defect64 = [&]() -> double {
+      unsigned long long mx = 0;
+      const double ih2 = 1.0 / (h * h), hs2 = 0.5 * ih2;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double ui = G.u[i], Ki = G.Kc[i];
+        double flux = 0.0, db = 0.0;
+        if (i > 0) flux += (Ki + G.Kc[i - 1]) * hs2 * (ui - G.u[i - 1]);
+        else db += 2.0 * kb64[0] * ih2;
+        if (i + 1 < n) flux += (Ki + G.Kc[i + 1]) * hs2 * (ui - G.u[i + 1]);
+        else db += 2.0 * kb64[1] * ih2;
+        double th;
+        if (outer == 0) {
+          th = thn[i];
+        } else {
+          th = theta_only_d<MODEL>(ui, D.p1, D.p2, P64);
+          thcur[i] = th;
+        }
+        double S, dS;
+        sink_direct(ui, G.smax ? G.smax[i] : 0.0, P64, S, dS);
+        const double di = G.g[i] - ((a * th + S) + (A.xi + db) * ui + flux);
+        Ls[0].g[i] = (float)di;
+        const_cast<float*>(Ls[0].psi0)[i] = (float)ui;
+        Ls[0].u[i] = 0.0f;
+        const unsigned long long b = nbits(di);
+        mx = b > mx ? b : mx;
+      }
+      return __longlong_as_double((long long)block_max(mx, sm));
+    };
+    bool use64 = false;                  // (the grid path's hand-over to FP64 defects)
+    double r_ff = INFINITY;
     for (;;) {
       unsigned long long mx = 0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      for (int i = threadIdx.x; i < n && !use64; i += blockDim.x) {
         const dd ui = dd_split(G.u[i]), Ki = dd_split(G.Kc[i]);
         dd flux = mk(0.0f), db = mk(0.0f);
         if (i > 0)
@@ -275,7 +333,7 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
           th = dd_split(thn[i]);
         } else {
           th = theta_x<MODEL>(ui, Q.p1, Q.p2, Q, P64);
-          thcur[i] = dd_join(th);
+          if (!A.fp64) thcur[i] = dd_join(th);     // (FP64 outer: from the FP64 defect)
         }
         const dd S = G.smax ? sink_x(ui, dd_split(G.smax[i]), Q) : mk(0.0f);
         dd N = dd_add(dd_mul(Q.a, th), S);
@@ -289,8 +347,18 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
         mx = b > mx ? b : mx;
       }
       fresh = outer > 0;
-      const double nrm = (double)__uint_as_float((unsigned)block_max(mx, sm));
-      resid = teff * nrm;
+      double nrm = 0.0;
+      if (!use64) {
+        nrm = (double)__uint_as_float((unsigned)block_max(mx, sm));
+        resid = teff * nrm;
+        const double prev = r_ff;
+        r_ff = resid;
+        use64 = A.fp64 && !isnan(resid) && (!(resid > A.tol) || outer >= A.max_outer || resid > 0.5 * prev);
+      }
+      if (use64) {
+        nrm = defect64();                     // the FP64 defect decides
+        resid = teff * nrm;
+      }
       if (!(resid > A.tol) || isnan(resid)) break;
       if (outer >= A.max_outer) { status = RICH_ENOCONV; break; }
       for (int l = 0; l + 1 < nl; ++l) {
@@ -422,6 +490,7 @@ richards_status launch_columns(richards_columns* c, double dt, int nsteps, int s
   A.inner_cycles = o.inner_cycles; A.nu1 = o.nu1; A.nu2 = o.nu2; A.cmax = o.coarse_max_sweeps;
   A.gamma = o.cycle_gamma; A.gamma_levels = o.gamma_levels; A.coarsest_max_n = o.coarsest_max_n;
   A.scheme = scheme; A.nsteps = nsteps; A.model = c->model;
+  A.fp64 = o.precision == 2 ? 1 : 0;
   const size_t smem = column_smem(c->max_n, o.coarsest_max_n);
   auto kern = c->model == HAVERKAMP ? k_columns<HAVERKAMP> : (c->model == GARDNER ? k_columns<GARDNER>
                                                                                   : k_columns<VANGENUCHTEN>);
@@ -453,11 +522,9 @@ richards_status richards_columns_create(int ncol, const richards_column* cols, c
   if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max_sweeps < 1 || o.coarsest_max_n < 1 || !(o.tol > 0.0) ||
       o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) || o.ordering != 1 ||
       !(o.xi >= 0.0) || !(o.kappa >= 0.0) || o.inner_cycles < 1 || o.max_outer < 0 || o.cycle_gamma < 1 ||
-      o.cycle_gamma > 3 || o.gamma_levels < 0)
+      o.cycle_gamma > 3 || o.gamma_levels < 0 || o.precision < 0 || o.precision > 2)
     return RICH_EINVAL;
-  if (sink->enabled && !(sink->h4 < sink->h3 && sink->h3 <= sink->h2 && sink->h2 < sink->h1 &&
-                         sink->root_decay > 0.0 && sink->root_depth > 0.0 && sink->Tp >= 0.0))
-    return RICH_EINVAL;
+  if (rich::sink_error(*sink)) return RICH_EINVAL;
   const int model = cols[0].soil.model;
   std::vector<ColDesc> hc(ncol);
   long long off = 0;
@@ -466,10 +533,8 @@ richards_status richards_columns_create(int ncol, const richards_column* cols, c
     const richards_column& q = cols[k];
     const richards_soil& s = q.soil;
     if (q.n < 1 || q.n > RICHARDS_COLUMN_MAX_CELLS || !(q.L > 0.0) || s.model != model) return RICH_EINVAL;
-    if (!(s.Ks > 0.0) || !(s.theta_s > s.theta_r) || !(s.theta_r >= 0.0)) return RICH_EINVAL;
-    if (model == RICH_VANGENUCHTEN && !(s.p1 > 0.0 && s.p2 > 1.0)) return RICH_EINVAL;
-    if (model == RICH_GARDNER && !(s.p1 > 0.0)) return RICH_EINVAL;
-    if (model == RICH_HAVERKAMP && !(s.p1 > 0.0 && s.p2 > 0.0 && s.p3 > 0.0 && s.p4 > 0.0)) return RICH_EINVAL;
+    if (rich::law_error(s.model, s.Ks, s.theta_s, s.theta_r, s.p1, s.p2, s.p3, s.p4, false, false))
+      return RICH_EINVAL;
     for (int f = 0; f < 2; ++f) {
       if (q.bc_kind[f] < 0 || q.bc_kind[f] > 3 || !std::isfinite(q.bc_value[f])) return RICH_EINVAL;
       if (q.bc_kind[f] == RICH_BC_FREE_DRAINAGE && f != 0) return RICH_EINVAL;

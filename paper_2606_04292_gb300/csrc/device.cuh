@@ -287,17 +287,22 @@ __device__ __forceinline__ float fast_expm1(float x) {
   return __expf(x) - 1.0f;
 }
 
-// x^y for x > 0 through the hardware approximations
-__device__ __forceinline__ float fast_pow(float x, float y) { return __expf(y * __logf(x)); }
-
 // Same increments as dlaw_f, built from the fast pieces above, split into
 // the part that depends on psi0 only (once per point update) and the part
 // that depends on the correction x (once per Newton step).
 struct DBase {
   float psi0, inv_psi0;
   bool wet0;
-  float a0, b0, c0;      // VG: t0, log1p(t0), Se0; Haverkamp: u0; Gardner: e0
+  float a0, b0, c0;      // VG: t0, log1p(t0), Se0; Haverkamp: u0, log(u0); Gardner: e0
 };
+
+// Largest exponent a power t = (alpha h)^n or u = h^beta of a trial state may
+// reach (e^80 ~ 5.5e34, below FLT_MAX with room for 1 + t and products).  A
+// bracketed point solve on a coarse level with a tiny coupling can probe
+// heads of -1e6 m and beyond, where the power would overflow and its ratios
+// turn into inf/inf; there theta = theta_r and theta' = 0 to far below FP32
+// resolution either way, so capping the exponent changes nothing else.
+constexpr float POW_EXP_MAX = 80.0f;
 
 template <int MODEL>
 __device__ __forceinline__ DBase dbase(float psi0, float p1, float p2) {
@@ -310,10 +315,12 @@ __device__ __forceinline__ DBase dbase(float psi0, float p1, float p2) {
     if (MODEL == GARDNER) {
       B.a0 = __expf(p1 * psi0);
     } else if (MODEL == HAVERKAMP) {
-      B.a0 = fast_pow(-psi0, p2);
+      const float lu = fminf(p2 * __logf(-psi0), POW_EXP_MAX);   // h0^beta through the hardware log/exp
+      B.a0 = __expf(lu);
+      B.b0 = lu;
     } else {
       const float m = 1.0f - __fdividef(1.0f, p2);
-      B.a0 = fast_pow(p1 * -psi0, p2);
+      B.a0 = __expf(fminf(p2 * __logf(p1 * -psi0), POW_EXP_MAX));   // (alpha h0)^n
       B.b0 = fast_log1p(B.a0);
       B.c0 = __expf(-m * B.b0);
     }
@@ -350,7 +357,10 @@ __device__ __forceinline__ void dincr(const DBase& B, float x, float p1, float p
     if (!B.wet0) {
       const float u0 = B.a0;
       if (!wet1) {
-        const float du = u0 * fast_expm1(be * fast_log1p(x * B.inv_psi0));
+        // (u1 = u0 (psi1/psi0)^beta, its exponent capped as in dbase)
+        // (psi1/psi0 > 0 here; its rounded value is kept above 2^-24)
+        const float q = fmaxf(x * B.inv_psi0, -0.99999994f);
+        const float du = u0 * fast_expm1(fminf(be * fast_log1p(q), POW_EXP_MAX - B.b0));
         const float u1 = u0 + du, h1 = -psi1;
         const float den1 = al + u1;
         Dth = __fdividef(-al * ds * du, (al + u0) * den1);
@@ -361,7 +371,7 @@ __device__ __forceinline__ void dincr(const DBase& B, float x, float p1, float p
       }
     } else if (!wet1) {
       const float h1 = -psi1;
-      const float u1 = fast_pow(h1, be);
+      const float u1 = __expf(fminf(be * __logf(h1), POW_EXP_MAX));
       const float den1 = al + u1;
       Dth = __fdividef(-ds * u1, den1);
       dth = __fdividef(al * ds * be * __fdividef(u1, h1), den1 * den1);
@@ -373,7 +383,9 @@ __device__ __forceinline__ void dincr(const DBase& B, float x, float p1, float p
     if (!B.wet0) {
       const float t0 = B.a0, L0 = B.b0, Se0 = B.c0;
       if (!wet1) {
-        const float dt = t0 * fast_expm1(n * fast_log1p(x * B.inv_psi0));
+        // (t1 = t0 (psi1/psi0)^n, its exponent capped as in dbase)
+        const float q = fmaxf(x * B.inv_psi0, -0.99999994f);     // (as for Haverkamp)
+        const float dt = t0 * fast_expm1(fminf(n * fast_log1p(q), POW_EXP_MAX - B.b0));
         const float t1 = t0 + dt;
         const float dSe = Se0 * fast_expm1(-m * fast_log1p(__fdividef(dt, 1.0f + t0)));
         const float Se1 = Se0 + dSe;
@@ -385,7 +397,7 @@ __device__ __forceinline__ void dincr(const DBase& B, float x, float p1, float p
       }
     } else if (!wet1) {
       const float h1 = -psi1;
-      const float t1 = fast_pow(al * h1, n);
+      const float t1 = __expf(fminf(n * __logf(al * h1), POW_EXP_MAX));
       const float L1 = fast_log1p(t1);
       Dth = ds * fast_expm1(-m * L1);
       dth = ds * m * n * __fdividef(t1, h1) * __fdividef(__expf(-m * L1), 1.0f + t1);
@@ -527,6 +539,14 @@ __device__ __forceinline__ void storage(T x, T psi0, T p1, T p2, T smax, const P
 // bisection whenever a step leaves the current bracket.
 // NK > 0: exactly NK steps fixed at compile time (must equal P.newton_k);
 // NK = 0: P.newton_k steps (0: to round-off).
+// FP32 increment form with a fixed step count: a solve does not end on a
+// bisection.  Where the coupling is tiny (dry cells of a steep law on a
+// coarse level) the bracket spans millions of metres and its midpoint is no
+// estimate of the root; after a bisection up to BISECT_EXTRA further steps
+// run until one is a Newton step inside the bracket.  Solves that never
+// bisect take exactly the fixed count, as before.
+constexpr int BISECT_EXTRA = 12;
+
 template <typename T, int FORM, int MODEL, int NK = 0>
 __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T smax,
                                          const Phys<T>& P) {
@@ -558,8 +578,10 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
     B = dbase<MODEL>(psi0, p1, p2);
     if (P.sink && smax > T(0)) sk0 = feddes(psi0, P, sa0, sda0);
   }
-#pragma unroll(NK > 0 ? NK : 1)
-  for (int it = 0; it < maxit; ++it) {
+  // one safeguarded step; returns true when the solve is done.  *bis: the
+  // step was a bisection
+  auto step = [&](bool* bis) -> bool {
+    *bis = false;
     T val, der;
     if constexpr (FORM == FORM_DELTA) {
       float Dth, dth;
@@ -578,7 +600,7 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
     }
     const T F = val + cc * x - f;
     const T dF = der + cc;
-    if (F == T(0)) break;
+    if (F == T(0)) return true;
     if (F > T(0)) hi = x; else lo = x;
     T xn;
     if constexpr (sizeof(T) == 4) xn = x - __fdividef(F, dF);    // dF > 0; a 2-ulp step error is harmless
@@ -586,15 +608,29 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
     // a step strictly inside the bracket, or below round-off, is kept;
     // anything else (outside, or onto an end) is replaced by bisection
     const T tiny = tol_of<T>() * (fabs(x) > T(1) ? fabs(x) : T(1));
-    if (!(xn > lo && xn < hi) && !(fabs(xn - x) <= tiny)) xn = T(0.5) * (lo + hi);
-    const T step = fabs(xn - x);
+    if (!(xn > lo && xn < hi) && !(fabs(xn - x) <= tiny)) {
+      xn = T(0.5) * (lo + hi);
+      *bis = true;
+    }
+    const T stp = fabs(xn - x);
     x = xn;
-    if (P.newton_k <= 0 && step <= tiny) break;
+    if (P.newton_k <= 0 && stp <= tiny) return true;
     // FP32 increment form: a step below 2^-20 of |x| leaves nothing for the
     // next one to change at this precision (quadratic convergence)
     if constexpr (FORM == FORM_DELTA) {
-      if (step <= 9.5367431640625e-7f * fabsf(x)) break;
+      if (stp <= 9.5367431640625e-7f * fabsf(x)) return true;
     }
+    return false;
+  };
+  bool bis = false, done = false;
+#pragma unroll(NK > 0 ? NK : 1)
+  for (int it = 0; it < maxit; ++it) {
+    if (step(&bis)) { done = true; break; }
+  }
+  if constexpr (FORM == FORM_DELTA) {
+    if (P.newton_k > 0 && !done)
+      for (int e = 0; e < BISECT_EXTRA && bis; ++e)
+        if (step(&bis)) break;
   }
   return x;
 }

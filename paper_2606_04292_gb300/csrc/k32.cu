@@ -5,8 +5,8 @@
 namespace rich {
 using D = Dispatch<float, FORM_DELTA>;
 void residual32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,
-                cudaStream_t s) {
-  D::residual(L, P, model, norm, s);
+                cudaStream_t s, int bx) {
+  D::residual(L, P, model, norm, s, bx);
 }
 void tau32(const Level<float>& C, const Phys<float>& P, int model, cudaStream_t s) { D::tau(C, P, model, s); }
 void restrict32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, const float* fa,

@@ -4,8 +4,9 @@
 
 namespace rich {
 using D = Dispatch<float, FORM_DELTA>;
-void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, int planes, cudaStream_t s) {
-  D::sweep_pipe(L, P, model, color, planes, s);
+void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, int planes, cudaStream_t s,
+             int bx) {
+  D::sweep_pipe(L, P, model, color, planes, s, bx);
 }
 bool resid_fusable32(const Level<float>& L, int planes) { return D::fusable(L, planes); }
 void sweep_resid32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,

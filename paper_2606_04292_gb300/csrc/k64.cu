@@ -369,12 +369,14 @@ __global__ void __launch_bounds__(128) k_outer_residual_dd(Level<double> L, Phys
 }
 
 // The same defect in FP64 (the FP64-outer mixed mode's accepting defect and
-// stop test): d = g - N(u) with the expression of the FP64 grid residual
-// (eq. Nh-def: a theta(u) + S(u) + xi u + m_ii u - sum_j m_ij u_j), theta in
-// FP64 from th_in when given (u = psi^n), else evaluated and kept in th_out
-// (nullable) for the next step's history.  Hands the FP32 inner problem r32,
-// psi0 and a zero correction like k_outer_residual_dd; ||d||_inf accumulates
-// as FP64 bits.
+// stop test): d = g - N(u) (eq. Nh-def) with the interior fluxes in
+// difference form m_f (u_i - u_j), as k_outer_residual_dd takes them -- the
+// form m_ii u_i - sum_j m_ij u_j of the grid residual would cancel the large
+// diagonal of a fine, conductive level (terms ~1e5 in theta units) down to
+// rounding above a tight tolerance.  theta in FP64 from th_in when given
+// (u = psi^n), else evaluated and kept in th_out (nullable) for the next
+// step's history.  Hands the FP32 inner problem r32, psi0 and a zero
+// correction like k_outer_residual_dd; ||d||_inf accumulates as FP64 bits.
 template <int MODEL>
 __global__ void __launch_bounds__(256) k_outer_residual64(Level<double> L, Phys<double> P, float* r32, float* psi0f,
                                                           float* delta, unsigned long long* norm,
@@ -385,11 +387,26 @@ __global__ void __launch_bounds__(256) k_outer_residual64(Level<double> L, Phys<
   const int i1 = blockIdx.y, i2 = blockIdx.z;
   if (i0 < L.n0) {
     const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
-    const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && i2 > 0 && i2 < L.n2 - 1;
-    double mii, off;
-    if (yzi) stencil<double, true>(L, i, i0, i1, i2, L.u, mii, off);
-    else stencil<double, false>(L, i, i0, i1, i2, L.u, mii, off);
-    const double ui = L.u[i];
+    const double* __restrict__ u = L.u;
+    const double* __restrict__ K = L.Kc;
+    const double ui = u[i], Ki = K[i];
+    double flux = 0.0, db = 0.0;
+    const int nn[3] = {L.n0, L.n1, L.n2};
+    const int ii[3] = {i0, i1, i2};
+    const long long st[3] = {1, L.n0, (long long)L.n0 * L.n1};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= L.dim) break;
+      const double s = L.ih2[a], hs = 0.5 * s;
+      long long fc;
+      if (a == 0) fc = i1 + (long long)L.n1 * i2;
+      else if (a == 1) fc = i0 + (long long)L.n0 * i2;
+      else fc = i0 + (long long)L.n0 * i1;
+      if (ii[a] > 0) flux += (Ki + K[i - st[a]]) * hs * (ui - u[i - st[a]]);
+      else db += 2.0 * L.kb[2 * a][fc] * s;
+      if (ii[a] < nn[a] - 1) flux += (Ki + K[i + st[a]]) * hs * (ui - u[i + st[a]]);
+      else db += 2.0 * L.kb[2 * a + 1][fc] * s;
+    }
     double th;
     if (th_in) {
       th = th_in[i];
@@ -402,7 +419,7 @@ __global__ void __launch_bounds__(256) k_outer_residual64(Level<double> L, Phys<
     }
     double S, dS;
     sink_direct(ui, L.smax ? L.smax[i] : 0.0, P, S, dS);
-    const double di = L.g[i] - ((P.a * th + S) + P.xi * ui + mii * ui - off);
+    const double di = L.g[i] - ((P.a * th + S) + (P.xi + db) * ui + flux);
     r32[i] = (float)di;
     psi0f[i] = (float)ui;
     delta[i] = 0.0f;

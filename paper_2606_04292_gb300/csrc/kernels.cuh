@@ -25,14 +25,21 @@ __device__ __forceinline__ float from_bits<float>(unsigned long long b) {
 // colour; cells of one colour do not couple, so the update is parallel).
 // ---------------------------------------------------------------------------
 // Launch grid: x = pairs of cells along a row, y = row, z = plane.
+// (The bodies of the grid kernels take the block's coordinates explicitly:
+// the batched kernels run the same bodies for the blocks of many grids.)
 template <typename T, int FORM, int MODEL, int NK = 0>
-__global__ void __launch_bounds__(256) k_sweep(Level<T> L, Phys<T> P, int color) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y, i2 = blockIdx.z;
+__device__ __forceinline__ void sweep_body(const Level<T>& L, const Phys<T>& P, int color, int bx, int by, int bz) {
+  const int p = bx * blockDim.x + threadIdx.x;
+  const int i1 = by, i2 = bz;
   const int i0 = 2 * p + ((color + i1 + i2) & 1);
   if (i0 >= L.n0) return;
   const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
   point_update<T, FORM, MODEL, NK>(L, P, i, i0, i1, i2);
+}
+
+template <typename T, int FORM, int MODEL, int NK = 0>
+__global__ void __launch_bounds__(256) k_sweep(Level<T> L, Phys<T> P, int color) {
+  sweep_body<T, FORM, MODEL, NK>(L, P, color, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // The same half-sweep with ZC planes per thread, software-pipelined: the
@@ -141,21 +148,26 @@ __global__ void __launch_bounds__(128) k_sweep_plane(Level<T> L, Phys<T> P, int 
 
 // d = g - N(u) on a level, with ||d||_inf accumulated into *norm (bit max).
 // Launch grid: x = cells along a row, y = row, z = plane.
+// (returns |d| of the thread's cell as bits, 0 without one)
+template <typename T, int FORM, int MODEL>
+__device__ __forceinline__ unsigned long long residual_body(const Level<T>& L, const Phys<T>& P, int bx, int by,
+                                                            int bz) {
+  const int i0 = bx * blockDim.x + threadIdx.x;
+  const int i1 = by, i2 = bz;
+  if (i0 >= L.n0) return 0;
+  const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
+  // rows away from the y/z boundaries skip those tests (uniform over the block)
+  const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && i2 > 0 && i2 < L.n2 - 1;
+  const T di = L.g[i] - (yzi ? apply_N<T, FORM, MODEL, true>(L, P, L.u, i, i0, i1, i2)
+                             : apply_N<T, FORM, MODEL, false>(L, P, L.u, i, i0, i1, i2));
+  L.d[i] = di;
+  return nbits(di);
+}
+
 template <typename T, int FORM, int MODEL>
 __global__ void __launch_bounds__(256) k_residual(Level<T> L, Phys<T> P, unsigned long long* norm) {
   __shared__ unsigned long long sm[33];
-  unsigned long long mx = 0;
-  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y, i2 = blockIdx.z;
-  if (i0 < L.n0) {
-    const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
-    // rows away from the y/z boundaries skip those tests (uniform over the block)
-    const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && i2 > 0 && i2 < L.n2 - 1;
-    const T di = L.g[i] - (yzi ? apply_N<T, FORM, MODEL, true>(L, P, L.u, i, i0, i1, i2)
-                               : apply_N<T, FORM, MODEL, false>(L, P, L.u, i, i0, i1, i2));
-    L.d[i] = di;
-    mx = nbits(di);
-  }
+  unsigned long long mx = residual_body<T, FORM, MODEL>(L, P, blockIdx.x, blockIdx.y, blockIdx.z);
   if (norm) {
     mx = block_max(mx, sm);
     if (threadIdx.x == 0) atomicMax(norm, mx);
@@ -164,21 +176,27 @@ __global__ void __launch_bounds__(256) k_residual(Level<T> L, Phys<T> P, unsigne
 
 // FAS step 3: psi_bar_H = R psi_h, d_H = R d_h (cb may be null).
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict(Level<T> F, Level<T> C, Xfer<T> X, const T* fa, const T* fb,
-                                                  T* ca, T* cb) {
-  const int J0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J1 = blockIdx.y, J2 = blockIdx.z;
+__device__ __forceinline__ void restrict_body(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, const T* fa,
+                                              const T* fb, T* ca, T* cb, int bx, int by, int bz) {
+  const int J0 = bx * blockDim.x + threadIdx.x;
+  const int J1 = by, J2 = bz;
   if (J0 >= C.n0) return;
   const long long J = J0 + (long long)C.n0 * (J1 + C.n1 * J2);
   ca[J] = restrict_at(F, X, fa, J0, J1, J2);
   if (cb) cb[J] = restrict_at(F, X, fb, J0, J1, J2);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(Level<T> F, Level<T> C, Xfer<T> X, const T* fa, const T* fb,
+                                                  T* ca, T* cb) {
+  restrict_body<T>(F, C, X, fa, fb, ca, cb, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // FAS step 4 on the coarse level: g_H = N_H(psi_bar_H) + d_H, psi_H = psi_bar_H.
 template <typename T, int FORM, int MODEL>
-__global__ void __launch_bounds__(256) k_tau(Level<T> C, Phys<T> P) {
-  const int J0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J1 = blockIdx.y, J2 = blockIdx.z;
+__device__ __forceinline__ void tau_body(const Level<T>& C, const Phys<T>& P, int bx, int by, int bz) {
+  const int J0 = bx * blockDim.x + threadIdx.x;
+  const int J1 = by, J2 = bz;
   if (J0 >= C.n0) return;
   const long long J = J0 + (long long)C.n0 * (J1 + C.n1 * J2);
   // rows away from the y/z boundaries skip those tests (uniform over the block)
@@ -188,14 +206,25 @@ __global__ void __launch_bounds__(256) k_tau(Level<T> C, Phys<T> P) {
   C.u[J] = C.ubar[J];
 }
 
+template <typename T, int FORM, int MODEL>
+__global__ void __launch_bounds__(256) k_tau(Level<T> C, Phys<T> P) {
+  tau_body<T, FORM, MODEL>(C, P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // FAS step 6: u_h += P (u_H - psi_bar_H).
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong(Level<T> F, Level<T> C, Xfer<T> X) {
-  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y, i2 = blockIdx.z;
+__device__ __forceinline__ void prolong_body(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, int bx, int by,
+                                             int bz) {
+  const int i0 = bx * blockDim.x + threadIdx.x;
+  const int i1 = by, i2 = bz;
   if (i0 >= F.n0) return;
   const long long i = i0 + (long long)F.n0 * (i1 + F.n1 * i2);
   F.u[i] += prolong_at(C, X, i0, i1, i2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong(Level<T> F, Level<T> C, Xfer<T> X) {
+  prolong_body<T>(F, C, X, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -227,10 +256,10 @@ __device__ __forceinline__ void restrict_taps(int J, int nc, int nf, int* idx, T
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict_nested(Level<T> F, Level<T> C, const T* fa, const T* fb, T* ca,
-                                                         T* cb) {
-  const int J0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J1 = blockIdx.y, J2 = blockIdx.z;
+__device__ __forceinline__ void restrict_nested_body(const Level<T>& F, const Level<T>& C, const T* fa, const T* fb,
+                                                     T* ca, T* cb, int bx, int by, int bz) {
+  const int J0 = bx * blockDim.x + threadIdx.x;
+  const int J1 = by, J2 = bz;
   if (J0 >= C.n0) return;
   int x[4], y[4], z[4];
   T wx[4], wy[4], wz[4];
@@ -268,6 +297,12 @@ __global__ void __launch_bounds__(256) k_restrict_nested(Level<T> F, Level<T> C,
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_nested(Level<T> F, Level<T> C, const T* fa, const T* fb, T* ca,
+                                                         T* cb) {
+  restrict_nested_body<T>(F, C, fa, fb, ca, cb, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T>
 __device__ __forceinline__ void prolong_taps(const Xfer<T>& X, int a, int i, int nf, int* j, T* w) {
   if (i > 0 && i < nf - 1) {
     const int J = i >> 1;
@@ -285,9 +320,10 @@ __device__ __forceinline__ void prolong_taps(const Xfer<T>& X, int a, int i, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong_nested(Level<T> F, Level<T> C, Xfer<T> X) {
-  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y, i2 = blockIdx.z;
+__device__ __forceinline__ void prolong_nested_body(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, int bx,
+                                                    int by, int bz) {
+  const int i0 = bx * blockDim.x + threadIdx.x;
+  const int i1 = by, i2 = bz;
   if (i0 >= F.n0) return;
   int jx[2], jy[2], jz[2];
   T wx[2], wy[2], wz[2];
@@ -312,6 +348,11 @@ __global__ void __launch_bounds__(256) k_prolong_nested(Level<T> F, Level<T> C, 
   }
   const unsigned i = (unsigned)(i0 + F.n0 * (i1 + F.n1 * i2));
   F.u[i] += s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_nested(Level<T> F, Level<T> C, Xfer<T> X) {
+  prolong_nested_body<T>(F, C, X, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -556,9 +597,11 @@ inline int grid_for(long long n, int bs = 256) {
 struct Launch3 {
   dim3 grid, block;
 };
-inline Launch3 launch3(int nx, int n1, int n2) {
+// (bx_force > 0: that block x-size, as the autotuner chose it)
+inline Launch3 launch3(int nx, int n1, int n2, int bx_force = 0) {
   int bx = 32;
   while (bx < nx && bx < 128) bx <<= 1;
+  if (bx_force > 0) bx = bx_force;
   Launch3 L;
   L.block = dim3(bx, 1, 1);
   L.grid = dim3((nx + bx - 1) / bx, n1, n2);
@@ -577,40 +620,44 @@ inline void by_model(int model, Fn&& fn) {
 template <typename T, int FORM>
 struct Dispatch {
   template <int NK>
-  static void sweep_nk(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
-    const Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
+  static void sweep_nk(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s, int bx = 0) {
+    const Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2, bx);
     by_model(model, [&](auto m) {
       k_sweep<T, FORM, decltype(m)::value, NK><<<g.grid, g.block, 0, s>>>(L, P, color);
     });
   }
   // the FP32 increment form compiles the common fixed step counts 1 and 2
-  static void sweep(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
-    if (FORM == FORM_DELTA && P.newton_k == 1) sweep_nk<(FORM == FORM_DELTA ? 1 : 0)>(L, P, model, color, s);
-    else if (FORM == FORM_DELTA && P.newton_k == 2) sweep_nk<(FORM == FORM_DELTA ? 2 : 0)>(L, P, model, color, s);
-    else sweep_nk<0>(L, P, model, color, s);
+  static void sweep(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s, int bx = 0) {
+    if (FORM == FORM_DELTA && P.newton_k == 1) sweep_nk<(FORM == FORM_DELTA ? 1 : 0)>(L, P, model, color, s, bx);
+    else if (FORM == FORM_DELTA && P.newton_k == 2)
+      sweep_nk<(FORM == FORM_DELTA ? 2 : 0)>(L, P, model, color, s, bx);
+    else sweep_nk<0>(L, P, model, color, s, bx);
   }
   template <int ZC, int NK>
-  static void sweep_pipe_zk(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
-    Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2);
+  static void sweep_pipe_zk(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s, int bx) {
+    Launch3 g = launch3((L.n0 + 1) >> 1, L.n1, L.n2, bx);
     g.grid.z = (L.n2 + ZC - 1) / ZC;
     by_model(model, [&](auto m) {
       k_sweep_pipe<T, FORM, decltype(m)::value, ZC, NK><<<g.grid, g.block, 0, s>>>(L, P, color, nullptr);
     });
   }
   template <int ZC>
-  static void sweep_pipe_z(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s) {
-    if (FORM == FORM_DELTA && P.newton_k == 1) sweep_pipe_zk<ZC, (FORM == FORM_DELTA ? 1 : 0)>(L, P, model, color, s);
+  static void sweep_pipe_z(const Level<T>& L, const Phys<T>& P, int model, int color, cudaStream_t s, int bx) {
+    if (FORM == FORM_DELTA && P.newton_k == 1)
+      sweep_pipe_zk<ZC, (FORM == FORM_DELTA ? 1 : 0)>(L, P, model, color, s, bx);
     else if (FORM == FORM_DELTA && P.newton_k == 2)
-      sweep_pipe_zk<ZC, (FORM == FORM_DELTA ? 2 : 0)>(L, P, model, color, s);
-    else sweep_pipe_zk<ZC, 0>(L, P, model, color, s);
+      sweep_pipe_zk<ZC, (FORM == FORM_DELTA ? 2 : 0)>(L, P, model, color, s, bx);
+    else sweep_pipe_zk<ZC, 0>(L, P, model, color, s, bx);
   }
-  // (levels below 2^20 cells keep one cell per thread: latency, not load
-  // throughput, bounds them)
-  static void sweep_pipe(const Level<T>& L, const Phys<T>& P, int model, int color, int planes, cudaStream_t s) {
-    if (planes <= 1 || L.n2 < 2 || L.ncell < (1LL << 20)) sweep(L, P, model, color, s);
-    else if (planes == 2) sweep_pipe_z<2>(L, P, model, color, s);
-    else if (planes == 4) sweep_pipe_z<4>(L, P, model, color, s);
-    else sweep_pipe_z<8>(L, P, model, color, s);
+  // (levels below 2^20 cells keep one cell per thread unless the autotuner
+  // chose otherwise (bx > 0): latency, not load throughput, bounds them.
+  // The pipelined kernels take blocks of at most 128 threads.)
+  static void sweep_pipe(const Level<T>& L, const Phys<T>& P, int model, int color, int planes, cudaStream_t s,
+                         int bx = 0) {
+    if (planes <= 1 || L.n2 < 2 || (bx == 0 && L.ncell < (1LL << 20))) sweep(L, P, model, color, s, bx);
+    else if (planes == 2) sweep_pipe_z<2>(L, P, model, color, s, bx > 128 ? 128 : bx);
+    else if (planes == 4) sweep_pipe_z<4>(L, P, model, color, s, bx > 128 ? 128 : bx);
+    else sweep_pipe_z<8>(L, P, model, color, s, bx > 128 ? 128 : bx);
   }
   // one lexicographic sweep: a launch per hyperplane, rows of the plane's
   // i2 range only
@@ -660,8 +707,8 @@ struct Dispatch {
     });
   }
   static void residual(const Level<T>& L, const Phys<T>& P, int model, unsigned long long* norm,
-                       cudaStream_t s) {
-    const Launch3 g = launch3(L.n0, L.n1, L.n2);
+                       cudaStream_t s, int bx = 0) {
+    const Launch3 g = launch3(L.n0, L.n1, L.n2, bx);
     by_model(model, [&](auto m) {
       k_residual<T, FORM, decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, norm);
     });

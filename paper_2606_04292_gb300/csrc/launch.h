@@ -39,9 +39,12 @@ void tail64(const Level<double>* dLs, const Xfer<double>* dXs, int l0, int nl, c
 void sweep_lex64(const Level<double>& L, const Phys<double>& P, int model, cudaStream_t s);
 
 // FP32, correction delta as unknown
-void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, int planes, cudaStream_t s);
+// (bx > 0: the block x-size and, for sweeps, the pipelined kernel below 2^20
+// cells too, as the autotuner chose them; 0: the defaults)
+void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, int planes, cudaStream_t s,
+             int bx = 0);
 void residual32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,
-                cudaStream_t s);
+                cudaStream_t s, int bx = 0);
 void tau32(const Level<float>& C, const Phys<float>& P, int model, cudaStream_t s);
 void restrict32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, const float* fa,
                 const float* fb, float* ca, float* cb, cudaStream_t s);
@@ -109,5 +112,49 @@ void flag_nonfinite(const double* x, long long n, unsigned* bad, cudaStream_t s)
 void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1, const double* p2,
                const uint8_t* mat, const Phys<double>& P, const DDPhys& Q, int model, bool dd, double* theta,
                double* K, cudaStream_t s);
+
+}  // namespace rich
+
+// ---------------------------------------------------------------------------
+// Batched FP32 inner cycles (batch.cu): one launch runs one stage of the
+// cycle on one level of every context in a list.  The device table holds a
+// descriptor per (context, level); a list names the descriptors of a launch
+// and the first block of each (blocks of BATCH_THREADS threads, laid out
+// per descriptor as the single-context launch lays out its grid).
+// ---------------------------------------------------------------------------
+namespace rich {
+
+constexpr int BATCH_THREADS = 128;
+constexpr int BATCH_MAX = 64;        // descriptors per launch
+
+struct BJob32 {
+  Level<float> F, C;                 // the level and the next coarser one (C unused on the coarsest)
+  Xfer<float> X;                     // transfers between them
+  Phys<float> P;
+  const Level<float>* dLs;           // the context's device level views (coarse tail)
+  const Xfer<float>* dXs;
+  int level, nlev;
+  unsigned long long* norm;          // the context's inner-norm slot (float bits)
+  unsigned long long* stats;         // the context's coarse-tail update counter
+};
+
+struct BList {
+  int n;
+  int job[BATCH_MAX];                // table index of each descriptor
+  int block0[BATCH_MAX + 1];         // first block of each; block0[n] = total
+};
+
+enum { BOP_SWEEP = 0, BOP_RESID = 1, BOP_RESTRICT = 2, BOP_TAU = 3, BOP_PROLONG = 4 };
+
+// blocks one descriptor takes for a stage
+int batch_blocks(int op, const BJob32& j);
+// one stage over the listed descriptors (all of one law and one fixed Newton
+// count nk: 1, 2, or 0 for P.newton_k); color for BOP_SWEEP; with_norm: the
+// defect's max into each descriptor's norm slot (BOP_RESID)
+void batch32(int op, int model, int nk, const BJob32* table, const BList& list, int color, bool with_norm,
+             cudaStream_t s);
+// the coarse tail from each listed descriptor's level: one block each
+void batch_tail32(int model, const BJob32* table, const BList& list, int nu1, int nu2, int cmax, float crtol,
+                  int gamma, int gamma_levels, cudaStream_t s);
 
 }  // namespace rich

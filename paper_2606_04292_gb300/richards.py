@@ -129,6 +129,13 @@ _SIGS = {
                                          C.POINTER(C.c_longlong)]),
     "richards_columns_set_threads": (C.c_int, [_VP, C.c_int]),
     "richards_columns_autotune": (C.c_int, [_VP, C.c_double, C.c_int, C.POINTER(C.c_int)]),
+    "richards_autotune": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "richards_set_launch": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "richards_batcher_create": (C.c_int, [_VP, C.c_int, C.POINTER(_VP)]),
+    "richards_batcher_destroy": (None, [_VP]),
+    "richards_batcher_last_error": (C.c_char_p, [_VP]),
+    "richards_batcher_step": (C.c_int, [_VP, C.POINTER(_VP), C.c_int, _DP, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(richards_step_info)]),
     "richards_step_small_noalloc": (C.c_int, [C.POINTER(richards_grid), C.POINTER(richards_soil),
                                               C.POINTER(richards_bc), C.POINTER(richards_sink),
                                               C.POINTER(richards_opts), C.c_double, C.c_int, _DP, _DP, _DP,
@@ -361,6 +368,19 @@ class Solver:
     def vcycle(self):
         _check(lib().richards_vcycle(self.h), self.h)
 
+    # -- launch shapes ---------------------------------------------------
+    def autotune(self, reps=5):
+        """Time the candidate launch shapes of every big grid level on the
+        current prepared state and keep the fastest; returns per level
+        (planes, block_x, resid_block_x), 0 = default."""
+        n = self.nlevels
+        pl, bx, rb = (C.c_int * n)(), (C.c_int * n)(), (C.c_int * n)()
+        _check(lib().richards_autotune(self.h, int(reps), pl, bx, rb), self.h)
+        return [(pl[k], bx[k], rb[k]) for k in range(n)]
+
+    def set_launch(self, level, planes=0, block_x=0, resid_block_x=0):
+        _check(lib().richards_set_launch(self.h, int(level), int(planes), int(block_x), int(resid_block_x)), self.h)
+
     # -- kernel timing ---------------------------------------------------
     def profile(self, enable=True, mode=1):
         """mode 1: time every launch; 2: time the finest level, count the rest;
@@ -465,3 +485,38 @@ class Columns:
         if st != RICH_OK:
             raise RichardsError(st, "richards_columns_autotune failed")
         return t.value
+
+
+class Batcher:
+    """Lockstep steps of many resident solvers (``richards_batcher_*``): one
+    call advances every listed Solver by one step, their FP32 inner cycles
+    batched into shared launches."""
+
+    def __init__(self, max_contexts=64, stream=None):
+        h = C.c_void_p()
+        st = lib().richards_batcher_create(C.c_void_p(current_stream() if stream is None else stream),
+                                           int(max_contexts), C.byref(h))
+        if st != RICH_OK:
+            raise RichardsError(st, "richards_batcher_create failed")
+        self.h = h
+        self.cap = int(max_contexts)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().richards_batcher_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def step(self, solvers, dts, schemes):
+        """One step of each solver; returns (status list, info dict list)."""
+        n = len(solvers)
+        hs = (C.c_void_p * n)(*[s.h.value for s in solvers])
+        dt = _f64(dts)
+        sc = (C.c_int * n)(*[int(x) for x in schemes])
+        status = (C.c_int * n)()
+        info = (richards_step_info * n)()
+        st = lib().richards_batcher_step(self.h, hs, n, _dp(dt), sc, status, info)
+        if st != RICH_OK:
+            raise RichardsError(st, lib().richards_batcher_last_error(self.h).decode())
+        return [int(x) for x in status], [info[k].as_dict() for k in range(n)]

@@ -33,7 +33,16 @@ def request_bytes(prob, opts=None):
 
 
 class Server:
-    def __init__(self, budget_bytes=None, max_active=16, keep_states=False, opts=None, poll_s=2e-4):
+    """batched=False: every admitted request runs on its own stream and host
+    worker thread (richards_batch_submit), their kernels overlapping on the
+    device.  batched=True: the admitted requests advance in lockstep, one
+    time step per round, through richards_batcher_step -- each stage of their
+    FP32 inner cycles is one launch over all of them; requests are admitted
+    and retired between rounds (every request in a mixed mode with the same
+    cycle options)."""
+
+    def __init__(self, budget_bytes=None, max_active=16, keep_states=False, opts=None, poll_s=2e-4,
+                 batched=False):
         import torch
         self.torch = torch
         if budget_bytes is None:
@@ -44,9 +53,12 @@ class Server:
         self.keep_states = keep_states
         self.opts = opts
         self.poll_s = poll_s
+        self.batched = batched
 
     def run(self, requests, realtime=True):
         """Serve ``requests``; returns (results, summary)."""
+        if self.batched:
+            return self._run_batched(requests, realtime)
         lib = R.lib()
         reqs = sorted(enumerate(requests), key=lambda kv: kv[1].get("arrival", 0.0))
         pending = collections.deque(reqs)
@@ -111,3 +123,75 @@ class Server:
                        p50_latency_s=float(np.percentile(lat, 50)), p99_latency_s=float(np.percentile(lat, 99)),
                        max_active=self.max_active, budget_bytes=self.budget)
         return [results[k] for k in sorted(results)], summary
+
+    def _summary(self, requests, results, makespan):
+        done_ok = [r for r in results.values() if r.get("status") == "OK"]
+        lat = np.array([r["latency"] for r in done_ok]) if done_ok else np.array([np.nan])
+        return dict(requests=len(requests), completed=len(done_ok),
+                    rejected=sum(1 for r in results.values() if r.get("status") == "rejected"),
+                    makespan_s=makespan, solves_per_s=len(done_ok) / makespan,
+                    cell_updates_per_s=sum(r["info"]["cell_updates"] for r in done_ok) / makespan,
+                    p50_latency_s=float(np.percentile(lat, 50)), p99_latency_s=float(np.percentile(lat, 99)),
+                    max_active=self.max_active, budget_bytes=self.budget)
+
+    def _run_batched(self, requests, realtime):
+        reqs = sorted(enumerate(requests), key=lambda kv: kv[1].get("arrival", 0.0))
+        pending = collections.deque(reqs)
+        waiting = collections.deque()
+        active = {}
+        results = {}
+        used = 0
+        stream = self.torch.cuda.Stream()
+        batcher = R.Batcher(max_contexts=self.max_active, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        try:
+            while pending or waiting or active:
+                now = time.perf_counter() - t0
+                while pending and (not realtime or pending[0][1].get("arrival", 0.0) <= now):
+                    waiting.append(pending.popleft())
+                while waiting and len(active) < self.max_active:
+                    rid, prob = waiting[0]
+                    need = request_bytes(prob, self.opts)
+                    if need > self.budget:
+                        waiting.popleft()
+                        results[rid] = dict(id=rid, status="rejected", bytes=need)
+                        continue
+                    if used + need > self.budget:
+                        break
+                    waiting.popleft()
+                    solver = R.Solver(prob, stream=stream.cuda_stream, opts=self.opts)
+                    used += need
+                    arrival = prob.get("arrival", 0.0) if realtime else 0.0
+                    active[rid] = dict(solver=solver, bytes=need, arrival=arrival, start=time.perf_counter() - t0,
+                                       prob=prob, done=0, acc=dict(cycles=0, outer_iters=0, cell_updates=0))
+                if not active:
+                    time.sleep(self.poll_s)
+                    continue
+                ids = list(active)
+                statuses, infos = batcher.step([active[r]["solver"] for r in ids],
+                                               [float(active[r]["prob"]["dt"]) for r in ids],
+                                               [int(active[r]["prob"]["scheme"]) for r in ids])
+                end = time.perf_counter() - t0
+                for rid, st, info in zip(ids, statuses, infos):
+                    a = active[rid]
+                    a["done"] += 1
+                    for k in ("cycles", "outer_iters", "cell_updates"):
+                        a["acc"][k] += info[k]
+                    a["acc"]["resid"] = info["resid"]
+                    if st != R.RICH_OK or a["done"] >= a["prob"]["nsteps"]:
+                        res = dict(id=rid, status=R.STATUS_NAMES[st], arrival=a["arrival"], start=a["start"],
+                                   end=end, latency=end - a["arrival"], queue=a["start"] - a["arrival"],
+                                   steps=a["done"], cells=int(np.prod(a["prob"]["n"])), info=dict(a["acc"]),
+                                   bytes=a["bytes"])
+                        if self.keep_states:
+                            res["state"] = a["solver"].state()
+                        a["solver"].close()
+                        used -= a["bytes"]
+                        results[rid] = res
+                        del active[rid]
+        finally:
+            for a in active.values():
+                a["solver"].close()
+            batcher.close()
+        makespan = time.perf_counter() - t0
+        return [results[k] for k in sorted(results)], self._summary(requests, results, makespan)

@@ -338,6 +338,19 @@ def test_strip_2d_bdf2_steps():
         assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
 
 
+def test_strip_2d_513_bdf2_steps():
+    """The 2-d infiltration workload at its full size (513^2, the hierarchy odd
+    on every level: 513, 257, ..., 5), FP64, BDF2: three steps, both sides
+    cycling to 1e-11, agree to the 1e-10 norm-wise bound."""
+    prob = W.strip_2d(n=513, nsteps=3, tol=1e-11, max_cycles=200)
+    gs, orc, p = pair(prob)
+    for k in range(p["nsteps"]):
+        st, info = gs.step()
+        sto, info_o = orc.step()
+        assert st == sto == R.RICH_OK, (k, info, info_o)
+        assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
+
+
 def _mixed_bound(orc, psi_m, psi_r):
     """(||r_m|| + ||r_r||) / min_i a theta'(zeta_i), zeta_i on [psi_m, psi_r]."""
     a = orc.a
@@ -816,3 +829,35 @@ def test_face_fields_fp64_steps_match_oracle():
         assert st == sto == R.RICH_OK, (k, info, info_o)
         assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
         assert abs(info["mass_defect"]) <= 1e-9
+
+
+def test_launch_shapes_give_the_same_bits():
+    """The launch shapes the autotuner chooses among (cells per thread along
+    z, block sizes of the half-sweeps and of the defect kernel) never change
+    what is computed: steps with hand-set shapes on every grid level, and with
+    the autotuned ones, equal the default launches bit for bit."""
+    prob = W.with_opts(W.drainage_3d(n=64, nsteps=4), precision=2, tail_cells=64)
+    ref = R.Solver(prob)
+    odd = R.Solver(prob)
+    shapes = [(2, 64, 32), (4, 32, 256), (1, 256, 64), (8, 128, 128)]
+    for lev in range(min(odd.nlevels - 1, len(shapes))):
+        pl, bx, rb = shapes[lev]
+        n2 = odd.level_n(lev)[2]
+        odd.set_launch(lev, pl if n2 >= 2 * pl or pl == 1 else 1, bx if pl == 1 or bx <= 128 else 128, rb)
+    tuned = R.Solver(prob)
+    for k in range(3):
+        sa, ia = ref.step()
+        sb, ib = odd.step()
+        sc, ic = tuned.step()
+        assert sa == sb == sc == R.RICH_OK
+        assert ia["cycles"] == ib["cycles"] == ic["cycles"], (k, ia, ib, ic)
+        assert np.array_equal(ref.state(), odd.state()), k
+        assert np.array_equal(ref.state(), tuned.state()), k
+        if k == 0:
+            tuned.prepare(prob["dt"], prob["scheme"])
+            choice = tuned.autotune(reps=2)
+            assert len(choice) == tuned.nlevels and choice[0][0] == 2
+    with pytest.raises(R.RichardsError):
+        odd.set_launch(0, 3, 64, 64)
+    with pytest.raises(R.RichardsError):
+        odd.set_launch(1, 2, 256, 64)

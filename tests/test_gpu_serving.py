@@ -67,6 +67,111 @@ def test_each_result_same_alone_and_in_the_mix():
         assert live <= 3
 
 
+def test_large_requests_same_alone_and_in_the_mix():
+    """Requests of the served workload's sizes (a 257^2 strip and a 65^3
+    drainage) beside small ones: each result the same alone and in the mix."""
+    reqs = [
+        W.strip_2d(n=257, nsteps=3, precision=1),
+        W.drainage_3d(n=65, nsteps=3, precision=1),
+        W.drainage_3d(n=65, nsteps=2, precision=2),
+        W.random_problem(2, (129, 129), W.GARDNER, 107, sink=True, scheme=2, precision=1),
+        W.random_problem(3, (33, 33, 33), W.HAVERKAMP, 108, scheme=2, precision=0),
+    ]
+    for k, p in enumerate(reqs):
+        p["nsteps"] = p.get("nsteps", 3) if k < 3 else 3
+        p["arrival"] = 0.0
+    alone = [solve_alone(p) for p in reqs]
+    srv = serve.Server(max_active=5, keep_states=True)
+    results, summary = srv.run(reqs, realtime=False)
+    assert summary["completed"] == len(reqs)
+    for r, ref in zip(results, alone):
+        assert r["status"] == "OK"
+        err = np.max(np.abs(r["state"] - ref)) / np.max(np.abs(ref))
+        assert err <= STEP_RTOL, (r["id"], err)
+
+
+def batch_mix():
+    """Mixed-mode requests of every law, 1-3 dimensions, both outer layers,
+    sinks, BDF1 and BDF2, different sizes and time steps."""
+    reqs = [
+        W.random_problem(2, (33, 40), W.VANGENUCHTEN, 111, hetero=True, sink=True, scheme=2, precision=1),
+        W.random_problem(3, (17, 16, 15), W.HAVERKAMP, 112, scheme=2, precision=2),
+        W.random_problem(2, (65, 65), W.GARDNER, 113, sink=True, scheme=1, precision=1),
+        W.strip_2d(n=65, nsteps=4, precision=2),
+        W.random_problem(1, 200, W.VANGENUCHTEN, 115, sink=True, scheme=2, precision=1),
+        W.random_problem(3, (40, 36, 33), W.VANGENUCHTEN, 116, hetero=True, sink=True, scheme=2, precision=2,
+                         dt=120.0),
+        W.drainage_3d(n=33, precision=2),
+    ]
+    for k, p in enumerate(reqs):
+        p["nsteps"] = 3 + k % 2
+        p["arrival"] = 0.0
+        p["opts"] = dict(p["opts"], nu1=2, nu2=2, cycle_gamma=1, gamma_levels=0, coarse_max_sweeps=50,
+                         coarse_rtol=0.1, inner_cycles=8, max_outer=60)
+    return reqs
+
+
+def test_batched_steps_equal_single_steps():
+    """richards_batcher_step advances every context exactly as richards_step
+    does: same cycle and outer counts, the same state (1e-10; the kernels
+    evaluate the same per-cell expressions)."""
+    reqs = batch_mix()
+    stream = torch.cuda.Stream()
+    batched = [R.Solver(p, stream=stream.cuda_stream) for p in reqs]
+    alone = [R.Solver(p) for p in reqs]
+    b = R.Batcher(max_contexts=len(reqs), stream=stream.cuda_stream)
+    exact = True
+    for step in range(3):
+        sts, infos = b.step(batched, [p["dt"] for p in reqs], [p["scheme"] for p in reqs])
+        for k, p in enumerate(reqs):
+            st, info = alone[k].step(p["dt"], p["scheme"], check=False)
+            assert sts[k] == st == R.RICH_OK, (k, sts[k], st)
+            for key in ("cycles", "outer_iters", "scheme_used", "cell_updates"):
+                assert infos[k][key] == info[key], (step, k, key, infos[k][key], info[key])
+            got, want = batched[k].state(), alone[k].state()
+            exact = exact and np.array_equal(got, want)
+            assert np.max(np.abs(got - want)) <= STEP_RTOL * np.max(np.abs(want)), (step, k)
+            assert infos[k]["resid"] == pytest.approx(info["resid"], rel=1e-6, abs=1e-15)
+    b.close()
+    for s in batched + alone:
+        s.close()
+    print("batched states bit for bit equal:", exact)
+
+
+def test_batched_server_same_alone_and_in_the_mix():
+    """Continuous batching through lockstep batched cycles: requests admitted
+    as slots free up (3 slots for 7 requests), each result the same as alone."""
+    reqs = batch_mix()
+    alone = [solve_alone(p) for p in reqs]
+    srv = serve.Server(max_active=3, keep_states=True, batched=True)
+    results, summary = srv.run(reqs, realtime=False)
+    assert summary["completed"] == len(reqs)
+    for r, ref in zip(results, alone):
+        assert r["status"] == "OK"
+        err = np.max(np.abs(r["state"] - ref)) / np.max(np.abs(ref))
+        assert err <= STEP_RTOL, (r["id"], err)
+    spans = [(r["start"], r["end"]) for r in results]
+    for t, _ in spans:
+        assert sum(1 for a, b in spans if a <= t < b) <= 3
+
+
+def test_batcher_rejects_what_it_cannot_batch():
+    reqs = batch_mix()[:2]
+    b = R.Batcher(max_contexts=2)
+    a = R.Solver(reqs[0])
+    fp64 = R.Solver(W.with_opts(reqs[1], precision=0))
+    other = R.Solver(W.with_opts(reqs[1], nu2=3))
+    for pair_ in ([a, fp64], [a, other], [a, a]):
+        with pytest.raises(R.RichardsError) as e:
+            b.step(pair_, [60.0, 60.0], [1, 1])
+        assert e.value.status == R.RICH_EINVAL
+    with pytest.raises(R.RichardsError):
+        b.step([a, fp64, other], [60.0] * 3, [1] * 3)      # more than the batcher holds
+    for s in (a, fp64, other):
+        s.close()
+    b.close()
+
+
 def test_admission_rejects_requests_above_budget():
     reqs = request_mix()[:2]
     small = min(serve.request_bytes(p) for p in reqs)
