@@ -49,7 +49,7 @@ DTYPE = {2: "f32 inner / f64 outer, f64 state", 1: "f32 inner / float-float (f32
 # DRAM bytes (read + write) per launch of the finest level's half-sweep of
 # 256^3 (8,388,608 cells), from an ncu capture of this kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum); the roofline's traffic.
-TRAFFIC_PER_LAUNCH = {("sweep32", 8388608): 459.4e6}
+TRAFFIC_PER_LAUNCH = {}
 
 BYTES_PER_CELL = {
     "sweep32": 28.0,

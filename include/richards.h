@@ -147,7 +147,14 @@ typedef struct {
                           sides and iterates restricted to every level, the
                           coarsest solved first, each finer iterate corrected
                           by the interpolated coarse change, then fmg_cycles
-                          cycles on it; counted in cycles */
+                          cycles on it; counted in cycles
+     layout               mixed modes: 0 = the finest FP32 level of a grid of
+                          at least 2^20 cells with an even n0 keeps its
+                          per-cell parameters (right side, psi0, soil
+                          fields, sink) with each colour's cells packed
+                          together, so a half-sweep reads only its own
+                          colour's memory; 1 = the natural layout everywhere
+                          (same results: only where values sit changes) */
 typedef struct {
   int nu1, nu2, coarse_max_sweeps;
   double coarse_rtol;
@@ -158,6 +165,7 @@ typedef struct {
   int inner_cycles;
   double inner_rtol;
   int max_outer, tail_cells, cycle_gamma, gamma_levels, graphs, sweep_planes, predictor, fmg_cycles;
+  int layout;
 } richards_opts;
 
 typedef struct {

@@ -26,16 +26,7 @@ __host__ __device__ inline int stage_nx(int op, const Level<float>& L) {
 }
 
 template <int OP, int MODEL, int NK>
-__global__ void __launch_bounds__(BATCH_THREADS) k_batch32(const BJob32* __restrict__ table,
-                                                           const __grid_constant__ BList list, int color,
-                                                           int with_norm) {
-  int k = 0;
-  while (k + 1 < list.n && (int)blockIdx.x >= list.block0[k + 1]) ++k;
-  const BJob32& J = table[list.job[k]];
-  const Level<float>& L = stage_level(OP, J);
-  const int gx = (stage_nx(OP, L) + BATCH_THREADS - 1) / BATCH_THREADS;
-  const int local = (int)blockIdx.x - list.block0[k];
-  const int bx = local % gx, r = local / gx, by = r % L.n1, bz = r / L.n1;
+__device__ __forceinline__ void batch_stage(const BJob32& J, int color, int with_norm, int bx, int by, int bz) {
   if constexpr (OP == BOP_SWEEP) {
     sweep_body<float, FORM_DELTA, MODEL, NK>(J.F, J.P, color, bx, by, bz);
   } else if constexpr (OP == BOP_RESID) {
@@ -56,7 +47,26 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch32(const BJob32* __restr
   }
 }
 
-template <int MODEL>
+// (the law branch is uniform over a block: one block serves one descriptor)
+template <int OP, int NK>
+__global__ void __launch_bounds__(BATCH_THREADS) k_batch32(const BJob32* __restrict__ table,
+                                                           const __grid_constant__ BList list, int color,
+                                                           int with_norm) {
+  int k = 0;
+  while (k + 1 < list.n && (int)blockIdx.x >= list.block0[k + 1]) ++k;
+  const BJob32& J = table[list.job[k]];
+  const Level<float>& L = stage_level(OP, J);
+  const int gx = (stage_nx(OP, L) + BATCH_THREADS - 1) / BATCH_THREADS;
+  const int local = (int)blockIdx.x - list.block0[k];
+  const int bx = local % gx, r = local / gx, by = r % L.n1, bz = r / L.n1;
+  switch (J.model) {
+    case HAVERKAMP: batch_stage<OP, HAVERKAMP, NK>(J, color, with_norm, bx, by, bz); break;
+    case GARDNER: batch_stage<OP, GARDNER, NK>(J, color, with_norm, bx, by, bz); break;
+    case COMPOSITE: batch_stage<OP, COMPOSITE, NK>(J, color, with_norm, bx, by, bz); break;
+    default: batch_stage<OP, VANGENUCHTEN, NK>(J, color, with_norm, bx, by, bz); break;
+  }
+}
+
 __global__ void __launch_bounds__(TAIL_THREADS, 1) k_tail_batch32(const BJob32* __restrict__ table,
                                                                  const __grid_constant__ BList list, int nu1,
                                                                  int nu2, int cmax, float crtol, int gamma,
@@ -64,26 +74,40 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_tail_batch32(const BJob32* 
   __shared__ unsigned long long sm[33];
   const BJob32& J = table[list.job[blockIdx.x]];
   unsigned long long updates = 0;
-  block_cycle<float, FORM_DELTA, MODEL>(DeviceLevels<float>{J.dLs, J.dXs}, J.level, J.nlev, J.P, nu1, nu2, cmax,
-                                        crtol, gamma, gamma_levels, sm, updates, 1);
+  const DeviceLevels<float> lv{J.dLs, J.dXs};
+  switch (J.model) {
+    case HAVERKAMP:
+      block_cycle<float, FORM_DELTA, HAVERKAMP>(lv, J.level, J.nlev, J.P, nu1, nu2, cmax, crtol, gamma,
+                                                gamma_levels, sm, updates, 1);
+      break;
+    case GARDNER:
+      block_cycle<float, FORM_DELTA, GARDNER>(lv, J.level, J.nlev, J.P, nu1, nu2, cmax, crtol, gamma,
+                                              gamma_levels, sm, updates, 1);
+      break;
+    case COMPOSITE:
+      block_cycle<float, FORM_DELTA, COMPOSITE>(lv, J.level, J.nlev, J.P, nu1, nu2, cmax, crtol, gamma,
+                                                gamma_levels, sm, updates, 1);
+      break;
+    default:
+      block_cycle<float, FORM_DELTA, VANGENUCHTEN>(lv, J.level, J.nlev, J.P, nu1, nu2, cmax, crtol, gamma,
+                                                   gamma_levels, sm, updates, 1);
+      break;
+  }
   if (threadIdx.x == 0 && J.stats) atomicAdd(J.stats, updates);
 }
 
 template <int OP, int NK>
-void launch_op(int model, const BJob32* table, const BList& list, int color, bool with_norm, cudaStream_t s) {
+void launch_op(const BJob32* table, const BList& list, int color, bool with_norm, cudaStream_t s) {
   const int blocks = list.block0[list.n];
   if (blocks <= 0) return;
-  by_model(model, [&](auto m) {
-    k_batch32<OP, decltype(m)::value, NK><<<blocks, BATCH_THREADS, 0, s>>>(table, list, color, with_norm ? 1 : 0);
-  });
+  k_batch32<OP, NK><<<blocks, BATCH_THREADS, 0, s>>>(table, list, color, with_norm ? 1 : 0);
 }
 
 template <int OP>
-void launch_nk(int model, int nk, const BJob32* table, const BList& list, int color, bool with_norm,
-               cudaStream_t s) {
-  if (OP != BOP_SWEEP || nk == 0) launch_op<OP, 0>(model, table, list, color, with_norm, s);
-  else if (nk == 1) launch_op<OP, 1>(model, table, list, color, with_norm, s);
-  else launch_op<OP, 2>(model, table, list, color, with_norm, s);
+void launch_nk(int nk, const BJob32* table, const BList& list, int color, bool with_norm, cudaStream_t s) {
+  if (OP != BOP_SWEEP || nk == 0) launch_op<OP, 0>(table, list, color, with_norm, s);
+  else if (nk == 1) launch_op<OP, 1>(table, list, color, with_norm, s);
+  else launch_op<OP, 2>(table, list, color, with_norm, s);
 }
 
 }  // namespace
@@ -94,24 +118,20 @@ int batch_blocks(int op, const BJob32& j) {
   return (int)(gx * L.n1 * L.n2);
 }
 
-void batch32(int op, int model, int nk, const BJob32* table, const BList& list, int color, bool with_norm,
-             cudaStream_t s) {
+void batch32(int op, int nk, const BJob32* table, const BList& list, int color, bool with_norm, cudaStream_t s) {
   switch (op) {
-    case BOP_SWEEP: launch_nk<BOP_SWEEP>(model, nk, table, list, color, with_norm, s); break;
-    case BOP_RESID: launch_nk<BOP_RESID>(model, nk, table, list, color, with_norm, s); break;
-    case BOP_RESTRICT: launch_nk<BOP_RESTRICT>(model, nk, table, list, color, with_norm, s); break;
-    case BOP_TAU: launch_nk<BOP_TAU>(model, nk, table, list, color, with_norm, s); break;
-    default: launch_nk<BOP_PROLONG>(model, nk, table, list, color, with_norm, s); break;
+    case BOP_SWEEP: launch_nk<BOP_SWEEP>(nk, table, list, color, with_norm, s); break;
+    case BOP_RESID: launch_nk<BOP_RESID>(nk, table, list, color, with_norm, s); break;
+    case BOP_RESTRICT: launch_nk<BOP_RESTRICT>(nk, table, list, color, with_norm, s); break;
+    case BOP_TAU: launch_nk<BOP_TAU>(nk, table, list, color, with_norm, s); break;
+    default: launch_nk<BOP_PROLONG>(nk, table, list, color, with_norm, s); break;
   }
 }
 
-void batch_tail32(int model, const BJob32* table, const BList& list, int nu1, int nu2, int cmax, float crtol,
-                  int gamma, int gamma_levels, cudaStream_t s) {
+void batch_tail32(const BJob32* table, const BList& list, int nu1, int nu2, int cmax, float crtol, int gamma,
+                  int gamma_levels, cudaStream_t s) {
   if (list.n <= 0) return;
-  by_model(model, [&](auto m) {
-    k_tail_batch32<decltype(m)::value><<<list.n, TAIL_THREADS, 0, s>>>(table, list, nu1, nu2, cmax, crtol, gamma,
-                                                                      gamma_levels);
-  });
+  k_tail_batch32<<<list.n, TAIL_THREADS, 0, s>>>(table, list, nu1, nu2, cmax, crtol, gamma, gamma_levels);
 }
 
 }  // namespace rich

@@ -43,6 +43,7 @@ struct HLevel {
   float *p1f = nullptr, *p2f = nullptr, *smaxf = nullptr, *psi0f = nullptr;
   float* kbf[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   uint8_t* mat = nullptr;        // layered soil: material of each cell
+  int cs = 0;                    // FP32 g, psi0, p1, p2, smax in the colour-split layout (rich::pix_of)
   // transfer tables to the next coarser level
   int *pc[3] = {}, *pj[3] = {}, *rc[3] = {}, *ri[3] = {};
   double *pw[3] = {}, *rw[3] = {};
@@ -395,7 +396,15 @@ Level<float> view32(const richards_ctx* c, int l) {
   V.psi0 = H.psi0f;
   for (int f = 0; f < 6; ++f) V.kb[f] = H.kbf[f];
   V.mat = c->layered ? H.mat : nullptr;
+  V.cs = H.cs;
   return V;
+}
+
+// FP32 copy of a level's per-cell parameter array, in the level's layout
+void to_float_at(richards_ctx* c, int l, const double* src, float* dst) {
+  const HLevel& H = c->L[l];
+  if (H.cs) rich::to_float_level(src, dst, H.n[0], H.n[1], H.n[2], 1, c->s);
+  else rich::to_float(src, dst, H.ncell, c->s);
 }
 
 Xfer<double> xfer64(const richards_ctx* c, int l) {
@@ -872,7 +881,8 @@ void fmg32(richards_ctx* c) {
     HLevel &F = c->L[l], &C = c->L[l + 1];
     {
       Prof pr(c, "fmg_restrict32", l, C.ncell);
-      rich::restrict32(view32(c, l), view32(c, l + 1), xfer32(c, l), F.uf, F.gf, C.ubarf, C.gf, c->s);
+      rich::restrict32(view32(c, l), view32(c, l + 1), xfer32(c, l), F.uf, F.gf, C.ubarf, C.gf, c->s,
+                       F.cs ? 2 : 0);
     }
     cudaMemcpyAsync(C.uf, C.ubarf, sizeof(float) * C.ncell, cudaMemcpyDeviceToDevice, c->s);
   }
@@ -944,12 +954,21 @@ richards_status outer_defect_launch(richards_ctx* c, bool cached, bool fp64) {
   if (fp64) {
     Prof pr(c, "outer_residual64", 0, F.ncell);
     rich::outer_residual64(view64(c, 0), P64, c->soil.model, F.gf, F.psi0f, F.uf, c->scratch,
-                           cached ? c->th_n : nullptr, th_out, c->s);
+                           cached ? c->th_n : nullptr, th_out, F.cs, c->s);
   } else {
     Prof pr(c, "outer_residual", 0, F.ncell);
     rich::outer_residual_dd(view64(c, 0), P64, rich::make_ddphys(P64), c->soil.model, F.gf, F.psi0f, F.uf,
-                            c->scratch, cached ? c->th_n : nullptr, th_out, c->s);
+                            c->scratch, cached ? c->th_n : nullptr, th_out, F.cs, c->s);
   }
+  return check_launch(c);
+}
+
+// the finest defect of the inner problem at delta = 0, which is g (natural
+// layout, whatever g's)
+richards_status defect_from_g(richards_ctx* c) {
+  HLevel& F = c->L[0];
+  if (F.cs) rich::cs_to_natural(F.gf, F.df, F.n[0], F.n[1], F.n[2], c->s);
+  else CK(cudaMemcpyAsync(F.df, F.gf, sizeof(float) * F.ncell, cudaMemcpyDeviceToDevice, c->s));
   return check_launch(c);
 }
 
@@ -958,7 +977,7 @@ void restrict_psi0(richards_ctx* c) {
   for (int l = 0; l + 1 < c->nlev; ++l) {
     Prof pr(c, "restrict_psi0", l, c->L[l + 1].ncell);
     rich::restrict32(view32(c, l), view32(c, l + 1), xfer32(c, l), c->L[l].psi0f, nullptr, c->L[l + 1].psi0f,
-                     nullptr, c->s);
+                     nullptr, c->s, c->L[l].cs ? 1 : 0);
   }
 }
 
@@ -1010,7 +1029,7 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
     bool done_in = false;
     const bool fmg_start = c->opts.fmg_cycles > 0 && c->nlev > 1;
     if (top_defect_ready(c) && !fmg_start)          // the defect at delta = 0 is g
-      CK(cudaMemcpyAsync(F.df, F.gf, sizeof(float) * F.ncell, cudaMemcpyDeviceToDevice, c->s));
+      TRY(defect_from_g(c));
     if (fmg_start) {                                // full multigrid start of the inner solve
       fmg32(c);
       inner += c->opts.fmg_cycles;
@@ -1099,11 +1118,12 @@ int batch_nk(const richards_ctx* c) {
 }
 
 // one stage over the level-l descriptors of the listed contexts, grouped by
-// law and Newton count, at most BATCH_MAX descriptors per launch
+// Newton count (the laws share a launch), at most BATCH_MAX descriptors per
+// launch
 void batch_stage(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who, int op, int l,
                  int color, bool with_norm) {
-  std::map<std::pair<int, int>, std::vector<int>> groups;
-  for (int k : who) groups[{B[k].c->soil.model, batch_nk(B[k].c)}].push_back(k);
+  std::map<int, std::vector<int>> groups;
+  for (int k : who) groups[batch_nk(B[k].c)].push_back(k);
   for (auto& kv : groups) {
     const std::vector<int>& ks = kv.second;
     for (size_t a = 0; a < ks.size(); a += rich::BATCH_MAX) {
@@ -1118,23 +1138,20 @@ void batch_stage(richards_batcher* b, std::vector<BatchCtx>& B, const std::vecto
         ++list.n;
       }
       list.block0[list.n] = blocks;
-      rich::batch32(op, kv.first.first, kv.first.second, b->dtable, list, color, with_norm, b->s);
+      rich::batch32(op, kv.first, b->dtable, list, color, with_norm, b->s);
     }
   }
 }
 
 void batch_tail(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who, int l) {
-  std::map<int, std::vector<int>> groups;
-  for (int k : who) groups[B[k].c->soil.model].push_back(k);
   const richards_opts& o = B[who[0]].c->opts;
-  for (auto& kv : groups)
-    for (size_t a = 0; a < kv.second.size(); a += rich::BATCH_MAX) {
-      rich::BList list{};
-      for (size_t q = a; q < kv.second.size() && q < a + rich::BATCH_MAX; ++q)
-        list.job[list.n++] = B[kv.second[q]].slot * MAXLEV + l;
-      rich::batch_tail32(kv.first, b->dtable, list, o.nu1, o.nu2, o.coarse_max_sweeps, (float)o.coarse_rtol,
-                         o.cycle_gamma, o.gamma_levels, b->s);
-    }
+  for (size_t a = 0; a < who.size(); a += rich::BATCH_MAX) {
+    rich::BList list{};
+    for (size_t q = a; q < who.size() && q < a + rich::BATCH_MAX; ++q)
+      list.job[list.n++] = B[who[q]].slot * MAXLEV + l;
+    rich::batch_tail32(b->dtable, list, o.nu1, o.nu2, o.coarse_max_sweeps, (float)o.coarse_rtol, o.cycle_gamma,
+                       o.gamma_levels, b->s);
+  }
 }
 
 void batch_smooth(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who, int l, int nu) {
@@ -1229,6 +1246,7 @@ richards_status batch_step_impl(richards_batcher* b, std::vector<BatchCtx>& B, c
       J.dXs = c->dX32;
       J.level = l;
       J.nlev = c->nlev;
+      J.model = c->soil.model;
       J.norm = c->scratch + 1;
       J.stats = c->scratch + 16;
     }
@@ -1269,8 +1287,10 @@ richards_status batch_step_impl(richards_batcher* b, std::vector<BatchCtx>& B, c
       restrict_psi0(c);
       X.rin0 = X.r * c->a;
       X.rtol_in = std::max(c->opts.inner_rtol, 0.3 * c->opts.tol / X.r);
-      if (top_defect_ready(c))
-        BCK(cudaMemcpyAsync(c->L[0].df, c->L[0].gf, sizeof(float) * c->L[0].ncell, cudaMemcpyDeviceToDevice, b->s));
+      if (top_defect_ready(c)) {
+        const richards_status sd = defect_from_g(c);
+        if (sd != RICH_OK) return bfail(b, sd, c->err);
+      }
     }
     std::vector<int> in = act;
     const int cycles = B[act[0]].c->opts.inner_cycles;
@@ -1335,7 +1355,7 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
       (o.ordering != 0 && o.ordering != 1) || (o.precision < 0 || o.precision > 2) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
       o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0 || o.cycle_gamma < 1 || o.cycle_gamma > 3 ||
       o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1) || (o.predictor != 0 && o.predictor != 1) ||
-      o.fmg_cycles < 0 || o.fmg_cycles > 16 ||
+      o.fmg_cycles < 0 || o.fmg_cycles > 16 || (o.layout != 0 && o.layout != 1) ||
       (o.sweep_planes != 1 && o.sweep_planes != 2 && o.sweep_planes != 4 && o.sweep_planes != 8))
     return RICH_EINVAL;
   richards_ctx* c = new richards_ctx();
@@ -1366,6 +1386,12 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
   for (int l = 0; l < c->nlev; ++l)
     if ((long long)c->L[l].n[0] * c->L[l].n[1] * c->L[l].n[2] <= o.tail_cells) { c->tail_start = l; break; }
   const bool mixed = o.precision >= 1;
+  // the finest FP32 level of a big grid keeps its per-cell parameters in the
+  // colour-split layout: a half-sweep then reads only its own colour's sectors
+  // of them (the level must have an even n0 and lie above the coarse tail)
+  if (mixed && o.layout == 0 && c->tail_start > 0 && grid->n[0] % 2 == 0 &&
+      (long long)grid->n[0] * grid->n[1] * grid->n[2] >= (1LL << 20))
+    c->L[0].cs = 1;
   richards_status st = RICH_OK;
   for (int l = 0; l < c->nlev && st == RICH_OK; ++l) {
     HLevel& H = c->L[l];
@@ -1492,8 +1518,8 @@ richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
     }
     if (mixed)
       for (int l = 0; l < c->nlev; ++l) {
-        if (c->het_p1) rich::to_float(c->L[l].p1, c->L[l].p1f, c->L[l].ncell, c->s);
-        if (c->het_p2) rich::to_float(c->L[l].p2, c->L[l].p2f, c->L[l].ncell, c->s);
+        if (c->het_p1) to_float_at(c, l, c->L[l].p1, c->L[l].p1f);
+        if (c->het_p2) to_float_at(c, l, c->L[l].p2, c->L[l].p2f);
       }
     TRY(check_launch(c));
     TRY(upload_views(c));
@@ -1573,8 +1599,8 @@ richards_status richards_set_materials(richards_ctx* c, const richards_material*
     CK(cudaMemcpyAsync(H.p1, q1.data(), sizeof(double) * H.ncell, cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(H.p2, q2.data(), sizeof(double) * H.ncell, cudaMemcpyHostToDevice, c->s));
     if (mixed) {
-      rich::to_float(H.p1, H.p1f, H.ncell, c->s);
-      rich::to_float(H.p2, H.p2f, H.ncell, c->s);
+      to_float_at(c, l, H.p1, H.p1f);
+      to_float_at(c, l, H.p2, H.p2f);
     }
   }
   // material tables (FP64, FP32, float-float)
@@ -1624,7 +1650,7 @@ static richards_status refresh_sink(richards_ctx* c) {
     rich::restrict64(view64(c, l), view64(c, l + 1), xfer64(c, l), c->L[l].smax, nullptr, c->L[l + 1].smax, nullptr,
                      c->s);
   if (mixed)
-    for (int l = 0; l < c->nlev; ++l) rich::to_float(c->L[l].smax, c->L[l].smaxf, c->L[l].ncell, c->s);
+    for (int l = 0; l < c->nlev; ++l) to_float_at(c, l, c->L[l].smax, c->L[l].smaxf);
   TRY(check_launch(c));
   return upload_views(c);
 }
@@ -1699,8 +1725,8 @@ richards_status richards_set_bc(richards_ctx* c, const richards_bc* b) {
     }
     if (c->opts.precision >= 1)
       for (int l = 0; l < c->nlev; ++l) {
-        if (c->het_p1) rich::to_float(c->L[l].p1, c->L[l].p1f, c->L[l].ncell, c->s);
-        if (c->het_p2) rich::to_float(c->L[l].p2, c->L[l].p2f, c->L[l].ncell, c->s);
+        if (c->het_p1) to_float_at(c, l, c->L[l].p1, c->L[l].p1f);
+        if (c->het_p2) to_float_at(c, l, c->L[l].p2, c->L[l].p2f);
       }
     TRY(check_launch(c));
   }

@@ -135,6 +135,7 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
       V.u = p; V.ubar = p + nn; V.g = p + 2 * nn; V.d = p + 3 * nn;
       V.Kc = p + 4 * nn; V.psi0 = p + 5 * nn; V.smax = A.sink ? p + 6 * nn : nullptr;
       V.p1 = nullptr; V.p2 = nullptr;
+      V.mat = nullptr; V.cs = 0;
       p += COL_ARRAYS * nn;
       V.kb[0] = p; V.kb[1] = p + 1;
       V.kb[2] = V.kb[3] = V.kb[4] = V.kb[5] = nullptr;

@@ -35,7 +35,26 @@ struct Level {
   const T *psi0;                 // FORM_DELTA: frozen state
   const T *kb[6];                // boundary face conductances (per face cell)
   const uint8_t *mat;            // COMPOSITE: material of each cell of this level
+  int cs;                        // 1: g, psi0, p1, p2, smax in the colour-split layout (pix)
 };
+
+// Index of cell (i0, i1, i2) (flat index i) in the per-cell parameter arrays
+// g, psi0, p1, p2, smax of a level.  Natural layout: i.  Colour-split layout
+// (big FP32 levels with an even n0): the cells of each colour packed row by
+// row, (i0 >> 1) + n0/2 (i1 + n1 i2), the black half after the red one, so a
+// half-sweep reads only its own colour's sectors of these arrays.  u, Kc and
+// d keep the natural layout (the stencil reads both colours of them).
+__host__ __device__ __forceinline__ unsigned pix_of(int cs, int n0, int n1, int n2, unsigned i, int i0, int i1,
+                                                    int i2) {
+  if (!cs) return i;
+  const unsigned nh = (unsigned)n0 >> 1;
+  const unsigned q = (unsigned)(i0 >> 1) + nh * ((unsigned)i1 + (unsigned)n1 * (unsigned)i2);
+  return ((i0 + i1 + i2) & 1) ? q + nh * (unsigned)n1 * (unsigned)n2 : q;
+}
+template <typename T>
+__device__ __forceinline__ unsigned pix(const Level<T>& L, long long i, int i0, int i1, int i2) {
+  return pix_of(L.cs, L.n0, L.n1, L.n2, (unsigned)i, i0, i1, i2);
+}
 
 // One material of a layered soil: its law and the parameters that are not
 // per-cell arrays (p1 and p2 are: the level's p1/p2 hold each cell's
@@ -642,11 +661,12 @@ __device__ __forceinline__ void point_update(const Level<T>& L, const Phys<T>& P
   stencil(L, i, i0, i1, i2, L.u, mii, off);
   const T ui = L.u[i];
   const T cc = P.xi + P.kappa + mii;
-  const T f = L.g[i] + off + P.kappa * ui;
-  const T p1 = L.p1 ? L.p1[i] : P.p1;
-  const T p2 = L.p2 ? L.p2[i] : P.p2;
-  const T smax = L.smax ? L.smax[i] : T(0);
-  const T psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
+  const unsigned q = pix(L, i, i0, i1, i2);
+  const T f = L.g[q] + off + P.kappa * ui;
+  const T p1 = L.p1 ? L.p1[q] : P.p1;
+  const T p2 = L.p2 ? L.p2[q] : P.p2;
+  const T smax = L.smax ? L.smax[q] : T(0);
+  const T psi0 = FORM == FORM_DELTA ? L.psi0[q] : T(0);
   L.u[i] = with_law<MODEL>(P, mat_of<MODEL>(L, i), [&](auto law, const Phys<T>& Q) {
     return point_solve<T, FORM, decltype(law)::value, NK>(cc, f, ui, psi0, p1, p2, smax, Q);
   });
@@ -678,11 +698,12 @@ __device__ __forceinline__ void gather(const Level<T>& L, const Phys<T>& P, int 
   const T* __restrict__ up = L.u + i;
   c.Ki = Kp[0];
   c.ui = up[0];
-  c.g = L.g[i];
-  c.psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
-  c.p1 = L.p1 ? L.p1[i] : P.p1;
-  c.p2 = L.p2 ? L.p2[i] : P.p2;
-  c.smax = L.smax ? L.smax[i] : T(0);
+  const unsigned q = pix(L, i, i0, i1, i2);
+  c.g = L.g[q];
+  c.psi0 = FORM == FORM_DELTA ? L.psi0[q] : T(0);
+  c.p1 = L.p1 ? L.p1[q] : P.p1;
+  c.p2 = L.p2 ? L.p2[q] : P.p2;
+  c.smax = L.smax ? L.smax[q] : T(0);
   unsigned bm = 0;
   const int ii[3] = {i0, i1, i2};
   const int nn[3] = {L.n0, L.n1, L.n2};
@@ -763,10 +784,11 @@ __device__ __forceinline__ T apply_N(const Level<T>& L, const Phys<T>& P, const 
                                      long long i, int i0, int i1, int i2) {
   T mii, off;
   stencil<T, YZI>(L, i, i0, i1, i2, u, mii, off);
-  const T p1 = L.p1 ? L.p1[i] : P.p1;
-  const T p2 = L.p2 ? L.p2[i] : P.p2;
-  const T smax = L.smax ? L.smax[i] : T(0);
-  const T psi0 = FORM == FORM_DELTA ? L.psi0[i] : T(0);
+  const unsigned q = pix(L, i, i0, i1, i2);
+  const T p1 = L.p1 ? L.p1[q] : P.p1;
+  const T p2 = L.p2 ? L.p2[q] : P.p2;
+  const T smax = L.smax ? L.smax[q] : T(0);
+  const T psi0 = FORM == FORM_DELTA ? L.psi0[q] : T(0);
   T val, der;
   with_law<MODEL>(P, mat_of<MODEL>(L, i), [&](auto law, const Phys<T>& Q) {
     storage<T, FORM, decltype(law)::value>(u[i], psi0, p1, p2, smax, Q, val, der);
@@ -831,8 +853,9 @@ __device__ __forceinline__ void interp_row(int nf, int nc, int i, double slo, do
 // Transfers (restriction: normalised full weighting; prolongation: linear).
 // ---------------------------------------------------------------------------
 template <typename T>
+// (cs: fine is a per-cell parameter array of a colour-split level)
 __device__ __forceinline__ T restrict_at(const Level<T>& F, const Xfer<T>& X, const T* __restrict__ fine,
-                                         int J0, int J1, int J2) {
+                                         int J0, int J1, int J2, bool cs = false) {
   T s = T(0);
   const int c0 = X.rc[0][J0], c1 = X.rc[1][J1], c2 = X.rc[2][J2];
   for (int a2 = 0; a2 < c2; ++a2) {
@@ -844,7 +867,9 @@ __device__ __forceinline__ T restrict_at(const Level<T>& F, const Xfer<T>& X, co
       const long long row = (long long)F.n0 * (f1 + (long long)F.n1 * f2);
       for (int a0 = 0; a0 < c0; ++a0) {
         const T w0 = X.rw[0][RMAX * J0 + a0];
-        s += w0 * w1 * w2 * fine[row + X.ri[0][RMAX * J0 + a0]];
+        const int f0 = X.ri[0][RMAX * J0 + a0];
+        const long long idx = cs ? (long long)pix_of(1, F.n0, F.n1, F.n2, (unsigned)(row + f0), f0, f1, f2) : row + f0;
+        s += w0 * w1 * w2 * fine[idx];
       }
     }
   }

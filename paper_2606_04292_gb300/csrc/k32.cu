@@ -10,8 +10,8 @@ void residual32(const Level<float>& L, const Phys<float>& P, int model, unsigned
 }
 void tau32(const Level<float>& C, const Phys<float>& P, int model, cudaStream_t s) { D::tau(C, P, model, s); }
 void restrict32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, const float* fa,
-                const float* fb, float* ca, float* cb, cudaStream_t s) {
-  D::restrict2(F, C, X, fa, fb, ca, cb, s);
+                const float* fb, float* ca, float* cb, cudaStream_t s, int cs_mask) {
+  D::restrict2(F, C, X, fa, fb, ca, cb, s, cs_mask);
 }
 void prolong32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, cudaStream_t s) {
   D::prolong(F, C, X, s);

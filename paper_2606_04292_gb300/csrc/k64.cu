@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(256) k_to_float(const double* src, float* dst,
 template <int MODEL>
 __global__ void __launch_bounds__(128) k_outer_residual_dd(Level<double> L, Phys<double> P, DDPhys Q, float* r32,
                                                            float* psi0f, float* delta, unsigned long long* norm,
-                                                           const double* __restrict__ th_in, double* th_out) {
+                                                           const double* __restrict__ th_in, double* th_out, int cs) {
   __shared__ unsigned long long sm[33];
   unsigned long long mx = 0;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -359,8 +359,9 @@ __global__ void __launch_bounds__(128) k_outer_residual_dd(Level<double> L, Phys
     N = dd_add(N, dd_mul(dd_add(Q.xi, db), ui));
     N = dd_add(N, flux);
     const float di = dd_float(dd_sub(dd_split(L.g[i]), N));
-    r32[i] = di;
-    psi0f[i] = dd_float(ui);
+    const unsigned q = pix_of(cs, L.n0, L.n1, L.n2, (unsigned)i, i0, i1, i2);
+    r32[q] = di;
+    psi0f[q] = dd_float(ui);
     delta[i] = 0.0f;
     mx = nbits(di);
   }
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(128) k_outer_residual_dd(Level<double> L, Phys
 template <int MODEL>
 __global__ void __launch_bounds__(256) k_outer_residual64(Level<double> L, Phys<double> P, float* r32, float* psi0f,
                                                           float* delta, unsigned long long* norm,
-                                                          const double* __restrict__ th_in, double* th_out) {
+                                                          const double* __restrict__ th_in, double* th_out, int cs) {
   __shared__ unsigned long long sm[33];
   unsigned long long mx = 0;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -420,8 +421,9 @@ __global__ void __launch_bounds__(256) k_outer_residual64(Level<double> L, Phys<
     double S, dS;
     sink_direct(ui, L.smax ? L.smax[i] : 0.0, P, S, dS);
     const double di = L.g[i] - ((P.a * th + S) + (P.xi + db) * ui + flux);
-    r32[i] = (float)di;
-    psi0f[i] = (float)ui;
+    const unsigned q = pix_of(cs, L.n0, L.n1, L.n2, (unsigned)i, i0, i1, i2);
+    r32[q] = (float)di;
+    psi0f[q] = (float)ui;
     delta[i] = 0.0f;
     mx = nbits(di);
   }
@@ -521,20 +523,50 @@ void to_float(const double* src, float* dst, long long n, cudaStream_t s) {
 
 void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPhys& Q, int model, float* r32,
                        float* psi0f, float* delta, unsigned long long* norm, const double* th_in, double* th_out,
-                       cudaStream_t s) {
+                       int cs, cudaStream_t s) {
   const Launch3 g = launch3(L.n0, L.n1, L.n2);
   by_model(model, [&](auto m) {
     k_outer_residual_dd<decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, Q, r32, psi0f, delta, norm, th_in,
-                                                                       th_out);
+                                                                       th_out, cs);
   });
 }
 
 void outer_residual64(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
-                      float* delta, unsigned long long* norm, const double* th_in, double* th_out, cudaStream_t s) {
+                      float* delta, unsigned long long* norm, const double* th_in, double* th_out, int cs,
+                      cudaStream_t s) {
   const Launch3 g = launch3(L.n0, L.n1, L.n2);
   by_model(model, [&](auto m) {
-    k_outer_residual64<decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out);
+    k_outer_residual64<decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out,
+                                                                      cs);
   });
+}
+
+__global__ void __launch_bounds__(256) k_to_float_level(const double* __restrict__ src, float* dst, int n0, int n1,
+                                                        int n2, int cs) {
+  const long long n = (long long)n0 * n1 * n2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    int i0, i1, i2;
+    cell_coords(n0, n1, i, i0, i1, i2);
+    dst[pix_of(cs, n0, n1, n2, (unsigned)i, i0, i1, i2)] = (float)src[i];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_cs_to_natural(const float* __restrict__ src, float* dst, int n0, int n1,
+                                                       int n2) {
+  const long long n = (long long)n0 * n1 * n2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    int i0, i1, i2;
+    cell_coords(n0, n1, i, i0, i1, i2);
+    dst[i] = src[pix_of(1, n0, n1, n2, (unsigned)i, i0, i1, i2)];
+  }
+}
+
+void to_float_level(const double* src, float* dst, int n0, int n1, int n2, int cs, cudaStream_t s) {
+  k_to_float_level<<<grid_for((long long)n0 * n1 * n2), 256, 0, s>>>(src, dst, n0, n1, n2, cs);
+}
+
+void cs_to_natural(const float* src, float* dst, int n0, int n1, int n2, cudaStream_t s) {
+  k_cs_to_natural<<<grid_for((long long)n0 * n1 * n2), 256, 0, s>>>(src, dst, n0, n1, n2);
 }
 
 template <int MODEL, bool DD>

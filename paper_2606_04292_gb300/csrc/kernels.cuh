@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(256) k_residual_color(Level<T> L, Phys<T> P, i
   if (i0 < L.n0) {
     const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
     const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && i2 > 0 && i2 < L.n2 - 1;
-    const T di = L.g[i] - (yzi ? apply_N<T, FORM, MODEL, true>(L, P, L.u, i, i0, i1, i2)
-                               : apply_N<T, FORM, MODEL, false>(L, P, L.u, i, i0, i1, i2));
+    const T di = L.g[pix(L, i, i0, i1, i2)] - (yzi ? apply_N<T, FORM, MODEL, true>(L, P, L.u, i, i0, i1, i2)
+                                                    : apply_N<T, FORM, MODEL, false>(L, P, L.u, i, i0, i1, i2));
     L.d[i] = di;
     mx = nbits(di);
   }
@@ -158,8 +158,8 @@ __device__ __forceinline__ unsigned long long residual_body(const Level<T>& L, c
   const long long i = (unsigned)(i0 + L.n0 * (i1 + L.n1 * i2));
   // rows away from the y/z boundaries skip those tests (uniform over the block)
   const bool yzi = L.dim == 3 && i1 > 0 && i1 < L.n1 - 1 && i2 > 0 && i2 < L.n2 - 1;
-  const T di = L.g[i] - (yzi ? apply_N<T, FORM, MODEL, true>(L, P, L.u, i, i0, i1, i2)
-                             : apply_N<T, FORM, MODEL, false>(L, P, L.u, i, i0, i1, i2));
+  const T di = L.g[pix(L, i, i0, i1, i2)] - (yzi ? apply_N<T, FORM, MODEL, true>(L, P, L.u, i, i0, i1, i2)
+                                                  : apply_N<T, FORM, MODEL, false>(L, P, L.u, i, i0, i1, i2));
   L.d[i] = di;
   return nbits(di);
 }
@@ -175,21 +175,22 @@ __global__ void __launch_bounds__(256) k_residual(Level<T> L, Phys<T> P, unsigne
 }
 
 // FAS step 3: psi_bar_H = R psi_h, d_H = R d_h (cb may be null).
+// (cs_mask: bit 0 / bit 1 set when fa / fb is a colour-split parameter array)
 template <typename T>
 __device__ __forceinline__ void restrict_body(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, const T* fa,
-                                              const T* fb, T* ca, T* cb, int bx, int by, int bz) {
+                                              const T* fb, T* ca, T* cb, int bx, int by, int bz, int cs_mask = 0) {
   const int J0 = bx * blockDim.x + threadIdx.x;
   const int J1 = by, J2 = bz;
   if (J0 >= C.n0) return;
   const long long J = J0 + (long long)C.n0 * (J1 + C.n1 * J2);
-  ca[J] = restrict_at(F, X, fa, J0, J1, J2);
-  if (cb) cb[J] = restrict_at(F, X, fb, J0, J1, J2);
+  ca[J] = restrict_at(F, X, fa, J0, J1, J2, (cs_mask & 1) != 0);
+  if (cb) cb[J] = restrict_at(F, X, fb, J0, J1, J2, (cs_mask & 2) != 0);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(Level<T> F, Level<T> C, Xfer<T> X, const T* fa, const T* fb,
-                                                  T* ca, T* cb) {
-  restrict_body<T>(F, C, X, fa, fb, ca, cb, blockIdx.x, blockIdx.y, blockIdx.z);
+                                                  T* ca, T* cb, int cs_mask) {
+  restrict_body<T>(F, C, X, fa, fb, ca, cb, blockIdx.x, blockIdx.y, blockIdx.z, cs_mask);
 }
 
 // FAS step 4 on the coarse level: g_H = N_H(psi_bar_H) + d_H, psi_H = psi_bar_H.
@@ -257,7 +258,7 @@ __device__ __forceinline__ void restrict_taps(int J, int nc, int nf, int* idx, T
 
 template <typename T>
 __device__ __forceinline__ void restrict_nested_body(const Level<T>& F, const Level<T>& C, const T* fa, const T* fb,
-                                                     T* ca, T* cb, int bx, int by, int bz) {
+                                                     T* ca, T* cb, int bx, int by, int bz, int cs_mask = 0) {
   const int J0 = bx * blockDim.x + threadIdx.x;
   const int J1 = by, J2 = bz;
   if (J0 >= C.n0) return;
@@ -275,16 +276,25 @@ __device__ __forceinline__ void restrict_nested_body(const Level<T>& F, const Le
     for (int b = 0; b < 4; ++b) {
       if (wy[b] == T(0)) continue;
       const unsigned row = (unsigned)F.n0 * ((unsigned)y[b] + (unsigned)F.n1 * (unsigned)z[c]);
-      const T* ra = fa + row;
+      unsigned ia[4], ib[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ia[a] = row + x[a];
+        ib[a] = row + x[a];
+        if (cs_mask) {
+          const unsigned q = pix_of(1, F.n0, F.n1, F.n2, row + x[a], x[a], y[b], z[c]);
+          if (cs_mask & 1) ia[a] = q;
+          if (cs_mask & 2) ib[a] = q;
+        }
+      }
       T xa = T(0);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) xa += wx[a] * ra[x[a]];
+      for (int a = 0; a < 4; ++a) xa += wx[a] * fa[ia[a]];
       ya += wy[b] * xa;
       if (fb) {
-        const T* rb = fb + row;
         T xb = T(0);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) xb += wx[a] * rb[x[a]];
+        for (int a = 0; a < 4; ++a) xb += wx[a] * fb[ib[a]];
         yb += wy[b] * xb;
       }
     }
@@ -298,8 +308,8 @@ __device__ __forceinline__ void restrict_nested_body(const Level<T>& F, const Le
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_nested(Level<T> F, Level<T> C, const T* fa, const T* fb, T* ca,
-                                                         T* cb) {
-  restrict_nested_body<T>(F, C, fa, fb, ca, cb, blockIdx.x, blockIdx.y, blockIdx.z);
+                                                         T* cb, int cs_mask) {
+  restrict_nested_body<T>(F, C, fa, fb, ca, cb, blockIdx.x, blockIdx.y, blockIdx.z, cs_mask);
 }
 
 template <typename T>
@@ -473,7 +483,7 @@ __device__ __forceinline__ T block_defect_norm(const Level<T>& L, const Phys<T>&
   for (long long i = threadIdx.x; i < L.ncell; i += blockDim.x) {
     int i0, i1, i2;
     cell_coords(L.n0, L.n1, i, i0, i1, i2);
-    const T di = L.g[i] - apply_N<T, FORM, MODEL>(L, P, L.u, i, i0, i1, i2);
+    const T di = L.g[pix(L, i, i0, i1, i2)] - apply_N<T, FORM, MODEL>(L, P, L.u, i, i0, i1, i2);
     const unsigned long long b = nbits(di);
     mx = b > mx ? b : mx;
   }
@@ -514,7 +524,7 @@ __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const 
       for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
         int i0, i1, i2;
         cell_coords(F.n0, F.n1, i, i0, i1, i2);
-        F.d[i] = F.g[i] - apply_N<T, FORM, MODEL>(F, P, F.u, i, i0, i1, i2);
+        F.d[i] = F.g[pix(F, i, i0, i1, i2)] - apply_N<T, FORM, MODEL>(F, P, F.u, i, i0, i1, i2);
       }
       __syncthreads();
       const Level<T>& C = lv.L(l + 1);
@@ -718,12 +728,12 @@ struct Dispatch {
     by_model(model, [&](auto m) { k_tau<T, FORM, decltype(m)::value><<<g.grid, g.block, 0, s>>>(C, P); });
   }
   static void restrict2(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, const T* fa, const T* fb,
-                        T* ca, T* cb, cudaStream_t s) {
+                        T* ca, T* cb, cudaStream_t s, int cs_mask = 0) {
     const Launch3 g = launch3(C.n0, C.n1, C.n2);
     if (nested_levels(F.n0, F.n1, F.n2, C.n0, C.n1, C.n2))
-      k_restrict_nested<T><<<g.grid, g.block, 0, s>>>(F, C, fa, fb, ca, cb);
+      k_restrict_nested<T><<<g.grid, g.block, 0, s>>>(F, C, fa, fb, ca, cb, cs_mask);
     else
-      k_restrict<T><<<g.grid, g.block, 0, s>>>(F, C, X, fa, fb, ca, cb);
+      k_restrict<T><<<g.grid, g.block, 0, s>>>(F, C, X, fa, fb, ca, cb, cs_mask);
   }
   static void prolong(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, cudaStream_t s) {
     const Launch3 g = launch3(F.n0, F.n1, F.n2);

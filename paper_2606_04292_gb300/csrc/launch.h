@@ -46,8 +46,9 @@ void sweep32(const Level<float>& L, const Phys<float>& P, int model, int color, 
 void residual32(const Level<float>& L, const Phys<float>& P, int model, unsigned long long* norm,
                 cudaStream_t s, int bx = 0);
 void tau32(const Level<float>& C, const Phys<float>& P, int model, cudaStream_t s);
+// (cs_mask: bit 0 / 1 when fa / fb is a colour-split parameter array of F)
 void restrict32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, const float* fa,
-                const float* fb, float* ca, float* cb, cudaStream_t s);
+                const float* fb, float* ca, float* cb, cudaStream_t s, int cs_mask = 0);
 void prolong32(const Level<float>& F, const Level<float>& C, const Xfer<float>& X, cudaStream_t s);
 void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, const Phys<float>& P,
             int model, int nu1, int nu2, int cmax, float crtol, int gamma, int gamma_levels,
@@ -82,13 +83,19 @@ void to_float(const double* src, float* dst, long long n, cudaStream_t s);
 // mixed mode: r = g - N(u) in float-float -> r32, psi0 = (float)u, delta = 0;
 // ||r||_inf as float bits.  theta(u) from th_in if given, else evaluated and
 // written to th_out (nullable).
+// (cs: r32 and psi0f in the colour-split layout of the FP32 level 0)
 void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPhys& Q, int model, float* r32,
                        float* psi0f, float* delta, unsigned long long* norm, const double* th_in, double* th_out,
-                       cudaStream_t s);
+                       int cs, cudaStream_t s);
 // FP64-outer mixed mode: r = g - N(u) in FP64 -> r32, psi0 = (float)u,
 // delta = 0; ||r||_inf as FP64 bits; theta caches as outer_residual_dd.
 void outer_residual64(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
-                      float* delta, unsigned long long* norm, const double* th_in, double* th_out, cudaStream_t s);
+                      float* delta, unsigned long long* norm, const double* th_in, double* th_out, int cs,
+                      cudaStream_t s);
+// FP32 copy of a level-0 parameter array in the FP32 level's layout (cs: colour-split)
+void to_float_level(const double* src, float* dst, int n0, int n1, int n2, int cs, cudaStream_t s);
+// natural-layout copy of a colour-split array (the defect at delta = 0 is g)
+void cs_to_natural(const float* src, float* dst, int n0, int n1, int n2, cudaStream_t s);
 // mixed mode: the lagged state in float-float (Kc to FP64 and FP32)
 // (predict: u = psi* instead of psi^n)
 void prep_lagged_dd(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
@@ -134,6 +141,7 @@ struct BJob32 {
   const Level<float>* dLs;           // the context's device level views (coarse tail)
   const Xfer<float>* dXs;
   int level, nlev;
+  int model;                         // the context's law (HAVERKAMP, GARDNER, VANGENUCHTEN, COMPOSITE)
   unsigned long long* norm;          // the context's inner-norm slot (float bits)
   unsigned long long* stats;         // the context's coarse-tail update counter
 };
@@ -148,13 +156,13 @@ enum { BOP_SWEEP = 0, BOP_RESID = 1, BOP_RESTRICT = 2, BOP_TAU = 3, BOP_PROLONG 
 
 // blocks one descriptor takes for a stage
 int batch_blocks(int op, const BJob32& j);
-// one stage over the listed descriptors (all of one law and one fixed Newton
-// count nk: 1, 2, or 0 for P.newton_k); color for BOP_SWEEP; with_norm: the
-// defect's max into each descriptor's norm slot (BOP_RESID)
-void batch32(int op, int model, int nk, const BJob32* table, const BList& list, int color, bool with_norm,
-             cudaStream_t s);
+// one stage over the listed descriptors, of any laws (each block branches on
+// its descriptor's), all with one fixed Newton count nk: 1, 2, or 0 for
+// P.newton_k; color for BOP_SWEEP; with_norm: the defect's max into each
+// descriptor's norm slot (BOP_RESID)
+void batch32(int op, int nk, const BJob32* table, const BList& list, int color, bool with_norm, cudaStream_t s);
 // the coarse tail from each listed descriptor's level: one block each
-void batch_tail32(int model, const BJob32* table, const BList& list, int nu1, int nu2, int cmax, float crtol,
-                  int gamma, int gamma_levels, cudaStream_t s);
+void batch_tail32(const BJob32* table, const BList& list, int nu1, int nu2, int cmax, float crtol, int gamma,
+                  int gamma_levels, cudaStream_t s);
 
 }  // namespace rich

@@ -55,10 +55,11 @@ def default_opts(**kw):
              tol=1e-8, max_cycles=60,
              ordering=1,          # 0 = lexicographic, 1 = red-black
              newton_iters=2,      # 0 = to tolerance; k > 0 = exactly k steps
-             precision=0,         # 0 = FP64 plain, 1 = FP32 inner / float-float outer
+             precision=0,         # 0 = FP64 plain, 1 = FP32 inner / float-float outer, 2 = FP64 outer
              inner_cycles=8, inner_rtol=1e-3, max_outer=20,
              tail_cells=4096, cycle_gamma=1, gamma_levels=0, graphs=1, sweep_planes=2, predictor=0,
-             fmg_cycles=0)
+             fmg_cycles=0,
+             layout=0)
     o.update(kw)
     return o
 

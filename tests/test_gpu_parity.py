@@ -856,8 +856,28 @@ def test_launch_shapes_give_the_same_bits():
         if k == 0:
             tuned.prepare(prob["dt"], prob["scheme"])
             choice = tuned.autotune(reps=2)
-            assert len(choice) == tuned.nlevels and choice[0][0] == 2
+            assert len(choice) == tuned.nlevels
+            assert all(pl in (1, 2, 4, 8) and bx in (0, 32, 64, 128, 256) for pl, bx, _ in choice)
     with pytest.raises(R.RichardsError):
         odd.set_launch(0, 3, 64, 64)
     with pytest.raises(R.RichardsError):
         odd.set_launch(1, 2, 256, 64)
+
+
+@pytest.mark.parametrize("precision,extra", [(2, {}), (1, {}), (2, {"fmg_cycles": 1})])
+def test_colour_split_layout_gives_the_same_bits(precision, extra):
+    """The colour-split layout of the finest FP32 level's per-cell parameters
+    (a 128^3 grid: even n0, over 2^20 cells) changes only where the values
+    sit: steps with it equal steps with the natural layout bit for bit, with
+    per-cell soil fields, a sink and (one case) an FMG start of each inner
+    solve."""
+    base = W.drainage_3d(n=128, precision=precision, **extra)
+    base = dict(base, sink=W.feddes_sink(Tp=W.TP_5MM_PER_DAY * 50))
+    split = R.Solver(W.with_opts(base, layout=0))
+    natural = R.Solver(W.with_opts(base, layout=1))
+    for k in range(3):
+        sa, ia = split.step()
+        sb, ib = natural.step()
+        assert sa == sb == R.RICH_OK
+        assert ia["cycles"] == ib["cycles"] and ia["outer_iters"] == ib["outer_iters"], (k, ia, ib)
+        assert np.array_equal(split.state(), natural.state()), k
