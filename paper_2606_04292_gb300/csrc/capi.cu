@@ -28,7 +28,7 @@ using rich::law_error;
 namespace {
 
 constexpr int MAXLEV = 24;
-constexpr int NSCRATCH = 32;   // norm slots + statistics
+constexpr int NSCRATCH = 64;   // norm slots + statistics (32..63: the single-block step's)
 constexpr int MASS_PARTS = 152 * 32;   // water-balance blocks (grid_for's cap)
 
 struct HLevel {
@@ -1822,7 +1822,66 @@ richards_status richards_step(richards_ctx* c, double dt, int scheme, richards_s
   return step_impl(c, dt, scheme, info);
 }
 
+// A grid of at most RICHARDS_NOALLOC_MAX_CELLS cells in FP64 (no FMG start):
+// the step -- preparation, stop tests and every cycle -- runs in one thread
+// block on the context's own hierarchy, one launch and one synchronisation
+// instead of a launch per stage and a host round trip per cycle (the same
+// arithmetic as the grid path: apply_N, the point update and the transfers
+// are shared; layered soils included).
+static bool small_path(const richards_ctx* c) {
+  return c->opts.precision == 0 && c->opts.fmg_cycles == 0 && c->L[0].ncell <= RICHARDS_NOALLOC_MAX_CELLS &&
+         c->prof == 0;
+}
+
+static richards_status step_small(richards_ctx* c, double dt, int scheme, richards_step_info* info) {
+  if (!c->soil_set) return fail(c, RICH_EINVAL, "soil not set");
+  if (!c->bc_set) return fail(c, RICH_EINVAL, "boundary conditions not set");
+  if (!c->have_state) return fail(c, RICH_EINVAL, "state not set");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, RICH_EINVAL, "dt must be positive and finite");
+  if (scheme != 1 && scheme != 2) return fail(c, RICH_EINVAL, "scheme must be 1 (BDF1) or 2 (BDF2)");
+  if (scheme == 2 && !c->have_prev) scheme = 1;
+  c->scheme_used = scheme;
+  c->dt = dt;
+  c->a = scheme == 1 ? 1.0 / dt : 1.5 / dt;
+  c->prepared = false;          // the coarse levels of the grid path are not set up by this step
+  HLevel& F = c->L[0];
+  richards_soil soil = c->soil;
+  soil.Ks_field = c->het_Ks ? c->Ks : nullptr;
+  soil.p1_field = c->het_p1 ? F.p1 : nullptr;
+  soil.p2_field = c->het_p2 ? F.p2 : nullptr;
+  richards_bc bc = c->bc;
+  for (int f = 0; f < 6; ++f) {
+    bc.value_field[f] = c->bcdev.vfield[f];
+    bc.mask_field[f] = c->bcdev.mask[f];
+  }
+  std::vector<Level<double>> lv(c->nlev);
+  std::vector<Xfer<double>> xv(c->nlev);
+  for (int l = 0; l < c->nlev; ++l) {
+    lv[l] = view64(c, l);
+    xv[l] = xfer64(c, l);
+  }
+  const rich::SmallCtx cx{c->nlev, lv.data(), xv.data(), c->layered ? c->dmat64 : nullptr};
+  double* stats = (double*)(c->hscratch + 32);         // 5 doubles of the pinned host slots
+  if (rich::small_step(&c->grid, &soil, &bc, &c->sink, &c->opts, dt, scheme, c->psi_n,
+                       scheme == 2 ? c->psi_nm1 : nullptr, F.u, (double*)(c->scratch + 32), &cx, c->opts.ordering,
+                       stats, c->s) != RICH_OK)
+    return fail(c, RICH_ECUDA, "single-block step failed");
+  const double r = stats[2];
+  const richards_status st = (richards_status)(int)stats[3];
+  if (info) {
+    info->cycles = (int)stats[0];
+    info->outer_iters = 0;
+    info->scheme_used = scheme;
+    info->resid0 = stats[1];
+    info->resid = r;
+    info->cell_updates = (long long)stats[4];
+  }
+  TRY(water_balance(c, r, info, nullptr, nullptr, nullptr));
+  return finish_step(c, r, st == RICH_OK ? RICH_OK : RICH_ENOCONV);
+}
+
 static richards_status step_impl(richards_ctx* c, double dt, int scheme, richards_step_info* info) {
+  if (small_path(c)) return step_small(c, dt, scheme, info);
   c->updates_host = 0;
   CK(cudaMemsetAsync(c->scratch + 16, 0, sizeof(unsigned long long), c->s));
   TRY(do_prepare(c, dt, scheme));

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "richards.h"
+
 #include "ddmath.cuh"
 #include "device.cuh"
 
@@ -164,5 +166,31 @@ void batch32(int op, int nk, const BJob32* table, const BList& list, int color, 
 // the coarse tail from each listed descriptor's level: one block each
 void batch_tail32(const BJob32* table, const BList& list, int nu1, int nu2, int cmax, float crtol, int gamma,
                   int gamma_levels, cudaStream_t s);
+
+}  // namespace rich
+
+// ---------------------------------------------------------------------------
+// One FP64 step of a small grid in a single thread block (noalloc.cu): the
+// allocation-free entry point and contexts whose grid fits one block use it.
+// ---------------------------------------------------------------------------
+namespace rich {
+
+// a context's hierarchy: level views (every array, material maps included),
+// transfer tables, material table (layered soils)
+struct SmallCtx {
+  int nlev;
+  const Level<double>* L;
+  const Xfer<double>* X;
+  const MatLaw<double>* mats;
+};
+
+// one step on the context's own levels (soil and bc fields are device
+// arrays); only the 32 doubles of statistics at stats_dev are extra; ordering
+// 1 red-black, 0 lexicographic; stats_out (host, 5 doubles): cycles, resid0,
+// resid, status, updates; synchronises s
+richards_status small_step(const richards_grid* grid, const richards_soil* soil, const richards_bc* bc,
+                           const richards_sink* sink, const richards_opts* opts, double dt, int scheme,
+                           const double* psi_n, const double* psi_prev, double* psi_out, double* stats_dev,
+                           const SmallCtx* cx, int ordering, double* stats_out, cudaStream_t s);
 
 }  // namespace rich

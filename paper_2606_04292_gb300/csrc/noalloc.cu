@@ -40,7 +40,8 @@ struct NaLevel {
 };
 
 struct NaPlan {
-  int nlev, dim, model, scheme, max_cycles, nu1, nu2, cmax, gamma, gamma_levels;
+  int nlev, dim, model, scheme, max_cycles, nu1, nu2, cmax, gamma, gamma_levels, ordering;
+  int ctx_mode;                    // 1: a context's hierarchy (its transfer tables, soil and sink arrays)
   double crtol, tol, dt, Lv, h[3];
   double slo[3], shi[3];           // prolongation ghost factors per axis
   int het_p1, het_p2, het_Ks, sink;
@@ -112,10 +113,15 @@ __device__ void na_prepare(const NaPlan& p) {
   const Phys<double>& P = p.P;
   for (long long i = threadIdx.x; i < L.ncell; i += blockDim.x) {
     const double p1 = p.p1_field ? p.p1_field[i] : P.p1, p2 = p.p2_field ? p.p2_field[i] : P.p2;
-    if (F.p1w) F.p1w[i] = p1;
-    if (F.p2w) F.p2w[i] = p2;
+    if (!p.ctx_mode) {
+      if (F.p1w) F.p1w[i] = p1;
+      if (F.p2w) F.p2w[i] = p2;
+    }
     const double pn = p.psin[i];
-    const double thn = theta_only_d<MODEL>(pn, p1, p2, P);
+    const unsigned mi = mat_at<MODEL>(L.mat, i);
+    const double thn = with_law<MODEL>(P, mi, [&](auto law, const Phys<double>& Q) {
+      return theta_only_d<decltype(law)::value>(pn, p1, p2, Q);
+    });
     double ps, hist;
     if (p.scheme == 1) {
       ps = pn;
@@ -123,12 +129,18 @@ __device__ void na_prepare(const NaPlan& p) {
     } else {
       const double pm = p.psinm1[i];
       ps = 2.0 * pn - pm;
-      hist = (4.0 * thn - theta_only_d<MODEL>(pm, p1, p2, P)) / (2.0 * p.dt);
+      const double thm = with_law<MODEL>(P, mi, [&](auto law, const Phys<double>& Q) {
+        return theta_only_d<decltype(law)::value>(pm, p1, p2, Q);
+      });
+      hist = (4.0 * thn - thm) / (2.0 * p.dt);
     }
-    F.Kcw[i] = cond_d<MODEL>(ps, p1, p2, p.Ks_field ? p.Ks_field[i] : p.Ks, P);
+    const double ks = p.Ks_field ? p.Ks_field[i] : p.Ks;
+    F.Kcw[i] = with_law<MODEL>(P, mi, [&](auto law, const Phys<double>& Q) {
+      return cond_d<decltype(law)::value>(ps, p1, p2, ks, Q);
+    });
     L.g[i] = hist + P.xi * ps;
     L.u[i] = pn;
-    if (F.smaxw) {
+    if (F.smaxw && !p.ctx_mode) {
       int ii[3];
       cell_coords(L.n0, L.n1, i, ii[0], ii[1], ii[2]);
       const int v = p.dim - 1;
@@ -164,7 +176,11 @@ __device__ void na_prepare(const NaPlan& p) {
         const double val = p.bc.vfield[f] ? p.bc.vfield[f][fc] : p.bc.value[f];
         if (dir) {
           const double p1 = p.p1_field ? p.p1_field[i] : P.p1, p2 = p.p2_field ? p.p2_field[i] : P.p2;
-          const double k = 0.5 * (Ki + cond_d<MODEL>(val, p1, p2, p.Ks_field ? p.Ks_field[i] : p.Ks, P));
+          const double ks = p.Ks_field ? p.Ks_field[i] : p.Ks;
+          const double kbv = with_law<MODEL>(P, mat_at<MODEL>(L.mat, i), [&](auto law, const Phys<double>& Q) {
+            return cond_d<decltype(law)::value>(val, p1, p2, ks, Q);
+          });
+          const double k = 0.5 * (Ki + kbv);
           F.kbw[f][fc] = k;
           const double dz = (ax == v) ? (side ? 0.5 * h : -0.5 * h) : 0.0;
           gi += 2.0 * k / (h * h) * (val + dz);
@@ -185,6 +201,7 @@ __device__ void na_prepare(const NaPlan& p) {
       int J0, J1, J2;
       cell_coords(Cl.L.n0, Cl.L.n1, J, J0, J1, J2);
       Cl.Kcw[J] = restrict_at(Fl.L, Fl.X, Fl.L.Kc, J0, J1, J2);
+      if (p.ctx_mode) continue;      // (a context's coarse soil and sink arrays are set up already)
       if (Cl.p1w) Cl.p1w[J] = restrict_at(Fl.L, Fl.X, Fl.L.p1, J0, J1, J2);
       if (Cl.p2w) Cl.p2w[J] = restrict_at(Fl.L, Fl.X, Fl.L.p2, J0, J1, J2);
       if (Cl.smaxw) Cl.smaxw[J] = restrict_at(Fl.L, Fl.X, Fl.L.smax, J0, J1, J2);
@@ -227,7 +244,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_small_step(const __grid_consta
   __shared__ int overflow;
   if (threadIdx.x == 0) overflow = 0;
   __syncthreads();
-  na_tables(p, &overflow);          // ends with a barrier
+  if (!p.ctx_mode) na_tables(p, &overflow);   // ends with a barrier
   if (overflow) {                   // (uniform over the block)
     if (threadIdx.x == 0) {
       p.stats[0] = 0.0;
@@ -246,7 +263,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_small_step(const __grid_consta
   unsigned long long updates = 0;
   while (!(r <= p.tol) && cycles < p.max_cycles && !isnan(r)) {
     block_cycle<double, FORM_DIRECT, MODEL>(PlanLevels{p.lev}, 0, p.nlev, P, p.nu1, p.nu2, p.cmax, p.crtol, p.gamma,
-                                            p.gamma_levels, sm, updates);
+                                            p.gamma_levels, sm, updates, p.ordering);
     ++cycles;
     r = teff * block_defect_norm<double, FORM_DIRECT, MODEL>(p.lev[0].L, P, sm);
   }
@@ -261,11 +278,165 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_small_step(const __grid_consta
   }
 }
 
+// Lays out the hierarchy of a small step over `base` (capacity doubles; base
+// may be null to only count) and fills the plan.  lev0 (nullable): arrays of
+// the finest level supplied by the caller (a context's own), so the step's
+// lagged K, boundary conductances and right side land there.  Returns the
+// doubles used, or -1 when they exceed the capacity.
+long long build_plan(const richards_grid* grid, const richards_soil* soil, const richards_bc* bc,
+                     const richards_sink* sink, const richards_opts& o, double dt, int scheme, const double* psi_n,
+                     const double* psi_prev, double* psi_out, double* base, long long capacity, const SmallCtx* cx,
+                     int ordering, NaPlan& p) {
+  std::memset(&p, 0, sizeof(p));
+  long long used = 0;
+  bool overflow = false;
+  auto take = [&](long long ndoubles) -> double* {
+    const long long n = (ndoubles + 31) / 32 * 32;   // keep 256-byte alignment
+    if (used + n > capacity) { overflow = true; return base; }
+    double* q = base ? base + used : nullptr;
+    used += n;
+    return q;
+  };
+  p.stats = take(8);
+  int n[NA_MAXLEV][3];
+  for (int a = 0; a < 3; ++a) n[0][a] = grid->n[a];
+  int nlev = 1;
+  for (;;) {
+    const int mx = n[nlev - 1][0] > n[nlev - 1][1] ? (n[nlev - 1][0] > n[nlev - 1][2] ? n[nlev - 1][0] : n[nlev - 1][2])
+                                                   : (n[nlev - 1][1] > n[nlev - 1][2] ? n[nlev - 1][1] : n[nlev - 1][2]);
+    if (mx <= o.coarsest_max_n || (o.max_levels > 0 && nlev >= o.max_levels) || nlev >= NA_MAXLEV) break;
+    for (int a = 0; a < 3; ++a) n[nlev][a] = n[nlev - 1][a] > 1 ? (n[nlev - 1][a] + 1) / 2 : 1;
+    ++nlev;
+  }
+  if (cx) {
+    if (cx->nlev != nlev) return -1;
+    p.ctx_mode = 1;
+  }
+  p.nlev = nlev;
+  p.dim = grid->dim;
+  const bool het_p1 = soil->p1_field != nullptr, het_p2 = soil->p2_field != nullptr;
+  for (int l = 0; l < nlev; ++l) {
+    NaLevel& H = p.lev[l];
+    Level<double>& L = H.L;
+    if (cx) {                        // every array and table of the context's level
+      L = cx->L[l];
+      H.X = cx->X[l];
+      H.Kcw = const_cast<double*>(L.Kc);
+      for (int f = 0; f < 6; ++f) H.kbw[f] = const_cast<double*>(L.kb[f]);
+      continue;
+    }
+    L.dim = grid->dim;
+    L.n0 = n[l][0]; L.n1 = n[l][1]; L.n2 = n[l][2];
+    L.ncell = (long long)L.n0 * L.n1 * L.n2;
+    for (int a = 0; a < 3; ++a) {
+      const double h = a < grid->dim ? grid->L[a] / n[l][a] : 1.0;
+      L.ih2[a] = a < grid->dim ? 1.0 / (h * h) : 0.0;
+    }
+    L.u = take(L.ncell); L.ubar = take(L.ncell); L.g = take(L.ncell); L.d = take(L.ncell);
+    H.Kcw = take(L.ncell);
+    H.p1w = het_p1 ? take(L.ncell) : nullptr;
+    H.p2w = het_p2 ? take(L.ncell) : nullptr;
+    H.smaxw = sink->enabled ? take(L.ncell) : nullptr;
+    for (int f = 0; f < 6; ++f) H.kbw[f] = f < 2 * grid->dim ? take(L.ncell / n[l][f / 2]) : nullptr;
+    L.Kc = H.Kcw;
+    L.p1 = H.p1w; L.p2 = H.p2w; L.smax = H.smaxw;
+    L.psi0 = nullptr;
+    for (int f = 0; f < 6; ++f) L.kb[f] = H.kbw[f];
+    if (l + 1 < nlev)
+      for (int a = 0; a < 3; ++a) {
+        const int nf = n[l][a], nc = n[l + 1][a];
+        H.pc[a] = (int*)take((nf + 1) / 2);
+        H.pj[a] = (int*)take(nf);
+        H.pw[a] = take(2LL * nf);
+        H.rc[a] = (int*)take((nc + 1) / 2);
+        H.ri[a] = (int*)take((RMAX * (long long)nc + 1) / 2);
+        H.rw[a] = take(RMAX * (long long)nc);
+        H.X.pc[a] = H.pc[a]; H.X.pj[a] = H.pj[a]; H.X.pw[a] = H.pw[a];
+        H.X.rc[a] = H.rc[a]; H.X.ri[a] = H.ri[a]; H.X.rw[a] = H.rw[a];
+      }
+  }
+  if (overflow) return -1;
+
+  p.model = soil->model;
+  p.scheme = (scheme == 2 && psi_prev) ? 2 : 1;
+  p.max_cycles = o.max_cycles;
+  p.nu1 = o.nu1;
+  p.nu2 = o.nu2;
+  p.cmax = o.coarse_max_sweeps;
+  p.gamma = o.cycle_gamma;
+  p.gamma_levels = o.gamma_levels;
+  p.crtol = o.coarse_rtol;
+  p.tol = o.tol;
+  p.dt = dt;
+  p.ordering = ordering;
+  for (int a = 0; a < 3; ++a) {
+    p.h[a] = a < grid->dim ? grid->L[a] / grid->n[a] : 1.0;
+    p.slo[a] = p.shi[a] = 1.0;
+    if (a < grid->dim) {
+      if (bc->kind[2 * a] == RICH_BC_DIRICHLET && !bc->mask_field[2 * a]) p.slo[a] = -1.0;
+      if (bc->kind[2 * a + 1] == RICH_BC_DIRICHLET && !bc->mask_field[2 * a + 1]) p.shi[a] = -1.0;
+    }
+  }
+  p.Lv = grid->L[grid->dim - 1];
+  p.Ks = soil->Ks;
+  p.Tp = sink->Tp;
+  p.root_depth = sink->root_depth;
+  p.root_decay = sink->root_decay;
+  p.psin = psi_n;
+  p.psinm1 = psi_prev;
+  p.Ks_field = soil->Ks_field;
+  p.p1_field = soil->p1_field;
+  p.p2_field = soil->p2_field;
+  p.psi_out = psi_out;
+  for (int f = 0; f < 6; ++f) {
+    p.bc.kind[f] = f < 2 * grid->dim ? bc->kind[f] : RICH_BC_NOFLUX;
+    p.bc.value[f] = f < 2 * grid->dim ? bc->value[f] : 0.0;
+    p.bc.vfield[f] = f < 2 * grid->dim ? bc->value_field[f] : nullptr;
+    p.bc.mask[f] = f < 2 * grid->dim ? bc->mask_field[f] : nullptr;
+  }
+  Phys<double>& P = p.P;
+  P.a = p.scheme == 1 ? 1.0 / dt : 1.5 / dt;
+  P.xi = o.xi;
+  P.kappa = o.kappa_mode == 0 ? o.kappa : 0.0;
+  P.ts = soil->theta_s;
+  P.tr = soil->theta_r;
+  P.p1 = soil->p1; P.p2 = soil->p2; P.p3 = soil->p3; P.p4 = soil->p4;
+  P.h1 = sink->h1; P.h2 = sink->h2; P.h3 = sink->h3; P.h4 = sink->h4;
+  P.newton_k = o.newton_iters;
+  P.sink = sink->enabled;
+  if (cx) P.mats = cx->mats;
+  return used;
+}
+
+void launch_plan(const NaPlan& p, cudaStream_t s) {
+  if (p.model == RICH_HAVERKAMP) k_small_step<HAVERKAMP><<<1, TAIL_THREADS, 0, s>>>(p);
+  else if (p.model == RICH_GARDNER) k_small_step<GARDNER><<<1, TAIL_THREADS, 0, s>>>(p);
+  else if (p.model == COMPOSITE) k_small_step<COMPOSITE><<<1, TAIL_THREADS, 0, s>>>(p);
+  else k_small_step<VANGENUCHTEN><<<1, TAIL_THREADS, 0, s>>>(p);
+}
+
 // device address of the scratch array, looked up once per device
 constexpr int NA_MAXDEV = 64;
 double* g_scratch_addr[NA_MAXDEV] = {nullptr};
 
 }  // namespace
+
+richards_status small_step(const richards_grid* grid, const richards_soil* soil, const richards_bc* bc,
+                           const richards_sink* sink, const richards_opts* opts, double dt, int scheme,
+                           const double* psi_n, const double* psi_prev, double* psi_out, double* stats_dev,
+                           const SmallCtx* cx, int ordering, double* stats_out, cudaStream_t s) {
+  NaPlan p;
+  if (build_plan(grid, soil, bc, sink, *opts, dt, scheme, psi_n, psi_prev, psi_out, stats_dev, 32, cx, ordering, p) <
+      0)
+    return RICH_EINVAL;
+  launch_plan(p, s);
+  if (cudaGetLastError() != cudaSuccess) return RICH_ECUDA;
+  if (cudaMemcpyAsync(stats_out, p.stats, 5 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return RICH_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RICH_ECUDA;
+  return RICH_OK;
+}
+
 }  // namespace rich
 
 extern "C" richards_status richards_step_small_noalloc(const richards_grid* grid, const richards_soil* soil,
@@ -303,122 +474,14 @@ extern "C" richards_status richards_step_small_noalloc(const richards_grid* grid
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return RICH_ECUDA;
     g_scratch_addr[dev] = (double*)ptr;
   }
-  double* base = g_scratch_addr[dev];
-
-  // carve the hierarchy out of the scratch array
+  // the hierarchy carved out of the scratch array (red-black sweeps)
   NaPlan p;
-  std::memset(&p, 0, sizeof(p));
-  long long used = 0;
-  bool overflow = false;
-  auto take = [&](long long ndoubles) -> double* {
-    const long long n = (ndoubles + 31) / 32 * 32;   // keep 256-byte alignment
-    if (used + n > NA_SCRATCH_DOUBLES) { overflow = true; return base; }
-    double* q = base + used;
-    used += n;
-    return q;
-  };
-  p.stats = take(8);
-  int n[NA_MAXLEV][3];
-  for (int a = 0; a < 3; ++a) n[0][a] = grid->n[a];
-  int nlev = 1;
-  for (;;) {
-    const int mx = n[nlev - 1][0] > n[nlev - 1][1] ? (n[nlev - 1][0] > n[nlev - 1][2] ? n[nlev - 1][0] : n[nlev - 1][2])
-                                                   : (n[nlev - 1][1] > n[nlev - 1][2] ? n[nlev - 1][1] : n[nlev - 1][2]);
-    if (mx <= o.coarsest_max_n || (o.max_levels > 0 && nlev >= o.max_levels) || nlev >= NA_MAXLEV) break;
-    for (int a = 0; a < 3; ++a) n[nlev][a] = n[nlev - 1][a] > 1 ? (n[nlev - 1][a] + 1) / 2 : 1;
-    ++nlev;
-  }
-  p.nlev = nlev;
-  p.dim = grid->dim;
-  const bool het_p1 = soil->p1_field != nullptr, het_p2 = soil->p2_field != nullptr;
-  for (int l = 0; l < nlev; ++l) {
-    NaLevel& H = p.lev[l];
-    Level<double>& L = H.L;
-    L.dim = grid->dim;
-    L.n0 = n[l][0]; L.n1 = n[l][1]; L.n2 = n[l][2];
-    L.ncell = (long long)L.n0 * L.n1 * L.n2;
-    for (int a = 0; a < 3; ++a) {
-      const double h = a < grid->dim ? grid->L[a] / n[l][a] : 1.0;
-      L.ih2[a] = a < grid->dim ? 1.0 / (h * h) : 0.0;
-    }
-    L.u = take(L.ncell); L.ubar = take(L.ncell); L.g = take(L.ncell); L.d = take(L.ncell);
-    H.Kcw = take(L.ncell);
-    L.Kc = H.Kcw;
-    H.p1w = het_p1 ? take(L.ncell) : nullptr;
-    H.p2w = het_p2 ? take(L.ncell) : nullptr;
-    H.smaxw = sink->enabled ? take(L.ncell) : nullptr;
-    L.p1 = H.p1w; L.p2 = H.p2w; L.smax = H.smaxw;
-    L.psi0 = nullptr;
-    for (int f = 0; f < 6; ++f) {
-      H.kbw[f] = f < 2 * grid->dim ? take(L.ncell / n[l][f / 2]) : nullptr;
-      L.kb[f] = H.kbw[f];
-    }
-    if (l + 1 < nlev)
-      for (int a = 0; a < 3; ++a) {
-        const int nf = n[l][a], nc = n[l + 1][a];
-        H.pc[a] = (int*)take((nf + 1) / 2);
-        H.pj[a] = (int*)take(nf);
-        H.pw[a] = take(2LL * nf);
-        H.rc[a] = (int*)take((nc + 1) / 2);
-        H.ri[a] = (int*)take((RMAX * (long long)nc + 1) / 2);
-        H.rw[a] = take(RMAX * (long long)nc);
-        H.X.pc[a] = H.pc[a]; H.X.pj[a] = H.pj[a]; H.X.pw[a] = H.pw[a];
-        H.X.rc[a] = H.rc[a]; H.X.ri[a] = H.ri[a]; H.X.rw[a] = H.rw[a];
-      }
-  }
-  if (overflow) return RICH_EINVAL;   // hierarchy larger than the fixed scratch
-
-  p.model = soil->model;
-  p.scheme = (scheme == 2 && psi_prev) ? 2 : 1;
-  p.max_cycles = o.max_cycles;
-  p.nu1 = o.nu1;
-  p.nu2 = o.nu2;
-  p.cmax = o.coarse_max_sweeps;
-  p.gamma = o.cycle_gamma;
-  p.gamma_levels = o.gamma_levels;
-  p.crtol = o.coarse_rtol;
-  p.tol = o.tol;
-  p.dt = dt;
-  for (int a = 0; a < 3; ++a) {
-    p.h[a] = a < grid->dim ? grid->L[a] / grid->n[a] : 1.0;
-    p.slo[a] = p.shi[a] = 1.0;
-    if (a < grid->dim) {
-      if (bc->kind[2 * a] == RICH_BC_DIRICHLET && !bc->mask_field[2 * a]) p.slo[a] = -1.0;
-      if (bc->kind[2 * a + 1] == RICH_BC_DIRICHLET && !bc->mask_field[2 * a + 1]) p.shi[a] = -1.0;
-    }
-  }
-  p.Lv = grid->L[grid->dim - 1];
-  p.Ks = soil->Ks;
-  p.Tp = sink->Tp;
-  p.root_depth = sink->root_depth;
-  p.root_decay = sink->root_decay;
-  p.psin = psi_n;
-  p.psinm1 = psi_prev;
-  p.Ks_field = soil->Ks_field;
-  p.p1_field = soil->p1_field;
-  p.p2_field = soil->p2_field;
-  p.psi_out = psi_out;
-  for (int f = 0; f < 6; ++f) {
-    p.bc.kind[f] = f < 2 * grid->dim ? bc->kind[f] : RICH_BC_NOFLUX;
-    p.bc.value[f] = f < 2 * grid->dim ? bc->value[f] : 0.0;
-    p.bc.vfield[f] = f < 2 * grid->dim ? bc->value_field[f] : nullptr;
-    p.bc.mask[f] = f < 2 * grid->dim ? bc->mask_field[f] : nullptr;
-  }
-  Phys<double>& P = p.P;
-  P.a = p.scheme == 1 ? 1.0 / dt : 1.5 / dt;
-  P.xi = o.xi;
-  P.kappa = o.kappa_mode == 0 ? o.kappa : 0.0;
-  P.ts = soil->theta_s;
-  P.tr = soil->theta_r;
-  P.p1 = soil->p1; P.p2 = soil->p2; P.p3 = soil->p3; P.p4 = soil->p4;
-  P.h1 = sink->h1; P.h2 = sink->h2; P.h3 = sink->h3; P.h4 = sink->h4;
-  P.newton_k = o.newton_iters;
-  P.sink = sink->enabled;
+  if (build_plan(grid, soil, bc, sink, o, dt, scheme, psi_n, psi_prev, psi_out, g_scratch_addr[dev],
+                 NA_SCRATCH_DOUBLES, nullptr, 1, p) < 0)
+    return RICH_EINVAL;   // hierarchy larger than the fixed scratch
 
   cudaStream_t s = (cudaStream_t)stream;
-  if (soil->model == RICH_HAVERKAMP) k_small_step<HAVERKAMP><<<1, TAIL_THREADS, 0, s>>>(p);
-  else if (soil->model == RICH_GARDNER) k_small_step<GARDNER><<<1, TAIL_THREADS, 0, s>>>(p);
-  else k_small_step<VANGENUCHTEN><<<1, TAIL_THREADS, 0, s>>>(p);
+  launch_plan(p, s);
   if (cudaGetLastError() != cudaSuccess) return RICH_ECUDA;
   double stats[5];
   if (cudaMemcpyAsync(stats, p.stats, sizeof(stats), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RICH_ECUDA;
