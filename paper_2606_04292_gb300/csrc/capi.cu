@@ -1026,6 +1026,10 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
     // asks of the next outer defect (with a margin of 0.3 for the FP32 and
     // nonlinear remainder): close to tol it stops early
     const double rtol_in = std::max(c->opts.inner_rtol, 0.3 * c->opts.tol / r);
+    // (FP64 outer: an inner solve aimed at the stop test itself is expected
+    // to pass it, so the next defect goes to FP64 straight away instead of
+    // after a float-float one that would only say so)
+    if (outer64 && rtol_in > c->opts.inner_rtol) use64 = true;
     bool done_in = false;
     const bool fmg_start = c->opts.fmg_cycles > 0 && c->nlev > 1;
     if (top_defect_ready(c) && !fmg_start)          // the defect at delta = 0 is g
@@ -1287,6 +1291,7 @@ richards_status batch_step_impl(richards_batcher* b, std::vector<BatchCtx>& B, c
       restrict_psi0(c);
       X.rin0 = X.r * c->a;
       X.rtol_in = std::max(c->opts.inner_rtol, 0.3 * c->opts.tol / X.r);
+      if (c->opts.precision == 2 && X.rtol_in > c->opts.inner_rtol) X.use64 = true;   // (as step_mixed)
       if (top_defect_ready(c)) {
         const richards_status sd = defect_from_g(c);
         if (sd != RICH_OK) return bfail(b, sd, c->err);

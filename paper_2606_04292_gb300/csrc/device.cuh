@@ -287,23 +287,21 @@ __device__ __forceinline__ void dlaw_f(float psi0, float x, float p1, float p2, 
 // use the hardware approximations __logf / __expf (relative error ~1e-6 of a
 // result that is then not small).
 // ---------------------------------------------------------------------------
+// (both forms are evaluated and one is selected: no branch, so lanes of a
+// warp on either side of 1/32 do not split it into two passes)
 __device__ __forceinline__ float fast_log1p(float x) {
-  if (fabsf(x) < 0.03125f) {
-    // x - x^2/2 + x^3/3 - x^4/4 + x^5/5 - x^6/6
-    const float p = fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f), -0.5f), 1.0f);
-    return x * p;
-  }
-  return __logf(1.0f + x);
+  // x - x^2/2 + x^3/3 - x^4/4 + x^5/5 - x^6/6
+  const float p = fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f), -0.5f), 1.0f);
+  const float big = __logf(1.0f + x);
+  return fabsf(x) < 0.03125f ? x * p : big;
 }
 
 __device__ __forceinline__ float fast_expm1(float x) {
-  if (fabsf(x) < 0.03125f) {
-    // x + x^2/2 + x^3/6 + x^4/24 + x^5/120 + x^6/720
-    const float p = fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f),
-                                             1.0f / 6.0f), 0.5f), 1.0f);
-    return x * p;
-  }
-  return __expf(x) - 1.0f;
+  // x + x^2/2 + x^3/6 + x^4/24 + x^5/120 + x^6/720
+  const float p = fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f),
+                                           1.0f / 6.0f), 0.5f), 1.0f);
+  const float big = __expf(x) - 1.0f;
+  return fabsf(x) < 0.03125f ? x * p : big;
 }
 
 // Same increments as dlaw_f, built from the fast pieces above, split into
