@@ -288,6 +288,14 @@ richards_status richards_batch_submit(richards_ctx *const *ctxs, int n, double d
 richards_status richards_batch_poll(richards_ctx *const *ctxs, int n, int *done, richards_status *status,
                                     richards_step_info *info);
 
+/* The FP64 elementary functions the soil laws use (Table 1's powers and
+   exponentials: fn 0 exp, 1 expm1, 2 log, 3 log1p; table-driven, a few ulps
+   from the correctly rounded value) or, for comparison, CUDA's own (fn 4..7
+   in the same order): y[i] = f(x[i]) for device arrays of n doubles, on the
+   given stream (synchronised).  The paper has no counterpart: a check of the
+   library's arithmetic.  EINVAL for a bad fn or null arrays. */
+richards_status richards_math_eval(int fn, const double *x, double *y, long long n, void *stream);
+
 /* ---------------------------------------------------------------------
  * Launch shapes of the FP32 grid kernels (mixed modes).  The paper has no
  * counterpart: these choose how the kernels of a level are laid out on the

@@ -1956,6 +1956,14 @@ richards_status richards_batch_poll(richards_ctx* const* ctxs, int n, int* done,
   return RICH_OK;
 }
 
+richards_status richards_math_eval(int fn, const double* x, double* y, long long n, void* stream) {
+  if (fn < 0 || fn > 7 || n < 0 || (n > 0 && (!x || !y))) return RICH_EINVAL;
+  if (n == 0) return RICH_OK;
+  rich::math_eval(fn, x, y, n, (cudaStream_t)stream);
+  if (cudaGetLastError() != cudaSuccess) return RICH_ECUDA;
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? RICH_OK : RICH_ECUDA;
+}
+
 richards_status richards_set_launch(richards_ctx* c, int level, int planes, int block_x, int resid_block_x) {
   if (!c || level < 0 || level >= c->nlev) return RICH_EINVAL;
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");

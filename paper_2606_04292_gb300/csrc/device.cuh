@@ -9,6 +9,8 @@
 
 #include <type_traits>
 
+#include "fp64math.cuh"
+
 namespace rich {
 
 // COMPOSITE: a layered soil (Section 4.1's composite law, Section 4.2's two
@@ -136,19 +138,19 @@ __device__ __forceinline__ void law_d(double psi, double p1, double p2, const Ph
   const double h = -psi, ds = P.ts - P.tr;
   if (MODEL == HAVERKAMP) {
     // theta = theta_r + alpha ds / (alpha + h^beta)
-    const double u = exp(p2 * log(h));
+    const double u = fx::exp(p2 * fx::log(h));
     const double den = p1 + u;
     th = P.tr + p1 * ds / den;
     dth = p1 * ds * p2 * (u / h) / (den * den);
   } else if (MODEL == GARDNER) {
-    const double e = exp(p1 * psi);
+    const double e = fx::exp(p1 * psi);
     th = P.tr + ds * e;
     dth = p1 * ds * e;
   } else {
     // Se = (1 + t)^-m, t = (alpha h)^n, m = 1 - 1/n
     const double n = p2, m = 1.0 - 1.0 / n;
-    const double t = exp(n * log(p1 * h));
-    const double Se = exp(-m * log1p(t));
+    const double t = fx::exp(n * fx::log(p1 * h));
+    const double Se = fx::exp(-m * fx::log1p(t));
     th = P.tr + ds * Se;
     dth = ds * m * n * (t / h) * Se / (1.0 + t);
   }
@@ -158,10 +160,10 @@ template <int MODEL>
 __device__ __forceinline__ double theta_only_d(double psi, double p1, double p2, const Phys<double>& P) {
   if (!(psi < 0.0)) return P.ts;
   const double h = -psi, ds = P.ts - P.tr;
-  if (MODEL == HAVERKAMP) return P.tr + p1 * ds / (p1 + exp(p2 * log(h)));
-  if (MODEL == GARDNER) return P.tr + ds * exp(p1 * psi);
+  if (MODEL == HAVERKAMP) return P.tr + p1 * ds / (p1 + fx::exp(p2 * fx::log(h)));
+  if (MODEL == GARDNER) return P.tr + ds * fx::exp(p1 * psi);
   const double n = p2, m = 1.0 - 1.0 / n;
-  return P.tr + ds * exp(-m * log1p(exp(n * log(p1 * h))));
+  return P.tr + ds * fx::exp(-m * fx::log1p(fx::exp(n * fx::log(p1 * h))));
 }
 
 // Hydraulic conductivity.  For van Genuchten-Mualem, Se^{1/m} = 1/(1+t), so
@@ -172,15 +174,15 @@ __device__ __forceinline__ double cond_d(double psi, double p1, double p2, doubl
                                          const Phys<double>& P) {
   if (!(psi < 0.0)) return Ks;
   const double h = -psi;
-  if (MODEL == HAVERKAMP) return Ks * P.p3 / (P.p3 + exp(P.p4 * log(h)));
-  if (MODEL == GARDNER) return Ks * exp(p1 * psi);
+  if (MODEL == HAVERKAMP) return Ks * P.p3 / (P.p3 + fx::exp(P.p4 * fx::log(h)));
+  if (MODEL == GARDNER) return Ks * fx::exp(p1 * psi);
   const double n = p2, m = 1.0 - 1.0 / n;
-  const double lt = n * log(p1 * h);
-  const double t = exp(lt);
-  const double L1 = log1p(t);
-  const double lr = t > 1.0 ? -log1p(1.0 / t) : lt - L1;     // log(t/(1+t))
-  const double inner = -expm1(m * lr);
-  return Ks * exp(-P.p3 * m * L1) * inner * inner;
+  const double lt = n * fx::log(p1 * h);
+  const double t = fx::exp(lt);
+  const double L1 = fx::log1p(t);
+  const double lr = t > 1.0 ? -fx::log1p(1.0 / t) : lt - L1;     // log(t/(1+t))
+  const double inner = -fx::expm1(m * lr);
+  return Ks * fx::exp(-P.p3 * m * L1) * inner * inner;
 }
 
 __device__ __forceinline__ double cond_model_d(int model, double psi, double p1, double p2,

@@ -1,0 +1,65 @@
+"""Writes fp64_tables.h: the constants of the table-driven FP64 elementary
+functions in fp64math.cuh (run from this directory: python gen_fp64_tables.py).
+
+Every value is computed in 60-digit decimal arithmetic from its definition
+and rounded once to the nearest double (hi), with the remainder rounded to a
+second double (lo) where a pair is kept:
+  2^(j/64) and 2^(j/64) - 1 for j = -32 .. 31       (exp, expm1)
+  log(1 + k/128) (k < 64), log((1 + k/128)/2) (k >= 64) and 1/(1 + k/128)
+                                                    (log, log1p)
+  ln 2 / 64 and ln 2 split so that a multiple by a small integer is exact.
+"""
+import math
+from decimal import Decimal, getcontext
+
+getcontext().prec = 60
+LN2 = Decimal(2).ln()
+
+
+def hx(x):
+    return float(x).hex()
+
+
+def pair(d):
+    hi = float(d)
+    lo = float(d - Decimal(hi))
+    return hi, lo
+
+
+def split_bits(d, bits):
+    """d rounded to a double whose significand has at most `bits` bits, and
+    the rounded remainder."""
+    f = float(d)
+    e = math.frexp(f)[1]
+    hi = math.ldexp(math.floor(math.ldexp(f, bits - e)), e - bits)
+    lo = float(d - Decimal(hi))
+    return hi, lo
+
+
+lines = ["// Generated by gen_fp64_tables.py; do not edit.  Constants of the",
+         "// table-driven FP64 exp / expm1 / log / log1p of fp64math.cuh.",
+         "#pragma once", "", "namespace rich {", "namespace fx {", ""]
+hi, lo = split_bits(LN2 / 64, 35)   # N * hi exact for |N| < 2^18
+lines += [f"constexpr double LN2_64_HI = {hx(hi)};", f"constexpr double LN2_64_LO = {hx(lo)};",
+          f"constexpr double INV_LN2_64 = {hx(Decimal(64) / LN2)};"]
+hi, lo = split_bits(LN2, 42)        # e * hi exact for |e| < 2^11
+lines += [f"constexpr double LN2_HI = {hx(hi)};", f"constexpr double LN2_LO = {hx(lo)};", ""]
+lines.append("// 2^(j/64) (hi, lo) and 2^(j/64) - 1 (hi, lo), j = -32 .. 31 at index j + 32")
+lines.append("__device__ const double kExp2[64][4] = {")
+for j in range(-32, 32):
+    t = (LN2 * j / 64).exp()
+    a, b = pair(t)
+    c, d = pair(t - 1)
+    lines.append(f"    {{{hx(a)}, {hx(b)}, {hx(c)}, {hx(d)}}},")
+lines.append("};")
+lines.append("// log(F) (hi, lo) with F = 1 + k/128 for k < 64 and F = (1 + k/128)/2 for")
+lines.append("// k >= 64 (the argument is then taken as 2^(e+1) F), and 1 / (1 + k/128)")
+lines.append("__device__ const double kLogF[128][3] = {")
+for k in range(128):
+    F = 1 + Decimal(k) / 128
+    a, b = pair((F if k < 64 else F / 2).ln())
+    lines.append(f"    {{{hx(a)}, {hx(b)}, {hx(1 / F)}}},")
+lines.append("};")
+lines += ["", "}  // namespace fx", "}  // namespace rich", ""]
+with open("fp64_tables.h", "w") as f:
+    f.write("\n".join(lines))

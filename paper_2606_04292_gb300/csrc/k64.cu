@@ -872,4 +872,28 @@ void apply_delta(double* u, const float* delta, long long n, cudaStream_t s) {
   k_apply_delta<<<grid_for(n), 256, 0, s>>>(u, delta, n);
 }
 
+// The FP64 elementary functions of the laws (fn 0 exp, 1 expm1, 2 log,
+// 3 log1p) and, for comparison, CUDA's (fn 4..7 in the same order).
+__global__ void __launch_bounds__(256) k_math_eval(int fn, const double* __restrict__ x, double* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    double r;
+    switch (fn) {
+      case 0: r = fx::exp(v); break;
+      case 1: r = fx::expm1(v); break;
+      case 2: r = fx::log(v); break;
+      case 3: r = fx::log1p(v); break;
+      case 4: r = ::exp(v); break;
+      case 5: r = ::expm1(v); break;
+      case 6: r = ::log(v); break;
+      default: r = ::log1p(v); break;
+    }
+    y[i] = r;
+  }
+}
+
+void math_eval(int fn, const double* x, double* y, long long n, cudaStream_t s) {
+  k_math_eval<<<grid_for(n), 256, 0, s>>>(fn, x, y, n);
+}
+
 }  // namespace rich

@@ -115,6 +115,9 @@ int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const P
 void restrict_face32(const Geom& F, const Geom& C, const Xfer<float>& X, int axis, const float* fine, float* coarse,
                      cudaStream_t s);
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);
+// y = f(x) elementwise for the laws' FP64 elementary functions (fn 0..3:
+// exp, expm1, log, log1p) or CUDA's (fn 4..7), device arrays
+void math_eval(int fn, const double* x, double* y, long long n, cudaStream_t s);
 // sets *bad to 1 if any of x[0..n) is NaN or infinite (device arrays)
 void flag_nonfinite(const double* x, long long n, unsigned* bad, cudaStream_t s);
 // theta(psi) and K(psi) per cell (FP64 or float-float); outputs nullable

@@ -129,6 +129,7 @@ _SIGS = {
                                          C.POINTER(C.c_longlong)]),
     "richards_columns_set_threads": (C.c_int, [_VP, C.c_int]),
     "richards_columns_autotune": (C.c_int, [_VP, C.c_double, C.c_int, C.POINTER(C.c_int)]),
+    "richards_math_eval": (C.c_int, [C.c_int, _DP, _DP, C.c_longlong, _VP]),
     "richards_autotune": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "richards_set_launch": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, C.c_int]),
     "richards_batcher_create": (C.c_int, [_VP, C.c_int, C.POINTER(_VP)]),
