@@ -47,9 +47,10 @@ DTYPE = {2: "f32 inner / f64 outer, f64 state", 1: "f32 inner / float-float (f32
 # figure is the mixed-mode inner update of the heterogeneous workload:
 # delta read+write, Kc, r, psi0, alpha, n (7 x 4 B).
 # DRAM bytes (read + write) per launch of the finest level's half-sweep of
-# 256^3 (8,388,608 cells), from an ncu capture of this kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum); the roofline's traffic.
-TRAFFIC_PER_LAUNCH = {}
+# 256^3 (8,388,608 cells, colour-split parameters, 128-thread blocks, two
+# planes), from an ncu capture of this kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); the roofline's traffic.
+TRAFFIC_PER_LAUNCH = {("sweep32", 8388608): 318.5e6}
 
 BYTES_PER_CELL = {
     "sweep32": 28.0,
