@@ -319,6 +319,15 @@ richards_status richards_autotune(richards_ctx *ctx, int reps, int *planes_out, 
    candidate sets above. */
 richards_status richards_set_launch(richards_ctx *ctx, int level, int planes, int block_x, int resid_block_x);
 
+/* FP32 inner cycles: the levels below the finest with at most max_cells
+   cells, down to the coarsest, run as one cooperative launch per visit --
+   every block of the grid walks the cycle, with a grid barrier between
+   stages instead of a launch per stage, and block 0 alone takes the levels
+   of the single-block tail.  Same values as the stage launches.  Off (0) by
+   default: on the 256^3 drainage the grid barriers cost more than the
+   graph-replayed launches they replace.  EINVAL for a negative size. */
+richards_status richards_set_coop(richards_ctx *ctx, long long max_cells);
+
 /* ---------------------------------------------------------------------
  * Lockstep batch of resident contexts (continuous batching of served
  * requests, at the granularity of a time step).  richards_batcher_step takes

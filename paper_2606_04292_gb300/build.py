@@ -56,8 +56,18 @@ def build(force=False, verbose=False, extra=()):
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    def cleanup():
+        for src in SOURCES:
+            o = os.path.join(OUT_DIR, src.replace(".cu", f".{tag}.o"))
+            if os.path.exists(o):
+                os.remove(o)
+
+    try:
+        with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+            results = list(ex.map(compile_one, SOURCES))
+    except Exception:
+        cleanup()           # objects of the units that did compile
+        raise
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:

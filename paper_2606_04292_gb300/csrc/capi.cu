@@ -28,7 +28,13 @@ using rich::law_error;
 namespace {
 
 constexpr int MAXLEV = 24;
-constexpr int NSCRATCH = 64;   // norm slots + statistics (32..63: the single-block step's)
+constexpr int NSCRATCH = 72;   // norm slots + statistics (32..63: the single-block step's; 64..66: the
+                               // cooperative cycle's reductions)
+// Levels of at most this many cells run as one cooperative launch: 0, off by
+// default -- on the 256^3 drainage its grid barriers cost more than the
+// graph-replayed stage launches they replace (32.8 ms per step without, 33.7
+// with 16^3 and below, 35.0 with 64^3 and below); richards_set_coop turns it on
+constexpr long long COOP_CELLS = 0;
 constexpr int MASS_PARTS = 152 * 32;   // water-balance blocks (grid_for's cap)
 
 struct HLevel {
@@ -123,6 +129,9 @@ struct richards_ctx {
   // richards_set_launch; 0 = the defaults): cells per thread along z of the
   // half-sweeps, their block x-size, the defect kernel's block x-size
   int tune_planes[MAXLEV] = {}, tune_bx[MAXLEV] = {}, tune_rbx[MAXLEV] = {};
+  // FP32 inner cycles: levels from coop_start down to the single-block tail
+  // run as one cooperative launch (MAXLEV: none); its grid size
+  int coop_start = MAXLEV, coop_blocks = 0;
 };
 
 namespace {
@@ -596,6 +605,21 @@ void vcycle64(richards_ctx* c, int l, bool d_ready = false) {
 void vcycle32(richards_ctx* c, int l, bool d_ready = false, bool fuse = false) {
   const int model = c->soil.model;
   const Phys<float> P = phys<float>(c);
+  if (l >= c->coop_start && l < c->tail_start && c->opts.ordering == 1) {
+    if (!c->coop_blocks) {
+      const long long need = (c->L[l].ncell / 2 + rich::COOP_THREADS - 1) / rich::COOP_THREADS;
+      c->coop_blocks = (int)std::max(1LL, std::min<long long>(rich::coop_max_blocks32(model), need));
+    }
+    Prof pr(c, "coop32", l, c->L[l].ncell);
+    const cudaError_t e = rich::coop32(c->dL32, c->dX32, l, c->nlev, c->tail_start, P, model, c->opts.nu1,
+                                       c->opts.nu2, c->opts.coarse_max_sweeps, (float)c->opts.coarse_rtol,
+                                       c->opts.cycle_gamma, c->opts.gamma_levels, c->scratch + 16, c->scratch + 64,
+                                       c->coop_blocks, c->s);
+    if (e == cudaSuccess) return;
+    cudaGetLastError();                 // no cooperative launch here: the stage launches below instead
+    c->graph_err = std::string("cooperative launch: ") + cudaGetErrorString(e);
+    c->coop_start = MAXLEV;
+  }
   if (l >= c->tail_start) {
     Prof pr(c, "tail32", l, c->L[l].ncell);
     rich::tail32(c->dL32, c->dX32, l, c->nlev, P, model, c->opts.nu1, c->opts.nu2, c->opts.coarse_max_sweeps,
@@ -1391,6 +1415,10 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
   for (int l = 0; l < c->nlev; ++l)
     if ((long long)c->L[l].n[0] * c->L[l].n[1] * c->L[l].n[2] <= o.tail_cells) { c->tail_start = l; break; }
   const bool mixed = o.precision >= 1;
+  c->coop_start = MAXLEV;
+  if (o.precision >= 1 && COOP_CELLS > 0)
+    for (int l = 1; l < c->tail_start; ++l)
+      if ((long long)c->L[l].n[0] * c->L[l].n[1] * c->L[l].n[2] <= COOP_CELLS) { c->coop_start = l; break; }
   // the finest FP32 level of a big grid keeps its per-cell parameters in the
   // colour-split layout: a half-sweep then reads only its own colour's sectors
   // of them (the level must have an even n0 and lie above the coarse tail)
@@ -1962,6 +1990,19 @@ richards_status richards_math_eval(int fn, const double* x, double* y, long long
   rich::math_eval(fn, x, y, n, (cudaStream_t)stream);
   if (cudaGetLastError() != cudaSuccess) return RICH_ECUDA;
   return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? RICH_OK : RICH_ECUDA;
+}
+
+richards_status richards_set_coop(richards_ctx* c, long long max_cells) {
+  if (!c || max_cells < 0) return RICH_EINVAL;
+  if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  cudaStreamSynchronize(c->s);
+  graphs_reset(c);
+  c->coop_start = MAXLEV;
+  c->coop_blocks = 0;
+  if (max_cells > 0 && c->opts.precision >= 1)
+    for (int l = 1; l < c->tail_start; ++l)
+      if (c->L[l].ncell <= max_cells) { c->coop_start = l; break; }
+  return RICH_OK;
 }
 
 richards_status richards_set_launch(richards_ctx* c, int level, int planes, int block_x, int resid_block_x) {

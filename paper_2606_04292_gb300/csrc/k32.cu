@@ -21,6 +21,14 @@ void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, con
             int ordering, cudaStream_t s) {
   D::tail(dLs, dXs, l0, nl, P, model, nu1, nu2, cmax, crtol, gamma, gamma_levels, stats, ordering, s);
 }
+int coop_max_blocks32(int model) { return D::coop_max_blocks(model); }
+cudaError_t coop32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, int tail_start,
+                   const Phys<float>& P, int model, int nu1, int nu2, int cmax, float crtol, int gamma,
+                   int gamma_levels, unsigned long long* stats, unsigned long long* slots, int blocks,
+                   cudaStream_t s) {
+  return D::coop(dLs, dXs, l0, nl, tail_start, P, model, nu1, nu2, cmax, crtol, gamma, gamma_levels, stats, slots,
+                 blocks, s);
+}
 void residual_color32(const Level<float>& L, const Phys<float>& P, int model, int color, unsigned long long* norm,
                       cudaStream_t s) {
   D::residual_color(L, P, model, color, norm, s);

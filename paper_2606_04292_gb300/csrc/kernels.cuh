@@ -4,6 +4,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "device.cuh"
 #include "launch.h"
 
@@ -329,12 +331,10 @@ __device__ __forceinline__ void prolong_taps(const Xfer<T>& X, int a, int i, int
   w[1] = c > 1 ? X.pw[a][2 * i + 1] : T(0);
 }
 
+// the interpolated coarse correction of fine cell (i0, i1, i2), nested levels
 template <typename T>
-__device__ __forceinline__ void prolong_nested_body(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, int bx,
-                                                    int by, int bz) {
-  const int i0 = bx * blockDim.x + threadIdx.x;
-  const int i1 = by, i2 = bz;
-  if (i0 >= F.n0) return;
+__device__ __forceinline__ T prolong_nested_at(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, int i0, int i1,
+                                               int i2) {
   int jx[2], jy[2], jz[2];
   T wx[2], wy[2], wz[2];
   prolong_taps<T>(X, 0, i0, F.n0, jx, wx);
@@ -356,8 +356,46 @@ __device__ __forceinline__ void prolong_nested_body(const Level<T>& F, const Lev
     }
     s += wz[c] * sy;
   }
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_nested_body(const Level<T>& F, const Level<T>& C, const Xfer<T>& X, int bx,
+                                                    int by, int bz) {
+  const int i0 = bx * blockDim.x + threadIdx.x;
+  const int i1 = by, i2 = bz;
+  if (i0 >= F.n0) return;
   const unsigned i = (unsigned)(i0 + F.n0 * (i1 + F.n1 * i2));
-  F.u[i] += s;
+  F.u[i] += prolong_nested_at(F, C, X, i0, i1, i2);
+}
+
+// one coarse value of the nested full-weighting restriction of a natural
+// layout array (the arithmetic of restrict_nested_body, one array)
+template <typename T>
+__device__ __forceinline__ T restrict_nested_at(const Level<T>& F, const Level<T>& C, const T* fa, int J0, int J1,
+                                                int J2) {
+  int x[4], y[4], z[4];
+  T wx[4], wy[4], wz[4];
+  restrict_taps<T>(J0, C.n0, F.n0, x, wx);
+  restrict_taps<T>(J1, C.n1, F.n1, y, wy);
+  restrict_taps<T>(J2, C.n2, F.n2, z, wz);
+  T sa = T(0);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (wz[c] == T(0)) continue;
+    T ya = T(0);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (wy[b] == T(0)) continue;
+      const unsigned row = (unsigned)F.n0 * ((unsigned)y[b] + (unsigned)F.n1 * (unsigned)z[c]);
+      T xa = T(0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xa += wx[a] * fa[row + x[a]];
+      ya += wy[b] * xa;
+    }
+    sa += wz[c] * ya;
+  }
+  return sa;
 }
 
 template <typename T>
@@ -435,7 +473,7 @@ inline bool tiled_transfer(int dim, int fn0, int fn1, int fn2) {
   return dim == 3 && fn2 >= 4 && fn1 >= 4 && (long long)fn0 * fn1 * fn2 >= (1LL << 15);
 }
 
-inline bool nested_levels(int fn0, int fn1, int fn2, int cn0, int cn1, int cn2) {
+__host__ __device__ inline bool nested_levels(int fn0, int fn1, int fn2, int cn0, int cn1, int cn2) {
   const int f[3] = {fn0, fn1, fn2}, c[3] = {cn0, cn1, cn2};
   for (int a = 0; a < 3; ++a)
     if (!(f[a] == 2 * c[a] || (f[a] == 1 && c[a] == 1))) return false;
@@ -448,100 +486,155 @@ inline bool nested_levels(int fn0, int fn1, int fn2, int cn0, int cn1, int cn2) 
 // a kernel per stage).  Same arithmetic as the grid kernels, phase by phase,
 // separated by block barriers.
 // ---------------------------------------------------------------------------
-// one NGS sweep of a level by one thread block: red then black half-sweeps
-// (ordering 1), or the lexicographic order hyperplane by hyperplane (0)
-template <typename T, int FORM, int MODEL>
-__device__ __forceinline__ void block_sweep(const Level<T>& L, const Phys<T>& P, int ordering = 1) {
+// The cycle's loops run over a "team" of threads: one thread block (the
+// coarse tail, the batched columns, the single-block step) or every thread of
+// a cooperative grid (the coarse levels of a big grid: no launch per stage).
+// rank/size index the team's threads, sync() is its barrier, max() its
+// max-reduction (every thread gets the result).
+struct BlockTeam {
+  __device__ unsigned rank() const { return threadIdx.x; }
+  __device__ unsigned size() const { return blockDim.x; }
+  __device__ void sync() const { __syncthreads(); }
+  __device__ unsigned long long max(unsigned long long v, unsigned long long* sm) const { return block_max(v, sm); }
+};
+
+// (three global slots rotate: the slot zeroed at one reduction was last read
+// two reductions earlier, with a grid barrier in between)
+struct GridTeam {
+  unsigned long long* slots;
+  int round;
+  __device__ unsigned rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+  __device__ unsigned size() const { return gridDim.x * blockDim.x; }
+  __device__ void sync() const { cooperative_groups::this_grid().sync(); }
+  __device__ unsigned long long max(unsigned long long v, unsigned long long* sm) {
+    v = block_max(v, sm);
+    unsigned long long* s = slots + round % 3;
+    if (threadIdx.x == 0) atomicMax(s, v);
+    if (rank() == 0) slots[(round + 1) % 3] = 0ull;
+    sync();
+    const unsigned long long r = *(volatile unsigned long long*)s;
+    ++round;
+    return r;
+  }
+};
+
+// one NGS sweep of a level by a team: red then black half-sweeps (ordering
+// 1), or the lexicographic order hyperplane by hyperplane (0)
+template <typename T, int FORM, int MODEL, typename TM = BlockTeam>
+__device__ __forceinline__ void block_sweep(const Level<T>& L, const Phys<T>& P, int ordering = 1, TM tm = TM{}) {
   if (ordering == 0) {
     const int nplanes = L.n0 + L.n1 + L.n2 - 2;
     const int nrows = L.n1 * L.n2;
     for (int s = 0; s < nplanes; ++s) {
-      for (int t = threadIdx.x; t < nrows; t += blockDim.x) {
+      for (int t = tm.rank(); t < nrows; t += tm.size()) {
         const int i1 = t % L.n1, i2 = t / L.n1;
         const int i0 = s - i1 - i2;
         if (i0 >= 0 && i0 < L.n0)
           point_update<T, FORM, MODEL>(L, P, (unsigned)(i0 + L.n0 * t), i0, i1, i2);
       }
-      __syncthreads();
+      tm.sync();
     }
     return;
   }
   const long long nh = (long long)((L.n0 + 1) >> 1) * L.n1 * L.n2;
   for (int color = 0; color < 2; ++color) {
-    for (long long t = threadIdx.x; t < nh; t += blockDim.x) {
+    for (long long t = tm.rank(); t < nh; t += tm.size()) {
       int i0, i1, i2;
       long long i;
       if (color_cell(L.n0, L.n1, t, color, i0, i1, i2, i)) point_update<T, FORM, MODEL>(L, P, i, i0, i1, i2);
     }
-    __syncthreads();
+    tm.sync();
   }
 }
 
-template <typename T, int FORM, int MODEL>
-__device__ __forceinline__ T block_defect_norm(const Level<T>& L, const Phys<T>& P, unsigned long long* sm) {
+template <typename T, int FORM, int MODEL, typename TM = BlockTeam>
+__device__ __forceinline__ T block_defect_norm(const Level<T>& L, const Phys<T>& P, unsigned long long* sm,
+                                               TM* tmp = nullptr) {
+  TM local{};
+  TM& tm = tmp ? *tmp : local;
   unsigned long long mx = 0;
-  for (long long i = threadIdx.x; i < L.ncell; i += blockDim.x) {
+  for (long long i = tm.rank(); i < L.ncell; i += tm.size()) {
     int i0, i1, i2;
     cell_coords(L.n0, L.n1, i, i0, i1, i2);
     const T di = L.g[pix(L, i, i0, i1, i2)] - apply_N<T, FORM, MODEL>(L, P, L.u, i, i0, i1, i2);
     const unsigned long long b = nbits(di);
     mx = b > mx ? b : mx;
   }
-  return from_bits<T>(block_max(mx, sm));
+  return from_bits<T>(tm.max(mx, sm));
 }
 
-// Levels l0..nl-1 of one multigrid cycle in one thread block, with the
-// recursion of Section 3.2 unrolled: pre-smoothing, defect, restriction and
-// the FAS right side on the way down; gamma visits of each coarser level
-// (1: V-cycle, 2: W-cycle); the coarsest level sweeps until its defect drops
-// by crtol or cmax sweeps are done; prolongation and post-smoothing on the
-// way up.  LV gives the level views (L(l)) and the transfers from level l:
+// Levels l0..nl-1 of one multigrid cycle by one team, with the recursion of
+// Section 3.2 unrolled: pre-smoothing, defect, restriction and the FAS right
+// side on the way down; gamma visits of each coarser level (1: V-cycle, 2:
+// W-cycle); the coarsest level sweeps until its defect drops by crtol or
+// cmax sweeps are done; prolongation and post-smoothing on the way up.  LV
+// gives the level views (L(l)) and the transfers from level l:
 // restrict(l, fine array, coarse coords) and prolong(l, fine coords).
-template <typename T, int FORM, int MODEL, typename LV>
+// (handoff < nl, grid teams only: from level handoff on, block 0 alone runs
+// the rest of the cycle with block barriers, as the single-block tail does,
+// while the other blocks wait at the next grid barrier; tail_lv gives that
+// part's levels and transfers)
+template <typename T, int FORM, int MODEL>
+struct NoTail {};
+
+template <typename T, int FORM, int MODEL, typename LV, typename TM = BlockTeam, typename TLV = NoTail<T, FORM, MODEL>>
 __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const Phys<T>& P, int nu1, int nu2, int cmax, T crtol,
                             int gamma, int gamma_levels, unsigned long long* sm, unsigned long long& updates,
-                            int ordering = 1) {
+                            int ordering = 1, TM* tmp = nullptr, int handoff = 1 << 30,
+                            const TLV* tail_lv = nullptr) {
+  TM local{};
+  TM& tm = tmp ? *tmp : local;
   int visits[24];
   int l = l0;
   bool down = true;
   for (;;) {
     if (down) {
+      if constexpr (!std::is_same<TLV, NoTail<T, FORM, MODEL>>::value) {
+        if (l == handoff) {
+          if (blockIdx.x == 0)
+            block_cycle<T, FORM, MODEL, TLV>(*tail_lv, l, nl, P, nu1, nu2, cmax, crtol, gamma, gamma_levels, sm,
+                                             updates, ordering);
+          tm.sync();
+          down = false;
+          continue;
+        }
+      }
       if (l == nl - 1) {
         const Level<T>& C = lv.L(l);
-        const T d0 = block_defect_norm<T, FORM, MODEL>(C, P, sm);
+        const T d0 = block_defect_norm<T, FORM, MODEL, TM>(C, P, sm, &tm);
         for (int s = 0; s < cmax; ++s) {
-          block_sweep<T, FORM, MODEL>(C, P, ordering);
+          block_sweep<T, FORM, MODEL, TM>(C, P, ordering, tm);
           updates += C.ncell;
-          const T dn = block_defect_norm<T, FORM, MODEL>(C, P, sm);
+          const T dn = block_defect_norm<T, FORM, MODEL, TM>(C, P, sm, &tm);
           if (!(dn > crtol * d0)) break;
         }
         down = false;
         continue;
       }
       const Level<T>& F = lv.L(l);
-      for (int s = 0; s < nu1; ++s) block_sweep<T, FORM, MODEL>(F, P, ordering);
+      for (int s = 0; s < nu1; ++s) block_sweep<T, FORM, MODEL, TM>(F, P, ordering, tm);
       updates += (unsigned long long)nu1 * F.ncell;
-      for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
+      for (long long i = tm.rank(); i < F.ncell; i += tm.size()) {
         int i0, i1, i2;
         cell_coords(F.n0, F.n1, i, i0, i1, i2);
         F.d[i] = F.g[pix(F, i, i0, i1, i2)] - apply_N<T, FORM, MODEL>(F, P, F.u, i, i0, i1, i2);
       }
-      __syncthreads();
+      tm.sync();
       const Level<T>& C = lv.L(l + 1);
-      for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
+      for (long long J = tm.rank(); J < C.ncell; J += tm.size()) {
         int J0, J1, J2;
         cell_coords(C.n0, C.n1, J, J0, J1, J2);
         C.ubar[J] = lv.restrict(l, F.u, J0, J1, J2);
         C.d[J] = lv.restrict(l, F.d, J0, J1, J2);
       }
-      __syncthreads();
-      for (long long J = threadIdx.x; J < C.ncell; J += blockDim.x) {
+      tm.sync();
+      for (long long J = tm.rank(); J < C.ncell; J += tm.size()) {
         int J0, J1, J2;
         cell_coords(C.n0, C.n1, J, J0, J1, J2);
         C.g[J] = apply_N<T, FORM, MODEL>(C, P, C.ubar, J, J0, J1, J2) + C.d[J];
         C.u[J] = C.ubar[J];
       }
-      __syncthreads();
+      tm.sync();
       visits[l] = 0;
       ++l;
       continue;
@@ -556,13 +649,13 @@ __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const 
       continue;
     }
     const Level<T>& F = lv.L(pl);
-    for (long long i = threadIdx.x; i < F.ncell; i += blockDim.x) {
+    for (long long i = tm.rank(); i < F.ncell; i += tm.size()) {
       int i0, i1, i2;
       cell_coords(F.n0, F.n1, i, i0, i1, i2);
       F.u[i] += lv.prolong(pl, i0, i1, i2);
     }
-    __syncthreads();
-    for (int s = 0; s < nu2; ++s) block_sweep<T, FORM, MODEL>(F, P, ordering);
+    tm.sync();
+    for (int s = 0; s < nu2; ++s) block_sweep<T, FORM, MODEL, TM>(F, P, ordering, tm);
     updates += (unsigned long long)nu2 * F.ncell;
     l = pl;
   }
@@ -589,6 +682,51 @@ __global__ void __launch_bounds__(TAIL_THREADS, 1) k_tail(const Level<T>* __rest
   block_cycle<T, FORM, MODEL>(DeviceLevels<T>{Ls, Xs}, l0, nl, P, nu1, nu2, cmax, crtol, gamma, gamma_levels, sm,
                               updates, ordering);
   if (threadIdx.x == 0 && stats) atomicAdd(stats, updates);
+}
+
+// The coarse levels of a big grid as one cooperative launch: block_cycle run
+// by every thread of the grid, a grid barrier between phases instead of a
+// launch per stage.  Above the single-block tail's first level the transfers
+// are the grid kernels' (nested formulas where the levels nest, tables
+// otherwise), from it on the tail's (tables): the values equal those of the
+// launches it replaces.
+template <typename T>
+struct CoopLevels {
+  const Level<T>* Ls;
+  const Xfer<T>* Xs;
+  int tail_start;
+  __device__ const Level<T>& L(int l) const { return Ls[l]; }
+  __device__ bool nested(int l) const {
+    const Level<T>& F = Ls[l];
+    const Level<T>& C = Ls[l + 1];
+    return l < tail_start && nested_levels(F.n0, F.n1, F.n2, C.n0, C.n1, C.n2);
+  }
+  __device__ T restrict(int l, const T* fine, int J0, int J1, int J2) const {
+    return nested(l) ? restrict_nested_at(Ls[l], Ls[l + 1], fine, J0, J1, J2)
+                     : restrict_at(Ls[l], Xs[l], fine, J0, J1, J2);
+  }
+  __device__ T prolong(int l, int i0, int i1, int i2) const {
+    return nested(l) ? prolong_nested_at(Ls[l], Ls[l + 1], Xs[l], i0, i1, i2) : prolong_at(Ls[l + 1], Xs[l], i0, i1, i2);
+  }
+};
+
+// slots: three global words for the grid reductions; stats: the update count
+template <typename T, int FORM, int MODEL>
+__global__ void __launch_bounds__(COOP_THREADS) k_coop_cycle(const Level<T>* __restrict__ Ls,
+                                                             const Xfer<T>* __restrict__ Xs, int l0, int nl,
+                                                             int tail_start, Phys<T> P, int nu1, int nu2, int cmax,
+                                                             T crtol, int gamma, int gamma_levels,
+                                                             unsigned long long* stats, unsigned long long* slots) {
+  __shared__ unsigned long long sm[33];
+  GridTeam tm{slots, 0};
+  if (tm.rank() == 0) slots[0] = slots[1] = slots[2] = 0ull;
+  tm.sync();
+  unsigned long long updates = 0;
+  const DeviceLevels<T> tail{Ls, Xs};
+  block_cycle<T, FORM, MODEL, CoopLevels<T>, GridTeam, DeviceLevels<T>>(CoopLevels<T>{Ls, Xs, tail_start}, l0, nl, P,
+                                                                        nu1, nu2, cmax, crtol, gamma, gamma_levels,
+                                                                        sm, updates, 1, &tm, tail_start, &tail);
+  if (tm.rank() == 0 && stats) atomicAdd(stats, updates);
 }
 
 // ---------------------------------------------------------------------------
@@ -745,6 +883,31 @@ struct Dispatch {
       k_prolong_nested<T><<<g.grid, g.block, 0, s>>>(F, C, X);
     else
       k_prolong<T><<<g.grid, g.block, 0, s>>>(F, C, X);
+  }
+  // the cooperative coarse cycle: the most blocks that can be co-resident
+  static int coop_max_blocks(int model) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    by_model(model, [&](auto m) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coop_cycle<T, FORM, decltype(m)::value>, COOP_THREADS,
+                                                    0);
+    });
+    return per_sm * nsm;
+  }
+  static cudaError_t coop(const Level<T>* dLs, const Xfer<T>* dXs, int l0, int nl, int tail_start, const Phys<T>& P,
+                          int model, int nu1, int nu2, int cmax, T crtol, int gamma, int gamma_levels,
+                          unsigned long long* stats, unsigned long long* slots, int blocks, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    Phys<T> Pv = P;
+    void* args[] = {(void*)&dLs, (void*)&dXs, (void*)&l0, (void*)&nl, (void*)&tail_start, (void*)&Pv, (void*)&nu1,
+                    (void*)&nu2, (void*)&cmax, (void*)&crtol, (void*)&gamma, (void*)&gamma_levels, (void*)&stats,
+                    (void*)&slots};
+    by_model(model, [&](auto m) {
+      e = cudaLaunchCooperativeKernel((const void*)k_coop_cycle<T, FORM, decltype(m)::value>, dim3(blocks),
+                                      dim3(COOP_THREADS), args, 0, s);
+    });
+    return e;
   }
   static void tail(const Level<T>* dLs, const Xfer<T>* dXs, int l0, int nl, const Phys<T>& P, int model,
                    int nu1, int nu2, int cmax, T crtol, int gamma, int gamma_levels, unsigned long long* stats,

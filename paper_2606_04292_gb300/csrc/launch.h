@@ -56,6 +56,15 @@ void tail32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, con
             int model, int nu1, int nu2, int cmax, float crtol, int gamma, int gamma_levels,
             unsigned long long* stats, int ordering, cudaStream_t s);
 void sweep_lex32(const Level<float>& L, const Phys<float>& P, int model, cudaStream_t s);
+// the cycle from level l0 down as one cooperative launch of `blocks` blocks
+// (levels from tail_start on take the single-block tail's transfers); slots:
+// three device words for its reductions; stats: its update count
+constexpr int COOP_THREADS = 256;
+int coop_max_blocks32(int model);
+cudaError_t coop32(const Level<float>* dLs, const Xfer<float>* dXs, int l0, int nl, int tail_start,
+                   const Phys<float>& P, int model, int nu1, int nu2, int cmax, float crtol, int gamma,
+                   int gamma_levels, unsigned long long* stats, unsigned long long* slots, int blocks,
+                   cudaStream_t s);
 // the last (colour 1) half-sweep of a smoothing that also writes its cells' defects and their
 // max into *norm (pipelined two-plane levels only: resid_fusable32), and the defects of one colour
 bool resid_fusable32(const Level<float>& L, int planes);

@@ -132,6 +132,7 @@ _SIGS = {
     "richards_math_eval": (C.c_int, [C.c_int, _DP, _DP, C.c_longlong, _VP]),
     "richards_autotune": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "richards_set_launch": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "richards_set_coop": (C.c_int, [_VP, C.c_longlong]),
     "richards_batcher_create": (C.c_int, [_VP, C.c_int, C.POINTER(_VP)]),
     "richards_batcher_destroy": (None, [_VP]),
     "richards_batcher_last_error": (C.c_char_p, [_VP]),
@@ -378,6 +379,9 @@ class Solver:
         pl, bx, rb = (C.c_int * n)(), (C.c_int * n)(), (C.c_int * n)()
         _check(lib().richards_autotune(self.h, int(reps), pl, bx, rb), self.h)
         return [(pl[k], bx[k], rb[k]) for k in range(n)]
+
+    def set_coop(self, max_cells):
+        _check(lib().richards_set_coop(self.h, int(max_cells)), self.h)
 
     def set_launch(self, level, planes=0, block_x=0, resid_block_x=0):
         _check(lib().richards_set_launch(self.h, int(level), int(planes), int(block_x), int(resid_block_x)), self.h)

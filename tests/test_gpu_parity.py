@@ -881,3 +881,33 @@ def test_colour_split_layout_gives_the_same_bits(precision, extra):
         assert sa == sb == R.RICH_OK
         assert ia["cycles"] == ib["cycles"] and ia["outer_iters"] == ib["outer_iters"], (k, ia, ib)
         assert np.array_equal(split.state(), natural.state()), k
+
+
+@pytest.mark.parametrize("n,gamma", [(64, 2), (96, 1), (50, 2)])
+def test_cooperative_coarse_cycle_gives_the_same_bits(n, gamma):
+    """The coarse levels of the FP32 inner cycles as one cooperative launch
+    per visit (grid barriers between stages) compute what the stage launches
+    compute: steps with it equal steps without it bit for bit, nested (64, 96)
+    and odd (50: 25, 13, 7 cells per axis) hierarchies, V- and W-cycles, with
+    the inner cycle captured into a CUDA graph and launched directly."""
+    prob = W.drainage_3d(n=n, nsteps=3, precision=2, cycle_gamma=gamma, gamma_levels=0, tail_cells=64,
+                         coarsest_max_n=4)
+    stream = torch.cuda.Stream()
+    coop = R.Solver(prob, stream=stream.cuda_stream)
+    coop.set_coop(1 << 18)
+    plain = R.Solver(prob, stream=stream.cuda_stream)
+    direct = R.Solver(W.with_opts(prob, graphs=0), stream=stream.cuda_stream)
+    direct.set_coop(1 << 18)
+    for k in range(3):
+        sa, ia = coop.step()
+        sb, ib = plain.step()
+        sc, ic = direct.step()
+        assert sa == sb == sc == R.RICH_OK
+        assert ia["cycles"] == ib["cycles"] == ic["cycles"], (k, ia, ib, ic)
+        assert ia["cell_updates"] == ib["cell_updates"] == ic["cell_updates"], (k, ia, ib, ic)
+        assert np.array_equal(coop.state(), plain.state()), k
+        assert np.array_equal(coop.state(), direct.state()), k
+    direct.profile(True)
+    direct.step()
+    names = {r["name"] for r in direct.profile_read()}
+    assert "coop32" in names, names
