@@ -154,7 +154,13 @@ typedef struct {
                           fields, sink) with each colour's cells packed
                           together, so a half-sweep reads only its own
                           colour's memory; 1 = the natural layout everywhere
-                          (same results: only where values sit changes) */
+                          (same results: only where values sit changes)
+     bdf2_lag             BDF2 state at which K and the xi term are lagged:
+                          0 = psi* = 2 psi^n - psi^(n-1) (second order in
+                          time); 1 = psi* = psi^n, the lag of eq. (fully-bdf1)
+                          (first order in the lag, robust where a sharp
+                          wetting front makes the extrapolated K jump by
+                          orders of magnitude between steps) */
 typedef struct {
   int nu1, nu2, coarse_max_sweeps;
   double coarse_rtol;
@@ -166,6 +172,7 @@ typedef struct {
   double inner_rtol;
   int max_outer, tail_cells, cycle_gamma, gamma_levels, graphs, sweep_planes, predictor, fmg_cycles;
   int layout;
+  int bdf2_lag;
 } richards_opts;
 
 typedef struct {

@@ -72,7 +72,7 @@ class _Opts(C.Structure):
                 ("max_levels", C.c_int), ("kappa_mode", C.c_int), ("kappa", C.c_double),
                 ("xi", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("ordering", C.c_int), ("newton_iters", C.c_int), ("cycle_gamma", C.c_int),
-                ("gamma_levels", C.c_int), ("fmg_cycles", C.c_int)]
+                ("gamma_levels", C.c_int), ("fmg_cycles", C.c_int), ("bdf2_lag", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -180,7 +180,8 @@ class Oracle:
         opts = _Opts(o["nu1"], o["nu2"], o["coarse_max_sweeps"], o["coarse_rtol"],
                      o["coarsest_max_n"], o["max_levels"], o["kappa_mode"], o["kappa"],
                      o["xi"], o["tol"], o["max_cycles"], o["ordering"], o["newton_iters"],
-                     o.get("cycle_gamma", 1), o.get("gamma_levels", 0), o.get("fmg_cycles", 0))
+                     o.get("cycle_gamma", 1), o.get("gamma_levels", 0), o.get("fmg_cycles", 0),
+                     o.get("bdf2_lag", 0))
         self.h = L.orc_create(C.byref(g), C.byref(soil), C.byref(bc), C.byref(sink),
                               C.byref(opts))
         if not self.h:

@@ -581,7 +581,7 @@ int orc_prepare(orc_ctx *c, double dt, int scheme) {
       c->hist[i] = thn / dt;
     } else {
       soil_law(soil_of(c, L, i), L->p1[i], L->p2[i], c->Ks[i], c->psi_nm1[i], &thm, NULL, NULL);
-      c->psistar[i] = 2.0 * c->psi_n[i] - c->psi_nm1[i];
+      c->psistar[i] = c->opts.bdf2_lag ? c->psi_n[i] : 2.0 * c->psi_n[i] - c->psi_nm1[i];
       c->hist[i] = (4.0 * thn - thm) / (2.0 * dt);
     }
     soil_law(soil_of(c, L, i), L->p1[i], L->p2[i], c->Ks[i], c->psistar[i], NULL, NULL, &L->Kc[i]);

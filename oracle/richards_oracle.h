@@ -81,6 +81,9 @@ typedef struct {
   int cycle_gamma;     /* coarse-grid visits per level: 1 V-cycle, 2 W-cycle */
   int gamma_levels;    /* cycle_gamma applies on levels < gamma_levels (0: all) */
   int fmg_cycles;      /* > 0: full multigrid pass first, this many cycles per level */
+  int bdf2_lag;        /* BDF2 state of the lagged K and the xi term: 0 psi* = 2 psi^n -
+                          psi^(n-1) (second order), 1 psi* = psi^n (the lag of eq.
+                          fully-bdf1) */
 } orc_opts;
 
 typedef struct {

@@ -448,6 +448,7 @@ Phys<T> phys(const richards_ctx* c) {
   P.h1 = (T)c->sink.h1; P.h2 = (T)c->sink.h2; P.h3 = (T)c->sink.h3; P.h4 = (T)c->sink.h4;
   P.newton_k = c->opts.newton_iters;
   P.sink = c->sink.enabled;
+  P.lag = c->opts.bdf2_lag;
   if (c->layered) {
     if constexpr (std::is_same<T, double>::value) P.mats = c->dmat64;
     else P.mats = c->dmat32;
@@ -1384,7 +1385,7 @@ richards_status richards_create(const richards_grid* grid, const richards_opts* 
       (o.ordering != 0 && o.ordering != 1) || (o.precision < 0 || o.precision > 2) || !(o.xi >= 0.0) || !(o.kappa >= 0.0) ||
       o.inner_cycles < 1 || o.max_outer < 0 || o.tail_cells < 0 || o.cycle_gamma < 1 || o.cycle_gamma > 3 ||
       o.gamma_levels < 0 || (o.graphs != 0 && o.graphs != 1) || (o.predictor != 0 && o.predictor != 1) ||
-      o.fmg_cycles < 0 || o.fmg_cycles > 16 || (o.layout != 0 && o.layout != 1) ||
+      o.fmg_cycles < 0 || o.fmg_cycles > 16 || (o.layout != 0 && o.layout != 1) || (o.bdf2_lag != 0 && o.bdf2_lag != 1) ||
       (o.sweep_planes != 1 && o.sweep_planes != 2 && o.sweep_planes != 4 && o.sweep_planes != 8))
     return RICH_EINVAL;
   richards_ctx* c = new richards_ctx();

@@ -47,7 +47,7 @@ struct ColArgs {
   int sink;
   int fp64;                        // outer layer: 1 FP64 (precision 2), 0 float-float
   double h1, h2, h3, h4, xi, kappa, tol, inner_rtol, crtol, dt;
-  int newton_k, max_outer, inner_cycles, nu1, nu2, cmax, gamma, gamma_levels, coarsest_max_n, scheme, nsteps,
+  int newton_k, max_outer, inner_cycles, nu1, nu2, cmax, gamma, gamma_levels, coarsest_max_n, scheme, nsteps, lag,
       model;
 };
 
@@ -161,12 +161,12 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
   P64.xi = A.xi; P64.kappa = A.kappa; P64.ts = D.ts; P64.tr = D.tr;
   P64.p1 = D.p1; P64.p2 = D.p2; P64.p3 = D.p3; P64.p4 = D.p4;
   P64.h1 = A.h1; P64.h2 = A.h2; P64.h3 = A.h3; P64.h4 = A.h4;
-  P64.newton_k = A.newton_k; P64.sink = A.sink;
+  P64.newton_k = A.newton_k; P64.sink = A.sink; P64.lag = A.lag;
   Phys<float> P32{};
   P32.xi = (float)A.xi; P32.kappa = (float)A.kappa; P32.ts = (float)D.ts; P32.tr = (float)D.tr;
   P32.p1 = (float)D.p1; P32.p2 = (float)D.p2; P32.p3 = (float)D.p3; P32.p4 = (float)D.p4;
   P32.h1 = (float)A.h1; P32.h2 = (float)A.h2; P32.h3 = (float)A.h3; P32.h4 = (float)A.h4;
-  P32.newton_k = A.newton_k; P32.sink = A.sink;
+  P32.newton_k = A.newton_k; P32.sink = A.sink; P32.lag = A.lag;
   double* psin = A.psin + off;
   double* psinm1 = A.psinm1 + off;
   double* thn = A.thn + off;
@@ -211,7 +211,7 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
         hist = th / A.dt;
       } else {
         const double pm = psinm1[i];
-        ps = 2.0 * pnd - pm;
+        ps = A.lag ? pnd : 2.0 * pnd - pm;
         hist = (4.0 * th - theta_only_d<MODEL>(pm, D.p1, D.p2, P64)) / (2.0 * A.dt);
       }
       A.Kc[off + i] = cond_d<MODEL>(ps, D.p1, D.p2, D.Ks, P64);
@@ -234,7 +234,7 @@ __device__ void column_solve(const ColArgs& A, int c, float* smem, Level<float>*
         hist = dd_mul(th, hist_scale);
       } else {
         const dd pm = dd_split(psinm1[i]);
-        ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
+        ps = A.lag ? pn : dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
         hist = dd_mul(dd_sub(mk(4.0f * th.hi, 4.0f * th.lo), theta_x<MODEL>(pm, Q.p1, Q.p2, Q, P64)), hist_scale);
       }
       A.Kc[off + i] = dd_join(cond_x<MODEL>(ps, Q.p1, Q.p2, Ks, Q, P64));
@@ -490,7 +490,7 @@ richards_status launch_columns(richards_columns* c, double dt, int nsteps, int s
   A.crtol = o.coarse_rtol; A.dt = dt; A.newton_k = o.newton_iters; A.max_outer = o.max_outer;
   A.inner_cycles = o.inner_cycles; A.nu1 = o.nu1; A.nu2 = o.nu2; A.cmax = o.coarse_max_sweeps;
   A.gamma = o.cycle_gamma; A.gamma_levels = o.gamma_levels; A.coarsest_max_n = o.coarsest_max_n;
-  A.scheme = scheme; A.nsteps = nsteps; A.model = c->model;
+  A.scheme = scheme; A.nsteps = nsteps; A.model = c->model; A.lag = o.bdf2_lag;
   A.fp64 = o.precision == 2 ? 1 : 0;
   const size_t smem = column_smem(c->max_n, o.coarsest_max_n);
   auto kern = c->model == HAVERKAMP ? k_columns<HAVERKAMP> : (c->model == GARDNER ? k_columns<GARDNER>
@@ -523,7 +523,8 @@ richards_status richards_columns_create(int ncol, const richards_column* cols, c
   if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max_sweeps < 1 || o.coarsest_max_n < 1 || !(o.tol > 0.0) ||
       o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) || o.ordering != 1 ||
       !(o.xi >= 0.0) || !(o.kappa >= 0.0) || o.inner_cycles < 1 || o.max_outer < 0 || o.cycle_gamma < 1 ||
-      o.cycle_gamma > 3 || o.gamma_levels < 0 || o.precision < 0 || o.precision > 2)
+      o.cycle_gamma > 3 || o.gamma_levels < 0 || o.precision < 0 || o.precision > 2 ||
+      (o.bdf2_lag != 0 && o.bdf2_lag != 1))
     return RICH_EINVAL;
   if (rich::sink_error(*sink)) return RICH_EINVAL;
   const int model = cols[0].soil.model;

@@ -77,6 +77,7 @@ struct Phys {
   T h1, h2, h3, h4;              // sink thresholds
   int newton_k;                  // > 0: fixed steps; 0: to round-off
   int sink;
+  int lag;                       // BDF2: 1 lags K and the xi term at psi^n, 0 at 2 psi^n - psi^(n-1)
   const MatLaw<T> *mats;         // COMPOSITE: material table (device, MAXMAT entries at most)
   const DDMat *ddmats;           // COMPOSITE, float-float outer layer: the same table as pairs
 };
@@ -168,7 +169,11 @@ __device__ __forceinline__ double theta_only_d(double psi, double p1, double p2,
 
 // Hydraulic conductivity.  For van Genuchten-Mualem, Se^{1/m} = 1/(1+t), so
 // 1 - (1 - Se^{1/m})^m = -expm1(m log(t/(1+t))), evaluated without
-// cancellation in both the wet (t < 1) and the dry (t > 1) range.
+// cancellation in both the wet (t < 1) and the dry (t > 1) range.  With
+// lt = log t and e = exp(-|lt|) (t when t <= 1, 1/t when t > 1):
+//   log(1 + t)       = log1p(e) + max(lt, 0),
+//   log(t / (1 + t)) = min(lt, 0) - log1p(e),
+// one exponential and one log1p for both ranges, no division and no branch.
 template <int MODEL>
 __device__ __forceinline__ double cond_d(double psi, double p1, double p2, double Ks,
                                          const Phys<double>& P) {
@@ -178,9 +183,9 @@ __device__ __forceinline__ double cond_d(double psi, double p1, double p2, doubl
   if (MODEL == GARDNER) return Ks * fx::exp(p1 * psi);
   const double n = p2, m = 1.0 - 1.0 / n;
   const double lt = n * fx::log(p1 * h);
-  const double t = fx::exp(lt);
-  const double L1 = fx::log1p(t);
-  const double lr = t > 1.0 ? -fx::log1p(1.0 / t) : lt - L1;     // log(t/(1+t))
+  const double l1 = fx::log1p(fx::exp(-fabs(lt)));
+  const double L1 = l1 + fmax(lt, 0.0);
+  const double lr = fmin(lt, 0.0) - l1;
   const double inner = -fx::expm1(m * lr);
   return Ks * fx::exp(-P.p3 * m * L1) * inner * inner;
 }

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
           thm = theta_only_d<ML>(pm, p1, p2, Q);
           if (thm_out) thm_out[i] = thm;
         }
-        ps = 2.0 * pn - pm;
+        ps = P.lag ? pn : 2.0 * pn - pm;
         hist = (4.0 * thn - thm) / (2.0 * dt);
       }
       const double K = cond_d<ML>(ps, p1, p2, ks, Q);
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_prep_lagged_dd(long long n, const doubl
           thm = theta_x<ML>(pm, p1, p2, Qc, Pc);
           if (thm_out) thm_out[i] = dd_join(thm);
         }
-        ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
+        ps = Pc.lag ? pn : dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
         hist = dd_mul(dd_sub(mk(4.0f * thn.hi, 4.0f * thn.lo), thm), hist_scale);
       }
       const dd K = cond_x<ML>(ps, p1, p2, Ks ? dd_split(Ks[i]) : Ks_s, Qc, Pc);
@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(256) k_mass_balance(Level<double> L, Geom G, B
         const dd pm = dd_split(psinm1[i]);
         const dd thm = th_nm1 ? dd_split(th_nm1[i]) : theta_x<ML>(pm, p1, p2, Qc, Pc);
         hist = dd_mul(dd_sub(mk(4.0f * thn.hi, 4.0f * thn.lo), thm), hist_scale);
-        ps = dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
+        ps = Pc.lag ? pn : dd_sub(mk(2.0f * pn.hi, 2.0f * pn.lo), pm);
       }
       return 0;
     });
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(256) k_mass_balance64(Level<double> L, Geom G,
         const double pm = psinm1[i];
         const double thm = th_nm1 ? th_nm1[i] : theta_only_d<ML>(pm, p1, p2, Q);
         hist = (4.0 * thn - thm) * hist_scale;
-        ps = 2.0 * pn - pm;
+        ps = Q.lag ? pn : 2.0 * pn - pm;
       }
       return 0;
     });

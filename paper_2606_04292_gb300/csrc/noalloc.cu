@@ -128,7 +128,7 @@ __device__ void na_prepare(const NaPlan& p) {
       hist = thn / p.dt;
     } else {
       const double pm = p.psinm1[i];
-      ps = 2.0 * pn - pm;
+      ps = P.lag ? pn : 2.0 * pn - pm;
       const double thm = with_law<MODEL>(P, mi, [&](auto law, const Phys<double>& Q) {
         return theta_only_d<decltype(law)::value>(pm, p1, p2, Q);
       });
@@ -404,6 +404,7 @@ long long build_plan(const richards_grid* grid, const richards_soil* soil, const
   P.h1 = sink->h1; P.h2 = sink->h2; P.h3 = sink->h3; P.h4 = sink->h4;
   P.newton_k = o.newton_iters;
   P.sink = sink->enabled;
+  P.lag = o.bdf2_lag;
   if (cx) P.mats = cx->mats;
   return used;
 }
@@ -457,7 +458,8 @@ extern "C" richards_status richards_step_small_noalloc(const richards_grid* grid
   if (!(dt > 0.0) || !std::isfinite(dt) || (scheme != 1 && scheme != 2) || o.nu1 < 0 || o.nu2 < 0 ||
       o.coarse_max_sweeps < 1 || o.max_cycles < 0 || o.coarsest_max_n < 1 || !(o.tol > 0.0) ||
       o.newton_iters < 0 || o.newton_iters > 200 || (o.kappa_mode != 0 && o.kappa_mode != 2) ||
-      !(o.xi >= 0.0) || !(o.kappa >= 0.0) || o.cycle_gamma < 1 || o.cycle_gamma > 3 || o.gamma_levels < 0)
+      !(o.xi >= 0.0) || !(o.kappa >= 0.0) || o.cycle_gamma < 1 || o.cycle_gamma > 3 || o.gamma_levels < 0 ||
+      (o.bdf2_lag != 0 && o.bdf2_lag != 1))
     return RICH_EINVAL;
   // the same checks as richards_set_soil / set_bc / set_sink (the fields are
   // device arrays here and are not read on the host)

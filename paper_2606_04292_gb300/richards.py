@@ -61,7 +61,7 @@ class richards_opts(C.Structure):
                 ("inner_cycles", C.c_int), ("inner_rtol", C.c_double), ("max_outer", C.c_int),
                 ("tail_cells", C.c_int), ("cycle_gamma", C.c_int), ("gamma_levels", C.c_int),
                 ("graphs", C.c_int), ("sweep_planes", C.c_int), ("predictor", C.c_int),
-                ("fmg_cycles", C.c_int), ("layout", C.c_int)]
+                ("fmg_cycles", C.c_int), ("layout", C.c_int), ("bdf2_lag", C.c_int)]
 
 
 class richards_step_info(C.Structure):
@@ -189,7 +189,7 @@ def make_opts(o):
                          o["ordering"], o["newton_iters"], o["precision"], o["inner_cycles"], o["inner_rtol"],
                          o["max_outer"], o["tail_cells"], o.get("cycle_gamma", 1), o.get("gamma_levels", 0),
                          o.get("graphs", 1), o.get("sweep_planes", 2), o.get("predictor", 0),
-                         o.get("fmg_cycles", 0), o.get("layout", 0))
+                         o.get("fmg_cycles", 0), o.get("layout", 0), o.get("bdf2_lag", 0))
 
 
 def current_stream():

@@ -412,6 +412,34 @@ def test_fp64_outer_prepare_matches_oracle(mk, scheme):
     assert rel(gs.get_level(0, 1), orc.g(0)) <= STAGE_RTOL
 
 
+LAG_PROBLEMS = [p for p in PROBLEMS if p[0] in ("3d_vg_hetero_sink", "2d_layers_3mat", "1d_celia_composite_40")]
+
+
+@pytest.mark.parametrize("mk", [p[1] for p in LAG_PROBLEMS], ids=[p[0] for p in LAG_PROBLEMS])
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_bdf2_lag_at_psi_n_matches_oracle(mk, precision):
+    """bdf2_lag = 1 (K and the xi term lagged at psi^n in a BDF2 step): the
+    finest level's Kc and g agree with the oracle's (to STAGE_RTOL in FP64 and
+    with the FP64 outer layer, to DD_EPS in float-float), and three FP64 steps
+    agree to STEP_RTOL."""
+    prob = W.with_opts(mk(), precision=precision, bdf2_lag=1, xi=1e-3)
+    rng = np.random.default_rng(9)
+    prob["psi_prev"] = prob["psi0"] + rng.uniform(-0.05, 0.05, len(prob["psi0"]))
+    gs, orc, p = pair(prob)
+    assert gs.prepare(p["dt"], 2) == 2
+    assert orc.prepare(p["dt"], 2) == 2
+    tol = DD_EPS if precision == 1 else STAGE_RTOL
+    assert rel(gs.get_level(0, 2), orc.Kc(0)) <= tol
+    assert rel(gs.get_level(0, 1), orc.g(0)) <= tol
+    if precision == 0:
+        gs, orc, p = pair(prob)
+        for k in range(3):
+            st, info = gs.step(p["dt"], 2)
+            sto, info_o = orc.step(p["dt"], 2)
+            assert st == sto == R.RICH_OK, (k, info, info_o)
+            assert rel(gs.state(), orc.state()) <= STEP_RTOL, k
+
+
 @pytest.mark.parametrize("mk", [p[1] for p in PROBLEMS if "sink" not in p[0]],
                          ids=[p[0] for p in PROBLEMS if "sink" not in p[0]])
 @pytest.mark.parametrize("predictor", [0, 1])

@@ -31,3 +31,14 @@ def test_runner_reports_failure_status(capsys):
     assert run.main(argv) == 1
     rows = [json.loads(l) for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
     assert len(rows) == 1 and rows[0]["status"] == "ENOCONV"
+
+
+def test_runner_batched_workloads(capsys):
+    """The columns and served workloads of the runner step every column and
+    request to RICH_OK."""
+    assert run.main(["--workload", "columns", "--n", "64", "--steps", "2"]) == 0
+    rows = [json.loads(l) for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(rows) == 2 and all(r["columns_ok"] and r["cell_updates"] > 0 for r in rows)
+    assert run.main(["--workload", "served", "--n", "3", "--steps", "2"]) == 0
+    rows = [json.loads(l) for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(rows) == 2 and all(s == "OK" for r in rows for s in r["status"])

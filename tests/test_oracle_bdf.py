@@ -53,3 +53,32 @@ def test_bdf1_run_is_first_order_forward_in_theta():
     for k in range(1, 5):
         assert o.step(p["dt"], 1)[0] == ORC_OK
         assert abs(o.soil(0, o.state()[0])[0] - (th0 - k * p["dt"] * S)) <= 1e-13 * k
+
+
+@pytest.mark.parametrize("lag", [0, 1])
+def test_bdf2_lagged_state_of_k_and_xi(lag):
+    """The BDF2 state at which K and the xi term are lagged: psi* = 2 psi^n -
+    psi^(n-1) (bdf2_lag 0) or psi^n (bdf2_lag 1, the lag of eq. fully-bdf1).
+    Every cell's Kc is the law's K at that state, and xi adds xi psi* to g
+    (against the same system with xi = 0)."""
+    p = W.random_problem(2, (9, 7), W.VANGENUCHTEN, 41, hetero=True, xi=2e-3, scheme=2)
+    rng = np.random.default_rng(4)
+    psi_n = np.asarray(p["psi0"], dtype=np.float64)
+    psi_m = psi_n + rng.uniform(-0.3, 0.3, psi_n.size)
+
+    def prepared(**kw):
+        o = Oracle(W.with_opts(p, bdf2_lag=lag, **kw))
+        o.set_state(psi_n, psi_m)
+        o.prepare(p["dt"], 2)
+        return o
+
+    o, o0 = prepared(), prepared(xi=0.0)
+    star = o.array(6)
+    assert np.array_equal(star, psi_n if lag else 2.0 * psi_n - psi_m)
+    assert not np.array_equal(star, 2.0 * psi_n - psi_m if lag else psi_n)
+    K = o.Kc(0)
+    for i in range(psi_n.size):
+        assert K[i] == o.soil(i, star[i])[2], i
+    assert np.array_equal(K, o0.Kc(0))
+    xi = p["opts"]["xi"]
+    assert np.max(np.abs((o.g(0) - o0.g(0)) - xi * star)) <= 1e-15 * np.max(np.abs(o.g(0)))
