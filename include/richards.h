@@ -523,8 +523,11 @@ long long richards_columns_ncell(const richards_columns *batch);
    doubles); psi_prev nullable (the next BDF2 step falls back to BDF1). */
 richards_status richards_columns_set_state(richards_columns *batch, const double *psi, const double *psi_prev);
 
-/* nsteps implicit steps of every column in one launch (scheme 1 = BDF1,
-   2 = BDF2).  Per-column outcomes are read with richards_columns_stats. */
+/* nsteps implicit steps of every column (scheme 1 = BDF1, 2 = BDF2): one
+   persistent launch per length class (columns of more than 512 cells,
+   257-512, at most 256; the two shorter classes on streams of the batch's
+   own, joined to its stream by events); returns once all are done.
+   Per-column outcomes are read with richards_columns_stats. */
 richards_status richards_columns_run(richards_columns *batch, double dt, int nsteps, int scheme);
 
 richards_status richards_columns_get_state(richards_columns *batch, double *psi, int on_device);
@@ -535,11 +538,14 @@ richards_status richards_columns_get_state(richards_columns *batch, double *psi,
 richards_status richards_columns_stats(richards_columns *batch, int *status, int *cycles, int *outer,
                                        double *resid, long long *updates);
 
-/* Threads per block (64, 128, 256 or 512). */
+/* Threads per block of the longest class (64, 128, 256 or 512); the next
+   classes take a half and a quarter of it (at least 32).  Results do not
+   depend on it. */
 richards_status richards_columns_set_threads(richards_columns *batch, int threads);
 
-/* Time one step of every column for each block size and keep the fastest;
-   the state is restored afterwards.  *threads_out (nullable) gets it. */
+/* For each block size (128, 256, 512): one untimed step, then two timed
+   steps of every column from the same state; keeps the fastest and restores
+   the state.  *threads_out (nullable) gets it. */
 richards_status richards_columns_autotune(richards_columns *batch, double dt, int scheme, int *threads_out);
 
 #ifdef __cplusplus

@@ -807,8 +807,9 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   return RICH_OK;
 }
 
-richards_status finish_step(richards_ctx* c, double r, richards_status st, int theta_fresh = -1) {
-  if (std::isnan(r)) return fail(c, RICH_ENAN, "NaN in the iterate; state kept at psi^n");
+// the history shift of an accepted step, as copies on the context's stream
+// (finish_step_launch), and what follows once they are done (finish_step_done)
+richards_status finish_step_launch(richards_ctx* c, int theta_fresh) {
   if (theta_fresh == 1) {            // th_cur = theta(psi^{n+1})
     double* t = c->th_nm1;
     c->th_nm1 = c->th_n;
@@ -821,11 +822,21 @@ richards_status finish_step(richards_ctx* c, double r, richards_status st, int t
   }
   std::swap(c->psi_n, c->psi_nm1);
   CK(cudaMemcpyAsync(c->psi_n, c->L[0].u, sizeof(double) * c->L[0].ncell, cudaMemcpyDeviceToDevice, c->s));
-  CK(cudaStreamSynchronize(c->s));
+  return RICH_OK;
+}
+
+richards_status finish_step_done(richards_ctx* c, richards_status st) {
   c->have_prev = true;
   c->t += c->dt;
   if (st != RICH_OK) return fail(c, st, "no convergence within the cycle limit");
   return RICH_OK;
+}
+
+richards_status finish_step(richards_ctx* c, double r, richards_status st, int theta_fresh = -1) {
+  if (std::isnan(r)) return fail(c, RICH_ENAN, "NaN in the iterate; state kept at psi^n");
+  TRY(finish_step_launch(c, theta_fresh));
+  CK(cudaStreamSynchronize(c->s));
+  return finish_step_done(c, st);
 }
 
 richards_status read_stats(richards_ctx* c, long long* tail_updates) {
@@ -835,15 +846,12 @@ richards_status read_stats(richards_ctx* c, long long* tail_updates) {
   return RICH_OK;
 }
 
-// Water balance and error bound of the iterate about to be accepted (before
-// the history shift); r = tau_eff ||g - N(psi)||_inf.  th_*: theta caches
-// (nullable: evaluated).  FP64 laws and sums, except in the float-float
-// mixed mode (precision 1).
-richards_status water_balance(richards_ctx* c, double r, richards_step_info* info, const double* th_new,
-                              const double* th_n, const double* th_nm1) {
-  if (!info) return RICH_OK;
-  info->mass_defect = NAN;
-  info->err_bound = NAN;
+// The water balance in two halves: its launches and copies to the host on
+// the context's stream (*nb_out: partial sums; 0 when r is not finite), and
+// the sums once the stream is done (water_balance_done).
+richards_status water_balance_launch(richards_ctx* c, double r, const double* th_new, const double* th_n,
+                                     const double* th_nm1, int* nb_out) {
+  *nb_out = 0;
   if (!std::isfinite(r)) return RICH_OK;
   unsigned* dmin = (unsigned*)(c->mass_part + MASS_PARTS);
   CK(cudaMemsetAsync(dmin, 0xff, sizeof(unsigned), c->s));
@@ -858,7 +866,14 @@ richards_status water_balance(richards_ctx* c, double r, richards_step_info* inf
   if (nb > MASS_PARTS) return fail(c, RICH_ECUDA, "water balance: too many blocks");
   CK(cudaMemcpyAsync(c->hmass, c->mass_part, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->s));
   CK(cudaMemcpyAsync(c->hmass + MASS_PARTS, dmin, sizeof(unsigned), cudaMemcpyDeviceToHost, c->s));
-  CK(cudaStreamSynchronize(c->s));
+  *nb_out = nb;
+  return RICH_OK;
+}
+
+void water_balance_done(richards_ctx* c, double r, int nb, richards_step_info* info) {
+  info->mass_defect = NAN;
+  info->err_bound = NAN;
+  if (nb <= 0) return;
   long double sum = 0.0L;
   for (int b = 0; b < nb; ++b) sum += (long double)c->hmass[b];
   info->mass_defect = (double)(sum / (long double)c->a);
@@ -868,6 +883,19 @@ richards_status water_balance(richards_ctx* c, double r, richards_step_info* inf
   std::memcpy(&dm, &bits, sizeof(float));
   const double nrm = r * c->a;      // ||N(psi) - g||_inf
   info->err_bound = (bits < 0x7f800000u && dm > 0.0f) ? nrm / (double)dm : INFINITY;
+}
+
+// Water balance and error bound of the iterate about to be accepted (before
+// the history shift); r = tau_eff ||g - N(psi)||_inf.  th_*: theta caches
+// (nullable: evaluated).  FP64 laws and sums, except in the float-float
+// mixed mode (precision 1).
+richards_status water_balance(richards_ctx* c, double r, richards_step_info* info, const double* th_new,
+                              const double* th_n, const double* th_nm1) {
+  if (!info) return RICH_OK;
+  int nb = 0;
+  TRY(water_balance_launch(c, r, th_new, th_n, th_nm1, &nb));
+  if (nb > 0) CK(cudaStreamSynchronize(c->s));
+  water_balance_done(c, r, nb, info);
   return RICH_OK;
 }
 
@@ -1117,13 +1145,21 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
 // context takes one implicit step; their outer defects, decisions and inner
 // stop tests are taken together (one synchronisation for all), and their
 // FP32 inner cycles run together, each stage of a cycle one launch over the
-// descriptors of all contexts that are at that stage (batch.cu).
+// descriptors of all contexts that are at that stage (batch.cu).  The work
+// of one context alone (preparation, outer defects, coarse copies of psi0,
+// updates, water balance) stays on the context's own stream, so that the
+// contexts' small launches overlap; events order it against the batched
+// stages on the batcher's stream.
 // ==========================================================================
 struct richards_batcher {
   cudaStream_t s = nullptr;
   int cap = 0;                               // contexts the tables hold
   rich::BJob32* dtable = nullptr;            // cap x MAXLEV descriptors (device)
   rich::BJob32* htable = nullptr;            // staging copy (pinned)
+  unsigned long long* dnorm = nullptr;       // inner-norm slot of each context (float bits; device)
+  unsigned long long* hnorm = nullptr;       // pinned copy
+  cudaEvent_t fork = nullptr;                // batcher stream -> context streams
+  std::vector<cudaEvent_t> join;             // context stream (per slot) -> batcher stream
   std::string err;
 };
 
@@ -1131,7 +1167,6 @@ namespace {
 
 struct BatchCtx {
   richards_ctx* c = nullptr;
-  cudaStream_t own = nullptr;                // the context's stream, restored at the end
   int slot = 0;
   bool ok = true;                            // prepared; takes part
   bool outer_active = false, inner_active = false, predicted = false;
@@ -1249,10 +1284,29 @@ richards_status batch_defects(richards_batcher* b, std::vector<BatchCtx>& B, con
     const bool cached = B[k].outer == 0 && !B[k].predicted;
     richards_status st = outer_defect_launch(c, cached, fp64);
     if (st != RICH_OK) return bfail(b, st, c->err);
-    BCK(cudaMemcpyAsync(c->hscratch, c->scratch, sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->s));
+    BCK(cudaMemcpyAsync(c->hscratch, c->scratch, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
   }
-  BCK(cudaStreamSynchronize(b->s));
+  for (int k : who) BCK(cudaStreamSynchronize(B[k].c->s));
   for (int k : who) B[k].r = host_norm(B[k].c, 0, !fp64) / B[k].c->a;
+  return RICH_OK;
+}
+
+// the listed contexts' streams wait for the batcher's stream
+richards_status bfork(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who) {
+  BCK(cudaEventRecord(b->fork, b->s));
+  for (int k : who)
+    if (B[k].c->s != b->s) BCK(cudaStreamWaitEvent(B[k].c->s, b->fork, 0));
+  return RICH_OK;
+}
+
+// the batcher's stream waits for the listed contexts' streams
+richards_status bjoin(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who) {
+  for (int k : who) {
+    cudaStream_t cs = B[k].c->s;
+    if (cs == b->s) continue;
+    BCK(cudaEventRecord(b->join[B[k].slot], cs));
+    BCK(cudaStreamWaitEvent(b->s, b->join[B[k].slot], 0));
+  }
   return RICH_OK;
 }
 
@@ -1276,7 +1330,7 @@ richards_status batch_step_impl(richards_batcher* b, std::vector<BatchCtx>& B, c
       J.level = l;
       J.nlev = c->nlev;
       J.model = c->soil.model;
-      J.norm = c->scratch + 1;
+      J.norm = b->dnorm + B[k].slot;
       J.stats = c->scratch + 16;
     }
   }
@@ -1322,6 +1376,7 @@ richards_status batch_step_impl(richards_batcher* b, std::vector<BatchCtx>& B, c
         if (sd != RICH_OK) return bfail(b, sd, c->err);
       }
     }
+    TRY_B(bjoin(b, B, act));
     std::vector<int> in = act;
     const int cycles = B[act[0]].c->opts.inner_cycles;
     for (int q = 0; q < cycles && !in.empty(); ++q) {
@@ -1332,23 +1387,27 @@ richards_status batch_step_impl(richards_batcher* b, std::vector<BatchCtx>& B, c
       for (int k : in)
         if (B[k].c->opts.inner_rtol > 0.0) test.push_back(k);
       if (test.empty()) continue;
-      for (int k : test) BCK(cudaMemsetAsync(B[k].c->scratch + 1, 0, sizeof(unsigned long long), b->s));
+      const size_t nb = sizeof(unsigned long long) * B.size();
+      BCK(cudaMemsetAsync(b->dnorm, 0, nb, b->s));
       batch_stage(b, B, test, rich::BOP_RESID, 0, 0, true);
-      for (int k : test)
-        BCK(cudaMemcpyAsync(B[k].c->hscratch + 1, B[k].c->scratch + 1, sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, b->s));
+      BCK(cudaMemcpyAsync(b->hnorm, b->dnorm, nb, cudaMemcpyDeviceToHost, b->s));
       BCK(cudaStreamSynchronize(b->s));
       std::vector<int> keep;
       for (int k : in) {
-        const bool tested = B[k].c->opts.inner_rtol > 0.0;
-        if (tested && host_norm(B[k].c, 1, true) <= B[k].rtol_in * B[k].rin0) continue;
+        if (B[k].c->opts.inner_rtol > 0.0) {
+          const unsigned u = (unsigned)b->hnorm[B[k].slot];
+          float f;
+          std::memcpy(&f, &u, 4);
+          if ((double)f <= B[k].rtol_in * B[k].rin0) continue;
+        }
         keep.push_back(k);
       }
       in.swap(keep);
     }
+    TRY_B(bfork(b, B, act));
     for (int k : act) {
       richards_ctx* c = B[k].c;
-      rich::apply_delta(c->L[0].u, c->L[0].uf, c->L[0].ncell, b->s);
+      rich::apply_delta(c->L[0].u, c->L[0].uf, c->L[0].ncell, c->s);
       ++B[k].outer;
     }
     const cudaError_t e = cudaGetLastError();
@@ -2107,8 +2166,16 @@ richards_status richards_batcher_create(void* stream, int max_contexts, richards
   b->s = (cudaStream_t)stream;
   b->cap = max_contexts;
   const size_t bytes = sizeof(rich::BJob32) * (size_t)max_contexts * MAXLEV;
-  if (cudaMalloc((void**)&b->dtable, bytes) != cudaSuccess ||
-      cudaMallocHost((void**)&b->htable, bytes) != cudaSuccess) {
+  const size_t nbytes = sizeof(unsigned long long) * (size_t)max_contexts;
+  b->join.assign(max_contexts, nullptr);
+  bool ok = cudaMalloc((void**)&b->dtable, bytes) == cudaSuccess &&
+            cudaMallocHost((void**)&b->htable, bytes) == cudaSuccess &&
+            cudaMalloc((void**)&b->dnorm, nbytes) == cudaSuccess &&
+            cudaMallocHost((void**)&b->hnorm, nbytes) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < max_contexts; ++k)
+    ok = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
     richards_batcher_destroy(b);
     return RICH_ENOMEM;
@@ -2122,6 +2189,11 @@ void richards_batcher_destroy(richards_batcher* b) {
   if (b->s) cudaStreamSynchronize(b->s); else cudaDeviceSynchronize();
   if (b->dtable) cudaFree(b->dtable);
   if (b->htable) cudaFreeHost(b->htable);
+  if (b->dnorm) cudaFree(b->dnorm);
+  if (b->hnorm) cudaFreeHost(b->hnorm);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
   delete b;
 }
 
@@ -2153,45 +2225,65 @@ richards_status richards_batcher_step(richards_batcher* b, richards_ctx* const* 
     richards_ctx* c = ctxs[k];
     B[k].c = c;
     B[k].slot = k;
-    B[k].own = c->s;
     c->busy.store(1);
-    cudaStreamSynchronize(c->s);               // earlier work of the context is done
-    c->s = b->s;
   }
+  // preparation on the contexts' own streams (their earlier work is ordered
+  // before it there)
   richards_status st = RICH_OK;
   for (int k = 0; k < n; ++k) {
     richards_ctx* c = B[k].c;
     c->updates_host = 0;
-    cudaMemsetAsync(c->scratch + 16, 0, sizeof(unsigned long long), b->s);
+    cudaMemsetAsync(c->scratch + 16, 0, sizeof(unsigned long long), c->s);
     B[k].st = do_prepare(c, dt[k], scheme[k]);
     B[k].ok = B[k].st == RICH_OK;
     B[k].predicted = c->opts.predictor == 1 && c->scheme_used == 2;
   }
   st = batch_step_impl(b, B, dt, scheme);
+  // water balance and history shift: launched for every context first, then
+  // one wait per stream
+  std::vector<int> all(n);
+  for (int k = 0; k < n; ++k) all[k] = k;
+  if (st == RICH_OK) st = bfork(b, B, all);
+  std::vector<richards_status> fin(n, RICH_OK);
+  std::vector<int> nbal(n, 0);
+  std::vector<richards_step_info> inf(n, richards_step_info{});
+  for (int k = 0; k < n && st == RICH_OK; ++k) {
+    BatchCtx& X = B[k];
+    if (!X.ok) continue;
+    richards_ctx* c = X.c;
+    const bool moved = X.outer > 0 || X.predicted;
+    richards_status sk = cudaMemcpyAsync(c->hscratch + 16, c->scratch + 16, sizeof(unsigned long long),
+                                         cudaMemcpyDeviceToHost, c->s) == cudaSuccess ? RICH_OK
+                                                                                      : fail(c, RICH_ECUDA, "stats copy");
+    if (sk == RICH_OK)
+      sk = water_balance_launch(c, X.r, moved ? c->th_cur : c->th_n, c->th_n, c->th_nm1_valid ? c->th_nm1 : nullptr,
+                                &nbal[k]);
+    if (sk == RICH_OK && !std::isnan(X.r)) sk = finish_step_launch(c, moved ? 1 : 0);
+    fin[k] = sk;
+  }
   for (int k = 0; k < n; ++k) {
     BatchCtx& X = B[k];
     richards_ctx* c = X.c;
+    const bool synced = cudaStreamSynchronize(c->s) == cudaSuccess;
     richards_status sk = st != RICH_OK ? st : X.st;
     if (st == RICH_OK && X.ok) {
-      long long tu = 0;
-      richards_step_info inf{};
-      sk = read_stats(c, &tu);
-      inf.cycles = X.inner;
-      inf.outer_iters = X.outer;
-      inf.scheme_used = c->scheme_used;
-      inf.resid0 = X.r0;
-      inf.resid = X.r;
-      inf.cell_updates = c->updates_host + tu;
-      const bool moved = X.outer > 0 || X.predicted;
+      sk = synced ? fin[k] : fail(c, RICH_ECUDA, "stream synchronisation");
+      richards_step_info& I = inf[k];
+      I.cycles = X.inner;
+      I.outer_iters = X.outer;
+      I.scheme_used = c->scheme_used;
+      I.resid0 = X.r0;
+      I.resid = X.r;
+      I.cell_updates = c->updates_host + (long long)c->hscratch[16];
+      water_balance_done(c, X.r, sk == RICH_OK ? nbal[k] : 0, &I);
       if (sk == RICH_OK)
-        sk = water_balance(c, X.r, &inf, moved ? c->th_cur : c->th_n, c->th_n, c->th_nm1_valid ? c->th_nm1 : nullptr);
-      if (sk == RICH_OK) sk = finish_step(c, X.r, X.st, moved ? 1 : 0);
-      if (info) info[k] = inf;
+        sk = std::isnan(X.r) ? fail(c, RICH_ENAN, "NaN in the iterate; state kept at psi^n")
+                             : finish_step_done(c, X.st);
+      if (info) info[k] = I;
     } else if (info) {
       info[k] = richards_step_info{};
     }
     if (status) status[k] = sk;
-    c->s = X.own;
     c->busy.store(0);
   }
   return st;

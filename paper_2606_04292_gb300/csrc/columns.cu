@@ -37,6 +37,7 @@ struct ColArgs {
   const ColDesc* cols;
   const int* order;                // processing order (longest first)
   int ncol;
+  int begin, end;                  // this launch's columns: order[begin, end)
   int* queue;                      // work counter, zero before the launch
   int* thn_valid;                  // per column: thn holds theta(psi^n)
   double *psin, *psinm1, *u, *g, *Kc, *thn, *thcur, *smax;
@@ -413,8 +414,8 @@ __global__ void __launch_bounds__(COL_THREADS_MAX, 1) k_columns(ColArgs A) {
   __shared__ int s_col, s_nl;
   for (;;) {
     if (threadIdx.x == 0) {
-      const int k = atomicAdd(A.queue, 1);
-      s_col = k < A.ncol ? A.order[k] : -1;
+      const int k = A.begin + atomicAdd(A.queue, 1);
+      s_col = k < A.end ? A.order[k] : -1;
     }
     __syncthreads();
     const int c = s_col;
@@ -443,9 +444,22 @@ size_t column_smem(int n, int coarsest_max_n) {
 using rich::ColArgs;
 using rich::ColDesc;
 
+// Columns go to three length classes (more than 512 cells, 257-512, at most
+// 256), each a persistent launch whose blocks hold the shared memory of the
+// class's longest column and take threads, threads/2, threads/4 (at least
+// 32): short columns then fit several blocks per SM.  The classes run
+// concurrently (the two shorter ones on streams of their own, ordered by
+// events); a column's arithmetic does not depend on its block's size (its
+// only reductions are maxima), so the results are those of any one launch.
+constexpr int COL_CLASSES = 3;
+inline int column_class(int n) { return n > 512 ? 0 : (n > 256 ? 1 : 2); }
+
 struct richards_columns {
   cudaStream_t s = nullptr;
   int ncol = 0, max_n = 0, model = 0, threads = 256;
+  int cls_begin[COL_CLASSES] = {0, 0, 0}, cls_end[COL_CLASSES] = {0, 0, 0}, cls_maxn[COL_CLASSES] = {0, 0, 0};
+  cudaStream_t aux[COL_CLASSES - 1] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[COL_CLASSES - 1] = {nullptr, nullptr};
   long long ncell = 0;
   richards_opts opts{};
   richards_sink sink{};
@@ -492,20 +506,36 @@ richards_status launch_columns(richards_columns* c, double dt, int nsteps, int s
   A.gamma = o.cycle_gamma; A.gamma_levels = o.gamma_levels; A.coarsest_max_n = o.coarsest_max_n;
   A.scheme = scheme; A.nsteps = nsteps; A.model = c->model; A.lag = o.bdf2_lag;
   A.fp64 = o.precision == 2 ? 1 : 0;
-  const size_t smem = column_smem(c->max_n, o.coarsest_max_n);
   auto kern = c->model == HAVERKAMP ? k_columns<HAVERKAMP> : (c->model == GARDNER ? k_columns<GARDNER>
                                                                                   : k_columns<VANGENUCHTEN>);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)column_smem(c->max_n, o.coarsest_max_n)) != cudaSuccess)
     return RICH_EINVAL;
-  int per_sm = 0, dev = 0, nsm = 0;
+  int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1)
-    return RICH_EINVAL;
-  const int grid = std::min(nsm * per_sm, c->ncol);
-  if (cudaMemsetAsync(c->queue, 0, sizeof(int), c->s) != cudaSuccess) return RICH_ECUDA;
-  kern<<<grid, threads, smem, c->s>>>(A);
-  if (cudaGetLastError() != cudaSuccess) return RICH_ECUDA;
+  if (cudaMemsetAsync(c->queue, 0, sizeof(int) * COL_CLASSES, c->s) != cudaSuccess) return RICH_ECUDA;
+  if (cudaEventRecord(c->ev_fork, c->s) != cudaSuccess) return RICH_ECUDA;
+  for (int k = 0; k < COL_CLASSES; ++k) {
+    const int count = c->cls_end[k] - c->cls_begin[k];
+    if (count <= 0) continue;
+    cudaStream_t s = k == 0 ? c->s : c->aux[k - 1];
+    if (k > 0 && cudaStreamWaitEvent(s, c->ev_fork, 0) != cudaSuccess) return RICH_ECUDA;
+    const int t = std::max(32, threads >> k);
+    const size_t smem = column_smem(c->cls_maxn[k], o.coarsest_max_n);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t, smem) != cudaSuccess || per_sm < 1)
+      return RICH_EINVAL;
+    ColArgs Ak = A;
+    Ak.begin = c->cls_begin[k];
+    Ak.end = c->cls_end[k];
+    Ak.queue = c->queue + k;
+    kern<<<std::min(nsm * per_sm, count), t, smem, s>>>(Ak);
+    if (cudaGetLastError() != cudaSuccess) return RICH_ECUDA;
+    if (k > 0 && (cudaEventRecord(c->ev_join[k - 1], s) != cudaSuccess ||
+                  cudaStreamWaitEvent(c->s, c->ev_join[k - 1], 0) != cudaSuccess))
+      return RICH_ECUDA;
+  }
   if (cudaStreamSynchronize(c->s) != cudaSuccess) return RICH_ECUDA;
   return RICH_OK;
 }
@@ -564,15 +594,29 @@ richards_status richards_columns_create(int ncol, const richards_column* cols, c
   std::vector<int> order(ncol);
   for (int k = 0; k < ncol; ++k) order[k] = k;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hc[a].n > hc[b].n; });
+  for (int q = 0; q < ncol; ++q) {               // (longest first: each class is one range of order)
+    const int k = column_class(hc[order[q]].n);
+    if (c->cls_end[k] == c->cls_begin[k]) {
+      c->cls_begin[k] = q;
+      c->cls_maxn[k] = hc[order[q]].n;
+    }
+    c->cls_end[k] = q + 1;
+  }
   const long long N = off;
-  bool ok = col_alloc(c, &c->cols, ncol) && col_alloc(c, &c->order, ncol) && col_alloc(c, &c->queue, 1) &&
+  bool ok = col_alloc(c, &c->cols, ncol) && col_alloc(c, &c->order, ncol) &&
+            col_alloc(c, &c->queue, COL_CLASSES) &&
             col_alloc(c, &c->thn_valid, ncol) && col_alloc(c, &c->have_prev, ncol) && col_alloc(c, &c->psin, N) &&
             col_alloc(c, &c->psinm1, N) && col_alloc(c, &c->u, N) && col_alloc(c, &c->g, N) &&
             col_alloc(c, &c->Kc, N) && col_alloc(c, &c->thn, N) && col_alloc(c, &c->thcur, N) &&
             col_alloc(c, &c->smax, N) && col_alloc(c, &c->st_status, ncol) && col_alloc(c, &c->st_cycles, ncol) &&
             col_alloc(c, &c->st_outer, ncol) && col_alloc(c, &c->st_resid, ncol) &&
             col_alloc(c, &c->st_updates, ncol);
+  for (int k = 0; ok && k < COL_CLASSES - 1; ++k)
+    ok = cudaStreamCreateWithFlags(&c->aux[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
+    cudaGetLastError();
     richards_columns_destroy(c);
     return RICH_ENOMEM;
   }
@@ -613,6 +657,11 @@ richards_status richards_columns_create(int ncol, const richards_column* cols, c
 void richards_columns_destroy(richards_columns* c) {
   if (!c) return;
   if (c->s) cudaStreamSynchronize(c->s); else cudaDeviceSynchronize();
+  for (int k = 0; k < COL_CLASSES - 1; ++k) {
+    if (c->aux[k]) { cudaStreamSynchronize(c->aux[k]); cudaStreamDestroy(c->aux[k]); }
+    if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -679,8 +728,8 @@ richards_status richards_columns_set_threads(richards_columns* c, int threads) {
 
 richards_status richards_columns_autotune(richards_columns* c, double dt, int scheme, int* threads_out) {
   if (!c || !c->have_state) return RICH_EINVAL;
-  // each candidate runs one step from the current state on the same data;
-  // the state is restored afterwards
+  // each candidate runs one untimed step and then two timed steps, each run
+  // from the current state on the same data; the state is restored afterwards
   const long long N = c->ncell;
   std::vector<double> psin(N), psinm1(N);
   std::vector<int> hp(c->ncol), tv(c->ncol);
@@ -695,14 +744,18 @@ richards_status richards_columns_autotune(richards_columns* c, double dt, int sc
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  auto restore = [&]() {
+    return cudaMemcpy(c->psin, psin.data(), sizeof(double) * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(c->psinm1, psinm1.data(), sizeof(double) * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(c->have_prev, hp.data(), sizeof(int) * c->ncol, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(c->thn_valid, tv.data(), sizeof(int) * c->ncol, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
   for (int t : cand) {
-    if (cudaMemcpy(c->psin, psin.data(), sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c->psinm1, psinm1.data(), sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c->have_prev, hp.data(), sizeof(int) * c->ncol, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c->thn_valid, tv.data(), sizeof(int) * c->ncol, cudaMemcpyHostToDevice) != cudaSuccess)
-      return RICH_ECUDA;
+    if (!restore()) return RICH_ECUDA;
+    if (launch_columns(c, dt, 1, scheme, t) != RICH_OK) continue;
+    if (!restore()) return RICH_ECUDA;
     cudaEventRecord(e0, c->s);
-    const richards_status st = launch_columns(c, dt, 1, scheme, t);
+    const richards_status st = launch_columns(c, dt, 2, scheme, t);
     cudaEventRecord(e1, c->s);
     cudaEventSynchronize(e1);
     if (st != RICH_OK) continue;
@@ -712,11 +765,7 @@ richards_status richards_columns_autotune(richards_columns* c, double dt, int sc
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (cudaMemcpy(c->psin, psin.data(), sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(c->psinm1, psinm1.data(), sizeof(double) * N, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(c->have_prev, hp.data(), sizeof(int) * c->ncol, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(c->thn_valid, tv.data(), sizeof(int) * c->ncol, cudaMemcpyHostToDevice) != cudaSuccess)
-    return RICH_ECUDA;
+  if (!restore()) return RICH_ECUDA;
   c->threads = best_t;
   if (threads_out) *threads_out = best_t;
   return RICH_OK;

@@ -109,11 +109,13 @@ def run_columns(args):
 
 
 def run_served(args):
+    import torch
     reqs = W.serving_trace(sizes2d=(129, 257), sizes3d=(65,), max_requests=args.n or 8)
+    streams = [torch.cuda.Stream() for _ in reqs]        # each request's own work overlaps
     solvers = []
-    for p in reqs:
+    for p, st in zip(reqs, streams):
         p["opts"] = _batched_opts(args, p["opts"])
-        solvers.append(R.Solver(p, stream=0))
+        solvers.append(R.Solver(p, stream=st.cuda_stream))
     ok = True
     b = R.Batcher(max_contexts=max(len(solvers), 1), stream=0)
     try:

@@ -143,6 +143,10 @@ class Server:
         used = 0
         stream = self.torch.cuda.Stream()
         batcher = R.Batcher(max_contexts=self.max_active, stream=stream.cuda_stream)
+        # each admitted request keeps a stream of its own for the work that is
+        # its alone (preparation, outer defects, water balance), which then
+        # overlaps between requests; the batched cycles run on `stream`
+        free_streams = [self.torch.cuda.Stream() for _ in range(self.max_active)]
         t0 = time.perf_counter()
         try:
             while pending or waiting or active:
@@ -159,11 +163,13 @@ class Server:
                     if used + need > self.budget:
                         break
                     waiting.popleft()
-                    solver = R.Solver(prob, stream=stream.cuda_stream, opts=self.opts)
+                    own = free_streams.pop()
+                    solver = R.Solver(prob, stream=own.cuda_stream, opts=self.opts)
                     used += need
                     arrival = prob.get("arrival", 0.0) if realtime else 0.0
-                    active[rid] = dict(solver=solver, bytes=need, arrival=arrival, start=time.perf_counter() - t0,
-                                       prob=prob, done=0, acc=dict(cycles=0, outer_iters=0, cell_updates=0))
+                    active[rid] = dict(solver=solver, stream=own, bytes=need, arrival=arrival,
+                                       start=time.perf_counter() - t0, prob=prob, done=0,
+                                       acc=dict(cycles=0, outer_iters=0, cell_updates=0))
                 if not active:
                     time.sleep(self.poll_s)
                     continue
@@ -186,6 +192,7 @@ class Server:
                         if self.keep_states:
                             res["state"] = a["solver"].state()
                         a["solver"].close()
+                        free_streams.append(a["stream"])
                         used -= a["bytes"]
                         results[rid] = res
                         del active[rid]
