@@ -336,38 +336,58 @@ richards_status richards_set_launch(richards_ctx *ctx, int level, int planes, in
 richards_status richards_set_coop(richards_ctx *ctx, long long max_cells);
 
 /* ---------------------------------------------------------------------
- * Lockstep batch of resident contexts (continuous batching of served
- * requests, at the granularity of a time step).  richards_batcher_step takes
- * one implicit step of each listed context: the outer defects, the FP64
- * decisions and the inner stop tests of all contexts are taken together
- * (one synchronisation for all per stage), and the FP32 inner V-cycles of
- * all of them run together -- every stage of a cycle (half-sweep, defect,
- * restriction, FAS right side, interpolation, coarse tail) is one launch
- * over a device table of (context, level) descriptors (Section 3.2's cycle
- * for each context; a context's arithmetic is the same as in richards_step,
- * and no reduction mixes contexts).  The caller may change the list from one
- * step to the next (admit new requests, retire finished ones).
+ * Batched steps of resident contexts (continuous batching of served
+ * requests).  A batcher advances many contexts in ticks: at every tick each
+ * context does the next part of its own current step -- its preparation and
+ * first outer defect, an outer defect and the decision after it, one FP32
+ * inner V-cycle, or the step's water balance and history shift -- whatever
+ * the other contexts are doing.  The inner V-cycles of all contexts that are
+ * in an inner solve run together: every stage of a cycle (half-sweep,
+ * defect, restriction, FAS right side, interpolation, coarse tail) is one
+ * launch over a device table of (context, level) descriptors on the
+ * batcher's stream (Section 3.2's cycle for each context); the work of one
+ * context alone runs on the context's own stream and overlaps them.  A
+ * context's arithmetic, decisions and results are those of richards_step
+ * (no reduction mixes contexts).  A context can be mid-step when a call
+ * returns; the next call continues it (a call that prepares a step of the
+ * context or changes its problem drops that progress: the step restarts
+ * from psi^n).  The caller may change the list between calls (admit new
+ * requests, retire finished ones).
  * --------------------------------------------------------------------- */
 typedef struct richards_batcher richards_batcher;   /* opaque; owns its descriptor tables */
 
-/* stream: the cudaStream_t every batched step runs on (NULL = default
-   stream); max_contexts: the most contexts one step takes (1..4096).
+/* stream: the cudaStream_t the batched cycles run on (NULL = default
+   stream); max_contexts: the most contexts one call takes (1..4096).
    Errors: EINVAL, ENOMEM. */
 richards_status richards_batcher_create(void *stream, int max_contexts, richards_batcher **out);
 void richards_batcher_destroy(richards_batcher *b);
 const char *richards_batcher_last_error(const richards_batcher *b);
 
-/* One step of each of the n contexts (dt[k], scheme[k]: as richards_step).
-   Every context must be in a mixed mode (precision 1 or 2) with red-black
-   sweeps and no FMG start, and all must share nu1, nu2, cycle_gamma,
-   gamma_levels, coarse_max_sweeps, coarse_rtol and inner_cycles; the calls
-   are ordered on the batcher's stream (each context's own stream is
-   synchronised first).  status[k] / info[k] (nullable) receive each
-   context's outcome as richards_step would return it.  Returns EINVAL /
-   EBUSY before doing anything when an argument or a context does not
-   qualify, ECUDA on a CUDA error, else RICH_OK. */
+/* One step of each of the n contexts (dt[k], scheme[k]: as richards_step);
+   returns when all are done.  Every context must be in a mixed mode
+   (precision 1 or 2) with red-black sweeps and no FMG start, and all must
+   share nu1, nu2, cycle_gamma, gamma_levels, coarse_max_sweeps, coarse_rtol
+   and inner_cycles.  Work is ordered after what the contexts' streams hold.
+   status[k] / info[k] (nullable) receive each context's outcome as
+   richards_step would return it.  Returns EINVAL / EBUSY before doing
+   anything when an argument or a context does not qualify, ECUDA on a CUDA
+   error (no context is then left mid-step), else RICH_OK. */
 richards_status richards_batcher_step(richards_batcher *b, richards_ctx *const *ctxs, int n, const double *dt,
                                       const int *scheme, richards_status *status, richards_step_info *info);
+
+/* Continuous batching: steps_left[k] (host, in/out) more steps of context
+   k, each context on its own schedule; returns after max_ticks ticks (> 0;
+   0 = no limit) or as soon as a context that wanted steps has done all of
+   them (a failed step ends a context's run: its steps_left becomes 0), or
+   when no context wants more.  Per context (host arrays, nullable):
+   steps_done[k] = steps completed in this call; status[k] = the last one's
+   status (RICH_OK if none); info[k] = their statistics: cycles,
+   outer_iters and cell_updates summed over them, resid0 from the first,
+   the rest from the last.  Same requirements and errors as
+   richards_batcher_step; EINVAL for a negative steps_left. */
+richards_status richards_batcher_advance(richards_batcher *b, richards_ctx *const *ctxs, int n, const double *dt,
+                                         const int *scheme, int *steps_left, int max_ticks, int *steps_done,
+                                         richards_status *status, richards_step_info *info);
 
 /* Device memory a context for this grid and these options allocates
    (upper estimate, bytes; no device is touched): soil_fields != 0 when the

@@ -56,6 +56,23 @@ struct HLevel {
   float *pwf[3] = {}, *rwf[3] = {};
 };
 
+// Progress of a context through its current step under a batcher, kept in
+// the context between calls (a call can return with a context mid-step):
+// which part of the step comes next, and the step's running values (those
+// of step_mixed).
+enum { BP_IDLE = 0, BP_DEFECT, BP_INNER, BP_FINISH };
+struct BatchProgress {
+  int phase = BP_IDLE;
+  bool use64 = false;                  // FP64 outer layer: FP64 defects from here on
+  bool predicted = false;
+  double r = 0.0, r0 = 0.0, rin0 = 0.0, rtol_in = 0.0, r_ff = INFINITY;
+  int outer = 0, inner = 0;            // outer iterations and inner cycles of the step
+  int k = 0;                           // cycles of the current inner solve
+  richards_status st = RICH_OK;        // RICH_ENOCONV once the outer limit is reached
+  int nbal = 0;                        // water-balance partial sums in flight (finish)
+  richards_status fin = RICH_OK;       // status of the finishing launches
+};
+
 }  // namespace
 
 struct richards_ctx {
@@ -132,6 +149,9 @@ struct richards_ctx {
   // FP32 inner cycles: levels from coop_start down to the single-block tail
   // run as one cooperative launch (MAXLEV: none); its grid size
   int coop_start = MAXLEV, coop_blocks = 0;
+  // batcher progress (richards_batcher_step / _advance); reset by any call
+  // that prepares a step or changes the problem
+  BatchProgress bp;
 };
 
 namespace {
@@ -758,6 +778,7 @@ richards_status restrict_coefficients(richards_ctx* c) {
 }
 
 richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
+  c->bp = BatchProgress{};                 // a batched step in progress restarts
   if (!c->soil_set) return fail(c, RICH_EINVAL, "soil not set");
   if (!c->bc_set) return fail(c, RICH_EINVAL, "boundary conditions not set");
   if (!c->have_state) return fail(c, RICH_EINVAL, "state not set");
@@ -1167,13 +1188,7 @@ namespace {
 
 struct BatchCtx {
   richards_ctx* c = nullptr;
-  int slot = 0;
-  bool ok = true;                            // prepared; takes part
-  bool outer_active = false, inner_active = false, predicted = false;
-  bool use64 = false;                        // FP64 outer: FP64 defects from here on (as step_mixed)
-  double r = 0.0, r0 = 0.0, rin0 = 0.0, rtol_in = 0.0, r_ff = INFINITY;
-  int outer = 0, inner = 0;
-  richards_status st = RICH_OK;
+  int slot = 0;                              // index in this call's table and norm slots
 };
 
 int batch_nk(const richards_ctx* c) {
@@ -1276,21 +1291,6 @@ richards_status bfail(richards_batcher* b, richards_status st, const std::string
     if (e_ != cudaSuccess) return bfail(b, RICH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// launch the outer defects of the listed contexts, one synchronisation,
-// their norms (fp64: the FP64 defect) into B[k].r
-richards_status batch_defects(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who, bool fp64) {
-  for (int k : who) {
-    richards_ctx* c = B[k].c;
-    const bool cached = B[k].outer == 0 && !B[k].predicted;
-    richards_status st = outer_defect_launch(c, cached, fp64);
-    if (st != RICH_OK) return bfail(b, st, c->err);
-    BCK(cudaMemcpyAsync(c->hscratch, c->scratch, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
-  }
-  for (int k : who) BCK(cudaStreamSynchronize(B[k].c->s));
-  for (int k : who) B[k].r = host_norm(B[k].c, 0, !fp64) / B[k].c->a;
-  return RICH_OK;
-}
-
 // the listed contexts' streams wait for the batcher's stream
 richards_status bfork(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who) {
   BCK(cudaEventRecord(b->fork, b->s));
@@ -1310,108 +1310,246 @@ richards_status bjoin(richards_batcher* b, std::vector<BatchCtx>& B, const std::
   return RICH_OK;
 }
 
-richards_status batch_step_impl(richards_batcher* b, std::vector<BatchCtx>& B, const double* dts,
-                                const int* schemes) {
+// descriptors of every level of context k (its physics record carries the
+// step's a = 1/dt or 3/(2 dt): rebuilt whenever the context prepares a step)
+void batch_table_slot(richards_batcher* b, std::vector<BatchCtx>& B, int k) {
+  richards_ctx* c = B[k].c;
+  for (int l = 0; l < c->nlev; ++l) {
+    rich::BJob32& J = b->htable[B[k].slot * MAXLEV + l];
+    J = rich::BJob32{};
+    J.F = view32(c, l);
+    if (l + 1 < c->nlev) {
+      J.C = view32(c, l + 1);
+      J.X = xfer32(c, l);
+    }
+    J.P = phys<float>(c);
+    J.dLs = c->dL32;
+    J.dXs = c->dX32;
+    J.level = l;
+    J.nlev = c->nlev;
+    J.model = c->soil.model;
+    J.norm = b->dnorm + B[k].slot;
+    J.stats = c->scratch + 16;
+  }
+}
+
+// the descriptors of the listed contexts to the device (the batcher's stream
+// is idle first, so that no earlier copy still reads the staging table)
+richards_status batch_upload(richards_batcher* b, std::vector<BatchCtx>& B, const std::vector<int>& who) {
+  if (who.empty()) return RICH_OK;
+  BCK(cudaStreamSynchronize(b->s));
+  for (int k : who) {
+    batch_table_slot(b, B, k);
+    const size_t off = (size_t)B[k].slot * MAXLEV;
+    BCK(cudaMemcpyAsync(b->dtable + off, b->htable + off, sizeof(rich::BJob32) * MAXLEV, cudaMemcpyHostToDevice,
+                        b->s));
+  }
+  return RICH_OK;
+}
+
+// One tick: every listed context does the next part of its current step
+// (the same operations, in the same order, as step_mixed):
+//   idle, with steps wanted  -> preparation and the first outer defect;
+//   defect                   -> the outer defect (float-float, or FP64 from
+//                               the point where step_mixed switches); the
+//                               decision after it: the FP64 defect next,
+//                               the end of the step, or an inner solve;
+//   inner                    -> one FP32 V-cycle (the cycles of all such
+//                               contexts as shared batched launches) and its
+//                               stop test; at the end of the inner solve
+//                               the correction is applied (-> defect);
+//   finish                   -> water balance and history shift.
+// Work of one context alone runs on its stream and overlaps the batched
+// cycle on the batcher's stream; one wait per stream ends the tick.
+// done[k] = 1 when context k completed a step (status in sst[k], its
+// statistics in sinfo[k]).
+richards_status batch_tick(richards_batcher* b, std::vector<BatchCtx>& B, const double* dt, const int* scheme,
+                           const std::vector<int>& want, std::vector<char>& done, std::vector<richards_status>& sst,
+                           std::vector<richards_step_info>& sinfo) {
   const int n = (int)B.size();
-  // descriptors of every level of every context
+  std::vector<int> defect, inner, finish, own, started;
   for (int k = 0; k < n; ++k) {
     richards_ctx* c = B[k].c;
-    for (int l = 0; l < c->nlev; ++l) {
-      rich::BJob32& J = b->htable[B[k].slot * MAXLEV + l];
-      J = rich::BJob32{};
-      J.F = view32(c, l);
-      if (l + 1 < c->nlev) {
-        J.C = view32(c, l + 1);
-        J.X = xfer32(c, l);
+    BatchProgress& X = c->bp;
+    done[k] = 0;
+    if (X.phase == BP_IDLE && want[k] > 0) {
+      c->updates_host = 0;
+      BCK(cudaMemsetAsync(c->scratch + 16, 0, sizeof(unsigned long long), c->s));
+      const richards_status sp = do_prepare(c, dt[k], scheme[k]);
+      own.push_back(k);
+      if (sp != RICH_OK) {                     // the step fails before it starts
+        done[k] = 1;
+        sst[k] = sp;
+        sinfo[k] = richards_step_info{};
+        continue;
       }
-      J.P = phys<float>(c);
-      J.dLs = c->dL32;
-      J.dXs = c->dX32;
-      J.level = l;
-      J.nlev = c->nlev;
-      J.model = c->soil.model;
-      J.norm = b->dnorm + B[k].slot;
-      J.stats = c->scratch + 16;
+      X = BatchProgress{};
+      X.phase = BP_DEFECT;
+      X.predicted = c->opts.predictor == 1 && c->scheme_used == 2;
+      started.push_back(k);
     }
+    if (X.phase == BP_DEFECT) defect.push_back(k);
+    else if (X.phase == BP_INNER) inner.push_back(k);
+    else if (X.phase == BP_FINISH) finish.push_back(k);
   }
-  (void)dts; (void)schemes;
-  BCK(cudaMemcpyAsync(b->dtable, b->htable, sizeof(rich::BJob32) * (size_t)n * MAXLEV, cudaMemcpyHostToDevice,
-                      b->s));
-  std::vector<int> act;
-  for (int k = 0; k < n; ++k)
-    if (B[k].ok) { B[k].outer_active = true; act.push_back(k); }
-  while (!act.empty()) {
-    std::vector<int> ff, need64;
-    for (int k : act) (B[k].use64 ? need64 : ff).push_back(k);
-    if (!ff.empty()) TRY_B(batch_defects(b, B, ff, false));
-    for (int k : ff) {
-      BatchCtx& X = B[k];
-      const richards_ctx* c = X.c;
-      const double prev = X.r_ff;
-      X.r_ff = X.r;
-      X.use64 = c->opts.precision == 2 && !std::isnan(X.r) &&
-                (!(X.r > c->opts.tol) || X.outer >= c->opts.max_outer || X.r > 0.5 * prev);
-      if (X.use64) need64.push_back(k);
+  TRY_B(batch_upload(b, B, started));
+  // work of one context alone, on its stream
+  for (int k : defect) {
+    richards_ctx* c = B[k].c;
+    const BatchProgress& X = c->bp;
+    const richards_status sd = outer_defect_launch(c, X.outer == 0 && !X.predicted, X.use64);
+    if (sd != RICH_OK) return bfail(b, sd, c->err);
+    BCK(cudaMemcpyAsync(c->hscratch, c->scratch, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
+    own.push_back(k);
+  }
+  for (int k : finish) {
+    richards_ctx* c = B[k].c;
+    BatchProgress& X = c->bp;
+    const bool moved = X.outer > 0 || X.predicted;
+    X.nbal = 0;
+    X.fin = cudaMemcpyAsync(c->hscratch + 16, c->scratch + 16, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            c->s) == cudaSuccess ? RICH_OK : fail(c, RICH_ECUDA, "stats copy");
+    if (X.fin == RICH_OK)
+      X.fin = water_balance_launch(c, X.r, moved ? c->th_cur : c->th_n, c->th_n,
+                                   c->th_nm1_valid ? c->th_nm1 : nullptr, &X.nbal);
+    if (X.fin == RICH_OK && !std::isnan(X.r)) X.fin = finish_step_launch(c, moved ? 1 : 0);
+    own.push_back(k);
+  }
+  // one FP32 V-cycle of every context in an inner solve, and the stop tests
+  std::vector<int> test;
+  if (!inner.empty()) {
+    TRY_B(bjoin(b, B, inner));
+    batch_vcycle(b, B, inner, 0, true);
+    for (int k : inner) {
+      BatchProgress& X = B[k].c->bp;
+      ++X.inner;
+      ++X.k;
+      if (B[k].c->opts.inner_rtol > 0.0 && X.k < B[k].c->opts.inner_cycles) test.push_back(k);
     }
-    if (!need64.empty()) TRY_B(batch_defects(b, B, need64, true));   // the FP64 defect decides
-    std::vector<int> go;
-    for (int k : act) {
-      BatchCtx& X = B[k];
-      if (X.outer == 0) X.r0 = X.r;
-      if (!(X.r > X.c->opts.tol) || std::isnan(X.r)) continue;
-      if (X.outer >= X.c->opts.max_outer) { X.st = RICH_ENOCONV; continue; }
-      go.push_back(k);
-    }
-    act.swap(go);
-    if (act.empty()) break;
-    for (int k : act) {
-      BatchCtx& X = B[k];
-      richards_ctx* c = X.c;
-      restrict_psi0(c);
-      X.rin0 = X.r * c->a;
-      X.rtol_in = std::max(c->opts.inner_rtol, 0.3 * c->opts.tol / X.r);
-      if (c->opts.precision == 2 && X.rtol_in > c->opts.inner_rtol) X.use64 = true;   // (as step_mixed)
-      if (top_defect_ready(c)) {
-        const richards_status sd = defect_from_g(c);
-        if (sd != RICH_OK) return bfail(b, sd, c->err);
-      }
-    }
-    TRY_B(bjoin(b, B, act));
-    std::vector<int> in = act;
-    const int cycles = B[act[0]].c->opts.inner_cycles;
-    for (int q = 0; q < cycles && !in.empty(); ++q) {
-      batch_vcycle(b, B, in, 0, true);
-      for (int k : in) ++B[k].inner;
-      if (q + 1 >= cycles) break;
-      std::vector<int> test;
-      for (int k : in)
-        if (B[k].c->opts.inner_rtol > 0.0) test.push_back(k);
-      if (test.empty()) continue;
+    if (!test.empty()) {
       const size_t nb = sizeof(unsigned long long) * B.size();
       BCK(cudaMemsetAsync(b->dnorm, 0, nb, b->s));
       batch_stage(b, B, test, rich::BOP_RESID, 0, 0, true);
       BCK(cudaMemcpyAsync(b->hnorm, b->dnorm, nb, cudaMemcpyDeviceToHost, b->s));
-      BCK(cudaStreamSynchronize(b->s));
-      std::vector<int> keep;
-      for (int k : in) {
-        if (B[k].c->opts.inner_rtol > 0.0) {
-          const unsigned u = (unsigned)b->hnorm[B[k].slot];
-          float f;
-          std::memcpy(&f, &u, 4);
-          if ((double)f <= B[k].rtol_in * B[k].rin0) continue;
-        }
-        keep.push_back(k);
-      }
-      in.swap(keep);
     }
-    TRY_B(bfork(b, B, act));
-    for (int k : act) {
+  }
+  for (int k : own) BCK(cudaStreamSynchronize(B[k].c->s));
+  if (!inner.empty()) BCK(cudaStreamSynchronize(b->s));
+  // decisions
+  std::vector<int> applied;
+  for (int k : inner) {
+    richards_ctx* c = B[k].c;
+    BatchProgress& X = c->bp;
+    bool end = X.k >= c->opts.inner_cycles;
+    if (!end && c->opts.inner_rtol > 0.0) {
+      const unsigned u = (unsigned)b->hnorm[B[k].slot];
+      float f;
+      std::memcpy(&f, &u, 4);
+      end = (double)f <= X.rtol_in * X.rin0;
+    }
+    if (end) applied.push_back(k);
+  }
+  if (!applied.empty()) {
+    TRY_B(bfork(b, B, applied));
+    for (int k : applied) {
       richards_ctx* c = B[k].c;
       rich::apply_delta(c->L[0].u, c->L[0].uf, c->L[0].ncell, c->s);
-      ++B[k].outer;
+      ++c->bp.outer;
+      c->bp.phase = BP_DEFECT;
     }
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return bfail(b, RICH_ECUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+  }
+  for (int k : defect) {
+    richards_ctx* c = B[k].c;
+    BatchProgress& X = c->bp;
+    X.r = host_norm(c, 0, !X.use64) / c->a;
+    if (!X.use64) {                            // a float-float defect: steer, or hand over to FP64
+      const double prev = X.r_ff;
+      X.r_ff = X.r;
+      X.use64 = c->opts.precision == 2 && !std::isnan(X.r) &&
+                (!(X.r > c->opts.tol) || X.outer >= c->opts.max_outer || X.r > 0.5 * prev);
+      if (X.use64) continue;                   // the FP64 defect decides, next tick
+    }
+    if (X.outer == 0) X.r0 = X.r;
+    if (!(X.r > c->opts.tol) || std::isnan(X.r)) { X.phase = BP_FINISH; continue; }
+    if (X.outer >= c->opts.max_outer) { X.st = RICH_ENOCONV; X.phase = BP_FINISH; continue; }
+    restrict_psi0(c);
+    X.rin0 = X.r * c->a;
+    X.rtol_in = std::max(c->opts.inner_rtol, 0.3 * c->opts.tol / X.r);
+    if (c->opts.precision == 2 && X.rtol_in > c->opts.inner_rtol) X.use64 = true;
+    if (top_defect_ready(c)) {
+      const richards_status sd = defect_from_g(c);
+      if (sd != RICH_OK) return bfail(b, sd, c->err);
+    }
+    X.k = 0;
+    X.phase = BP_INNER;
+  }
+  for (int k : finish) {
+    richards_ctx* c = B[k].c;
+    BatchProgress& X = c->bp;
+    richards_step_info& I = sinfo[k];
+    I = richards_step_info{};
+    I.cycles = X.inner;
+    I.outer_iters = X.outer;
+    I.scheme_used = c->scheme_used;
+    I.resid0 = X.r0;
+    I.resid = X.r;
+    I.cell_updates = c->updates_host + (long long)c->hscratch[16];
+    water_balance_done(c, X.r, X.fin == RICH_OK ? X.nbal : 0, &I);
+    richards_status sk = X.fin;
+    if (sk == RICH_OK)
+      sk = std::isnan(X.r) ? fail(c, RICH_ENAN, "NaN in the iterate; state kept at psi^n") : finish_step_done(c, X.st);
+    sst[k] = sk;
+    done[k] = 1;
+    X.phase = BP_IDLE;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bfail(b, RICH_ECUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+  return RICH_OK;
+}
+
+// Ticks until every context has done the steps it wants (until_all) or until
+// one context that wanted steps has done all of them, or max_ticks ticks
+// (> 0).  want: steps still wanted, counted down; steps[k], info[k]: steps
+// completed here and their statistics (sums of cycles, outer iterations and
+// updates; the rest from the last one); status[k]: the last step's.
+richards_status batch_run(richards_batcher* b, std::vector<BatchCtx>& B, const double* dt, const int* scheme,
+                          std::vector<int>& want, bool until_all, int max_ticks, std::vector<int>& steps,
+                          std::vector<richards_status>& status, std::vector<richards_step_info>& info) {
+  const int n = (int)B.size();
+  std::vector<char> done(n, 0);
+  std::vector<richards_status> sst(n, RICH_OK);
+  std::vector<richards_step_info> sinfo(n);
+  std::vector<int> all(n);
+  for (int k = 0; k < n; ++k) all[k] = k;
+  TRY_B(batch_upload(b, B, all));
+  for (int tick = 0; max_ticks <= 0 || tick < max_ticks; ++tick) {
+    bool busy = false;
+    for (int k = 0; k < n; ++k) busy = busy || want[k] > 0 || B[k].c->bp.phase != BP_IDLE;
+    if (!busy) break;
+    TRY_B(batch_tick(b, B, dt, scheme, want, done, sst, sinfo));
+    bool finished_one = false;
+    for (int k = 0; k < n; ++k) {
+      if (!done[k]) continue;
+      richards_step_info& I = info[k];
+      const richards_step_info& S = sinfo[k];
+      if (steps[k] == 0) {
+        I = S;
+      } else {
+        const int cyc = I.cycles + S.cycles, outer = I.outer_iters + S.outer_iters;
+        const long long upd = I.cell_updates + S.cell_updates;
+        const double r0 = I.resid0;
+        I = S;
+        I.cycles = cyc;
+        I.outer_iters = outer;
+        I.cell_updates = upd;
+        I.resid0 = r0;
+      }
+      ++steps[k];
+      status[k] = sst[k];
+      want[k] = sst[k] == RICH_OK ? want[k] - 1 : 0;   // a failed step ends the context's run
+      if (want[k] == 0) finished_one = true;
+    }
+    if (!until_all && finished_one) break;
   }
   return RICH_OK;
 }
@@ -1559,6 +1697,7 @@ richards_status richards_level_dims(const richards_ctx* c, int level, int n_out[
 richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
   if (!c || !s) return RICH_EINVAL;
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  c->bp = BatchProgress{};
   cudaStreamSynchronize(c->s);
   graphs_reset(c);
   const long long N = c->L[0].ncell;
@@ -1624,6 +1763,7 @@ richards_status richards_set_materials(richards_ctx* c, const richards_material*
                                        const unsigned char* index) {
   if (!c || !mats || !index) return RICH_EINVAL;
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  c->bp = BatchProgress{};
   if (nmat < 1 || nmat > rich::MAXMAT) return fail(c, RICH_EINVAL, "need 1 to 8 materials");
   for (int m = 0; m < nmat; ++m) {
     const richards_material& M = mats[m];
@@ -1751,6 +1891,7 @@ static richards_status refresh_sink(richards_ctx* c) {
 richards_status richards_set_sink(richards_ctx* c, const richards_sink* k) {
   if (!c || !k) return RICH_EINVAL;
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  c->bp = BatchProgress{};
   cudaStreamSynchronize(c->s);
   graphs_reset(c);
   if (const char* e = rich::sink_error(*k)) return fail(c, RICH_EINVAL, e);
@@ -1761,6 +1902,7 @@ richards_status richards_set_sink(richards_ctx* c, const richards_sink* k) {
 richards_status richards_set_bc(richards_ctx* c, const richards_bc* b) {
   if (!c || !b) return RICH_EINVAL;
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  c->bp = BatchProgress{};
   cudaStreamSynchronize(c->s);
   graphs_reset(c);
   const int dim = c->grid.dim;
@@ -1829,6 +1971,7 @@ richards_status richards_set_bc(richards_ctx* c, const richards_bc* b) {
 richards_status richards_set_state(richards_ctx* c, const double* psi, const double* psi_prev, double t) {
   if (!c || !psi) return RICH_EINVAL;
   if (c->busy.load()) return fail(c, RICH_EBUSY, "context busy: a batch is running on it");
+  c->bp = BatchProgress{};
   const long long N = c->L[0].ncell;
   if (!std::isfinite(t)) return fail(c, RICH_EINVAL, "non-finite time");
   // the values are staged in two finest-level work arrays (FAS restricted
@@ -2199,9 +2342,13 @@ void richards_batcher_destroy(richards_batcher* b) {
 
 const char* richards_batcher_last_error(const richards_batcher* b) { return b ? b->err.c_str() : "null batcher"; }
 
-richards_status richards_batcher_step(richards_batcher* b, richards_ctx* const* ctxs, int n, const double* dt,
-                                      const int* scheme, richards_status* status, richards_step_info* info) {
-  if (!b || !ctxs || !dt || !scheme || n < 1) return RICH_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// checks shared by richards_batcher_step and _advance
+richards_status batch_check(richards_batcher* b, richards_ctx* const* ctxs, int n, const double* dt,
+                            const int* scheme) {
   if (n > b->cap) return bfail(b, RICH_EINVAL, "more contexts than the batcher holds");
   const richards_opts* o0 = ctxs[0] ? &ctxs[0]->opts : nullptr;
   for (int k = 0; k < n; ++k) {
@@ -2220,71 +2367,62 @@ richards_status richards_batcher_step(richards_batcher* b, richards_ctx* const* 
     if (!(dt[k] > 0.0) || !std::isfinite(dt[k]) || (scheme[k] != 1 && scheme[k] != 2))
       return bfail(b, RICH_EINVAL, "bad dt or scheme");
   }
+  return RICH_OK;
+}
+
+richards_status batch_call(richards_batcher* b, richards_ctx* const* ctxs, int n, const double* dt,
+                           const int* scheme, std::vector<int>& want, bool until_all, int max_ticks,
+                           std::vector<int>& steps, std::vector<richards_status>& status,
+                           std::vector<richards_step_info>& info) {
   std::vector<BatchCtx> B(n);
   for (int k = 0; k < n; ++k) {
-    richards_ctx* c = ctxs[k];
-    B[k].c = c;
+    B[k].c = ctxs[k];
     B[k].slot = k;
-    c->busy.store(1);
+    ctxs[k]->busy.store(1);
   }
-  // preparation on the contexts' own streams (their earlier work is ordered
-  // before it there)
-  richards_status st = RICH_OK;
+  const richards_status st = batch_run(b, B, dt, scheme, want, until_all, max_ticks, steps, status, info);
   for (int k = 0; k < n; ++k) {
-    richards_ctx* c = B[k].c;
-    c->updates_host = 0;
-    cudaMemsetAsync(c->scratch + 16, 0, sizeof(unsigned long long), c->s);
-    B[k].st = do_prepare(c, dt[k], scheme[k]);
-    B[k].ok = B[k].st == RICH_OK;
-    B[k].predicted = c->opts.predictor == 1 && c->scheme_used == 2;
+    if (st != RICH_OK) ctxs[k]->bp = BatchProgress{};     // a failed call leaves no step in progress
+    ctxs[k]->busy.store(0);
   }
-  st = batch_step_impl(b, B, dt, scheme);
-  // water balance and history shift: launched for every context first, then
-  // one wait per stream
-  std::vector<int> all(n);
-  for (int k = 0; k < n; ++k) all[k] = k;
-  if (st == RICH_OK) st = bfork(b, B, all);
-  std::vector<richards_status> fin(n, RICH_OK);
-  std::vector<int> nbal(n, 0);
-  std::vector<richards_step_info> inf(n, richards_step_info{});
-  for (int k = 0; k < n && st == RICH_OK; ++k) {
-    BatchCtx& X = B[k];
-    if (!X.ok) continue;
-    richards_ctx* c = X.c;
-    const bool moved = X.outer > 0 || X.predicted;
-    richards_status sk = cudaMemcpyAsync(c->hscratch + 16, c->scratch + 16, sizeof(unsigned long long),
-                                         cudaMemcpyDeviceToHost, c->s) == cudaSuccess ? RICH_OK
-                                                                                      : fail(c, RICH_ECUDA, "stats copy");
-    if (sk == RICH_OK)
-      sk = water_balance_launch(c, X.r, moved ? c->th_cur : c->th_n, c->th_n, c->th_nm1_valid ? c->th_nm1 : nullptr,
-                                &nbal[k]);
-    if (sk == RICH_OK && !std::isnan(X.r)) sk = finish_step_launch(c, moved ? 1 : 0);
-    fin[k] = sk;
-  }
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+richards_status richards_batcher_step(richards_batcher* b, richards_ctx* const* ctxs, int n, const double* dt,
+                                      const int* scheme, richards_status* status, richards_step_info* info) {
+  if (!b || !ctxs || !dt || !scheme || n < 1) return RICH_EINVAL;
+  TRY_B(batch_check(b, ctxs, n, dt, scheme));
+  std::vector<int> want(n, 1), steps(n, 0);
+  std::vector<richards_status> sst(n, RICH_OK);
+  std::vector<richards_step_info> inf(n);
+  const richards_status st = batch_call(b, ctxs, n, dt, scheme, want, true, 0, steps, sst, inf);
   for (int k = 0; k < n; ++k) {
-    BatchCtx& X = B[k];
-    richards_ctx* c = X.c;
-    const bool synced = cudaStreamSynchronize(c->s) == cudaSuccess;
-    richards_status sk = st != RICH_OK ? st : X.st;
-    if (st == RICH_OK && X.ok) {
-      sk = synced ? fin[k] : fail(c, RICH_ECUDA, "stream synchronisation");
-      richards_step_info& I = inf[k];
-      I.cycles = X.inner;
-      I.outer_iters = X.outer;
-      I.scheme_used = c->scheme_used;
-      I.resid0 = X.r0;
-      I.resid = X.r;
-      I.cell_updates = c->updates_host + (long long)c->hscratch[16];
-      water_balance_done(c, X.r, sk == RICH_OK ? nbal[k] : 0, &I);
-      if (sk == RICH_OK)
-        sk = std::isnan(X.r) ? fail(c, RICH_ENAN, "NaN in the iterate; state kept at psi^n")
-                             : finish_step_done(c, X.st);
-      if (info) info[k] = I;
-    } else if (info) {
-      info[k] = richards_step_info{};
-    }
-    if (status) status[k] = sk;
-    c->busy.store(0);
+    if (status) status[k] = st != RICH_OK ? st : sst[k];
+    if (info) info[k] = st == RICH_OK && steps[k] > 0 ? inf[k] : richards_step_info{};
+  }
+  return st;
+}
+
+richards_status richards_batcher_advance(richards_batcher* b, richards_ctx* const* ctxs, int n, const double* dt,
+                                         const int* scheme, int* steps_left, int max_ticks, int* steps_done,
+                                         richards_status* status, richards_step_info* info) {
+  if (!b || !ctxs || !dt || !scheme || !steps_left || n < 1) return RICH_EINVAL;
+  for (int k = 0; k < n; ++k)
+    if (steps_left[k] < 0) return bfail(b, RICH_EINVAL, "negative steps_left");
+  TRY_B(batch_check(b, ctxs, n, dt, scheme));
+  std::vector<int> want(steps_left, steps_left + n), steps(n, 0);
+  std::vector<richards_status> sst(n, RICH_OK);
+  std::vector<richards_step_info> inf(n);
+  const richards_status st = batch_call(b, ctxs, n, dt, scheme, want, false, max_ticks, steps, sst, inf);
+  for (int k = 0; k < n; ++k) {
+    if (st == RICH_OK) steps_left[k] = want[k];
+    if (steps_done) steps_done[k] = st == RICH_OK ? steps[k] : 0;
+    if (status) status[k] = st != RICH_OK ? st : sst[k];
+    if (info) info[k] = st == RICH_OK && steps[k] > 0 ? inf[k] : richards_step_info{};
   }
   return st;
 }

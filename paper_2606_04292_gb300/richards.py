@@ -138,6 +138,9 @@ _SIGS = {
     "richards_batcher_last_error": (C.c_char_p, [_VP]),
     "richards_batcher_step": (C.c_int, [_VP, C.POINTER(_VP), C.c_int, _DP, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                         C.POINTER(richards_step_info)]),
+    "richards_batcher_advance": (C.c_int, [_VP, C.POINTER(_VP), C.c_int, _DP, C.POINTER(C.c_int),
+                                           C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                           C.POINTER(richards_step_info)]),
     "richards_step_small_noalloc": (C.c_int, [C.POINTER(richards_grid), C.POINTER(richards_soil),
                                               C.POINTER(richards_bc), C.POINTER(richards_sink),
                                               C.POINTER(richards_opts), C.c_double, C.c_int, _DP, _DP, _DP,
@@ -525,3 +528,23 @@ class Batcher:
         if st != RICH_OK:
             raise RichardsError(st, lib().richards_batcher_last_error(self.h).decode())
         return [int(x) for x in status], [info[k].as_dict() for k in range(n)]
+
+    def advance(self, solvers, dts, schemes, steps_left, max_ticks=0):
+        """Continuous batching (``richards_batcher_advance``): each solver
+        takes up to steps_left[k] more steps on its own schedule; returns
+        when one of them has done all its steps (or after max_ticks ticks).
+        Returns (steps_left, steps_done, status, info) lists; info[k] sums
+        cycles, outer iterations and updates over the steps done."""
+        n = len(solvers)
+        hs = (C.c_void_p * n)(*[s.h.value for s in solvers])
+        dt = _f64(dts)
+        sc = (C.c_int * n)(*[int(x) for x in schemes])
+        left = (C.c_int * n)(*[int(x) for x in steps_left])
+        done = (C.c_int * n)()
+        status = (C.c_int * n)()
+        info = (richards_step_info * n)()
+        st = lib().richards_batcher_advance(self.h, hs, n, _dp(dt), sc, left, int(max_ticks), done, status, info)
+        if st != RICH_OK:
+            raise RichardsError(st, lib().richards_batcher_last_error(self.h).decode())
+        return ([int(x) for x in left], [int(x) for x in done], [int(x) for x in status],
+                [info[k].as_dict() for k in range(n)])

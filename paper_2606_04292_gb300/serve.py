@@ -35,14 +35,17 @@ def request_bytes(prob, opts=None):
 class Server:
     """batched=False: every admitted request runs on its own stream and host
     worker thread (richards_batch_submit), their kernels overlapping on the
-    device.  batched=True: the admitted requests advance in lockstep, one
-    time step per round, through richards_batcher_step -- each stage of their
-    FP32 inner cycles is one launch over all of them; requests are admitted
-    and retired between rounds (every request in a mixed mode with the same
-    cycle options)."""
+    device.  batched=True: continuous batching through
+    richards_batcher_advance -- every admitted request advances on its own
+    schedule (preparation, outer defects, inner cycles, end of step), the
+    FP32 inner cycles of all requests in an inner solve run as shared
+    launches, and a call returns when a request has done all its steps (or,
+    while more requests may be admitted, after admit_ticks ticks); requests
+    are admitted and retired between calls (every request in a mixed mode
+    with the same cycle options)."""
 
     def __init__(self, budget_bytes=None, max_active=16, keep_states=False, opts=None, poll_s=2e-4,
-                 batched=False):
+                 batched=False, admit_ticks=8):
         import torch
         self.torch = torch
         if budget_bytes is None:
@@ -54,6 +57,7 @@ class Server:
         self.opts = opts
         self.poll_s = poll_s
         self.batched = batched
+        self.admit_ticks = int(admit_ticks)
 
     def run(self, requests, realtime=True):
         """Serve ``requests``; returns (results, summary)."""
@@ -174,17 +178,25 @@ class Server:
                     time.sleep(self.poll_s)
                     continue
                 ids = list(active)
-                statuses, infos = batcher.step([active[r]["solver"] for r in ids],
-                                               [float(active[r]["prob"]["dt"]) for r in ids],
-                                               [int(active[r]["prob"]["scheme"]) for r in ids])
+                # continuous batching: every request advances on its own
+                # schedule until one of them is done (or, while requests may
+                # still be admitted, for a few ticks)
+                more = bool(pending or waiting)
+                left, done, statuses, infos = batcher.advance(
+                    [active[r]["solver"] for r in ids], [float(active[r]["prob"]["dt"]) for r in ids],
+                    [int(active[r]["prob"]["scheme"]) for r in ids],
+                    [active[r]["prob"]["nsteps"] - active[r]["done"] for r in ids],
+                    max_ticks=self.admit_ticks if more else 0)
                 end = time.perf_counter() - t0
-                for rid, st, info in zip(ids, statuses, infos):
+                for rid, rest, d, st, info in zip(ids, left, done, statuses, infos):
                     a = active[rid]
-                    a["done"] += 1
+                    if d == 0:
+                        continue
+                    a["done"] += d
                     for k in ("cycles", "outer_iters", "cell_updates"):
                         a["acc"][k] += info[k]
                     a["acc"]["resid"] = info["resid"]
-                    if st != R.RICH_OK or a["done"] >= a["prob"]["nsteps"]:
+                    if st != R.RICH_OK or rest == 0:
                         res = dict(id=rid, status=R.STATUS_NAMES[st], arrival=a["arrival"], start=a["start"],
                                    end=end, latency=end - a["arrival"], queue=a["start"] - a["arrival"],
                                    steps=a["done"], cells=int(np.prod(a["prob"]["n"])), info=dict(a["acc"]),

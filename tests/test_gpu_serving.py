@@ -138,9 +138,60 @@ def test_batched_steps_equal_single_steps():
     print("batched states bit for bit equal:", exact)
 
 
+def test_continuous_advance_equals_single_steps():
+    """richards_batcher_advance: each context takes its own number of steps
+    on its own schedule (calls of a few ticks leave contexts mid-step and
+    the next call continues them); every state, and the summed cycle and
+    outer counts, equal those of richards_step alone (1e-10)."""
+    reqs = batch_mix()
+    want = [2 + k % 3 for k in range(len(reqs))]
+    streams = [torch.cuda.Stream() for _ in reqs]
+    batched = [R.Solver(p, stream=s.cuda_stream) for p, s in zip(reqs, streams)]
+    alone = [R.Solver(p) for p in reqs]
+    ref_cycles, ref_outer = [], []
+    for k, p in enumerate(reqs):
+        cyc = outer = 0
+        for _ in range(want[k]):
+            st, info = alone[k].step(p["dt"], p["scheme"], check=False)
+            assert st == R.RICH_OK
+            cyc += info["cycles"]
+            outer += info["outer_iters"]
+        ref_cycles.append(cyc)
+        ref_outer.append(outer)
+    b = R.Batcher(max_contexts=len(reqs))
+    left = list(want)
+    got_steps = [0] * len(reqs)
+    got_cycles = [0] * len(reqs)
+    got_outer = [0] * len(reqs)
+    calls = 0
+    while any(left):
+        idx = [k for k in range(len(reqs)) if left[k] > 0]
+        new_left, done, sts, infos = b.advance([batched[k] for k in idx], [reqs[k]["dt"] for k in idx],
+                                               [reqs[k]["scheme"] for k in idx], [left[k] for k in idx],
+                                               max_ticks=3)
+        calls += 1
+        for j, k in enumerate(idx):
+            assert sts[j] == R.RICH_OK, (k, sts[j])
+            left[k] = new_left[j]
+            got_steps[k] += done[j]
+            if done[j]:
+                got_cycles[k] += infos[j]["cycles"]
+                got_outer[k] += infos[j]["outer_iters"]
+        assert calls < 500
+    assert calls > 3                                  # calls did return mid-way
+    for k in range(len(reqs)):
+        assert got_steps[k] == want[k]
+        assert (got_cycles[k], got_outer[k]) == (ref_cycles[k], ref_outer[k]), k
+        got, ref = batched[k].state(), alone[k].state()
+        assert np.max(np.abs(got - ref)) <= STEP_RTOL * np.max(np.abs(ref)), k
+    b.close()
+    for s in batched + alone:
+        s.close()
+
+
 def test_batched_server_same_alone_and_in_the_mix():
-    """Continuous batching through lockstep batched cycles: requests admitted
-    as slots free up (3 slots for 7 requests), each result the same as alone."""
+    """Continuous batching (richards_batcher_advance): requests admitted as
+    slots free up (3 slots for 7 requests), each result the same as alone."""
     reqs = batch_mix()
     alone = [solve_alone(p) for p in reqs]
     srv = serve.Server(max_active=3, keep_states=True, batched=True)
@@ -167,6 +218,9 @@ def test_batcher_rejects_what_it_cannot_batch():
         assert e.value.status == R.RICH_EINVAL
     with pytest.raises(R.RichardsError):
         b.step([a, fp64, other], [60.0] * 3, [1] * 3)      # more than the batcher holds
+    with pytest.raises(R.RichardsError) as e:
+        b.advance([a], [60.0], [1], [-1])
+    assert e.value.status == R.RICH_EINVAL
     for s in (a, fp64, other):
         s.close()
     b.close()
