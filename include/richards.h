@@ -274,6 +274,15 @@ long long richards_ncell(const richards_ctx *ctx);
    owned by the context); "" when none. */
 const char *richards_last_error(const richards_ctx *ctx);
 
+/* Why a step of this context launches its FP32 inner cycles one by one
+   instead of as CUDA graphs (static storage owned by the context; "" when
+   every graph it needed so far was built): the cycle graph (one replay per
+   cycle) and the inner-loop graph (the whole inner solve: a conditional
+   while node around the cycle and its stop test, so that no cycle waits
+   for the host).  Graphs are used on a stream of the context's own
+   (not the NULL stream) with opts.graphs set and kernel timing off. */
+const char *richards_graph_status(const richards_ctx *ctx);
+
 /* Release the context and all its device memory.  NULL is accepted. */
 void richards_destroy(richards_ctx *ctx);
 

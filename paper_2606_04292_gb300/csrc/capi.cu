@@ -29,7 +29,7 @@ namespace {
 
 constexpr int MAXLEV = 24;
 constexpr int NSCRATCH = 72;   // norm slots + statistics (32..63: the single-block step's; 64..66: the
-                               // cooperative cycle's reductions)
+                               // cooperative cycle's reductions; 67..71: the inner-loop graph's control)
 // Levels of at most this many cells run as one cooperative launch: 0, off by
 // default -- on the 256^3 drainage its grid barriers cost more than the
 // graph-replayed stage launches they replace (32.8 ms per step without, 33.7
@@ -137,6 +137,18 @@ struct richards_ctx {
   };
   GraphRec graphs[3];
   bool graphs_ok = true, capturing = false;
+  // the whole FP32 inner solve as one graph (a conditional while node around
+  // the cycle and its stop test), one per scheme; loop_ok: the device takes
+  // conditional nodes
+  struct LoopRec {
+    cudaGraphExec_t exec = nullptr;
+    double a = 0.0;
+    long long updates = 0;             // NGS updates of one cycle
+  };
+  LoopRec loops[3];
+  bool loop_ok = true;
+  std::string loop_err;
+  std::string graph_status;             // richards_graph_status's message
   std::string graph_err;
   GraphRec* harvest = nullptr;
   std::vector<ProfRec> capture_recs;
@@ -280,6 +292,10 @@ void graphs_reset(richards_ctx* c) {
     for (auto& r : g.prof)
       if (r.a) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     g.prof.clear();
+  }
+  for (auto& g : c->loops) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
   }
   c->harvest = nullptr;
 }
@@ -752,6 +768,122 @@ void run_cycle32(richards_ctx* c) {
   vcycle32(c, 0, ready, fuse);
 }
 
+// ---------------------------------------------------------------------------
+// The FP32 inner solve as one graph: a conditional while node whose body is
+// the inner cycle, its stop test (the defect norm into scratch slot 1) and
+// k_inner_loop_cond, which counts the cycle and continues while the count is
+// below inner_cycles and the defect above its target -- the loop of
+// step_mixed, decided on the device instead of after a host round trip per
+// cycle.  The loop's control words sit in scratch slots LOOP_SLOT.. (count,
+// cap, target bits, test flag), staged through the same slots of hscratch.
+// ---------------------------------------------------------------------------
+constexpr int LOOP_SLOT = 67;     // 67..70 on the device; 71 receives the count on the host
+
+__global__ void k_inner_loop_cond(cudaGraphConditionalHandle h, const unsigned long long* nrm,
+                                  unsigned long long* ctl) {
+  const unsigned long long k = ++ctl[0];
+  bool more = k < ctl[1];
+  if (more && ctl[3]) {
+    const float f = __uint_as_float((unsigned)*nrm);
+    more = !((double)f <= __longlong_as_double((long long)ctl[2]));
+  }
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// builds the loop graph of the current scheme and a; false when the device
+// or the driver refuses it (loop_ok is then cleared: host loop from then on)
+bool build_inner_loop(richards_ctx* c, richards_ctx::LoopRec& G) {
+  const bool ready = top_defect_ready(c), fuse = fuse_defect(c);
+  const bool test = c->opts.inner_rtol > 0.0;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  cudaGraphNodeParams np{};
+  cudaGraphNode_t node = nullptr;
+  const char* where = "cudaGraphCreate";
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) {
+    where = "cudaGraphConditionalHandleCreate";
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  }
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    where = "cudaGraphAddNode";
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  }
+  const long long before = c->updates_host;
+  if (e == cudaSuccess) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    where = "cudaStreamBeginCaptureToGraph";
+    e = cudaStreamBeginCaptureToGraph(c->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      c->capturing = true;
+      vcycle32(c, 0, ready, fuse);
+      G.updates = c->updates_host - before;
+      if (test && !fuse) {
+        cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s);
+        rich::residual32(view32(c, 0), phys<float>(c), c->soil.model, c->scratch + 1, c->s, c->tune_rbx[0]);
+      }
+      k_inner_loop_cond<<<1, 1, 0, c->s>>>(h, c->scratch + 1, c->scratch + LOOP_SLOT);
+      c->capturing = false;
+      const cudaError_t el = cudaGetLastError();
+      cudaGraph_t out = nullptr;
+      e = cudaStreamEndCapture(c->s, &out);
+      where = "cudaStreamEndCapture";
+      if (e == cudaSuccess && el != cudaSuccess) { e = el; where = "launch during capture"; }
+    }
+  }
+  c->updates_host = before;
+  if (e == cudaSuccess) {
+    where = "cudaGraphInstantiate";
+    e = cudaGraphInstantiate(&G.exec, g, 0);
+  }
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    G.exec = nullptr;
+    c->loop_ok = false;
+    c->loop_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return false;
+  }
+  G.a = c->a;
+  return true;
+}
+
+// whether the inner solve runs as the loop graph (graphs on, no timing, no
+// cooperative levels, a stream of the context's own)
+bool inner_loop_usable(const richards_ctx* c) {
+  return c->opts.graphs && c->graphs_ok && c->loop_ok && c->s != nullptr && c->prof == 0 && !c->capturing &&
+         c->coop_start >= c->nlev && c->opts.inner_cycles >= 1;
+}
+
+// one inner solve through the loop graph: at most inner_cycles cycles, until
+// the defect norm is at most target (test: inner_rtol > 0); *cycles gets the
+// count.  RICH_EINVAL (nothing launched) when the graph cannot be built.
+richards_status run_inner_loop(richards_ctx* c, double target, int* cycles) {
+  richards_ctx::LoopRec& G = c->loops[c->scheme_used];
+  if (!G.exec || G.a != c->a) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    if (!build_inner_loop(c, G)) return RICH_EINVAL;
+  }
+  unsigned long long* h = c->hscratch + LOOP_SLOT;
+  h[0] = 0;
+  h[1] = (unsigned long long)c->opts.inner_cycles;
+  std::memcpy(&h[2], &target, sizeof(double));
+  h[3] = c->opts.inner_rtol > 0.0 ? 1ull : 0ull;
+  CK(cudaMemcpyAsync(c->scratch + LOOP_SLOT, h, 4 * sizeof(unsigned long long), cudaMemcpyHostToDevice, c->s));
+  CK(cudaGraphLaunch(G.exec, c->s));
+  CK(cudaMemcpyAsync(c->hscratch + LOOP_SLOT + 4, c->scratch + LOOP_SLOT, sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  *cycles = (int)c->hscratch[LOOP_SLOT + 4];
+  c->updates_host += (long long)*cycles * G.updates;
+  return RICH_OK;
+}
+
 // coarse copies of the lagged conductivity and boundary conductances
 // (mixed mode: the coarse coefficients only feed the FP32 inner cycles, so
 // they are restricted in FP32 from the finest level's FP32 copies)
@@ -1123,6 +1255,13 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
       }
     }
     const bool fused = fuse_defect(c);           // the cycle leaves d and its norm
+    if (!done_in && inner_loop_usable(c)) {     // the whole inner solve on the device
+      int k = 0;
+      if (run_inner_loop(c, rtol_in * rin0, &k) == RICH_OK) {
+        inner += k;
+        done_in = true;
+      }
+    }
     for (int k = 0; k < c->opts.inner_cycles && !done_in; ++k) {
       run_cycle32(c);
       ++inner;
@@ -1683,6 +1822,16 @@ void richards_destroy(richards_ctx* c) {
 }
 
 const char* richards_last_error(const richards_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+const char* richards_graph_status(const richards_ctx* c) {
+  if (!c) return "null context";
+  richards_ctx* m = const_cast<richards_ctx*>(c);
+  m->graph_status.clear();
+  if (!c->graph_err.empty()) m->graph_status = "cycle graph: " + c->graph_err;
+  if (!c->loop_err.empty())
+    m->graph_status += (m->graph_status.empty() ? "" : "; ") + std::string("inner-loop graph: ") + c->loop_err;
+  return m->graph_status.c_str();
+}
 
 double richards_time(const richards_ctx* c) { return c ? c->t : 0.0; }
 long long richards_ncell(const richards_ctx* c) { return c ? c->L[0].ncell : 0; }

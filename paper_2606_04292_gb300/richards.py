@@ -133,6 +133,7 @@ _SIGS = {
     "richards_autotune": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "richards_set_launch": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, C.c_int]),
     "richards_set_coop": (C.c_int, [_VP, C.c_longlong]),
+    "richards_graph_status": (C.c_char_p, [_VP]),
     "richards_batcher_create": (C.c_int, [_VP, C.c_int, C.POINTER(_VP)]),
     "richards_batcher_destroy": (None, [_VP]),
     "richards_batcher_last_error": (C.c_char_p, [_VP]),
@@ -300,6 +301,10 @@ class Solver:
         if check and st not in (RICH_OK,):
             _check(st, self.h)
         return st, info.as_dict()
+
+    def graph_status(self):
+        """"" when the inner cycles run as CUDA graphs, else why not."""
+        return lib().richards_graph_status(self.h).decode()
 
     def state(self):
         out = np.empty(self.N)

@@ -634,7 +634,9 @@ def test_full_size_drainage_step_solves_the_oracle_system(precision):
 
 
 def test_graph_replay_matches_direct_launches():
-    """The captured FP32 inner cycle replays exactly the launches it replaced."""
+    """The captured FP32 inner solve (cycle graphs inside a conditional while
+    node that takes the inner stop test on the device) makes exactly the
+    launches and decisions of the host-driven loop it replaced."""
     prob = W.with_opts(W.random_problem(3, (40, 36, 33), W.VANGENUCHTEN, 12, hetero=True, sink=True, scheme=2),
                        precision=1)
     stream = torch.cuda.Stream()
@@ -646,6 +648,7 @@ def test_graph_replay_matches_direct_launches():
         assert sa == sb == R.RICH_OK
         assert ia["cycles"] == ib["cycles"] and ia["cell_updates"] == ib["cell_updates"]
     assert np.array_equal(a.state(), b.state())
+    assert a.graph_status() == ""                  # both graphs were built and used
     a.profile(True)
     a.step()
     prof = a.profile_read()
