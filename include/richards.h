@@ -131,10 +131,13 @@ typedef struct {
                           paper's), 2 = W-cycle
      gamma_levels         cycle_gamma applies on the levels above this one
                           (0: on every level); coarser levels use V-cycles
-     graphs               1: capture the FP32 inner cycle of the mixed mode
-                          into a CUDA graph and replay it (needs a stream
-                          other than the legacy default stream; falls back
-                          to direct launches otherwise)
+     graphs               1: the FP32 inner solve of the mixed mode as CUDA
+                          graphs -- the cycle captured once and replayed,
+                          inside a conditional while node that takes the
+                          inner stop test on the device (needs a stream
+                          other than the legacy default stream and kernel
+                          timing off; falls back to direct launches and a
+                          host-driven loop otherwise: richards_graph_status) 
      sweep_planes         FP32 half-sweeps: cells per thread along z (1, 2,
                           4 or 8); above 1 a thread loads the operands of
                           its next cell before it solves the current one
@@ -498,10 +501,9 @@ int richards_profile_read(richards_ctx *ctx, richards_kernel_stat *out, int max)
  * Scratch: one fixed 2 MiB array in the library's device memory (every
  * device that loads the library keeps it until the process exits); nothing
  * is allocated.  The first call on each device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make the first
- * call on a device before any stream capture.  All calls share the array:
- * calls that overlap on the GPU (two streams, two host threads) race and
- * must be serialised by the caller.  The array keeps the last call's
+ * address (cudaGetSymbolAddress) with the device current.  All calls share
+ * the array: calls that overlap on the GPU (two streams, two host threads)
+ * race and must be serialised by the caller.  The array keeps the last call's
  * contents; a call writes every value before reading it, so nothing has to
  * start at zero.
  *
