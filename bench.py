@@ -51,6 +51,11 @@ DTYPE = {2: "f32 inner / f64 outer, f64 state", 1: "f32 inner / float-float (f32
 # planes), from an ncu capture of this kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); the roofline's traffic.
 TRAFFIC_PER_LAUNCH = {("sweep32", 8388608): 318.5e6}
+# What binds that launch instead of DRAM, from the same capture: the share of
+# issue slots active (smsp__issue_active) and of DRAM bandwidth in use.
+BINDING_PER_LAUNCH = {("sweep32", 8388608): {"limit": "instruction issue", "issue_active": 0.81,
+                                             "dram_throughput": 0.43, "thread_instructions_per_update": 343,
+                                             "source": "ncu --set full (profiles/sweep32_drainage256_mixed.md)"}}
 
 BYTES_PER_CELL = {
     "sweep32": 28.0,
@@ -192,7 +197,8 @@ def roofline(prof, steps, ms_pass):
         out.update({"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / pk["hbm_gbs"], "peak_source": src + " hbm_gbs",
                     "algorithmic_bytes_per_launch": bytes_per_launch,
-                    "traffic": TRAFFIC_PER_LAUNCH.get((dom, round(cells / max(launches, 1))))})
+                    "traffic": TRAFFIC_PER_LAUNCH.get((dom, round(cells / max(launches, 1)))),
+                    "binding": BINDING_PER_LAUNCH.get((dom, round(cells / max(launches, 1))))})
     else:
         out.update({"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": None,
                     "traffic": None})
