@@ -777,6 +777,10 @@ void run_cycle32(richards_ctx* c) {
 // cycle.  The loop's control words sit in scratch slots LOOP_SLOT.. (count,
 // cap, target bits, test flag), staged through the same slots of hscratch.
 // ---------------------------------------------------------------------------
+// finest levels of at least this many cells run their inner cycles as
+// richards_step does, on their own stream, under a batcher too
+constexpr long long BATCH_OWN_CELLS = 1LL << 20;
+
 constexpr int LOOP_SLOT = 67;     // 67..70 on the device; 71 receives the count on the host
 
 __global__ void k_inner_loop_cond(cudaGraphConditionalHandle h, const unsigned long long* nrm,
@@ -1554,12 +1558,32 @@ richards_status batch_tick(richards_batcher* b, std::vector<BatchCtx>& B, const 
     if (X.fin == RICH_OK && !std::isnan(X.r)) X.fin = finish_step_launch(c, moved ? 1 : 0);
     own.push_back(k);
   }
-  // one FP32 V-cycle of every context in an inner solve, and the stop tests
-  std::vector<int> test;
-  if (!inner.empty()) {
-    TRY_B(bjoin(b, B, inner));
-    batch_vcycle(b, B, inner, 0, true);
-    for (int k : inner) {
+  // one FP32 V-cycle of every context in an inner solve, and the stop tests.
+  // A context whose finest level has BATCH_OWN_CELLS cells or more fills the
+  // GPU alone: its cycle is richards_step's (the context's cycle graph, on its
+  // own stream); the others share the batched launches.
+  std::vector<int> test, inner_b, inner_own;
+  for (int k : inner) (B[k].c->L[0].ncell >= BATCH_OWN_CELLS ? inner_own : inner_b).push_back(k);
+  for (int k : inner_own) {
+    richards_ctx* c = B[k].c;
+    BatchProgress& X = c->bp;
+    run_cycle32(c);
+    ++X.inner;
+    ++X.k;
+    if (c->opts.inner_rtol > 0.0 && X.k < c->opts.inner_cycles) {
+      if (!fuse_defect(c)) {                   // (fused: the cycle left the defect norm in slot 1)
+        BCK(cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s));
+        rich::residual32(view32(c, 0), phys<float>(c), c->soil.model, c->scratch + 1, c->s, c->tune_rbx[0]);
+      }
+      BCK(cudaMemcpyAsync(c->hscratch + 1, c->scratch + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                          c->s));
+    }
+    own.push_back(k);
+  }
+  if (!inner_b.empty()) {
+    TRY_B(bjoin(b, B, inner_b));
+    batch_vcycle(b, B, inner_b, 0, true);
+    for (int k : inner_b) {
       BatchProgress& X = B[k].c->bp;
       ++X.inner;
       ++X.k;
@@ -1573,23 +1597,27 @@ richards_status batch_tick(richards_batcher* b, std::vector<BatchCtx>& B, const 
     }
   }
   for (int k : own) BCK(cudaStreamSynchronize(B[k].c->s));
-  if (!inner.empty()) BCK(cudaStreamSynchronize(b->s));
+  if (!inner_b.empty()) BCK(cudaStreamSynchronize(b->s));
   // decisions
-  std::vector<int> applied;
+  std::vector<int> applied, applied_b;
   for (int k : inner) {
     richards_ctx* c = B[k].c;
     BatchProgress& X = c->bp;
+    const bool alone = c->L[0].ncell >= BATCH_OWN_CELLS;
     bool end = X.k >= c->opts.inner_cycles;
     if (!end && c->opts.inner_rtol > 0.0) {
-      const unsigned u = (unsigned)b->hnorm[B[k].slot];
+      const unsigned u = (unsigned)(alone ? c->hscratch[1] : b->hnorm[B[k].slot]);
       float f;
       std::memcpy(&f, &u, 4);
       end = (double)f <= X.rtol_in * X.rin0;
     }
-    if (end) applied.push_back(k);
+    if (end) {
+      applied.push_back(k);
+      if (!alone) applied_b.push_back(k);
+    }
   }
   if (!applied.empty()) {
-    TRY_B(bfork(b, B, applied));
+    TRY_B(bfork(b, B, applied_b));
     for (int k : applied) {
       richards_ctx* c = B[k].c;
       rich::apply_delta(c->L[0].u, c->L[0].uf, c->L[0].ncell, c->s);

@@ -189,6 +189,30 @@ def test_continuous_advance_equals_single_steps():
         s.close()
 
 
+def test_batcher_runs_big_requests_on_their_own_cycles():
+    """A request whose finest level has at least 2^20 cells takes its inner
+    cycles through its own cycle graph under the batcher, beside batched small
+    ones; every state and count still equals richards_step's."""
+    reqs = [W.drainage_3d(n=129, precision=2), W.drainage_3d(n=33, precision=2),
+            W.drainage_3d(n=17, precision=1)]        # 2,146,689 cells (one's own cycles), 35,937, 4,913
+    streams = [torch.cuda.Stream() for _ in reqs]
+    batched = [R.Solver(p, stream=s.cuda_stream) for p, s in zip(reqs, streams)]
+    alone = [R.Solver(p) for p in reqs]
+    b = R.Batcher(max_contexts=len(reqs))
+    for step in range(2):
+        sts, infos = b.step(batched, [p["dt"] for p in reqs], [p["scheme"] for p in reqs])
+        for k, p in enumerate(reqs):
+            st, info = alone[k].step(p["dt"], p["scheme"], check=False)
+            assert sts[k] == st == R.RICH_OK, (step, k, sts[k], st)
+            for key in ("cycles", "outer_iters", "cell_updates"):
+                assert infos[k][key] == info[key], (step, k, key, infos[k][key], info[key])
+            got, want = batched[k].state(), alone[k].state()
+            assert np.max(np.abs(got - want)) <= STEP_RTOL * np.max(np.abs(want)), (step, k)
+    b.close()
+    for s in batched + alone:
+        s.close()
+
+
 def test_batched_server_same_alone_and_in_the_mix():
     """Continuous batching (richards_batcher_advance): requests admitted as
     slots free up (3 slots for 7 requests), each result the same as alone."""
