@@ -359,6 +359,8 @@ richards_status richards_set_coop(richards_ctx *ctx, long long max_cells);
  * launch over a device table of (context, level) descriptors on the
  * batcher's stream (Section 3.2's cycle for each context); the work of one
  * context alone runs on the context's own stream and overlaps them.  A
+ * context whose finest level has 2^20 cells or more fills the GPU alone: its
+ * cycles run as in richards_step (its own cycle graph, on its own stream).  A
  * context's arithmetic, decisions and results are those of richards_step
  * (no reduction mixes contexts).  A context can be mid-step when a call
  * returns; the next call continues it (a call that prepares a step of the
