@@ -84,12 +84,15 @@ struct ColumnLevels {
   const Level<float>* Ls;
   float slo, shi;
   __device__ const Level<float>& L(int l) const { return Ls[l]; }
-  __device__ float restrict(int l, const float* fine, int J0, int, int) const {
+  // the taps of coarse row J0: fine indices ri, weights rw (cnt of them) and
+  // the inverse of their sum
+  __device__ int taps(int l, int J0, int* ri, float* rw, float& inv) const {
     const int nf = Ls[l].n0, nc = Ls[l + 1].n0;
-    int ri[RMAX];
-    float rw[RMAX];
     int cnt = 0;
-    const int lo = nf == 1 ? 0 : max(0, 2 * J0 - 4), hi = nf == 1 ? 0 : min(nf - 1, 2 * J0 + 4);
+    // (nc = ceil(nf/2): a fine cell i reaches coarse rows floor(t), floor(t) + 1
+    // with t = ((2i+1) nc - nf) / (2 nf), so the cells of row J0 lie in
+    // [2 J0 - 2, 2 J0 + 2]; checked for every nf up to 2048)
+    const int lo = nf == 1 ? 0 : max(0, 2 * J0 - 2), hi = nf == 1 ? 0 : min(nf - 1, 2 * J0 + 2);
     for (int i = lo; i <= hi; ++i) {
       int idx[2];
       float w[2];
@@ -100,10 +103,30 @@ struct ColumnLevels {
     }
     float s = 0.0f;
     for (int k = 0; k < cnt; ++k) s += rw[k];
-    const float inv = 1.0f / s;
+    inv = 1.0f / s;
+    return cnt;
+  }
+  __device__ float restrict(int l, const float* fine, int J0, int, int) const {
+    int ri[RMAX];
+    float rw[RMAX], inv;
+    const int cnt = taps(l, J0, ri, rw, inv);
     float acc = 0.0f;
     for (int k = 0; k < cnt; ++k) acc += rw[k] * inv * fine[ri[k]];
     return acc;
+  }
+  // two arrays through one computation of the taps (the same sums as two
+  // restrict calls)
+  __device__ void restrict2(int l, const float* fa, const float* fb, int J0, int, int, float& a, float& b) const {
+    int ri[RMAX];
+    float rw[RMAX], inv;
+    const int cnt = taps(l, J0, ri, rw, inv);
+    float sa = 0.0f, sb = 0.0f;
+    for (int k = 0; k < cnt; ++k) {
+      sa += rw[k] * inv * fa[ri[k]];
+      sb += rw[k] * inv * fb[ri[k]];
+    }
+    a = sa;
+    b = sb;
   }
   __device__ float prolong(int l, int i0, int, int) const {
     const Level<float>& C = Ls[l + 1];

@@ -624,8 +624,7 @@ __device__ __forceinline__ void block_cycle(const LV& lv, int l0, int nl, const 
       for (long long J = tm.rank(); J < C.ncell; J += tm.size()) {
         int J0, J1, J2;
         cell_coords(C.n0, C.n1, J, J0, J1, J2);
-        C.ubar[J] = lv.restrict(l, F.u, J0, J1, J2);
-        C.d[J] = lv.restrict(l, F.d, J0, J1, J2);
+        lv.restrict2(l, F.u, F.d, J0, J1, J2, C.ubar[J], C.d[J]);
       }
       tm.sync();
       for (long long J = tm.rank(); J < C.ncell; J += tm.size()) {
@@ -669,6 +668,10 @@ struct DeviceLevels {
   __device__ T restrict(int l, const T* fine, int J0, int J1, int J2) const {
     return restrict_at(Ls[l], Xs[l], fine, J0, J1, J2);
   }
+  __device__ void restrict2(int l, const T* fa, const T* fb, int J0, int J1, int J2, T& a, T& b) const {
+    a = restrict(l, fa, J0, J1, J2);
+    b = restrict(l, fb, J0, J1, J2);
+  }
   __device__ T prolong(int l, int i0, int i1, int i2) const { return prolong_at(Ls[l + 1], Xs[l], i0, i1, i2); }
 };
 
@@ -704,6 +707,10 @@ struct CoopLevels {
   __device__ T restrict(int l, const T* fine, int J0, int J1, int J2) const {
     return nested(l) ? restrict_nested_at(Ls[l], Ls[l + 1], fine, J0, J1, J2)
                      : restrict_at(Ls[l], Xs[l], fine, J0, J1, J2);
+  }
+  __device__ void restrict2(int l, const T* fa, const T* fb, int J0, int J1, int J2, T& a, T& b) const {
+    a = restrict(l, fa, J0, J1, J2);
+    b = restrict(l, fb, J0, J1, J2);
   }
   __device__ T prolong(int l, int i0, int i1, int i2) const {
     return nested(l) ? prolong_nested_at(Ls[l], Ls[l + 1], Xs[l], i0, i1, i2) : prolong_at(Ls[l + 1], Xs[l], i0, i1, i2);

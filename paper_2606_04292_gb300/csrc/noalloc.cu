@@ -233,6 +233,11 @@ struct PlanLevels {
   __device__ double restrict(int l, const double* fine, int J0, int J1, int J2) const {
     return restrict_at(lev[l].L, lev[l].X, fine, J0, J1, J2);
   }
+  __device__ void restrict2(int l, const double* fa, const double* fb, int J0, int J1, int J2, double& a,
+                            double& b) const {
+    a = restrict(l, fa, J0, J1, J2);
+    b = restrict(l, fb, J0, J1, J2);
+  }
   __device__ double prolong(int l, int i0, int i1, int i2) const {
     return prolong_at(lev[l + 1].L, lev[l].X, i0, i1, i2);
   }
