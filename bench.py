@@ -308,7 +308,7 @@ def _serve(trace, ids, precision, batched):
 def serving_bench(nreq=24, max_steps=20, rank=0, world=1):
     """Served streams of Poisson arrivals at 200/s (three soil laws, half with a
     sink, BDF2), at most `max_steps` steps each.  Two traces: a reduced size
-    mix (2D 129^2/257^2, 3D 65^3), served by lockstep batched cycles
+    mix (2D 129^2/257^2, 3D 65^3), served by continuous batching
     (richards_batcher_step) and by per-request streams, in the FP64-outer and
     float-float mixed modes and FP64 plain; and the configured size mix (2D
     129^2-1025^2, 3D 65^3-257^3), mixed with the FP64 outer layer, batched and

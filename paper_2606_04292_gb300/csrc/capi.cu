@@ -1305,11 +1305,12 @@ richards_status step_mixed(richards_ctx* c, richards_step_info* info) {
 }  // namespace
 
 // ==========================================================================
-// Lockstep batch of mixed-precision contexts (served requests): every
-// context takes one implicit step; their outer defects, decisions and inner
-// stop tests are taken together (one synchronisation for all), and their
-// FP32 inner cycles run together, each stage of a cycle one launch over the
-// descriptors of all contexts that are at that stage (batch.cu).  The work
+// Batched steps of mixed-precision contexts (served requests), in ticks:
+// every context does the next part of its own step (batch_tick); the outer
+// defects and decisions of all contexts that are at one are taken together
+// (one synchronisation per stream), and the FP32 inner cycles of all
+// contexts in an inner solve run together, each stage of a cycle one launch
+// over the descriptors of all of them (batch.cu).  The work
 // of one context alone (preparation, outer defects, coarse copies of psi0,
 // updates, water balance) stays on the context's own stream, so that the
 // contexts' small launches overlap; events order it against the batched

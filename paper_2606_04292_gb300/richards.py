@@ -501,9 +501,10 @@ class Columns:
 
 
 class Batcher:
-    """Lockstep steps of many resident solvers (``richards_batcher_*``): one
-    call advances every listed Solver by one step, their FP32 inner cycles
-    batched into shared launches."""
+    """Batched steps of many resident solvers (``richards_batcher_*``): step()
+    advances every listed Solver by one step, advance() each by its own
+    number of steps on its own schedule (continuous batching); the FP32 inner
+    cycles of all solvers in an inner solve share launches."""
 
     def __init__(self, max_contexts=64, stream=None):
         h = C.c_void_p()

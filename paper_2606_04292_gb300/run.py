@@ -15,7 +15,7 @@ every step returned RICH_OK, 1 otherwise.
 Two batched workloads: ``columns`` (n root-uptake columns of U{64..1024}
 cells, default 4096, one ``richards_columns_run`` launch per step) and
 ``served`` (the first n requests, default 8, of the Poisson serving trace
-with 2-d 129^2-257^2 and 3-d 65^3 grids, advanced in lockstep by one
+with 2-d 129^2-257^2 and 3-d 65^3 grids, all advanced by one
 ``richards_batcher_step`` per step); ``--opt`` applies to every column or
 request, ``--psi0`` does not apply.
 """
