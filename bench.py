@@ -209,7 +209,8 @@ def roofline(prof, steps, ms_pass):
 def columns_bench(stream, steps=10, rank=0, world=1):
     """Batched root-uptake columns: 4096 columns of U{64..1024} cells, per-column
     van Genuchten soil, Feddes sink, BDF1 dt = 600 s; every column advances
-    `steps` steps in one persistent launch (block size autotuned first).
+    `steps` steps in one call: a persistent launch per length class (block
+    size autotuned first).
     Under torchrun each rank takes every world-th column (replicas.shard) and
     the ranks' summaries are merged: the slowest rank's time, summed work."""
     import numpy as np

@@ -521,9 +521,9 @@ richards_status richards_step_small_noalloc(const richards_grid *grid, const ric
 
 /* ---------------------------------------------------------------------
  * Batched soil columns: many independent 1D columns of uneven length solved
- * in one persistent launch (a device work queue, longest column first; each
- * thread block runs all time steps of one column with the column's whole
- * multigrid hierarchy in shared memory).  Mixed precision as for
+ * in persistent launches, one per length class (a device work queue per
+ * class, longest column first; each thread block runs all time steps of one
+ * column with the column's whole multigrid hierarchy in shared memory).  Mixed precision as for
  * richards_step: FP32 FAS cycles on the correction equation inside an outer
  * defect correction whose lagged K, history, defect and stop test run in
  * float-float arithmetic (laws ~1e-12 relative) with opts->precision 1, or

@@ -13,7 +13,7 @@ corrections, cell updates and wall time are printed.  Exit status is 0 when
 every step returned RICH_OK, 1 otherwise.
 
 Two batched workloads: ``columns`` (n root-uptake columns of U{64..1024}
-cells, default 4096, one ``richards_columns_run`` launch per step) and
+cells, default 4096, one ``richards_columns_run`` call per step) and
 ``served`` (the first n requests, default 8, of the Poisson serving trace
 with 2-d 129^2-257^2 and 3-d 65^3 grids, all advanced by one
 ``richards_batcher_step`` per step); ``--opt`` applies to every column or
