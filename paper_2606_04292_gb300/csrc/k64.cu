@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
                                                      const double* __restrict__ psinm1, const double* __restrict__ Ks,
                                                      double Ks_s, const double* __restrict__ p1f,
                                                      const double* __restrict__ p2f, const uint8_t* __restrict__ mat,
-                                                     Phys<double> P, int scheme, double dt, double* Kc, float* Kcf,
+                                                     Phys<double> P, int scheme, double hist_scale, double* Kc,
+                                                     float* Kcf,
                                                      double* g, double* u, const double* thn_in,
                                                      const double* thm_in, double* thn_out, double* thm_out,
                                                      bool predict) {
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
       double ps, hist;
       if (scheme == 1) {
         ps = pn;
-        hist = thn / dt;
+        hist = thn * hist_scale;
       } else {
         const double pm = psinm1[i];
         double thm;
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
           if (thm_out) thm_out[i] = thm;
         }
         ps = P.lag ? pn : 2.0 * pn - pm;
-        hist = (4.0 * thn - thm) / (2.0 * dt);
+        hist = (4.0 * thn - thm) * hist_scale;
       }
       const double K = cond_d<ML>(ps, p1, p2, ks, Q);
       Kc[i] = K;
@@ -153,13 +154,14 @@ __global__ void __launch_bounds__(256) k_prep_rhs(Geom G, BcDev bc, const double
   const int v = G.dim - 1;
   const int nn[3] = {G.n0, G.n1, G.n2};
   const long long stride[3] = {1, G.n0, (long long)G.n0 * G.n1};
+  const double ihv = 1.0 / G.h[v];    // (one FP64 division per thread, not two per cell)
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     int ii[3];
     cell_coords(G.n0, G.n1, i, ii[0], ii[1], ii[2]);
     double gi = g[i];
     const double Ki = Kc[i];
-    if (ii[v] + 1 < nn[v]) gi += 0.5 * (Ki + Kc[i + stride[v]]) / G.h[v];
-    if (ii[v] > 0) gi -= 0.5 * (Ki + Kc[i - stride[v]]) / G.h[v];
+    if (ii[v] + 1 < nn[v]) gi += 0.5 * (Ki + Kc[i + stride[v]]) * ihv;
+    if (ii[v] > 0) gi -= 0.5 * (Ki + Kc[i - stride[v]]) * ihv;
     for (int ax = 0; ax < G.dim; ++ax) {
       for (int side = 0; side < 2; ++side) {
         if (ii[ax] != (side ? nn[ax] - 1 : 0)) continue;
@@ -444,7 +446,9 @@ void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const 
   const int b = grid_for(n);
   predict = predict && scheme == 2;
   by_model(model, [&](auto m) {
-    k_prep_lagged<decltype(m)::value><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, mat, P, scheme, dt, Kc,
+    // (the history's 1/tau or 1/(2 tau) as one factor, as in the water balance)
+    const double hs = scheme == 1 ? 1.0 / dt : 1.0 / (2.0 * dt);
+    k_prep_lagged<decltype(m)::value><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, mat, P, scheme, hs, Kc,
                                                         Kcf, g, u, thn_in, thm_in, thn_out, thm_out, predict);
   });
 }
