@@ -44,6 +44,7 @@ struct HLevel {
   long long nface[6] = {0, 0, 0, 0, 0, 0};
   double *u = nullptr, *ubar = nullptr, *g = nullptr, *d = nullptr, *Kc = nullptr;
   double *p1 = nullptr, *p2 = nullptr, *smax = nullptr;
+  double* vgm = nullptr;         // finest level, van Genuchten n field: m = 1 - 1/n per cell
   double* kb[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   float *uf = nullptr, *ubarf = nullptr, *gf = nullptr, *df = nullptr, *Kcf = nullptr;
   float *p1f = nullptr, *p2f = nullptr, *smaxf = nullptr, *psi0f = nullptr;
@@ -496,6 +497,11 @@ Phys<T> phys(const richards_ctx* c) {
 // fine material index for the preparation kernels (null unless layered)
 const uint8_t* fine_mat(const richards_ctx* c) { return c->layered ? c->L[0].mat : nullptr; }
 
+// m = 1 - 1/n per cell of a van Genuchten n field (null otherwise)
+const double* fine_vgm(const richards_ctx* c) {
+  return !c->layered && c->soil.model == RICH_VANGENUCHTEN && c->het_p2 ? c->L[0].vgm : nullptr;
+}
+
 // upload the level views and transfer tables the coarse-tail kernel reads
 richards_status upload_views(richards_ctx* c) {
   std::vector<Level<double>> v64(c->nlev);
@@ -934,7 +940,7 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
                       c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, c->soil.model, scheme,
                       dt, F.Kc, F.Kcf, F.g, F.u, c->th_n_valid ? c->th_n : nullptr,
                       c->th_nm1_valid ? c->th_nm1 : nullptr, c->th_n_valid ? nullptr : c->th_n,
-                      c->th_nm1_valid ? nullptr : c->th_nm1, c->opts.predictor == 1, c->s);
+                      c->th_nm1_valid ? nullptr : c->th_nm1, c->opts.predictor == 1, c->s, fine_vgm(c));
   else if (dd)    // mixed mode: float-float arithmetic, theta caches
     rich::prep_lagged_dd(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
                          c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, rich::make_ddphys(P),
@@ -944,7 +950,7 @@ richards_status do_prepare(richards_ctx* c, double dt, int scheme) {
   else
     rich::prep_lagged(geom(c, 0), c->psi_n, c->psi_nm1, c->het_Ks ? c->Ks : nullptr, c->soil.Ks,
                       c->het_p1 ? F.p1 : nullptr, c->het_p2 ? F.p2 : nullptr, fine_mat(c), P, c->soil.model, scheme,
-                      dt, F.Kc, nullptr, F.g, F.u, nullptr, nullptr, nullptr, nullptr, false, c->s);
+                      dt, F.Kc, nullptr, F.g, F.u, nullptr, nullptr, nullptr, nullptr, false, c->s, fine_vgm(c));
   if (cache) {
     c->th_n_valid = true;
     if (scheme == 2) c->th_nm1_valid = true;
@@ -1164,7 +1170,7 @@ richards_status outer_defect_launch(richards_ctx* c, bool cached, bool fp64) {
   if (fp64) {
     Prof pr(c, "outer_residual64", 0, F.ncell);
     rich::outer_residual64(view64(c, 0), P64, c->soil.model, F.gf, F.psi0f, F.uf, c->scratch,
-                           cached ? c->th_n : nullptr, th_out, F.cs, c->s);
+                           cached ? c->th_n : nullptr, th_out, F.cs, c->s, fine_vgm(c));
   } else {
     Prof pr(c, "outer_residual", 0, F.ncell);
     rich::outer_residual_dd(view64(c, 0), P64, rich::make_ddphys(P64), c->soil.model, F.gf, F.psi0f, F.uf,
@@ -1916,6 +1922,10 @@ richards_status richards_set_soil(richards_ctx* c, const richards_soil* s) {
     }
     CK(cudaMemcpyAsync(k == 0 ? c->L[0].p1 : c->L[0].p2, fields[k], sizeof(double) * N, cudaMemcpyHostToDevice,
                        c->s));
+  }
+  if (s->model == RICH_VANGENUCHTEN && c->het_p2) {   // m per cell for the FP64 laws: no division per evaluation
+    if (!c->L[0].vgm) TRY(dalloc(c, &c->L[0].vgm, N));
+    rich::vg_m_field(c->L[0].p2, c->L[0].vgm, N, c->s);
   }
   CK(cudaStreamSynchronize(c->s));
   c->soil_set = true;

@@ -158,13 +158,23 @@ __device__ __forceinline__ void law_d(double psi, double p1, double p2, const Ph
 }
 
 template <int MODEL>
-__device__ __forceinline__ double theta_only_d(double psi, double p1, double p2, const Phys<double>& P) {
+__device__ __forceinline__ double theta_only_dm(double psi, double p1, double p2, double m, const Phys<double>& P) {
   if (!(psi < 0.0)) return P.ts;
   const double h = -psi, ds = P.ts - P.tr;
   if (MODEL == HAVERKAMP) return P.tr + p1 * ds / (p1 + fx::exp(p2 * fx::log(h)));
   if (MODEL == GARDNER) return P.tr + ds * fx::exp(p1 * psi);
-  const double n = p2, m = 1.0 - 1.0 / n;
+  const double n = p2;
   return P.tr + ds * fx::exp(-m * fx::log1p(fx::exp(n * fx::log(p1 * h))));
+}
+
+// van Genuchten's m = 1 - 1/n (kernels that evaluate the laws of a per-cell
+// n field read it from a copy made with this same expression)
+__device__ __forceinline__ double vg_m(double n) { return 1.0 - 1.0 / n; }
+
+// theta of one law; m (van Genuchten only) from n
+template <int MODEL>
+__device__ __forceinline__ double theta_only_d(double psi, double p1, double p2, const Phys<double>& P) {
+  return theta_only_dm<MODEL>(psi, p1, p2, (MODEL == VANGENUCHTEN && psi < 0.0) ? vg_m(p2) : 0.0, P);
 }
 
 // Hydraulic conductivity.  For van Genuchten-Mualem, Se^{1/m} = 1/(1+t), so
@@ -175,19 +185,24 @@ __device__ __forceinline__ double theta_only_d(double psi, double p1, double p2,
 //   log(t / (1 + t)) = min(lt, 0) - log1p(e),
 // one exponential and one log1p for both ranges, no division and no branch.
 template <int MODEL>
-__device__ __forceinline__ double cond_d(double psi, double p1, double p2, double Ks,
-                                         const Phys<double>& P) {
+__device__ __forceinline__ double cond_dm(double psi, double p1, double p2, double m, double Ks,
+                                          const Phys<double>& P) {
   if (!(psi < 0.0)) return Ks;
   const double h = -psi;
   if (MODEL == HAVERKAMP) return Ks * P.p3 / (P.p3 + fx::exp(P.p4 * fx::log(h)));
   if (MODEL == GARDNER) return Ks * fx::exp(p1 * psi);
-  const double n = p2, m = 1.0 - 1.0 / n;
+  const double n = p2;
   const double lt = n * fx::log(p1 * h);
   const double l1 = fx::log1p(fx::exp(-fabs(lt)));
   const double L1 = l1 + fmax(lt, 0.0);
   const double lr = fmin(lt, 0.0) - l1;
   const double inner = -fx::expm1(m * lr);
   return Ks * fx::exp(-P.p3 * m * L1) * inner * inner;
+}
+
+template <int MODEL>
+__device__ __forceinline__ double cond_d(double psi, double p1, double p2, double Ks, const Phys<double>& P) {
+  return cond_dm<MODEL>(psi, p1, p2, (MODEL == VANGENUCHTEN && psi < 0.0) ? vg_m(p2) : 0.0, Ks, P);
 }
 
 __device__ __forceinline__ double cond_model_d(int model, double psi, double p1, double p2,

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
                                                      float* Kcf,
                                                      double* g, double* u, const double* thn_in,
                                                      const double* thm_in, double* thn_out, double* thm_out,
-                                                     bool predict) {
+                                                     bool predict, const double* __restrict__ mf) {
   // thn_in / thm_in: theta(psi^n), theta(psi^{n-1}) kept from earlier FP64
   // evaluations (nullable: evaluate here, and keep them in *_out if given).
   // Kcf (nullable): an FP32 copy of Kc for the inner cycles of the mixed
@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
         ps = P.lag ? pn : 2.0 * pn - pm;
         hist = (4.0 * thn - thm) * hist_scale;
       }
-      const double K = cond_d<ML>(ps, p1, p2, ks, Q);
+      const double K = (ML == VANGENUCHTEN && mf) ? cond_dm<ML>(ps, p1, p2, mf[i], ks, Q)
+                                                  : cond_d<ML>(ps, p1, p2, ks, Q);
       Kc[i] = K;
       if (Kcf) Kcf[i] = (float)K;
       g[i] = hist + P.xi * ps;
@@ -383,7 +384,8 @@ __global__ void __launch_bounds__(128) k_outer_residual_dd(Level<double> L, Phys
 template <int MODEL>
 __global__ void __launch_bounds__(256) k_outer_residual64(Level<double> L, Phys<double> P, float* r32, float* psi0f,
                                                           float* delta, unsigned long long* norm,
-                                                          const double* __restrict__ th_in, double* th_out, int cs) {
+                                                          const double* __restrict__ th_in, double* th_out, int cs,
+                                                          const double* __restrict__ mf) {
   __shared__ unsigned long long sm[33];
   unsigned long long mx = 0;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -416,7 +418,9 @@ __global__ void __launch_bounds__(256) k_outer_residual64(Level<double> L, Phys<
     } else {
       const double p1 = L.p1 ? L.p1[i] : P.p1, p2 = L.p2 ? L.p2[i] : P.p2;
       th = with_law<MODEL>(P, mat_of<MODEL>(L, i), [&](auto law, const Phys<double>& Q) {
-        return theta_only_d<decltype(law)::value>(ui, p1, p2, Q);
+        constexpr int ML = decltype(law)::value;
+        return (ML == VANGENUCHTEN && mf) ? theta_only_dm<ML>(ui, p1, p2, mf[i], Q)
+                                          : theta_only_d<ML>(ui, p1, p2, Q);
       });
       if (th_out) th_out[i] = th;
     }
@@ -441,7 +445,8 @@ __global__ void __launch_bounds__(256) k_apply_delta(double* u, const float* del
 void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
                  const double* p1, const double* p2, const uint8_t* mat, const Phys<double>& P, int model, int scheme,
                  double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
-                 const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s) {
+                 const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s,
+                 const double* vgm) {
   const long long n = (long long)G.n0 * G.n1 * G.n2;
   const int b = grid_for(n);
   predict = predict && scheme == 2;
@@ -449,7 +454,8 @@ void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const 
     // (the history's 1/tau or 1/(2 tau) as one factor, as in the water balance)
     const double hs = scheme == 1 ? 1.0 / dt : 1.0 / (2.0 * dt);
     k_prep_lagged<decltype(m)::value><<<b, 256, 0, s>>>(n, psin, psinm1, Ks, Ks_s, p1, p2, mat, P, scheme, hs, Kc,
-                                                        Kcf, g, u, thn_in, thm_in, thn_out, thm_out, predict);
+                                                        Kcf, g, u, thn_in, thm_in, thn_out, thm_out, predict,
+                                                        decltype(m)::value == VANGENUCHTEN ? vgm : nullptr);
   });
 }
 
@@ -537,12 +543,23 @@ void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPh
 
 void outer_residual64(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
                       float* delta, unsigned long long* norm, const double* th_in, double* th_out, int cs,
-                      cudaStream_t s) {
+                      cudaStream_t s, const double* vgm) {
   const Launch3 g = launch3(L.n0, L.n1, L.n2);
   by_model(model, [&](auto m) {
     k_outer_residual64<decltype(m)::value><<<g.grid, g.block, 0, s>>>(L, P, r32, psi0f, delta, norm, th_in, th_out,
-                                                                      cs);
+                                                                      cs, decltype(m)::value == VANGENUCHTEN ? vgm
+                                                                                                           : nullptr);
   });
+}
+
+// m = 1 - 1/n of a van Genuchten n field (vg_m, the laws' own expression)
+__global__ void __launch_bounds__(256) k_vg_m(const double* __restrict__ n, double* m, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    m[i] = vg_m(n[i]);
+}
+
+void vg_m_field(const double* n, double* m, long long count, cudaStream_t s) {
+  k_vg_m<<<grid_for(count), 256, 0, s>>>(n, m, count);
 }
 
 __global__ void __launch_bounds__(256) k_to_float_level(const double* __restrict__ src, float* dst, int n0, int n1,

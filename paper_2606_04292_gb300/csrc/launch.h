@@ -78,7 +78,8 @@ void residual_color32(const Level<float>& L, const Phys<float>& P, int model, in
 void prep_lagged(const Geom& G, const double* psin, const double* psinm1, const double* Ks, double Ks_s,
                  const double* p1, const double* p2, const uint8_t* mat, const Phys<double>& P, int model, int scheme,
                  double dt, double* Kc, float* Kcf, double* g, double* u, const double* thn_in,
-                 const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s);
+                 const double* thm_in, double* thn_out, double* thm_out, bool predict, cudaStream_t s,
+                 const double* vgm = nullptr);
 void prep_rhs(const Geom& G, const BcDev& bc, const double* Ks, double Ks_s, const double* p1, const double* p2,
               const uint8_t* mat, const Phys<double>& P, int model, const double* Kc, double* g, double* const kb[6],
               cudaStream_t s);
@@ -102,7 +103,10 @@ void outer_residual_dd(const Level<double>& L, const Phys<double>& P, const DDPh
 // delta = 0; ||r||_inf as FP64 bits; theta caches as outer_residual_dd.
 void outer_residual64(const Level<double>& L, const Phys<double>& P, int model, float* r32, float* psi0f,
                       float* delta, unsigned long long* norm, const double* th_in, double* th_out, int cs,
-                      cudaStream_t s);
+                      cudaStream_t s, const double* vgm = nullptr);
+// (vgm, nullable: m = 1 - 1/n of the finest level's van Genuchten n field,
+// read instead of divided per cell; vg_m_field makes it)
+void vg_m_field(const double* n, double* m, long long count, cudaStream_t s);
 // FP32 copy of a level-0 parameter array in the FP32 level's layout (cs: colour-split)
 void to_float_level(const double* src, float* dst, int n0, int n1, int n2, int cs, cudaStream_t s);
 // natural-layout copy of a colour-split array (the defect at delta = 0 is g)
