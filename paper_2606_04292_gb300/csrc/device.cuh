@@ -333,6 +333,7 @@ struct DBase {
   float psi0, inv_psi0;
   bool wet0;
   float a0, b0, c0;      // VG: t0, log1p(t0), Se0; Haverkamp: u0, log(u0); Gardner: e0
+  float m;               // VG: 1 - 1/n
 };
 
 // Largest exponent a power t = (alpha h)^n or u = h^beta of a trial state may
@@ -350,6 +351,7 @@ __device__ __forceinline__ DBase dbase(float psi0, float p1, float p2) {
   B.wet0 = !(psi0 < 0.0f);
   B.inv_psi0 = B.wet0 ? 0.0f : __fdividef(1.0f, psi0);
   B.a0 = B.b0 = B.c0 = 0.0f;
+  B.m = MODEL == VANGENUCHTEN ? 1.0f - __fdividef(1.0f, p2) : 0.0f;
   if (!B.wet0) {
     if (MODEL == GARDNER) {
       B.a0 = __expf(p1 * psi0);
@@ -358,7 +360,7 @@ __device__ __forceinline__ DBase dbase(float psi0, float p1, float p2) {
       B.a0 = __expf(lu);
       B.b0 = lu;
     } else {
-      const float m = 1.0f - __fdividef(1.0f, p2);
+      const float m = B.m;
       B.a0 = __expf(fminf(p2 * __logf(p1 * -psi0), POW_EXP_MAX));   // (alpha h0)^n
       B.b0 = fast_log1p(B.a0);
       B.c0 = __expf(-m * B.b0);
@@ -418,7 +420,7 @@ __device__ __forceinline__ void dincr(const DBase& B, float x, float p1, float p
       Dth = 0.0f; dth = 0.0f;
     }
   } else {
-    const float al = p1, n = p2, m = 1.0f - __fdividef(1.0f, n);
+    const float al = p1, n = p2, m = B.m;
     if (!B.wet0) {
       const float t0 = B.a0, L0 = B.b0, Se0 = B.c0;
       if (!wet1) {
@@ -653,7 +655,7 @@ __device__ __forceinline__ T point_solve(T cc, T f, T x0, T psi0, T p1, T p2, T 
     }
     const T stp = fabs(xn - x);
     x = xn;
-    if (P.newton_k <= 0 && stp <= tiny) return true;
+    if (NK == 0 && P.newton_k <= 0 && stp <= tiny) return true;
     // FP32 increment form: a step below 2^-20 of |x| leaves nothing for the
     // next one to change at this precision (quadratic convergence)
     if constexpr (FORM == FORM_DELTA) {
