@@ -54,7 +54,7 @@ TRAFFIC_PER_LAUNCH = {("sweep32", 8388608): 318.5e6}
 # What binds that launch instead of DRAM, from the same capture: the share of
 # issue slots active (smsp__issue_active) and of DRAM bandwidth in use.
 BINDING_PER_LAUNCH = {("sweep32", 8388608): {"limit": "instruction issue", "issue_active": 0.81,
-                                             "dram_throughput": 0.43, "thread_instructions_per_update": 343,
+                                             "dram_throughput": 0.42, "thread_instructions_per_update": 345,
                                              "source": "ncu --set full (profiles/sweep32_drainage256_mixed.md)"}}
 
 BYTES_PER_CELL = {
