@@ -4,7 +4,7 @@ The FP64 laws (Table 1) take their powers and exponentials through the
 library's table-driven exp, expm1, log and log1p.  Each must stay within a few
 ulps of CUDA's own function (itself within ~1 ulp of the correctly rounded
 value) over the ranges the laws reach and across the edges of its reduction
-(the table steps, the series thresholds at 1/128, 1 for log, ln2/128 for exp),
+(the table steps, the series thresholds at 1/128, 1 for log, ln2/512 for exp),
 and hand the rest to CUDA's function unchanged.
 """
 import ctypes as C
@@ -40,18 +40,19 @@ def _ulp_err(got, want):
 def _inputs(rng, fn):
     u = lambda a, b, n=20000: rng.uniform(a, b, n)
     if fn in (0, 1):                                   # exp, expm1
-        edges = np.concatenate([k * np.log(2) / 64 + np.array([-1e-15, 0.0, 1e-15]) for k in range(-300, 300)])
+        edges = np.concatenate([k * np.log(2) / 256 + np.array([-1e-15, 0.0, 1e-15]) for k in range(-1200, 1200)])
         xs = [u(-700, 700), u(-30, 30), u(-1, 1), u(-0.01, 0.01), u(-1e-4, 1e-4),
-              np.log(2) / 128 * np.array([-1.0001, -0.9999, 0.9999, 1.0001]), 0.0078125 * np.array([-1.001, -0.999,
+              np.log(2) / 512 * np.array([-1.0001, -0.9999, 0.9999, 1.0001]), 0.0078125 * np.array([-1.001, -0.999,
                                                                                                     0.999, 1.001]),
               edges, -np.logspace(-300, 2.8, 2000), np.logspace(-300, 2.8, 2000)]
     elif fn == 2:                                      # log
         xs = [np.exp(u(-700, 700)), u(0.9, 1.1), u(0.99, 1.01), u(1e-3, 1e4), 2.0 ** np.arange(-1000, 1000),
               1 + np.array([-0.0078125, -0.0078124, 0.0078124, 0.0078125, 0.0078126]),
-              1 + np.arange(256) / 128.0, (1 + np.arange(256) / 128.0) * 0.5]
+              1 + np.arange(512) / 256.0, (1 + np.arange(512) / 256.0) * 0.5,
+              np.nextafter(1 + np.arange(1, 512) / 256.0, 0.0)]
     else:                                              # log1p
         xs = [u(0, 1), u(0, 1e-2), u(0, 1e-6), np.exp(u(-700, 40)), np.logspace(-300, 300, 4000),
-              np.array([0.0078124, 0.0078125, 0.0078126]), np.arange(256) / 128.0, u(-0.0078, 0.0078)]
+              np.array([0.0078124, 0.0078125, 0.0078126]), np.arange(512) / 256.0, u(-0.0078, 0.0078), u(1, 1000)]
     return np.concatenate(xs)
 
 
@@ -68,7 +69,14 @@ def test_table_driven_functions_within_a_few_ulps_of_cuda(fn, name):
 
 
 def test_outside_the_law_ranges_cuda_decides():
-    x = np.array([-800.0, 710.0, 1e-310, 0.0, -1.0, np.inf, np.nan])
-    for fn in range(4):
+    """Arguments outside the ranges each function serves itself go to CUDA's
+    function: |x| > 700 for exp and expm1; x <= 0, subnormal, infinite or NaN
+    for log; s < -1/128, infinite or NaN for log1p."""
+    outside = {0: [-800.0, 710.0, np.inf, -np.inf, np.nan],
+               1: [-800.0, 710.0, np.inf, -np.inf, np.nan],
+               2: [1e-310, 0.0, -1.0, np.inf, np.nan],
+               3: [-800.0, -1.0, -0.5, -0.0079, np.inf, np.nan]}
+    for fn, xs in outside.items():
+        x = np.array(xs)
         got, want = _eval(fn, x), _eval(fn + 4, x)
-        assert np.array_equal(got, want, equal_nan=True), fn
+        assert np.array_equal(got, want, equal_nan=True), (fn, got, want)
