@@ -145,6 +145,7 @@ struct richards_ctx {
     cudaGraphExec_t exec = nullptr;
     double a = 0.0;
     long long updates = 0;             // NGS updates of one cycle
+    std::vector<ProfRec> recs;         // the launches of one pass of the loop's body (counted, not timed)
   };
   LoopRec loops[3];
   bool loop_ok = true;
@@ -824,6 +825,11 @@ bool build_inner_loop(richards_ctx* c, richards_ctx::LoopRec& G) {
     e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
   }
   const long long before = c->updates_host;
+  // the body's launches are listed as a count-only profile would list them
+  // (that profile adds no nodes), for richards_profile's counts
+  const int prof_saved = c->prof;
+  c->prof = 3;
+  c->capture_recs.clear();
   if (e == cudaSuccess) {
     cudaGraph_t body = np.conditional.phGraph_out[0];
     where = "cudaStreamBeginCaptureToGraph";
@@ -834,9 +840,13 @@ bool build_inner_loop(richards_ctx* c, richards_ctx::LoopRec& G) {
       G.updates = c->updates_host - before;
       if (test && !fuse) {
         cudaMemsetAsync(c->scratch + 1, 0, sizeof(unsigned long long), c->s);
+        Prof pr(c, "residual32", 0, c->L[0].ncell);
         rich::residual32(view32(c, 0), phys<float>(c), c->soil.model, c->scratch + 1, c->s, c->tune_rbx[0]);
       }
-      k_inner_loop_cond<<<1, 1, 0, c->s>>>(h, c->scratch + 1, c->scratch + LOOP_SLOT);
+      {
+        Prof pr(c, "inner_loop_cond", 0, 1);
+        k_inner_loop_cond<<<1, 1, 0, c->s>>>(h, c->scratch + 1, c->scratch + LOOP_SLOT);
+      }
       c->capturing = false;
       const cudaError_t el = cudaGetLastError();
       cudaGraph_t out = nullptr;
@@ -846,6 +856,9 @@ bool build_inner_loop(richards_ctx* c, richards_ctx::LoopRec& G) {
     }
   }
   c->updates_host = before;
+  c->prof = prof_saved;
+  G.recs.swap(c->capture_recs);
+  c->capture_recs.clear();
   if (e == cudaSuccess) {
     where = "cudaGraphInstantiate";
     e = cudaGraphInstantiate(&G.exec, g, 0);
@@ -865,7 +878,8 @@ bool build_inner_loop(richards_ctx* c, richards_ctx::LoopRec& G) {
 // whether the inner solve runs as the loop graph (graphs on, no timing, no
 // cooperative levels, a stream of the context's own)
 bool inner_loop_usable(const richards_ctx* c) {
-  return c->opts.graphs && c->graphs_ok && c->loop_ok && c->s != nullptr && c->prof == 0 && !c->capturing &&
+  return c->opts.graphs && c->graphs_ok && c->loop_ok && c->s != nullptr && (c->prof == 0 || c->prof == 3) &&
+         !c->capturing &&
          c->coop_start >= c->nlev && c->opts.inner_cycles >= 1;
 }
 
@@ -891,6 +905,9 @@ richards_status run_inner_loop(richards_ctx* c, double target, int* cycles) {
   CK(cudaStreamSynchronize(c->s));
   *cycles = (int)c->hscratch[LOOP_SLOT + 4];
   c->updates_host += (long long)*cycles * G.updates;
+  if (c->prof == 3)                     // counted launches: the body's, once per pass
+    for (int k = 0; k < *cycles; ++k)
+      for (const auto& r : G.recs) prof_count(c, r.name, r.level, r.cells);
   return RICH_OK;
 }
 
