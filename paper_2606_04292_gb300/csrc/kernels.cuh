@@ -441,6 +441,23 @@ k_prolong_tiled(Level<T> F, Level<T> C, Xfer<T> X) {
   T wx[2], wy[2];
   prolong_taps<T>(X, 0, i0, F.n0, jx, wx);
   prolong_taps<T>(X, 1, i1, F.n1, jy, wy);
+  // the x-y interpolation of each staged coarse plane, once for the PZ fine
+  // cells of the column that share it (the sums of prolong_nested_at)
+  T py[CZ];
+#pragma unroll
+  for (int p = 0; p < CZ; ++p) {
+    T sy = T(0);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (wy[b] == T(0)) continue;
+      const T* row = &se[p][jy[b] - cy0][0];
+      T sx = T(0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) sx += wx[a] * row[jx[a] - cx0];
+      sy += wy[b] * sx;
+    }
+    py[p] = sy;
+  }
   for (int k = 0; k < PZ; ++k) {
     const int i2 = z0 + k;
     if (i2 >= F.n2) break;
@@ -451,17 +468,7 @@ k_prolong_tiled(Level<T> F, Level<T> C, Xfer<T> X) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       if (wz[c] == T(0)) continue;
-      T sy = T(0);
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        if (wy[b] == T(0)) continue;
-        const T* row = &se[jz[c] - cz0][jy[b] - cy0][0];
-        T sx = T(0);
-#pragma unroll
-        for (int a = 0; a < 2; ++a) sx += wx[a] * row[jx[a] - cx0];
-        sy += wy[b] * sx;
-      }
-      s += wz[c] * sy;
+      s += wz[c] * py[jz[c] - cz0];
     }
     const unsigned i = (unsigned)(i0 + F.n0 * (i1 + F.n1 * i2));
     F.u[i] += s;
