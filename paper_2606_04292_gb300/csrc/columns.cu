@@ -69,7 +69,12 @@ __device__ __forceinline__ void interp_row_f(int nf, int nc, int i, float slo, f
   };
   if (nf == 1) { add(0, 1.0f); return; }
   const int num = (2 * i + 1) * nc - nf, den = 2 * nf;
-  const int J0 = num >= 0 ? num / den : -((-num + den - 1) / den);
+  // floor(num / den) through the FP32 quotient, then corrected: |num| and den
+  // are below 2^24 (exact in FP32) and the quotient's floor is off by at most
+  // one, so one test each way gives the exact integer floor
+  int J0 = (int)floorf(__fdividef((float)num, (float)den));
+  if (J0 * den > num) --J0;
+  else if ((J0 + 1) * den <= num) ++J0;
   const float wt = (float)(num - J0 * den) / (float)den;
   const int J1 = J0 + 1;
   if (J0 < 0) add(0, (1.0f - wt) * slo); else add(J0, 1.0f - wt);
