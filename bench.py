@@ -798,19 +798,20 @@ def main():
         ge.autotune()
         barrier()
         ke = max(1, min(args.steps, 5))
-        upd = 0
+        upd = cyc = 0
         t0 = time.perf_counter()
         for _ in range(ke):
             ge.set_state(host_psi, host_prev)
             st, info = ge.step(check=False)
             upd += info["cell_updates"]
+            cyc += info["cycles"]
             lib = R.lib()
             R._check(lib.richards_get_state(ge.h, R._dp(host_out), 0), ge.h)
             host_prev, host_psi, host_out = host_psi, host_out, host_prev
         barrier()
         te = time.perf_counter() - t0
         e2e = {"value": upd / te * world, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N,
-               "steps": ke, "time_steps_per_s": ke / te}
+               "steps": ke, "time_steps_per_s": ke / te, "v_cycles_per_step": cyc / ke}
         ge.close()
 
     # the other outer layer on the same workload: float-float beside an FP64

@@ -2181,24 +2181,33 @@ richards_status richards_set_state(richards_ctx* c, const double* psi, const dou
   if (!std::isfinite(t)) return fail(c, RICH_EINVAL, "non-finite time");
   // the values are staged in two finest-level work arrays (FAS restricted
   // iterate and defect, rewritten by every step) and checked there on the
-  // device, so that a rejected state leaves the context as it was
+  // device, so that a rejected state leaves the context as it was.  The same
+  // pass compares them with the context's own psi^n and psi^{n-1} where those
+  // have a theta cache: a state handed back bit for bit keeps its cache
+  // (flag bit 1: psi^n changed, bit 2: psi^{n-1} changed)
   HLevel& F = c->L[0];
+  const bool cmp_n = c->have_state && c->th_n_valid;
+  const bool cmp_nm1 = psi_prev && c->have_state && c->have_prev && c->th_nm1_valid;
   CK(cudaMemcpyAsync(F.ubar, psi, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
   if (psi_prev) CK(cudaMemcpyAsync(F.d, psi_prev, sizeof(double) * N, cudaMemcpyHostToDevice, c->s));
-  unsigned* bad = (unsigned*)(c->scratch + 17);
-  CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), c->s));
-  rich::flag_nonfinite(F.ubar, N, bad, c->s);
-  if (psi_prev) rich::flag_nonfinite(F.d, N, bad, c->s);
+  unsigned* flags = (unsigned*)(c->scratch + 17);
+  CK(cudaMemsetAsync(flags, 0, sizeof(unsigned), c->s));
+  rich::screen_state(F.ubar, cmp_n ? c->psi_n : nullptr, N, 2u, flags, c->s);
+  if (psi_prev) rich::screen_state(F.d, cmp_nm1 ? c->psi_nm1 : nullptr, N, 4u, flags, c->s);
   TRY(check_launch(c));
   CK(cudaMemcpyAsync(c->hscratch + 17, c->scratch + 17, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
-  if ((unsigned)c->hscratch[17] != 0u) return fail(c, RICH_EINVAL, "non-finite state");
-  CK(cudaMemcpyAsync(c->psi_n, F.ubar, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->s));
-  if (psi_prev) CK(cudaMemcpyAsync(c->psi_nm1, F.d, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->s));
+  const unsigned fl = (unsigned)c->hscratch[17];
+  if (fl & 1u) return fail(c, RICH_EINVAL, "non-finite state");
+  const bool same_n = cmp_n && !(fl & 2u), same_nm1 = cmp_nm1 && !(fl & 4u);
+  if (!same_n) CK(cudaMemcpyAsync(c->psi_n, F.ubar, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->s));
+  if (psi_prev && !same_nm1)
+    CK(cudaMemcpyAsync(c->psi_nm1, F.d, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->s));
   CK(cudaStreamSynchronize(c->s));
   c->have_state = true;
   c->have_prev = psi_prev != nullptr;
-  c->th_n_valid = c->th_nm1_valid = false;
+  c->th_n_valid = same_n;
+  c->th_nm1_valid = same_nm1;
   c->t = t;
   return RICH_OK;
 }

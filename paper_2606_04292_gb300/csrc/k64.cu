@@ -52,11 +52,16 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
     const double pn = psin[i];
     with_law<MODEL>(P, mat_at<MODEL>(mat, i), [&](auto law, const Phys<double>& Q) {
       constexpr int ML = decltype(law)::value;
+      // (the expression of the defect kernel's theta, so that a cache filled
+      // here and one filled there hold the same bits for the same state)
+      auto theta_at = [&](double x) {
+        return (ML == VANGENUCHTEN && mf) ? theta_only_dm<ML>(x, p1, p2, mf[i], Q) : theta_only_d<ML>(x, p1, p2, Q);
+      };
       double thn;
       if (thn_in) {
         thn = thn_in[i];
       } else {
-        thn = theta_only_d<ML>(pn, p1, p2, Q);
+        thn = theta_at(pn);
         if (thn_out) thn_out[i] = thn;
       }
       double ps, hist;
@@ -69,7 +74,7 @@ __global__ void __launch_bounds__(256) k_prep_lagged(long long n, const double* 
         if (thm_in) {
           thm = thm_in[i];
         } else {
-          thm = theta_only_d<ML>(pm, p1, p2, Q);
+          thm = theta_at(pm);
           if (thm_out) thm_out[i] = thm;
         }
         ps = P.lag ? pn : 2.0 * pn - pm;
@@ -874,19 +879,28 @@ int mass_balance(const Level<double>& L, const Geom& G, const BcDev& bc, const P
   return b;
 }
 
-// *bad = 1 if any of x[0..n) is not finite (the exponent field all ones:
-// integer test, so no FP64 instruction)
-__global__ void __launch_bounds__(256) k_nonfinite(const double* __restrict__ x, long long n, unsigned* bad) {
-  bool any = false;
+// *flags |= 1 if any of x[0..n) is not finite (the exponent field all ones:
+// integer test, so no FP64 instruction); with ref, *flags |= changed_bit if
+// any x[i] differs from ref[i] in its bits (-0 and +0 differ)
+__global__ void __launch_bounds__(256) k_screen(const double* __restrict__ x, const double* __restrict__ ref,
+                                                long long n, unsigned changed_bit, unsigned* flags) {
+  bool nf = false, ch = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x[i]);
-    any |= ((b >> 52) & 0x7ffull) == 0x7ffull;
+    nf |= ((b >> 52) & 0x7ffull) == 0x7ffull;
+    if (ref) ch |= b != (unsigned long long)__double_as_longlong(ref[i]);
   }
-  if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+  const unsigned v = __reduce_or_sync(0xffffffffu, (nf ? 1u : 0u) | (ch ? changed_bit : 0u));
+  if (v && (threadIdx.x & 31) == 0) atomicOr(flags, v);
 }
 
 void flag_nonfinite(const double* x, long long n, unsigned* bad, cudaStream_t s) {
-  k_nonfinite<<<grid_for(n), 256, 0, s>>>(x, n, bad);
+  k_screen<<<grid_for(n), 256, 0, s>>>(x, nullptr, n, 0u, bad);
+}
+
+void screen_state(const double* x, const double* ref, long long n, unsigned changed_bit, unsigned* flags,
+                  cudaStream_t s) {
+  k_screen<<<grid_for(n), 256, 0, s>>>(x, ref, n, changed_bit, flags);
 }
 
 void apply_delta(double* u, const float* delta, long long n, cudaStream_t s) {

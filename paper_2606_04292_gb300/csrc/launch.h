@@ -133,6 +133,10 @@ void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);
 void math_eval(int fn, const double* x, double* y, long long n, cudaStream_t s);
 // sets *bad to 1 if any of x[0..n) is NaN or infinite (device arrays)
 void flag_nonfinite(const double* x, long long n, unsigned* bad, cudaStream_t s);
+// *flags |= 1 if any of x[0..n) is NaN or infinite, and, with ref non-null,
+// *flags |= changed_bit if any x[i] differs from ref[i] bit for bit
+void screen_state(const double* x, const double* ref, long long n, unsigned changed_bit, unsigned* flags,
+                  cudaStream_t s);
 // theta(psi) and K(psi) per cell (FP64 or float-float); outputs nullable
 void soil_eval(long long n, const double* psi, const double* Ks, double Ks_s, const double* p1, const double* p2,
                const uint8_t* mat, const Phys<double>& P, const DDPhys& Q, int model, bool dd, double* theta,

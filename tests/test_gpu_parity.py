@@ -724,6 +724,58 @@ def test_rejected_state_leaves_the_context_unchanged():
     assert st == R.RICH_OK
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("model", [W.VANGENUCHTEN, W.HAVERKAMP, W.GARDNER])
+def test_state_handed_back_steps_like_the_resident_one(precision, model):
+    """A caller that reads every step's result back and hands it in again
+    (psi^n the result, psi^{n-1} the state it stepped from) advances bit for
+    bit like a context that keeps its state on the device: a state equal to
+    the context's own keeps that state's cached theta, which is what the
+    resident context steps with."""
+    prob = W.random_problem(3, (19, 14, 11), model, 31, hetero=True, sink=True, scheme=2, precision=precision)
+    a, b = R.Solver(prob), R.Solver(prob)
+    psi, prev = b.state(), None
+    for k in range(4):
+        sa, ia = a.step(check=False)
+        if k:
+            b.set_state(psi, prev)
+        sb, ib = b.step(check=False)
+        assert sa == sb == R.RICH_OK, (k, ia, ib)
+        assert (ia["cycles"], ia["outer_iters"]) == (ib["cycles"], ib["outer_iters"]), k
+        prev, psi = psi, b.state()
+        assert np.array_equal(a.state(), psi), k
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("which", ["psi", "prev"])
+def test_changed_state_does_not_reuse_the_theta_cache(which):
+    """A state that differs from the context's own in one cell of psi^n (or
+    of psi^{n-1}) takes theta afresh there: the BDF2 step equals that of a
+    new context given the same state.  (A stale cache would move the
+    history term of that cell by theta' x 0.05 m, ~1e-3, far above the
+    1e-12 allowed.)"""
+    prob = W.random_problem(3, (19, 14, 11), W.VANGENUCHTEN, 32, hetero=True, scheme=2, precision=2)
+    b = R.Solver(prob)
+    psi0 = b.state()
+    st, info = b.step()                      # b: psi^n = X, psi^{n-1} = psi0, both cached
+    X, Y = b.state(), psi0.copy()
+    k = X.size // 2 + 7
+    if which == "psi":
+        X[k] -= 0.05
+    else:
+        Y[k] -= 0.05
+    b.set_state(X, Y)
+    c = R.Solver(prob)
+    c.set_state(X, Y)
+    sb, ib = b.step(check=False)
+    sc, ic = c.step(check=False)
+    assert sb == sc == R.RICH_OK
+    assert rel(b.state(), c.state()) <= 1e-12
+    b.close()
+    c.close()
+
+
 def test_pipelined_half_sweeps_equal_one_cell_per_thread():
     """Levels of >= 2^20 cells take the pipelined half-sweep (sweep_planes
     cells along z per thread, blocks away from the y/z boundaries without
