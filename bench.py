@@ -811,7 +811,9 @@ def main():
         barrier()
         te = time.perf_counter() - t0
         e2e = {"value": upd / te * world, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N,
-               "steps": ke, "time_steps_per_s": ke / te, "v_cycles_per_step": cyc / ke}
+               "steps": ke, "time_steps_per_s": ke / te, "v_cycles_per_step": cyc / ke,
+               "note": "each step hands psi^n (the last result) and psi^{n-1} in from pinned host memory and reads "
+                       "psi back; a state equal bit for bit to the context's own keeps its FP64 theta cache"}
         ge.close()
 
     # the other outer layer on the same workload: float-float beside an FP64
