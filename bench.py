@@ -306,6 +306,9 @@ def _serve(trace, ids, precision, batched):
             "p99_latency_s": m["p99_latency_s"]}
 
 
+SERVING_RATES = (25.0, 50.0, 100.0, 200.0)   # offered loads of the rate sweep, requests/s
+
+
 def serving_bench(nreq=24, max_steps=20, rank=0, world=1):
     """Served streams of Poisson arrivals at 200/s (three soil laws, half with a
     sink, BDF2), at most `max_steps` steps each.  Two traces: a reduced size
@@ -313,7 +316,8 @@ def serving_bench(nreq=24, max_steps=20, rank=0, world=1):
     (richards_batcher_step) and by per-request streams, in the FP64-outer and
     float-float mixed modes and FP64 plain; and the configured size mix (2D
     129^2-1025^2, 3D 65^3-257^3), mixed with the FP64 outer layer, batched and
-    per-stream.  Offered load is the arrival rate; served load the solve rate.
+    per-stream.  Offered load is the arrival rate; served load the solve rate;
+    the reduced mix is also served at 25, 50, 100 and 200 requests/s.
     Under torchrun each rank serves every world-th request (replicas.shard);
     completions and latencies are merged over the ranks."""
     from paper_2606_04292_gb300 import replicas
@@ -332,6 +336,15 @@ def serving_bench(nreq=24, max_steps=20, rank=0, world=1):
                                       f"<= {max_steps} BDF2 steps"}
     for label, (prec, batched) in SERVING_MODES.items():
         out["reduced_mix"][label] = _serve(red, ids, prec, batched)
+    # offered against served load: the same requests at lower Poisson rates
+    # (an exponential gap drawn at 200/s, times 200/r, is one drawn at r/s),
+    # continuous batching with the FP64 outer layer
+    sweep = []
+    for rate in SERVING_RATES:
+        r = _serve([dict(p, arrival=p["arrival"] * 200.0 / rate) for p in red], ids, 2, True)
+        sweep.append({"offered_requests_per_s": rate, "served_solves_per_s": r["solves_per_s"],
+                      "p50_latency_s": r["p50_latency_s"], "p99_latency_s": r["p99_latency_s"]})
+    out["reduced_mix"]["rate_sweep_batched_mixed_fp64_outer"] = sweep
     full = trace_of((129, 257, 513, 1025), (65, 129, 257))
     ids = replicas.shard(range(len(full)), rank, world)
     out["configured_mix"] = {
