@@ -33,3 +33,29 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_serving_rate_sweep_stretches_the_same_requests(monkeypatch):
+    """The offered-load sweep serves the reduced trace's own requests, their
+    Poisson arrival times scaled by 200/r (exponential gaps at rate 200/s
+    become gaps at rate r/s), once per rate, with the FP64 outer layer and
+    continuous batching; no GPU call is made (the server is a stand-in)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    seen = []
+
+    def fake_serve(trace, ids, precision, batched):
+        seen.append(([p["name"] for p in trace], [p["arrival"] for p in trace], precision, batched))
+        return {"completed": len(ids), "makespan_s": 1.0, "solves_per_s": float(len(ids)),
+                "cell_updates_per_s": 1.0, "p50_latency_s": 0.1, "p99_latency_s": 0.2}
+
+    monkeypatch.setattr(bench, "_serve", fake_serve)
+    out = bench.serving_bench(nreq=12, max_steps=3)
+    sweep = out["reduced_mix"]["rate_sweep_batched_mixed_fp64_outer"]
+    assert [s["offered_requests_per_s"] for s in sweep] == list(bench.SERVING_RATES)
+    base_names, base_arrivals = seen[0][0], seen[0][1]
+    runs = seen[len(bench.SERVING_MODES):len(bench.SERVING_MODES) + len(bench.SERVING_RATES)]
+    for rate, (names, arrivals, precision, batched) in zip(bench.SERVING_RATES, runs):
+        assert names == base_names and precision == 2 and batched
+        for a, b in zip(arrivals, base_arrivals):
+            assert abs(a - b * 200.0 / rate) <= 1e-12 * max(1.0, a)
