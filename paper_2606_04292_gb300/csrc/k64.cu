@@ -894,10 +894,6 @@ __global__ void __launch_bounds__(256) k_screen(const double* __restrict__ x, co
   if (v && (threadIdx.x & 31) == 0) atomicOr(flags, v);
 }
 
-void flag_nonfinite(const double* x, long long n, unsigned* bad, cudaStream_t s) {
-  k_screen<<<grid_for(n), 256, 0, s>>>(x, nullptr, n, 0u, bad);
-}
-
 void screen_state(const double* x, const double* ref, long long n, unsigned changed_bit, unsigned* flags,
                   cudaStream_t s) {
   k_screen<<<grid_for(n), 256, 0, s>>>(x, ref, n, changed_bit, flags);

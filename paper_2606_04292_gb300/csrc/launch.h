@@ -131,8 +131,6 @@ void apply_delta(double* u, const float* delta, long long n, cudaStream_t s);
 // y = f(x) elementwise for the laws' FP64 elementary functions (fn 0..3:
 // exp, expm1, log, log1p) or CUDA's (fn 4..7), device arrays
 void math_eval(int fn, const double* x, double* y, long long n, cudaStream_t s);
-// sets *bad to 1 if any of x[0..n) is NaN or infinite (device arrays)
-void flag_nonfinite(const double* x, long long n, unsigned* bad, cudaStream_t s);
 // *flags |= 1 if any of x[0..n) is NaN or infinite, and, with ref non-null,
 // *flags |= changed_bit if any x[i] differs from ref[i] bit for bit
 void screen_state(const double* x, const double* ref, long long n, unsigned changed_bit, unsigned* flags,
