@@ -238,10 +238,12 @@ richards_status richards_set_sink(richards_ctx *ctx, const richards_sink *sink);
 /* State psi^n (host array, ncell doubles) and, for BDF2, psi^{n-1}
    (nullable: the next BDF2 step then falls back to BDF1).  t: model time.
    EINVAL on a non-finite value (the context is then left as it was).  In
-   the mixed modes a value equal bit for bit to the context's current psi^n
-   (psi^{n-1}) keeps the cached theta of that state -- the state a caller
-   got from richards_get_state and hands back unchanged -- so the next step
-   does not evaluate the law there again; any other value replaces it. */
+   the mixed modes an array equal bit for bit, cell by cell, to the
+   context's current psi^n (psi^{n-1}) keeps the cached theta of that state
+   -- the state a caller got from richards_get_state and hands back
+   unchanged -- so the next step does not evaluate the law there again; an
+   array that differs anywhere replaces the cache (the comparison runs on
+   the device, in the same pass as the finiteness check). */
 richards_status richards_set_state(richards_ctx *ctx, const double *psi,
                                    const double *psi_prev, double t);
 
