@@ -3,12 +3,14 @@
 Requests (problem dicts with an ``arrival`` time in seconds) are admitted in
 arrival order as soon as a slot is free and their device memory fits the
 budget (``richards_device_bytes``).  Each admitted request gets its own
-context on its own CUDA stream, keeps its state resident on the device for
-all of its time steps, and runs on a native worker thread
-(``richards_batch_submit``); the kernels of all running requests overlap on
-the device.  Finished requests free their slot and memory at once, so later
-arrivals are admitted while others are still running.  Latency = completion
-time minus arrival time.
+context on its own CUDA stream and keeps its state resident on the device for
+all of its time steps.  Two ways to run them: continuous batching
+(``batched=True``, ``richards_batcher_advance``: the inner cycles of all
+resident requests run as shared launches over a device table of their
+levels), or a native worker thread per request (``richards_batch_submit``)
+whose kernels overlap with the others' on the device.  Finished requests
+free their slot and memory at once, so later arrivals are admitted while
+others are still running.  Latency = completion time minus arrival time.
 """
 from __future__ import annotations
 
