@@ -901,7 +901,11 @@ def test_fmg_pass_beats_one_cycle(mk):
     psi0 = np.array(p["psi0"], dtype=np.float64)
     _, r_start = o.residual(psi0)
     _, r_v = o.residual(o.vcycle(psi0))
-    _, r_fmg = o.residual(o.fmg(psi0))
+    # the pass on a fresh context: a cycle leaves FAS right sides on the
+    # coarse levels, which would stand in for unrestricted ones
+    f = Oracle(W.with_opts(p, fmg_cycles=1))
+    f.prepare(p["dt"], 1)
+    _, r_fmg = f.residual(f.fmg(psi0))
     assert r_fmg < 0.8 * r_v < r_start, (r_start, r_v, r_fmg)
 
 
@@ -914,3 +918,57 @@ def test_fmg_step_reaches_the_cycle_solution():
     assert sa == sb == ORC_OK
     assert ib["resid"] <= 1e-12 and ib["resid0"] == pytest.approx(ia["resid0"])
     assert np.max(np.abs(a.state() - b.state())) <= 1e-9 * np.max(np.abs(a.state()))
+
+
+# ---------------------------------------------------------------------------
+# The cycle's structure (Section 3.2): steps 1-7 of the two-grid FAS step with
+# the coarse solve replaced by gamma recursive cycles (gamma = 2 on the
+# gamma_levels finest levels when gamma_levels > 0, V below), and the
+# coarsest level swept until its defect is coarse_rtol times the initial one
+# or coarse_max_sweeps sweeps have run (R7).  Written here from the oracle's
+# single stages; the recursion must give the oracle's cycle bit for bit.
+# ---------------------------------------------------------------------------
+def _fas_cycle(o, opts, psi, g, lev):
+    nl = o.nlevels
+    if lev == nl - 1:
+        _, d0 = o.residual(psi, g, lev)
+        for _ in range(opts["coarse_max_sweeps"]):
+            psi = o.sweep(psi, g, lev)
+            _, d = o.residual(psi, g, lev)
+            if not d > opts["coarse_rtol"] * d0:
+                break
+        return psi
+    for _ in range(opts["nu1"]):                                   # 1 pre-smoothing
+        psi = o.sweep(psi, g, lev)
+    d, _ = o.residual(psi, g, lev)                                 # 2 defect
+    psibar = o.restrict(psi, lev)                                  # 3 restriction
+    dH = o.restrict(d, lev)
+    gH = o.apply_N(psibar, lev + 1) + dH                           # 4 coarse right side
+    gam = max(opts["cycle_gamma"], 1)
+    if opts["gamma_levels"] > 0 and lev >= opts["gamma_levels"]:
+        gam = 1
+    psiH = psibar.copy()
+    for _ in range(gam):                                           # 5 coarse solve
+        psiH = _fas_cycle(o, opts, psiH, gH, lev + 1)
+    psi = o.prolong_add(psiH - psibar, psi, lev)                   # 6 correction
+    for _ in range(opts["nu2"]):                                   # 7 post-smoothing
+        psi = o.sweep(psi, g, lev)
+    return psi
+
+
+@pytest.mark.parametrize("gamma,glev,nu1,nu2", [(1, 0, 2, 2), (2, 0, 1, 1), (2, 1, 0, 2), (2, 2, 2, 1), (3, 1, 1, 0)])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cycle_is_fas_steps_1_to_7_recursively(dim, gamma, glev, nu1, nu2):
+    shape = (21, 17) if dim == 2 else (13, 10, 9)
+    p = W.random_problem(dim, shape, W.VANGENUCHTEN, 40 + dim, hetero=True, sink=True, newton_iters=0,
+                         cycle_gamma=gamma, gamma_levels=glev, nu1=nu1, nu2=nu2, coarse_max_sweeps=7)
+    o = Oracle(p)
+    assert o.nlevels >= 3
+    o.prepare(p["dt"], 1)
+    psi = np.array(p["psi0"], dtype=np.float64)
+    g = o.g()
+    for _ in range(2):
+        ref = o.vcycle(psi)
+        mine = _fas_cycle(o, p["opts"], psi, g, 0)
+        assert np.array_equal(mine, ref)
+        psi = ref
