@@ -319,8 +319,9 @@ def columns(ncol=4096, seed=5, dt=600.0, nsteps=144, nmin=64, nmax=1024, **optkw
                      p1=alpha[c], p2=nvg[c], p3=0.5)
         bc = _bc([FREE_DRAINAGE, FLUX], [0.0, 0.0])
         # two safeguarded Newton steps per point update (the default): one
-        # step is 6% faster on this workload at tol 1e-8, but long columns
-        # at tol 1e-9 and below then stop making progress and end non-finite
+        # step is 6% faster on this workload, but columns with a top inflow
+        # and a varying initial head then stall in the FP32 inner solve and
+        # end non-finite (the step is rejected with psi^n kept)
         opts = default_opts(kappa_mode=0, kappa=0.0, xi=0.0, precision=1)
         opts.update(optkw)
         out.append(dict(name=f"column{c}_n{m}", dim=1, n=(m, 1, 1), L=(1.0, 1.0, 1.0),
