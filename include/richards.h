@@ -228,15 +228,21 @@ typedef struct {
 richards_status richards_set_materials(richards_ctx *ctx, const richards_material *mats, int nmat,
                                        const unsigned char *index);
 
-/* Boundary conditions (see richards_bc).  EINVAL: unknown kind, free
-   drainage off the bottom face, non-finite value. */
+/* Boundary conditions (see richards_bc) of the operator of Section 2
+   (eq. discrete-strong, written as fluxes: a Dirichlet face contributes a
+   half-cell conductance to the diagonal and its head to g; an inflow q/h
+   and free drainage -Kc/h go into g).  EINVAL: unknown kind, free drainage
+   off the bottom face, non-finite value. */
 richards_status richards_set_bc(richards_ctx *ctx, const richards_bc *bc);
 
-/* Sink S(psi) (reading of assumption (A2)).  EINVAL: not h4 < h3 <= h2 < h1. */
+/* Sink S(psi) (reading of assumption (A2), Section 2: S non-decreasing on
+   its rising branch; Feddes shape times a root-zone profile).  EINVAL: not
+   h4 < h3 <= h2 < h1. */
 richards_status richards_set_sink(richards_ctx *ctx, const richards_sink *sink);
 
 /* State psi^n (host array, ncell doubles) and, for BDF2, psi^{n-1}
-   (nullable: the next BDF2 step then falls back to BDF1).  t: model time.
+   (nullable: the next BDF2 step then falls back to BDF1): the history of
+   eq. fully-bdf1 and of the BDF2 reading.  t: model time.
    EINVAL on a non-finite value (the context is then left as it was).  In
    the mixed modes an array equal bit for bit, cell by cell, to the
    context's current psi^n (psi^{n-1}) keeps the cached theta of that state
@@ -255,8 +261,9 @@ richards_status richards_set_state(richards_ctx *ctx, const double *psi,
 richards_status richards_step(richards_ctx *ctx, double dt, int scheme,
                               richards_step_info *info);
 
-/* nsteps calls of richards_step; stops at the first error.  last receives
-   the last step's statistics. */
+/* nsteps calls of richards_step (eq. fully-bdf1 or the BDF2 reading, one
+   after the other); stops at the first error.  last receives the last
+   step's statistics. */
 richards_status richards_solve(richards_ctx *ctx, double dt, int nsteps, int scheme,
                                richards_step_info *last);
 
@@ -297,7 +304,8 @@ void richards_destroy(richards_ctx *ctx);
 
 /* ---------------------------------------------------------------------
  * Concurrent requests.  richards_batch_submit starts, for each context, a
- * host worker thread that runs nsteps steps on the context's stream; the
+ * host worker thread that runs nsteps steps (richards_step: eq. fully-bdf1
+ * or the BDF2 reading, Section 3.2's cycles) on the context's stream; the
  * contexts' work overlaps on the device when they have distinct streams.
  * While a context runs, every other call on it returns RICH_EBUSY.
  * --------------------------------------------------------------------- */
@@ -383,8 +391,9 @@ richards_status richards_batcher_create(void *stream, int max_contexts, richards
 void richards_batcher_destroy(richards_batcher *b);
 const char *richards_batcher_last_error(const richards_batcher *b);
 
-/* One step of each of the n contexts (dt[k], scheme[k]: as richards_step);
-   returns when all are done.  Every context must be in a mixed mode
+/* One step of each of the n contexts (dt[k], scheme[k]: as richards_step,
+   an implicit step of eq. fully-bdf1 or the BDF2 reading solved by Section
+   3.2's cycles); returns when all are done.  Every context must be in a mixed mode
    (precision 1 or 2) with red-black sweeps and no FMG start, and all must
    share nu1, nu2, cycle_gamma, gamma_levels, coarse_max_sweeps, coarse_rtol
    and inner_cycles.  Work is ordered after what the contexts' streams hold.
@@ -444,8 +453,9 @@ richards_status richards_set_level(richards_ctx *ctx, int level, int which, cons
    ordering 0 only color -1 is accepted: one lexicographic sweep. */
 richards_status richards_sweep(richards_ctx *ctx, int level, int color);
 
-/* d = g - N(psi) on a level (FP64) into the level's defect; *norm gets
-   ||d||_inf (nullable). */
+/* d = g - N(psi) on a level (FP64; N of eq. Nh-def, the defect of FAS
+   step 2, Section 3.2) into the level's defect; *norm gets ||d||_inf
+   (nullable). */
 richards_status richards_residual(richards_ctx *ctx, int level, double *norm);
 
 /* FAS steps 2-4 from `level` to level+1: defect, restriction of iterate and
@@ -453,10 +463,12 @@ richards_status richards_residual(richards_ctx *ctx, int level, double *norm);
    psi_bar_H (FP64). */
 richards_status richards_restrict_tau(richards_ctx *ctx, int level);
 
-/* FAS step 6: psi_level += P (psi_{level+1} - psi_bar_{level+1}) (FP64). */
+/* FAS step 6 (Section 3.2): psi_level += P (psi_{level+1} -
+   psi_bar_{level+1}) (FP64). */
 richards_status richards_prolong(richards_ctx *ctx, int level);
 
-/* One FP64 V-cycle from the finest level (the same launches as a step). */
+/* One FP64 cycle from the finest level (Section 3.2's recursive FAS cycle;
+   the same launches as a step). */
 richards_status richards_vcycle(richards_ctx *ctx);
 
 /* ---------------------------------------------------------------------
@@ -492,9 +504,10 @@ int richards_profile_read(richards_ctx *ctx, richards_kernel_stat *out, int max)
  * block and synchronise the device), plug-ins that may only touch memory
  * handed to them.
  *
- * One implicit step (same arithmetic as richards_step in FP64 mode) of a
- * grid with at most RICHARDS_NOALLOC_MAX_CELLS cells, run in a single thread
- * block.  psi_n, psi_prev (nullable: BDF1 is used) and psi_out are device
+ * One implicit step (eq. fully-bdf1 or the BDF2 reading, solved by the FAS
+ * cycles of Section 3.2 with the point update of eq. point-update: the same
+ * arithmetic as richards_step in FP64 mode) of a grid with at most
+ * RICHARDS_NOALLOC_MAX_CELLS cells, run in a single thread block.  psi_n, psi_prev (nullable: BDF1 is used) and psi_out are device
  * arrays of ncell doubles; psi_out may alias psi_n or psi_prev (both are
  * read before anything is written).  In this call the optional soil fields
  * (Ks_field, p1_field, p2_field) and boundary fields (value_field,
@@ -562,10 +575,12 @@ long long richards_columns_ncell(const richards_columns *batch);
    doubles); psi_prev nullable (the next BDF2 step falls back to BDF1). */
 richards_status richards_columns_set_state(richards_columns *batch, const double *psi, const double *psi_prev);
 
-/* nsteps implicit steps of every column (scheme 1 = BDF1, 2 = BDF2): one
-   persistent launch per length class (columns of more than 512 cells,
-   257-512, at most 256; the two shorter classes on streams of the batch's
-   own, joined to its stream by events); returns once all are done.
+/* nsteps implicit steps of every column (scheme 1 = BDF1 of eq.
+   fully-bdf1, 2 = the BDF2 reading; Section 4.1's column problem, solved by
+   the FAS cycles of Section 3.2): one persistent launch per length class
+   (columns of more than 512 cells, 257-512, at most 256; the two shorter
+   classes on streams of the batch's own, joined to its stream by events);
+   returns once all are done.
    Per-column outcomes are read with richards_columns_stats. */
 richards_status richards_columns_run(richards_columns *batch, double dt, int nsteps, int scheme);
 
