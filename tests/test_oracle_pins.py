@@ -297,6 +297,36 @@ def test_hydrostatic_state_with_face_fields_and_masks(dim):
     assert big.tolist() == (top0 + np.flatnonzero(mask)).tolist()
 
 
+@pytest.mark.parametrize("face", [0, 3, 4])
+def test_face_conductances_restrict_as_the_cell_restriction(face):
+    """A coarse boundary conductance is the full-weighting restriction of the
+    fine face array over the face's two in-plane axes (R5): the numbers that
+    the cell transfer (R6) gives for a 3-d field repeating the fine face
+    array along the face normal (whose restriction rows sum to one).  On a
+    non-square face with a varying boundary head, a transposed in-plane index
+    or a wrong axis breaks it."""
+    n = (9, 7, 6)
+    kinds = [W.NOFLUX] * 6
+    kinds[face] = W.DIRICHLET
+    p = W.random_problem(3, n, W.VANGENUCHTEN, 21, bc_kinds=kinds, hetero=True)
+    ax = face // 2
+    ia, ib = [a for a in range(3) if a != ax]
+    p["bc"]["value_field"][face] = np.random.default_rng(5).uniform(-2.0, -0.05, n[ia] * n[ib])
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    kb0, kb1 = o.array(10 + face, 0), o.array(10 + face, 1)
+    assert np.ptp(kb0) > 0
+    idx = np.indices((n[2], n[1], n[0]))[::-1]          # idx[a] = cell index along axis a (x fastest)
+    f3 = kb0[idx[ia] + n[ia] * idx[ib]]
+    c3 = o.restrict(f3.ravel(), 0)
+    nc = o.level_n(1)
+    cidx = np.indices((nc[2], nc[1], nc[0]))[::-1]
+    on_plane = (cidx[ax] == 0).ravel()
+    ref = np.empty(nc[ia] * nc[ib])
+    ref[(cidx[ia] + nc[ia] * cidx[ib]).ravel()[on_plane]] = c3[on_plane]
+    assert np.max(np.abs(kb1 - ref)) <= 1e-14 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("dim", [1, 2])
 def test_saturated_linear_head_is_exact(dim):
     """Saturated (psi >= 0, K = Ks) flow between two Dirichlet heads: the
