@@ -939,6 +939,35 @@ def test_fmg_pass_beats_one_cycle(mk):
     assert r_fmg < 0.8 * r_v < r_start, (r_start, r_v, r_fmg)
 
 
+@pytest.mark.parametrize("cycles", [1, 2])
+@pytest.mark.parametrize("mk", [p[1] for p in FMG_PROBLEMS], ids=[p[0] for p in FMG_PROBLEMS])
+def test_fmg_pass_is_nested_iteration(mk, cycles):
+    """The pass written out from the oracle's single stages (Section 3.2's
+    nested iteration, R17): right sides g_{l+1} = R g_l and starting iterates
+    psi_{l+1} = R psi_l on the way down; on the way up each level first
+    takes the interpolated change of the coarser one, psi_l += P(psi_{l+1} -
+    R psi_l), then `cycles` cycles on its own right side.  Bit for bit."""
+    p = W.with_opts(mk(), fmg_cycles=cycles)
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    nl = o.nlevels
+    psi = [np.array(p["psi0"], dtype=np.float64)]
+    g = [o.g(0)]
+    for l in range(nl - 1):
+        psi.append(o.restrict(psi[l], l))
+        g.append(o.restrict(g[l], l))
+    start = [x.copy() for x in psi]
+    for _ in range(cycles):
+        psi[nl - 1] = o.vcycle(psi[nl - 1], g[nl - 1], nl - 1)
+    for l in range(nl - 2, -1, -1):
+        psi[l] = o.prolong_add(psi[l + 1] - start[l + 1], psi[l], l)
+        for _ in range(cycles):
+            psi[l] = o.vcycle(psi[l], g[l], l)
+    fresh = Oracle(p)
+    fresh.prepare(p["dt"], 1)
+    assert np.array_equal(fresh.fmg(p["psi0"]), psi[0])
+
+
 def test_fmg_step_reaches_the_cycle_solution():
     """The FMG start changes the iterates, not the solution of the step."""
     p = W.with_opts(FMG_PROBLEMS[1][1](), tol=1e-12, max_cycles=200)
