@@ -731,6 +731,52 @@ def test_point_solve_matches_bracketing_root(model):
         assert abs(x60 - root) <= 1e-12 * max(1.0, abs(root))
 
 
+@pytest.mark.parametrize("model", [W.HAVERKAMP, W.GARDNER, W.VANGENUCHTEN])
+def test_fixed_count_point_solve_takes_plain_newton_steps(model):
+    """With a fixed count k the point solve takes k textbook Newton steps
+    x <- x - F(x)/F'(x), F'(x) = a theta'(x) + S'(x) + c, as long as each
+    lands strictly inside the running bracket (eq. point-update, Section
+    3.1's Newton steps); a damped or a bisected step breaks it."""
+    p = W.random_problem(1, 6, model, 51, sink=True)
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    a = o.a
+    rng = np.random.default_rng(7)
+    cell = p["n"][0] - 1
+    soil = p["soil"]
+    smax = o.array(4, 0)[cell]
+    used = 0
+    for _ in range(40):
+        cc = 10 ** rng.uniform(-3, 1)
+        target = rng.uniform(-3.0, -0.05)
+        f = a * o.soil(cell, target)[0] + o.sink(cell, target)[0] + cc * target
+        x0 = target + rng.uniform(-0.05, 0.05) * max(1.0, abs(target))
+        lo = (f - a * soil["theta_s"] - smax) / cc
+        hi = (f - a * soil["theta_r"]) / cc
+        xs, x, ok = [], min(max(x0, lo), hi), True
+        for _k in range(2):
+            th, dth, _ = o.soil(cell, x)
+            S, dS = o.sink(cell, x)
+            F = a * th + S + cc * x - f
+            if F > 0:
+                hi = x
+            else:
+                lo = x
+            xn = x - F / (a * dth + dS + cc)
+            if not (lo < xn < hi):
+                ok = False
+                break
+            x = xn
+            xs.append(x)
+        if not ok:
+            continue
+        used += 1
+        for k in (1, 2):
+            got, it = o.point_solve(cell, cc, f, x0=x0, newton_iters=k)
+            assert it == k and abs(got - xs[k - 1]) <= 4e-15 * max(1.0, abs(got)), (k, got, xs[k - 1])
+    assert used >= 20
+
+
 # ---------------------------------------------------------------------------
 # Coarse operators (Section 3.2, "complete analogy").
 # ---------------------------------------------------------------------------
