@@ -662,6 +662,24 @@ def test_sweep_orders_by_where_a_perturbation_travels(n, cells):
     assert all(_expected_changes(n, rb, c) != _expected_changes(n, lex, c) for c in cells)
 
 
+@pytest.mark.parametrize("n", [(9,), (5, 4), (3, 4, 3)])
+def test_half_sweeps_are_the_two_colours_of_a_red_black_sweep(n):
+    """Half-sweep colour c updates exactly the cells with (i0 + i1 + i2) mod 2
+    = c, and colour 0 then colour 1 is one red-black sweep, bit for bit (the
+    half-sweeps the GPU stages are compared with)."""
+    p = W.random_problem(len(n), n, W.VANGENUCHTEN, 60, sink=True, newton_iters=0)
+    o = Oracle(p)
+    o.prepare(p["dt"], 1)
+    psi = np.array(p["psi0"], dtype=np.float64) + np.random.default_rng(1).uniform(-0.2, 0.2, W.ncells(p))
+    coords = np.stack(np.unravel_index(np.arange(psi.size), n[::-1])[::-1])
+    colour = coords.sum(axis=0) % 2
+    red = o.sweep(psi, color=0)
+    assert np.array_equal(red[colour == 1], psi[colour == 1]) and np.all(red[colour == 0] != psi[colour == 0])
+    both = o.sweep(red, color=1)
+    assert np.array_equal(both[colour == 0], red[colour == 0]) and np.all(both[colour == 1] != red[colour == 1])
+    assert np.array_equal(both, o.sweep(psi, ordering=1))
+
+
 @pytest.mark.parametrize("ordering", [0, 1])
 @pytest.mark.parametrize("model", [W.HAVERKAMP, W.VANGENUCHTEN])
 def test_theorem31_contraction_per_sweep(ordering, model):
