@@ -82,3 +82,22 @@ def test_bdf2_lagged_state_of_k_and_xi(lag):
     assert np.array_equal(K, o0.Kc(0))
     xi = p["opts"]["xi"]
     assert np.max(np.abs((o.g(0) - o0.g(0)) - xi * star)) <= 1e-15 * np.max(np.abs(o.g(0)))
+
+
+@pytest.mark.parametrize("max_cycles", [1, 60])
+def test_a_step_shifts_the_history_converged_or_not(max_cycles):
+    """After a step -- converged, or stopped at the cycle limit (ENOCONV, the
+    state then being the last iterate, as the C ABI documents) -- the next
+    BDF2 step's history is (the step's result, the state it started from):
+    its lagged state is 2 psi^{n+1} - psi^n bit for bit."""
+    from oracle.oracle import ORC_ENOCONV
+    p = W.random_problem(2, (9, 8), W.GARDNER, 70, scheme=2, tol=1e-14 if max_cycles == 1 else 1e-9,
+                         max_cycles=max_cycles)
+    o = Oracle(p)
+    psi0 = o.state()
+    st, info = o.step(p["dt"], 1)
+    assert st == (ORC_ENOCONV if max_cycles == 1 else ORC_OK), (st, info)
+    psi1 = o.state()
+    assert not np.array_equal(psi1, psi0)
+    o.prepare(p["dt"], 2)
+    assert np.array_equal(o.array(6), 2.0 * psi1 - psi0)
