@@ -798,6 +798,24 @@ def test_fixed_count_point_solve_takes_plain_newton_steps(model):
 # ---------------------------------------------------------------------------
 # Coarse operators (Section 3.2, "complete analogy").
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,cmax", [((8,), 4), ((9,), 4), ((129,), 4), ((7, 10), 4), ((33, 17), 8),
+                                    ((6, 4, 8), 4), ((5, 6, 7), 2), ((256,), 8)])
+def test_hierarchy_halves_every_axis_up_to_the_coarsest_size(n, cmax):
+    """Levels (R6, R7): every axis with more than one cell goes from N to
+    ceil(N/2) until the largest axis has at most coarsest_max_n cells; the
+    spacing of each level is L/N."""
+    dim = len(n)
+    p = W.random_problem(dim, n, W.GARDNER, 3, coarsest_max_n=cmax)
+    o = Oracle(p)
+    want = [list(n) + [1] * (3 - dim)]
+    while max(want[-1]) > cmax:
+        want.append([(x + 1) // 2 if x > 1 else 1 for x in want[-1]])
+    assert o.nlevels == len(want)
+    for lev, w in enumerate(want):
+        assert list(o.level_n(lev)) == w, (lev, o.level_n(lev), w)
+        assert o.cell_volume(lev) == pytest.approx(np.prod([p["L"][a] / w[a] for a in range(dim)]), rel=1e-15)
+
+
 COARSE_CASES = [(1, (8,)), (1, (9,)), (2, (8, 6)), (2, (7, 10)), (3, (6, 4, 8)), (3, (5, 6, 7))]
 
 
