@@ -99,3 +99,24 @@ def test_admission_by_slot_and_memory_budget(monkeypatch, max_active):
     assert dev.peak_active <= max_active
     assert dev.started == sorted(dev.started)        # admitted in arrival order, never overtaken
     assert dev.peak_active >= min(2, max_active)     # requests overlap when they fit
+
+
+def test_realtime_admission_waits_for_each_arrival(monkeypatch):
+    """With realtime=True no request starts before its arrival time (the
+    Poisson trace replayed on the wall clock); latency counts from arrival."""
+    trace = W.serving_trace(rate=200.0, seconds=60.0, seed=6, sizes2d=(129,), sizes3d=(65,), max_requests=8)
+    for k, p in enumerate(trace):
+        p["order"] = k
+        p["arrival"] = 0.03 * (k + 1)
+    budget = 64 * max(serve.request_bytes(p) for p in trace)
+    dev = _FakeDevice(R.lib(), budget, 8)
+    monkeypatch.setattr(R, "lib", lambda *a, **k: dev)
+    monkeypatch.setattr(R, "Solver", _fake_solver_class(dev))
+    srv = serve.Server(budget_bytes=budget, max_active=8, poll_s=1e-3)
+    srv.torch = _FakeTorch
+    results, summary = srv.run(trace, realtime=True)
+    assert summary["completed"] == 8
+    for r in results:
+        assert r["start"] >= r["arrival"], r
+        assert r["latency"] == pytest.approx(r["end"] - r["arrival"]) and r["queue"] >= 0.0
+    assert dev.started == list(range(8))
