@@ -13,6 +13,10 @@ from paper_2606_04292_gb300 import richards as R
 from paper_2606_04292_gb300 import serve
 from paper_2606_04292_gb300 import workloads as W
 
+# a serving loop that never admits or never releases a request spins
+# forever: fail such a regression instead of hanging the suite
+pytestmark = pytest.mark.timeout(120)
+
 
 class _FakeDevice:
     def __init__(self, real, budget, max_active):
