@@ -2,9 +2,12 @@
 
 This module only *describes* problems: grid sizes, soil parameters, boundary
 descriptors, sink parameters, initial states and time-step settings.  It holds
-none of the method's arithmetic (no constitutive law, no operator, no solver),
-so that both the CUDA path and the CPU oracle can consume the same inputs
-without sharing any code that computes a result.
+none of the method's arithmetic (no constitutive law that a result is
+computed with, no operator, no solver), so that both the CUDA path and the
+CPU oracle can consume the same inputs without sharing any code that
+computes a result.  The one law-shaped helper, ``head_at_saturation``,
+inverts Table 1's theta only to choose starting heads for the serving trace:
+any head is a valid input, and no result is checked against it.
 
 Problem layout (a plain ``dict``):
 
