@@ -433,7 +433,8 @@ def gardner_cpu(states):
 def celia_bench(stream):
     """The 1-d infiltration column in full (128 cells over 40 cm, Haverkamp,
     BDF1 dt = 10 s for 36 steps, V(2,2), FP64), red-black and the paper's
-    lexicographic order: wall time of the whole run and cycles per step."""
+    lexicographic order: wall time of the whole run and cycles per step; and
+    the same run in mixed precision through the batched-column solver."""
     import torch
     from paper_2606_04292_gb300 import richards as R
     from paper_2606_04292_gb300 import workloads as W
@@ -454,6 +455,30 @@ def celia_bench(stream):
                       "worst_status": R.STATUS_NAMES[worst], "cycles_per_step": cyc / prob["nsteps"]}
         states[label] = gs.state()
         gs.close()
+    # the same column through the batched-column solver: the whole run in one
+    # launch, FP32 inner cycles inside the float-float outer layer (the path
+    # of Table 3's column); a first one-step run loads the column kernels
+    import numpy as np
+    prob = W.celia_1d(precision=1)
+    try:
+        warm = R.Columns([prob], stream=stream.cuda_stream)
+        warm.run(prob["dt"], 1, 1)
+        warm.close()
+        cols = R.Columns([prob], stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = cols.run(prob["dt"], prob["nsteps"], 1)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        sts = cols.stats()
+        out["columns_mixed_float_float_outer"] = {
+            "total_s": wall, "steps": prob["nsteps"], "run_status": R.STATUS_NAMES.get(st, str(st)),
+            "status": R.STATUS_NAMES.get(int(sts["status"][0]), str(int(sts["status"][0]))),
+            "cycles_per_step": float(sts["cycles"][0]) / prob["nsteps"],
+            "max_abs_dpsi_vs_red_black_fp64": float(np.max(np.abs(cols.state() - states["red_black_fp64"])))}
+        cols.close()
+    except R.RichardsError as e:
+        out["columns_mixed_float_float_outer"] = {"error": str(e)}
     return out, states
 
 
